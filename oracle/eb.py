@@ -1,0 +1,354 @@
+"""Line-by-line embedded-boundary discretisation of the Laplacian (oracle).
+
+Follows Algorithm 1 of the paper:
+  step 1  mask, boundary points (BP) and computational points (CP)  (Sec. 2)
+  step 2  central differences (eq. 3, beta = 1) at the CPs only
+  step 3  line-by-line interpolation at each BP neighbour (Sec. 2.1, eqs. 4-6)
+
+Readings of the paper taken here:
+
+* Unknowns are the CPs only, ordered lexicographically (x fastest); the BP
+  values are eliminated through the interpolant of eq. (6) (Algorithm 1).
+* A = -L is assembled (the SPD sign), interior rows (1/h^2)[2 dim, -1 ...].
+* Closure of one CP k towards a BP neighbour in direction s: the interpolant
+  through (xi_Gamma, u_Gamma) and (xi_1 = x_k, u_k) evaluated at the BP gives
+  u_BP = g_Gamma u_Gamma + g_1 u_k with g_Gamma = h/(h+delta), g_1 =
+  delta/(h+delta), where delta = |x_BP - x_Gamma| (Sec. 2.1).  Substituted in
+  (u_BP - u_k)/h^2 this leaves c_s = g_Gamma = h/(h+delta) on the diagonal of
+  h^2 A and +c_s u_Gamma / h^2 on the right-hand side.
+* When the node beyond the BP is also inside, the paper switches to RBF
+  interpolation (Algorithm 1 step 3).  The line-by-line-only reading used here
+  walks outward from the BP along the grid line to the first node that is not
+  inside and takes the first crossing of Gamma there; delta may then exceed h
+  but c_s stays in (0, 1), so symmetry and strict diagonal dominance hold.
+* The outermost ring of grid nodes must lie outside Omega (the paper assumes
+  the geometry is contained in the grid), otherwise GeometryError.
+* Right-hand side: b = -f + sum_s c_s u_Gamma,s / h^2 for div(grad u) = f.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.sparse as sp
+
+import eb_inputs as ei
+from . import geometry as geo
+
+OUTSIDE, BOUNDARY, COMPUTATIONAL = 0, 1, 2
+
+
+class GeometryError(ValueError):
+    pass
+
+
+@dataclass
+class EBSystem:
+    grid: ei.Grid
+    ls: ei.LevelSet
+    psi: np.ndarray          # full grid
+    cls: np.ndarray          # uint8 full grid: 0 outside, 1 BP, 2 CP
+    cp_nodes: np.ndarray     # int64 [N_C], linear node index of CP k (ascending)
+    cp_of_node: np.ndarray   # int64 full grid (flattened), -1 off CP
+    cut_cp: np.ndarray       # int64 [n_cut], CP index of each cut
+    cut_dir: np.ndarray      # int64 [n_cut], 2*axis + (0 for -, 1 for +)
+    cut_delta: np.ndarray    # float64 [n_cut], distance BP -> Gamma
+    cut_xg: np.ndarray       # float64 [n_cut, dim], intersection point
+    cut_c: np.ndarray        # float64 [n_cut], c_s = h/(h+delta)
+    diag: np.ndarray         # float64 [N_C], D_k = sum_s c_s (h^2 units)
+    A: sp.csr_matrix         # [N_C, N_C], A = -L
+
+    @property
+    def num_cp(self) -> int:
+        return int(self.cp_nodes.size)
+
+    def to_grid(self, v: np.ndarray) -> np.ndarray:
+        out = np.zeros(self.grid.num_nodes, dtype=np.float64)
+        out[self.cp_nodes] = v
+        return out.reshape(self.grid.shape())
+
+    def from_grid(self, g: np.ndarray) -> np.ndarray:
+        return np.asarray(g, dtype=np.float64).reshape(-1)[self.cp_nodes]
+
+
+def strides(grid: ei.Grid):
+    return (1, grid.n[0], grid.n[0] * grid.n[1])
+
+
+def classify(grid: ei.Grid, psi: np.ndarray) -> np.ndarray:
+    """Mask and BP / CP classes (Sec. 2): a BP is inside with fewer than 2*dim
+    inside nearest neighbours, a CP is inside with all of them inside."""
+    inside = psi < 0.0
+    border = np.zeros_like(inside)
+    if grid.dim == 2:
+        border[0, :] = border[-1, :] = border[:, 0] = border[:, -1] = True
+    else:
+        border[0] = border[-1] = True
+        border[:, 0] = border[:, -1] = True
+        border[:, :, 0] = border[:, :, -1] = True
+    if (inside & border).any():
+        raise GeometryError("the geometry touches the outermost ring of grid nodes")
+    cnt = np.zeros(inside.shape, dtype=np.int32)
+    m = inside.astype(np.int32)
+    for ax in range(grid.dim):
+        npax = grid.dim - 1 - ax          # numpy axis of grid axis ax
+        cnt += np.roll(m, 1, axis=npax) + np.roll(m, -1, axis=npax)
+    cls = np.zeros(inside.shape, dtype=np.uint8)
+    cls[inside] = BOUNDARY
+    cls[inside & (cnt == 2 * grid.dim)] = COMPUTATIONAL
+    return cls
+
+
+def build(grid: ei.Grid, ls: ei.LevelSet) -> EBSystem:
+    """Algorithm 1, steps 1-3, for beta = 1."""
+    dim, h = grid.dim, grid.h
+    psi = geo.psi_nodes(grid, ls)
+    cls = classify(grid, psi)
+    flat_cls = cls.reshape(-1)
+    flat_psi = psi.reshape(-1)
+    cp_nodes = np.flatnonzero(flat_cls == COMPUTATIONAL).astype(np.int64)
+    if cp_nodes.size == 0:
+        raise GeometryError("no computational point")
+    cp_of_node = np.full(flat_cls.size, -1, dtype=np.int64)
+    cp_of_node[cp_nodes] = np.arange(cp_nodes.size)
+    st = strides(grid)
+
+    # node coordinates of every node, per axis (x_i = lo + i h)
+    idx = [None] * dim
+    rem = cp_nodes.copy()
+    for ax in range(dim):
+        idx[ax] = rem % grid.n[ax]
+        rem = rem // grid.n[ax]
+
+    cut_cp, cut_dir, cut_delta, cut_xg = [], [], [], []
+    diag = np.zeros(cp_nodes.size, dtype=np.float64)
+    cs_per_dir = []
+    for ax in range(dim):
+        for sgn_bit, sgn in ((0, -1), (1, 1)):
+            nb = cp_nodes + sgn * st[ax]
+            is_bp = flat_cls[nb] == BOUNDARY
+            cs = np.ones(cp_nodes.size, dtype=np.float64)
+            k = np.flatnonzero(is_bp)
+            if k.size:
+                bp = nb[k]
+                # walk outward from the BP to the first node that is not inside
+                m = np.ones(k.size, dtype=np.int64)
+                cur = bp + sgn * st[ax]
+                active = flat_psi[cur] < 0.0
+                while active.any():
+                    m = np.where(active, m + 1, m)
+                    cur = np.where(active, cur + sgn * st[ax], cur)
+                    active = flat_psi[cur] < 0.0
+                # BP coordinates
+                p = []
+                for a2 in range(dim):
+                    ia = idx[a2][k] + (sgn if a2 == ax else 0)
+                    p.append(grid.lo[a2] + ia.astype(np.float64) * h)
+                if ls.kind == ei.LS_QUADRIC:
+                    delta = geo.quadric_line_root(ls, dim, p, ax, float(sgn))
+                else:
+                    ta = (m - 1).astype(np.float64) * h
+                    tb = m.astype(np.float64) * h
+                    axes = np.full(k.size, ax)
+                    delta = geo.star_line_root(ls, p, axes, np.full(k.size, float(sgn)), ta, tb, h)
+                c = h / (h + delta)
+                cs[k] = c
+                xg = np.stack(p, axis=1)
+                xg[:, ax] = p[ax] + sgn * delta
+                cut_cp.append(k)
+                cut_dir.append(np.full(k.size, 2 * ax + sgn_bit))
+                cut_delta.append(delta)
+                cut_xg.append(xg)
+            cs_per_dir.append(cs)
+    # D_k = sum_s c_s, summed in direction order (-x, +x, -y, +y, -z, +z)
+    for cs in cs_per_dir:
+        diag = diag + cs
+
+    if cut_cp:
+        cut_cp_a = np.concatenate(cut_cp)
+        cut_dir_a = np.concatenate(cut_dir)
+        cut_delta_a = np.concatenate(cut_delta)
+        cut_xg_a = np.concatenate(cut_xg, axis=0)
+        order = np.lexsort((cut_dir_a, cut_cp_a))
+        cut_cp_a, cut_dir_a = cut_cp_a[order], cut_dir_a[order]
+        cut_delta_a, cut_xg_a = cut_delta_a[order], cut_xg_a[order]
+    else:
+        cut_cp_a = np.zeros(0, np.int64)
+        cut_dir_a = np.zeros(0, np.int64)
+        cut_delta_a = np.zeros(0)
+        cut_xg_a = np.zeros((0, dim))
+    cut_c_a = h / (h + cut_delta_a)
+
+    A = assemble(grid, cp_nodes, cp_of_node, flat_cls, diag)
+    return EBSystem(grid, ls, psi, cls, cp_nodes, cp_of_node, cut_cp_a, cut_dir_a,
+                    cut_delta_a, cut_xg_a, cut_c_a, diag, A)
+
+
+def assemble(grid, cp_nodes, cp_of_node, flat_cls, diag) -> sp.csr_matrix:
+    """Eq. (3) with beta = 1 at the CPs (Algorithm 1 step 2); BP neighbours are
+    dropped from the off-diagonal pattern (their value is eliminated by the
+    closure, step 3), CP neighbours give -1/h^2."""
+    h2 = grid.h * grid.h
+    st = strides(grid)
+    rows = [np.arange(cp_nodes.size)]
+    cols = [np.arange(cp_nodes.size)]
+    vals = [diag / h2]
+    for ax in range(grid.dim):
+        for sgn in (-1, 1):
+            nb = cp_nodes + sgn * st[ax]
+            j = cp_of_node[nb]
+            k = np.flatnonzero(j >= 0)
+            rows.append(k)
+            cols.append(j[k])
+            vals.append(np.full(k.size, -1.0 / h2))
+    r = np.concatenate(rows)
+    c = np.concatenate(cols)
+    v = np.concatenate(vals)
+    A = sp.csr_matrix((v, (r, c)), shape=(cp_nodes.size, cp_nodes.size))
+    A.sort_indices()
+    return A
+
+
+def rhs(eb: EBSystem, f_nodes: np.ndarray, ugamma: np.ndarray) -> np.ndarray:
+    """b = -f + sum_s c_s u_Gamma,s / h^2 (Sec. 2.1, the g_Gamma u_Gamma term;
+    Algorithm 1 step 3 correction of b)."""
+    h2 = eb.grid.h * eb.grid.h
+    b = -eb.from_grid(f_nodes)
+    add = np.zeros(eb.num_cp)
+    np.add.at(add, eb.cut_cp, eb.cut_c * ugamma / h2)
+    return b + add
+
+
+def apply(eb: EBSystem, x: np.ndarray) -> np.ndarray:
+    return eb.A @ x
+
+
+# ------------------------------------------------ Lemma 1 / Theorem 2
+
+def line_segments(eb: EBSystem):
+    """Split every grid line of CPs into segments of consecutive CPs and return
+    (axis, n, a, b) per segment, a / b the first / last diagonal entry of
+    h^2 D_xx (resp. D_yy, D_zz) on that segment (Sec. 2.3, eqs. 11-12)."""
+    grid = eb.grid
+    st = strides(grid)
+    flat_cls = eb.cls.reshape(-1)
+    # per-direction c_s for every CP
+    cdir = np.ones((eb.num_cp, 2 * grid.dim))
+    cdir[eb.cut_cp, eb.cut_dir] = eb.cut_c
+    out = []
+    for ax in range(grid.dim):
+        is_cp = flat_cls == COMPUTATIONAL
+        nodes = eb.cp_nodes
+        prev_cp = is_cp[nodes - st[ax]]
+        next_cp = is_cp[nodes + st[ax]]
+        starts = nodes[~prev_cp]
+        for s in starts:
+            n = 1
+            cur = s
+            while is_cp[cur + st[ax]]:
+                cur += st[ax]
+                n += 1
+            k0 = eb.cp_of_node[s]
+            k1 = eb.cp_of_node[cur]
+            lo_c = cdir[k0, 2 * ax]
+            hi_c = cdir[k1, 2 * ax + 1]
+            if n == 1:
+                a = lo_c + hi_c
+                b = a
+            else:
+                a = 1.0 + lo_c
+                b = 1.0 + hi_c
+            out.append((ax, n, a, b))
+        del prev_cp, next_cp
+    return out
+
+
+def lemma1_holds(n: int, a: float, b: float) -> bool:
+    """The three conditions of Lemma 1 for D^(n)(a, b) to be SPD."""
+    if n == 1:
+        return a > 0
+    if n == 2:
+        return a > 0 and a * b > 1
+    r = (n - 2) / (n - 1)
+    return a > r and b > r and a > ((n - 2) * b - (n - 3)) / ((n - 1) * b - (n - 2))
+
+
+def tridiag_segment(n: int, a: float, b: float) -> np.ndarray:
+    """The matrix D^(n)(a, b) of eq. (11)."""
+    M = 2.0 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    M[0, 0] = a
+    M[-1, -1] = b if n > 1 else a
+    return M
+
+
+def directional_parts(eb: EBSystem):
+    """h^2 A split as the sum over axes of the 1D operators (Theorem 2):
+    returns one CSR per axis with diagonal c_lo + c_hi and -1 to CP neighbours."""
+    grid = eb.grid
+    st = strides(grid)
+    cdir = np.ones((eb.num_cp, 2 * grid.dim))
+    cdir[eb.cut_cp, eb.cut_dir] = eb.cut_c
+    parts = []
+    for ax in range(grid.dim):
+        r = [np.arange(eb.num_cp)]
+        c = [np.arange(eb.num_cp)]
+        v = [cdir[:, 2 * ax] + cdir[:, 2 * ax + 1]]
+        for sgn in (-1, 1):
+            j = eb.cp_of_node[eb.cp_nodes + sgn * st[ax]]
+            k = np.flatnonzero(j >= 0)
+            r.append(k)
+            c.append(j[k])
+            v.append(-np.ones(k.size))
+        parts.append(sp.csr_matrix((np.concatenate(v), (np.concatenate(r), np.concatenate(c))),
+                                   shape=(eb.num_cp, eb.num_cp)))
+    return parts
+
+
+# ------------------------------------------------ ghost-point negative control
+
+def ghost_point_operator(grid: ei.Grid, ls: ei.LevelSet) -> sp.csr_matrix:
+    """Exterior ghost-point closure (Sec. 1, Sec. 2.1 right panel of Fig. 3):
+    every inside node is an unknown; an outside neighbour at distance theta h
+    from the boundary (theta in (0, 1]) is extrapolated linearly, which puts
+    1/theta on the diagonal of h^2 A.  Used only as the negative control of the
+    small-cell-stiffness tests."""
+    dim, h = grid.dim, grid.h
+    psi = geo.psi_nodes(grid, ls)
+    inside = (psi < 0.0).reshape(-1)
+    nodes = np.flatnonzero(inside)
+    idx_of = np.full(inside.size, -1, dtype=np.int64)
+    idx_of[nodes] = np.arange(nodes.size)
+    st = strides(grid)
+    ii = []
+    rem = nodes.copy()
+    for ax in range(dim):
+        ii.append(rem % grid.n[ax])
+        rem //= grid.n[ax]
+    diag = np.zeros(nodes.size)
+    rows, cols, vals = [], [], []
+    for ax in range(dim):
+        for sgn in (-1, 1):
+            nb = nodes + sgn * st[ax]
+            j = idx_of[nb]
+            inn = j >= 0
+            k = np.flatnonzero(inn)
+            rows.append(k)
+            cols.append(j[k])
+            vals.append(-np.ones(k.size))
+            diag[k] += 1.0
+            k2 = np.flatnonzero(~inn)
+            if k2.size:
+                p = [grid.lo[a] + ii[a][k2].astype(np.float64) * h for a in range(dim)]
+                if ls.kind == ei.LS_QUADRIC:
+                    t = geo.quadric_line_root(ls, dim, p, ax, float(sgn))
+                else:
+                    t = geo.star_line_root(ls, p, np.full(k2.size, ax), np.full(k2.size, float(sgn)),
+                                           np.zeros(k2.size), np.full(k2.size, h), h)
+                theta = np.maximum(t / h, 1e-300)
+                diag[k2] += 1.0 / theta
+    rows.append(np.arange(nodes.size))
+    cols.append(np.arange(nodes.size))
+    vals.append(diag)
+    M = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(nodes.size, nodes.size)) / (h * h)
+    return M

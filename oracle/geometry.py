@@ -1,0 +1,157 @@
+"""Level sets, the node mask and grid-line / boundary intersections (oracle).
+
+Sec. 2: the mask m_ij is 1 inside Omega and 0 outside, read off the sign of the
+level set psi.  Reading of the sign convention: inside <=> psi < 0 strictly
+(psi = 0 counts as outside).
+
+Two descriptor families:
+
+* quadric   psi = sum_a (y_a / s_a)^2 - 1,  y = Q^T (x - c)   (circle, sphere,
+            rotated ellipsoid).  Evaluated in the fixed operation order
+            t_d = x_d - c_d;  y_a = (Q[0][a] t_0 + Q[1][a] t_1) + Q[2][a] t_2;
+            w_a = y_a / s_a;  psi = ((w_0 w_0 + w_1 w_1) + w_2 w_2) - 1,
+            every operation an IEEE-rounded FP64 operation.
+* star2d    psi = rho - r(phi), rho = |x - c|, phi = atan2(y - c_y, x - c_x),
+            r(phi) = r0 + sum_k a_k sin(k phi + p_k) (summed in list order).
+
+Grid-line roots (Sec. 2.1: psi(xi_Gamma, y_j) = 0, "found by a root-finding
+algorithm such as the secant method"):
+
+* quadric: psi along the line x(t) = p + sign t e_axis is the quadratic
+  alpha t^2 + beta t + gamma, solved in closed form for its root t > 0
+  (p inside, gamma < 0, so exactly one positive root).
+* star2d: Illinois (safeguarded secant) iteration on the bracket
+  [last inside node, first outside node].
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import eb_inputs as ei
+
+
+def quadric_parts(ls: ei.LevelSet, dim: int):
+    Q = np.asarray(ls.rot, dtype=np.float64).reshape(3, 3)
+    c = np.asarray(ls.center, dtype=np.float64)
+    s = np.asarray(ls.semi, dtype=np.float64)
+    return Q, c, s
+
+
+def psi_points(ls: ei.LevelSet, dim: int, pts):
+    """psi at points; ``pts`` is a list of ``dim`` coordinate arrays."""
+    if ls.kind == ei.LS_QUADRIC:
+        Q, c, s = quadric_parts(ls, dim)
+        t = [pts[d] - c[d] for d in range(dim)]
+        w = []
+        for a in range(dim):
+            y = Q[0][a] * t[0] + Q[1][a] * t[1]
+            if dim == 3:
+                y = y + Q[2][a] * t[2]
+            w.append(y / s[a])
+        acc = w[0] * w[0] + w[1] * w[1]
+        if dim == 3:
+            acc = acc + w[2] * w[2]
+        return acc - 1.0
+    if ls.kind == ei.LS_STAR2D:
+        dx = pts[0] - ls.center[0]
+        dy = pts[1] - ls.center[1]
+        rho = np.sqrt(dx * dx + dy * dy)
+        phi = np.arctan2(dy, dx)
+        r = np.full_like(rho, ls.r0)
+        for k, a, p in zip(ls.ks, ls.amps, ls.phases):
+            r = r + a * np.sin(k * phi + p)
+        return rho - r
+    raise ValueError("unknown level-set kind")
+
+
+def psi_nodes(grid: ei.Grid, ls: ei.LevelSet) -> np.ndarray:
+    """psi on the full grid, numpy shape grid.shape() (x fastest)."""
+    pts = ei.grid_points(grid)
+    return psi_points(ls, grid.dim, list(pts))
+
+
+def quadric_line_root(ls: ei.LevelSet, dim: int, p, axis: int, sign):
+    """Positive root t of psi(p + sign t e_axis) = 0 for a quadric (p inside).
+
+    alpha = sum_a u_a^2 with u_a = Q[axis][a] / s_a;
+    beta  = 2 sign sum_a w_a u_a with w_a = y_a(p) / s_a;
+    gamma = psi(p) < 0.
+    t = -2 gamma / (beta + sqrt(disc)) if beta >= 0 else (sqrt(disc) - beta) / (2 alpha),
+    disc = beta^2 - 4 alpha gamma (the two cancellation-free forms of the root).
+    Vectorised over the points in ``p`` (list of coordinate arrays), with
+    ``axis`` an integer array and ``sign`` an array of +-1.0.
+    """
+    Q, c, s = quadric_parts(ls, dim)
+    t = [p[d] - c[d] for d in range(dim)]
+    w = []
+    for a in range(dim):
+        y = Q[0][a] * t[0] + Q[1][a] * t[1]
+        if dim == 3:
+            y = y + Q[2][a] * t[2]
+        w.append(y / s[a])
+    u = [Q[axis, a] / s[a] for a in range(dim)]
+    alpha = u[0] * u[0] + u[1] * u[1]
+    dot = w[0] * u[0] + w[1] * u[1]
+    gamma = w[0] * w[0] + w[1] * w[1]
+    if dim == 3:
+        alpha = alpha + u[2] * u[2]
+        dot = dot + w[2] * u[2]
+        gamma = gamma + w[2] * w[2]
+    gamma = gamma - 1.0
+    beta = 2.0 * (sign * dot)
+    disc = beta * beta - 4.0 * alpha * gamma
+    sq = np.sqrt(disc)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t_pos = (-2.0 * gamma) / (beta + sq)
+        t_neg = (sq - beta) / (2.0 * alpha)
+    return np.where(beta >= 0.0, t_pos, t_neg)
+
+
+def star_line_root(ls: ei.LevelSet, p, axis, sign, ta, tb, h, maxit: int = 100):
+    """Root of g(t) = psi(p + sign t e_axis) in [ta, tb], g(ta) < 0 <= g(tb).
+
+    Illinois variant of regula falsi: the secant point of the current bracket
+    replaces the end with the same sign of g; when the same end is kept twice
+    in a row, the kept end's g value is halved.  Stops when g(t) == 0 or when
+    the iterate moves by at most 1e-15 h; vectorised over the cuts.
+    """
+    p = [np.asarray(v, dtype=np.float64) for v in p]
+
+    def g(t):
+        q = [p[0].copy(), p[1].copy()]
+        for a in (0, 1):
+            m = axis == a
+            q[a] = np.where(m, p[a] + sign * t, p[a])
+        return psi_points(ls, 2, q)
+
+    ta = np.asarray(ta, dtype=np.float64).copy()
+    tb = np.asarray(tb, dtype=np.float64).copy()
+    fa = g(ta)
+    fb = g(tb)
+    t = tb.copy()
+    done = fb == 0.0
+    side = np.zeros_like(ta)
+    told = ta.copy()
+    for _ in range(maxit):
+        act = ~done
+        if not act.any():
+            break
+        tn = (ta * fb - tb * fa) / (fb - fa)
+        tn = np.where(act, tn, t)
+        ft = g(tn)
+        t = np.where(act, tn, t)
+        hit0 = act & (ft == 0.0)
+        lower = act & (ft < 0.0)
+        upper = act & (ft > 0.0)
+        # keep bracket [ta, tb] with g(ta) < 0 < g(tb)
+        fb = np.where(lower & (side == -1), 0.5 * fb, fb)
+        fa = np.where(upper & (side == 1), 0.5 * fa, fa)
+        ta = np.where(lower, tn, ta)
+        fa = np.where(lower, ft, fa)
+        tb = np.where(upper, tn, tb)
+        fb = np.where(upper, ft, fb)
+        side = np.where(lower, -1.0, np.where(upper, 1.0, side))
+        conv = act & (np.abs(tn - told) <= 1e-15 * h)
+        told = np.where(act, tn, told)
+        done = done | hit0 | conv
+    return t

@@ -1,0 +1,112 @@
+"""Krylov solvers, dense reference solves, spectra and time stepping (oracle).
+
+* CG / PCG: Algorithm 1 step 4 (CG with an AMG preconditioner, Sec. 3
+  preamble).  Reading of "relative residual": ||b - A x_k||_2 / ||b||_2 on the
+  recurrence residual; at exit the true residual is recomputed and the
+  iteration continues if it does not meet the tolerance.
+* Dense Cholesky: the textbook solve used to pin CG / PCG on tiny grids.
+* Lanczos extremes (ARPACK through scipy): the spectrum statements of Sec. 1
+  and Sec. 3.1 (eigenvalues bounded like the periodic problem).
+* Leapfrog: the theta-scheme of Sec. 3.5 at theta = 0,
+  u^{n+1} = 2 u^n - u^{n-1} - dt^2 A u^n (homogeneous Dirichlet data).
+* theta-method heat step (Sec. 3.4 uses Crank-Nicolson, theta = 1/2; theta = 1
+  is backward Euler):
+  (I/dt + theta A) u^{n+1} = (I/dt - (1-theta) A) u^n + theta b^{n+1}
+  + (1-theta) b^n, with b the right-hand side of -L u = b for the source F and
+  the boundary data at that time (b = F + sum_s c_s u_Gamma / h^2).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+
+@dataclass
+class SolveStats:
+    iterations: int
+    rel_residual: float
+    true_rel_residual: float
+    converged: bool
+
+
+def pcg(A, b, x0=None, M=None, rtol=1e-10, maxit=10000):
+    """Preconditioned CG; ``M`` maps r -> z (None = identity)."""
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    bnorm = float(np.linalg.norm(b))
+    if bnorm == 0.0:
+        return np.zeros_like(b), SolveStats(0, 0.0, 0.0, True)
+    r = b - A @ x
+    it = 0
+    while True:
+        if np.linalg.norm(r) / bnorm <= rtol:
+            break
+        z = r if M is None else M(r)
+        p = z.copy()
+        rz = float(r @ z)
+        conv = False
+        while it < maxit:
+            q = A @ p
+            pq = float(p @ q)
+            alpha = rz / pq
+            x = x + alpha * p
+            r = r - alpha * q
+            it += 1
+            if np.linalg.norm(r) / bnorm <= rtol:
+                conv = True
+                break
+            z = r if M is None else M(r)
+            rz_new = float(r @ z)
+            beta = rz_new / rz
+            p = z + beta * p
+            rz = rz_new
+        r = b - A @ x
+        if not conv or np.linalg.norm(r) / bnorm <= rtol or it >= maxit:
+            break
+    tr = float(np.linalg.norm(b - A @ x)) / bnorm
+    return x, SolveStats(it, float(np.linalg.norm(r)) / bnorm, tr, tr <= rtol)
+
+
+def dense_cholesky_solve(A, b):
+    Ad = A.toarray() if sp.issparse(A) else np.asarray(A)
+    c = sla.cho_factor(Ad, lower=True)
+    return sla.cho_solve(c, b)
+
+
+def extreme_eigs(A):
+    """(lambda_min, lambda_max) of the SPD matrix A."""
+    n = A.shape[0]
+    if n <= 2000:
+        w = np.linalg.eigvalsh(A.toarray())
+        return float(w[0]), float(w[-1])
+    lmax = spla.eigsh(A, k=1, which="LA", return_eigenvectors=False, tol=1e-10)[0]
+    lmin = spla.eigsh(A, k=1, sigma=0.0, which="LM", return_eigenvectors=False, tol=1e-10)[0]
+    return float(lmin), float(lmax)
+
+
+def leapfrog(A, u_prev, u_cur, dt, nsteps):
+    """Returns (u^{N-1}, u^N) after ``nsteps`` steps from (u^{-1}, u^0)."""
+    a, b = np.array(u_prev, dtype=np.float64), np.array(u_cur, dtype=np.float64)
+    dt2 = dt * dt
+    for _ in range(nsteps):
+        a, b = b, 2.0 * b - a - dt2 * (A @ b)
+    return a, b
+
+
+def leapfrog_energy(A, u_n, u_np1, dt):
+    """Discrete energy ||(u^{n+1}-u^n)/dt||^2 + <u^{n+1}, A u^n>, conserved
+    exactly by the leapfrog recursion for symmetric A."""
+    v = (u_np1 - u_n) / dt
+    return float(v @ v + u_np1 @ (A @ u_n))
+
+
+def theta_heat_step(A, u, dt, theta, b_next, b_cur, M=None, rtol=1e-10, maxit=1000):
+    """One theta-method step; warm start from u^n."""
+    n = A.shape[0]
+    I = sp.identity(n, format="csr")
+    lhs = (I / dt + theta * A).tocsr()
+    r = u / dt - (1.0 - theta) * (A @ u) + theta * b_next + (1.0 - theta) * b_cur
+    return pcg(lhs, r, x0=u, M=M, rtol=rtol, maxit=maxit)
