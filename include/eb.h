@@ -1,0 +1,222 @@
+/*
+ * eb.h -- C ABI of the GB300 (sm_103a) embedded-boundary Laplacian library.
+ *
+ * The method: Peng, Appelo & Liu, "Universal AMG accelerated embedded boundary
+ * method without small cell stiffness" (arXiv 2204.06083).  Dirichlet problems
+ * on a domain Omega embedded in a uniform Cartesian grid are discretised by
+ * central differences (eq. 3, beta = 1) at the computational points (CPs,
+ * Sec. 2); the values at the interior boundary points (BPs) are eliminated by
+ * the line-by-line interpolant of Sec. 2.1 (eqs. 4-6), which changes only the
+ * diagonal of the matrix.  The resulting A = -L is symmetric and diagonally
+ * dominant; it is solved by CG with an AMG preconditioner (Algorithm 1 step 4)
+ * and marched in time by the theta-scheme of Sec. 3.5 (theta = 0: leapfrog)
+ * and by the theta-method for the heat equation (Sec. 3.4).
+ *
+ * Conventions shared by every call
+ *   - Every call returns an eb_status; EB_OK is 0.  eb_last_error() gives a
+ *     thread-local message for the last failing call on this host thread.
+ *     No C++ exception crosses this boundary.
+ *   - Vectors are caller-owned DEVICE pointers in the full-grid layout: one
+ *     entry per grid node, node (i, j, k) at i + n0 (j + n1 k) (x fastest),
+ *     n0*n1*n2 entries.  The entries at nodes that are not CPs are ignored on
+ *     input.  On output every node of the "active tiles" (the tiles of the
+ *     grid that contain at least one CP, see eb_info) is written, with 0 at
+ *     the non-CP nodes; nodes outside the active tiles are never written, so
+ *     callers that read the whole grid should zero-initialise outputs once.
+ *   - Geometry and option structs are HOST pointers read during the call.
+ *   - Calls that take a cudaStream_t are asynchronous on that stream unless
+ *     noted "synchronous" (those read a result back to the host).
+ *   - Handles own all their device memory and are released by *_destroy.
+ */
+#ifndef EB_H_
+#define EB_H_
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EB_OK = 0,
+  EB_ERR_INVALID = 1,        /* bad argument, size or handle */
+  EB_ERR_GEOMETRY = 2,       /* Omega touches the outermost node ring, or no CP */
+  EB_ERR_CUDA = 3,           /* a CUDA runtime call failed (message has details) */
+  EB_ERR_NONFINITE = 4,      /* NaN / Inf in an input or a reduction */
+  EB_ERR_NO_CONVERGENCE = 5, /* maxit reached; statistics are still filled */
+  EB_ERR_BREAKDOWN = 6,      /* p^T A p <= 0 or r^T z <= 0 in CG */
+  EB_ERR_TIMEOUT = 7,        /* a device-wide barrier gave up waiting */
+  EB_ERR_OOM = 8,            /* device allocation failed or a capacity was exceeded */
+  EB_ERR_NOT_IMPLEMENTED = 9
+} eb_status;
+
+typedef enum { EB_F64 = 0, EB_F32 = 1, EB_BF16 = 2 } eb_prec;
+
+/* Uniform grid: n[a] nodes on axis a at lo[a] + i h, i = 0..n[a]-1 (Sec. 2).
+ * dim is 2 or 3; for dim 2, n[2] must be 1.  n[0] must be a multiple of 2. */
+typedef struct {
+  int dim;
+  int n[3];
+  double lo[3];
+  double h;
+} eb_grid;
+
+/* Level set psi, psi < 0 strictly inside Omega (Sec. 2, mask m_ij).
+ *  EB_LS_QUADRIC: psi = sum_a (y_a/semi[a])^2 - 1, y = Q^T (x - center),
+ *                 Q = rot (row-major 3x3; only the leading dim x dim block is
+ *                 used in 2D).  Circle, sphere and rotated ellipsoid.
+ *                 Grid-line roots are found in closed form.
+ *  EB_LS_STAR2D:  psi = |x - c| - r(phi), r(phi) = r0 + sum_k a[k] sin(k[k]
+ *                 phi + p[k]), phi = atan2(y - c_y, x - c_x); 2D only.  Grid-
+ *                 line roots by the Illinois (safeguarded secant) iteration,
+ *                 the secant root finder named in Sec. 2.1. */
+typedef enum { EB_LS_QUADRIC = 0, EB_LS_STAR2D = 1 } eb_ls_kind;
+
+#define EB_STAR_MAX_TERMS 16
+typedef struct {
+  int kind;
+  double center[3];
+  double semi[3];
+  double rot[9];
+  double r0;
+  int nk;
+  int k[EB_STAR_MAX_TERMS];
+  double a[EB_STAR_MAX_TERMS];
+  double p[EB_STAR_MAX_TERMS];
+} eb_levelset;
+
+typedef struct eb_handle eb_handle;
+typedef struct amg_handle amg_handle;
+
+typedef struct {
+  int64_t num_nodes;     /* n0 n1 n2 */
+  int64_t num_cp;        /* N_C, the number of unknowns (Algorithm 1 step 1) */
+  int64_t num_bp;        /* interior boundary points */
+  int64_t num_cut;       /* (CP, direction) pairs with a BP neighbour */
+  int64_t num_far;       /* cuts whose boundary crossing lies beyond the BP's next node (delta > h) */
+  int64_t num_tiles;     /* active tiles (tiles holding >= 1 CP) */
+  int tile[3];           /* tile extents in nodes */
+  double max_delta_over_h;
+  double min_abs_psi;    /* smallest |psi| over all nodes: the classification margin */
+} eb_info_t;
+
+/* Algorithm 1 steps 1-3 on the device: classifies every node (mask, BP, CP),
+ * numbers the CPs lexicographically, finds for every CP and axis direction
+ * whose neighbour is a BP the first crossing of Gamma walking outward from the
+ * BP along the grid line (delta = distance BP -> Gamma), and forms the
+ * diagonal D_k = sum_s c_s with c_s = 1 towards a CP and c_s = h/(h+delta)
+ * towards a BP (Sec. 2.1: g_Gamma of eq. 6 evaluated at the BP).
+ * Synchronous (reads N_C back).  EB_ERR_GEOMETRY when an inside node lies on
+ * the outermost ring of the grid or when there is no CP. */
+int eb_build(const eb_grid* grid, const eb_levelset* ls, eb_handle** out, cudaStream_t stream);
+void eb_destroy(eb_handle* eb);
+int eb_info(const eb_handle* eb, eb_info_t* out);
+
+/* Node classes as one byte per node (full grid), written to a device buffer
+ * of num_nodes bytes: 0 outside, 0x40 BP, 0x80|m CP where bit s of m (s = 2
+ * axis + (0 for -, 1 for +)) marks a BP neighbour in direction s. */
+int eb_classes(const eb_handle* eb, uint8_t* code_dev, cudaStream_t stream);
+/* Per-CP data, device buffers of num_cp entries: the node index of CP k and
+ * its diagonal D_k in units of 1/h^2. */
+int eb_cp_data(const eb_handle* eb, int32_t* cp_node_dev, double* diag_dev, cudaStream_t stream);
+/* Per-cut data, device buffers of num_cut entries, ordered by (CP, direction):
+ * CP index, direction s, delta, and the crossing point (num_cut x dim, row-major).
+ * Any pointer may be NULL. */
+int eb_cuts(const eb_handle* eb, int32_t* cut_cp_dev, int32_t* cut_dir_dev, double* delta_dev,
+            double* xg_dev, cudaStream_t stream);
+
+/* Right-hand side of A u = b for div(grad u) = f with u = u_Gamma on Gamma:
+ * b_k = -f_k + sum_s c_s u_Gamma,s / h^2 (the g_Gamma u_Gamma term of
+ * Sec. 2.1).  f: full grid; ugamma: one value per cut (eb_cuts order);
+ * b: full grid output. */
+int eb_rhs(const eb_handle* eb, const double* f_dev, const double* ugamma_dev, double* b_dev,
+           cudaStream_t stream);
+
+/* y = A x, A = -L of eq. 3 with the line-by-line diagonal (Sec. 2.1), matrix
+ * free.  x and y have the element type of prec (double, float, bf16). */
+int eb_apply(const eb_handle* eb, int prec, const void* x_dev, void* y_dev, cudaStream_t stream);
+
+/* ---------------------------------------------------------------- AMG + PCG */
+typedef enum { EB_PC_AMG = 0, EB_PC_JACOBI = 1, EB_PC_NONE = 2 } eb_pc_kind;
+
+typedef struct {
+  int max_levels;        /* default 25 */
+  int coarse_max;        /* coarsen until n <= coarse_max (default 1024) */
+  double strength;       /* theta of |a_ij| >= theta sqrt(a_ii a_jj), default 0.08 */
+  int cheb_degree;       /* Chebyshev smoother degree, default 2 */
+  int vcycle_prec;       /* EB_F64 (default) or EB_F32: storage of level vectors/matrices */
+} amg_opts;
+
+typedef struct {
+  int num_levels;
+  int64_t rows[32];
+  int64_t nnz[32];
+  double operator_complexity;
+  double setup_ms;
+} amg_info_t;
+
+/* Smoothed-aggregation AMG hierarchy for sigma I + A (sigma = shift >= 0;
+ * sigma = 1/dt for the implicit heat step).  The paper uses a library AMG
+ * (Sec. 3, first paragraph); this hierarchy is deterministic: strength
+ * |a_ij| >= theta sqrt(a_ii a_jj); distance-2 maximal independent set with
+ * priorities (lowbias32 hash of the index, index); aggregates grown from its
+ * nodes; P = (I - 4/(3 rho) D^-1 A) P_hat; Galerkin A_c = P^T A P; dense
+ * Cholesky on the coarsest level.  opts may be NULL for the defaults.
+ * Synchronous. */
+int amg_setup(const eb_handle* eb, double shift, const amg_opts* opts, amg_handle** out, cudaStream_t stream);
+void amg_destroy(amg_handle* amg);
+int amg_info(const amg_handle* amg, amg_info_t* out);
+/* Copies of one level for inspection: CSR of A_l (which = 0) or P_l (which =
+ * 1) into caller device buffers sized from amg_info (rows + 1, nnz), and the
+ * aggregate id of each row of level l (which = 2, into col_dev). */
+int amg_level_copy(const amg_handle* amg, int level, int which, int32_t* rowptr_dev, int32_t* col_dev,
+                   double* val_dev, cudaStream_t stream);
+/* z = M^-1 r: one symmetric V-cycle (Chebyshev pre/post smoothing). */
+int amg_vcycle(const amg_handle* amg, const double* r_dev, double* z_dev, cudaStream_t stream);
+
+typedef struct {
+  int precond;           /* eb_pc_kind, default EB_PC_AMG */
+  int check_every;       /* host convergence check period in iterations (default 1) */
+  int use_graph;         /* capture the iteration in a CUDA graph (default 1) */
+} pcg_opts;
+
+typedef struct {
+  int iterations;
+  double rel_residual;       /* ||r_k|| / ||b|| of the recurrence at exit */
+  double true_rel_residual;  /* ||b - A x|| / ||b|| recomputed at exit */
+  double solve_ms;
+  int converged;
+} pcg_stats;
+
+/* Solves (sigma I + A) x = b by PCG (Algorithm 1 step 4) with the
+ * preconditioner of opts, stopping when ||r_k||_2 / ||b||_2 <= rtol; at exit
+ * the true residual is recomputed and the iteration continues if it misses
+ * rtol.  x holds the initial guess on entry.  Synchronous (fills stats).
+ * Returns EB_ERR_NO_CONVERGENCE after maxit iterations. */
+int pcg_solve(const amg_handle* amg, const double* b_dev, double* x_dev, double rtol, int maxit,
+              const pcg_opts* opts, pcg_stats* stats, cudaStream_t stream);
+
+/* One theta-method step of u_t = L u + F (Sec. 3.4 uses theta = 1/2; theta = 1
+ * is backward Euler): (I/dt + theta A) u1 = (I/dt - (1-theta) A) u0 + theta
+ * b1 + (1-theta) b0, where b = eb_rhs(-F, u_Gamma) at the two times.  amg
+ * must have been set up with shift = 1/(theta dt).  u is overwritten with u1
+ * (warm start from u0).  b0 may be NULL when theta = 1. */
+int heat_step(const amg_handle* amg, double dt, double theta, const double* b1_dev, const double* b0_dev,
+              double* u_dev, double rtol, int maxit, pcg_stats* stats, cudaStream_t stream);
+
+/* nsteps of the explicit leapfrog scheme (the theta-scheme of Sec. 3.5 with
+ * theta = 0): u^{n+1} = 2 u^n - u^{n-1} - dt^2 A u^n (homogeneous Dirichlet
+ * data).  On entry (u_prev, u_cur) = (u^{n-1}, u^n); on exit they hold
+ * (u^{n+nsteps-1}, u^{n+nsteps}).  One persistent cooperative launch; its
+ * grid-wide barrier gives up after a bounded spin and returns EB_ERR_TIMEOUT.
+ * prec: EB_F64 or EB_F32 element type of both fields. */
+int wave_step(const eb_handle* eb, int prec, double dt, void* u_prev_dev, void* u_cur_dev, int nsteps,
+              cudaStream_t stream);
+
+const char* eb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EB_H_ */

@@ -1,0 +1,344 @@
+"""Python binding of the GB300 embedded-boundary Laplacian library.
+
+Thin ctypes layer over the C ABI of ``include/eb.h`` (``_lib/libeb.so``, built
+by ``build.py``): argument marshalling only.  Every step of the method runs in
+the library's CUDA kernels; vectors are ``torch`` CUDA tensors passed by their
+device pointers together with torch's current CUDA stream.  Importing the
+package does not load the library; the first call does, and raises if the
+library is missing (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libeb.so")
+
+EB_OK, EB_ERR_INVALID, EB_ERR_GEOMETRY, EB_ERR_CUDA, EB_ERR_NONFINITE = 0, 1, 2, 3, 4
+EB_ERR_NO_CONVERGENCE, EB_ERR_BREAKDOWN, EB_ERR_TIMEOUT, EB_ERR_OOM, EB_ERR_NOT_IMPLEMENTED = 5, 6, 7, 8, 9
+EB_F64, EB_F32, EB_BF16 = 0, 1, 2
+EB_PC_AMG, EB_PC_JACOBI, EB_PC_NONE = 0, 1, 2
+STAR_MAX = 16
+
+CODE_BP = 0x40
+CODE_CP = 0x80
+
+
+class EBError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[eb status {code}] {msg}")
+        self.code = code
+
+
+class eb_grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("lo", C.c_double * 3), ("h", C.c_double)]
+
+
+class eb_levelset(C.Structure):
+    _fields_ = [("kind", C.c_int), ("center", C.c_double * 3), ("semi", C.c_double * 3), ("rot", C.c_double * 9),
+                ("r0", C.c_double), ("nk", C.c_int), ("k", C.c_int * STAR_MAX), ("a", C.c_double * STAR_MAX),
+                ("p", C.c_double * STAR_MAX)]
+
+
+class eb_info_t(C.Structure):
+    _fields_ = [("num_nodes", C.c_int64), ("num_cp", C.c_int64), ("num_bp", C.c_int64), ("num_cut", C.c_int64),
+                ("num_far", C.c_int64), ("num_tiles", C.c_int64), ("tile", C.c_int * 3),
+                ("max_delta_over_h", C.c_double), ("min_abs_psi", C.c_double)]
+
+
+class amg_opts(C.Structure):
+    _fields_ = [("max_levels", C.c_int), ("coarse_max", C.c_int), ("strength", C.c_double),
+                ("cheb_degree", C.c_int), ("vcycle_prec", C.c_int)]
+
+
+class amg_info_t(C.Structure):
+    _fields_ = [("num_levels", C.c_int), ("rows", C.c_int64 * 32), ("nnz", C.c_int64 * 32),
+                ("operator_complexity", C.c_double), ("setup_ms", C.c_double)]
+
+
+class pcg_opts(C.Structure):
+    _fields_ = [("precond", C.c_int), ("check_every", C.c_int), ("use_graph", C.c_int)]
+
+
+class pcg_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("rel_residual", C.c_double), ("true_rel_residual", C.c_double),
+                ("solve_ms", C.c_double), ("converged", C.c_int)]
+
+
+_P = C.c_void_p
+_SIGS = {
+    "eb_build": (C.c_int, [C.POINTER(eb_grid), C.POINTER(eb_levelset), C.POINTER(_P), _P]),
+    "eb_destroy": (None, [_P]),
+    "eb_info": (C.c_int, [_P, C.POINTER(eb_info_t)]),
+    "eb_classes": (C.c_int, [_P, _P, _P]),
+    "eb_cp_data": (C.c_int, [_P, _P, _P, _P]),
+    "eb_cuts": (C.c_int, [_P, _P, _P, _P, _P, _P]),
+    "eb_rhs": (C.c_int, [_P, _P, _P, _P, _P]),
+    "eb_apply": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "amg_setup": (C.c_int, [_P, C.c_double, C.POINTER(amg_opts), C.POINTER(_P), _P]),
+    "amg_destroy": (None, [_P]),
+    "amg_info": (C.c_int, [_P, C.POINTER(amg_info_t)]),
+    "amg_level_copy": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P, _P]),
+    "amg_vcycle": (C.c_int, [_P, _P, _P, _P]),
+    "pcg_solve": (C.c_int, [_P, _P, _P, C.c_double, C.c_int, C.POINTER(pcg_opts), C.POINTER(pcg_stats), _P]),
+    "heat_step": (C.c_int, [_P, C.c_double, C.c_double, _P, _P, _P, C.c_double, C.c_int, C.POINTER(pcg_stats), _P]),
+    "wave_step": (C.c_int, [_P, C.c_int, C.c_double, _P, _P, C.c_int, _P]),
+    "eb_last_error": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+def load(path: Optional[str] = None) -> C.CDLL:
+    """Loads the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"CUDA library {p} is missing: run paper_2204_06083_gb300.build.build() first")
+    lib = C.CDLL(p)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS.keys())
+
+
+def _check(code: int, allow=()):
+    if code != EB_OK and code not in allow:
+        raise EBError(code, load().eb_last_error().decode())
+    return code
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def make_grid(g) -> eb_grid:
+    """eb_grid from an ``eb_inputs.Grid``-like object (dim, n, lo, h)."""
+    out = eb_grid()
+    out.dim = g.dim
+    for a in range(3):
+        out.n[a] = int(g.n[a])
+        out.lo[a] = float(g.lo[a])
+    out.h = float(g.h)
+    return out
+
+
+def make_levelset(ls) -> eb_levelset:
+    """eb_levelset from an ``eb_inputs.LevelSet``-like descriptor."""
+    out = eb_levelset()
+    out.kind = int(ls.kind)
+    for a in range(3):
+        out.center[a] = float(ls.center[a])
+        out.semi[a] = float(ls.semi[a])
+    for a in range(9):
+        out.rot[a] = float(ls.rot[a])
+    out.r0 = float(ls.r0)
+    if len(ls.ks) > STAR_MAX:
+        raise ValueError("too many star terms")
+    out.nk = len(ls.ks)
+    for j, (k, a, p) in enumerate(zip(ls.ks, ls.amps, ls.phases)):
+        out.k[j] = int(k)
+        out.a[j] = float(a)
+        out.p[j] = float(p)
+    return out
+
+
+@dataclass
+class Info:
+    num_nodes: int
+    num_cp: int
+    num_bp: int
+    num_cut: int
+    num_far: int
+    num_tiles: int
+    tile: tuple
+    max_delta_over_h: float
+    min_abs_psi: float
+
+
+class EB:
+    """Handle of eb_build: the classified grid, cuts and diagonal."""
+
+    def __init__(self, grid, levelset, stream=None):
+        lib = load()
+        self._h = C.c_void_p()
+        self.grid = grid
+        self.dim = grid.dim
+        g = make_grid(grid)
+        ls = make_levelset(levelset)
+        _check(lib.eb_build(C.byref(g), C.byref(ls), C.byref(self._h), _stream(stream)))
+        inf = eb_info_t()
+        _check(lib.eb_info(self._h, C.byref(inf)))
+        self.info = Info(inf.num_nodes, inf.num_cp, inf.num_bp, inf.num_cut, inf.num_far, inf.num_tiles,
+                         tuple(inf.tile), inf.max_delta_over_h, inf.min_abs_psi)
+
+    def close(self):
+        if self._h:
+            load().eb_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def shape(self):
+        g = self.grid
+        return (g.n[1], g.n[0]) if g.dim == 2 else (g.n[2], g.n[1], g.n[0])
+
+    def classes(self, stream=None):
+        import torch
+        out = torch.empty(self.info.num_nodes, dtype=torch.uint8, device="cuda")
+        _check(load().eb_classes(self._h, _ptr(out), _stream(stream)))
+        return out.view(self.shape())
+
+    def cp_data(self, stream=None):
+        import torch
+        n = self.info.num_cp
+        nodes = torch.empty(n, dtype=torch.int32, device="cuda")
+        diag = torch.empty(n, dtype=torch.float64, device="cuda")
+        _check(load().eb_cp_data(self._h, _ptr(nodes), _ptr(diag), _stream(stream)))
+        return nodes, diag
+
+    def cuts(self, stream=None):
+        import torch
+        n = self.info.num_cut
+        cp = torch.empty(n, dtype=torch.int32, device="cuda")
+        d = torch.empty(n, dtype=torch.int32, device="cuda")
+        delta = torch.empty(n, dtype=torch.float64, device="cuda")
+        xg = torch.empty((n, self.dim), dtype=torch.float64, device="cuda")
+        _check(load().eb_cuts(self._h, _ptr(cp), _ptr(d), _ptr(delta), _ptr(xg), _stream(stream)))
+        return cp, d, delta, xg
+
+    def rhs(self, f, ugamma, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.zeros(self.shape(), dtype=torch.float64, device="cuda")
+        _check(load().eb_rhs(self._h, _ptr(f), _ptr(ugamma), _ptr(out), _stream(stream)))
+        return out
+
+    def apply(self, x, out=None, stream=None):
+        import torch
+        prec = {torch.float64: EB_F64, torch.float32: EB_F32, torch.bfloat16: EB_BF16}[x.dtype]
+        if out is None:
+            out = torch.zeros_like(x)
+        _check(load().eb_apply(self._h, prec, _ptr(x), _ptr(out), _stream(stream)))
+        return out
+
+    def wave_step(self, u_prev, u_cur, dt, nsteps, stream=None):
+        import torch
+        prec = {torch.float64: EB_F64, torch.float32: EB_F32}[u_cur.dtype]
+        return _check(load().wave_step(self._h, prec, float(dt), _ptr(u_prev), _ptr(u_cur), int(nsteps),
+                                       _stream(stream)))
+
+
+class AMG:
+    """Handle of amg_setup: AMG hierarchy (or Jacobi only) for sigma I + A."""
+
+    def __init__(self, eb: EB, shift: float = 0.0, max_levels: int = 25, coarse_max: int = 1024,
+                 strength: float = 0.08, cheb_degree: int = 2, vcycle_prec: int = EB_F64, stream=None):
+        lib = load()
+        self.eb = eb
+        self.shift = shift
+        o = amg_opts(max_levels, coarse_max, strength, cheb_degree, vcycle_prec)
+        self._h = C.c_void_p()
+        _check(lib.amg_setup(eb.handle, float(shift), C.byref(o), C.byref(self._h), _stream(stream)))
+        inf = amg_info_t()
+        _check(lib.amg_info(self._h, C.byref(inf)))
+        self.num_levels = inf.num_levels
+        self.rows = [inf.rows[i] for i in range(inf.num_levels)]
+        self.nnz = [inf.nnz[i] for i in range(inf.num_levels)]
+        self.operator_complexity = inf.operator_complexity
+        self.setup_ms = inf.setup_ms
+
+    def close(self):
+        if self._h:
+            load().amg_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def level(self, level: int, which: int):
+        """CSR of A_l (which=0) or P_l (which=1) as torch tensors; which=2: aggregates."""
+        import torch
+        if which == 2:
+            agg = torch.empty(self.rows[level], dtype=torch.int32, device="cuda")
+            _check(load().amg_level_copy(self._h, level, 2, None, _ptr(agg), None, _stream()))
+            return agg
+        nrow = self.rows[level]
+        if which == 0:
+            nnz = self.nnz[level]
+        else:
+            nnz = self._p_nnz(level)
+        rp = torch.empty(nrow + 1, dtype=torch.int32, device="cuda")
+        col = torch.empty(max(nnz, 1), dtype=torch.int32, device="cuda")
+        val = torch.empty(max(nnz, 1), dtype=torch.float64, device="cuda")
+        _check(load().amg_level_copy(self._h, level, which, _ptr(rp), _ptr(col), _ptr(val), _stream()))
+        return rp, col[:nnz], val[:nnz]
+
+    def _p_nnz(self, level):
+        import torch
+        rp = torch.empty(self.rows[level] + 1, dtype=torch.int32, device="cuda")
+        _check(load().amg_level_copy(self._h, level, 1, _ptr(rp), None, None, _stream()))
+        return int(rp[-1].item())
+
+    def vcycle(self, r, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.zeros_like(r)
+        _check(load().amg_vcycle(self._h, _ptr(r), _ptr(out), _stream(stream)))
+        return out
+
+    def solve(self, b, x=None, rtol=1e-10, maxit=1000, precond=None, check_every=1, use_graph=1,
+              stream=None, allow_noconv=False):
+        import torch
+        if x is None:
+            x = torch.zeros_like(b)
+        o = pcg_opts(EB_PC_AMG if (precond is None and self.num_levels > 0) else
+                     (EB_PC_JACOBI if precond is None else precond), check_every, use_graph)
+        st = pcg_stats()
+        _check(load().pcg_solve(self._h, _ptr(b), _ptr(x), float(rtol), int(maxit), C.byref(o), C.byref(st),
+                                _stream(stream)), allow=(EB_ERR_NO_CONVERGENCE,) if allow_noconv else ())
+        return x, st
+
+    def heat_step(self, u, b1, dt, theta=1.0, b0=None, rtol=1e-10, maxit=1000, stream=None):
+        st = pcg_stats()
+        _check(load().heat_step(self._h, float(dt), float(theta), _ptr(b1), _ptr(b0), _ptr(u), float(rtol),
+                                int(maxit), C.byref(st), _stream(stream)))
+        return st

@@ -1,0 +1,466 @@
+// Device construction of the line-by-line EB operator (Algorithm 1 steps 1-3)
+// and the matrix-free stencil apply / right-hand side.
+//
+// Level-set arithmetic is written with explicit round-to-nearest intrinsics
+// (__dmul_rn, __dadd_rn, ...) so that no multiply-add is contracted: the
+// quadric level set and its closed-form grid-line roots are then the same
+// IEEE operations, in the same order, as the FP64 definition they follow.
+#include "eb_internal.cuh"
+
+#include <cmath>
+
+namespace ebk {
+
+struct LSDev {
+  int kind;
+  int dim;
+  double c[3], s[3], q[9];
+  double r0;
+  int nk;
+  int k[EB_STAR_MAX_TERMS];
+  double a[EB_STAR_MAX_TERMS], p[EB_STAR_MAX_TERMS];
+};
+
+__device__ __forceinline__ double node_coord(double lo, int64_t i, double h) {
+  return __dadd_rn(lo, __dmul_rn((double)i, h));
+}
+
+// psi = sum_a (y_a/s_a)^2 - 1 with y = Q^T (x - c)  (fixed operation order)
+__device__ double psi_quadric(const LSDev& L, const double* x) {
+  double t0 = __dsub_rn(x[0], L.c[0]);
+  double t1 = __dsub_rn(x[1], L.c[1]);
+  double t2 = L.dim == 3 ? __dsub_rn(x[2], L.c[2]) : 0.0;
+  double acc = 0.0;
+  for (int a = 0; a < L.dim; ++a) {
+    double y = __dadd_rn(__dmul_rn(L.q[0 * 3 + a], t0), __dmul_rn(L.q[1 * 3 + a], t1));
+    if (L.dim == 3) y = __dadd_rn(y, __dmul_rn(L.q[2 * 3 + a], t2));
+    double w = __ddiv_rn(y, L.s[a]);
+    acc = (a == 0) ? __dmul_rn(w, w) : __dadd_rn(acc, __dmul_rn(w, w));
+  }
+  return __dsub_rn(acc, 1.0);
+}
+
+// psi = |x - c| - (r0 + sum_k a_k sin(k phi + p_k))
+__device__ double psi_star(const LSDev& L, double x, double y) {
+  double dx = __dsub_rn(x, L.c[0]);
+  double dy = __dsub_rn(y, L.c[1]);
+  double rho = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+  double phi = atan2(dy, dx);
+  double r = L.r0;
+  for (int j = 0; j < L.nk; ++j)
+    r = __dadd_rn(r, __dmul_rn(L.a[j], sin(__dadd_rn(__dmul_rn((double)L.k[j], phi), L.p[j]))));
+  return __dsub_rn(rho, r);
+}
+
+__device__ double psi_at(const LSDev& L, const double* x) {
+  return L.kind == EB_LS_QUADRIC ? psi_quadric(L, x) : psi_star(L, x[0], x[1]);
+}
+
+// Positive root t of psi(p + sign t e_axis) = 0 for a quadric, p inside:
+// alpha t^2 + beta t + gamma with the cancellation-free root formulas.
+__device__ double quadric_root(const LSDev& L, const double* p, int axis, double sign) {
+  double t0 = __dsub_rn(p[0], L.c[0]);
+  double t1 = __dsub_rn(p[1], L.c[1]);
+  double t2 = L.dim == 3 ? __dsub_rn(p[2], L.c[2]) : 0.0;
+  double alpha = 0.0, dot = 0.0, gamma = 0.0;
+  for (int a = 0; a < L.dim; ++a) {
+    double y = __dadd_rn(__dmul_rn(L.q[0 * 3 + a], t0), __dmul_rn(L.q[1 * 3 + a], t1));
+    if (L.dim == 3) y = __dadd_rn(y, __dmul_rn(L.q[2 * 3 + a], t2));
+    double w = __ddiv_rn(y, L.s[a]);
+    double u = __ddiv_rn(L.q[axis * 3 + a], L.s[a]);
+    if (a == 0) {
+      alpha = __dmul_rn(u, u);
+      dot = __dmul_rn(w, u);
+      gamma = __dmul_rn(w, w);
+    } else {
+      alpha = __dadd_rn(alpha, __dmul_rn(u, u));
+      dot = __dadd_rn(dot, __dmul_rn(w, u));
+      gamma = __dadd_rn(gamma, __dmul_rn(w, w));
+    }
+  }
+  gamma = __dsub_rn(gamma, 1.0);
+  double beta = __dmul_rn(2.0, __dmul_rn(sign, dot));
+  double disc = __dsub_rn(__dmul_rn(beta, beta), __dmul_rn(__dmul_rn(4.0, alpha), gamma));
+  double sq = __dsqrt_rn(disc);
+  if (beta >= 0.0) return __ddiv_rn(__dmul_rn(-2.0, gamma), __dadd_rn(beta, sq));
+  return __ddiv_rn(__dsub_rn(sq, beta), __dmul_rn(2.0, alpha));
+}
+
+// Illinois iteration on g(t) = psi(p + sign t e_axis) over [ta, tb],
+// g(ta) < 0 <= g(tb); stops at g == 0 or when the iterate moves <= 1e-15 h.
+__device__ double star_root(const LSDev& L, const double* p, int axis, double sign, double ta, double tb,
+                            double h) {
+  double q[2] = {p[0], p[1]};
+  auto g = [&](double t) {
+    double qq[2] = {q[0], q[1]};
+    qq[axis] = __dadd_rn(p[axis], __dmul_rn(sign, t));
+    return psi_star(L, qq[0], qq[1]);
+  };
+  double fa = g(ta), fb = g(tb);
+  double t = tb;
+  if (fb == 0.0) return t;
+  int side = 0;
+  double told = ta;
+  for (int it = 0; it < 100; ++it) {
+    double tn = __ddiv_rn(__dsub_rn(__dmul_rn(ta, fb), __dmul_rn(tb, fa)), __dsub_rn(fb, fa));
+    double ft = g(tn);
+    t = tn;
+    if (ft == 0.0) break;
+    if (ft < 0.0) {
+      if (side == -1) fb = __dmul_rn(0.5, fb);
+      ta = tn;
+      fa = ft;
+      side = -1;
+    } else {
+      if (side == 1) fa = __dmul_rn(0.5, fa);
+      tb = tn;
+      fb = ft;
+      side = 1;
+    }
+    if (fabs(__dsub_rn(tn, told)) <= __dmul_rn(1e-15, h)) break;
+    told = tn;
+  }
+  return t;
+}
+
+__device__ __forceinline__ void unflatten(const Geometry& G, int64_t node, int64_t* i) {
+  i[0] = node % G.n0;
+  int64_t r = node / G.n0;
+  i[1] = r % G.n1;
+  i[2] = r / G.n1;
+}
+
+__device__ __forceinline__ int64_t stride_of(const Geometry& G, int axis) {
+  return axis == 0 ? 1 : (axis == 1 ? (int64_t)G.n0 : (int64_t)G.n0 * G.n1);
+}
+
+__device__ __forceinline__ bool on_border(const Geometry& G, const int64_t* i) {
+  bool b = i[0] == 0 || i[0] == G.n0 - 1 || i[1] == 0 || i[1] == G.n1 - 1;
+  if (G.dim == 3) b = b || i[2] == 0 || i[2] == G.n2 - 1;
+  return b;
+}
+
+__device__ __forceinline__ void atomic_min_pos(double* addr, double v) {
+  atomicMin(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
+}
+__device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
+  atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+struct BuildStats {
+  int border_inside;
+  int pad;
+  unsigned long long num_bp;
+  unsigned long long num_far;
+  double min_abs_psi;
+  double max_delta_over_h;
+};
+
+// pass 1: psi at every node; border check; |psi| margin
+__global__ void k_psi(Geometry G, LSDev L, double* psi, BuildStats* st) {
+  int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool live = node < G.num_nodes;
+  if (!live) node = G.num_nodes - 1;   // keep the warp whole for the shuffle reduction
+  int64_t i[3];
+  unflatten(G, node, i);
+  double x[3];
+  for (int a = 0; a < 3; ++a) x[a] = a < G.dim ? node_coord(G.lo[a], i[a], G.h) : 0.0;
+  double v = psi_at(L, x);
+  if (live) psi[node] = v;
+  if (v < 0.0 && on_border(G, i)) atomicExch(&st->border_inside, 1);
+  double av = fabs(v);
+  if (!(av >= 0.0)) av = 0.0;  // NaN -> 0 margin
+  for (int o = 16; o > 0; o >>= 1) av = fmin(av, __shfl_xor_sync(0xffffffffu, av, o));
+  if ((threadIdx.x & 31) == 0) atomic_min_pos(&st->min_abs_psi, av);
+}
+
+// pass 2: inside / BP / CP (Sec. 2 definitions)
+__global__ void k_class(Geometry G, const double* psi, uint8_t* code, int32_t* is_cp, BuildStats* st) {
+  int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= G.num_nodes) return;
+  int64_t i[3];
+  unflatten(G, node, i);
+  uint8_t c = CODE_OUT;
+  int cp = 0;
+  if (psi[node] < 0.0 && !on_border(G, i)) {
+    int cnt = 0;
+    for (int a = 0; a < G.dim; ++a) {
+      int64_t s = stride_of(G, a);
+      cnt += (psi[node - s] < 0.0) + (psi[node + s] < 0.0);
+    }
+    if (cnt == 2 * G.dim) {
+      c = CODE_CP;
+      cp = 1;
+    } else {
+      c = CODE_BP;
+    }
+  }
+  code[node] = c;
+  unsigned bal = __ballot_sync(__activemask(), c == CODE_BP);
+  if (bal && (threadIdx.x & 31) == (unsigned)(__ffs(bal) - 1)) atomicAdd(&st->num_bp, (unsigned long long)__popc(bal));
+  is_cp[node] = cp;
+}
+
+// pass 3: CP numbering, BP-neighbour direction masks, cuts per CP
+__global__ void k_cp_mask(Geometry G, uint8_t* code, const int32_t* cp_off, int32_t* cp_of_node,
+                          int32_t* cp_node, int32_t* ncut, int64_t num_nodes) {
+  int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= num_nodes) return;
+  uint8_t c = code[node];
+  if (!(c & CODE_CP)) {
+    cp_of_node[node] = -1;
+    return;
+  }
+  int32_t k = cp_off[node];
+  cp_of_node[node] = k;
+  cp_node[k] = (int32_t)node;
+  uint8_t m = 0;
+  for (int a = 0; a < G.dim; ++a) {
+    int64_t s = stride_of(G, a);
+    if (code[node - s] == CODE_BP) m |= (uint8_t)(1u << (2 * a));
+    if (code[node + s] == CODE_BP) m |= (uint8_t)(1u << (2 * a + 1));
+  }
+  code[node] = (uint8_t)(CODE_CP | m);
+  ncut[k] = __popc((unsigned)m);
+}
+
+// pass 4: per CP, its cuts (walk + root) and the diagonal D_k = sum_s c_s
+__global__ void k_cut(Geometry G, LSDev L, const double* psi, const uint8_t* code, const int32_t* cp_node,
+                      const int32_t* cut_off, int64_t num_cp, double* diag, int32_t* cut_cp, int32_t* cut_dir,
+                      double* cut_delta, double* cut_c, double* cut_xg, BuildStats* st) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= num_cp) return;
+  int64_t node = cp_node[k];
+  uint8_t m = code[node] & 0x3F;
+  double D = 0.0;
+  int j = cut_off[k];
+  int64_t i[3];
+  unflatten(G, node, i);
+  const double h = G.h;
+  for (int s = 0; s < 2 * G.dim; ++s) {
+    double cs = 1.0;
+    if (m & (1u << s)) {
+      int axis = s >> 1;
+      int sg = (s & 1) ? 1 : -1;
+      int64_t st_ax = stride_of(G, axis) * sg;
+      int64_t bp = node + st_ax;
+      int64_t cur = bp + st_ax;
+      int64_t mm = 1;
+      while (psi[cur] < 0.0) {
+        ++mm;
+        cur += st_ax;
+      }
+      double p[3];
+      for (int a = 0; a < 3; ++a) {
+        int64_t ia = i[a] + (a == axis ? sg : 0);
+        p[a] = a < G.dim ? node_coord(G.lo[a], ia, h) : 0.0;
+      }
+      double delta;
+      if (L.kind == EB_LS_QUADRIC) {
+        delta = quadric_root(L, p, axis, (double)sg);
+      } else {
+        double ta = __dmul_rn((double)(mm - 1), h);
+        double tb = __dmul_rn((double)mm, h);
+        delta = star_root(L, p, axis, (double)sg, ta, tb, h);
+      }
+      cs = __ddiv_rn(h, __dadd_rn(h, delta));
+      cut_cp[j] = (int32_t)k;
+      cut_dir[j] = s;
+      cut_delta[j] = delta;
+      cut_c[j] = cs;
+      for (int a = 0; a < G.dim; ++a)
+        cut_xg[(int64_t)j * G.dim + a] = (a == axis) ? __dadd_rn(p[a], __dmul_rn((double)sg, delta)) : p[a];
+      if (delta > h) atomicAdd(&st->num_far, 1ull);
+      atomic_max_pos(&st->max_delta_over_h, fabs(delta / h));
+      ++j;
+    }
+    D = (s == 0) ? cs : __dadd_rn(D, cs);
+  }
+  diag[node] = D;
+}
+
+__global__ void k_tile_flags(Geometry G, const uint8_t* code, int32_t* tflag) {
+  int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= G.num_nodes) return;
+  if (!(code[node] & CODE_CP)) return;
+  int64_t i[3];
+  unflatten(G, node, i);
+  int64_t t = i[0] / G.tx + (int64_t)G.ntx * (i[1] / G.ty + (int64_t)G.nty * (i[2] / G.tz));
+  tflag[t] = 1;
+}
+
+__global__ void k_compact(const int32_t* flag, const int32_t* off, int64_t n, int32_t* out) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n && flag[t]) out[off[t]] = (int32_t)t;
+}
+
+static LSDev to_dev(const eb_levelset& ls, int dim) {
+  LSDev L{};
+  L.kind = ls.kind;
+  L.dim = dim;
+  for (int a = 0; a < 3; ++a) {
+    L.c[a] = ls.center[a];
+    L.s[a] = ls.semi[a];
+  }
+  for (int a = 0; a < 9; ++a) L.q[a] = ls.rot[a];
+  L.r0 = ls.r0;
+  L.nk = ls.nk;
+  for (int j = 0; j < ls.nk; ++j) {
+    L.k[j] = ls.k[j];
+    L.a[j] = ls.a[j];
+    L.p[j] = ls.p[j];
+  }
+  return L;
+}
+
+void build_handle(EBHandle& eb, const eb_grid& grid, const eb_levelset& ls, cudaStream_t s) {
+  EB_REQUIRE(grid.dim == 2 || grid.dim == 3, EB_ERR_INVALID, "grid.dim must be 2 or 3");
+  EB_REQUIRE(grid.n[0] >= 3 && grid.n[1] >= 3 && (grid.dim == 2 ? grid.n[2] == 1 : grid.n[2] >= 3),
+             EB_ERR_INVALID, "grid needs >= 3 nodes per used axis (and n[2] == 1 in 2D)");
+  EB_REQUIRE(grid.n[0] % 2 == 0, EB_ERR_INVALID, "n[0] must be even");
+  EB_REQUIRE(grid.h > 0.0 && std::isfinite(grid.h), EB_ERR_INVALID, "h must be positive");
+  EB_REQUIRE(ls.kind == EB_LS_QUADRIC || (ls.kind == EB_LS_STAR2D && grid.dim == 2), EB_ERR_INVALID,
+             "unknown level-set kind (STAR2D is 2D only)");
+  EB_REQUIRE(ls.nk >= 0 && ls.nk <= EB_STAR_MAX_TERMS, EB_ERR_INVALID, "star: nk out of range");
+  if (ls.kind == EB_LS_QUADRIC)
+    for (int a = 0; a < grid.dim; ++a) EB_REQUIRE(ls.semi[a] > 0.0, EB_ERR_INVALID, "quadric semi-axes must be > 0");
+  int64_t nn = (int64_t)grid.n[0] * grid.n[1] * grid.n[2];
+  EB_REQUIRE(nn < ((int64_t)1 << 31) - 1, EB_ERR_INVALID, "grid larger than 2^31 nodes");
+
+  Geometry& G = eb.g;
+  G.dim = grid.dim;
+  G.n0 = grid.n[0];
+  G.n1 = grid.n[1];
+  G.n2 = grid.n[2];
+  G.num_nodes = nn;
+  for (int a = 0; a < 3; ++a) G.lo[a] = grid.lo[a];
+  G.h = grid.h;
+  if (grid.dim == 2) {
+    G.tx = 32; G.ty = 8; G.tz = 1;
+  } else {
+    G.tx = 16; G.ty = 4; G.tz = 4;
+  }
+  G.ntx = (G.n0 + G.tx - 1) / G.tx;
+  G.nty = (G.n1 + G.ty - 1) / G.ty;
+  G.ntz = (G.n2 + G.tz - 1) / G.tz;
+  eb.ls = ls;
+  eb.home = s;
+  LSDev L = to_dev(ls, grid.dim);
+
+  BuildStats* st = dalloc<BuildStats>(1, s);
+  BuildStats init{};
+  init.min_abs_psi = 1e300;
+  init.max_delta_over_h = 0.0;
+  EB_CUDA(cudaMemcpyAsync(st, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+
+  double* psi = dalloc<double>(nn, s, false);
+  int32_t* is_cp = dalloc<int32_t>(nn, s, false);
+  int32_t* cp_off = dalloc<int32_t>(nn + 1, s, false);
+  eb.code = dalloc<uint8_t>(nn, s);
+  eb.diag = dalloc<double>(nn, s);
+  eb.cp_of_node = dalloc<int32_t>(nn, s, false);
+
+  const int T = 256;
+  k_psi<<<blocks_for(nn, T), T, 0, s>>>(G, L, psi, st);
+  k_class<<<blocks_for(nn, T), T, 0, s>>>(G, psi, eb.code, is_cp, st);
+  EB_CUDA(cudaGetLastError());
+  exclusive_scan_i32(is_cp, cp_off, nn, s);
+  BuildStats hst{};
+  int32_t ncp = 0;
+  EB_CUDA(cudaMemcpyAsync(&ncp, cp_off + nn, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  EB_CUDA(cudaMemcpyAsync(&hst, st, sizeof(hst), cudaMemcpyDeviceToHost, s));
+  EB_CUDA(cudaStreamSynchronize(s));
+  if (hst.border_inside || ncp == 0) {
+    dfree(psi, s); dfree(is_cp, s); dfree(cp_off, s); dfree(st, s);
+    EB_CUDA(cudaStreamSynchronize(s));
+    throw Failure{EB_ERR_GEOMETRY, hst.border_inside ? "the geometry touches the outermost ring of grid nodes"
+                                                     : "no computational point"};
+  }
+  eb.num_cp = ncp;
+  eb.num_bp = (int64_t)hst.num_bp;
+  eb.cp_node = dalloc<int32_t>(ncp, s, false);
+  int32_t* ncut = dalloc<int32_t>(ncp + 1, s);
+  eb.cut_off = dalloc<int32_t>(ncp + 1, s, false);
+  k_cp_mask<<<blocks_for(nn, T), T, 0, s>>>(G, eb.code, cp_off, eb.cp_of_node, eb.cp_node, ncut, nn);
+  EB_CUDA(cudaGetLastError());
+  exclusive_scan_i32(ncut, eb.cut_off, ncp, s);
+  int32_t nc = 0;
+  EB_CUDA(cudaMemcpyAsync(&nc, eb.cut_off + ncp, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  EB_CUDA(cudaStreamSynchronize(s));
+  eb.num_cut = nc;
+  eb.cut_cp = dalloc<int32_t>(nc, s, false);
+  eb.cut_dir = dalloc<int32_t>(nc, s, false);
+  eb.cut_delta = dalloc<double>(nc, s, false);
+  eb.cut_c = dalloc<double>(nc, s, false);
+  eb.cut_xg = dalloc<double>((int64_t)nc * G.dim, s, false);
+  k_cut<<<blocks_for(ncp, 128), 128, 0, s>>>(G, L, psi, eb.code, eb.cp_node, eb.cut_off, ncp, eb.diag, eb.cut_cp,
+                                             eb.cut_dir, eb.cut_delta, eb.cut_c, eb.cut_xg, st);
+  EB_CUDA(cudaGetLastError());
+
+  int64_t ntiles_all = (int64_t)G.ntx * G.nty * G.ntz;
+  int32_t* tflag = dalloc<int32_t>(ntiles_all, s);
+  int32_t* toff = dalloc<int32_t>(ntiles_all + 1, s, false);
+  k_tile_flags<<<blocks_for(nn, T), T, 0, s>>>(G, eb.code, tflag);
+  exclusive_scan_i32(tflag, toff, ntiles_all, s);
+  int32_t nt = 0;
+  EB_CUDA(cudaMemcpyAsync(&nt, toff + ntiles_all, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  EB_CUDA(cudaMemcpyAsync(&hst, st, sizeof(hst), cudaMemcpyDeviceToHost, s));
+  EB_CUDA(cudaStreamSynchronize(s));
+  eb.num_tiles = nt;
+  eb.tiles = dalloc<int32_t>(nt, s, false);
+  k_compact<<<blocks_for(ntiles_all, T), T, 0, s>>>(tflag, toff, ntiles_all, eb.tiles);
+  EB_CUDA(cudaGetLastError());
+  eb.num_far = (int64_t)hst.num_far;
+  eb.max_delta_over_h = hst.max_delta_over_h;
+  eb.min_abs_psi = hst.min_abs_psi;
+  dfree(psi, s); dfree(is_cp, s); dfree(cp_off, s); dfree(ncut, s);
+  dfree(tflag, s); dfree(toff, s); dfree(st, s);
+  EB_CUDA(cudaStreamSynchronize(s));
+}
+
+void destroy_handle(EBHandle& eb) {
+  cudaStream_t s = eb.home;
+  dfree(eb.code, s); dfree(eb.diag, s); dfree(eb.cp_of_node, s); dfree(eb.cp_node, s);
+  dfree(eb.tiles, s); dfree(eb.cut_cp, s); dfree(eb.cut_dir, s); dfree(eb.cut_delta, s);
+  dfree(eb.cut_c, s); dfree(eb.cut_xg, s); dfree(eb.cut_off, s);
+  cudaStreamSynchronize(s);
+}
+
+// ------------------------------------------------------------------- RHS
+__global__ void k_rhs(Geometry G, const int32_t* tiles, int64_t ntiles, const uint8_t* code,
+                      const int32_t* cp_of_node, const int32_t* cut_off, const double* cut_c, const double* f,
+                      const double* ug, double* b, double h2) {
+  const int tsz = G.tx * G.ty * G.tz;
+  for (int64_t tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+    int64_t t = tiles[tt];
+    int64_t bx = t % G.ntx, r = t / G.ntx, by = r % G.nty, bz = r / G.nty;
+    for (int l = threadIdx.x; l < tsz; l += blockDim.x) {
+      int lx = l % G.tx, ly = (l / G.tx) % G.ty, lz = l / (G.tx * G.ty);
+      int64_t ix = bx * G.tx + lx, iy = by * G.ty + ly, iz = bz * G.tz + lz;
+      if (ix >= G.n0 || iy >= G.n1 || iz >= G.n2) continue;
+      int64_t node = ix + (int64_t)G.n0 * (iy + (int64_t)G.n1 * iz);
+      uint8_t c = code[node];
+      double v = 0.0;
+      if (c & CODE_CP) {
+        double acc = 0.0;
+        if (c & 0x3F) {
+          int32_t k = cp_of_node[node];
+          for (int j = cut_off[k]; j < cut_off[k + 1]; ++j) acc = __dadd_rn(acc, __ddiv_rn(__dmul_rn(cut_c[j], ug[j]), h2));
+        }
+        v = __dadd_rn(-f[node], acc);
+      }
+      b[node] = v;
+    }
+  }
+}
+
+void launch_rhs(const EBHandle& eb, const double* f, const double* ug, double* b, cudaStream_t s) {
+  const Geometry& G = eb.g;
+  double h2 = G.h * G.h;
+  unsigned blocks = (unsigned)std::min<int64_t>(eb.num_tiles, (int64_t)num_sms() * 8);
+  k_rhs<<<blocks, 256, 0, s>>>(G, eb.tiles, eb.num_tiles, eb.code, eb.cp_of_node, eb.cut_off, eb.cut_c, f, ug, b,
+                               h2);
+  EB_CUDA(cudaGetLastError());
+}
+
+}  // namespace ebk

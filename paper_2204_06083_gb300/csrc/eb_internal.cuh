@@ -1,0 +1,150 @@
+// Internal declarations of the EB library (sm_103a).  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/eb.h"
+
+namespace ebk {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+const char* last_error();
+
+struct Failure {
+  int code;
+  std::string msg;
+};
+
+#define EB_CUDA(call)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      throw ::ebk::Failure{EB_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+#define EB_REQUIRE(cond, code, msg)                   \
+  do {                                                \
+    if (!(cond)) throw ::ebk::Failure{(code), (msg)}; \
+  } while (0)
+
+// Runs body, translating Failure / std exceptions into a status code.
+template <class F>
+int guarded(F&& body) {
+  try {
+    body();
+    return EB_OK;
+  } catch (const Failure& f) {
+    set_error(f.msg);
+    return f.code;
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return EB_ERR_OOM;
+  } catch (...) {
+    set_error("unexpected internal error");
+    return EB_ERR_INVALID;
+  }
+}
+
+// Device allocation that reports EB_ERR_OOM.
+template <class T>
+T* dalloc(size_t count, cudaStream_t s, bool zero = true) {
+  if (count == 0) count = 1;
+  void* p = nullptr;
+  cudaError_t e = cudaMallocAsync(&p, count * sizeof(T), s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Failure{EB_ERR_OOM, std::string("device allocation of ") + std::to_string(count * sizeof(T)) +
+                                  " bytes failed: " + cudaGetErrorString(e)};
+  }
+  if (zero) EB_CUDA(cudaMemsetAsync(p, 0, count * sizeof(T), s));
+  return static_cast<T*>(p);
+}
+
+template <class T>
+void dfree(T*& p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+  p = nullptr;
+}
+
+// ------------------------------------------------------------- node codes
+constexpr uint8_t CODE_OUT = 0x00;
+constexpr uint8_t CODE_BP = 0x40;
+constexpr uint8_t CODE_CP = 0x80;   // | mask of BP-neighbour directions
+
+// --------------------------------------------------------------- geometry
+struct Geometry {
+  int dim;
+  int n0, n1, n2;
+  int64_t num_nodes;
+  double lo[3];
+  double h;
+  int tx, ty, tz;          // tile extents (nodes)
+  int ntx, nty, ntz;       // tiles per axis
+};
+
+// ------------------------------------------------------------------ handle
+struct EBHandle {
+  Geometry g;
+  eb_levelset ls;
+  int64_t num_cp = 0, num_bp = 0, num_cut = 0, num_far = 0, num_tiles = 0;
+  double max_delta_over_h = 0.0, min_abs_psi = 0.0;
+  uint8_t* code = nullptr;       // [num_nodes]
+  double* diag = nullptr;        // [num_nodes] D_k (h^2 units) at CPs, 0 elsewhere
+  int32_t* cp_of_node = nullptr; // [num_nodes]
+  int32_t* cp_node = nullptr;    // [num_cp]
+  int32_t* tiles = nullptr;      // [num_tiles] linear tile index, ascending
+  int32_t* cut_cp = nullptr;     // [num_cut]
+  int32_t* cut_dir = nullptr;    // [num_cut]
+  double* cut_delta = nullptr;   // [num_cut]
+  double* cut_c = nullptr;       // [num_cut]
+  double* cut_xg = nullptr;      // [num_cut * dim]
+  int32_t* cut_off = nullptr;    // [num_cp + 1] first cut of CP k
+  cudaStream_t home = 0;
+};
+
+// ----------------------------------------------------------- build / apply
+void build_handle(EBHandle& eb, const eb_grid& grid, const eb_levelset& ls, cudaStream_t s);
+void destroy_handle(EBHandle& eb);
+
+// y = (sigma I + A) x over the active tiles (masked, non-CP outputs 0).
+template <class T>
+void launch_apply(const EBHandle& eb, const T* x, T* y, double sigma, cudaStream_t s);
+
+void launch_rhs(const EBHandle& eb, const double* f, const double* ug, double* b, cudaStream_t s);
+
+// Scans: exclusive prefix sum of n int32 values into out (out[n] = total).
+void exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s);
+int64_t scan_total(const int32_t* out, int64_t n, cudaStream_t s);
+
+// --------------------------------------------------------- launch helpers
+inline int num_sms() {
+  static int v = 0;
+  if (!v) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    if (v <= 0) v = 1;
+  }
+  return v;
+}
+
+inline unsigned blocks_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > (int64_t)1 << 30) b = (int64_t)1 << 30;
+  return (unsigned)b;
+}
+
+}  // namespace ebk
+
+namespace ebk {
+template <class T>
+int launch_leapfrog(const EBHandle& eb, T* ua, T* ub, int nsteps, double dt, cudaStream_t s);
+}

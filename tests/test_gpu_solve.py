@@ -1,0 +1,183 @@
+"""GPU parity of pcg_solve, heat_step and wave_step against the FP64 oracle,
+through the C ABI.
+
+Solution tolerance: both sides solve to rtol 1e-13; the solutions then agree
+to rel-L2 <= 1e-10 (the bound kappa_hat * rtol with kappa_hat ~ 2 dim /
+(h^2 lambda_min) ~ 1e3 for these grids).
+Leapfrog: the recursion is the same on both sides, up to the rounding order of
+the stencil sum; after N steps the FP64 fields agree to rel-L2 <= 1e-11.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import eb_inputs as ei
+from oracle import eb as oeb
+from oracle import solvers as osol
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import __graft_entry__ as ge
+    ge.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+
+
+def _eb():
+    import paper_2204_06083_gb300 as eb
+    return eb
+
+
+def _poisson(grid, ls):
+    eb = _eb()
+    h = eb.EB(grid, ls)
+    ref = oeb.build(grid, ls)
+    pts = ei.grid_points(grid)
+    ufun, ffun = (ei.u_k1, ei.f_k1) if grid.dim == 2 else (ei.u_k3, ei.f_k3)
+    f = ffun(*pts)
+    ug = ufun(*[ref.cut_xg[:, a] for a in range(grid.dim)])
+    b = h.rhs(torch.tensor(f, device="cuda"), torch.tensor(ug, device="cuda"))
+    return h, ref, b, oeb.rhs(ref, f, ug)
+
+
+@pytest.mark.parametrize("case", ["circle130", "ellipsoid34"])
+def test_jacobi_pcg_parity(case):
+    eb = _eb()
+    grid, ls = ei.circle_k1(130) if case == "circle130" else ei.ellipsoid_k3(34, seed=0)
+    h, ref, b, b_ref = _poisson(grid, ls)
+    solver = eb.AMG(h, 0.0, max_levels=0)
+    x, st = solver.solve(b, rtol=1e-13, maxit=20000, precond=eb.EB_PC_JACOBI, check_every=8)
+    assert st.converged and st.true_rel_residual <= 1e-13
+    x_ref = osol.dense_cholesky_solve(ref.A, b_ref) if ref.num_cp < 6000 else osol.pcg(ref.A, b_ref, rtol=1e-14)[0]
+    got = ref.from_grid(x.cpu().numpy())
+    assert np.linalg.norm(got - x_ref) / np.linalg.norm(x_ref) <= 1e-10
+
+
+def test_pcg_one_step_matches_oracle_cg_iterates():
+    """With no preconditioner and maxit = k the GPU iterate is the k-th CG
+    iterate of the oracle (same recursion, different rounding order)."""
+    eb = _eb()
+    grid, ls = ei.circle_k1(64)
+    h, ref, b, b_ref = _poisson(grid, ls)
+    solver = eb.AMG(h, 0.0, max_levels=0)
+    for k in (1, 5, 20):
+        x, st = solver.solve(b, rtol=1e-30, maxit=k, precond=eb.EB_PC_NONE, allow_noconv=True)
+        assert st.iterations == k
+        xo, sto = osol.pcg(ref.A, b_ref, rtol=1e-30, maxit=k)
+        got = ref.from_grid(x.cpu().numpy())
+        assert np.linalg.norm(got - xo) / np.linalg.norm(xo) <= 1e-12
+
+
+def test_pcg_error_paths():
+    eb = _eb()
+    grid, ls = ei.circle_k1(64)
+    h, ref, b, b_ref = _poisson(grid, ls)
+    solver = eb.AMG(h, 0.0, max_levels=0)
+    # maxit exhausted -> EB_ERR_NO_CONVERGENCE with statistics filled
+    with pytest.raises(eb.EBError) as e:
+        solver.solve(b, rtol=1e-14, maxit=3)
+    assert e.value.code == eb.EB_ERR_NO_CONVERGENCE
+    x, st = solver.solve(b, rtol=1e-14, maxit=3, allow_noconv=True)
+    assert st.iterations == 3 and not st.converged
+    # NaN in the right-hand side -> EB_ERR_NONFINITE
+    bn = b.clone()
+    nodes, _ = h.cp_data()
+    bn.view(-1)[nodes[5].long()] = float("nan")
+    with pytest.raises(eb.EBError) as e:
+        solver.solve(bn, rtol=1e-10)
+    assert e.value.code == eb.EB_ERR_NONFINITE
+    # zero right-hand side -> x = 0, converged
+    x, st = solver.solve(torch.zeros_like(b), x=torch.ones_like(b), rtol=1e-10)
+    assert st.converged and float(x.abs().max()) == 0.0
+
+
+def test_heat_backward_euler_matches_oracle():
+    eb = _eb()
+    grid, ls = ei.circle_k1(66)
+    h = eb.EB(grid, ls)
+    ref = oeb.build(grid, ls)
+    X, Y = ei.grid_points(grid)
+    dt = grid.h
+
+    def bvec(t):
+        F = ei.f_heat(X, Y, t)
+        ug = ei.u_heat(ref.cut_xg[:, 0], ref.cut_xg[:, 1], t)
+        return -F, ug
+
+    solver = eb.AMG(h, 1.0 / dt, max_levels=0)
+    u0 = ei.u_heat(X, Y, 0.0)
+    u = torch.tensor(u0, device="cuda")
+    u_ref = ref.from_grid(u0)
+    for k in range(5):
+        mf, ug = bvec((k + 1) * dt)
+        b1 = h.rhs(torch.tensor(mf, device="cuda"), torch.tensor(ug, device="cuda"))
+        st = solver.heat_step(u, b1, dt, theta=1.0, rtol=1e-13)
+        assert st.converged
+        b1_ref = oeb.rhs(ref, mf, ug)
+        u_ref, _ = osol.theta_heat_step(ref.A, u_ref, dt, 1.0, b1_ref, b1_ref, rtol=1e-14)
+    got = ref.from_grid(u.cpu().numpy())
+    assert np.linalg.norm(got - u_ref) / np.linalg.norm(u_ref) <= 1e-10
+
+
+@pytest.mark.parametrize("nsteps", [1, 2, 37])
+def test_wave_leapfrog_parity(nsteps):
+    eb = _eb()
+    grid, ls = ei.box_grid(2, 258), ei.star(ei.STAR_CENTER, 0.5, [5], [0.1], [0.0])
+    h = eb.EB(grid, ls)
+    ref = oeb.build(grid, ls)
+    X, Y = ei.grid_points(grid)
+    c, w = ei.pulse_params(0)
+    u0g = ei.pulse(X, Y, c, max(w, 4 * grid.h))
+    u0 = ref.from_grid(u0g)
+    dt = 0.9 * grid.h / math.sqrt(2.0)
+    u1 = u0 - 0.5 * dt * dt * (ref.A @ u0)
+    a, bref = osol.leapfrog(ref.A, u0, u1, dt, nsteps)
+    ua = torch.tensor(ref.to_grid(u0), device="cuda")
+    ub = torch.tensor(ref.to_grid(u1), device="cuda")
+    h.wave_step(ua, ub, dt, nsteps)
+    ga = ref.from_grid(ua.cpu().numpy())
+    gb = ref.from_grid(ub.cpu().numpy())
+    assert np.linalg.norm(gb - bref) / np.linalg.norm(bref) <= 1e-11
+    assert np.linalg.norm(ga - a) / np.linalg.norm(a) <= 1e-11
+
+
+def test_wave_fp32_error_vs_fp64_stated():
+    eb = _eb()
+    grid, ls = ei.box_grid(2, 258), ei.star(ei.STAR_CENTER, 0.5, [5], [0.1], [0.0])
+    h = eb.EB(grid, ls)
+    ref = oeb.build(grid, ls)
+    X, Y = ei.grid_points(grid)
+    c, w = ei.pulse_params(0)
+    u0 = ref.from_grid(ei.pulse(X, Y, c, max(w, 4 * grid.h)))
+    dt = 0.9 * grid.h / math.sqrt(2.0)
+    u1 = u0 - 0.5 * dt * dt * (ref.A @ u0)
+    _, bref = osol.leapfrog(ref.A, u0, u1, dt, 500)
+    ua = torch.tensor(ref.to_grid(u0), device="cuda", dtype=torch.float32)
+    ub = torch.tensor(ref.to_grid(u1), device="cuda", dtype=torch.float32)
+    h.wave_step(ua, ub, dt, 500)
+    got = ref.from_grid(ub.double().cpu().numpy())
+    err = np.linalg.norm(got - bref) / np.linalg.norm(bref)
+    print(f"FP32 leapfrog rel-L2 vs FP64 after 500 steps: {err:.2e}")
+    assert err <= 1e-4
+
+
+def test_wave_energy_conserved_on_gpu():
+    eb = _eb()
+    grid, ls = ei.box_grid(2, 514), ei.star(ei.STAR_CENTER, 0.5, [5], [0.1], [0.0])
+    h = eb.EB(grid, ls)
+    ref = oeb.build(grid, ls)
+    X, Y = ei.grid_points(grid)
+    c, w = ei.pulse_params(1)
+    u0 = ref.from_grid(ei.pulse(X, Y, c, max(w, 4 * grid.h)))
+    dt = 0.9 * grid.h / math.sqrt(2.0)
+    u1 = u0 - 0.5 * dt * dt * (ref.A @ u0)
+    e0 = osol.leapfrog_energy(ref.A, u0, u1, dt)
+    ua = torch.tensor(ref.to_grid(u0), device="cuda")
+    ub = torch.tensor(ref.to_grid(u1), device="cuda")
+    h.wave_step(ua, ub, dt, 2001)
+    e1 = osol.leapfrog_energy(ref.A, ref.from_grid(ua.cpu().numpy()), ref.from_grid(ub.cpu().numpy()), dt)
+    assert abs(e1 - e0) / e0 < 1e-9
