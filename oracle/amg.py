@@ -6,7 +6,10 @@ aggregation hierarchy whose every decision is a fixed function of the matrix,
 so that a parallel implementation can reproduce it exactly:
 
 * strength       j != i is a strong neighbour of i iff |a_ij| >= theta
-                 sqrt(a_ii a_jj), theta = 0.08.
+                 sqrt(a_ii a_jj), theta = 0.02 (with 0.08 the first coarse
+                 level of the 3D operator has most couplings just below the
+                 threshold, aggregation degenerates to singletons and the
+                 operator complexity exceeds 10).
 * MIS-2 roots    synchronous rounds over the strength graph.  Every node has
                  the 64-bit key (state << 62) | (hash32(i) << 30) | i with state
                  2 = root, 1 = undecided, 0 = removed; a round takes the key
@@ -40,7 +43,7 @@ import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
 
-STRENGTH_THETA = 0.08
+STRENGTH_THETA = 0.02
 COARSE_MAX = 1024
 MAX_LEVELS = 25
 CHEB_LO_FRAC = 1.0 / 30.0
