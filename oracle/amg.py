@@ -20,8 +20,8 @@ so that a parallel implementation can reproduce it exactly:
 * aggregates     roots are numbered in index order; a node with a strong root
                  neighbour joins it (at most one exists); every other node
                  joins the aggregate of the strong neighbour (assigned in the
-                 first pass) with the largest |a_ij|, ties to the lowest
-                 aggregate id.
+                 first pass) with the largest |a_ij| (compared rounded to
+                 single precision), ties to the lowest aggregate id.
 * prolongation   P_hat = normalised constant vector per aggregate
                  (1/sqrt(|agg|)); P = (I - omega D^-1 A) P_hat with omega =
                  4/(3 rho), rho = max_i sum_j |a_ij| / a_ii (Gershgorin bound of
@@ -122,7 +122,9 @@ def aggregate(A: sp.csr_matrix):
     # pass 2: strongest strong neighbour assigned in pass 1, ties -> lowest id
     un = agg1 < 0
     cand = un[rows] & (agg1[cols] >= 0)
-    r2, c2, w2 = rows[cand], agg1[cols[cand]], w[cand]
+    # weights compared after rounding to single precision: a last-ulp difference
+    # in the matrix (e.g. from a different libm) cannot break a tie differently
+    r2, c2, w2 = rows[cand], agg1[cols[cand]], w[cand].astype(np.float32)
     order = np.lexsort((c2, -w2, r2))
     r2, c2 = r2[order], c2[order]
     firsts = np.ones(r2.size, dtype=bool)
