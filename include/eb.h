@@ -143,7 +143,7 @@ typedef enum { EB_PC_AMG = 0, EB_PC_JACOBI = 1, EB_PC_NONE = 2 } eb_pc_kind;
 typedef struct {
   int max_levels;        /* default 25 */
   int coarse_max;        /* coarsen until n <= coarse_max (default 1024) */
-  double strength;       /* theta of |a_ij| >= theta sqrt(a_ii a_jj), default 0.08 */
+  double strength;       /* theta of |a_ij| >= theta sqrt(a_ii a_jj), default 0.02 */
   int cheb_degree;       /* Chebyshev smoother degree, default 2 */
   int vcycle_prec;       /* EB_F64 (default) or EB_F32: storage of level vectors/matrices */
 } amg_opts;
@@ -179,6 +179,7 @@ typedef struct {
   int precond;           /* eb_pc_kind, default EB_PC_AMG */
   int check_every;       /* host convergence check period in iterations (default 1) */
   int use_graph;         /* capture the iteration in a CUDA graph (default 1) */
+  int profile;           /* 1: time every level-0 smoother launch with CUDA events */
 } pcg_opts;
 
 typedef struct {
@@ -187,6 +188,9 @@ typedef struct {
   double true_rel_residual;  /* ||b - A x|| / ||b|| recomputed at exit */
   double solve_ms;
   int converged;
+  double prof_kernel_ms;     /* with opts.profile: summed duration of the level-0 smoother launches */
+  int prof_launches;         /* with opts.profile: their number */
+  int64_t launches;          /* kernel launches this solve issued */
 } pcg_stats;
 
 /* Solves (sigma I + A) x = b by PCG (Algorithm 1 step 4) with the

@@ -60,12 +60,13 @@ class amg_info_t(C.Structure):
 
 
 class pcg_opts(C.Structure):
-    _fields_ = [("precond", C.c_int), ("check_every", C.c_int), ("use_graph", C.c_int)]
+    _fields_ = [("precond", C.c_int), ("check_every", C.c_int), ("use_graph", C.c_int), ("profile", C.c_int)]
 
 
 class pcg_stats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("rel_residual", C.c_double), ("true_rel_residual", C.c_double),
-                ("solve_ms", C.c_double), ("converged", C.c_int)]
+                ("solve_ms", C.c_double), ("converged", C.c_int), ("prof_kernel_ms", C.c_double),
+                ("prof_launches", C.c_int), ("launches", C.c_int64)]
 
 
 _P = C.c_void_p
@@ -268,7 +269,7 @@ class AMG:
     """Handle of amg_setup: AMG hierarchy (or Jacobi only) for sigma I + A."""
 
     def __init__(self, eb: EB, shift: float = 0.0, max_levels: int = 25, coarse_max: int = 1024,
-                 strength: float = 0.08, cheb_degree: int = 2, vcycle_prec: int = EB_F64, stream=None):
+                 strength: float = 0.02, cheb_degree: int = 2, vcycle_prec: int = EB_F64, stream=None):
         lib = load()
         self.eb = eb
         self.shift = shift
@@ -326,12 +327,12 @@ class AMG:
         return out
 
     def solve(self, b, x=None, rtol=1e-10, maxit=1000, precond=None, check_every=1, use_graph=1,
-              stream=None, allow_noconv=False):
+              stream=None, allow_noconv=False, profile=False):
         import torch
         if x is None:
             x = torch.zeros_like(b)
         o = pcg_opts(EB_PC_AMG if (precond is None and self.num_levels > 0) else
-                     (EB_PC_JACOBI if precond is None else precond), check_every, use_graph)
+                     (EB_PC_JACOBI if precond is None else precond), check_every, use_graph, int(profile))
         st = pcg_stats()
         _check(load().pcg_solve(self._h, _ptr(b), _ptr(x), float(rtol), int(maxit), C.byref(o), C.byref(st),
                                 _stream(stream)), allow=(EB_ERR_NO_CONVERGENCE,) if allow_noconv else ())

@@ -1,0 +1,419 @@
+// V-cycle of the smoothed-aggregation hierarchy (AMG preconditioner of
+// Algorithm 1 step 4), in FP64 or in FP32 storage with FP32 arithmetic.
+//
+// Level 0 is matrix free on the grid (stencil.cuh); coarser levels use CSR.
+// Smoother: Chebyshev polynomial of degree k for D^-1 A on [rho/30, 1.1 rho],
+// one sweep before and one after the coarse correction; the first sweep
+// starts from x = 0 and needs no operator apply.  The coarsest level is solved
+// by its FP64 explicit inverse.  With FP32 storage the right-hand side is
+// rounded to FP32 on entry and the result is widened to FP64 on exit; the
+// outer PCG (eb_solve.cu) then uses the flexible (Polak-Ribiere) beta.
+#include "amg_internal.cuh"
+#include "stencil.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <type_traits>
+
+namespace ebk {
+
+template <class V>
+struct CsrV {
+  int64_t n;
+  const int32_t* rp;
+  const int32_t* ci;
+  const V* v;
+};
+
+struct GOp {
+  double inv_h2, sigma, dinv_int;
+};
+
+template <class A>
+__device__ __forceinline__ A inv_diag_t(uint32_t c, const double* __restrict__ diag, int32_t node, const GOp& o) {
+  if (!(c & 0x3F)) return (A)o.dinv_int;
+  return (A)1 / ((A)o.sigma + (A)__ldg(diag + node) * (A)o.inv_h2);
+}
+
+__device__ __forceinline__ void st2o(double* p, double a, double b) { st2(p, a, b); }
+__device__ __forceinline__ void st2o(float* p, float a, float b) { st2(p, a, b); }
+
+// level 0 ----------------------------------------------------------------
+// b_out = (V) r; x = d = D^-1 b / theta
+template <int DIM, class V>
+__global__ void __launch_bounds__(TILE_NODES) k_g_cheb_first(TileView tv, const uint8_t* __restrict__ code,
+                                                             const double* __restrict__ diag, GOp o,
+                                                             const double* __restrict__ r, V* __restrict__ b_out,
+                                                             V* __restrict__ x, V* __restrict__ d, double theta) {
+  using A = typename AccOf<V>::type;
+  EB_PAIR_LOOP(DIM, tv, node) {
+    uint32_t c0, c1;
+    ld_codes(code, node, c0, c1);
+    const Two<double> rv = LdRO::ld2(r + node);
+    const A b0 = (c0 & CODE_CP) ? (A)rv.x : (A)0, b1 = (c1 & CODE_CP) ? (A)rv.y : (A)0;
+    if (b_out) st2o(b_out + node, b0, b1);
+    const A v0 = (c0 & CODE_CP) ? inv_diag_t<A>(c0, diag, node, o) * b0 / (A)theta : (A)0;
+    const A v1 = (c1 & CODE_CP) ? inv_diag_t<A>(c1, diag, node + 1, o) * b1 / (A)theta : (A)0;
+    st2o(x + node, v0, v1);
+    st2o(d + node, v0, v1);
+  }
+}
+
+// res = D^-1 (b - A x); d = c1 d + c2 res; xo = x + d   (xo may be FP64)
+template <int DIM, class V, class O>
+__global__ void __launch_bounds__(TILE_NODES) k_g_cheb_step(TileView tv, const uint8_t* __restrict__ code,
+                                                            const double* __restrict__ diag, GOp o,
+                                                            const V* __restrict__ b, const V* __restrict__ x,
+                                                            O* __restrict__ xo, V* __restrict__ d, double c1,
+                                                            double c2) {
+  using A = typename AccOf<V>::type;
+  EB_PAIR_LOOP(DIM, tv, node) {
+    uint32_t k0, k1;
+    ld_codes(code, node, k0, k1);
+    Two<A> xc, core;
+    stencil_pair<DIM, LdRO>(x, node, tv.nn, k0, k1, diag, tv.sy, tv.sz, xc, core);
+    const Two<A> bv = LdRO::ld2(b + node);
+    Two<A> dv{0, 0};
+    if (c1 != 0.0) {
+      const Two<A> t = LdRO::ld2(d + node);
+      dv = t;
+    }
+    const A ih = (A)o.inv_h2, sg = (A)o.sigma;
+    const A res0 = inv_diag_t<A>(k0, diag, node, o) * (bv.x - (core.x * ih + sg * xc.x));
+    const A res1 = inv_diag_t<A>(k1, diag, node + 1, o) * (bv.y - (core.y * ih + sg * xc.y));
+    const A d0 = (k0 & CODE_CP) ? (A)c1 * dv.x + (A)c2 * res0 : (A)0;
+    const A d1 = (k1 & CODE_CP) ? (A)c1 * dv.y + (A)c2 * res1 : (A)0;
+    st2o(d + node, d0, d1);
+    st2(xo + node, (O)((k0 & CODE_CP) ? xc.x + d0 : (A)0), (O)((k1 & CODE_CP) ? xc.y + d1 : (A)0));
+  }
+}
+
+template <int DIM, class V>
+__global__ void __launch_bounds__(TILE_NODES) k_g_resid(TileView tv, const uint8_t* __restrict__ code,
+                                                        const double* __restrict__ diag, GOp o,
+                                                        const V* __restrict__ b, const V* __restrict__ x,
+                                                        V* __restrict__ r) {
+  using A = typename AccOf<V>::type;
+  EB_PAIR_LOOP(DIM, tv, node) {
+    uint32_t c0, c1;
+    ld_codes(code, node, c0, c1);
+    Two<A> xc, core;
+    stencil_pair<DIM, LdRO>(x, node, tv.nn, c0, c1, diag, tv.sy, tv.sz, xc, core);
+    const Two<A> bv = LdRO::ld2(b + node);
+    const A ih = (A)o.inv_h2, sg = (A)o.sigma;
+    st2o(r + node, (c0 & CODE_CP) ? bv.x - (core.x * ih + sg * xc.x) : (A)0,
+         (c1 & CODE_CP) ? bv.y - (core.y * ih + sg * xc.y) : (A)0);
+  }
+}
+
+// out = R r with R's columns given as grid nodes
+template <class V>
+__global__ void k_restrict0(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ node_col,
+                            const V* __restrict__ v, const V* __restrict__ r, V* __restrict__ out) {
+  using A = typename AccOf<V>::type;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  A s = 0;
+  for (int32_t e = rp[i]; e < rp[i + 1]; ++e) s += (A)v[e] * (A)r[node_col[e]];
+  out[i] = (V)s;
+}
+
+// x[node(i)] += sum_c P_ic e_c over the CPs i
+template <class V>
+__global__ void k_prolong0(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const V* __restrict__ v, const int32_t* __restrict__ cp_node, const V* __restrict__ e,
+                           V* __restrict__ x) {
+  using A = typename AccOf<V>::type;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  A s = 0;
+  for (int32_t f = rp[i]; f < rp[i + 1]; ++f) s += (A)v[f] * (A)e[ci[f]];
+  const int32_t node = cp_node[i];
+  x[node] = (V)((A)x[node] + s);
+}
+
+// compact levels -----------------------------------------------------------
+template <class V>
+__global__ void k_c_cheb_first(int64_t n, const V* dinv, const V* b, V* x, V* d, double theta) {
+  using A = typename AccOf<V>::type;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const V v = (V)((A)dinv[i] * (A)b[i] / (A)theta);
+  x[i] = v;
+  d[i] = v;
+}
+
+template <class V>
+__global__ void k_c_cheb_step(CsrV<V> M, const V* dinv, const V* b, const V* x, V* xo, V* d, double c1, double c2) {
+  using A = typename AccOf<V>::type;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M.n) return;
+  A ax = 0;
+  for (int32_t e = M.rp[i]; e < M.rp[i + 1]; ++e) ax += (A)M.v[e] * (A)x[M.ci[e]];
+  const A res = (A)dinv[i] * ((A)b[i] - ax);
+  const A dv = (c1 == 0.0 ? (A)0 : (A)c1 * (A)d[i]) + (A)c2 * res;
+  d[i] = (V)dv;
+  xo[i] = (V)((A)x[i] + dv);
+}
+
+template <class V>
+__global__ void k_c_resid(CsrV<V> M, const V* b, const V* x, V* r) {
+  using A = typename AccOf<V>::type;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M.n) return;
+  A ax = 0;
+  for (int32_t e = M.rp[i]; e < M.rp[i + 1]; ++e) ax += (A)M.v[e] * (A)x[M.ci[e]];
+  r[i] = (V)((A)b[i] - ax);
+}
+
+template <class V>
+__global__ void k_c_spmv(CsrV<V> M, const V* x, V* y) {
+  using A = typename AccOf<V>::type;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M.n) return;
+  A s = 0;
+  for (int32_t e = M.rp[i]; e < M.rp[i + 1]; ++e) s += (A)M.v[e] * (A)x[M.ci[e]];
+  y[i] = (V)s;
+}
+
+template <class V>
+__global__ void k_c_prolong_add(CsrV<V> P, const V* e, V* x) {
+  using A = typename AccOf<V>::type;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P.n) return;
+  A s = 0;
+  for (int32_t f = P.rp[i]; f < P.rp[i + 1]; ++f) s += (A)P.v[f] * (A)e[P.ci[f]];
+  x[i] = (V)((A)x[i] + s);
+}
+
+// x = M b with M the FP64 inverse (row-major); one warp per row
+template <class V>
+__global__ void k_dense_gemv(const double* __restrict__ M, int64_t n, const V* __restrict__ b, V* __restrict__ x) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  double s = 0.0;
+  for (int64_t j = lane; j < n; j += 32) s += M[row * n + j] * (double)b[j];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) x[row] = (V)s;
+}
+
+template <class V>
+__global__ void k_gather_cp(int64_t n, const int32_t* cp_node, const double* g, V* out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (V)g[cp_node[i]];
+}
+
+template <class V>
+__global__ void k_scatter_cp(int64_t n, const int32_t* cp_node, const V* in, double* g) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) g[cp_node[i]] = (double)in[i];
+}
+
+__global__ void k_to_f32(int64_t n, const double* a, float* b) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+// ------------------------------------------------------------------ host
+struct ChebCoef {
+  double theta, c1[9], c2[9];
+  int deg;
+};
+
+static ChebCoef cheb_coef(double rho, int deg) {
+  ChebCoef c{};
+  const double lo = rho / 30.0, hi = 1.1 * rho;
+  c.theta = 0.5 * (hi + lo);
+  const double delta = 0.5 * (hi - lo);
+  const double sigma = c.theta / delta;
+  double r0 = 1.0 / sigma;
+  c.deg = deg;
+  c.c1[0] = 0.0;
+  c.c2[0] = 1.0 / c.theta;
+  for (int k = 1; k < deg; ++k) {
+    const double r1 = 1.0 / (2.0 * sigma - r0);
+    c.c1[k] = r1 * r0;
+    c.c2[k] = 2.0 * r1 / delta;
+    r0 = r1;
+  }
+  return c;
+}
+
+template <class V>
+struct LevelView;
+template <>
+struct LevelView<double> {
+  static VecSet<double>& vec(Level& L) { return L.v64; }
+  static VecSet<double>& grid(Hierarchy& H) { return H.g64; }
+  static CsrV<double> A(const Level& L) { return {L.A.n, L.A.rp, L.A.ci, L.A.v}; }
+  static CsrV<double> P(const Level& L) { return {L.P.n, L.P.rp, L.P.ci, L.P.v}; }
+  static CsrV<double> R(const Level& L) { return {L.R.n, L.R.rp, L.R.ci, L.R.v}; }
+  static const double* dinv(const Level& L) { return L.dinv; }
+};
+template <>
+struct LevelView<float> {
+  static VecSet<float>& vec(Level& L) { return L.v32; }
+  static VecSet<float>& grid(Hierarchy& H) { return H.g32; }
+  static CsrV<float> A(const Level& L) { return {L.A.n, L.A.rp, L.A.ci, L.A32}; }
+  static CsrV<float> P(const Level& L) { return {L.P.n, L.P.rp, L.P.ci, L.P32}; }
+  static CsrV<float> R(const Level& L) { return {L.R.n, L.R.rp, L.R.ci, L.R32}; }
+  static const float* dinv(const Level& L) { return L.dinv32; }
+};
+
+template <class V>
+static void vcycle_compact(Solver& S, size_t l, cudaStream_t s) {
+  using LV = LevelView<V>;
+  Hierarchy& H = *S.H;
+  Level& L = H.L[l];
+  VecSet<V>& v = LV::vec(L);
+  const int64_t n = L.A.n;
+  const unsigned nb = blocks_for(n, 256);
+  if (l + 1 == H.L.size()) {
+    S.nlaunch += 1;
+    k_dense_gemv<V><<<blocks_for(n * 32, 256), 256, 0, s>>>(H.coarse_inv, n, v.b, v.x);
+    return;
+  }
+  const ChebCoef cc = cheb_coef(L.rho, S.opts.cheb_degree);
+  S.nlaunch += 3 + 2 * cc.deg;  // first step, deg-1 steps, residual, restriction, prolongation, deg steps
+  const CsrV<V> A = LV::A(L);
+  k_c_cheb_first<V><<<nb, 256, 0, s>>>(n, LV::dinv(L), v.b, v.x, v.d, cc.theta);
+  for (int k = 1; k < cc.deg; ++k) {
+    k_c_cheb_step<V><<<nb, 256, 0, s>>>(A, LV::dinv(L), v.b, v.x, v.x2, v.d, cc.c1[k], cc.c2[k]);
+    std::swap(v.x, v.x2);
+  }
+  k_c_resid<V><<<nb, 256, 0, s>>>(A, v.b, v.x, v.r);
+  Level& C = H.L[l + 1];
+  VecSet<V>& cv = LV::vec(C);
+  k_c_spmv<V><<<blocks_for(C.A.n, 256), 256, 0, s>>>(LV::R(L), v.r, cv.b);
+  vcycle_compact<V>(S, l + 1, s);
+  k_c_prolong_add<V><<<nb, 256, 0, s>>>(LV::P(L), cv.x, v.x);
+  for (int k = 0; k < cc.deg; ++k) {
+    k_c_cheb_step<V><<<nb, 256, 0, s>>>(A, LV::dinv(L), v.b, v.x, v.x2, v.d, cc.c1[k], cc.c2[k]);
+    std::swap(v.x, v.x2);
+  }
+}
+
+template <class V, int DIM>
+static void vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s) {
+  using LV = LevelView<V>;
+  Hierarchy& H = *S.H;
+  const EBHandle& eb = *S.eb;
+  const Geometry& G = eb.g;
+  Level& L0 = H.L[0];
+  if (H.L.size() == 1) {  // single level: the dense inverse acts on the CP vector
+    VecSet<V>& v = LV::vec(L0);
+    const int64_t n = L0.A.n;
+    EB_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * G.num_nodes, s));
+    k_gather_cp<V><<<blocks_for(n, 256), 256, 0, s>>>(n, eb.cp_node, r, v.b);
+    k_dense_gemv<V><<<blocks_for(n * 32, 256), 256, 0, s>>>(H.coarse_inv, n, v.b, v.x);
+    k_scatter_cp<V><<<blocks_for(n, 256), 256, 0, s>>>(n, eb.cp_node, v.x, z);
+    EB_CUDA(cudaGetLastError());
+    S.nlaunch += 3;
+    return;
+  }
+  const double inv_h2 = 1.0 / (G.h * G.h);
+  const unsigned gb = tile_grid(eb);
+  const ChebCoef cc = cheb_coef(L0.rho, S.opts.cheb_degree);
+  const TileView tv = eb.tv();
+  const GOp o{inv_h2, S.shift, 1.0 / (S.shift + 2.0 * G.dim * inv_h2)};
+  S.nlaunch += 3 + 2 * cc.deg;
+  VecSet<V>& g = LV::grid(H);
+  // FP64 storage reads r directly; FP32 storage keeps a rounded copy in g.b
+  V* bcopy = std::is_same<V, double>::value ? nullptr : g.b;
+  const V* b = std::is_same<V, double>::value ? reinterpret_cast<const V*>(r) : g.b;
+  V* x = g.x;
+  V* x2 = g.x2;
+  k_g_cheb_first<DIM, V><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, eb.diag, o, r, bcopy, x, g.d, cc.theta);
+  for (int k = 1; k < cc.deg; ++k) {
+    S.prof_mark(s, true);
+    k_g_cheb_step<DIM, V, V><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, eb.diag, o, b, x, x2, g.d, cc.c1[k], cc.c2[k]);
+    S.prof_mark(s, false);
+    std::swap(x, x2);
+  }
+  k_g_resid<DIM, V><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, eb.diag, o, b, x, g.r);
+  Level& C = H.L[1];
+  VecSet<V>& cv = LV::vec(C);
+  const CsrV<V> R0 = LV::R(L0), P0 = LV::P(L0);
+  k_restrict0<V><<<blocks_for(C.A.n, 256), 256, 0, s>>>(C.A.n, R0.rp, L0.R0node, R0.v, g.r, cv.b);
+  vcycle_compact<V>(S, 1, s);
+  k_prolong0<V><<<blocks_for(P0.n, 256), 256, 0, s>>>(P0.n, P0.rp, P0.ci, P0.v, eb.cp_node, cv.x, x);
+  for (int k = 0; k < cc.deg; ++k) {
+    S.prof_mark(s, true);
+    if (k == cc.deg - 1)
+      k_g_cheb_step<DIM, V, double>
+          <<<gb, TILE_NODES, 0, s>>>(tv, eb.code, eb.diag, o, b, x, z, g.d, cc.c1[k], cc.c2[k]);
+    else
+      k_g_cheb_step<DIM, V, V><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, eb.diag, o, b, x, x2, g.d, cc.c1[k], cc.c2[k]);
+    S.prof_mark(s, false);
+    if (k != cc.deg - 1) std::swap(x, x2);
+  }
+  g.x = x;
+  g.x2 = x2;
+  EB_CUDA(cudaGetLastError());
+}
+
+void amg_vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s) {
+  const int dim = S.eb->g.dim;
+  if (S.opts.vcycle_prec == EB_F32) {
+    if (dim == 2) vcycle_grid<float, 2>(S, r, z, s);
+    else vcycle_grid<float, 3>(S, r, z, s);
+  } else {
+    if (dim == 2) vcycle_grid<double, 2>(S, r, z, s);
+    else vcycle_grid<double, 3>(S, r, z, s);
+  }
+}
+
+template <class V>
+static void alloc_set(VecSet<V>& v, int64_t n, bool with_b, cudaStream_t s) {
+  if (with_b) v.b = dalloc<V>(n, s);
+  v.x = dalloc<V>(n, s);
+  v.x2 = dalloc<V>(n, s);
+  v.d = dalloc<V>(n, s);
+  v.r = dalloc<V>(n, s);
+}
+
+template <class V>
+static void free_set(VecSet<V>& v, cudaStream_t s) {
+  dfree(v.b, s); dfree(v.x, s); dfree(v.x2, s); dfree(v.d, s); dfree(v.r, s);
+}
+
+static float* to_f32(const double* a, int64_t n, cudaStream_t s) {
+  float* b = dalloc<float>(n, s, false);
+  if (n > 0) k_to_f32<<<blocks_for(n, 256), 256, 0, s>>>(n, a, b);
+  return b;
+}
+
+void amg_alloc_vcycle(Solver& S, cudaStream_t s) {
+  Hierarchy& H = *S.H;
+  const int64_t nn = S.eb->g.num_nodes;
+  const bool f32 = S.opts.vcycle_prec == EB_F32;
+  const size_t first = H.L.size() == 1 ? 0 : 1;
+  if (f32) {
+    alloc_set(H.g32, nn, true, s);
+    for (size_t l = first; l < H.L.size(); ++l) alloc_set(H.L[l].v32, H.L[l].A.n, true, s);
+    for (size_t l = 0; l < H.L.size(); ++l) {
+      Level& L = H.L[l];
+      L.A32 = to_f32(L.A.v, L.A.nnz, s);
+      if (L.dinv) L.dinv32 = to_f32(L.dinv, L.A.n, s);
+      if (L.P.v) L.P32 = to_f32(L.P.v, L.P.nnz, s);
+      if (L.R.v) L.R32 = to_f32(L.R.v, L.R.nnz, s);
+    }
+  } else {
+    alloc_set(H.g64, nn, false, s);
+    for (size_t l = first; l < H.L.size(); ++l) alloc_set(H.L[l].v64, H.L[l].A.n, true, s);
+  }
+  EB_CUDA(cudaGetLastError());
+}
+
+void amg_free_vcycle(Hierarchy& H, cudaStream_t s) {
+  free_set(H.g64, s);
+  free_set(H.g32, s);
+  for (Level& L : H.L) {
+    free_set(L.v64, s);
+    free_set(L.v32, s);
+    dfree(L.A32, s); dfree(L.P32, s); dfree(L.R32, s); dfree(L.dinv32, s);
+  }
+}
+
+}  // namespace ebk

@@ -184,7 +184,7 @@ int amg_setup(const eb_handle* eb, double shift, const amg_opts* opts, amg_handl
   Solver& S = a->s;
   S.eb = const_cast<EBHandle*>(&eb->h);
   S.shift = shift;
-  amg_opts o{25, 1024, 0.08, 2, EB_F64};
+  amg_opts o{25, 1024, 0.02, 2, EB_F64};
   if (opts) o = *opts;
   S.opts = o;
   int st = guarded([&] {
@@ -213,6 +213,7 @@ void amg_destroy(amg_handle* amg) {
   if (!amg) return;
   amg_free(amg->s);
   amg->s.free_work();
+  amg->s.prof_release();
   cudaStreamSynchronize(amg->s.eb->home);
   delete amg;
 }
@@ -254,7 +255,7 @@ int pcg_solve(const amg_handle* amg, const double* b_dev, double* x_dev, double 
     set_error("pcg_solve: NULL argument");
     return EB_ERR_INVALID;
   }
-  pcg_opts o{amg->s.H ? EB_PC_AMG : EB_PC_JACOBI, 1, 1};
+  pcg_opts o{amg->s.H ? EB_PC_AMG : EB_PC_JACOBI, 1, 1, 0};
   if (opts) o = *opts;
   int rc = EB_OK;
   int st = guarded([&] { rc = const_cast<Solver&>(amg->s).pcg(b_dev, x_dev, rtol, maxit, o, stats, stream); });

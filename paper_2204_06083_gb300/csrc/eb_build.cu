@@ -294,6 +294,19 @@ __global__ void k_compact(const int32_t* flag, const int32_t* off, int64_t n, in
   if (t < n && flag[t]) out[off[t]] = (int32_t)t;
 }
 
+// corner node and extents of each listed tile
+__global__ void k_tile_geom(Geometry G, const int32_t* tiles, int64_t nt, int32_t* base, int32_t* lim) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nt) return;
+  int64_t t = tiles[k];
+  int64_t bx = t % G.ntx, r = t / G.ntx, by = r % G.nty, bz = r / G.nty;
+  int64_t x0 = bx * G.tx, y0 = by * G.ty, z0 = bz * G.tz;
+  base[k] = (int32_t)(x0 + (int64_t)G.n0 * (y0 + (int64_t)G.n1 * z0));
+  const int64_t rx = G.n0 - x0, ry = G.n1 - y0, rz = G.n2 - z0;
+  const int lx = (int)(rx < G.tx ? rx : G.tx), ly = (int)(ry < G.ty ? ry : G.ty), lz = (int)(rz < G.tz ? rz : G.tz);
+  lim[k] = lx | (ly << 8) | (lz << 16);
+}
+
 static LSDev to_dev(const eb_levelset& ls, int dim) {
   LSDev L{};
   L.kind = ls.kind;
@@ -336,9 +349,9 @@ void build_handle(EBHandle& eb, const eb_grid& grid, const eb_levelset& ls, cuda
   for (int a = 0; a < 3; ++a) G.lo[a] = grid.lo[a];
   G.h = grid.h;
   if (grid.dim == 2) {
-    G.tx = 32; G.ty = 8; G.tz = 1;
+    G.tx = TileShape<2>::X; G.ty = TileShape<2>::Y; G.tz = TileShape<2>::Z;
   } else {
-    G.tx = 16; G.ty = 4; G.tz = 4;
+    G.tx = TileShape<3>::X; G.ty = TileShape<3>::Y; G.tz = TileShape<3>::Z;
   }
   G.ntx = (G.n0 + G.tx - 1) / G.tx;
   G.nty = (G.n1 + G.ty - 1) / G.ty;
@@ -409,6 +422,9 @@ void build_handle(EBHandle& eb, const eb_grid& grid, const eb_levelset& ls, cuda
   eb.num_tiles = nt;
   eb.tiles = dalloc<int32_t>(nt, s, false);
   k_compact<<<blocks_for(ntiles_all, T), T, 0, s>>>(tflag, toff, ntiles_all, eb.tiles);
+  eb.tile_base = dalloc<int32_t>(nt, s, false);
+  eb.tile_lim = dalloc<int32_t>(nt, s, false);
+  k_tile_geom<<<blocks_for(nt, T), T, 0, s>>>(G, eb.tiles, nt, eb.tile_base, eb.tile_lim);
   EB_CUDA(cudaGetLastError());
   eb.num_far = (int64_t)hst.num_far;
   eb.max_delta_over_h = hst.max_delta_over_h;
@@ -421,45 +437,41 @@ void build_handle(EBHandle& eb, const eb_grid& grid, const eb_levelset& ls, cuda
 void destroy_handle(EBHandle& eb) {
   cudaStream_t s = eb.home;
   dfree(eb.code, s); dfree(eb.diag, s); dfree(eb.cp_of_node, s); dfree(eb.cp_node, s);
-  dfree(eb.tiles, s); dfree(eb.cut_cp, s); dfree(eb.cut_dir, s); dfree(eb.cut_delta, s);
+  dfree(eb.tiles, s); dfree(eb.tile_base, s); dfree(eb.tile_lim, s); dfree(eb.cut_cp, s); dfree(eb.cut_dir, s); dfree(eb.cut_delta, s);
   dfree(eb.cut_c, s); dfree(eb.cut_xg, s); dfree(eb.cut_off, s);
   cudaStreamSynchronize(s);
 }
 
 // ------------------------------------------------------------------- RHS
-__global__ void k_rhs(Geometry G, const int32_t* tiles, int64_t ntiles, const uint8_t* code,
-                      const int32_t* cp_of_node, const int32_t* cut_off, const double* cut_c, const double* f,
-                      const double* ug, double* b, double h2) {
-  const int tsz = G.tx * G.ty * G.tz;
-  for (int64_t tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
-    int64_t t = tiles[tt];
-    int64_t bx = t % G.ntx, r = t / G.ntx, by = r % G.nty, bz = r / G.nty;
-    for (int l = threadIdx.x; l < tsz; l += blockDim.x) {
-      int lx = l % G.tx, ly = (l / G.tx) % G.ty, lz = l / (G.tx * G.ty);
-      int64_t ix = bx * G.tx + lx, iy = by * G.ty + ly, iz = bz * G.tz + lz;
-      if (ix >= G.n0 || iy >= G.n1 || iz >= G.n2) continue;
-      int64_t node = ix + (int64_t)G.n0 * (iy + (int64_t)G.n1 * iz);
-      uint8_t c = code[node];
-      double v = 0.0;
-      if (c & CODE_CP) {
-        double acc = 0.0;
-        if (c & 0x3F) {
-          int32_t k = cp_of_node[node];
-          for (int j = cut_off[k]; j < cut_off[k + 1]; ++j) acc = __dadd_rn(acc, __ddiv_rn(__dmul_rn(cut_c[j], ug[j]), h2));
-        }
-        v = __dadd_rn(-f[node], acc);
+// b_k = -f_k + sum over the cuts of k of (c_s u_Gamma) / h^2, summed in cut
+// order; 0 at the non-CP nodes of the active tiles.
+template <int DIM>
+__global__ void __launch_bounds__(TILE_NODES) k_rhs(TileView tv, const uint8_t* code, const int32_t* cp_of_node,
+                                                    const int32_t* cut_off, const double* cut_c, const double* f,
+                                                    const double* ug, double* b, double h2) {
+  EB_TILE_LOOP(DIM, tv, node) {
+    const uint8_t c = code[node];
+    double v = 0.0;
+    if (c & CODE_CP) {
+      double acc = 0.0;
+      if (c & 0x3F) {
+        const int32_t k = cp_of_node[node];
+        for (int j = cut_off[k]; j < cut_off[k + 1]; ++j) acc = __dadd_rn(acc, __ddiv_rn(__dmul_rn(cut_c[j], ug[j]), h2));
       }
-      b[node] = v;
+      v = __dadd_rn(-f[node], acc);
     }
+    b[node] = v;
   }
 }
 
 void launch_rhs(const EBHandle& eb, const double* f, const double* ug, double* b, cudaStream_t s) {
   const Geometry& G = eb.g;
-  double h2 = G.h * G.h;
-  unsigned blocks = (unsigned)std::min<int64_t>(eb.num_tiles, (int64_t)num_sms() * 8);
-  k_rhs<<<blocks, 256, 0, s>>>(G, eb.tiles, eb.num_tiles, eb.code, eb.cp_of_node, eb.cut_off, eb.cut_c, f, ug, b,
-                               h2);
+  const double h2 = G.h * G.h;
+  const unsigned blocks = tile_grid(eb);
+  if (G.dim == 2)
+    k_rhs<2><<<blocks, TILE_NODES, 0, s>>>(eb.tv(), eb.code, eb.cp_of_node, eb.cut_off, eb.cut_c, f, ug, b, h2);
+  else
+    k_rhs<3><<<blocks, TILE_NODES, 0, s>>>(eb.tv(), eb.code, eb.cp_of_node, eb.cut_off, eb.cut_c, f, ug, b, h2);
   EB_CUDA(cudaGetLastError());
 }
 

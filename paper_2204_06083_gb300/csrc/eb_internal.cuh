@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/eb.h"
+#include "tiles.cuh"
 
 namespace ebk {
 
@@ -100,6 +101,9 @@ struct EBHandle {
   int32_t* cp_of_node = nullptr; // [num_nodes]
   int32_t* cp_node = nullptr;    // [num_cp]
   int32_t* tiles = nullptr;      // [num_tiles] linear tile index, ascending
+  int32_t* tile_base = nullptr;  // [num_tiles] corner node of each listed tile
+  int32_t* tile_lim = nullptr;   // [num_tiles] extents x | y << 8 | z << 16
+  TileView tv() const { return TileView{tile_base, tile_lim, num_tiles, g.n0, g.n0 * g.n1, (int32_t)g.num_nodes}; }
   int32_t* cut_cp = nullptr;     // [num_cut]
   int32_t* cut_dir = nullptr;    // [num_cut]
   double* cut_delta = nullptr;   // [num_cut]
@@ -133,6 +137,12 @@ inline int num_sms() {
     if (v <= 0) v = 1;
   }
   return v;
+}
+
+// CTAs for a grid-stride loop over the active tiles (8 resident per SM)
+inline unsigned tile_grid(const EBHandle& eb, int per_sm = 8) {
+  int64_t b = eb.num_tiles < (int64_t)num_sms() * per_sm ? eb.num_tiles : (int64_t)num_sms() * per_sm;
+  return (unsigned)(b < 1 ? 1 : b);
 }
 
 inline unsigned blocks_for(int64_t n, int threads) {

@@ -4,10 +4,11 @@
 // Vectors live in the full-grid layout and are touched on the active tiles
 // only.  Every reduction is two-pass and deterministic: each CTA of a fixed
 // grid reduces its nodes in a fixed order to one partial, and a single CTA
-// combines the partials in a fixed tree and updates the scalar recurrences
-// (alpha, beta, ...) in device memory, so no scalar crosses to the host except
+// combines the partials in a fixed tree and advances the scalar recurrences
+// (alpha, beta, ...) in device memory.  No scalar crosses to the host except
 // the convergence flag, read every check_every iterations.
 #include "eb_solver.cuh"
+#include "stencil.cuh"
 
 #include <algorithm>
 #include <chrono>
@@ -15,11 +16,9 @@
 
 namespace ebk {
 
-constexpr int VT = 256;
-
 __device__ __forceinline__ double block_sum(double v, double* sm) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __syncthreads();
   if (lane == 0) sm[w] = v;
   __syncthreads();
@@ -29,101 +28,69 @@ __device__ __forceinline__ double block_sum(double v, double* sm) {
   return s;
 }
 
-struct TileIt {
-  const Geometry G;
-  __device__ __forceinline__ bool node(int64_t t, int l, int64_t& out) const {
-    int64_t bx = t % G.ntx, r = t / G.ntx, by = r % G.nty, bz = r / G.nty;
-    int lx = l % G.tx, ly = (l / G.tx) % G.ty, lz = l / (G.tx * G.ty);
-    int64_t ix = bx * G.tx + lx, iy = by * G.ty + ly, iz = bz * G.tz + lz;
-    out = ix + (int64_t)G.n0 * (iy + (int64_t)G.n1 * iz);
-    return ix < G.n0 && iy < G.n1 && iz < G.n2;
-  }
+struct OpParams {
+  double inv_h2, sigma, dinv_int;
 };
 
-#define FOR_TILE_NODES(G, tiles, ntiles, node)                                  \
-  const int tsz_ = (G).tx * (G).ty * (G).tz;                                    \
-  TileIt it_{G};                                                                \
-  for (int64_t tt_ = blockIdx.x; tt_ < (ntiles); tt_ += gridDim.x)              \
-    for (int l_ = threadIdx.x; l_ < tsz_; l_ += blockDim.x)                     \
-      if (int64_t node = 0; it_.node((tiles)[tt_], l_, node))
-
-__device__ __forceinline__ double cp_stencil(const Geometry& G, const double* x, int64_t node, uint8_t c,
-                                             const double* diag, double inv_h2, double sigma) {
-  const int64_t sy = G.n0, sz = (int64_t)G.n0 * G.n1;
-  const double xc = x[node];
-  const uint8_t m = c & 0x3F;
-  double sum = 0.0;
-  if (!(m & 1)) sum += x[node - 1];
-  if (!(m & 2)) sum += x[node + 1];
-  if (!(m & 4)) sum += x[node - sy];
-  if (!(m & 8)) sum += x[node + sy];
-  if (G.dim == 3) {
-    if (!(m & 16)) sum += x[node - sz];
-    if (!(m & 32)) sum += x[node + sz];
-  }
-  const double D = m ? diag[node] : (double)(2 * G.dim);
-  return (D * xc - sum) * inv_h2 + sigma * xc;
-}
-
-// dinv = 1 / (sigma + D/h^2) at the CPs
-__global__ void k_dinv(Geometry G, const int32_t* tiles, int64_t ntiles, const uint8_t* code, const double* diag,
-                       double sigma, double inv_h2, double* dinv) {
-  FOR_TILE_NODES(G, tiles, ntiles, node) {
-    uint8_t c = code[node];
-    double v = 0.0;
-    if (c & CODE_CP) {
-      double D = (c & 0x3F) ? diag[node] : (double)(2 * G.dim);
-      v = 1.0 / (sigma + D * inv_h2);
-    }
-    dinv[node] = v;
-  }
+// (sigma I + A) x for the pair at node
+template <int DIM>
+__device__ __forceinline__ void op_pair(const TileView& tv, const double* x, int32_t node, uint32_t c0, uint32_t c1,
+                                        const double* diag, const OpParams& o, Two<double>& xc, Two<double>& ax) {
+  Two<double> core;
+  stencil_pair<DIM, LdRO>(x, node, tv.nn, c0, c1, diag, tv.sy, tv.sz, xc, core);
+  ax.x = core.x * o.inv_h2 + o.sigma * xc.x;
+  ax.y = core.y * o.inv_h2 + o.sigma * xc.y;
 }
 
 // r = b - (sigma I + A) x  (b masked to the CPs); partials (b.b, r.r)
-__global__ void k_resid(Geometry G, const int32_t* tiles, int64_t ntiles, const uint8_t* code, const double* diag,
-                        double sigma, double inv_h2, const double* b, const double* x, double* r, double* part) {
+template <int DIM>
+__global__ void __launch_bounds__(TILE_NODES) k_resid(TileView tv, const uint8_t* code, const double* diag, OpParams o,
+                                                      const double* b, const double* x, double* r, double* part) {
   __shared__ double sm[32];
   double sbb = 0.0, srr = 0.0;
-  FOR_TILE_NODES(G, tiles, ntiles, node) {
-    uint8_t c = code[node];
-    double rv = 0.0;
-    if (c & CODE_CP) {
-      double bv = b[node];
-      rv = bv - cp_stencil(G, x, node, c, diag, inv_h2, sigma);
-      sbb += bv * bv;
-      srr += rv * rv;
-    }
-    r[node] = rv;
+  EB_PAIR_LOOP(DIM, tv, node) {
+    uint32_t c0, c1;
+    ld_codes(code, node, c0, c1);
+    Two<double> xc, ax;
+    op_pair<DIM>(tv, x, node, c0, c1, diag, o, xc, ax);
+    const Two<double> bv = LdRO::ld2(b + node);
+    const double b0 = (c0 & CODE_CP) ? bv.x : 0.0, b1 = (c1 & CODE_CP) ? bv.y : 0.0;
+    const double r0 = (c0 & CODE_CP) ? b0 - ax.x : 0.0, r1 = (c1 & CODE_CP) ? b1 - ax.y : 0.0;
+    sbb += b0 * b0 + b1 * b1;
+    srr += r0 * r0 + r1 * r1;
+    st2(r + node, r0, r1);
   }
-  double a = block_sum(sbb, sm);
-  double bsum = block_sum(srr, sm);
+  const double a = block_sum(sbb, sm);
+  const double q = block_sum(srr, sm);
   if (threadIdx.x == 0) {
     part[2 * blockIdx.x] = a;
-    part[2 * blockIdx.x + 1] = bsum;
+    part[2 * blockIdx.x + 1] = q;
   }
 }
 
 // q = (sigma I + A) p; partial p.q
-__global__ void k_apply_dot(Geometry G, const int32_t* tiles, int64_t ntiles, const uint8_t* code, const double* diag,
-                            double sigma, double inv_h2, const double* p, double* q, double* part) {
+template <int DIM>
+__global__ void __launch_bounds__(TILE_NODES) k_apply_dot(TileView tv, const uint8_t* code, const double* diag,
+                                                          OpParams o, const double* p, double* q, double* part) {
   __shared__ double sm[32];
   double s = 0.0;
-  FOR_TILE_NODES(G, tiles, ntiles, node) {
-    uint8_t c = code[node];
-    double qv = 0.0;
-    if (c & CODE_CP) {
-      qv = cp_stencil(G, p, node, c, diag, inv_h2, sigma);
-      s += p[node] * qv;
-    }
-    q[node] = qv;
+  EB_PAIR_LOOP(DIM, tv, node) {
+    uint32_t c0, c1;
+    ld_codes(code, node, c0, c1);
+    Two<double> xc, ax;
+    op_pair<DIM>(tv, p, node, c0, c1, diag, o, xc, ax);
+    const double q0 = (c0 & CODE_CP) ? ax.x : 0.0, q1 = (c1 & CODE_CP) ? ax.y : 0.0;
+    s += xc.x * q0 + xc.y * q1;
+    st2(q + node, q0, q1);
   }
-  double t = block_sum(s, sm);
+  const double t = block_sum(s, sm);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 // x += alpha p; r -= alpha q; partial r.r
-__global__ void k_update_xr(Geometry G, const int32_t* tiles, int64_t ntiles, const PcgScalars* sc, double* x,
-                            double* r, const double* p, const double* q, double* part) {
+template <int DIM>
+__global__ void __launch_bounds__(TILE_NODES) k_update_xr(TileView tv, const PcgScalars* sc, double* x, double* r,
+                                                          const double* p, const double* q, double* part) {
   __shared__ double sm[32];
   if (sc->done) {
     if (threadIdx.x == 0) part[blockIdx.x] = 0.0;
@@ -131,77 +98,134 @@ __global__ void k_update_xr(Geometry G, const int32_t* tiles, int64_t ntiles, co
   }
   const double alpha = sc->alpha;
   double s = 0.0;
-  FOR_TILE_NODES(G, tiles, ntiles, node) {
-    double rv = r[node] - alpha * q[node];
-    x[node] += alpha * p[node];
-    r[node] = rv;
-    s += rv * rv;
+  EB_PAIR_LOOP(DIM, tv, node) {
+    const Two<double> rv = ld2d(r + node), qv = LdRO::ld2(q + node), pv = LdRO::ld2(p + node), xv = ld2d(x + node);
+    const double r0 = rv.x - alpha * qv.x, r1 = rv.y - alpha * qv.y;
+    st2(x + node, xv.x + alpha * pv.x, xv.y + alpha * pv.y);
+    st2(r + node, r0, r1);
+    s += r0 * r0 + r1 * r1;
   }
-  double t = block_sum(s, sm);
+  const double t = block_sum(s, sm);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
-// z = dinv r; partial r.z
-__global__ void k_jacobi_dot(Geometry G, const int32_t* tiles, int64_t ntiles, const double* dinv, const double* r,
-                             double* z, double* part) {
+// z = D^-1 r (Jacobi); partial r.z
+template <int DIM>
+__global__ void __launch_bounds__(TILE_NODES) k_jacobi_dot(TileView tv, const uint8_t* code, const double* diag,
+                                                           OpParams o, const double* r, double* z, double* part) {
   __shared__ double sm[32];
   double s = 0.0;
-  FOR_TILE_NODES(G, tiles, ntiles, node) {
-    double rv = r[node];
-    double zv = dinv[node] * rv;
-    z[node] = zv;
-    s += rv * zv;
+  EB_PAIR_LOOP(DIM, tv, node) {
+    uint32_t c0, c1;
+    ld_codes(code, node, c0, c1);
+    const Two<double> rv = LdRO::ld2(r + node);
+    const double z0 = (c0 & CODE_CP) ? inv_diag(c0, diag, node, o.inv_h2, o.sigma, o.dinv_int) * rv.x : 0.0;
+    const double z1 = (c1 & CODE_CP) ? inv_diag(c1, diag, node + 1, o.inv_h2, o.sigma, o.dinv_int) * rv.y : 0.0;
+    st2(z + node, z0, z1);
+    s += rv.x * z0 + rv.y * z1;
   }
-  double t = block_sum(s, sm);
+  const double t = block_sum(s, sm);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
-__global__ void k_dot(Geometry G, const int32_t* tiles, int64_t ntiles, const double* a, const double* b, double* part) {
+template <int DIM>
+__global__ void __launch_bounds__(TILE_NODES) k_dot(TileView tv, const double* a, const double* b, double* part) {
   __shared__ double sm[32];
   double s = 0.0;
-  FOR_TILE_NODES(G, tiles, ntiles, node) { s += a[node] * b[node]; }
-  double t = block_sum(s, sm);
+  EB_PAIR_LOOP(DIM, tv, node) {
+    const Two<double> av = LdRO::ld2(a + node), bv = LdRO::ld2(b + node);
+    s += av.x * bv.x + av.y * bv.y;
+  }
+  const double t = block_sum(s, sm);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
-// p = z + beta p   (beta = 0 on the first iteration of a cycle)
-__global__ void k_xpby(Geometry G, const int32_t* tiles, int64_t ntiles, const PcgScalars* sc, const double* z,
-                       double* p, int first) {
+// partials (r.z, r.zold) for the flexible beta
+template <int DIM>
+__global__ void __launch_bounds__(TILE_NODES) k_dot2(TileView tv, const double* r, const double* z, const double* zo,
+                                                     double* part) {
+  __shared__ double sm[32];
+  double s = 0.0, t = 0.0;
+  EB_PAIR_LOOP(DIM, tv, node) {
+    const Two<double> rv = LdRO::ld2(r + node), zv = LdRO::ld2(z + node), ov = LdRO::ld2(zo + node);
+    s += rv.x * zv.x + rv.y * zv.y;
+    t += rv.x * ov.x + rv.y * ov.y;
+  }
+  const double a = block_sum(s, sm);
+  const double b = block_sum(t, sm);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = b;
+  }
+}
+
+// p = z + beta p   (p = z on the first iteration of a cycle); zold = z when
+// zold is given (flexible CG)
+template <int DIM>
+__global__ void __launch_bounds__(TILE_NODES) k_xpby(TileView tv, const PcgScalars* sc, const double* z, double* p,
+                                                     double* zold, int first) {
   if (sc->done) return;
   const double beta = first ? 0.0 : sc->beta;
-  FOR_TILE_NODES(G, tiles, ntiles, node) { p[node] = first ? z[node] : z[node] + beta * p[node]; }
-}
-
-// rhs for the theta-method: (u/dt - (1-theta) A u + theta b1 + (1-theta) b0) / theta
-__global__ void k_heat_rhs(Geometry G, const int32_t* tiles, int64_t ntiles, const uint8_t* code, const double* diag,
-                           double inv_h2, double dt, double theta, const double* u, const double* b1,
-                           const double* b0, double* out) {
-  FOR_TILE_NODES(G, tiles, ntiles, node) {
-    uint8_t c = code[node];
-    double v = 0.0;
-    if (c & CODE_CP) {
-      double uv = u[node];
-      v = uv / dt + theta * b1[node];
-      if (theta < 1.0) v += (1.0 - theta) * (b0[node] - cp_stencil(G, u, node, c, diag, inv_h2, 0.0));
-      v /= theta;
+  EB_PAIR_LOOP(DIM, tv, node) {
+    const Two<double> zv = LdRO::ld2(z + node);
+    if (first) {
+      st2(p + node, zv.x, zv.y);
+    } else {
+      const Two<double> pv = ld2d(p + node);
+      st2(p + node, zv.x + beta * pv.x, zv.y + beta * pv.y);
     }
-    out[node] = v;
+    if (zold) st2(zold + node, zv.x, zv.y);
   }
 }
 
-__global__ void k_mask_copy(Geometry G, const int32_t* tiles, int64_t ntiles, const uint8_t* code, const double* in,
-                            double* out) {
-  FOR_TILE_NODES(G, tiles, ntiles, node) { out[node] = (code[node] & CODE_CP) ? in[node] : 0.0; }
+template <int DIM>
+__global__ void __launch_bounds__(TILE_NODES) k_copy_tiles(TileView tv, const double* a, double* b) {
+  EB_PAIR_LOOP(DIM, tv, node) {
+    const Two<double> v = LdRO::ld2(a + node);
+    st2(b + node, v.x, v.y);
+  }
+}
+
+// rhs of the theta-method: (u/dt - (1-theta) A u + theta b1 + (1-theta) b0) / theta
+template <int DIM>
+__global__ void __launch_bounds__(TILE_NODES) k_heat_rhs(TileView tv, const uint8_t* code, const double* diag,
+                                                         double inv_h2, double dt, double theta, const double* u,
+                                                         const double* b1, const double* b0, double* out) {
+  EB_PAIR_LOOP(DIM, tv, node) {
+    uint32_t c0, c1;
+    ld_codes(code, node, c0, c1);
+    Two<double> uc, core;
+    stencil_pair<DIM, LdRO>(u, node, tv.nn, c0, c1, diag, tv.sy, tv.sz, uc, core);
+    const Two<double> b1v = LdRO::ld2(b1 + node), b0v = LdRO::ld2(b0 + node);
+    double v0 = uc.x / dt + theta * b1v.x, v1 = uc.y / dt + theta * b1v.y;
+    if (theta < 1.0) {
+      v0 += (1.0 - theta) * (b0v.x - core.x * inv_h2);
+      v1 += (1.0 - theta) * (b0v.y - core.y * inv_h2);
+    }
+    st2(out + node, (c0 & CODE_CP) ? v0 / theta : 0.0, (c1 & CODE_CP) ? v1 / theta : 0.0);
+  }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(TILE_NODES) k_mask_copy(TileView tv, const uint8_t* code, const double* in,
+                                                          double* out) {
+  EB_PAIR_LOOP(DIM, tv, node) {
+    uint32_t c0, c1;
+    ld_codes(code, node, c0, c1);
+    const Two<double> v = ld2d(in + node);
+    st2(out + node, (c0 & CODE_CP) ? v.x : 0.0, (c1 & CODE_CP) ? v.y : 0.0);
+  }
 }
 
 // Combine partials in a fixed order and advance the scalar recurrences.
 __global__ void k_finalize(const double* part, int nblk, int op, PcgScalars* sc) {
   __shared__ double sm[2][1024];
   double a = 0.0, b = 0.0;
-  const int stride = (op == FIN_INIT) ? 2 : 1;
+  const bool pairs = op == FIN_INIT || op == FIN_RZ0F || op == FIN_BETAF;
+  const int stride = pairs ? 2 : 1;
   for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
     a += part[stride * i];
-    if (op == FIN_INIT) b += part[2 * i + 1];
+    if (pairs) b += part[2 * i + 1];
   }
   sm[0][threadIdx.x] = a;
   sm[1][threadIdx.x] = b;
@@ -223,8 +247,19 @@ __global__ void k_finalize(const double* part, int nblk, int op, PcgScalars* sc)
       sc->done = (sm[1][0] <= sc->tol2 * v) ? 1 : 0;
       break;
     case FIN_RZ0:
+    case FIN_RZ0F:
       sc->rz = v;
       if (!isfinite(v)) sc->flags |= PCG_FLAG_NONFINITE;
+      break;
+    case FIN_BETAF:  // flexible (Polak-Ribiere): beta = r'(z - zold) / rz_old
+      if (sc->done) break;
+      if (!(v > 0.0)) {
+        sc->flags |= isfinite(v) ? PCG_FLAG_BREAKDOWN : PCG_FLAG_NONFINITE;
+        sc->done = 1;
+        break;
+      }
+      sc->beta = (v - sm[1][0]) / sc->rz;
+      sc->rz = v;
       break;
     case FIN_ALPHA:
       if (sc->done) break;
@@ -262,6 +297,24 @@ __global__ void k_finalize(const double* part, int nblk, int op, PcgScalars* sc)
 }
 
 // ---------------------------------------------------------------- host side
+#define EB_DIM_LAUNCH(dim, kernel, grid, ...)                                 \
+  do {                                                                       \
+    ++nlaunch;                                                               \
+    if ((dim) == 2)                                                          \
+      kernel<2><<<(grid), TILE_NODES, 0, s>>>(__VA_ARGS__);                  \
+    else                                                                     \
+      kernel<3><<<(grid), TILE_NODES, 0, s>>>(__VA_ARGS__);                  \
+  } while (0)
+
+static OpParams op_params(const Solver& S) {
+  const Geometry& G = S.eb->g;
+  OpParams o;
+  o.inv_h2 = 1.0 / (G.h * G.h);
+  o.sigma = S.shift;
+  o.dinv_int = 1.0 / (S.shift + 2.0 * G.dim * o.inv_h2);
+  return o;
+}
+
 void Solver::alloc_work(cudaStream_t s) {
   const int64_t nn = eb->g.num_nodes;
   r = dalloc<double>(nn, s);
@@ -269,50 +322,58 @@ void Solver::alloc_work(cudaStream_t s) {
   p = dalloc<double>(nn, s);
   q = dalloc<double>(nn, s);
   tmp = dalloc<double>(nn, s);
-  dinv = dalloc<double>(nn, s);
+  if (opts.vcycle_prec == EB_F32) zold = dalloc<double>(nn, s);
   nblk = (int)std::min<int64_t>(std::max<int64_t>(eb->num_tiles, 1), (int64_t)num_sms() * 4);
-  nblk = std::min(nblk, 1024 * 8);
   part = dalloc<double>(2 * (int64_t)nblk, s);
   sc = dalloc<PcgScalars>(1, s);
   EB_CUDA(cudaMallocHost((void**)&sc_host, sizeof(PcgScalars)));
-  const Geometry& G = eb->g;
-  k_dinv<<<nblk, VT, 0, s>>>(G, eb->tiles, eb->num_tiles, eb->code, eb->diag, shift, 1.0 / (G.h * G.h), dinv);
-  EB_CUDA(cudaGetLastError());
 }
 
 void Solver::free_work() {
   cudaStream_t s = eb->home;
-  dfree(r, s); dfree(z, s); dfree(p, s); dfree(q, s); dfree(tmp, s); dfree(dinv, s); dfree(part, s); dfree(sc, s);
+  graph_release();
+  if (cap_stream) cudaStreamDestroy(cap_stream);
+  cap_stream = nullptr;
+  dfree(r, s); dfree(z, s); dfree(p, s); dfree(q, s); dfree(tmp, s); dfree(zold, s); dfree(part, s); dfree(sc, s);
   if (sc_host) cudaFreeHost(sc_host);
   sc_host = nullptr;
 }
 
 void Solver::finalize(int op, cudaStream_t s) {
+  ++nlaunch;
   k_finalize<<<1, 1024, 0, s>>>(part, nblk, op, sc);
 }
 
 void Solver::precondition(int kind, const double* rin, double* zout, cudaStream_t s) {
-  const Geometry& G = eb->g;
+  const int dim = eb->g.dim;
+  const TileView tv = eb->tv();
   if (kind == EB_PC_AMG && H) {
     amg_vcycle_grid(*this, rin, zout, s);
-    k_dot<<<nblk, VT, 0, s>>>(G, eb->tiles, eb->num_tiles, rin, zout, part);
+    if (flexible())
+      EB_DIM_LAUNCH(dim, k_dot2, nblk, tv, rin, zout, zold, part);
+    else
+      EB_DIM_LAUNCH(dim, k_dot, nblk, tv, rin, zout, part);
   } else if (kind == EB_PC_NONE) {
-    EB_CUDA(cudaMemcpyAsync(zout, rin, sizeof(double) * G.num_nodes, cudaMemcpyDeviceToDevice, s));
-    k_dot<<<nblk, VT, 0, s>>>(G, eb->tiles, eb->num_tiles, rin, zout, part);
+    EB_DIM_LAUNCH(dim, k_copy_tiles, nblk, tv, rin, zout);
+    EB_DIM_LAUNCH(dim, k_dot, nblk, tv, rin, zout, part);
   } else {
-    k_jacobi_dot<<<nblk, VT, 0, s>>>(G, eb->tiles, eb->num_tiles, dinv, rin, zout, part);
+    EB_DIM_LAUNCH(dim, k_jacobi_dot, nblk, tv, eb->code, eb->diag, op_params(*this), rin, zout, part);
   }
 }
 
 int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_opts& o, pcg_stats* stats,
                 cudaStream_t s) {
-  const Geometry& G = eb->g;
-  const double inv_h2 = 1.0 / (G.h * G.h);
+  const int dim = eb->g.dim;
+  const TileView tv = eb->tv();
+  const OpParams op = op_params(*this);
   const int kind = o.precond;
   EB_REQUIRE(kind == EB_PC_AMG || kind == EB_PC_JACOBI || kind == EB_PC_NONE, EB_ERR_INVALID, "bad preconditioner");
   EB_REQUIRE(kind != EB_PC_AMG || H != nullptr, EB_ERR_INVALID, "AMG preconditioner requested without a hierarchy");
   EB_REQUIRE(rtol > 0.0 && maxit >= 0, EB_ERR_INVALID, "rtol must be > 0 and maxit >= 0");
+  EB_REQUIRE(b != x, EB_ERR_INVALID, "pcg: b and x must be different buffers");
   const int check = std::max(1, o.check_every);
+  prof_begin(o.profile != 0, s);
+  nlaunch = 0;
   auto t0 = std::chrono::steady_clock::now();
   PcgScalars init{};
   init.tol2 = rtol * rtol;
@@ -323,8 +384,8 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
   for (int restart = 0; restart < 4 && !converged; ++restart) {
     EB_CUDA(cudaMemcpyAsync(sc, &init, sizeof(init), cudaMemcpyHostToDevice, s));
     // x is masked to the CPs (its non-CP entries are ignored on input)
-    k_mask_copy<<<nblk, VT, 0, s>>>(G, eb->tiles, eb->num_tiles, eb->code, x, x);
-    k_resid<<<nblk, VT, 0, s>>>(G, eb->tiles, eb->num_tiles, eb->code, eb->diag, shift, inv_h2, b, x, r, part);
+    EB_DIM_LAUNCH(dim, k_mask_copy, nblk, tv, eb->code, x, x);
+    EB_DIM_LAUNCH(dim, k_resid, nblk, tv, eb->code, eb->diag, op, b, x, r, part);
     finalize(FIN_INIT, s);
     EB_CUDA(cudaMemcpyAsync(sc_host, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
     EB_CUDA(cudaStreamSynchronize(s));
@@ -333,7 +394,7 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
       break;
     }
     if (sc_host->bb == 0.0) {  // b = 0: x = 0 is the solution
-      EB_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * G.num_nodes, s));
+      EB_DIM_LAUNCH(dim, k_mask_copy, nblk, tv, eb->code, b, x);
       converged = true;
       rel = 0.0;
       break;
@@ -345,30 +406,38 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
     }
     if (total_iters >= maxit) break;
     precondition(kind, r, z, s);
-    finalize(FIN_RZ0, s);
-    k_xpby<<<nblk, VT, 0, s>>>(G, eb->tiles, eb->num_tiles, sc, z, p, 1);
+    const bool flex = kind == EB_PC_AMG && flexible();
+    finalize(flex ? FIN_RZ0F : FIN_RZ0, s);
+    EB_DIM_LAUNCH(dim, k_xpby, nblk, tv, sc, z, p, flex ? zold : nullptr, 1);
     int it = 0;
     bool stop = false;
     while (!stop) {
-      for (int j = 0; j < check && total_iters + it < maxit; ++j, ++it) {
-        k_apply_dot<<<nblk, VT, 0, s>>>(G, eb->tiles, eb->num_tiles, eb->code, eb->diag, shift, inv_h2, p, q, part);
-        finalize(FIN_ALPHA, s);
-        k_update_xr<<<nblk, VT, 0, s>>>(G, eb->tiles, eb->num_tiles, sc, x, r, p, q, part);
-        finalize(FIN_RR, s);
-        precondition(kind, r, z, s);
-        finalize(FIN_BETA, s);
-        k_xpby<<<nblk, VT, 0, s>>>(G, eb->tiles, eb->num_tiles, sc, z, p, 0);
+      const int nb = std::min(check, maxit - (total_iters + it));
+      bool graphed = false;
+      if (o.use_graph && nb == check) {
+        graph_prepare(kind, b, x, check, prof_on, s);
+        EB_CUDA(cudaGraphLaunch(gexec, s));
+        nlaunch += g_launches;
+        graphed = true;
+        it += nb;
+      } else {
+        for (int j = 0; j < nb; ++j, ++it) iteration(kind, b, x, s);
       }
       EB_CUDA(cudaGetLastError());
       EB_CUDA(cudaMemcpyAsync(sc_host, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
       EB_CUDA(cudaStreamSynchronize(s));
+      if (prof_on) {
+        if (graphed) prof_collect(0, g_pairs);
+        prof_collect(g_pairs, prof_n - g_pairs);
+        prof_n = g_pairs;
+      }
       if (sc_host->done || total_iters + it >= maxit) stop = true;
     }
     total_iters += sc_host->iters;
     flags |= sc_host->flags;
     if (flags & (PCG_FLAG_NONFINITE | PCG_FLAG_BREAKDOWN)) break;
     // true residual at exit
-    k_resid<<<nblk, VT, 0, s>>>(G, eb->tiles, eb->num_tiles, eb->code, eb->diag, shift, inv_h2, b, x, r, part);
+    EB_DIM_LAUNCH(dim, k_resid, nblk, tv, eb->code, eb->diag, op, b, x, r, part);
     finalize(FIN_INIT, s);
     EB_CUDA(cudaMemcpyAsync(sc_host, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
     EB_CUDA(cudaStreamSynchronize(s));
@@ -383,6 +452,8 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
     stats->true_rel_residual = rel;
     stats->solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     stats->converged = converged ? 1 : 0;
+    stats->launches = nlaunch;
+    prof_end(stats, s);
   }
   if (flags & PCG_FLAG_NONFINITE) {
     set_error("pcg: non-finite value in the right-hand side or a reduction");
@@ -407,12 +478,134 @@ int Solver::heat(double dt, double theta, const double* b1, const double* b0, do
   EB_REQUIRE(std::fabs(want - shift) <= 1e-12 * want, EB_ERR_INVALID,
              "heat: the hierarchy shift must equal 1/(theta dt)");
   const Geometry& G = eb->g;
-  k_heat_rhs<<<nblk, VT, 0, s>>>(G, eb->tiles, eb->num_tiles, eb->code, eb->diag, 1.0 / (G.h * G.h), dt, theta, u,
-                                 b1, b0 ? b0 : b1, tmp);
+  EB_DIM_LAUNCH(G.dim, k_heat_rhs, nblk, eb->tv(), eb->code, eb->diag, 1.0 / (G.h * G.h), dt, theta, u, b1,
+                b0 ? b0 : b1, tmp);
   EB_CUDA(cudaGetLastError());
-  pcg_opts o{EB_PC_AMG, 1, 0};
-  if (!H) o.precond = EB_PC_JACOBI;
+  pcg_opts o{H ? EB_PC_AMG : EB_PC_JACOBI, 1, 0, 0};
   return pcg(tmp, u, rtol, maxit, o, stats, s);
+}
+
+// One PCG iteration (device-side scalars; no host synchronisation).
+void Solver::iteration(int kind, const double* b, double* x, cudaStream_t s) {
+  (void)b;
+  const int dim = eb->g.dim;
+  const TileView tv = eb->tv();
+  const OpParams op = op_params(*this);
+  EB_DIM_LAUNCH(dim, k_apply_dot, nblk, tv, eb->code, eb->diag, op, p, q, part);
+  finalize(FIN_ALPHA, s);
+  EB_DIM_LAUNCH(dim, k_update_xr, nblk, tv, sc, x, r, p, q, part);
+  finalize(FIN_RR, s);
+  precondition(kind, r, z, s);
+  const bool flex = kind == EB_PC_AMG && flexible();
+  finalize(flex ? FIN_BETAF : FIN_BETA, s);
+  EB_DIM_LAUNCH(dim, k_xpby, nblk, tv, sc, z, p, flex ? zold : nullptr, 0);
+}
+
+// Captures `iters` iterations into a CUDA graph (once per argument set).  The
+// capture runs on a private stream forked from s, so s may be the legacy
+// default stream.
+void Solver::graph_prepare(int kind, const double* b, double* x, int iters, bool profile, cudaStream_t s) {
+  if (gexec && g_b == b && g_x == x && g_iters == iters && g_kind == kind && g_prof == (int)profile) return;
+  if (prof_on) {  // settle event pairs recorded so far before the capture reuses them
+    EB_CUDA(cudaStreamSynchronize(s));
+    prof_collect(g_pairs, prof_n - g_pairs);
+  }
+  graph_release();
+  if (!cap_stream) EB_CUDA(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+  cudaEvent_t fork;
+  EB_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  EB_CUDA(cudaEventRecord(fork, s));
+  EB_CUDA(cudaStreamWaitEvent(cap_stream, fork, 0));
+  const int64_t n0 = nlaunch;
+  prof_n = 0;
+  EB_CUDA(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
+  for (int j = 0; j < iters; ++j) iteration(kind, b, x, cap_stream);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cap_stream, &graph);
+  cudaEventDestroy(fork);
+  EB_CUDA(e);
+  e = cudaGraphInstantiate(&gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  EB_CUDA(e);
+  g_launches = nlaunch - n0;
+  nlaunch = n0;
+  g_pairs = prof_n;
+  g_b = b;
+  g_x = x;
+  g_iters = iters;
+  g_kind = kind;
+  g_prof = (int)profile;
+}
+
+void Solver::graph_release() {
+  if (gexec) cudaGraphExecDestroy(gexec);
+  gexec = nullptr;
+  g_pairs = 0;
+  g_b = nullptr;
+  g_x = nullptr;
+}
+
+static bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(s, &st) == cudaSuccess && st == cudaStreamCaptureStatusActive;
+}
+
+// ---------------------------------------------------------- kernel timing
+// Optional CUDA-event timing of the level-0 smoother launches (the kernel
+// that dominates an AMG-PCG iteration), on the stream they are launched on.
+// Inside a captured iteration the event records are graph nodes, so the
+// pairs time the kernels back to back, without host-enqueue gaps.
+void Solver::prof_begin(bool on, cudaStream_t) {
+  prof_on = on;
+  prof_n = g_pairs;
+  prof_acc_ms = 0.0;
+  prof_acc_n = 0;
+}
+
+void Solver::prof_collect(int first, int count) {
+  for (int i = first; i < first + count; ++i) {
+    float ms = 0.0f;
+    EB_CUDA(cudaEventElapsedTime(&ms, prof_ev[i].first, prof_ev[i].second));
+    prof_acc_ms += ms;
+    ++prof_acc_n;
+  }
+}
+
+void Solver::prof_mark(cudaStream_t s, bool start) {
+  if (!prof_on) return;
+  if (start) {
+    if (prof_n >= (int)prof_ev.size()) {
+      cudaEvent_t a, b;
+      EB_CUDA(cudaEventCreate(&a));
+      EB_CUDA(cudaEventCreate(&b));
+      prof_ev.push_back({a, b});
+    }
+    // external records stay observable (and timeable) when captured in a graph
+    EB_CUDA(cudaEventRecordWithFlags(prof_ev[prof_n].first, s, capturing(s) ? cudaEventRecordExternal : 0));
+  } else {
+    EB_CUDA(cudaEventRecordWithFlags(prof_ev[prof_n].second, s, capturing(s) ? cudaEventRecordExternal : 0));
+    ++prof_n;
+  }
+}
+
+void Solver::prof_end(pcg_stats* st, cudaStream_t s) {
+  st->prof_kernel_ms = 0.0;
+  st->prof_launches = 0;
+  if (!prof_on) return;
+  EB_CUDA(cudaStreamSynchronize(s));
+  prof_collect(g_pairs, prof_n - g_pairs);
+  prof_n = g_pairs;
+  st->prof_kernel_ms = prof_acc_ms;
+  st->prof_launches = prof_acc_n;
+  prof_on = false;
+}
+
+void Solver::prof_release() {
+  for (auto& e : prof_ev) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  prof_ev.clear();
 }
 
 }  // namespace ebk

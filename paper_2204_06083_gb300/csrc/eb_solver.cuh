@@ -1,11 +1,15 @@
 // Internal solver state: PCG scalars, work vectors and the AMG hierarchy.
 #pragma once
 
+#include <utility>
+#include <vector>
+
 #include "eb_internal.cuh"
 
 namespace ebk {
 
-enum { FIN_INIT = 0, FIN_RZ0 = 1, FIN_ALPHA = 2, FIN_RR = 3, FIN_BETA = 4 };
+// FIN_RZ0F / FIN_BETAF: flexible CG, partials are pairs (r.z, r.z_previous)
+enum { FIN_INIT = 0, FIN_RZ0 = 1, FIN_ALPHA = 2, FIN_RR = 3, FIN_BETA = 4, FIN_RZ0F = 5, FIN_BETAF = 6 };
 enum { PCG_FLAG_NONFINITE = 1, PCG_FLAG_BREAKDOWN = 2 };
 
 struct PcgScalars {
@@ -21,12 +25,28 @@ struct Solver {
   amg_opts opts{};
   Hierarchy* H = nullptr;
   double setup_ms = 0.0;
-  // full-grid work vectors
-  double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *tmp = nullptr, *dinv = nullptr;
+  // full-grid work vectors (touched on the active tiles only)
+  double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *tmp = nullptr;
+  double* zold = nullptr;  // previous z (flexible CG with a reduced-precision V-cycle)
+  bool flexible() const { return H != nullptr && opts.vcycle_prec == EB_F32; }
   double* part = nullptr;
   int nblk = 1;
   PcgScalars* sc = nullptr;
   PcgScalars* sc_host = nullptr;
+  int64_t nlaunch = 0;  // kernel launches issued (reported per solve)
+  // event timing of the level-0 smoother launches
+  bool prof_on = false;
+  int prof_n = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
+  double prof_acc_ms = 0.0;
+  int prof_acc_n = 0;
+  // captured PCG iteration (CUDA graph), keyed by its arguments
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const double* g_b = nullptr;
+  double* g_x = nullptr;
+  int g_iters = 0, g_kind = -1, g_prof = -1, g_pairs = 0;
+  int64_t g_launches = 0;
 
   void alloc_work(cudaStream_t s);
   void free_work();
@@ -35,6 +55,14 @@ struct Solver {
   int pcg(const double* b, double* x, double rtol, int maxit, const pcg_opts& o, pcg_stats* stats, cudaStream_t s);
   int heat(double dt, double theta, const double* b1, const double* b0, double* u, double rtol, int maxit,
            pcg_stats* stats, cudaStream_t s);
+  void prof_begin(bool on, cudaStream_t s);
+  void prof_mark(cudaStream_t s, bool start);
+  void prof_collect(int first, int count);
+  void prof_end(pcg_stats* st, cudaStream_t s);
+  void prof_release();
+  void iteration(int kind, const double* b, double* x, cudaStream_t s);
+  void graph_prepare(int kind, const double* b, double* x, int iters, bool profile, cudaStream_t s);
+  void graph_release();
 };
 
 // AMG (amg.cu)

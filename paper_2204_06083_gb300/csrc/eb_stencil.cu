@@ -2,12 +2,12 @@
 // device prefix scan, and the persistent leapfrog kernel (theta-scheme of
 // Sec. 3.5 at theta = 0).
 //
-// Layout: full grid, x fastest.  Work is distributed over the list of active
-// tiles (tiles holding at least one CP); a CTA of 256 threads covers one tile
-// per iteration of a grid-stride loop.  The node code byte carries the CP flag
-// and the mask of directions whose neighbour is a BP, so a CP never reads a
-// non-CP value: interior CPs (code 0x80) use D = 2 dim, cut CPs read D_k.
+// Layout: full grid, x fastest; work is distributed over the active tiles
+// (tiles.cuh).  The node code byte carries the CP flag and the mask of
+// directions whose neighbour is a BP, so a CP never reads a non-CP value:
+// interior CPs (code 0x80) use D = 2 dim, cut CPs read D_k (stencil.cuh).
 #include "eb_internal.cuh"
+#include "stencil.cuh"
 
 #include <algorithm>
 
@@ -108,95 +108,30 @@ void exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t
 }
 
 // ---------------------------------------------------------------- stencil
-template <class T>
-struct Acc {
-  using type = float;
-};
-template <>
-struct Acc<double> {
-  using type = double;
-};
-
-__device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
-__device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
-__device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(p[0]); }
-__device__ __forceinline__ void st(float* p, float v) { *p = v; }
-__device__ __forceinline__ void st(double* p, double v) { *p = v; }
-__device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
-
-// L2-coherent loads for data written by other CTAs during the same launch
-__device__ __forceinline__ double ld_plain(const double* p) { return __ldcg(p); }
-__device__ __forceinline__ float ld_plain(const float* p) { return __ldcg(p); }
-
-struct TileCursor {
-  int64_t node;
-  bool valid;
-};
-
-__device__ __forceinline__ TileCursor tile_node(const Geometry& G, int64_t t, int l) {
-  int64_t bx = t % G.ntx, r = t / G.ntx, by = r % G.nty, bz = r / G.nty;
-  int lx = l % G.tx, ly = (l / G.tx) % G.ty, lz = l / (G.tx * G.ty);
-  int64_t ix = bx * G.tx + lx, iy = by * G.ty + ly, iz = bz * G.tz + lz;
-  TileCursor c;
-  c.valid = ix < G.n0 && iy < G.n1 && iz < G.n2;
-  c.node = ix + (int64_t)G.n0 * (iy + (int64_t)G.n1 * iz);
-  return c;
-}
-
-// (sigma I + A) x at one CP, in the accumulation type of T
+// y = (sigma I + A) x on the active tiles, 0 at their non-CP nodes.
 template <class T, int DIM>
-__device__ __forceinline__ typename Acc<T>::type stencil_at(const T* x, int64_t node, uint8_t c, const double* diag,
-                                                            int64_t sy, int64_t sz, typename Acc<T>::type inv_h2,
-                                                            typename Acc<T>::type sigma) {
-  using A = typename Acc<T>::type;
-  const A xc = ld(x + node);
-  const uint8_t m = c & 0x3F;
-  A sum = 0;
-  if (!(m & 1)) sum += ld(x + node - 1);
-  if (!(m & 2)) sum += ld(x + node + 1);
-  if (!(m & 4)) sum += ld(x + node - sy);
-  if (!(m & 8)) sum += ld(x + node + sy);
-  if (DIM == 3) {
-    if (!(m & 16)) sum += ld(x + node - sz);
-    if (!(m & 32)) sum += ld(x + node + sz);
+__global__ void __launch_bounds__(TILE_NODES) k_apply(TileView tv, const uint8_t* __restrict__ code,
+                                                      const double* __restrict__ diag, const T* __restrict__ x,
+                                                      T* __restrict__ y, double sigma, double inv_h2) {
+  using A = typename AccOf<T>::type;
+  EB_PAIR_LOOP(DIM, tv, node) {
+    uint32_t c0, c1;
+    ld_codes(code, node, c0, c1);
+    Two<A> xc, core;
+    stencil_pair<DIM, LdRO>(x, node, tv.nn, c0, c1, diag, tv.sy, tv.sz, xc, core);
+    const A v0 = (c0 & CODE_CP) ? core.x * (A)inv_h2 + (A)sigma * xc.x : (A)0;
+    const A v1 = (c1 & CODE_CP) ? core.y * (A)inv_h2 + (A)sigma * xc.y : (A)0;
+    st2(y + node, v0, v1);
   }
-  const A D = m ? (A)__ldg(diag + node) : (A)(2 * DIM);
-  return (D * xc - sum) * inv_h2 + sigma * xc;
-}
-
-template <class T, int DIM>
-__global__ void __launch_bounds__(256) k_apply(Geometry G, const int32_t* __restrict__ tiles, int64_t ntiles,
-                                               const uint8_t* __restrict__ code, const double* __restrict__ diag,
-                                               const T* __restrict__ x, T* __restrict__ y, double sigma, double inv_h2) {
-  using A = typename Acc<T>::type;
-  const int tsz = G.tx * G.ty * G.tz;
-  const int64_t sy = G.n0, sz = (int64_t)G.n0 * G.n1;
-  for (int64_t tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
-    const int64_t t = tiles[tt];
-    for (int l = threadIdx.x; l < tsz; l += blockDim.x) {
-      TileCursor cur = tile_node(G, t, l);
-      if (!cur.valid) continue;
-      const uint8_t c = code[cur.node];
-      A v = 0;
-      if (c & CODE_CP) v = stencil_at<T, DIM>(x, cur.node, c, diag, sy, sz, (A)inv_h2, (A)sigma);
-      st(y + cur.node, v);
-    }
-  }
-}
-
-inline unsigned tile_blocks(const EBHandle& eb, int per_sm = 8) {
-  int64_t b = std::min<int64_t>(eb.num_tiles, (int64_t)num_sms() * per_sm);
-  return (unsigned)std::max<int64_t>(b, 1);
 }
 
 template <class T>
 void launch_apply(const EBHandle& eb, const T* x, T* y, double sigma, cudaStream_t s) {
-  const Geometry& G = eb.g;
-  double inv_h2 = 1.0 / (G.h * G.h);
-  if (G.dim == 2)
-    k_apply<T, 2><<<tile_blocks(eb), 256, 0, s>>>(G, eb.tiles, eb.num_tiles, eb.code, eb.diag, x, y, sigma, inv_h2);
+  const double inv_h2 = 1.0 / (eb.g.h * eb.g.h);
+  if (eb.g.dim == 2)
+    k_apply<T, 2><<<tile_grid(eb), TILE_NODES, 0, s>>>(eb.tv(), eb.code, eb.diag, x, y, sigma, inv_h2);
   else
-    k_apply<T, 3><<<tile_blocks(eb), 256, 0, s>>>(G, eb.tiles, eb.num_tiles, eb.code, eb.diag, x, y, sigma, inv_h2);
+    k_apply<T, 3><<<tile_grid(eb), TILE_NODES, 0, s>>>(eb.tv(), eb.code, eb.diag, x, y, sigma, inv_h2);
   EB_CUDA(cudaGetLastError());
 }
 
@@ -205,9 +140,9 @@ template void launch_apply<float>(const EBHandle&, const float*, float*, double,
 template void launch_apply<__nv_bfloat16>(const EBHandle&, const __nv_bfloat16*, __nv_bfloat16*, double, cudaStream_t);
 
 // -------------------------------------------------------------- leapfrog
-// Grid-wide barrier for a cooperative launch: sense-reversing counter with a
-// bounded spin.  On timeout the block sets *err and every later barrier of
-// the launch returns at once, so the kernel always terminates.
+// Grid-wide barrier for a cooperative launch: counter + generation with a
+// bounded spin.  On timeout the CTA sets err, and every later barrier of the
+// launch returns at once, so the kernel always terminates.
 struct GridBarrier {
   unsigned int count;
   unsigned int gen;
@@ -215,7 +150,7 @@ struct GridBarrier {
   int pad;
 };
 
-constexpr long long BARRIER_SPIN_LIMIT = 20000000;  // ~ seconds of polling
+constexpr long long BARRIER_SPIN_LIMIT = 20000000;  // ~ a second of polling
 
 __device__ bool grid_sync(GridBarrier* gb) {
   __syncthreads();
@@ -227,9 +162,9 @@ __device__ bool grid_sync(GridBarrier* gb) {
       failed = 1;
     } else {
       volatile unsigned int* pgen = &gb->gen;
-      unsigned int g = *pgen;
+      const unsigned int g = *pgen;
       __threadfence();
-      unsigned int arrived = atomicAdd(&gb->count, 1u) + 1u;
+      const unsigned int arrived = atomicAdd(&gb->count, 1u) + 1u;
       if (arrived == gridDim.x) {
         gb->count = 0;
         __threadfence();
@@ -252,91 +187,64 @@ __device__ bool grid_sync(GridBarrier* gb) {
   return failed == 0;
 }
 
+// nsteps of u_new = 2 u - u_old - dt^2 A u, u_new overwriting u_old in place:
+// step s reads cur = (s even ? ub : ua) and overwrites prev = the other field.
+// Fields written during the launch are read through L2 (ld.global.cg).
 template <class T, int DIM>
-__global__ void __launch_bounds__(256) k_leapfrog(Geometry G, const int32_t* __restrict__ tiles, int64_t ntiles,
-                                                  const uint8_t* __restrict__ code, const double* __restrict__ diag,
-                                                  T* ua, T* ub, int nsteps, double dt2, double inv_h2, GridBarrier* gb) {
-  using A = typename Acc<T>::type;
-  const int tsz = G.tx * G.ty * G.tz;
-  const int64_t sy = G.n0, sz = (int64_t)G.n0 * G.n1;
-  // step s reads cur = (s even ? ub : ua) and overwrites prev = the other
+__global__ void __launch_bounds__(TILE_NODES) k_leapfrog(TileView tv, const uint8_t* __restrict__ code,
+                                                         const double* __restrict__ diag, T* ua, T* ub, int nsteps,
+                                                         double dt2, double inv_h2, GridBarrier* gb) {
+  using A = typename AccOf<T>::type;
+  const A c2 = (A)(dt2 * inv_h2);
   for (int s = 0; s < nsteps; ++s) {
     T* prev = (s & 1) ? ub : ua;
     const T* cur = (s & 1) ? ua : ub;
-    for (int64_t tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
-      const int64_t t = tiles[tt];
-      for (int l = threadIdx.x; l < tsz; l += blockDim.x) {
-        TileCursor c = tile_node(G, t, l);
-        if (!c.valid) continue;
-        const uint8_t cc = code[c.node];
-        if (!(cc & CODE_CP)) continue;
-        // plain loads: cur was written by other CTAs in the previous step
-        const A xc = (A)ld_plain(cur + c.node);
-        const uint8_t m = cc & 0x3F;
-        A sum = 0;
-        if (!(m & 1)) sum += (A)ld_plain(cur + c.node - 1);
-        if (!(m & 2)) sum += (A)ld_plain(cur + c.node + 1);
-        if (!(m & 4)) sum += (A)ld_plain(cur + c.node - sy);
-        if (!(m & 8)) sum += (A)ld_plain(cur + c.node + sy);
-        if (DIM == 3) {
-          if (!(m & 16)) sum += (A)ld_plain(cur + c.node - sz);
-          if (!(m & 32)) sum += (A)ld_plain(cur + c.node + sz);
-        }
-        const A D = m ? (A)__ldg(diag + c.node) : (A)(2 * DIM);
-        const A Au = (D * xc - sum) * (A)inv_h2;
-        const A un = (A)2 * xc - (A)ld_plain(prev + c.node) - (A)dt2 * Au;
-        st(prev + c.node, un);
-      }
+    EB_PAIR_LOOP(DIM, tv, node) {
+      uint32_t c0, c1;
+      ld_codes(code, node, c0, c1);
+      Two<A> xc, core;
+      stencil_pair<DIM, LdCG>(cur, node, tv.nn, c0, c1, diag, tv.sy, tv.sz, xc, core);
+      const Two<A> po = LdCG::ld2(prev + node);
+      const A n0 = (c0 & CODE_CP) ? (A)2 * xc.x - po.x - c2 * core.x : (A)0;
+      const A n1 = (c1 & CODE_CP) ? (A)2 * xc.y - po.y - c2 * core.y : (A)0;
+      st2(prev + node, n0, n1);
     }
     if (!grid_sync(gb)) return;
   }
-  // odd step count: the newest field is in ua; swap so that (ua, ub) = (prev, cur)
-  if (nsteps & 1) {
-    for (int64_t tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
-      const int64_t t = tiles[tt];
-      for (int l = threadIdx.x; l < tsz; l += blockDim.x) {
-        TileCursor c = tile_node(G, t, l);
-        if (!c.valid) continue;
-        T a = __ldcg(ua + c.node);
-        ua[c.node] = __ldcg(ub + c.node);
-        ub[c.node] = a;
-      }
+  if (nsteps & 1) {  // newest field sits in ua: swap so that (ua, ub) = (u^{N-1}, u^N)
+    EB_PAIR_LOOP(DIM, tv, node) {
+      const Two<A> a = LdCG::ld2(ua + node);
+      const Two<A> b = LdCG::ld2(ub + node);
+      st2(ua + node, b.x, b.y);
+      st2(ub + node, a.x, a.y);
     }
   }
 }
 
-}  // namespace ebk
-
-namespace ebk {
-
 template <class T>
 int launch_leapfrog(const EBHandle& eb, T* ua, T* ub, int nsteps, double dt, cudaStream_t s) {
-  const Geometry& G = eb.g;
   if (nsteps <= 0) return EB_OK;
+  const Geometry& G = eb.g;
   GridBarrier* gb = dalloc<GridBarrier>(1, s);
-  int dev = 0;
-  EB_CUDA(cudaGetDevice(&dev));
-  int per_sm = 0;
   void* fn = G.dim == 2 ? (void*)k_leapfrog<T, 2> : (void*)k_leapfrog<T, 3>;
-  EB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0));
+  int per_sm = 0;
+  EB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TILE_NODES, 0));
   EB_REQUIRE(per_sm > 0, EB_ERR_INVALID, "leapfrog kernel cannot be resident");
   int64_t nb = std::min<int64_t>(eb.num_tiles, (int64_t)per_sm * num_sms());
   unsigned blocks = (unsigned)std::max<int64_t>(nb, 1);
   double dt2 = dt * dt, inv_h2 = 1.0 / (G.h * G.h);
-  int64_t ntiles = eb.num_tiles;
-  const int32_t* tiles = eb.tiles;
+  TileView tv = eb.tv();
   const uint8_t* code = eb.code;
   const double* diag = eb.diag;
-  Geometry g = G;
-  void* args[] = {(void*)&g, (void*)&tiles, (void*)&ntiles, (void*)&code, (void*)&diag, (void*)&ua, (void*)&ub,
-                  (void*)&nsteps, (void*)&dt2, (void*)&inv_h2, (void*)&gb};
-  EB_CUDA(cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(256), args, 0, s));
+  void* args[] = {(void*)&tv, (void*)&code, (void*)&diag, (void*)&ua, (void*)&ub, (void*)&nsteps,
+                  (void*)&dt2, (void*)&inv_h2, (void*)&gb};
+  EB_CUDA(cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(TILE_NODES), args, 0, s));
   GridBarrier hb{};
   EB_CUDA(cudaMemcpyAsync(&hb, gb, sizeof(hb), cudaMemcpyDeviceToHost, s));
   EB_CUDA(cudaStreamSynchronize(s));
   dfree(gb, s);
   if (hb.err) {
-    set_error("leapfrog: grid barrier timed out");
+    set_error("wave_step: grid barrier timed out");
     return EB_ERR_TIMEOUT;
   }
   return EB_OK;

@@ -1,0 +1,72 @@
+// Active-tile traversal shared by every grid kernel.
+//
+// The grid is cut into tiles of 256 nodes (2D: 32 x 8, 3D: 16 x 4 x 4, x
+// fastest); only tiles that hold a CP are listed.  For each listed tile the
+// build stores the node index of its corner and its extents (ragged at the
+// high ends of the grid), so a thread finds its nodes with shifts and one
+// multiply-add -- no integer division in the hot loops.
+//
+// Hot kernels work on PAIRS of x-adjacent nodes (n0 even, tile origins even,
+// so a pair is 16-byte aligned in FP64): 128 threads cover a tile and a CTA of
+// 256 threads covers two tiles per iteration of a grid-stride loop.
+#pragma once
+
+#include <stdint.h>
+
+namespace ebk {
+
+constexpr int TILE_NODES = 256;
+constexpr int PAIR_THREADS = 128;  // threads per tile in the pair layout
+
+template <int DIM>
+struct TileShape;
+template <>
+struct TileShape<2> {
+  static constexpr int X = 32, Y = 8, Z = 1;
+};
+template <>
+struct TileShape<3> {
+  static constexpr int X = 16, Y = 4, Z = 4;
+};
+
+struct TileView {
+  const int32_t* base;  // node index of the tile's (0,0,0) corner
+  const int32_t* lim;   // extents: x | y << 8 | z << 16
+  int64_t ntiles;
+  int32_t sy, sz;       // node strides of y and z
+  int32_t nn;           // number of grid nodes (even)
+};
+
+// Node of this thread in listed tile tt (one node per thread, 256 threads).
+template <int DIM>
+__device__ __forceinline__ bool tile_node(const TileView& tv, int64_t tt, int32_t& node) {
+  using S = TileShape<DIM>;
+  const int l = threadIdx.x;
+  const int lx = l % S::X, ly = (l / S::X) % S::Y, lz = l / (S::X * S::Y);
+  const int32_t lim = __ldg(tv.lim + tt);
+  node = __ldg(tv.base + tt) + lx + ly * tv.sy + lz * tv.sz;
+  return lx < (lim & 0xFF) && ly < ((lim >> 8) & 0xFF) && lz < ((lim >> 16) & 0xFF);
+}
+
+// First node of this thread's pair in listed tile tt (pair layout).
+template <int DIM>
+__device__ __forceinline__ bool tile_pair(const TileView& tv, int64_t tt, int t, int32_t& node) {
+  using S = TileShape<DIM>;
+  constexpr int PX = S::X / 2;
+  const int px = t % PX, ly = (t / PX) % S::Y, lz = t / (PX * S::Y);
+  const int32_t lim = __ldg(tv.lim + tt);
+  node = __ldg(tv.base + tt) + 2 * px + ly * tv.sy + lz * tv.sz;
+  return 2 * px < (lim & 0xFF) && ly < ((lim >> 8) & 0xFF) && lz < ((lim >> 16) & 0xFF);
+}
+
+}  // namespace ebk
+
+// for (each listed tile of this CTA) if (this thread's node is in the grid) body
+#define EB_TILE_LOOP(DIM, tv, node)                                    \
+  for (int64_t tt_ = blockIdx.x; tt_ < (tv).ntiles; tt_ += gridDim.x) \
+    if (int32_t node = 0; ::ebk::tile_node<DIM>((tv), tt_, node))
+
+// pair layout: node and node + 1 belong to this thread
+#define EB_PAIR_LOOP(DIM, tv, node)                                                                      \
+  for (int64_t tt_ = 2 * (int64_t)blockIdx.x + (threadIdx.x >> 7); tt_ < (tv).ntiles; tt_ += 2 * (int64_t)gridDim.x) \
+    if (int32_t node = 0; ::ebk::tile_pair<DIM>((tv), tt_, threadIdx.x & 127, node))
