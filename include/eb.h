@@ -218,6 +218,26 @@ int heat_step(const amg_handle* amg, double dt, double theta, const double* b1_d
 int wave_step(const eb_handle* eb, int prec, double dt, void* u_prev_dev, void* u_cur_dev, int nsteps,
               cudaStream_t stream);
 
+/* The leapfrog step of wave_step for callers that must not allocate device
+ * memory during the call.  The paper has no counterpart: this is a service of
+ * this library.  wave_step allocates a small barrier record per call; code
+ * running while a surrounding CUDA graph is being captured, loops that must not
+ * touch the allocator after start-up, and programs whose device memory is held
+ * by another framework's pool cannot allow that.  This entry point keeps the
+ * barrier in a fixed device array of the library instead (one flag per
+ * cooperative CTA, at most 2048 CTAs, about 8 KB, held by every GPU that loads
+ * the library until the process exits) and calls no cudaMalloc, cudaFree or
+ * allocating library routine.  Same arguments, arithmetic and results as
+ * wave_step; the handle and the fields are created by the caller beforehand.
+ * The first call on each device looks up the array's device address (no
+ * allocation); make that first call before any stream capture.  All calls
+ * share the array and each clears the part it uses before its launch, so two
+ * calls whose kernels overlap on the GPU race and must not be issued.  A launch
+ * that would need more than 2048 CTAs is rejected with EB_ERR_INVALID.
+ * Synchronous, like wave_step. */
+int wave_step_noalloc(const eb_handle* eb, int prec, double dt, void* u_prev_dev, void* u_cur_dev, int nsteps,
+                      cudaStream_t stream);
+
 const char* eb_last_error(void);
 
 #ifdef __cplusplus

@@ -87,6 +87,7 @@ _SIGS = {
     "pcg_solve": (C.c_int, [_P, _P, _P, C.c_double, C.c_int, C.POINTER(pcg_opts), C.POINTER(pcg_stats), _P]),
     "heat_step": (C.c_int, [_P, C.c_double, C.c_double, _P, _P, _P, C.c_double, C.c_int, C.POINTER(pcg_stats), _P]),
     "wave_step": (C.c_int, [_P, C.c_int, C.c_double, _P, _P, C.c_int, _P]),
+    "wave_step_noalloc": (C.c_int, [_P, C.c_int, C.c_double, _P, _P, C.c_int, _P]),
     "eb_last_error": (C.c_char_p, []),
 }
 

@@ -17,6 +17,7 @@ namespace ebk {
 static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
 const char* last_error() { return g_last_error.c_str(); }
+const EBHandle& handle_of(const eb_handle* eb) { return eb->h; }
 }  // namespace ebk
 
 using namespace ebk;
