@@ -407,21 +407,69 @@ __global__ void k_tr_scatter(DCsr A, const int32_t* rp, int32_t* fill, int32_t* 
   }
 }
 
+// Sorts every row of C by column: one warp per row, bitonic sort in shared
+// memory for rows of up to SORT_CAP entries (column indices are distinct), a
+// serial insertion sort by lane 0 beyond.
+constexpr int SORT_WARPS = 2;  // 2 x 2048 x 12 B = 48 KB of static shared memory
+constexpr int SORT_CAP = 2048;
+
 __global__ void k_row_sort(DCsr C) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= C.n) return;
-  const int32_t b = C.rp[i], e = C.rp[i + 1];
-  for (int32_t p = b + 1; p < e; ++p) {
-    int32_t kc = C.ci[p];
-    double kv = C.v[p];
-    int32_t q = p - 1;
-    while (q >= b && C.ci[q] > kc) {
-      C.ci[q + 1] = C.ci[q];
-      C.v[q + 1] = C.v[q];
-      --q;
+  __shared__ int32_t skey[SORT_WARPS][SORT_CAP];
+  __shared__ double sval[SORT_WARPS][SORT_CAP];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int32_t* key = skey[warp];
+  double* val = sval[warp];
+  for (int64_t i = (int64_t)blockIdx.x * SORT_WARPS + warp; i < C.n; i += (int64_t)gridDim.x * SORT_WARPS) {
+    const int32_t b = C.rp[i], e = C.rp[i + 1], m = e - b;
+    if (m <= 1) continue;
+    if (m > SORT_CAP) {
+      if (lane == 0) {
+        for (int32_t p = b + 1; p < e; ++p) {
+          const int32_t kc = C.ci[p];
+          const double kv = C.v[p];
+          int32_t q = p - 1;
+          while (q >= b && C.ci[q] > kc) {
+            C.ci[q + 1] = C.ci[q];
+            C.v[q + 1] = C.v[q];
+            --q;
+          }
+          C.ci[q + 1] = kc;
+          C.v[q + 1] = kv;
+        }
+      }
+      __syncwarp();
+      continue;
     }
-    C.ci[q + 1] = kc;
-    C.v[q + 1] = kv;
+    int M = 1;
+    while (M < m) M <<= 1;
+    for (int t = lane; t < M; t += 32) {
+      key[t] = t < m ? C.ci[b + t] : INT32_MAX;
+      val[t] = t < m ? C.v[b + t] : 0.0;
+    }
+    __syncwarp();
+    for (int k = 2; k <= M; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int t = lane; t < M; t += 32) {
+          const int u = t ^ j;
+          if (u > t) {
+            const bool up = (t & k) == 0;
+            const int32_t kt = key[t], ku = key[u];
+            if ((kt > ku) == up) {
+              key[t] = ku;
+              key[u] = kt;
+              const double vt = val[t];
+              val[t] = val[u];
+              val[u] = vt;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    for (int t = lane; t < m; t += 32) {
+      C.ci[b + t] = key[t];
+      C.v[b + t] = val[t];
+    }
+    __syncwarp();
   }
 }
 
@@ -438,7 +486,7 @@ static DCsr transpose(const DCsr& A, cudaStream_t s) {
   exclusive_scan_i32(cnt, T.rp, A.m, s);
   EB_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (A.m + 1), s));
   k_tr_scatter<<<blocks_for(A.n, 256), 256, 0, s>>>(A, T.rp, cnt, T.ci, T.v);
-  k_row_sort<<<blocks_for(T.n, 128), 128, 0, s>>>(T);
+  k_row_sort<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((T.n + SORT_WARPS - 1) / SORT_WARPS, (int64_t)num_sms() * 16)), 32 * SORT_WARPS, 0, s>>>(T);
   EB_CUDA(cudaGetLastError());
   dfree(cnt, s);
   return T;

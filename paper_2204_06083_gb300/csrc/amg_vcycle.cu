@@ -25,14 +25,16 @@ struct CsrV {
   const V* v;
 };
 
+// operator constants in the arithmetic type of the kernel
+template <class A>
 struct GOp {
-  double inv_h2, sigma, dinv_int;
+  A inv_h2, sigma, dinv_int;
 };
 
-template <class A>
-__device__ __forceinline__ A inv_diag_t(uint32_t c, const double* __restrict__ diag, int32_t node, const GOp& o) {
-  if (!(c & 0x3F)) return (A)o.dinv_int;
-  return (A)1 / ((A)o.sigma + (A)__ldg(diag + node) * (A)o.inv_h2);
+template <class A, class DT>
+__device__ __forceinline__ A inv_diag_t(uint32_t c, const DT* __restrict__ diag, int32_t node, const GOp<A>& o) {
+  if (!(c & 0x3F)) return o.dinv_int;
+  return (A)1 / (o.sigma + (A)__ldg(diag + node) * o.inv_h2);
 }
 
 __device__ __forceinline__ void st2o(double* p, double a, double b) { st2(p, a, b); }
@@ -42,9 +44,11 @@ __device__ __forceinline__ void st2o(float* p, float a, float b) { st2(p, a, b);
 // b_out = (V) r; x = d = D^-1 b / theta
 template <int DIM, class V>
 __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_first(TileView tv, const uint8_t* __restrict__ code,
-                                                             const double* __restrict__ diag, GOp o,
+                                                             const typename DiagOf<V>::type* __restrict__ diag,
+                                                             GOp<typename AccOf<V>::type> o,
                                                              const double* __restrict__ r, V* __restrict__ b_out,
-                                                             V* __restrict__ x, V* __restrict__ d, double theta) {
+                                                             V* __restrict__ x, V* __restrict__ d,
+                                                             typename AccOf<V>::type theta) {
   using A = typename AccOf<V>::type;
   EB_PAIR_LOOP(DIM, tv, node) {
     uint32_t c0, c1;
@@ -52,8 +56,8 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_first(TileView tv, const 
     const Two<double> rv = LdRO::ld2(r + node);
     const A b0 = (c0 & CODE_CP) ? (A)rv.x : (A)0, b1 = (c1 & CODE_CP) ? (A)rv.y : (A)0;
     if (b_out) st2o(b_out + node, b0, b1);
-    const A v0 = (c0 & CODE_CP) ? inv_diag_t<A>(c0, diag, node, o) * b0 / (A)theta : (A)0;
-    const A v1 = (c1 & CODE_CP) ? inv_diag_t<A>(c1, diag, node + 1, o) * b1 / (A)theta : (A)0;
+    const A v0 = (c0 & CODE_CP) ? inv_diag_t<A>(c0, diag, node, o) * b0 / theta : (A)0;
+    const A v1 = (c1 & CODE_CP) ? inv_diag_t<A>(c1, diag, node + 1, o) * b1 / theta : (A)0;
     st2o(x + node, v0, v1);
     st2o(d + node, v0, v1);
   }
@@ -62,10 +66,11 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_first(TileView tv, const 
 // res = D^-1 (b - A x); d = c1 d + c2 res; xo = x + d   (xo may be FP64)
 template <int DIM, class V, class O>
 __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_step(TileView tv, const uint8_t* __restrict__ code,
-                                                            const double* __restrict__ diag, GOp o,
+                                                            const typename DiagOf<V>::type* __restrict__ diag,
+                                                            GOp<typename AccOf<V>::type> o,
                                                             const V* __restrict__ b, const V* __restrict__ x,
-                                                            O* __restrict__ xo, V* __restrict__ d, double c1,
-                                                            double c2) {
+                                                            O* __restrict__ xo, V* __restrict__ d,
+                                                            typename AccOf<V>::type c1, typename AccOf<V>::type c2) {
   using A = typename AccOf<V>::type;
   EB_PAIR_LOOP(DIM, tv, node) {
     uint32_t k0, k1;
@@ -74,15 +79,14 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_step(TileView tv, const u
     stencil_pair<DIM, LdRO>(x, node, tv.nn, k0, k1, diag, tv.sy, tv.sz, xc, core);
     const Two<A> bv = LdRO::ld2(b + node);
     Two<A> dv{0, 0};
-    if (c1 != 0.0) {
+    if (c1 != (A)0) {
       const Two<A> t = LdRO::ld2(d + node);
       dv = t;
     }
-    const A ih = (A)o.inv_h2, sg = (A)o.sigma;
-    const A res0 = inv_diag_t<A>(k0, diag, node, o) * (bv.x - (core.x * ih + sg * xc.x));
-    const A res1 = inv_diag_t<A>(k1, diag, node + 1, o) * (bv.y - (core.y * ih + sg * xc.y));
-    const A d0 = (k0 & CODE_CP) ? (A)c1 * dv.x + (A)c2 * res0 : (A)0;
-    const A d1 = (k1 & CODE_CP) ? (A)c1 * dv.y + (A)c2 * res1 : (A)0;
+    const A res0 = inv_diag_t<A>(k0, diag, node, o) * (bv.x - (core.x * o.inv_h2 + o.sigma * xc.x));
+    const A res1 = inv_diag_t<A>(k1, diag, node + 1, o) * (bv.y - (core.y * o.inv_h2 + o.sigma * xc.y));
+    const A d0 = (k0 & CODE_CP) ? c1 * dv.x + c2 * res0 : (A)0;
+    const A d1 = (k1 & CODE_CP) ? c1 * dv.y + c2 * res1 : (A)0;
     st2o(d + node, d0, d1);
     st2(xo + node, (O)((k0 & CODE_CP) ? xc.x + d0 : (A)0), (O)((k1 & CODE_CP) ? xc.y + d1 : (A)0));
   }
@@ -90,7 +94,8 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_step(TileView tv, const u
 
 template <int DIM, class V>
 __global__ void __launch_bounds__(TILE_NODES) k_g_resid(TileView tv, const uint8_t* __restrict__ code,
-                                                        const double* __restrict__ diag, GOp o,
+                                                        const typename DiagOf<V>::type* __restrict__ diag,
+                                                        GOp<typename AccOf<V>::type> o,
                                                         const V* __restrict__ b, const V* __restrict__ x,
                                                         V* __restrict__ r) {
   using A = typename AccOf<V>::type;
@@ -100,91 +105,139 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_resid(TileView tv, const uint8
     Two<A> xc, core;
     stencil_pair<DIM, LdRO>(x, node, tv.nn, c0, c1, diag, tv.sy, tv.sz, xc, core);
     const Two<A> bv = LdRO::ld2(b + node);
-    const A ih = (A)o.inv_h2, sg = (A)o.sigma;
-    st2o(r + node, (c0 & CODE_CP) ? bv.x - (core.x * ih + sg * xc.x) : (A)0,
-         (c1 & CODE_CP) ? bv.y - (core.y * ih + sg * xc.y) : (A)0);
+    st2o(r + node, (c0 & CODE_CP) ? bv.x - (core.x * o.inv_h2 + o.sigma * xc.x) : (A)0,
+         (c1 & CODE_CP) ? bv.y - (core.y * o.inv_h2 + o.sigma * xc.y) : (A)0);
   }
 }
 
+// CSR kernels: a group of G lanes (G = 1..32, chosen per matrix from its mean
+// row length) owns one row; lane g sums entries g, g+G, ... and the group
+// reduces by xor-shuffles in a fixed order (deterministic).
+template <int G, class A>
+__device__ __forceinline__ A group_reduce(A s) {
+  for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, G);
+  return s;
+}
+
 // out = R r with R's columns given as grid nodes
-template <class V>
+template <int G, class V>
 __global__ void k_restrict0(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ node_col,
                             const V* __restrict__ v, const V* __restrict__ r, V* __restrict__ out) {
   using A = typename AccOf<V>::type;
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = t / G;
+  const int g = (int)(t % G);
   A s = 0;
-  for (int32_t e = rp[i]; e < rp[i + 1]; ++e) s += (A)v[e] * (A)r[node_col[e]];
-  out[i] = (V)s;
+  if (i < n)
+    for (int32_t e = rp[i] + g; e < rp[i + 1]; e += G) s += (A)v[e] * (A)r[node_col[e]];
+  s = group_reduce<G>(s);
+  if (i < n && g == 0) out[i] = (V)s;
 }
 
 // x[node(i)] += sum_c P_ic e_c over the CPs i
-template <class V>
+template <int G, class V>
 __global__ void k_prolong0(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                            const V* __restrict__ v, const int32_t* __restrict__ cp_node, const V* __restrict__ e,
                            V* __restrict__ x) {
   using A = typename AccOf<V>::type;
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = t / G;
+  const int g = (int)(t % G);
   A s = 0;
-  for (int32_t f = rp[i]; f < rp[i + 1]; ++f) s += (A)v[f] * (A)e[ci[f]];
-  const int32_t node = cp_node[i];
-  x[node] = (V)((A)x[node] + s);
+  if (i < n)
+    for (int32_t f = rp[i] + g; f < rp[i + 1]; f += G) s += (A)v[f] * (A)e[ci[f]];
+  s = group_reduce<G>(s);
+  if (i < n && g == 0) {
+    const int32_t node = cp_node[i];
+    x[node] = (V)((A)x[node] + s);
+  }
 }
 
 // compact levels -----------------------------------------------------------
 template <class V>
-__global__ void k_c_cheb_first(int64_t n, const V* dinv, const V* b, V* x, V* d, double theta) {
+__global__ void k_c_cheb_first(int64_t n, const V* dinv, const V* b, V* x, V* d, typename AccOf<V>::type theta) {
   using A = typename AccOf<V>::type;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const V v = (V)((A)dinv[i] * (A)b[i] / (A)theta);
+  const V v = (V)((A)dinv[i] * (A)b[i] / theta);
   x[i] = v;
   d[i] = v;
 }
 
-template <class V>
-__global__ void k_c_cheb_step(CsrV<V> M, const V* dinv, const V* b, const V* x, V* xo, V* d, double c1, double c2) {
+template <int G, class V>
+__device__ __forceinline__ typename AccOf<V>::type csr_row(const CsrV<V>& M, const V* x, int64_t i, int g) {
   using A = typename AccOf<V>::type;
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M.n) return;
-  A ax = 0;
-  for (int32_t e = M.rp[i]; e < M.rp[i + 1]; ++e) ax += (A)M.v[e] * (A)x[M.ci[e]];
+  A s = 0;
+  if (i < M.n)
+    for (int32_t e = M.rp[i] + g; e < M.rp[i + 1]; e += G) s += (A)M.v[e] * (A)x[M.ci[e]];
+  return group_reduce<G>(s);
+}
+
+template <int G, class V>
+__global__ void k_c_cheb_step(CsrV<V> M, const V* dinv, const V* b, const V* x, V* xo, V* d,
+                              typename AccOf<V>::type c1, typename AccOf<V>::type c2) {
+  using A = typename AccOf<V>::type;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = t / G;
+  const int g = (int)(t % G);
+  const A ax = csr_row<G>(M, x, i, g);
+  if (i >= M.n || g != 0) return;
   const A res = (A)dinv[i] * ((A)b[i] - ax);
-  const A dv = (c1 == 0.0 ? (A)0 : (A)c1 * (A)d[i]) + (A)c2 * res;
+  const A dv = (c1 == (A)0 ? (A)0 : c1 * (A)d[i]) + c2 * res;
   d[i] = (V)dv;
   xo[i] = (V)((A)x[i] + dv);
 }
 
-template <class V>
+template <int G, class V>
 __global__ void k_c_resid(CsrV<V> M, const V* b, const V* x, V* r) {
   using A = typename AccOf<V>::type;
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M.n) return;
-  A ax = 0;
-  for (int32_t e = M.rp[i]; e < M.rp[i + 1]; ++e) ax += (A)M.v[e] * (A)x[M.ci[e]];
-  r[i] = (V)((A)b[i] - ax);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = t / G;
+  const int g = (int)(t % G);
+  const A ax = csr_row<G>(M, x, i, g);
+  if (i < M.n && g == 0) r[i] = (V)((A)b[i] - ax);
 }
 
-template <class V>
+template <int G, class V>
 __global__ void k_c_spmv(CsrV<V> M, const V* x, V* y) {
-  using A = typename AccOf<V>::type;
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M.n) return;
-  A s = 0;
-  for (int32_t e = M.rp[i]; e < M.rp[i + 1]; ++e) s += (A)M.v[e] * (A)x[M.ci[e]];
-  y[i] = (V)s;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = t / G;
+  const int g = (int)(t % G);
+  const auto s = csr_row<G>(M, x, i, g);
+  if (i < M.n && g == 0) y[i] = (V)s;
 }
 
-template <class V>
+template <int G, class V>
 __global__ void k_c_prolong_add(CsrV<V> P, const V* e, V* x) {
   using A = typename AccOf<V>::type;
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= P.n) return;
-  A s = 0;
-  for (int32_t f = P.rp[i]; f < P.rp[i + 1]; ++f) s += (A)P.v[f] * (A)e[P.ci[f]];
-  x[i] = (V)((A)x[i] + s);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = t / G;
+  const int g = (int)(t % G);
+  const A s = csr_row<G>(P, e, i, g);
+  if (i < P.n && g == 0) x[i] = (V)((A)x[i] + s);
 }
+
+// group width for a CSR matrix: the power of two nearest half its mean row
+// length, in [1, 32]
+inline int group_width(int64_t nnz, int64_t n) {
+  const double avg = n > 0 ? (double)nnz / (double)n : 1.0;
+  int g = 1;
+  while (g < 32 && 2 * g <= avg) g *= 2;
+  return g;
+}
+
+#define EB_GROUP_LAUNCH(G, kernel, V, rows, s, ...)                                               \
+  do {                                                                                           \
+    const unsigned nb_ = blocks_for((int64_t)(rows) * (G), 256);                                 \
+    switch (G) {                                                                                 \
+      case 1: kernel<1, V><<<nb_, 256, 0, s>>>(__VA_ARGS__); break;                              \
+      case 2: kernel<2, V><<<nb_, 256, 0, s>>>(__VA_ARGS__); break;                              \
+      case 4: kernel<4, V><<<nb_, 256, 0, s>>>(__VA_ARGS__); break;                              \
+      case 8: kernel<8, V><<<nb_, 256, 0, s>>>(__VA_ARGS__); break;                              \
+      case 16: kernel<16, V><<<nb_, 256, 0, s>>>(__VA_ARGS__); break;                            \
+      default: kernel<32, V><<<nb_, 256, 0, s>>>(__VA_ARGS__); break;                            \
+    }                                                                                            \
+  } while (0)
 
 // x = M b with M the FP64 inverse (row-major); one warp per row
 template <class V>
@@ -277,19 +330,20 @@ static void vcycle_compact(Solver& S, size_t l, cudaStream_t s) {
   const ChebCoef cc = cheb_coef(L.rho, S.opts.cheb_degree);
   S.nlaunch += 3 + 2 * cc.deg;  // first step, deg-1 steps, residual, restriction, prolongation, deg steps
   const CsrV<V> A = LV::A(L);
+  const int gA = group_width(L.A.nnz, L.A.n), gP = group_width(L.P.nnz, L.P.n), gR = group_width(L.R.nnz, L.R.n);
   k_c_cheb_first<V><<<nb, 256, 0, s>>>(n, LV::dinv(L), v.b, v.x, v.d, cc.theta);
   for (int k = 1; k < cc.deg; ++k) {
-    k_c_cheb_step<V><<<nb, 256, 0, s>>>(A, LV::dinv(L), v.b, v.x, v.x2, v.d, cc.c1[k], cc.c2[k]);
+    EB_GROUP_LAUNCH(gA, k_c_cheb_step, V, n, s, A, LV::dinv(L), v.b, v.x, v.x2, v.d, cc.c1[k], cc.c2[k]);
     std::swap(v.x, v.x2);
   }
-  k_c_resid<V><<<nb, 256, 0, s>>>(A, v.b, v.x, v.r);
+  EB_GROUP_LAUNCH(gA, k_c_resid, V, n, s, A, v.b, v.x, v.r);
   Level& C = H.L[l + 1];
   VecSet<V>& cv = LV::vec(C);
-  k_c_spmv<V><<<blocks_for(C.A.n, 256), 256, 0, s>>>(LV::R(L), v.r, cv.b);
+  EB_GROUP_LAUNCH(gR, k_c_spmv, V, C.A.n, s, LV::R(L), v.r, cv.b);
   vcycle_compact<V>(S, l + 1, s);
-  k_c_prolong_add<V><<<nb, 256, 0, s>>>(LV::P(L), cv.x, v.x);
+  EB_GROUP_LAUNCH(gP, k_c_prolong_add, V, n, s, LV::P(L), cv.x, v.x);
   for (int k = 0; k < cc.deg; ++k) {
-    k_c_cheb_step<V><<<nb, 256, 0, s>>>(A, LV::dinv(L), v.b, v.x, v.x2, v.d, cc.c1[k], cc.c2[k]);
+    EB_GROUP_LAUNCH(gA, k_c_cheb_step, V, n, s, A, LV::dinv(L), v.b, v.x, v.x2, v.d, cc.c1[k], cc.c2[k]);
     std::swap(v.x, v.x2);
   }
 }
@@ -316,7 +370,9 @@ static void vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s) {
   const unsigned gb = tile_grid(eb);
   const ChebCoef cc = cheb_coef(L0.rho, S.opts.cheb_degree);
   const TileView tv = eb.tv();
-  const GOp o{inv_h2, S.shift, 1.0 / (S.shift + 2.0 * G.dim * inv_h2)};
+  using A = typename AccOf<V>::type;
+  const GOp<A> o{(A)inv_h2, (A)S.shift, (A)(1.0 / (S.shift + 2.0 * G.dim * inv_h2))};
+  const typename DiagOf<V>::type* diag = diag_of<V>(eb);
   S.nlaunch += 3 + 2 * cc.deg;
   VecSet<V>& g = LV::grid(H);
   // FP64 storage reads r directly; FP32 storage keeps a rounded copy in g.b
@@ -324,27 +380,28 @@ static void vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s) {
   const V* b = std::is_same<V, double>::value ? reinterpret_cast<const V*>(r) : g.b;
   V* x = g.x;
   V* x2 = g.x2;
-  k_g_cheb_first<DIM, V><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, eb.diag, o, r, bcopy, x, g.d, cc.theta);
+  k_g_cheb_first<DIM, V><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, r, bcopy, x, g.d, (A)cc.theta);
   for (int k = 1; k < cc.deg; ++k) {
     S.prof_mark(s, true);
-    k_g_cheb_step<DIM, V, V><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, eb.diag, o, b, x, x2, g.d, cc.c1[k], cc.c2[k]);
+    k_g_cheb_step<DIM, V, V><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, x, x2, g.d, (A)cc.c1[k], (A)cc.c2[k]);
     S.prof_mark(s, false);
     std::swap(x, x2);
   }
-  k_g_resid<DIM, V><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, eb.diag, o, b, x, g.r);
+  k_g_resid<DIM, V><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, x, g.r);
   Level& C = H.L[1];
   VecSet<V>& cv = LV::vec(C);
   const CsrV<V> R0 = LV::R(L0), P0 = LV::P(L0);
-  k_restrict0<V><<<blocks_for(C.A.n, 256), 256, 0, s>>>(C.A.n, R0.rp, L0.R0node, R0.v, g.r, cv.b);
+  const int gR = group_width(L0.R.nnz, L0.R.n), gP = group_width(L0.P.nnz, L0.P.n);
+  EB_GROUP_LAUNCH(gR, k_restrict0, V, C.A.n, s, C.A.n, R0.rp, L0.R0node, R0.v, g.r, cv.b);
   vcycle_compact<V>(S, 1, s);
-  k_prolong0<V><<<blocks_for(P0.n, 256), 256, 0, s>>>(P0.n, P0.rp, P0.ci, P0.v, eb.cp_node, cv.x, x);
+  EB_GROUP_LAUNCH(gP, k_prolong0, V, P0.n, s, P0.n, P0.rp, P0.ci, P0.v, eb.cp_node, cv.x, x);
   for (int k = 0; k < cc.deg; ++k) {
     S.prof_mark(s, true);
     if (k == cc.deg - 1)
       k_g_cheb_step<DIM, V, double>
-          <<<gb, TILE_NODES, 0, s>>>(tv, eb.code, eb.diag, o, b, x, z, g.d, cc.c1[k], cc.c2[k]);
+          <<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, x, z, g.d, (A)cc.c1[k], (A)cc.c2[k]);
     else
-      k_g_cheb_step<DIM, V, V><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, eb.diag, o, b, x, x2, g.d, cc.c1[k], cc.c2[k]);
+      k_g_cheb_step<DIM, V, V><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, x, x2, g.d, (A)cc.c1[k], (A)cc.c2[k]);
     S.prof_mark(s, false);
     if (k != cc.deg - 1) std::swap(x, x2);
   }

@@ -294,6 +294,11 @@ __global__ void k_compact(const int32_t* flag, const int32_t* off, int64_t n, in
   if (t < n && flag[t]) out[off[t]] = (int32_t)t;
 }
 
+__global__ void k_diag32(int64_t n, const double* d, float* f) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) f[i] = (float)d[i];
+}
+
 // corner node and extents of each listed tile
 __global__ void k_tile_geom(Geometry G, const int32_t* tiles, int64_t nt, int32_t* base, int32_t* lim) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -425,6 +430,8 @@ void build_handle(EBHandle& eb, const eb_grid& grid, const eb_levelset& ls, cuda
   eb.tile_base = dalloc<int32_t>(nt, s, false);
   eb.tile_lim = dalloc<int32_t>(nt, s, false);
   k_tile_geom<<<blocks_for(nt, T), T, 0, s>>>(G, eb.tiles, nt, eb.tile_base, eb.tile_lim);
+  eb.diag32 = dalloc<float>(nn, s, false);
+  k_diag32<<<blocks_for(nn, T), T, 0, s>>>(nn, eb.diag, eb.diag32);
   EB_CUDA(cudaGetLastError());
   eb.num_far = (int64_t)hst.num_far;
   eb.max_delta_over_h = hst.max_delta_over_h;
@@ -436,7 +443,7 @@ void build_handle(EBHandle& eb, const eb_grid& grid, const eb_levelset& ls, cuda
 
 void destroy_handle(EBHandle& eb) {
   cudaStream_t s = eb.home;
-  dfree(eb.code, s); dfree(eb.diag, s); dfree(eb.cp_of_node, s); dfree(eb.cp_node, s);
+  dfree(eb.code, s); dfree(eb.diag, s); dfree(eb.diag32, s); dfree(eb.cp_of_node, s); dfree(eb.cp_node, s);
   dfree(eb.tiles, s); dfree(eb.tile_base, s); dfree(eb.tile_lim, s); dfree(eb.cut_cp, s); dfree(eb.cut_dir, s); dfree(eb.cut_delta, s);
   dfree(eb.cut_c, s); dfree(eb.cut_xg, s); dfree(eb.cut_off, s);
   cudaStreamSynchronize(s);

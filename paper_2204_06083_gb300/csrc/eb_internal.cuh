@@ -98,6 +98,7 @@ struct EBHandle {
   double max_delta_over_h = 0.0, min_abs_psi = 0.0;
   uint8_t* code = nullptr;       // [num_nodes]
   double* diag = nullptr;        // [num_nodes] D_k (h^2 units) at CPs, 0 elsewhere
+  float* diag32 = nullptr;       // [num_nodes] FP32 copy for the FP32 / BF16 kernels
   int32_t* cp_of_node = nullptr; // [num_nodes]
   int32_t* cp_node = nullptr;    // [num_cp]
   int32_t* tiles = nullptr;      // [num_tiles] linear tile index, ascending
@@ -112,6 +113,25 @@ struct EBHandle {
   int32_t* cut_off = nullptr;    // [num_cp + 1] first cut of CP k
   cudaStream_t home = 0;
 };
+
+// D_k array matching a kernel's element type: FP64 kernels read the FP64
+// diagonal, FP32 / BF16 kernels its FP32 copy (no FP64 instruction in them)
+template <class T>
+struct DiagOf {
+  using type = float;
+};
+template <>
+struct DiagOf<double> {
+  using type = double;
+};
+template <class T>
+inline const typename DiagOf<T>::type* diag_of(const EBHandle& eb) {
+  return eb.diag32;
+}
+template <>
+inline const double* diag_of<double>(const EBHandle& eb) {
+  return eb.diag;
+}
 
 // ----------------------------------------------------------- build / apply
 void build_handle(EBHandle& eb, const eb_grid& grid, const eb_levelset& ls, cudaStream_t s);

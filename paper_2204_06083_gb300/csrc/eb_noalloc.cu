@@ -90,11 +90,10 @@ __device__ bool noalloc_sync(NoAllocWaveScratch* sc, unsigned int k) {
 // Same arithmetic as the leapfrog kernel of wave_step.
 template <class T, int DIM>
 __global__ void __launch_bounds__(TILE_NODES) k_leapfrog_noalloc(TileView tv, const uint8_t* __restrict__ code,
-                                                                 const double* __restrict__ diag, T* ua, T* ub,
-                                                                 int nsteps, double dt2, double inv_h2,
+                                                                 const typename DiagOf<T>::type* __restrict__ diag,
+                                                                 T* ua, T* ub, int nsteps, typename AccOf<T>::type c2,
                                                                  NoAllocWaveScratch* sc) {
   using A = typename AccOf<T>::type;
-  const A c2 = (A)(dt2 * inv_h2);
   for (int s = 0; s < nsteps; ++s) {
     T* prev = (s & 1) ? ub : ua;
     const T* cur = (s & 1) ? ua : ub;
@@ -155,12 +154,12 @@ static int leapfrog_noalloc(const EBHandle& eb, T* ua, T* ub, int nsteps, double
                                       std::to_string(EB_NOALLOC_MAX_CTAS)};
   // clear the counter, the error word and the flags this launch uses
   EB_CUDA(cudaMemsetAsync(sc, 0, offsetof(NoAllocWaveScratch, arrive) + sizeof(unsigned int) * (size_t)nb, s));
-  double dt2 = dt * dt, inv_h2 = 1.0 / (G.h * G.h);
+  typename AccOf<T>::type c2 = (typename AccOf<T>::type)(dt * dt / (G.h * G.h));
   TileView tv = eb.tv();
   const uint8_t* code = eb.code;
-  const double* diag = eb.diag;
+  const typename DiagOf<T>::type* diag = diag_of<T>(eb);
   void* args[] = {(void*)&tv, (void*)&code, (void*)&diag, (void*)&ua, (void*)&ub, (void*)&nsteps,
-                  (void*)&dt2, (void*)&inv_h2, (void*)&sc};
+                  (void*)&c2, (void*)&sc};
   EB_CUDA(cudaLaunchCooperativeKernel(fn, dim3((unsigned)nb), dim3(TILE_NODES), args, 0, s));
   int err = 0;
   EB_CUDA(cudaMemcpyAsync(&err, &sc->err, sizeof(int), cudaMemcpyDeviceToHost, s));

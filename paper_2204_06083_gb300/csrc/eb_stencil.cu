@@ -111,27 +111,29 @@ void exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t
 // y = (sigma I + A) x on the active tiles, 0 at their non-CP nodes.
 template <class T, int DIM>
 __global__ void __launch_bounds__(TILE_NODES) k_apply(TileView tv, const uint8_t* __restrict__ code,
-                                                      const double* __restrict__ diag, const T* __restrict__ x,
-                                                      T* __restrict__ y, double sigma, double inv_h2) {
+                                                      const typename DiagOf<T>::type* __restrict__ diag,
+                                                      const T* __restrict__ x, T* __restrict__ y,
+                                                      typename AccOf<T>::type sigma, typename AccOf<T>::type inv_h2) {
   using A = typename AccOf<T>::type;
   EB_PAIR_LOOP(DIM, tv, node) {
     uint32_t c0, c1;
     ld_codes(code, node, c0, c1);
     Two<A> xc, core;
     stencil_pair<DIM, LdRO>(x, node, tv.nn, c0, c1, diag, tv.sy, tv.sz, xc, core);
-    const A v0 = (c0 & CODE_CP) ? core.x * (A)inv_h2 + (A)sigma * xc.x : (A)0;
-    const A v1 = (c1 & CODE_CP) ? core.y * (A)inv_h2 + (A)sigma * xc.y : (A)0;
+    const A v0 = (c0 & CODE_CP) ? core.x * inv_h2 + sigma * xc.x : (A)0;
+    const A v1 = (c1 & CODE_CP) ? core.y * inv_h2 + sigma * xc.y : (A)0;
     st2(y + node, v0, v1);
   }
 }
 
 template <class T>
 void launch_apply(const EBHandle& eb, const T* x, T* y, double sigma, cudaStream_t s) {
-  const double inv_h2 = 1.0 / (eb.g.h * eb.g.h);
+  using A = typename AccOf<T>::type;
+  const A inv_h2 = (A)(1.0 / (eb.g.h * eb.g.h));
   if (eb.g.dim == 2)
-    k_apply<T, 2><<<tile_grid(eb), TILE_NODES, 0, s>>>(eb.tv(), eb.code, eb.diag, x, y, sigma, inv_h2);
+    k_apply<T, 2><<<tile_grid(eb), TILE_NODES, 0, s>>>(eb.tv(), eb.code, diag_of<T>(eb), x, y, (A)sigma, inv_h2);
   else
-    k_apply<T, 3><<<tile_grid(eb), TILE_NODES, 0, s>>>(eb.tv(), eb.code, eb.diag, x, y, sigma, inv_h2);
+    k_apply<T, 3><<<tile_grid(eb), TILE_NODES, 0, s>>>(eb.tv(), eb.code, diag_of<T>(eb), x, y, (A)sigma, inv_h2);
   EB_CUDA(cudaGetLastError());
 }
 
@@ -192,10 +194,10 @@ __device__ bool grid_sync(GridBarrier* gb) {
 // Fields written during the launch are read through L2 (ld.global.cg).
 template <class T, int DIM>
 __global__ void __launch_bounds__(TILE_NODES) k_leapfrog(TileView tv, const uint8_t* __restrict__ code,
-                                                         const double* __restrict__ diag, T* ua, T* ub, int nsteps,
-                                                         double dt2, double inv_h2, GridBarrier* gb) {
+                                                         const typename DiagOf<T>::type* __restrict__ diag, T* ua,
+                                                         T* ub, int nsteps, typename AccOf<T>::type c2,
+                                                         GridBarrier* gb) {
   using A = typename AccOf<T>::type;
-  const A c2 = (A)(dt2 * inv_h2);
   for (int s = 0; s < nsteps; ++s) {
     T* prev = (s & 1) ? ub : ua;
     const T* cur = (s & 1) ? ua : ub;
@@ -232,12 +234,13 @@ int launch_leapfrog(const EBHandle& eb, T* ua, T* ub, int nsteps, double dt, cud
   EB_REQUIRE(per_sm > 0, EB_ERR_INVALID, "leapfrog kernel cannot be resident");
   int64_t nb = std::min<int64_t>(eb.num_tiles, (int64_t)per_sm * num_sms());
   unsigned blocks = (unsigned)std::max<int64_t>(nb, 1);
-  double dt2 = dt * dt, inv_h2 = 1.0 / (G.h * G.h);
+  // dt^2 / h^2, the only constant of the step, in the field's arithmetic type
+  typename AccOf<T>::type c2 = (typename AccOf<T>::type)(dt * dt / (G.h * G.h));
   TileView tv = eb.tv();
   const uint8_t* code = eb.code;
-  const double* diag = eb.diag;
+  const typename DiagOf<T>::type* diag = diag_of<T>(eb);
   void* args[] = {(void*)&tv, (void*)&code, (void*)&diag, (void*)&ua, (void*)&ub, (void*)&nsteps,
-                  (void*)&dt2, (void*)&inv_h2, (void*)&gb};
+                  (void*)&c2, (void*)&gb};
   EB_CUDA(cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(TILE_NODES), args, 0, s));
   GridBarrier hb{};
   EB_CUDA(cudaMemcpyAsync(&hb, gb, sizeof(hb), cudaMemcpyDeviceToHost, s));

@@ -77,10 +77,12 @@ __device__ __forceinline__ Two<double> ld2d(const double* p) {
 }
 
 // D_k x_k - sum of the CP-neighbour values, for the pair (node, node + 1).
-// nn = number of grid nodes (even); the pair's codes c0, c1 are given.
-template <int DIM, class L, class T>
+// nn = number of grid nodes (even); the pair's codes c0, c1 are given.  diag
+// is the FP64 D_k array for FP64 kernels and its FP32 copy for the others, so
+// that FP32 kernels run no FP64 instruction (GB300's FP64 pipe is narrow).
+template <int DIM, class L, class T, class DT>
 __device__ __forceinline__ void stencil_pair(const T* __restrict__ x, int32_t node, int32_t nn, uint32_t c0,
-                                             uint32_t c1, const double* __restrict__ diag, int32_t sy, int32_t sz,
+                                             uint32_t c1, const DT* __restrict__ diag, int32_t sy, int32_t sz,
                                              Two<typename AccOf<T>::type>& xc, Two<typename AccOf<T>::type>& core) {
   using A = typename AccOf<T>::type;
   const Two<A> z{0, 0};
