@@ -218,6 +218,51 @@ int heat_step(const amg_handle* amg, double dt, double theta, const double* b1_d
 int wave_step(const eb_handle* eb, int prec, double dt, void* u_prev_dev, void* u_cur_dev, int nsteps,
               cudaStream_t stream);
 
+/* ---------------------------------------------------------------- batches
+ * Many 2D geometries of uneven size advanced together: one launch per PCG
+ * phase over the active tiles of all of them, per-geometry CG recurrences and
+ * convergence, one AMG hierarchy on the block-diagonal operator.  Used for
+ * batches of implicit heat steps (Sec. 3.4) on different domains.
+ *
+ * Batch layout of every batch vector: geometry g's full grid (n0_g x n1_g
+ * nodes, x fastest) at node offset node_off[g], rows of common stride S
+ * (batch_info.stride): node (i, j) of g is node_off[g] + j S + i.  Cut values
+ * (u_Gamma) are concatenated geometry by geometry (cut_off[g]), each in the
+ * eb_cuts order of that geometry.  Entries outside the CPs are ignored on
+ * input; outputs follow the active-tile rule of the single-grid calls. */
+typedef struct batch_handle batch_handle;
+
+typedef struct {
+  int count;
+  int64_t stride;        /* S, the common row stride */
+  int64_t num_nodes;     /* total nodes of the batch layout */
+  int64_t num_cp;
+  int64_t num_cut;
+  int64_t num_tiles;
+} batch_info_t;
+
+/* Builds every geometry (eb_build semantics, 2D only) and the batch layout.
+ * grids / lss: host arrays of count entries.  Synchronous. */
+int batch_build(const eb_grid* grids, const eb_levelset* lss, int count, batch_handle** out, cudaStream_t stream);
+void batch_destroy(batch_handle* b);
+int batch_info(const batch_handle* b, batch_info_t* out);
+/* Host arrays of count + 1 entries each (any may be NULL): node, cut and CP
+ * offsets of the geometries in the batch layout. */
+int batch_offsets(const batch_handle* b, int64_t* node_off, int64_t* cut_off, int64_t* cp_off);
+/* The batch's own handle of geometry g (owned by the batch; valid until
+ * batch_destroy), for eb_cuts / eb_classes / eb_apply on that grid alone. */
+const eb_handle* batch_geometry(const batch_handle* b, int g);
+/* eb_rhs for every geometry, in the batch layout. */
+int batch_rhs(const batch_handle* b, const double* f_all, const double* ug_all, double* b_all, cudaStream_t stream);
+/* Fixes the time steps dt[g] (host array) and theta of the theta-method and
+ * builds the AMG hierarchy of the batch.  Synchronous. */
+int batch_heat_setup(batch_handle* b, const double* dt, double theta, const amg_opts* opts, cudaStream_t stream);
+/* One theta-method step of every geometry (heat_step semantics, warm start
+ * from u), u overwritten.  stats: host array of count entries (may be NULL).
+ * Returns EB_ERR_NO_CONVERGENCE if any geometry missed rtol.  Synchronous. */
+int batch_heat_step(batch_handle* b, const double* b1_all, const double* b0_all, double* u_all, double rtol,
+                    int maxit, pcg_stats* stats, cudaStream_t stream);
+
 /* The leapfrog step of wave_step for callers that must not allocate device
  * memory during the call.  The paper has no counterpart: this is a service of
  * this library.  wave_step allocates a small barrier record per call; code

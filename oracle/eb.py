@@ -352,3 +352,24 @@ def ghost_point_operator(grid: ei.Grid, ls: ei.LevelSet) -> sp.csr_matrix:
     M = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                       shape=(nodes.size, nodes.size)) / (h * h)
     return M
+
+
+def assemble_unit(eb: EBSystem, shift: float) -> sp.csr_matrix:
+    """h^2 (sigma I + A) written with unit spacing: off-diagonals -1 towards CP
+    neighbours, diagonal D_k + shift with shift = sigma h^2 (eq. 3 multiplied
+    by h^2; used for batches of grids with different h)."""
+    n = eb.num_cp
+    st = strides(eb.grid)
+    rows = [np.arange(n)]
+    cols = [np.arange(n)]
+    vals = [eb.diag + shift]
+    for ax in range(eb.grid.dim):
+        for sgn in (-1, 1):
+            j = eb.cp_of_node[eb.cp_nodes + sgn * st[ax]]
+            k = np.flatnonzero(j >= 0)
+            rows.append(k)
+            cols.append(j[k])
+            vals.append(np.full(k.size, -1.0))
+    M = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+    M.sort_indices()
+    return M

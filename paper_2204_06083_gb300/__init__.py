@@ -88,6 +88,14 @@ _SIGS = {
     "heat_step": (C.c_int, [_P, C.c_double, C.c_double, _P, _P, _P, C.c_double, C.c_int, C.POINTER(pcg_stats), _P]),
     "wave_step": (C.c_int, [_P, C.c_int, C.c_double, _P, _P, C.c_int, _P]),
     "wave_step_noalloc": (C.c_int, [_P, C.c_int, C.c_double, _P, _P, C.c_int, _P]),
+    "batch_build": (C.c_int, [_P, _P, C.c_int, C.POINTER(_P), _P]),
+    "batch_destroy": (None, [_P]),
+    "batch_info": (C.c_int, [_P, _P]),
+    "batch_offsets": (C.c_int, [_P, _P, _P, _P]),
+    "batch_geometry": (_P, [_P, C.c_int]),
+    "batch_rhs": (C.c_int, [_P, _P, _P, _P, _P]),
+    "batch_heat_setup": (C.c_int, [_P, _P, C.c_double, C.POINTER(amg_opts), _P]),
+    "batch_heat_step": (C.c_int, [_P, _P, _P, _P, C.c_double, C.c_int, _P, _P]),
     "eb_last_error": (C.c_char_p, []),
 }
 
@@ -344,3 +352,90 @@ class AMG:
         _check(load().heat_step(self._h, float(dt), float(theta), _ptr(b1), _ptr(b0), _ptr(u), float(rtol),
                                 int(maxit), C.byref(st), _stream(stream)))
         return st
+
+
+class batch_info_t(C.Structure):
+    _fields_ = [("count", C.c_int), ("stride", C.c_int64), ("num_nodes", C.c_int64), ("num_cp", C.c_int64),
+                ("num_cut", C.c_int64), ("num_tiles", C.c_int64)]
+
+
+class _Borrowed(EB):
+    """EB view of a geometry owned by a batch (never destroyed here)."""
+
+    def __init__(self, handle, grid):
+        self._h = C.c_void_p(handle)
+        self.grid = grid
+        self.dim = grid.dim
+        inf = eb_info_t()
+        _check(load().eb_info(self._h, C.byref(inf)))
+        self.info = Info(inf.num_nodes, inf.num_cp, inf.num_bp, inf.num_cut, inf.num_far, inf.num_tiles,
+                         tuple(inf.tile), inf.max_delta_over_h, inf.min_abs_psi)
+
+    def close(self):
+        self._h = C.c_void_p()
+
+
+class Batch:
+    """Handle of batch_build: many 2D geometries in one batch layout."""
+
+    def __init__(self, grids, levelsets, stream=None):
+        lib = load()
+        n = len(grids)
+        G = (eb_grid * n)(*[make_grid(g) for g in grids])
+        L = (eb_levelset * n)(*[make_levelset(l) for l in levelsets])
+        self._h = C.c_void_p()
+        self.grids = list(grids)
+        _check(lib.batch_build(C.cast(G, C.c_void_p), C.cast(L, C.c_void_p), n, C.byref(self._h), _stream(stream)))
+        inf = batch_info_t()
+        _check(lib.batch_info(self._h, C.cast(C.byref(inf), C.c_void_p)))
+        self.count, self.stride, self.num_nodes = inf.count, inf.stride, inf.num_nodes
+        self.num_cp, self.num_cut, self.num_tiles = inf.num_cp, inf.num_cut, inf.num_tiles
+        no, co, po = (C.c_int64 * (n + 1))(), (C.c_int64 * (n + 1))(), (C.c_int64 * (n + 1))()
+        _check(lib.batch_offsets(self._h, C.cast(no, C.c_void_p), C.cast(co, C.c_void_p), C.cast(po, C.c_void_p)))
+        self.node_off, self.cut_off, self.cp_off = list(no), list(co), list(po)
+
+    def close(self):
+        if self._h:
+            load().batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def geometry(self, g):
+        h = load().batch_geometry(self._h, g)
+        if not h:
+            raise EBError(EB_ERR_INVALID, load().eb_last_error().decode())
+        return _Borrowed(h, self.grids[g])
+
+    def view(self, v, g):
+        """Geometry g's (n1, n0) grid inside a batch-layout vector."""
+        gr = self.grids[g]
+        a = v[self.node_off[g]:self.node_off[g + 1]].view(gr.n[1], self.stride)
+        return a[:, :gr.n[0]]
+
+    def zeros(self, dtype=None):
+        import torch
+        return torch.zeros(self.num_nodes, dtype=dtype or torch.float64, device="cuda")
+
+    def rhs(self, f_all, ug_all, out=None, stream=None):
+        if out is None:
+            out = self.zeros()
+        _check(load().batch_rhs(self._h, _ptr(f_all), _ptr(ug_all), _ptr(out), _stream(stream)))
+        return out
+
+    def heat_setup(self, dt, theta=1.0, max_levels=25, coarse_max=1024, strength=0.02, cheb_degree=2,
+                   vcycle_prec=EB_F64, stream=None):
+        d = (C.c_double * self.count)(*[float(v) for v in dt])
+        o = amg_opts(max_levels, coarse_max, strength, cheb_degree, vcycle_prec)
+        _check(load().batch_heat_setup(self._h, C.cast(d, C.c_void_p), float(theta), C.byref(o), _stream(stream)))
+
+    def heat_step(self, u_all, b1_all, b0_all=None, rtol=1e-10, maxit=500, stream=None, allow_noconv=False):
+        st = (pcg_stats * self.count)()
+        _check(load().batch_heat_step(self._h, _ptr(b1_all), _ptr(b0_all), _ptr(u_all), float(rtol), int(maxit),
+                                      C.cast(st, C.c_void_p), _stream(stream)),
+               allow=(EB_ERR_NO_CONVERGENCE,) if allow_noconv else ())
+        return list(st)

@@ -601,31 +601,37 @@ __global__ void k_map_cols(int64_t nnz, const int32_t* ci, const int32_t* map, i
   if (e < nnz) out[e] = map[ci[e]];
 }
 
-void amg_build(Solver& S, cudaStream_t s) {
-  const EBHandle& eb = *S.eb;
+// level-0 matrix sigma I + A over the CPs of one grid, in CSR
+DCsr level0_csr(const EBHandle& eb, double sigma, cudaStream_t s) {
   const Geometry& G = eb.g;
-  Hierarchy* H = new Hierarchy();
-  S.H = H;
   const int64_t ncp = eb.num_cp;
-  // level-0 matrix sigma I + A over the CPs
   DCsr A0;
   A0.n = A0.m = ncp;
-  {
-    int32_t* cnt = dalloc<int32_t>(ncp + 1, s);
-    k_l0_count<<<blocks_for(ncp, 256), 256, 0, s>>>(G, eb.cp_node, eb.code, ncp, cnt);
-    A0.rp = dalloc<int32_t>(ncp + 1, s, false);
-    exclusive_scan_i32(cnt, A0.rp, ncp, s);
-    int32_t nnz = 0;
-    EB_CUDA(cudaMemcpyAsync(&nnz, A0.rp + ncp, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    EB_CUDA(cudaStreamSynchronize(s));
-    A0.nnz = nnz;
-    A0.ci = dalloc<int32_t>(nnz, s, false);
-    A0.v = dalloc<double>(nnz, s, false);
-    k_l0_fill<<<blocks_for(ncp, 256), 256, 0, s>>>(G, eb.cp_node, eb.cp_of_node, eb.code, eb.diag, ncp, S.shift,
-                                                    A0.rp, A0.ci, A0.v);
-    EB_CUDA(cudaGetLastError());
-    dfree(cnt, s);
-  }
+  int32_t* cnt = dalloc<int32_t>(ncp + 1, s);
+  k_l0_count<<<blocks_for(ncp, 256), 256, 0, s>>>(G, eb.cp_node, eb.code, ncp, cnt);
+  A0.rp = dalloc<int32_t>(ncp + 1, s, false);
+  exclusive_scan_i32(cnt, A0.rp, ncp, s);
+  int32_t nnz = 0;
+  EB_CUDA(cudaMemcpyAsync(&nnz, A0.rp + ncp, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  EB_CUDA(cudaStreamSynchronize(s));
+  A0.nnz = nnz;
+  A0.ci = dalloc<int32_t>(nnz, s, false);
+  A0.v = dalloc<double>(nnz, s, false);
+  k_l0_fill<<<blocks_for(ncp, 256), 256, 0, s>>>(G, eb.cp_node, eb.cp_of_node, eb.code, eb.diag, ncp, sigma, A0.rp,
+                                                  A0.ci, A0.v);
+  EB_CUDA(cudaGetLastError());
+  dfree(cnt, s);
+  return A0;
+}
+
+void amg_build(Solver& S, cudaStream_t s) { amg_build_from(S, level0_csr(*S.eb, S.shift, s), s); }
+
+// Hierarchy from a given level-0 CSR whose row k is the CP at node
+// S.eb->cp_node[k] of the (possibly batched) grid view.
+void amg_build_from(Solver& S, DCsr A0, cudaStream_t s) {
+  const EBHandle& eb = *S.eb;
+  Hierarchy* H = new Hierarchy();
+  S.H = H;
   DCsr A = A0;
   const int max_levels = std::max(1, S.opts.max_levels);
   for (int lev = 0;; ++lev) {

@@ -48,6 +48,8 @@ struct Hierarchy {
   VecSet<float> g32;
 };
 
+DCsr level0_csr(const EBHandle& eb, double sigma, cudaStream_t s);
+void amg_build_from(Solver& S, DCsr A0, cudaStream_t s);
 void amg_alloc_vcycle(Solver& S, cudaStream_t s);
 void amg_free_vcycle(Hierarchy& H, cudaStream_t s);
 

@@ -37,6 +37,24 @@ __device__ __forceinline__ A inv_diag_t(uint32_t c, const DT* __restrict__ diag,
   return (A)1 / (o.sigma + (A)__ldg(diag + node) * o.inv_h2);
 }
 
+// per-tile shift of a batched view (unit spacing, sigma_g per geometry)
+__device__ __forceinline__ GOp<float> tile_op(const TileView& tv, int64_t tt, GOp<float> o) {
+  if (tv.tshift32) {
+    const float2 t = __ldg(tv.tshift32 + tt);
+    o.sigma = t.x;
+    o.dinv_int = t.y;
+  }
+  return o;
+}
+__device__ __forceinline__ GOp<double> tile_op(const TileView& tv, int64_t tt, GOp<double> o) {
+  if (tv.tshift64) {
+    const double2 t = __ldg(tv.tshift64 + tt);
+    o.sigma = t.x;
+    o.dinv_int = t.y;
+  }
+  return o;
+}
+
 __device__ __forceinline__ void st2o(double* p, double a, double b) { st2(p, a, b); }
 __device__ __forceinline__ void st2o(float* p, float a, float b) { st2(p, a, b); }
 
@@ -51,13 +69,14 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_first(TileView tv, const 
                                                              typename AccOf<V>::type theta) {
   using A = typename AccOf<V>::type;
   EB_PAIR_LOOP(DIM, tv, node) {
+    const GOp<A> ot = tile_op(tv, tt_, o);
     uint32_t c0, c1;
     ld_codes(code, node, c0, c1);
     const Two<double> rv = LdRO::ld2(r + node);
     const A b0 = (c0 & CODE_CP) ? (A)rv.x : (A)0, b1 = (c1 & CODE_CP) ? (A)rv.y : (A)0;
     if (b_out) st2o(b_out + node, b0, b1);
-    const A v0 = (c0 & CODE_CP) ? inv_diag_t<A>(c0, diag, node, o) * b0 / theta : (A)0;
-    const A v1 = (c1 & CODE_CP) ? inv_diag_t<A>(c1, diag, node + 1, o) * b1 / theta : (A)0;
+    const A v0 = (c0 & CODE_CP) ? inv_diag_t<A>(c0, diag, node, ot) * b0 / theta : (A)0;
+    const A v1 = (c1 & CODE_CP) ? inv_diag_t<A>(c1, diag, node + 1, ot) * b1 / theta : (A)0;
     st2o(x + node, v0, v1);
     st2o(d + node, v0, v1);
   }
@@ -73,6 +92,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_step(TileView tv, const u
                                                             typename AccOf<V>::type c1, typename AccOf<V>::type c2) {
   using A = typename AccOf<V>::type;
   EB_PAIR_LOOP(DIM, tv, node) {
+    const GOp<A> ot = tile_op(tv, tt_, o);
     uint32_t k0, k1;
     ld_codes(code, node, k0, k1);
     Two<A> xc, core;
@@ -83,8 +103,8 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_step(TileView tv, const u
       const Two<A> t = LdRO::ld2(d + node);
       dv = t;
     }
-    const A res0 = inv_diag_t<A>(k0, diag, node, o) * (bv.x - (core.x * o.inv_h2 + o.sigma * xc.x));
-    const A res1 = inv_diag_t<A>(k1, diag, node + 1, o) * (bv.y - (core.y * o.inv_h2 + o.sigma * xc.y));
+    const A res0 = inv_diag_t<A>(k0, diag, node, ot) * (bv.x - (core.x * ot.inv_h2 + ot.sigma * xc.x));
+    const A res1 = inv_diag_t<A>(k1, diag, node + 1, ot) * (bv.y - (core.y * ot.inv_h2 + ot.sigma * xc.y));
     const A d0 = (k0 & CODE_CP) ? c1 * dv.x + c2 * res0 : (A)0;
     const A d1 = (k1 & CODE_CP) ? c1 * dv.y + c2 * res1 : (A)0;
     st2o(d + node, d0, d1);
@@ -100,13 +120,14 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_resid(TileView tv, const uint8
                                                         V* __restrict__ r) {
   using A = typename AccOf<V>::type;
   EB_PAIR_LOOP(DIM, tv, node) {
+    const GOp<A> ot = tile_op(tv, tt_, o);
     uint32_t c0, c1;
     ld_codes(code, node, c0, c1);
     Two<A> xc, core;
     stencil_pair<DIM, LdRO>(x, node, tv.nn, c0, c1, diag, tv.sy, tv.sz, xc, core);
     const Two<A> bv = LdRO::ld2(b + node);
-    st2o(r + node, (c0 & CODE_CP) ? bv.x - (core.x * o.inv_h2 + o.sigma * xc.x) : (A)0,
-         (c1 & CODE_CP) ? bv.y - (core.y * o.inv_h2 + o.sigma * xc.y) : (A)0);
+    st2o(r + node, (c0 & CODE_CP) ? bv.x - (core.x * ot.inv_h2 + ot.sigma * xc.x) : (A)0,
+         (c1 & CODE_CP) ? bv.y - (core.y * ot.inv_h2 + ot.sigma * xc.y) : (A)0);
   }
 }
 

@@ -6,9 +6,6 @@
 #include <chrono>
 #include <cmath>
 
-struct eb_handle {
-  ebk::EBHandle h;
-};
 struct amg_handle {
   ebk::Solver s;
 };

@@ -104,7 +104,12 @@ struct EBHandle {
   int32_t* tiles = nullptr;      // [num_tiles] linear tile index, ascending
   int32_t* tile_base = nullptr;  // [num_tiles] corner node of each listed tile
   int32_t* tile_lim = nullptr;   // [num_tiles] extents x | y << 8 | z << 16
-  TileView tv() const { return TileView{tile_base, tile_lim, num_tiles, g.n0, g.n0 * g.n1, (int32_t)g.num_nodes}; }
+  double2* tile_shift64 = nullptr;  // batched view only: per-tile (sigma, 1 / (sigma + 2 dim))
+  float2* tile_shift32 = nullptr;
+  TileView tv() const {
+    return TileView{tile_base, tile_lim, num_tiles, g.n0, g.n0 * g.n1, (int32_t)g.num_nodes, tile_shift64,
+                    tile_shift32};
+  }
   int32_t* cut_cp = nullptr;     // [num_cut]
   int32_t* cut_dir = nullptr;    // [num_cut]
   double* cut_delta = nullptr;   // [num_cut]
@@ -113,6 +118,15 @@ struct EBHandle {
   int32_t* cut_off = nullptr;    // [num_cp + 1] first cut of CP k
   cudaStream_t home = 0;
 };
+
+}  // namespace ebk
+
+// the opaque handle of the C ABI
+struct eb_handle {
+  ebk::EBHandle h;
+};
+
+namespace ebk {
 
 // D_k array matching a kernel's element type: FP64 kernels read the FP64
 // diagonal, FP32 / BF16 kernels its FP32 copy (no FP64 instruction in them)

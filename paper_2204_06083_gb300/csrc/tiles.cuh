@@ -35,6 +35,10 @@ struct TileView {
   int64_t ntiles;
   int32_t sy, sz;       // node strides of y and z
   int32_t nn;           // number of grid nodes (even)
+  // batched grids only (null for one grid): per-tile shift sigma and
+  // 1 / (sigma + 2 dim) of the unit-spacing operator, FP64 and FP32 copies
+  const double2* tshift64 = nullptr;
+  const float2* tshift32 = nullptr;
 };
 
 // Node of this thread in listed tile tt (one node per thread, 256 threads).

@@ -238,3 +238,16 @@ def test_rhs_sign_convention():
     r = s.A @ u.reshape(-1)[s.cp_nodes] - b
     interior = np.setdiff1d(np.arange(s.num_cp), s.cut_cp)
     assert np.abs(r[interior]).max() < 1e-9
+
+
+def test_unit_operator_is_scaled_operator():
+    grid, ls = ei.box_grid(2, 70), ei.random_star(12)
+    s = eb.build(grid, ls)
+    sig = 3.7
+    U = eb.assemble_unit(s, sig * grid.h ** 2)
+    ref = (s.A * grid.h ** 2 + sig * grid.h ** 2 * __import__("scipy.sparse", fromlist=["identity"]).identity(s.num_cp)).tocsr()
+    assert np.abs((U - ref).toarray()).max() < 1e-12
+    off = U - __import__("scipy.sparse", fromlist=["diags"]).diags(U.diagonal())
+    off = off.tocsr()
+    off.eliminate_zeros()
+    assert np.all(off.data == -1.0)
