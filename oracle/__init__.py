@@ -21,6 +21,9 @@ Modules
             a library, Sec. 3 preamble), V-cycle with Chebyshev smoothing
   solvers   CG / PCG (Algorithm 1 step 4), dense Cholesky, Lanczos
             extremes, leapfrog and theta-method time stepping (Sec. 3.4-3.5)
+  cnn       the learned correction stage added to the preconditioner (no
+            counterpart in the paper): network forward / backward, energy-norm
+            loss, solver-generated training pairs, Adam, flexible PCG
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_*.py`` against a closed form, an invariant the paper states,
