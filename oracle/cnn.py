@@ -18,7 +18,7 @@ Network N (6 layers, zero-padded 3x3 cross-correlations, 32 hidden channels):
 
 Flat parameter vector theta (float):
     W1 [32][9][2], b1 [32], then for l = 1..4: W_l [32][9][32], b_l [32],
-    then W6 [9][32], b6 [1]                               (NPARAM = 38,721).
+    then W6 [9][32], b6 [1]                               (NPARAM = 37,889).
 
 Training pairs (the solver's own residual / error pairs).  For an SPD operator
 A (shift included), right-hand side b, its solution x* and the V-cycle V:
@@ -158,24 +158,30 @@ def forward(theta: np.ndarray, s_hat: np.ndarray, mask: np.ndarray, storage: str
         acts.append(a)
     W6, b6 = layers[5]
     y6 = conv3x3(a, W6, b6)[0]
-    return mask * y6, {"acts": acts, "mask": np.asarray(mask, np.float64)}
+    return mask * y6, {"acts": acts, "mask": np.asarray(mask, np.float64), "storage": storage}
 
 
 def backward(theta: np.ndarray, cache, dout: np.ndarray) -> np.ndarray:
-    """Gradient of sum(dout * N(s_hat, m)) in theta (reverse of forward)."""
+    """Gradient of sum(dout * N(s_hat, m)) in theta (reverse of forward).
+
+    After a forward with storage = "bf16" the gradients of the five hidden
+    layers' outputs are rounded to bfloat16 as a BF16 implementation stores
+    them, and their propagation through the four 32 -> 32 layers uses the
+    bf16 weights."""
     layers = unpack(theta)
     acts = cache["acts"]
+    rnd = bf16 if cache.get("storage") == "bf16" else (lambda v: v)
     grads = [None] * 6
     g = (dout * cache["mask"])[None]
     dW, db = conv3x3_wgrad(acts[5], g)
     grads[5] = (dW, db)
     ga = conv3x3_transpose(g, layers[5][0])
     for l in range(4, -1, -1):
-        g = ga * (acts[l + 1] > 0)           # through ReLU of layer l
+        g = rnd(ga * (acts[l + 1] > 0))      # through ReLU of layer l
         dW, db = conv3x3_wgrad(acts[l], g)
         grads[l] = (dW, db)
         if l > 0:
-            ga = conv3x3_transpose(g, layers[l][0])
+            ga = conv3x3_transpose(g, rnd(layers[l][0]))
     return pack(grads)
 
 
