@@ -138,7 +138,9 @@ int eb_rhs(const eb_handle* eb, const double* f_dev, const double* ugamma_dev, d
 int eb_apply(const eb_handle* eb, int prec, const void* x_dev, void* y_dev, cudaStream_t stream);
 
 /* ---------------------------------------------------------------- AMG + PCG */
-typedef enum { EB_PC_AMG = 0, EB_PC_JACOBI = 1, EB_PC_NONE = 2 } eb_pc_kind;
+/* EB_PC_AMG_NN (V-cycle followed by the learned stage) is selected by
+ * pcg_solve_nn only; pcg_solve rejects it. */
+typedef enum { EB_PC_AMG = 0, EB_PC_JACOBI = 1, EB_PC_NONE = 2, EB_PC_AMG_NN = 3 } eb_pc_kind;
 
 typedef struct {
   int max_levels;        /* default 25 */
@@ -262,6 +264,81 @@ int batch_heat_setup(batch_handle* b, const double* dt, double theta, const amg_
  * Returns EB_ERR_NO_CONVERGENCE if any geometry missed rtol.  Synchronous. */
 int batch_heat_step(batch_handle* b, const double* b1_all, const double* b0_all, double* u_all, double rtol,
                     int maxit, pcg_stats* stats, cudaStream_t stream);
+
+/* ------------------------------------------------------------ learned stage
+ * A small convolutional network N on the 2D Cartesian grid used as an extra
+ * stage of the preconditioner.  The paper has no learned component: this is
+ * an extension of its AMG-PCG (Algorithm 1 step 4).
+ *
+ * N(s_hat, m): six zero-padded 3x3 cross-correlations, 2 -> 32 -> 32 -> 32 ->
+ * 32 -> 32 -> 1 channels, ReLU after the first five; the output is multiplied
+ * by the mask channel m (1 at the CPs, 0 elsewhere).  Tap d = 3 (dy+1) +
+ * (dx+1) reads the pixel (row + dy, column + dx); x is the column.
+ * Parameters: one float vector of nn_num_params() = 37889 entries,
+ *   W1 [32][9][2], b1 [32], 4 x (W [32][9][32], b [32]), W6 [9][32], b6 [1]
+ * (W[co][d][ci]).  Hidden activations are stored in bfloat16 (NHWC, 64 bytes
+ * per pixel) and the four 32 -> 32 layers run on the tensor cores with bf16
+ * weights; every sum is accumulated in float.
+ *
+ * Images: "images" images of height x width pixels, stored one after the
+ * other, row-major (x fastest); each image is zero-padded separately.
+ *
+ * Training pairs (nn_pairs) come from the solver itself: for a right-hand side
+ * b with solution x*, x_0 = 0, x_k = x_{k-1} + V(b - A x_{k-1}) (V: the
+ * handle's V-cycle), e_k = x* - x_k, t_k = h^2 A e_k, rho_k = rms of t_k over
+ * the CPs, s_hat_k = t_k / rho_k, e_hat_k = e_k / rho_k, c_k = e_hat_k' s_hat_k.
+ * Loss of an output o on pair k: (o'A~o - 2 o's_hat_k + c_k) / c_k =
+ * ||o - e_hat_k||^2 / ||e_hat_k||^2 in the energy norm of A~ = h^2 A.
+ * Stage in the flexible PCG: z1 = V(r), s = r - A z1,
+ * z = z1 + h^2 rms(s) N(s / rms(s), m).
+ */
+typedef struct nn_handle nn_handle;
+
+/* A network with all parameters 0 (set them with nn_set_params).  Synchronous. */
+int nn_create(nn_handle** out, cudaStream_t stream);
+void nn_destroy(nn_handle* nn);
+int nn_num_params(void);
+/* Copies nn_num_params() floats from HOST memory into the network and resets
+ * the Adam state (moments and step count).  Synchronous. */
+int nn_set_params(nn_handle* nn, const float* params_host, cudaStream_t stream);
+/* Copies the parameters and / or the gradient of the last nn_backward or
+ * nn_train_step to HOST memory (either pointer may be NULL).  Synchronous. */
+int nn_get_params(const nn_handle* nn, float* params_host, float* grad_host, cudaStream_t stream);
+/* out = N(in): in is [images][height][width][2] floats (s_hat, m), out is
+ * [images][height][width] floats, both device buffers (in 8-byte aligned).
+ * width, height >= 1.  Activation memory is held by the handle and grows to
+ * the largest images x height x width seen (64 bytes x 7 per pixel). */
+int nn_forward(nn_handle* nn, int width, int height, int images, const float* in_dev, float* out_dev,
+               cudaStream_t stream);
+/* Gradient of sum(dout * N(in)) in the parameters (kept in the handle, read
+ * with nn_get_params).  Runs the forward pass itself; dout has the layout of
+ * nn_forward's out. */
+int nn_backward(nn_handle* nn, int width, int height, int images, const float* in_dev, const float* dout_dev,
+                cudaStream_t stream);
+/* The first `count` training pairs of the V-cycle iteration of amg (above)
+ * for b and x* (full-grid device vectors): s_hat into s_hat_dev[count][num_nodes]
+ * (float), c_k into c_dev[count] (double), e_hat into e_hat_dev[count][num_nodes]
+ * (double; may be NULL).  Entries off the CPs are 0. */
+int nn_pairs(const amg_handle* amg, const double* b_dev, const double* xstar_dev, int count, float* s_hat_dev,
+             double* c_dev, double* e_hat_dev, cudaStream_t stream);
+/* The geometry a training image needs: the eb_classes byte of every node and
+ * the diagonal D_k as float (0 off the CPs), into num_nodes-entry buffers. */
+int nn_geometry(const eb_handle* eb, uint8_t* code_dev, float* diag_dev, cudaStream_t stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, step size lr) on the mean
+ * loss of `batch` pairs.  Pair j of the batch is pair pick[j] of a store:
+ * s_hat[pick[j]] (float, height x width), c[pick[j]] (double), on the
+ * geometry geo_of[pick[j]] of code[][height x width] / diag[][height x width]
+ * (nn_geometry).  pick and geo_of are device int32 arrays; the caller keeps
+ * every index in range.  loss_dev (may be NULL): device floats, batch + 1
+ * entries, the loss of every pair before the step and their mean last. */
+int nn_train_step(nn_handle* nn, int width, int height, int batch, const float* s_hat_dev, const double* c_dev,
+                  const int32_t* geo_of_dev, const uint8_t* code_dev, const float* diag_dev, const int32_t* pick_dev,
+                  float lr, float* loss_dev, cudaStream_t stream);
+/* pcg_solve with the preconditioner V-cycle + learned stage (above), flexible
+ * (Polak-Ribiere) beta.  2D grids; amg must hold a hierarchy.  opts->precond
+ * is ignored. */
+int pcg_solve_nn(const amg_handle* amg, nn_handle* nn, const double* b_dev, double* x_dev, double rtol, int maxit,
+                 const pcg_opts* opts, pcg_stats* stats, cudaStream_t stream);
 
 /* The leapfrog step of wave_step for callers that must not allocate device
  * memory during the call.  The paper has no counterpart: this is a service of

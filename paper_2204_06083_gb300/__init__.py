@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libeb.so")
 EB_OK, EB_ERR_INVALID, EB_ERR_GEOMETRY, EB_ERR_CUDA, EB_ERR_NONFINITE = 0, 1, 2, 3, 4
 EB_ERR_NO_CONVERGENCE, EB_ERR_BREAKDOWN, EB_ERR_TIMEOUT, EB_ERR_OOM, EB_ERR_NOT_IMPLEMENTED = 5, 6, 7, 8, 9
 EB_F64, EB_F32, EB_BF16 = 0, 1, 2
-EB_PC_AMG, EB_PC_JACOBI, EB_PC_NONE = 0, 1, 2
+EB_PC_AMG, EB_PC_JACOBI, EB_PC_NONE, EB_PC_AMG_NN = 0, 1, 2, 3
 STAR_MAX = 16
 
 CODE_BP = 0x40
@@ -96,6 +96,18 @@ _SIGS = {
     "batch_rhs": (C.c_int, [_P, _P, _P, _P, _P]),
     "batch_heat_setup": (C.c_int, [_P, _P, C.c_double, C.POINTER(amg_opts), _P]),
     "batch_heat_step": (C.c_int, [_P, _P, _P, _P, C.c_double, C.c_int, _P, _P]),
+    "nn_create": (C.c_int, [C.POINTER(_P), _P]),
+    "nn_destroy": (None, [_P]),
+    "nn_num_params": (C.c_int, []),
+    "nn_set_params": (C.c_int, [_P, _P, _P]),
+    "nn_get_params": (C.c_int, [_P, _P, _P, _P]),
+    "nn_forward": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P]),
+    "nn_backward": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P]),
+    "nn_pairs": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, _P, _P]),
+    "nn_geometry": (C.c_int, [_P, _P, _P, _P]),
+    "nn_train_step": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P, _P, C.c_float, _P, _P]),
+    "pcg_solve_nn": (C.c_int, [_P, _P, _P, _P, C.c_double, C.c_int, C.POINTER(pcg_opts), C.POINTER(pcg_stats),
+                               _P]),
     "eb_last_error": (C.c_char_p, []),
 }
 
@@ -439,3 +451,104 @@ class Batch:
                                       C.cast(st, C.c_void_p), _stream(stream)),
                allow=(EB_ERR_NO_CONVERGENCE,) if allow_noconv else ())
         return list(st)
+
+
+class Net:
+    """Handle of nn_create: the learned preconditioner stage (a 6-layer BF16
+    convolutional network on the 2D grid), its training and its use in the
+    flexible PCG."""
+
+    def __init__(self, params=None, stream=None):
+        lib = load()
+        self._h = C.c_void_p()
+        _check(lib.nn_create(C.byref(self._h), _stream(stream)))
+        self.num_params = lib.nn_num_params()
+        if params is not None:
+            self.set_params(params, stream)
+
+    def close(self):
+        if self._h:
+            load().nn_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_params(self, params, stream=None):
+        """params: numpy-convertible vector of num_params floats (host)."""
+        import numpy as np
+        a = np.ascontiguousarray(np.asarray(params, dtype=np.float32).reshape(-1))
+        if a.size != self.num_params:
+            raise ValueError(f"expected {self.num_params} parameters, got {a.size}")
+        _check(load().nn_set_params(self._h, a.ctypes.data_as(C.c_void_p), _stream(stream)))
+
+    def params(self, stream=None):
+        import numpy as np
+        p = np.empty(self.num_params, dtype=np.float32)
+        g = np.empty(self.num_params, dtype=np.float32)
+        _check(load().nn_get_params(self._h, p.ctypes.data_as(C.c_void_p), g.ctypes.data_as(C.c_void_p),
+                                    _stream(stream)))
+        return p, g
+
+    def forward(self, inp, out=None, stream=None):
+        """inp: float32 [images, height, width, 2] (s_hat, m); returns [images, height, width]."""
+        import torch
+        if inp.dim() == 3:
+            inp = inp.unsqueeze(0)
+        nimg, h, w, two = inp.shape
+        if two != 2 or inp.dtype != torch.float32:
+            raise ValueError("expected a float32 [images, height, width, 2] tensor")
+        if out is None:
+            out = torch.empty((nimg, h, w), dtype=torch.float32, device="cuda")
+        _check(load().nn_forward(self._h, w, h, nimg, _ptr(inp), _ptr(out), _stream(stream)))
+        return out
+
+    def backward(self, inp, dout, stream=None):
+        """Gradient of sum(dout * N(inp)) in the parameters (read with params())."""
+        if inp.dim() == 3:
+            inp = inp.unsqueeze(0)
+        nimg, h, w, _ = inp.shape
+        _check(load().nn_backward(self._h, w, h, nimg, _ptr(inp), _ptr(dout), _stream(stream)))
+
+    def train_step(self, s_hat, c, geo_of, code, diag, pick, lr, loss=None, stream=None):
+        """One Adam step over the pairs pick[] of a pair store (nn_train_step).
+        s_hat [n_pairs, height, width] float32, c [n_pairs] float64, geo_of
+        [n_pairs] int32, code [n_geo, height, width] uint8, diag [n_geo,
+        height, width] float32, pick [batch] int32, all on the device; loss:
+        optional float32 [batch + 1] device tensor."""
+        batch = pick.numel()
+        h, w = s_hat.shape[1], s_hat.shape[2]
+        _check(load().nn_train_step(self._h, w, h, batch, _ptr(s_hat), _ptr(c), _ptr(geo_of), _ptr(code),
+                                    _ptr(diag), _ptr(pick), float(lr), _ptr(loss), _stream(stream)))
+        return loss
+
+
+def nn_geometry(eb: EB, code_out, diag_out, stream=None):
+    _check(load().nn_geometry(eb.handle, _ptr(code_out), _ptr(diag_out), _stream(stream)))
+
+
+def nn_pairs(amg: AMG, b, x_star, count, s_out, c_out, e_out=None, stream=None):
+    """The first count training pairs of the V-cycle iteration (nn_pairs)."""
+    _check(load().nn_pairs(amg._h, _ptr(b), _ptr(x_star), int(count), _ptr(s_out), _ptr(c_out), _ptr(e_out),
+                           _stream(stream)))
+
+
+def solve_nn(amg: AMG, net: Net, b, x=None, rtol=1e-10, maxit=1000, check_every=1, use_graph=1, stream=None,
+             allow_noconv=False):
+    """Flexible PCG with the V-cycle followed by the learned stage (pcg_solve_nn)."""
+    import torch
+    if x is None:
+        x = torch.zeros_like(b)
+    o = pcg_opts(EB_PC_AMG_NN, check_every, use_graph, 0)
+    st = pcg_stats()
+    _check(load().pcg_solve_nn(amg._h, net.handle, _ptr(b), _ptr(x), float(rtol), int(maxit), C.byref(o),
+                               C.byref(st), _stream(stream)), allow=(EB_ERR_NO_CONVERGENCE,) if allow_noconv else ())
+    return x, st
+

@@ -1,0 +1,1115 @@
+// Learned correction stage of the preconditioner: a small convolutional
+// network on the 2D Cartesian grid, its training on the device, the
+// solver-generated training pairs, and the stage inside the flexible PCG.
+// The paper has no learned component; this extends its AMG-PCG (Algorithm 1
+// step 4).  Definitions (network, pairs, loss, stage) are those of include/eb.h.
+//
+// Storage: hidden activations BF16 NHWC (32 channels = 64 bytes per pixel);
+// FP32 master parameters, BF16 copies of the 32 -> 32 weights; every sum in
+// FP32.  The four 32 -> 32 layers (99.6 % of the FLOPs) are implicit GEMMs on
+// the tensor cores: a CTA owns 128 pixels of one image row and all 32 output
+// channels; the three input rows it needs (130 pixels x 32 channels) and the
+// 9 x 32 x 32 weights sit in shared memory; K = 9 taps x 32 channels.  Data
+// gradients run through the same kernel with flipped, transposed weights and
+// the ReLU mask of the layer input applied in its epilogue; weight gradients
+// are GEMMs over pixels with per-CTA partials summed in a fixed order.  The
+// 2 -> 32 and 32 -> 1 layers run on the CUDA cores.
+#include "eb_solver.cuh"
+
+#include <mma.h>
+
+#include <algorithm>
+#include <cmath>
+#include <utility>
+
+namespace ebk {
+
+using bf16 = __nv_bfloat16;
+namespace wm = nvcuda::wmma;
+
+constexpr int NC = 32;    // hidden channels
+constexpr int NMID = 4;   // 32 -> 32 layers
+constexpr int TPX = 128;  // pixels per CTA job (one row segment)
+constexpr int LDA = 48;   // shared-memory pixel stride in bf16 (96 bytes: 32-byte aligned rows)
+constexpr int LDC = 36;   // FP32 epilogue stride
+
+// flat parameter vector
+constexpr int W1_N = NC * 9 * 2, B1_N = NC;
+constexpr int WM_N = NC * 9 * NC, BM_N = NC;
+constexpr int W6_N = 9 * NC, B6_N = 1;
+constexpr int OFF_W1 = 0;
+constexpr int OFF_WM = OFF_W1 + W1_N + B1_N;  // middle layer l at OFF_WM + l (WM_N + BM_N)
+constexpr int OFF_W6 = OFF_WM + NMID * (WM_N + BM_N);
+constexpr int NPARAM = OFF_W6 + W6_N + B6_N;
+static_assert(NPARAM == 37889, "parameter layout");
+
+__host__ __device__ constexpr int off_wm(int l) { return OFF_WM + l * (WM_N + BM_N); }
+
+// A stack of images: H rows of W pixels, image boundaries every R rows.
+struct Image {
+  int W, H, R;
+  __device__ int64_t npx() const { return (int64_t)W * H; }
+};
+
+// ------------------------------------------------------------ forward
+// layer 1 (2 -> 32) + ReLU; in: (s_hat, m) per pixel
+__global__ void k_l1_fwd(Image im, const float2* __restrict__ in, const float* __restrict__ P,
+                         bf16* __restrict__ y) {
+  __shared__ float w[W1_N + B1_N];
+  for (int i = threadIdx.x; i < W1_N + B1_N; i += blockDim.x) w[i] = P[OFF_W1 + i];
+  __syncthreads();
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= im.npx()) return;
+  const int x = (int)(p % im.W), r = (int)(p / im.W);
+  const int lo = (r / im.R) * im.R, hi = lo + im.R;
+  float2 v[9];
+#pragma unroll
+  for (int d = 0; d < 9; ++d) {
+    const int xx = x + d % 3 - 1, rr = r + d / 3 - 1;
+    v[d] = (xx >= 0 && xx < im.W && rr >= lo && rr < hi) ? in[(int64_t)rr * im.W + xx] : make_float2(0.f, 0.f);
+  }
+  __align__(16) bf16 ov[NC];
+#pragma unroll 4
+  for (int co = 0; co < NC; ++co) {
+    float a = w[W1_N + co];
+#pragma unroll
+    for (int d = 0; d < 9; ++d) a += w[(co * 9 + d) * 2] * v[d].x + w[(co * 9 + d) * 2 + 1] * v[d].y;
+    ov[co] = __float2bfloat16_rn(fmaxf(a, 0.0f));
+  }
+  int4* dst = reinterpret_cast<int4*>(y + p * NC);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) dst[q] = reinterpret_cast<const int4*>(ov)[q];
+}
+
+// Stages the rows r-1, r, r+1 (pixels x0-1 .. x0+TPX) of x into sIn [3][TPX+2][LDA],
+// zero outside the image.
+__device__ __forceinline__ void stage_rows(const Image& im, const bf16* __restrict__ x, int r, int x0, bf16* sIn) {
+  const int lo = (r / im.R) * im.R, hi = lo + im.R;
+  for (int i = threadIdx.x; i < 3 * (TPX + 2) * 4; i += blockDim.x) {
+    const int q = i & 3, px = (i >> 2) % (TPX + 2), rr = (i >> 2) / (TPX + 2);
+    const int gx = x0 - 1 + px, gr = r - 1 + rr;
+    int4 v = make_int4(0, 0, 0, 0);
+    if (gx >= 0 && gx < im.W && gr >= lo && gr < hi)
+      v = *reinterpret_cast<const int4*>(x + ((int64_t)gr * im.W + gx) * NC + q * 8);
+    *reinterpret_cast<int4*>(sIn + (rr * (TPX + 2) + px) * LDA + q * 8) = v;
+  }
+}
+
+// 32 -> 32 convolution on the tensor cores.  wk: bf16 [9][32 (k)][32 (n)];
+// y = conv + bias (if bias), then ReLU (if relu), then 0 where mask_ref <= 0
+// (if mask_ref: the ReLU derivative of a data gradient).
+__global__ void __launch_bounds__(128) k_conv32(Image im, const bf16* __restrict__ x, const bf16* __restrict__ wk,
+                                                const float* __restrict__ bias, bf16* __restrict__ y, int relu,
+                                                const bf16* __restrict__ mask_ref) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  bf16* sIn = reinterpret_cast<bf16*>(smem_raw);   // [3][TPX + 2][LDA]
+  bf16* sW = sIn + 3 * (TPX + 2) * LDA;            // [9 * 32][LDA]
+  float* sC = reinterpret_cast<float*>(smem_raw);  // [TPX][LDC], aliases sIn after the MMAs
+  const int segs = (im.W + TPX - 1) / TPX;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int i = tid; i < 9 * NC * 4; i += blockDim.x) {
+    const int row = i >> 2, q = i & 3;
+    *reinterpret_cast<int4*>(sW + row * LDA + q * 8) = *reinterpret_cast<const int4*>(wk + row * NC + q * 8);
+  }
+  float bv[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) bv[c] = bias ? bias[c] : 0.0f;
+  const int64_t jobs = (int64_t)segs * im.H;
+  for (int64_t job = blockIdx.x; job < jobs; job += gridDim.x) {
+    const int r = (int)(job / segs), x0 = (int)(job % segs) * TPX;
+    __syncthreads();  // the previous job's epilogue is done with sC / sIn
+    stage_rows(im, x, r, x0, sIn);
+    __syncthreads();
+    wm::fragment<wm::accumulator, 16, 16, 16, float> acc[2][2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) wm::fill_fragment(acc[a][b], 0.0f);
+#pragma unroll 1
+    for (int d = 0; d < 9; ++d) {
+      const int dy = d / 3, dx = d % 3;
+#pragma unroll
+      for (int cb = 0; cb < 2; ++cb) {
+        wm::fragment<wm::matrix_a, 16, 16, 16, bf16, wm::row_major> fa[2];
+        wm::fragment<wm::matrix_b, 16, 16, 16, bf16, wm::row_major> fb[2];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+          wm::load_matrix_sync(fa[mt], sIn + (dy * (TPX + 2) + 32 * warp + 16 * mt + dx) * LDA + cb * 16, LDA);
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) wm::load_matrix_sync(fb[nt], sW + (d * NC + cb * 16) * LDA + nt * 16, LDA);
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+          for (int nt = 0; nt < 2; ++nt) wm::mma_sync(acc[mt][nt], fa[mt], fb[nt], acc[mt][nt]);
+      }
+    }
+    __syncthreads();  // all warps are done reading sIn before it becomes sC
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+        wm::store_matrix_sync(sC + (32 * warp + 16 * mt) * LDC + nt * 16, acc[mt][nt], LDC, wm::mem_row_major);
+    __syncthreads();
+    const int gx = x0 + tid;
+    if (gx < im.W) {
+      const int64_t p = (int64_t)r * im.W + gx;
+      __align__(16) bf16 ov[NC];
+      __align__(16) bf16 mr[NC];
+      if (mask_ref) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          reinterpret_cast<int4*>(mr)[q] = reinterpret_cast<const int4*>(mask_ref + p * NC)[q];
+      }
+#pragma unroll
+      for (int co = 0; co < NC; ++co) {
+        float v = sC[tid * LDC + co] + bv[co];
+        if (relu) v = fmaxf(v, 0.0f);
+        if (mask_ref && !(__bfloat162float(mr[co]) > 0.0f)) v = 0.0f;
+        ov[co] = __float2bfloat16_rn(v);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) reinterpret_cast<int4*>(y + p * NC)[q] = reinterpret_cast<const int4*>(ov)[q];
+    }
+  }
+}
+
+// layer 6 (32 -> 1); out = m * (conv + b6)
+__global__ void k_l6_fwd(Image im, const bf16* __restrict__ y5, const float* __restrict__ P,
+                         const float2* __restrict__ in, float* __restrict__ out) {
+  __shared__ float w[W6_N + B6_N];
+  for (int i = threadIdx.x; i < W6_N + B6_N; i += blockDim.x) w[i] = P[OFF_W6 + i];
+  __syncthreads();
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= im.npx()) return;
+  const int x = (int)(p % im.W), r = (int)(p / im.W);
+  const int lo = (r / im.R) * im.R, hi = lo + im.R;
+  float a = w[W6_N];
+  for (int d = 0; d < 9; ++d) {
+    const int xx = x + d % 3 - 1, rr = r + d / 3 - 1;
+    if (xx < 0 || xx >= im.W || rr < lo || rr >= hi) continue;
+    const int4* src = reinterpret_cast<const int4*>(y5 + ((int64_t)rr * im.W + xx) * NC);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int4 v = src[q];
+      const bf16* e = reinterpret_cast<const bf16*>(&v);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) a += w[d * NC + q * 8 + c] * __bfloat162float(e[c]);
+    }
+  }
+  out[p] = in[p].y * a;
+}
+
+// ----------------------------------------------------------- backward
+// g6 = dout * m; dy5[p][ci] = (sum_d W6[d][ci] g6[p - off(d)]) * (y5[p][ci] > 0)
+__global__ void k_l6_bwd(Image im, const float* __restrict__ dout, const float2* __restrict__ in,
+                         const bf16* __restrict__ y5, const float* __restrict__ P, bf16* __restrict__ dy5) {
+  __shared__ float w[W6_N];
+  for (int i = threadIdx.x; i < W6_N; i += blockDim.x) w[i] = P[OFF_W6 + i];
+  __syncthreads();
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= im.npx()) return;
+  const int x = (int)(p % im.W), r = (int)(p / im.W);
+  const int lo = (r / im.R) * im.R, hi = lo + im.R;
+  float g[9];
+#pragma unroll
+  for (int d = 0; d < 9; ++d) {
+    const int xx = x - (d % 3 - 1), rr = r - (d / 3 - 1);
+    const int64_t q = (int64_t)rr * im.W + xx;
+    g[d] = (xx >= 0 && xx < im.W && rr >= lo && rr < hi) ? dout[q] * in[q].y : 0.0f;
+  }
+  __align__(16) bf16 yv[NC];
+  __align__(16) bf16 ov[NC];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) reinterpret_cast<int4*>(yv)[q] = reinterpret_cast<const int4*>(y5 + p * NC)[q];
+#pragma unroll 4
+  for (int ci = 0; ci < NC; ++ci) {
+    float a = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 9; ++d) a += w[d * NC + ci] * g[d];
+    ov[ci] = __float2bfloat16_rn(__bfloat162float(yv[ci]) > 0.0f ? a : 0.0f);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) reinterpret_cast<int4*>(dy5 + p * NC)[q] = reinterpret_cast<const int4*>(ov)[q];
+}
+
+// pixels [p0, p1) of CTA b out of nb over n pixels
+__device__ __forceinline__ void chunk_of(int64_t n, int b, int nb, int64_t& p0, int64_t& p1) {
+  const int64_t c = (n + nb - 1) / nb;
+  p0 = (int64_t)b * c < n ? (int64_t)b * c : n;
+  p1 = p0 + c < n ? p0 + c : n;
+}
+
+// layer 6 gradient partials: slot d * 32 + ci: sum g6[p] y5[p + off(d)][ci]; slot 288: sum g6[p]
+__global__ void __launch_bounds__(320) k_l6_wgrad(Image im, const float* __restrict__ dout,
+                                                  const float2* __restrict__ in, const bf16* __restrict__ y5,
+                                                  float* __restrict__ part) {
+  const int slot = threadIdx.x;
+  if (slot > W6_N) return;
+  const int d = slot / NC, ci = slot % NC;
+  const int dx = d % 3 - 1, dy = d / 3 - 1;
+  int64_t p0, p1;
+  chunk_of(im.npx(), blockIdx.x, gridDim.x, p0, p1);
+  float a = 0.0f;
+  for (int64_t p = p0; p < p1; ++p) {
+    const float g = dout[p] * in[p].y;
+    if (g == 0.0f) continue;
+    if (slot == W6_N) {
+      a += g;
+      continue;
+    }
+    const int x = (int)(p % im.W) + dx, r = (int)(p / im.W);
+    const int lo = (r / im.R) * im.R, rr = r + dy;
+    if (x < 0 || x >= im.W || rr < lo || rr >= lo + im.R) continue;
+    a += g * __bfloat162float(y5[((int64_t)rr * im.W + x) * NC + ci]);
+  }
+  part[(int64_t)blockIdx.x * (W6_N + B6_N) + slot] = a;
+}
+
+// layer 1 gradient partials: slot (co * 9 + d) * 2 + ci: sum dy1[p][co] in[p + off(d)][ci];
+// slot 576 + co: sum dy1[p][co]
+__global__ void __launch_bounds__(640) k_l1_wgrad(Image im, const bf16* __restrict__ dy1,
+                                                  const float2* __restrict__ in, float* __restrict__ part) {
+  const int slot = threadIdx.x;
+  if (slot >= W1_N + B1_N) return;
+  int64_t p0, p1;
+  chunk_of(im.npx(), blockIdx.x, gridDim.x, p0, p1);
+  float a = 0.0f;
+  if (slot < W1_N) {
+    const int co = slot / 18, d = (slot / 2) % 9, ci = slot & 1;
+    const int dx = d % 3 - 1, dy = d / 3 - 1;
+    for (int64_t p = p0; p < p1; ++p) {
+      const float g = __bfloat162float(dy1[p * NC + co]);
+      if (g == 0.0f) continue;
+      const int x = (int)(p % im.W) + dx, r = (int)(p / im.W);
+      const int lo = (r / im.R) * im.R, rr = r + dy;
+      if (x < 0 || x >= im.W || rr < lo || rr >= lo + im.R) continue;
+      const float2 v = in[(int64_t)rr * im.W + x];
+      a += g * (ci ? v.y : v.x);
+    }
+  } else {
+    const int co = slot - W1_N;
+    for (int64_t p = p0; p < p1; ++p) a += __bfloat162float(dy1[p * NC + co]);
+  }
+  part[(int64_t)blockIdx.x * (W1_N + B1_N) + slot] = a;
+}
+
+// 32 -> 32 weight-gradient partials on the tensor cores:
+// part[cta][d][k = ci][n = co] = sum_p x[p + off(d)][ci] dy[p][co]
+__global__ void __launch_bounds__(128) k_conv32_wgrad(Image im, const bf16* __restrict__ x,
+                                                      const bf16* __restrict__ dy, float* __restrict__ part) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  bf16* sIn = reinterpret_cast<bf16*>(smem_raw);  // [3][TPX + 2][LDA]
+  bf16* sDy = sIn + 3 * (TPX + 2) * LDA;          // [TPX][LDA]
+  const int segs = (im.W + TPX - 1) / TPX;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // warp w owns the taps w, w + 4, w + 8 (< 9)
+  wm::fragment<wm::accumulator, 16, 16, 16, float> acc[3][2][2];
+#pragma unroll
+  for (int t = 0; t < 3; ++t)
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) wm::fill_fragment(acc[t][a][b], 0.0f);
+  const int64_t jobs = (int64_t)segs * im.H;
+  for (int64_t job = blockIdx.x; job < jobs; job += gridDim.x) {
+    const int r = (int)(job / segs), x0 = (int)(job % segs) * TPX;
+    __syncthreads();
+    stage_rows(im, x, r, x0, sIn);
+    for (int i = tid; i < TPX * 4; i += blockDim.x) {
+      const int q = i & 3, px = i >> 2, gx = x0 + px;
+      int4 v = make_int4(0, 0, 0, 0);
+      if (gx < im.W) v = *reinterpret_cast<const int4*>(dy + ((int64_t)r * im.W + gx) * NC + q * 8);
+      *reinterpret_cast<int4*>(sDy + px * LDA + q * 8) = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      const int d = warp + 4 * t;
+      if (d < 9) {
+        const int ty = d / 3, tx = d % 3;
+#pragma unroll 2
+        for (int ks = 0; ks < TPX / 16; ++ks) {
+          wm::fragment<wm::matrix_a, 16, 16, 16, bf16, wm::col_major> fa[2];
+          wm::fragment<wm::matrix_b, 16, 16, 16, bf16, wm::row_major> fb[2];
+#pragma unroll
+          for (int kb = 0; kb < 2; ++kb)
+            wm::load_matrix_sync(fa[kb], sIn + (ty * (TPX + 2) + 16 * ks + tx) * LDA + kb * 16, LDA);
+#pragma unroll
+          for (int nb = 0; nb < 2; ++nb) wm::load_matrix_sync(fb[nb], sDy + (16 * ks) * LDA + nb * 16, LDA);
+#pragma unroll
+          for (int kb = 0; kb < 2; ++kb)
+#pragma unroll
+            for (int nb = 0; nb < 2; ++nb) wm::mma_sync(acc[t][kb][nb], fa[kb], fb[nb], acc[t][kb][nb]);
+        }
+      }
+    }
+  }
+  float* out = part + (int64_t)blockIdx.x * WM_N;
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const int d = warp + 4 * t;
+    if (d < 9) {
+#pragma unroll
+      for (int kb = 0; kb < 2; ++kb)
+#pragma unroll
+        for (int nb = 0; nb < 2; ++nb)
+          wm::store_matrix_sync(out + (d * NC + 16 * kb) * NC + 16 * nb, acc[t][kb][nb], NC, wm::mem_row_major);
+    }
+  }
+}
+
+// bias-gradient partials of a 32-channel gradient: part[cta][c] = sum over the CTA's pixels
+__global__ void __launch_bounds__(256) k_bias_grad(int64_t npx, const bf16* __restrict__ dy,
+                                                   float* __restrict__ part) {
+  __shared__ float sm[8][NC];
+  const int c = threadIdx.x & 31, row = threadIdx.x >> 5;
+  int64_t p0, p1;
+  chunk_of(npx, blockIdx.x, gridDim.x, p0, p1);
+  float a = 0.0f;
+  for (int64_t p = p0 + row; p < p1; p += 8) a += __bfloat162float(dy[p * NC + c]);
+  sm[row][c] = a;
+  __syncthreads();
+  if (row == 0) {
+    float s = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += sm[i][c];
+    part[(int64_t)blockIdx.x * NC + c] = s;
+  }
+}
+
+// out[i] = sum over parts of part[c][i] (fixed order)
+__global__ void k_sum_parts(const float* __restrict__ part, int nparts, int n, float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float s = 0.0f;
+  for (int c = 0; c < nparts; ++c) s += part[(int64_t)c * n + i];
+  out[i] = s;
+}
+
+// middle-layer weight gradient: G[(co 9 + d) 32 + ci] = sum over parts of part[c][(d 32 + ci) 32 + co]
+__global__ void k_sum_wgrad(const float* __restrict__ part, int nparts, float* __restrict__ G) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= WM_N) return;
+  float s = 0.0f;
+  for (int c = 0; c < nparts; ++c) s += part[(int64_t)c * WM_N + j];
+  const int co = j % NC, ci = (j / NC) % NC, d = j / (NC * NC);
+  G[(co * 9 + d) * NC + ci] = s;
+}
+
+// ------------------------------------------------------------- weights
+// forward: wf[l][d][k = ci][n = co] = W_l[co][d][ci]
+// data gradient: wb[l][8 - d][k = co][n = ci] = W_l[co][d][ci]
+__global__ void k_pack_weights(const float* __restrict__ P, bf16* __restrict__ wf, bf16* __restrict__ wb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= NMID * WM_N) return;
+  const int l = i / WM_N, rem = i % WM_N;
+  const int co = rem / (9 * NC), d = (rem / NC) % 9, ci = rem % NC;
+  const bf16 w = __float2bfloat16_rn(P[off_wm(l) + rem]);
+  wf[(int64_t)l * WM_N + (d * NC + ci) * NC + co] = w;
+  wb[(int64_t)l * WM_N + ((8 - d) * NC + co) * NC + ci] = w;
+}
+
+__global__ void k_adam(int n, float* __restrict__ P, const float* __restrict__ G, float* __restrict__ m,
+                       float* __restrict__ v, float lr, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const float g = G[i];
+  const float mi = b1 * m[i] + (1.0f - b1) * g;
+  const float vi = b2 * v[i] + (1.0f - b2) * g * g;
+  m[i] = mi;
+  v[i] = vi;
+  P[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// ----------------------------------------------------------------- loss
+// Gathers batch image k from the pair store: input (s_hat, m), node codes,
+// diagonal and c.
+__global__ void k_gather(Image im, const float* __restrict__ s_store, const double* __restrict__ c_store,
+                         const int32_t* __restrict__ geo_of, const uint8_t* __restrict__ code_store,
+                         const float* __restrict__ diag_store, const int32_t* __restrict__ pick,
+                         float2* __restrict__ in, uint8_t* __restrict__ code, float* __restrict__ diag,
+                         double* __restrict__ cimg) {
+  const int64_t per = (int64_t)im.W * im.R;
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= im.npx()) return;
+  const int k = (int)(p / per);
+  const int64_t q = p - (int64_t)k * per;
+  const int64_t s = pick[k];
+  const int64_t g = geo_of[s];
+  const uint8_t c = code_store[g * per + q];
+  const bool cp = (c & CODE_CP) != 0;
+  in[p] = make_float2(cp ? s_store[s * per + q] : 0.0f, cp ? 1.0f : 0.0f);
+  code[p] = c;
+  diag[p] = diag_store[g * per + q];
+  if (q == 0) cimg[k] = c_store[s];
+}
+
+// Per image k (grid.y): per-CTA sums of o'A~o - 2 o's_hat (double);
+// dout = (2 / batch) (A~ o - s_hat) / c_k at the CPs, 0 elsewhere.
+__global__ void __launch_bounds__(256) k_loss(Image im, const uint8_t* __restrict__ code,
+                                              const float* __restrict__ diag, const float2* __restrict__ in,
+                                              const float* __restrict__ o, const double* __restrict__ cimg,
+                                              float inv_batch, float* __restrict__ dout, double* __restrict__ part) {
+  const int k = blockIdx.y;
+  const int64_t per = (int64_t)im.W * im.R;
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double contrib = 0.0;
+  if (q < per) {
+    const int64_t p = (int64_t)k * per + q;
+    const uint8_t c = code[p];
+    float g = 0.0f;
+    if (c & CODE_CP) {
+      const int x = (int)(q % im.W), r = (int)(q / im.W);
+      const float oc = o[p];
+      float sum = 0.0f;
+      if (!(c & 1) && x > 0) sum += o[p - 1];
+      if (!(c & 2) && x + 1 < im.W) sum += o[p + 1];
+      if (!(c & 4) && r > 0) sum += o[p - im.W];
+      if (!(c & 8) && r + 1 < im.R) sum += o[p + im.W];
+      const float Ao = diag[p] * oc - sum;
+      const float sh = in[p].x;
+      contrib = (double)oc * Ao - 2.0 * (double)oc * sh;
+      g = 2.0f * inv_batch * (Ao - sh) / (float)cimg[k];
+    }
+    dout[p] = g;
+  }
+  __shared__ double sm[256];
+  sm[threadIdx.x] = contrib;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(int64_t)k * gridDim.x + blockIdx.x] = sm[0];
+}
+
+// loss[k] = (sum of part[k][*] + c_k) / c_k; loss[batch] = their mean
+__global__ void k_loss_reduce(const double* __restrict__ part, int nblk, int batch, const double* __restrict__ cimg,
+                              float* __restrict__ loss) {
+  __shared__ double sl[256];
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < batch; k += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(int64_t)k * nblk + b];
+    const double L = (s + cimg[k]) / cimg[k];
+    loss[k] = (float)L;
+    acc += L;
+  }
+  sl[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)blockDim.x; ++i) t += sl[i];
+    loss[batch] = (float)(t / batch);
+  }
+}
+
+// ------------------------------------------------ full-grid operator helpers
+// (sigma I + A) x at the CP node p; only CP neighbours are read (mask bits of the code)
+struct GridOp {
+  int dim;
+  int64_t st[3];
+  double inv_h2, sigma;
+};
+
+__device__ __forceinline__ double op_at(const GridOp& G, const uint8_t c, const double* diag, const double* x,
+                                        int64_t p) {
+  double sum = 0.0;
+  for (int s = 0; s < 2 * G.dim; ++s)
+    if (!(c & (1u << s))) sum += x[p + ((s & 1) ? G.st[s >> 1] : -G.st[s >> 1])];
+  return (G.sigma + diag[p] * G.inv_h2) * x[p] - sum * G.inv_h2;
+}
+
+// per-CTA sums of a and b into out2[0..1] (blockDim.x = 256)
+__device__ __forceinline__ void block_sum2(double a, double b, double* out2) {
+  __shared__ double s0[256], s1[256];
+  s0[threadIdx.x] = a;
+  s1[threadIdx.x] = b;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      s0[threadIdx.x] += s0[threadIdx.x + w];
+      s1[threadIdx.x] += s1[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out2[0] = s0[0];
+    out2[1] = s1[0];
+  }
+}
+
+// r = b - (sigma I + A) x at the CPs, 0 elsewhere
+__global__ void __launch_bounds__(256) k_pr_resid(GridOp G, int64_t nn, const uint8_t* __restrict__ code,
+                                                  const double* __restrict__ diag, const double* __restrict__ b,
+                                                  const double* __restrict__ x, double* __restrict__ r) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nn; p += (int64_t)gridDim.x * blockDim.x) {
+    const uint8_t c = code[p];
+    r[p] = (c & CODE_CP) ? b[p] - op_at(G, c, diag, x, p) : 0.0;
+  }
+}
+
+// x += z; e = x* - x at the CPs (e = 0 elsewhere)
+__global__ void k_pr_update(int64_t nn, const uint8_t* __restrict__ code, const double* __restrict__ z,
+                            const double* __restrict__ xs, double* __restrict__ x, double* __restrict__ e) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nn; p += (int64_t)gridDim.x * blockDim.x) {
+    if (code[p] & CODE_CP) {
+      const double xv = x[p] + z[p];
+      x[p] = xv;
+      e[p] = xs[p] - xv;
+    } else {
+      e[p] = 0.0;
+    }
+  }
+}
+
+// t = h^2 (sigma I + A) e at the CPs; per-CTA partials (sum t^2, sum e t)
+__global__ void __launch_bounds__(256) k_pr_unit(GridOp G, double h2, int64_t nn, const uint8_t* __restrict__ code,
+                                                 const double* __restrict__ diag, const double* __restrict__ e,
+                                                 double* __restrict__ t, double* __restrict__ part) {
+  double a = 0.0, b = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nn; p += (int64_t)gridDim.x * blockDim.x) {
+    const uint8_t c = code[p];
+    double tv = 0.0;
+    if (c & CODE_CP) {
+      tv = h2 * op_at(G, c, diag, e, p);
+      a += tv * tv;
+      b += e[p] * tv;
+    }
+    t[p] = tv;
+  }
+  block_sum2(a, b, part + 2 * blockIdx.x);
+}
+
+// rho = rms(t) over the CPs; scal = (1 / rho, c = sum e t / rho^2), c also into c_out
+__global__ void k_pr_norm(const double* __restrict__ part, int nblk, double ncp, double* __restrict__ scal,
+                          double* __restrict__ c_out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double a = 0.0, b = 0.0;
+  for (int i = 0; i < nblk; ++i) {
+    a += part[2 * i];
+    b += part[2 * i + 1];
+  }
+  const double rho = sqrt(a / ncp);
+  const double inv = rho > 0.0 ? 1.0 / rho : 0.0;
+  scal[0] = inv;
+  scal[1] = b * inv * inv;
+  *c_out = b * inv * inv;
+}
+
+__global__ void k_pr_write(int64_t nn, const double* __restrict__ t, const double* __restrict__ e,
+                           const double* __restrict__ scal, float* __restrict__ s_out, double* __restrict__ e_out) {
+  const double inv = scal[0];
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nn; p += (int64_t)gridDim.x * blockDim.x) {
+    s_out[p] = (float)(t[p] * inv);
+    if (e_out) e_out[p] = e[p] * inv;
+  }
+}
+
+// ------------------------------------------------------ stage in the PCG
+// s = r - (sigma I + A) z at the CPs; per-CTA sums of s^2
+__global__ void __launch_bounds__(256) k_st_resid(GridOp G, int64_t nn, const uint8_t* __restrict__ code,
+                                                  const double* __restrict__ diag, const double* __restrict__ r,
+                                                  const double* __restrict__ z, double* __restrict__ s,
+                                                  double* __restrict__ part) {
+  double a = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nn; p += (int64_t)gridDim.x * blockDim.x) {
+    const uint8_t c = code[p];
+    double v = 0.0;
+    if (c & CODE_CP) {
+      v = r[p] - op_at(G, c, diag, z, p);
+      a += v * v;
+    }
+    s[p] = v;
+  }
+  block_sum2(a, 0.0, part + 2 * blockIdx.x);
+}
+
+// scal = (1 / rms(s), or 0 when s = 0; h^2 rms(s))
+__global__ void k_st_norm(const double* __restrict__ part, int nblk, double ncp, double h2,
+                          double* __restrict__ scal) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double a = 0.0;
+  for (int i = 0; i < nblk; ++i) a += part[2 * i];
+  const double rms = sqrt(a / ncp);
+  scal[0] = rms > 0.0 ? 1.0 / rms : 0.0;
+  scal[1] = h2 * rms;
+}
+
+__global__ void k_st_input(int64_t nn, const uint8_t* __restrict__ code, const double* __restrict__ s,
+                           const double* __restrict__ scal, float2* __restrict__ in) {
+  const double inv = scal[0];
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nn; p += (int64_t)gridDim.x * blockDim.x) {
+    const bool cp = (code[p] & CODE_CP) != 0;
+    in[p] = make_float2(cp ? (float)(s[p] * inv) : 0.0f, cp ? 1.0f : 0.0f);
+  }
+}
+
+__global__ void k_st_correct(int64_t nn, const uint8_t* __restrict__ code, const float* __restrict__ o,
+                             const double* __restrict__ scal, double* __restrict__ z) {
+  const double a = scal[1];
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nn; p += (int64_t)gridDim.x * blockDim.x)
+    if (code[p] & CODE_CP) z[p] += a * (double)o[p];
+}
+
+// ---------------------------------------------------------------- host
+struct NN {
+  float* P = nullptr;  // FP32 master parameters
+  float* G = nullptr;  // gradient
+  float* m = nullptr;  // Adam moments
+  float* v = nullptr;
+  bf16* wf = nullptr;  // packed forward weights of the middle layers
+  bf16* wb = nullptr;  // packed data-gradient weights
+  int64_t steps = 0;
+  cudaStream_t home = 0;
+  // activations (grown to the largest stack seen)
+  int64_t cap_px = 0;
+  bf16* act[6] = {};  // act[1..5]: outputs of layers 1..5
+  bf16* gA = nullptr;
+  bf16* gB = nullptr;
+  float* out = nullptr;
+  float* dout = nullptr;
+  float2* in = nullptr;     // gathered / staged input
+  uint8_t* code = nullptr;  // gathered batch geometry
+  float* diag = nullptr;
+  // reductions
+  float* part = nullptr;
+  int64_t cap_part = 0;
+  double* lpart = nullptr;
+  int64_t cap_lpart = 0;
+  double* cimg = nullptr;
+  float* loss = nullptr;
+  int cap_batch = 0;
+  // stage in the PCG
+  int64_t cap_nodes = 0;
+  double* s64 = nullptr;
+  double* spart = nullptr;
+  double* scal = nullptr;
+  int snblk = 0;
+};
+
+static size_t conv_smem() { return (size_t)(3 * (TPX + 2) * LDA + 9 * NC * LDA) * sizeof(bf16); }
+static size_t wgrad_smem() { return (size_t)(3 * (TPX + 2) * LDA + TPX * LDA) * sizeof(bf16); }
+
+static void set_attrs() {
+  static bool done = false;
+  if (done) return;
+  EB_CUDA(cudaFuncSetAttribute(k_conv32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem()));
+  EB_CUDA(cudaFuncSetAttribute(k_conv32_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wgrad_smem()));
+  done = true;
+}
+
+static void ensure_act(NN& N, int64_t px, cudaStream_t s) {
+  if (px <= N.cap_px) return;
+  for (int l = 1; l <= 5; ++l) dfree(N.act[l], s);
+  dfree(N.gA, s); dfree(N.gB, s); dfree(N.out, s); dfree(N.dout, s); dfree(N.in, s); dfree(N.code, s);
+  dfree(N.diag, s);
+  N.cap_px = 0;
+  for (int l = 1; l <= 5; ++l) N.act[l] = dalloc<bf16>((size_t)px * NC, s, false);
+  N.gA = dalloc<bf16>((size_t)px * NC, s, false);
+  N.gB = dalloc<bf16>((size_t)px * NC, s, false);
+  N.out = dalloc<float>(px, s, false);
+  N.dout = dalloc<float>(px, s, false);
+  N.in = dalloc<float2>(px, s, false);
+  N.code = dalloc<uint8_t>(px, s, false);
+  N.diag = dalloc<float>(px, s, false);
+  N.cap_px = px;
+}
+
+static float* ensure_part(NN& N, int64_t n, cudaStream_t s) {
+  if (n > N.cap_part) {
+    dfree(N.part, s);
+    N.cap_part = 0;
+    N.part = dalloc<float>(n, s, false);
+    N.cap_part = n;
+  }
+  return N.part;
+}
+
+static unsigned conv_grid(const Image& im, int per_sm) {
+  const int64_t jobs = (int64_t)((im.W + TPX - 1) / TPX) * im.H;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(jobs, (int64_t)num_sms() * per_sm));
+}
+
+static int64_t npx_of(const Image& im) { return (int64_t)im.W * im.H; }
+
+static void pack(NN& N, cudaStream_t s, int64_t& nl) {
+  k_pack_weights<<<blocks_for(NMID * WM_N, 256), 256, 0, s>>>(N.P, N.wf, N.wb);
+  ++nl;
+}
+
+// out = N(in) over the stack; the activations stay for backward
+static void forward(NN& N, const Image& im, const float2* in, float* out, cudaStream_t s, int64_t& nl) {
+  const int64_t npx = npx_of(im);
+  k_l1_fwd<<<blocks_for(npx, 128), 128, 0, s>>>(im, in, N.P, N.act[1]);
+  for (int l = 0; l < NMID; ++l)
+    k_conv32<<<conv_grid(im, 3), 128, conv_smem(), s>>>(im, N.act[l + 1], N.wf + (int64_t)l * WM_N,
+                                                         N.P + off_wm(l) + WM_N, N.act[l + 2], 1, nullptr);
+  k_l6_fwd<<<blocks_for(npx, 128), 128, 0, s>>>(im, N.act[5], N.P, in, out);
+  nl += 6;
+  EB_CUDA(cudaGetLastError());
+}
+
+// gradient of sum(dout * out) into N.G (forward ran on the same input)
+static void backward(NN& N, const Image& im, const float2* in, const float* dout, cudaStream_t s, int64_t& nl) {
+  const int64_t npx = npx_of(im);
+  const int nsm = num_sms();
+  {
+    const int nb = nsm * 4;
+    float* part = ensure_part(N, (int64_t)nb * (W6_N + B6_N), s);
+    k_l6_wgrad<<<nb, 320, 0, s>>>(im, dout, in, N.act[5], part);
+    k_sum_parts<<<blocks_for(W6_N + B6_N, 256), 256, 0, s>>>(part, nb, W6_N + B6_N, N.G + OFF_W6);
+    k_l6_bwd<<<blocks_for(npx, 128), 128, 0, s>>>(im, dout, in, N.act[5], N.P, N.gA);
+    nl += 3;
+  }
+  bf16* cur = N.gA;
+  bf16* nxt = N.gB;
+  for (int l = NMID - 1; l >= 0; --l) {
+    const unsigned gw = conv_grid(im, 4);
+    const int nbb = nsm * 4;
+    float* part = ensure_part(N, std::max<int64_t>((int64_t)gw * WM_N, (int64_t)nbb * NC), s);
+    k_conv32_wgrad<<<gw, 128, wgrad_smem(), s>>>(im, N.act[l + 1], cur, part);
+    k_sum_wgrad<<<blocks_for(WM_N, 256), 256, 0, s>>>(part, (int)gw, N.G + off_wm(l));
+    k_bias_grad<<<nbb, 256, 0, s>>>(npx, cur, part);
+    k_sum_parts<<<1, 32, 0, s>>>(part, nbb, NC, N.G + off_wm(l) + WM_N);
+    k_conv32<<<conv_grid(im, 3), 128, conv_smem(), s>>>(im, cur, N.wb + (int64_t)l * WM_N, nullptr, nxt, 0,
+                                                         N.act[l + 1]);
+    std::swap(cur, nxt);
+    nl += 5;
+  }
+  {
+    const int nb = nsm * 4;
+    float* part = ensure_part(N, (int64_t)nb * (W1_N + B1_N), s);
+    k_l1_wgrad<<<nb, 640, 0, s>>>(im, cur, in, part);
+    k_sum_parts<<<blocks_for(W1_N + B1_N, 256), 256, 0, s>>>(part, nb, W1_N + B1_N, N.G + OFF_W1);
+    nl += 2;
+  }
+  EB_CUDA(cudaGetLastError());
+}
+
+static GridOp grid_op(const EBHandle& eb, double sigma) {
+  GridOp G;
+  G.dim = eb.g.dim;
+  G.st[0] = 1;
+  G.st[1] = eb.g.n0;
+  G.st[2] = (int64_t)eb.g.n0 * eb.g.n1;
+  G.inv_h2 = 1.0 / (eb.g.h * eb.g.h);
+  G.sigma = sigma;
+  return G;
+}
+
+static unsigned grid_blocks(int64_t nn) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((nn + 255) / 256, (int64_t)num_sms() * 8));
+}
+
+}  // namespace ebk
+
+struct nn_handle {
+  ebk::NN n;
+};
+
+namespace ebk {
+
+void nn_stage_prepare(nn_handle* h, const EBHandle& eb, cudaStream_t s) {
+  NN& N = h->n;
+  EB_REQUIRE(eb.g.dim == 2, EB_ERR_INVALID, "learned stage: 2D grids only");
+  const int64_t nn = eb.g.num_nodes;
+  ensure_act(N, nn, s);
+  if (nn > N.cap_nodes) {
+    dfree(N.s64, s);
+    dfree(N.spart, s);
+    N.cap_nodes = 0;
+    N.snblk = (int)grid_blocks(nn);
+    N.s64 = dalloc<double>(nn, s, false);
+    N.spart = dalloc<double>(2 * (int64_t)N.snblk, s, false);
+    N.cap_nodes = nn;
+  }
+  if (!N.scal) N.scal = dalloc<double>(2, s);
+}
+
+// z = z1 + h^2 rms(s) N(s / rms(s), m) with s = r - (sigma I + A) z1 and z1 = z on entry
+void nn_stage_apply(nn_handle* h, const EBHandle& eb, double shift, const double* r, double* z, int64_t& nl,
+                    cudaStream_t s) {
+  NN& N = h->n;
+  const int64_t nn = eb.g.num_nodes;
+  const unsigned nb = grid_blocks(nn);
+  EB_REQUIRE(nn <= N.cap_nodes && (int)nb <= N.snblk && N.scal, EB_ERR_INVALID, "learned stage: not prepared");
+  const GridOp G = grid_op(eb, shift);
+  k_st_resid<<<nb, 256, 0, s>>>(G, nn, eb.code, eb.diag, r, z, N.s64, N.spart);
+  k_st_norm<<<1, 32, 0, s>>>(N.spart, (int)nb, (double)eb.num_cp, eb.g.h * eb.g.h, N.scal);
+  k_st_input<<<nb, 256, 0, s>>>(nn, eb.code, N.s64, N.scal, N.in);
+  const Image im{eb.g.n0, eb.g.n1, eb.g.n1};
+  forward(N, im, N.in, N.out, s, nl);
+  k_st_correct<<<nb, 256, 0, s>>>(nn, eb.code, N.out, N.scal, z);
+  nl += 4;
+}
+
+}  // namespace ebk
+
+using namespace ebk;
+
+static int check_shape(int width, int height, int images) {
+  if (width < 1 || height < 1 || images < 1 || (int64_t)height * images >= ((int64_t)1 << 30)) {
+    set_error("nn: width, height and images must be >= 1 and height x images < 2^30");
+    return EB_ERR_INVALID;
+  }
+  return EB_OK;
+}
+
+extern "C" {
+
+int nn_create(nn_handle** out, cudaStream_t stream) {
+  if (!out) {
+    set_error("nn_create: NULL argument");
+    return EB_ERR_INVALID;
+  }
+  *out = nullptr;
+  nn_handle* h = new (std::nothrow) nn_handle();
+  if (!h) {
+    set_error("nn_create: host allocation failed");
+    return EB_ERR_OOM;
+  }
+  h->n.home = stream;
+  int st = guarded([&] {
+    NN& N = h->n;
+    set_attrs();
+    N.P = dalloc<float>(NPARAM, stream);
+    N.G = dalloc<float>(NPARAM, stream);
+    N.m = dalloc<float>(NPARAM, stream);
+    N.v = dalloc<float>(NPARAM, stream);
+    N.wf = dalloc<bf16>(NMID * WM_N, stream);
+    N.wb = dalloc<bf16>(NMID * WM_N, stream);
+    EB_CUDA(cudaStreamSynchronize(stream));
+  });
+  if (st != EB_OK) {
+    nn_destroy(h);
+    return st;
+  }
+  *out = h;
+  return EB_OK;
+}
+
+void nn_destroy(nn_handle* h) {
+  if (!h) return;
+  NN& N = h->n;
+  cudaStream_t s = N.home;
+  dfree(N.P, s); dfree(N.G, s); dfree(N.m, s); dfree(N.v, s); dfree(N.wf, s); dfree(N.wb, s);
+  for (int l = 1; l <= 5; ++l) dfree(N.act[l], s);
+  dfree(N.gA, s); dfree(N.gB, s); dfree(N.out, s); dfree(N.dout, s); dfree(N.in, s); dfree(N.code, s);
+  dfree(N.diag, s); dfree(N.part, s); dfree(N.lpart, s); dfree(N.cimg, s); dfree(N.loss, s);
+  dfree(N.s64, s); dfree(N.spart, s); dfree(N.scal, s);
+  cudaStreamSynchronize(s);
+  delete h;
+}
+
+int nn_num_params(void) { return NPARAM; }
+
+int nn_set_params(nn_handle* h, const float* params_host, cudaStream_t stream) {
+  if (!h || !params_host) {
+    set_error("nn_set_params: NULL argument");
+    return EB_ERR_INVALID;
+  }
+  return guarded([&] {
+    NN& N = h->n;
+    int64_t nl = 0;
+    EB_CUDA(cudaMemcpyAsync(N.P, params_host, sizeof(float) * NPARAM, cudaMemcpyHostToDevice, stream));
+    EB_CUDA(cudaMemsetAsync(N.m, 0, sizeof(float) * NPARAM, stream));
+    EB_CUDA(cudaMemsetAsync(N.v, 0, sizeof(float) * NPARAM, stream));
+    pack(N, stream, nl);
+    N.steps = 0;
+    EB_CUDA(cudaStreamSynchronize(stream));
+  });
+}
+
+int nn_get_params(const nn_handle* h, float* params_host, float* grad_host, cudaStream_t stream) {
+  if (!h) {
+    set_error("nn_get_params: NULL handle");
+    return EB_ERR_INVALID;
+  }
+  return guarded([&] {
+    const NN& N = h->n;
+    if (params_host)
+      EB_CUDA(cudaMemcpyAsync(params_host, N.P, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost, stream));
+    if (grad_host) EB_CUDA(cudaMemcpyAsync(grad_host, N.G, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost, stream));
+    EB_CUDA(cudaStreamSynchronize(stream));
+  });
+}
+
+int nn_forward(nn_handle* h, int width, int height, int images, const float* in_dev, float* out_dev,
+               cudaStream_t stream) {
+  if (!h || !in_dev || !out_dev) {
+    set_error("nn_forward: NULL argument");
+    return EB_ERR_INVALID;
+  }
+  if (int st = check_shape(width, height, images)) return st;
+  if (reinterpret_cast<uintptr_t>(in_dev) % 8) {
+    set_error("nn_forward: in must be 8-byte aligned");
+    return EB_ERR_INVALID;
+  }
+  return guarded([&] {
+    NN& N = h->n;
+    const Image im{width, height * images, height};
+    ensure_act(N, npx_of(im), stream);
+    int64_t nl = 0;
+    forward(N, im, reinterpret_cast<const float2*>(in_dev), out_dev, stream, nl);
+  });
+}
+
+int nn_backward(nn_handle* h, int width, int height, int images, const float* in_dev, const float* dout_dev,
+                cudaStream_t stream) {
+  if (!h || !in_dev || !dout_dev) {
+    set_error("nn_backward: NULL argument");
+    return EB_ERR_INVALID;
+  }
+  if (int st = check_shape(width, height, images)) return st;
+  if (reinterpret_cast<uintptr_t>(in_dev) % 8) {
+    set_error("nn_backward: in must be 8-byte aligned");
+    return EB_ERR_INVALID;
+  }
+  return guarded([&] {
+    NN& N = h->n;
+    const Image im{width, height * images, height};
+    ensure_act(N, npx_of(im), stream);
+    int64_t nl = 0;
+    const float2* in = reinterpret_cast<const float2*>(in_dev);
+    forward(N, im, in, N.out, stream, nl);
+    backward(N, im, in, dout_dev, stream, nl);
+  });
+}
+
+int nn_geometry(const eb_handle* eb, uint8_t* code_dev, float* diag_dev, cudaStream_t stream) {
+  if (!eb || !code_dev || !diag_dev) {
+    set_error("nn_geometry: NULL argument");
+    return EB_ERR_INVALID;
+  }
+  return guarded([&] {
+    const EBHandle& E = eb->h;
+    EB_CUDA(cudaMemcpyAsync(code_dev, E.code, (size_t)E.g.num_nodes, cudaMemcpyDeviceToDevice, stream));
+    EB_CUDA(cudaMemcpyAsync(diag_dev, E.diag32, sizeof(float) * E.g.num_nodes, cudaMemcpyDeviceToDevice, stream));
+  });
+}
+
+int nn_pairs(const amg_handle* amg, const double* b_dev, const double* xstar_dev, int count, float* s_hat_dev,
+             double* c_dev, double* e_hat_dev, cudaStream_t stream) {
+  if (!amg || !b_dev || !xstar_dev || !s_hat_dev || !c_dev || count < 0) {
+    set_error("nn_pairs: NULL argument or count < 0");
+    return EB_ERR_INVALID;
+  }
+  return guarded([&] {
+    Solver& S = const_cast<Solver&>(amg->s);
+    EB_REQUIRE(S.H != nullptr, EB_ERR_INVALID, "nn_pairs: handle has no hierarchy");
+    const EBHandle& eb = *S.eb;
+    const int64_t nn = eb.g.num_nodes;
+    const unsigned nb = grid_blocks(nn);
+    const GridOp G = grid_op(eb, S.shift);
+    double *x = nullptr, *r = nullptr, *z = nullptr, *e = nullptr, *t = nullptr, *part = nullptr, *scal = nullptr;
+    auto release = [&] {
+      dfree(x, stream); dfree(r, stream); dfree(z, stream); dfree(e, stream); dfree(t, stream);
+      dfree(part, stream); dfree(scal, stream);
+    };
+    try {
+      x = dalloc<double>(nn, stream);
+      r = dalloc<double>(nn, stream);
+      z = dalloc<double>(nn, stream);
+      e = dalloc<double>(nn, stream);
+      t = dalloc<double>(nn, stream);
+      part = dalloc<double>(2 * (int64_t)nb, stream);
+      scal = dalloc<double>(2, stream);
+      for (int k = 0; k < count; ++k) {
+        k_pr_resid<<<nb, 256, 0, stream>>>(G, nn, eb.code, eb.diag, b_dev, x, r);
+        amg_vcycle_grid(S, r, z, stream);
+        k_pr_update<<<nb, 256, 0, stream>>>(nn, eb.code, z, xstar_dev, x, e);
+        k_pr_unit<<<nb, 256, 0, stream>>>(G, eb.g.h * eb.g.h, nn, eb.code, eb.diag, e, t, part);
+        k_pr_norm<<<1, 32, 0, stream>>>(part, (int)nb, (double)eb.num_cp, scal, c_dev + k);
+        k_pr_write<<<nb, 256, 0, stream>>>(nn, t, e, scal, s_hat_dev + (int64_t)k * nn,
+                                           e_hat_dev ? e_hat_dev + (int64_t)k * nn : nullptr);
+        EB_CUDA(cudaGetLastError());
+      }
+      EB_CUDA(cudaStreamSynchronize(stream));
+    } catch (...) {
+      release();
+      throw;
+    }
+    release();
+  });
+}
+
+int nn_train_step(nn_handle* h, int width, int height, int batch, const float* s_hat_dev, const double* c_dev,
+                  const int32_t* geo_of_dev, const uint8_t* code_dev, const float* diag_dev, const int32_t* pick_dev,
+                  float lr, float* loss_dev, cudaStream_t stream) {
+  if (!h || !s_hat_dev || !c_dev || !geo_of_dev || !code_dev || !diag_dev || !pick_dev) {
+    set_error("nn_train_step: NULL argument");
+    return EB_ERR_INVALID;
+  }
+  if (int st = check_shape(width, height, batch)) return st;
+  if (!(lr > 0.0f)) {
+    set_error("nn_train_step: lr must be > 0");
+    return EB_ERR_INVALID;
+  }
+  return guarded([&] {
+    NN& N = h->n;
+    const Image im{width, height * batch, height};
+    const int64_t npx = npx_of(im);
+    ensure_act(N, npx, stream);
+    const int64_t per = (int64_t)width * height;
+    const int lnb = (int)((per + 255) / 256);
+    if ((int64_t)batch * lnb > N.cap_lpart) {
+      dfree(N.lpart, stream);
+      N.cap_lpart = 0;
+      N.lpart = dalloc<double>((int64_t)batch * lnb, stream, false);
+      N.cap_lpart = (int64_t)batch * lnb;
+    }
+    if (batch > N.cap_batch) {
+      dfree(N.cimg, stream);
+      dfree(N.loss, stream);
+      N.cap_batch = 0;
+      N.cimg = dalloc<double>(batch, stream);
+      N.loss = dalloc<float>(batch + 1, stream);
+      N.cap_batch = batch;
+    }
+    int64_t nl = 0;
+    k_gather<<<blocks_for(npx, 256), 256, 0, stream>>>(im, s_hat_dev, c_dev, geo_of_dev, code_dev, diag_dev,
+                                                       pick_dev, N.in, N.code, N.diag, N.cimg);
+    forward(N, im, N.in, N.out, stream, nl);
+    k_loss<<<dim3((unsigned)lnb, (unsigned)batch), 256, 0, stream>>>(im, N.code, N.diag, N.in, N.out, N.cimg,
+                                                                      1.0f / (float)batch, N.dout, N.lpart);
+    k_loss_reduce<<<1, 256, 0, stream>>>(N.lpart, lnb, batch, N.cimg, loss_dev ? loss_dev : N.loss);
+    backward(N, im, N.in, N.dout, stream, nl);
+    N.steps += 1;
+    const float c1 = (float)(1.0 - std::pow(0.9, (double)N.steps));
+    const float c2 = (float)(1.0 - std::pow(0.999, (double)N.steps));
+    k_adam<<<blocks_for(NPARAM, 256), 256, 0, stream>>>(NPARAM, N.P, N.G, N.m, N.v, lr, c1, c2);
+    pack(N, stream, nl);
+    EB_CUDA(cudaGetLastError());
+  });
+}
+
+int pcg_solve_nn(const amg_handle* amg, nn_handle* nn, const double* b_dev, double* x_dev, double rtol, int maxit,
+                 const pcg_opts* opts, pcg_stats* stats, cudaStream_t stream) {
+  if (!amg || !nn || !b_dev || !x_dev) {
+    set_error("pcg_solve_nn: NULL argument");
+    return EB_ERR_INVALID;
+  }
+  pcg_opts o{EB_PC_AMG_NN, 1, 1, 0};
+  if (opts) o = *opts;
+  o.precond = EB_PC_AMG_NN;
+  int rc = EB_OK;
+  int st = guarded([&] {
+    Solver& S = const_cast<Solver&>(amg->s);
+    EB_REQUIRE(S.H != nullptr, EB_ERR_INVALID, "pcg_solve_nn: handle has no hierarchy");
+    nn_stage_prepare(nn, *S.eb, stream);
+    if (!S.zold) S.zold = dalloc<double>(S.eb->g.num_nodes, stream);
+    S.nn = nn;
+    try {
+      rc = S.pcg(b_dev, x_dev, rtol, maxit, o, stats, stream);
+    } catch (...) {
+      S.nn = nullptr;
+      throw;
+    }
+    S.nn = nullptr;
+  });
+  return st != EB_OK ? st : rc;
+}
+
+}  // extern "C"

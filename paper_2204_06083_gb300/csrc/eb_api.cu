@@ -6,10 +6,6 @@
 #include <chrono>
 #include <cmath>
 
-struct amg_handle {
-  ebk::Solver s;
-};
-
 namespace ebk {
 static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }

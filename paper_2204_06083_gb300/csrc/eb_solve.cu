@@ -347,7 +347,11 @@ void Solver::finalize(int op, cudaStream_t s) {
 void Solver::precondition(int kind, const double* rin, double* zout, cudaStream_t s) {
   const int dim = eb->g.dim;
   const TileView tv = eb->tv();
-  if (kind == EB_PC_AMG && H) {
+  if (kind == EB_PC_AMG_NN) {
+    amg_vcycle_grid(*this, rin, zout, s);
+    nn_stage_apply(nn, *eb, shift, rin, zout, nlaunch, s);
+    EB_DIM_LAUNCH(dim, k_dot2, nblk, tv, rin, zout, zold, part);
+  } else if (kind == EB_PC_AMG && H) {
     amg_vcycle_grid(*this, rin, zout, s);
     if (flexible())
       EB_DIM_LAUNCH(dim, k_dot2, nblk, tv, rin, zout, zold, part);
@@ -367,8 +371,12 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
   const TileView tv = eb->tv();
   const OpParams op = op_params(*this);
   const int kind = o.precond;
-  EB_REQUIRE(kind == EB_PC_AMG || kind == EB_PC_JACOBI || kind == EB_PC_NONE, EB_ERR_INVALID, "bad preconditioner");
-  EB_REQUIRE(kind != EB_PC_AMG || H != nullptr, EB_ERR_INVALID, "AMG preconditioner requested without a hierarchy");
+  EB_REQUIRE(kind == EB_PC_AMG || kind == EB_PC_JACOBI || kind == EB_PC_NONE || kind == EB_PC_AMG_NN,
+             EB_ERR_INVALID, "bad preconditioner");
+  EB_REQUIRE(kind != EB_PC_AMG_NN || (nn != nullptr && zold != nullptr), EB_ERR_INVALID,
+             "the learned stage is selected by pcg_solve_nn");
+  EB_REQUIRE((kind != EB_PC_AMG && kind != EB_PC_AMG_NN) || H != nullptr, EB_ERR_INVALID,
+             "AMG preconditioner requested without a hierarchy");
   EB_REQUIRE(rtol > 0.0 && maxit >= 0, EB_ERR_INVALID, "rtol must be > 0 and maxit >= 0");
   EB_REQUIRE(b != x, EB_ERR_INVALID, "pcg: b and x must be different buffers");
   const int check = std::max(1, o.check_every);
@@ -406,7 +414,7 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
     }
     if (total_iters >= maxit) break;
     precondition(kind, r, z, s);
-    const bool flex = kind == EB_PC_AMG && flexible();
+    const bool flex = flex_for(kind);
     finalize(flex ? FIN_RZ0F : FIN_RZ0, s);
     EB_DIM_LAUNCH(dim, k_xpby, nblk, tv, sc, z, p, flex ? zold : nullptr, 1);
     int it = 0;
@@ -496,7 +504,7 @@ void Solver::iteration(int kind, const double* b, double* x, cudaStream_t s) {
   EB_DIM_LAUNCH(dim, k_update_xr, nblk, tv, sc, x, r, p, q, part);
   finalize(FIN_RR, s);
   precondition(kind, r, z, s);
-  const bool flex = kind == EB_PC_AMG && flexible();
+  const bool flex = flex_for(kind);
   finalize(flex ? FIN_BETAF : FIN_BETA, s);
   EB_DIM_LAUNCH(dim, k_xpby, nblk, tv, sc, z, p, flex ? zold : nullptr, 0);
 }
@@ -505,7 +513,8 @@ void Solver::iteration(int kind, const double* b, double* x, cudaStream_t s) {
 // capture runs on a private stream forked from s, so s may be the legacy
 // default stream.
 void Solver::graph_prepare(int kind, const double* b, double* x, int iters, bool profile, cudaStream_t s) {
-  if (gexec && g_b == b && g_x == x && g_iters == iters && g_kind == kind && g_prof == (int)profile) return;
+  if (gexec && g_b == b && g_x == x && g_iters == iters && g_kind == kind && g_prof == (int)profile && g_nn == nn)
+    return;
   if (prof_on) {  // settle event pairs recorded so far before the capture reuses them
     EB_CUDA(cudaStreamSynchronize(s));
     prof_collect(g_pairs, prof_n - g_pairs);
@@ -535,6 +544,7 @@ void Solver::graph_prepare(int kind, const double* b, double* x, int iters, bool
   g_iters = iters;
   g_kind = kind;
   g_prof = (int)profile;
+  g_nn = nn;
 }
 
 void Solver::graph_release() {

@@ -29,6 +29,9 @@ struct Solver {
   double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *tmp = nullptr;
   double* zold = nullptr;  // previous z (flexible CG with a reduced-precision V-cycle)
   bool flexible() const { return H != nullptr && opts.vcycle_prec == EB_F32; }
+  // the flexible (Polak-Ribiere) beta: reduced-precision V-cycle or learned stage
+  bool flex_for(int kind) const { return kind == EB_PC_AMG_NN || (kind == EB_PC_AMG && flexible()); }
+  nn_handle* nn = nullptr;  // learned stage of EB_PC_AMG_NN (set for one solve)
   double* part = nullptr;
   int nblk = 1;
   PcgScalars* sc = nullptr;
@@ -45,6 +48,7 @@ struct Solver {
   cudaGraphExec_t gexec = nullptr;
   const double* g_b = nullptr;
   double* g_x = nullptr;
+  const nn_handle* g_nn = nullptr;
   int g_iters = 0, g_kind = -1, g_prof = -1, g_pairs = 0;
   int64_t g_launches = 0;
 
@@ -72,4 +76,15 @@ void amg_vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s);
 void amg_fill_info(const Solver& S, amg_info_t* out);
 void amg_copy_level(const Solver& S, int level, int which, int32_t* rowptr, int32_t* col, double* val, cudaStream_t s);
 
+// learned stage (cnn.cu): buffers for grids of eb's size (before any capture),
+// then z <- z + h^2 rms(s) N(s / rms(s), m), s = r - (shift I + A) z
+void nn_stage_prepare(nn_handle* nn, const EBHandle& eb, cudaStream_t s);
+void nn_stage_apply(nn_handle* nn, const EBHandle& eb, double shift, const double* r, double* z, int64_t& nlaunch,
+                    cudaStream_t s);
+
 }  // namespace ebk
+
+// the opaque AMG / solver handle of the C ABI
+struct amg_handle {
+  ebk::Solver s;
+};

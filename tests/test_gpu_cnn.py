@@ -1,0 +1,285 @@
+"""GPU parity of the learned preconditioner stage against the oracle (P11).
+
+* forward: BF16 activations, FP32 sums vs the FP64 oracle: rel-L2 <= 2e-2;
+  vs the oracle rounding the same stored values to bf16: rel-L2 <= 4e-3
+  (what remains is FP32 vs FP64 summation flipping a bf16 rounding).
+* a one-tap shift network: exact up to FP32 rounding of the final bias add,
+  across a ragged row segment and stacked images.
+* backward: per-layer gradient rel-L2 <= 2e-2 vs the oracle storing the same
+  values in bf16.  Against the FP64 oracle the gradients differ by ~10 %
+  (<= 0.2 asserted): the weight gradients are sums over pixels with heavy
+  cancellation, and bf16 storage of the activations alone moves them that much
+  (the oracle's own bf16 mode shows the same difference from its FP64 mode).
+* training pairs from the device V-cycle iteration vs the oracle's (same b and
+  x*): s_hat (stored in float) within 1e-6 of its maximum, e_hat and c within
+  1e-7 (the two V-cycles agree to ~1e-12; e_k shrinks by the V-cycle's
+  convergence factor per iteration while that difference does not).
+* one training step: per-pair losses within 2e-2 of the oracle's, and Adam's
+  first step -lr g / (|g| + eps) reproduced wherever the oracle gradient is not
+  tiny.
+* flexible PCG with the stage converges to the oracle's solution; with a zero
+  network it takes exactly the iterations of plain AMG-PCG.
+"""
+import numpy as np
+import pytest
+import torch
+
+import eb_inputs as ei
+from oracle import amg as oamg
+from oracle import cnn as ocnn
+from oracle import eb as oeb
+from oracle import solvers as osol
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import __graft_entry__ as ge
+    ge.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+
+
+def _pkg():
+    import paper_2204_06083_gb300 as eb
+    return eb
+
+
+def _params(seed, bias=0.05, scale=1.0):
+    rng = np.random.default_rng(seed + 1000)
+    layers = [(W * scale, rng.uniform(-bias, bias, size=b.shape)) for W, b in ocnn.unpack(ocnn.init_params(seed))]
+    return ocnn.pack(layers)
+
+
+def _inputs(seed, nimg, H, W):
+    rng = np.random.default_rng(seed)
+    s = rng.standard_normal((nimg, H, W))
+    m = (rng.random((nimg, H, W)) < 0.6).astype(np.float64)
+    return s, m
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("shape", [(3, 37, 200), (1, 16, 64), (2, 9, 129)])
+def test_forward_parity(shape):
+    eb = _pkg()
+    nimg, H, W = shape
+    theta = _params(1)
+    s, m = _inputs(2, nimg, H, W)
+    # the device input is float: give the oracle the same rounded values
+    s = s.astype(np.float32).astype(np.float64)
+    net = eb.Net(theta)
+    theta32 = theta.astype(np.float32).astype(np.float64)
+    inp = torch.from_numpy(np.stack([s, m], axis=-1).astype(np.float32)).cuda()
+    out = net.forward(inp).cpu().numpy().astype(np.float64)
+    for k in range(nimg):
+        ref, _ = ocnn.forward(theta32, s[k], m[k])
+        refb, _ = ocnn.forward(theta32, s[k], m[k], storage="bf16")
+        assert np.all(out[k][m[k] == 0] == 0)
+        assert _rel(out[k], ref) <= 2e-2, _rel(out[k], ref)
+        assert _rel(out[k], refb) <= 4e-3, _rel(out[k], refb)
+
+
+def test_shift_network_exact():
+    eb = _pkg()
+    nimg, H, W = 2, 11, 150
+    s, m = _inputs(3, nimg, H, W)
+    s = s.astype(np.float32).astype(np.float64)
+    taps = [5, 7, 5, 4, 8, 5]
+    layers = []
+    for (ci, co), d in zip(ocnn.LAYER_IO, taps):
+        Wl = np.zeros((co, 9, ci))
+        Wl[0, d, 0] = 1.0
+        layers.append((Wl, np.zeros(co)))
+    layers[5] = (layers[5][0], np.array([0.25]))
+    theta = ocnn.pack(layers)
+    net = eb.Net(theta)
+    inp = torch.from_numpy(np.stack([s, m], axis=-1).astype(np.float32)).cuda()
+    out = net.forward(inp).cpu().numpy().astype(np.float64)
+    for k in range(nimg):
+        ref, _ = ocnn.forward(theta, s[k], m[k], storage="bf16")
+        assert np.allclose(out[k], ref, rtol=1e-7, atol=1e-7)
+
+
+def test_backward_parity():
+    eb = _pkg()
+    nimg, H, W = 2, 40, 170
+    theta = _params(4)
+    theta32 = theta.astype(np.float32).astype(np.float64)
+    s, m = _inputs(5, nimg, H, W)
+    s = s.astype(np.float32).astype(np.float64)
+    dout = np.random.default_rng(6).standard_normal((nimg, H, W)).astype(np.float32)
+    net = eb.Net(theta)
+    inp = torch.from_numpy(np.stack([s, m], axis=-1).astype(np.float32)).cuda()
+    net.backward(inp, torch.from_numpy(dout).cuda())
+    _, g = net.params()
+    ref = np.zeros(ocnn.NPARAM)
+    refb = np.zeros(ocnn.NPARAM)
+    for k in range(nimg):
+        _, cache = ocnn.forward(theta32, s[k], m[k])
+        ref += ocnn.backward(theta32, cache, dout[k].astype(np.float64))
+        _, cache = ocnn.forward(theta32, s[k], m[k], storage="bf16")
+        refb += ocnn.backward(theta32, cache, dout[k].astype(np.float64))
+    offs = np.cumsum([0] + [w + b for w, b in ocnn.layer_sizes()])
+    g = g.astype(np.float64)
+    errs = [_rel(g[offs[l]:offs[l + 1]], ref[offs[l]:offs[l + 1]]) for l in range(6)]
+    errsb = [_rel(g[offs[l]:offs[l + 1]], refb[offs[l]:offs[l + 1]]) for l in range(6)]
+    assert max(errsb) <= 2e-2, errsb
+    assert max(errs) <= 0.2, errs
+
+
+def _geometry(n, seed):
+    return ei.box_grid(2, n), ei.random_star(seed)
+
+
+def _oracle_pairs(grid, ls, b_seed, count):
+    ref = oeb.build(grid, ls)
+    H = oamg.setup(ref.A)
+    b = np.random.default_rng(b_seed).standard_normal(ref.num_cp)
+    x_star = osol.dense_cholesky_solve(ref.A, b) if ref.num_cp <= 3000 else \
+        osol.pcg(ref.A, b, M=lambda r: oamg.vcycle(H, r), rtol=1e-14, maxit=500)[0]
+    S, E, Cs = ocnn.pairs(ref, ref.A, H, b, x_star, count)
+    return ref, b, x_star, S, E, Cs
+
+
+def _device_pairs(grid, ls, ref, b, x_star, count):
+    eb = _pkg()
+    h = eb.EB(grid, ls)
+    amg = eb.AMG(h)
+    bg = torch.from_numpy(ref.to_grid(b)).cuda()
+    xg = torch.from_numpy(ref.to_grid(x_star)).cuda()
+    nn = h.info.num_nodes
+    S = torch.zeros((count, nn), dtype=torch.float32, device="cuda")
+    Cv = torch.zeros(count, dtype=torch.float64, device="cuda")
+    E = torch.zeros((count, nn), dtype=torch.float64, device="cuda")
+    eb.nn_pairs(amg, bg, xg, count, S, Cv, E)
+    return h, amg, S, Cv, E
+
+
+def test_pairs_parity():
+    grid, ls = _geometry(96, 21)
+    ref, b, x_star, S, E, Cs = _oracle_pairs(grid, ls, 22, 4)
+    h, amg, Sd, Cd, Ed = _device_pairs(grid, ls, ref, b, x_star, 4)
+    assert amg.num_levels >= 2
+    for k in range(4):
+        sd = Sd[k].cpu().numpy().astype(np.float64)
+        ed = Ed[k].cpu().numpy()
+        assert np.abs(sd - S[k].reshape(-1)).max() <= 1e-6 * np.abs(S[k]).max()
+        assert np.abs(ed - E[k].reshape(-1)).max() <= 1e-7 * np.abs(E[k]).max()
+        assert abs(Cd[k].item() - Cs[k]) <= 1e-7 * Cs[k]
+
+
+def test_train_step_loss_and_adam():
+    eb = _pkg()
+    n, count = 96, 3      # > 1024 CPs: a multi-level hierarchy (V is not exact)
+    geos = [_geometry(n, 31), _geometry(n, 32)]
+    store_s, store_c, geo_of, codes, diags, oracle_pairs = [], [], [], [], [], []
+    handles = []
+    for gi, (grid, ls) in enumerate(geos):
+        ref, b, x_star, S, E, Cs = _oracle_pairs(grid, ls, 40 + gi, count)
+        h, amg, Sd, Cd, Ed = _device_pairs(grid, ls, ref, b, x_star, count)
+        handles.append((h, amg))
+        code = torch.empty(h.info.num_nodes, dtype=torch.uint8, device="cuda")
+        diag = torch.empty(h.info.num_nodes, dtype=torch.float32, device="cuda")
+        eb.nn_geometry(h, code, diag)
+        codes.append(code)
+        diags.append(diag)
+        for k in range(count):
+            store_s.append(Sd[k])
+            store_c.append(Cd[k])
+            geo_of.append(gi)
+            oracle_pairs.append((ref, S[k], Cs[k]))
+    s_store = torch.stack(store_s).view(-1, n, n)
+    c_store = torch.stack(store_c)
+    geo = torch.tensor(geo_of, dtype=torch.int32, device="cuda")
+    code = torch.stack(codes).view(-1, n, n)
+    diag = torch.stack(diags).view(-1, n, n)
+    pick_l = [0, 4, 2, 5]
+    pick = torch.tensor(pick_l, dtype=torch.int32, device="cuda")
+    theta = _params(7, scale=0.3)
+    net = eb.Net(theta)
+    loss = torch.zeros(len(pick_l) + 1, dtype=torch.float32, device="cuda")
+    lr = 1e-3
+    net.train_step(s_store, c_store, geo, code, diag, pick, lr, loss)
+    p1, _ = net.params()
+    lossd = loss.cpu().numpy()
+    theta32 = theta.astype(np.float32).astype(np.float64)
+    g = np.zeros(ocnn.NPARAM)
+    Ls = []
+    for j in pick_l:
+        ref, s_hat, c = oracle_pairs[j]
+        mask = ocnn.cp_mask(ref)
+        o, cache = ocnn.forward(theta32, s_hat, mask)
+        L, dL = ocnn.loss(ref, o, s_hat, c)
+        Ls.append(L)
+        g += ocnn.backward(theta32, cache, dL) / len(pick_l)
+    for j in range(len(pick_l)):
+        assert abs(lossd[j] - Ls[j]) <= 2e-2 * max(1.0, abs(Ls[j])), (lossd, Ls)
+    assert abs(lossd[-1] - np.mean(Ls)) <= 2e-2 * max(1.0, abs(np.mean(Ls)))
+    t1, _, _ = ocnn.adam(theta32, g, np.zeros_like(g), np.zeros_like(g), 1, lr)
+    big = np.abs(g) > 1e-2 * np.abs(g).max()
+    close = np.abs(p1.astype(np.float64) - t1) <= 1e-2 * lr + 1e-6 * np.abs(theta32)
+    assert close[big].mean() >= 0.98, close[big].mean()
+    # every parameter moved by at most lr (first Adam step)
+    assert np.abs(p1.astype(np.float64) - theta32).max() <= lr * (1 + 1e-3)
+
+
+def test_fpcg_stage_converges_to_oracle_solution():
+    eb = _pkg()
+    grid, ls = _geometry(128, 51)
+    ref = oeb.build(grid, ls)
+    b = np.random.default_rng(52).standard_normal(ref.num_cp)
+    xd = osol.dense_cholesky_solve(ref.A, b) if ref.num_cp <= 4000 else None
+    if xd is None:
+        Ho = oamg.setup(ref.A)
+        xd = osol.pcg(ref.A, b, M=lambda r: oamg.vcycle(Ho, r), rtol=1e-14, maxit=500)[0]
+    h = eb.EB(grid, ls)
+    amg = eb.AMG(h)
+    bg = torch.from_numpy(ref.to_grid(b)).cuda()
+    x0, st0 = amg.solve(bg, rtol=1e-10)
+    zero = eb.Net(np.zeros(ocnn.NPARAM))
+    xz, stz = eb.solve_nn(amg, zero, bg, rtol=1e-10)
+    assert stz.iterations == st0.iterations
+    net = eb.Net(_params(53, scale=0.1))
+    x1, st1 = eb.solve_nn(amg, net, bg, rtol=1e-12, maxit=300)
+    assert st1.converged and st1.true_rel_residual <= 1e-12
+    xs = ref.from_grid(x1.cpu().numpy())
+    assert np.linalg.norm(xs - xd) <= 1e-9 * np.linalg.norm(xd)
+    # graph-captured and direct iterations agree
+    x2, st2 = eb.solve_nn(amg, net, bg, rtol=1e-12, maxit=300, use_graph=0)
+    assert st2.iterations == st1.iterations
+    assert torch.equal(x1, x2)
+
+
+def test_rejects_learned_kind_in_plain_solve():
+    eb = _pkg()
+    grid, ls = _geometry(64, 61)
+    h = eb.EB(grid, ls)
+    amg = eb.AMG(h)
+    b = torch.ones(h.shape(), dtype=torch.float64, device="cuda")
+    with pytest.raises(eb.EBError) as e:
+        amg.solve(b, precond=eb.EB_PC_AMG_NN)
+    assert e.value.code == eb.EB_ERR_INVALID
+
+
+def test_training_lowers_loss_and_reports_gain():
+    """Trains on solver pairs of 16 random stars at 128^2 and reports what the
+    trained stage gains on a held-out star (iterations to 1e-10)."""
+    from paper_2204_06083_gb300 import learned
+    eb = _pkg()
+    n = 128
+    geos = [(ei.box_grid(2, n), ei.random_star(100 + i)) for i in range(16)]
+    store = learned.make_pairs(geos, 6, seed=5)
+    net = eb.Net(learned.init_params(8))
+    log = learned.train(net, store, steps=300, batch=8, lr=1e-3, seed=9, log_every=25)
+    grid, ls = ei.box_grid(2, n), ei.random_star(999)
+    h = eb.EB(grid, ls)
+    amg = eb.AMG(h)
+    b = torch.from_numpy(np.random.default_rng(3).standard_normal(h.shape())).cuda()
+    x0, st0 = amg.solve(b, rtol=1e-10)
+    x1, st1 = eb.solve_nn(amg, net, b, rtol=1e-10)
+    print(f"loss {log[0][1]:.4f} -> {log[-1][1]:.4f}; iterations plain {st0.iterations}, with stage {st1.iterations}")
+    assert log[-1][1] < 0.8 * log[0][1]
+    assert st1.converged and torch.linalg.norm(x1 - x0) <= 1e-8 * torch.linalg.norm(x0)
