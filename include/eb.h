@@ -334,11 +334,22 @@ int nn_geometry(const eb_handle* eb, uint8_t* code_dev, float* diag_dev, cudaStr
 int nn_train_step(nn_handle* nn, int width, int height, int batch, const float* s_hat_dev, const double* c_dev,
                   const int32_t* geo_of_dev, const uint8_t* code_dev, const float* diag_dev, const int32_t* pick_dev,
                   float lr, float* loss_dev, cudaStream_t stream);
+/* Step length of the stage: EB_NN_PLAIN uses z1 + h^2 rms(s) N (as above);
+ * EB_NN_ENERGY multiplies the correction by omega = (o's_hat) / (o'A~o),
+ * o = N(s_hat, m), A~ = h^2 (shift I + A): the step along o that minimises the
+ * energy norm of the error left after z1, so that the stage never increases
+ * it (omega = 1 for a network returning A~^-1 s_hat exactly; omega = 0 when
+ * o'A~o <= 0). */
+typedef enum { EB_NN_PLAIN = 0, EB_NN_ENERGY = 1 } eb_nn_mode;
+/* One application of the preconditioner with the stage: z = V(r) followed by
+ * the stage of the given mode (full-grid device vectors, r != z). */
+int nn_precondition(const amg_handle* amg, nn_handle* nn, int mode, const double* r_dev, double* z_dev,
+                    cudaStream_t stream);
 /* pcg_solve with the preconditioner V-cycle + learned stage (above), flexible
  * (Polak-Ribiere) beta.  2D grids; amg must hold a hierarchy.  opts->precond
  * is ignored. */
-int pcg_solve_nn(const amg_handle* amg, nn_handle* nn, const double* b_dev, double* x_dev, double rtol, int maxit,
-                 const pcg_opts* opts, pcg_stats* stats, cudaStream_t stream);
+int pcg_solve_nn(const amg_handle* amg, nn_handle* nn, int mode, const double* b_dev, double* x_dev, double rtol,
+                 int maxit, const pcg_opts* opts, pcg_stats* stats, cudaStream_t stream);
 
 /* The leapfrog step of wave_step for callers that must not allocate device
  * memory during the call.  The paper has no counterpart: this is a service of

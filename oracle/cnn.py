@@ -35,7 +35,9 @@ Loss (relative energy norm of the error of the correction):
 A batch loss is the mean of L over its images.
 
 Preconditioner stage (flexible PCG): z1 = V(r); s = r - A z1;
-    z = z1 + h^2 rms(s) N(s / rms(s), m).
+    z = z1 + omega h^2 rms(s) N(s / rms(s), m)
+with omega = 1 (mode "plain") or the energy-optimal step of stage() (mode
+"energy").
 
 Adam (Kingma & Ba, 2015) with beta1 = 0.9, beta2 = 0.999, eps = 1e-8 and the
 bias corrections 1 - beta^t.
@@ -234,15 +236,28 @@ def adam(theta, g, m, v, t: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8):
     return theta - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
-def stage(eb: ebm.EBSystem, A: sp.csr_matrix, H: amg_mod.Hierarchy, theta: np.ndarray, r: np.ndarray):
-    """Preconditioner with the learned stage on a CP vector r (header)."""
+def stage(eb: ebm.EBSystem, A: sp.csr_matrix, H: amg_mod.Hierarchy, theta: np.ndarray, r: np.ndarray,
+          mode: str = "plain"):
+    """Preconditioner with the learned stage on a CP vector r (header).
+
+    mode "energy" scales the correction by omega = (o's_hat) / (o'A~o) with
+    A~ = h^2 A (shift included): the step along o that minimises the energy
+    norm of the remaining error A^-1 s - step, so the stage never increases
+    it; a network returning exactly A~^-1 s_hat gives omega = 1."""
     z1 = amg_mod.vcycle(H, r)
     s = r - A @ z1
     rms = np.sqrt(np.mean(s * s))
     if rms == 0.0:
         return z1
-    o, _ = forward(theta, eb.to_grid(s / rms), cp_mask(eb))
-    return z1 + eb.grid.h ** 2 * rms * eb.from_grid(o)
+    sh = s / rms
+    o, _ = forward(theta, eb.to_grid(sh), cp_mask(eb))
+    ov = eb.from_grid(o)
+    h2 = eb.grid.h ** 2
+    omega = 1.0
+    if mode == "energy":
+        den = ov @ (h2 * (A @ ov))
+        omega = (ov @ sh) / den if den > 0.0 else 0.0
+    return z1 + h2 * rms * omega * ov
 
 
 def fpcg(A: sp.csr_matrix, b: np.ndarray, M, rtol=1e-10, maxit=500):

@@ -21,6 +21,7 @@ EB_OK, EB_ERR_INVALID, EB_ERR_GEOMETRY, EB_ERR_CUDA, EB_ERR_NONFINITE = 0, 1, 2,
 EB_ERR_NO_CONVERGENCE, EB_ERR_BREAKDOWN, EB_ERR_TIMEOUT, EB_ERR_OOM, EB_ERR_NOT_IMPLEMENTED = 5, 6, 7, 8, 9
 EB_F64, EB_F32, EB_BF16 = 0, 1, 2
 EB_PC_AMG, EB_PC_JACOBI, EB_PC_NONE, EB_PC_AMG_NN = 0, 1, 2, 3
+EB_NN_PLAIN, EB_NN_ENERGY = 0, 1
 STAR_MAX = 16
 
 CODE_BP = 0x40
@@ -106,8 +107,9 @@ _SIGS = {
     "nn_pairs": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, _P, _P]),
     "nn_geometry": (C.c_int, [_P, _P, _P, _P]),
     "nn_train_step": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P, _P, C.c_float, _P, _P]),
-    "pcg_solve_nn": (C.c_int, [_P, _P, _P, _P, C.c_double, C.c_int, C.POINTER(pcg_opts), C.POINTER(pcg_stats),
-                               _P]),
+    "nn_precondition": (C.c_int, [_P, _P, C.c_int, _P, _P, _P]),
+    "pcg_solve_nn": (C.c_int, [_P, _P, C.c_int, _P, _P, C.c_double, C.c_int, C.POINTER(pcg_opts),
+                               C.POINTER(pcg_stats), _P]),
     "eb_last_error": (C.c_char_p, []),
 }
 
@@ -540,15 +542,24 @@ def nn_pairs(amg: AMG, b, x_star, count, s_out, c_out, e_out=None, stream=None):
                            _stream(stream)))
 
 
-def solve_nn(amg: AMG, net: Net, b, x=None, rtol=1e-10, maxit=1000, check_every=1, use_graph=1, stream=None,
-             allow_noconv=False):
+def precondition_nn(amg: AMG, net: Net, r, out=None, mode=EB_NN_PLAIN, stream=None):
+    """z = V(r) followed by the learned stage (nn_precondition)."""
+    import torch
+    if out is None:
+        out = torch.zeros_like(r)
+    _check(load().nn_precondition(amg._h, net.handle, int(mode), _ptr(r), _ptr(out), _stream(stream)))
+    return out
+
+
+def solve_nn(amg: AMG, net: Net, b, x=None, rtol=1e-10, maxit=1000, mode=EB_NN_PLAIN, check_every=1, use_graph=1,
+             stream=None, allow_noconv=False):
     """Flexible PCG with the V-cycle followed by the learned stage (pcg_solve_nn)."""
     import torch
     if x is None:
         x = torch.zeros_like(b)
     o = pcg_opts(EB_PC_AMG_NN, check_every, use_graph, 0)
     st = pcg_stats()
-    _check(load().pcg_solve_nn(amg._h, net.handle, _ptr(b), _ptr(x), float(rtol), int(maxit), C.byref(o),
+    _check(load().pcg_solve_nn(amg._h, net.handle, int(mode), _ptr(b), _ptr(x), float(rtol), int(maxit), C.byref(o),
                                C.byref(st), _stream(stream)), allow=(EB_ERR_NO_CONVERGENCE,) if allow_noconv else ())
     return x, st
 

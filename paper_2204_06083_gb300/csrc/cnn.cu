@@ -513,12 +513,12 @@ struct GridOp {
   double inv_h2, sigma;
 };
 
-__device__ __forceinline__ double op_at(const GridOp& G, const uint8_t c, const double* diag, const double* x,
-                                        int64_t p) {
+template <class T>
+__device__ __forceinline__ double op_at(const GridOp& G, const uint8_t c, const double* diag, const T* x, int64_t p) {
   double sum = 0.0;
   for (int s = 0; s < 2 * G.dim; ++s)
-    if (!(c & (1u << s))) sum += x[p + ((s & 1) ? G.st[s >> 1] : -G.st[s >> 1])];
-  return (G.sigma + diag[p] * G.inv_h2) * x[p] - sum * G.inv_h2;
+    if (!(c & (1u << s))) sum += (double)x[p + ((s & 1) ? G.st[s >> 1] : -G.st[s >> 1])];
+  return (G.sigma + diag[p] * G.inv_h2) * (double)x[p] - sum * G.inv_h2;
 }
 
 // per-CTA sums of a and b into out2[0..1] (blockDim.x = 256)
@@ -644,6 +644,33 @@ __global__ void k_st_input(int64_t nn, const uint8_t* __restrict__ code, const d
     const bool cp = (code[p] & CODE_CP) != 0;
     in[p] = make_float2(cp ? (float)(s[p] * inv) : 0.0f, cp ? 1.0f : 0.0f);
   }
+}
+
+// energy-optimal step: per-CTA sums of o's_hat and o'A~o, A~ = h^2 (sigma I + A)
+__global__ void __launch_bounds__(256) k_st_energy(GridOp G, double h2, int64_t nn, const uint8_t* __restrict__ code,
+                                                   const double* __restrict__ diag, const float2* __restrict__ in,
+                                                   const float* __restrict__ o, double* __restrict__ part) {
+  double a = 0.0, b = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nn; p += (int64_t)gridDim.x * blockDim.x) {
+    const uint8_t c = code[p];
+    if (c & CODE_CP) {
+      const double ov = (double)o[p];
+      a += ov * (double)in[p].x;
+      b += ov * h2 * op_at(G, c, diag, o, p);
+    }
+  }
+  block_sum2(a, b, part + 2 * blockIdx.x);
+}
+
+// scal[1] *= omega = (o's_hat) / (o'A~o), 0 when o'A~o <= 0
+__global__ void k_st_omega(const double* __restrict__ part, int nblk, double* __restrict__ scal) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double a = 0.0, b = 0.0;
+  for (int i = 0; i < nblk; ++i) {
+    a += part[2 * i];
+    b += part[2 * i + 1];
+  }
+  scal[1] *= b > 0.0 ? a / b : 0.0;
 }
 
 __global__ void k_st_correct(int64_t nn, const uint8_t* __restrict__ code, const float* __restrict__ o,
@@ -828,9 +855,10 @@ void nn_stage_prepare(nn_handle* h, const EBHandle& eb, cudaStream_t s) {
   if (!N.scal) N.scal = dalloc<double>(2, s);
 }
 
-// z = z1 + h^2 rms(s) N(s / rms(s), m) with s = r - (sigma I + A) z1 and z1 = z on entry
-void nn_stage_apply(nn_handle* h, const EBHandle& eb, double shift, const double* r, double* z, int64_t& nl,
-                    cudaStream_t s) {
+// z = z1 + omega h^2 rms(s) N(s / rms(s), m) with s = r - (sigma I + A) z1 and z1 = z on
+// entry; omega = 1 (EB_NN_PLAIN) or the energy-optimal step (EB_NN_ENERGY)
+void nn_stage_apply(nn_handle* h, const EBHandle& eb, double shift, int mode, const double* r, double* z,
+                    int64_t& nl, cudaStream_t s) {
   NN& N = h->n;
   const int64_t nn = eb.g.num_nodes;
   const unsigned nb = grid_blocks(nn);
@@ -841,6 +869,11 @@ void nn_stage_apply(nn_handle* h, const EBHandle& eb, double shift, const double
   k_st_input<<<nb, 256, 0, s>>>(nn, eb.code, N.s64, N.scal, N.in);
   const Image im{eb.g.n0, eb.g.n1, eb.g.n1};
   forward(N, im, N.in, N.out, s, nl);
+  if (mode == EB_NN_ENERGY) {
+    k_st_energy<<<nb, 256, 0, s>>>(G, eb.g.h * eb.g.h, nn, eb.code, eb.diag, N.in, N.out, N.spart);
+    k_st_omega<<<1, 32, 0, s>>>(N.spart, (int)nb, N.scal);
+    nl += 2;
+  }
   k_st_correct<<<nb, 256, 0, s>>>(nn, eb.code, N.out, N.scal, z);
   nl += 4;
 }
@@ -1085,10 +1118,35 @@ int nn_train_step(nn_handle* h, int width, int height, int batch, const float* s
   });
 }
 
-int pcg_solve_nn(const amg_handle* amg, nn_handle* nn, const double* b_dev, double* x_dev, double rtol, int maxit,
-                 const pcg_opts* opts, pcg_stats* stats, cudaStream_t stream) {
+int nn_precondition(const amg_handle* amg, nn_handle* nn, int mode, const double* r_dev, double* z_dev,
+                    cudaStream_t stream) {
+  if (!amg || !nn || !r_dev || !z_dev) {
+    set_error("nn_precondition: NULL argument");
+    return EB_ERR_INVALID;
+  }
+  if (mode != EB_NN_PLAIN && mode != EB_NN_ENERGY) {
+    set_error("nn_precondition: mode must be EB_NN_PLAIN or EB_NN_ENERGY");
+    return EB_ERR_INVALID;
+  }
+  return guarded([&] {
+    Solver& S = const_cast<Solver&>(amg->s);
+    EB_REQUIRE(S.H != nullptr, EB_ERR_INVALID, "nn_precondition: handle has no hierarchy");
+    nn_stage_prepare(nn, *S.eb, stream);
+    int64_t nl = 0;
+    amg_vcycle_grid(S, r_dev, z_dev, stream);
+    nn_stage_apply(nn, *S.eb, S.shift, mode, r_dev, z_dev, nl, stream);
+    EB_CUDA(cudaGetLastError());
+  });
+}
+
+int pcg_solve_nn(const amg_handle* amg, nn_handle* nn, int mode, const double* b_dev, double* x_dev, double rtol,
+                 int maxit, const pcg_opts* opts, pcg_stats* stats, cudaStream_t stream) {
   if (!amg || !nn || !b_dev || !x_dev) {
     set_error("pcg_solve_nn: NULL argument");
+    return EB_ERR_INVALID;
+  }
+  if (mode != EB_NN_PLAIN && mode != EB_NN_ENERGY) {
+    set_error("pcg_solve_nn: mode must be EB_NN_PLAIN or EB_NN_ENERGY");
     return EB_ERR_INVALID;
   }
   pcg_opts o{EB_PC_AMG_NN, 1, 1, 0};
@@ -1101,6 +1159,7 @@ int pcg_solve_nn(const amg_handle* amg, nn_handle* nn, const double* b_dev, doub
     nn_stage_prepare(nn, *S.eb, stream);
     if (!S.zold) S.zold = dalloc<double>(S.eb->g.num_nodes, stream);
     S.nn = nn;
+    S.nn_mode = mode;
     try {
       rc = S.pcg(b_dev, x_dev, rtol, maxit, o, stats, stream);
     } catch (...) {

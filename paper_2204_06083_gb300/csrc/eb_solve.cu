@@ -349,7 +349,7 @@ void Solver::precondition(int kind, const double* rin, double* zout, cudaStream_
   const TileView tv = eb->tv();
   if (kind == EB_PC_AMG_NN) {
     amg_vcycle_grid(*this, rin, zout, s);
-    nn_stage_apply(nn, *eb, shift, rin, zout, nlaunch, s);
+    nn_stage_apply(nn, *eb, shift, nn_mode, rin, zout, nlaunch, s);
     EB_DIM_LAUNCH(dim, k_dot2, nblk, tv, rin, zout, zold, part);
   } else if (kind == EB_PC_AMG && H) {
     amg_vcycle_grid(*this, rin, zout, s);
@@ -513,7 +513,8 @@ void Solver::iteration(int kind, const double* b, double* x, cudaStream_t s) {
 // capture runs on a private stream forked from s, so s may be the legacy
 // default stream.
 void Solver::graph_prepare(int kind, const double* b, double* x, int iters, bool profile, cudaStream_t s) {
-  if (gexec && g_b == b && g_x == x && g_iters == iters && g_kind == kind && g_prof == (int)profile && g_nn == nn)
+  if (gexec && g_b == b && g_x == x && g_iters == iters && g_kind == kind && g_prof == (int)profile && g_nn == nn &&
+      g_nn_mode == nn_mode)
     return;
   if (prof_on) {  // settle event pairs recorded so far before the capture reuses them
     EB_CUDA(cudaStreamSynchronize(s));
@@ -545,6 +546,7 @@ void Solver::graph_prepare(int kind, const double* b, double* x, int iters, bool
   g_kind = kind;
   g_prof = (int)profile;
   g_nn = nn;
+  g_nn_mode = nn_mode;
 }
 
 void Solver::graph_release() {

@@ -32,6 +32,7 @@ struct Solver {
   // the flexible (Polak-Ribiere) beta: reduced-precision V-cycle or learned stage
   bool flex_for(int kind) const { return kind == EB_PC_AMG_NN || (kind == EB_PC_AMG && flexible()); }
   nn_handle* nn = nullptr;  // learned stage of EB_PC_AMG_NN (set for one solve)
+  int nn_mode = 0;          // eb_nn_mode of that stage
   double* part = nullptr;
   int nblk = 1;
   PcgScalars* sc = nullptr;
@@ -49,6 +50,7 @@ struct Solver {
   const double* g_b = nullptr;
   double* g_x = nullptr;
   const nn_handle* g_nn = nullptr;
+  int g_nn_mode = -1;
   int g_iters = 0, g_kind = -1, g_prof = -1, g_pairs = 0;
   int64_t g_launches = 0;
 
@@ -77,10 +79,10 @@ void amg_fill_info(const Solver& S, amg_info_t* out);
 void amg_copy_level(const Solver& S, int level, int which, int32_t* rowptr, int32_t* col, double* val, cudaStream_t s);
 
 // learned stage (cnn.cu): buffers for grids of eb's size (before any capture),
-// then z <- z + h^2 rms(s) N(s / rms(s), m), s = r - (shift I + A) z
+// then z <- z + omega h^2 rms(s) N(s / rms(s), m), s = r - (shift I + A) z
 void nn_stage_prepare(nn_handle* nn, const EBHandle& eb, cudaStream_t s);
-void nn_stage_apply(nn_handle* nn, const EBHandle& eb, double shift, const double* r, double* z, int64_t& nlaunch,
-                    cudaStream_t s);
+void nn_stage_apply(nn_handle* nn, const EBHandle& eb, double shift, int mode, const double* r, double* z,
+                    int64_t& nlaunch, cudaStream_t s);
 
 }  // namespace ebk
 

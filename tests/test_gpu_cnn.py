@@ -17,8 +17,12 @@
 * one training step: per-pair losses within 2e-2 of the oracle's, and Adam's
   first step -lr g / (|g| + eps) reproduced wherever the oracle gradient is not
   tiny.
+* one application of the preconditioner with the stage (both modes): the
+  correction beyond the V-cycle within 3e-2 of the oracle's (bf16 network),
+  the V-cycle part within 1e-12.
 * flexible PCG with the stage converges to the oracle's solution; with a zero
-  network it takes exactly the iterations of plain AMG-PCG.
+  network it takes exactly the iterations of plain AMG-PCG; with the
+  energy-optimal step even a random network costs at most a few iterations.
 """
 import numpy as np
 import pytest
@@ -283,3 +287,46 @@ def test_training_lowers_loss_and_reports_gain():
     print(f"loss {log[0][1]:.4f} -> {log[-1][1]:.4f}; iterations plain {st0.iterations}, with stage {st1.iterations}")
     assert log[-1][1] < 0.8 * log[0][1]
     assert st1.converged and torch.linalg.norm(x1 - x0) <= 1e-8 * torch.linalg.norm(x0)
+
+
+@pytest.mark.parametrize("mode", ["plain", "energy"])
+def test_stage_application_parity(mode):
+    eb = _pkg()
+    grid, ls = _geometry(112, 71)
+    ref = oeb.build(grid, ls)
+    Ho = oamg.setup(ref.A)
+    r = np.random.default_rng(72).standard_normal(ref.num_cp)
+    theta = _params(73, scale=0.5)
+    theta32 = theta.astype(np.float32).astype(np.float64)
+    zo = ocnn.stage(ref, ref.A, Ho, theta32, r, mode=mode)
+    z1o = oamg.vcycle(Ho, r)
+    h = eb.EB(grid, ls)
+    amg = eb.AMG(h)
+    net = eb.Net(theta)
+    rg = torch.from_numpy(ref.to_grid(r)).cuda()
+    z = eb.precondition_nn(amg, net, rg, mode=eb.EB_NN_ENERGY if mode == "energy" else eb.EB_NN_PLAIN)
+    z1 = amg.vcycle(rg)
+    zd = ref.from_grid(z.cpu().numpy())
+    z1d = ref.from_grid(z1.cpu().numpy())
+    assert _rel(z1d, z1o) <= 1e-12
+    assert _rel(zd - z1d, zo - z1o) <= 3e-2, _rel(zd - z1d, zo - z1o)
+
+
+def test_energy_mode_limits_a_bad_network():
+    eb = _pkg()
+    grid, ls = _geometry(256, 81)
+    h = eb.EB(grid, ls)
+    amg = eb.AMG(h)
+    b = torch.from_numpy(np.random.default_rng(82).standard_normal(h.shape())).cuda()
+    x0, st0 = amg.solve(b, rtol=1e-10)
+    net = eb.Net(_params(83, bias=0.3))
+    x1, st1 = eb.solve_nn(amg, net, b, rtol=1e-10, mode=eb.EB_NN_ENERGY, maxit=500)
+    try:   # the plain step with a bad network may make the preconditioner indefinite
+        _, st2 = eb.solve_nn(amg, net, b, rtol=1e-10, mode=eb.EB_NN_PLAIN, maxit=500, allow_noconv=True)
+        plain = st2.iterations
+    except eb.EBError as e:
+        assert e.code == eb.EB_ERR_BREAKDOWN
+        plain = "breakdown"
+    print(f"iterations: AMG-PCG {st0.iterations}, random stage with energy step {st1.iterations}, plain step {plain}")
+    assert st1.converged and st1.iterations <= st0.iterations + 3
+    assert torch.linalg.norm(x1 - x0) <= 1e-8 * torch.linalg.norm(x0)

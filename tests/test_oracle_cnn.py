@@ -13,6 +13,8 @@ P11 (oracle side)
   * Adam's first step is -lr g / (|g| + eps); Adam minimises a quadratic
   * flexible PCG with the stage converges to the direct solution; with a zero
     network it reproduces plain AMG-PCG
+  * the energy-optimal step never leaves more error energy than the V-cycle
+    alone, and is 1 for a network returning the exact error
   * bf16() rounds to nearest even and agrees with torch's conversion
 """
 import numpy as np
@@ -199,3 +201,29 @@ def test_bf16_rounding():
     x = np.random.default_rng(10).standard_normal(4096).astype(np.float32) * 100
     ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
     assert np.array_equal(cnn.bf16(x), ref)
+
+
+def test_energy_step_never_increases_error_energy():
+    s = _small_system(84, 14)
+    H = amg.setup(s.A)
+    assert len(H.levels) >= 2   # V is not the exact inverse
+    rng = np.random.default_rng(15)
+    A = s.A
+    Ad = A.toarray()
+    for trial in range(4):
+        r = rng.standard_normal(s.num_cp)
+        delta = np.linalg.solve(Ad, r)             # exact error of the preconditioning step
+        z1 = amg.vcycle(H, r)
+        theta = cnn.init_params(20 + trial) * (0.5 + trial)
+        z = cnn.stage(s, A, H, theta, r, mode="energy")
+        e1, e2 = delta - z1, delta - z
+        assert e2 @ (A @ e2) <= e1 @ (A @ e1) * (1 + 1e-12)
+    # a "network" equal to the exact correction: omega = 1, zero error left
+    r = rng.standard_normal(s.num_cp)
+    z1 = amg.vcycle(H, r)
+    res = r - A @ z1
+    exact = np.linalg.solve(Ad, res)
+    ov = exact * s.grid.h ** -2 / np.sqrt(np.mean(res * res))
+    sh = res / np.sqrt(np.mean(res * res))
+    omega = (ov @ sh) / (ov @ (s.grid.h ** 2 * (A @ ov)))
+    assert abs(omega - 1.0) < 1e-10
