@@ -1,16 +1,34 @@
-"""Benchmark: AMG-PCG time to 1e-10 relative residual on the 3D Poisson
-workload (ellipsoid, semi-axes 0.7/0.5/0.4, seeded rotation, 256^3 nodes on
-[-1,1]^3, u = exp(x) sin(y+z)).
+"""Benchmarks of the embedded-boundary hot path on one GB300, one JSON line per run.
 
-One step = one pcg_solve from x = 0 to ||r||/||b|| <= 1e-10 with the AMG
-hierarchy built beforehand; the metric is DOF/s = N_C / time-to-tolerance
-(N_C = computational points).  Build and setup times are reported beside it.
+--workload (default poisson3d):
+
+poisson3d  3D Poisson AMG-PCG: ellipsoid with semi-axes 0.7/0.5/0.4 and a seeded
+           rotation, 256^3 nodes on [-1,1]^3, u = exp(x) sin(y+z).  One step =
+           one pcg_solve from x = 0 to ||r||/||b|| <= 1e-10 (FP32 V-cycle,
+           flexible FP64 PCG); the plain FP64 V-cycle is timed beside it.
+poisson2d  2D Poisson, plain FP64 AMG-PCG: circle R = 0.5 at (0.02, 0.01),
+           128^2 nodes, u = sin(2x) cos(3y), rtol 1e-10.
+wave       Leapfrog wave equation on the star r = 0.5 + 0.1 sin(5 phi), 4096^2
+           nodes, dt = 0.9 of the periodic CFL limit, 10,000 steps from a
+           seeded Gaussian pulse; one step = the whole 10,000-step run in FP32
+           (one persistent launch), FP64 timed beside it.
+batched    64 seeded stars on grids from 128^2 to 1024^2, backward-Euler heat
+           with dt = h, 50 steps of all 64 geometries per bench step (one
+           batch_heat_step per time step, forcing and boundary data frozen at
+           t = 0); the same time step solved geometry by geometry with the
+           plain FP64 AMG-PCG is timed beside it.
+learned    The learned preconditioner stage: trained (outside the timed
+           region) on 20,000 solver-generated pairs at 512^2 on random stars,
+           then one step = one flexible PCG solve with V-cycle + stage to
+           1e-10 on a random star at 2048^2 (u = sin(2x) cos(3y)); the plain
+           FP64 AMG-PCG is timed beside it.
+
 L2 (129 MB) is flushed between timed steps by a 512 MB write outside the
-timed events.  Under torchrun every rank solves its own copy (replicas; no
-collective on the data path) and rank 0 prints one JSON line.
+timed events.  Under torchrun every rank runs its own copy (replicas; no
+collective on the data path) and rank 0 prints the line.
 
---impl reference runs the FP64 CPU oracle (plain numpy / scipy) on a bounded
-sample of the same workload on the host cores instead.
+--impl reference runs the FP64 CPU oracle (plain numpy / scipy) of the same
+workload on a bounded sample on the host cores instead.
 """
 from __future__ import annotations
 
@@ -29,30 +47,24 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "AMG-PCG DOF/s and time to 1e-10 rel. residual; stencil HBM GB/s vs peak"
-UNIT = "DOF/s"
 RTOL = 1e-10
 N_FULL = 256
-# level-0 Chebyshev step of the FP32 V-cycle: reads x, b, d and writes x_out, d
-# (4 bytes each) per computational point
-CHEB_BYTES_PER_DOF = 20
-ROOFLINE_KERNEL = "k_g_cheb_step<3, float, float>"
+# level-0 Chebyshev step: reads x, b, d and writes x_out, d per computational point
+CHEB_BYTES_PER_DOF = {"f32": 20, "f64": 40}
+# leapfrog step per computational point: reads u^n, u^{n-1}, the node code, writes u^{n+1}
+LEAPFROG_BYTES_PER_DOF = {"f32": 13, "f64": 25}
+# one 32 -> 32 convolution of the learned stage per pixel: 2 x 9 x 32 x 32 FLOP
+CONV_FLOP_PER_PX = 18432
 CPU_SAMPLE_N = 112
-
-
-def workload_config(n=N_FULL):
-    return {"workload": f"3D Poisson AMG-PCG, ellipsoid (0.7,0.5,0.4) seeded rotation, {n}^3 nodes on [-1,1]^3, "
-                        f"u=exp(x)sin(y+z), rtol {RTOL:g}",
-            "n": n, "rtol": RTOL,
-            "vcycle": "FP32 storage and arithmetic, Chebyshev-2, smoothed aggregation; outer flexible PCG in FP64",
-            "l2": "flushed between timed steps (512 MB write outside the timed events)"}
+WORKLOADS = ("poisson3d", "poisson2d", "wave", "batched", "learned")
 
 
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
-        return float(d["hbm_gbs"]), "measured"
-    return 6800.0, "fallback"
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
 def kernel_fingerprint():
@@ -63,7 +75,7 @@ def kernel_fingerprint():
 
 
 def recorded_traffic():
-    """Per-launch DRAM bytes of the roofline kernel from the committed ncu
+    """Per-launch DRAM bytes of the 3D roofline kernel from the committed ncu
     summary, if it was taken on the current kernel source."""
     p = os.path.join(ROOT, "profiles", "cheb_step_3d_256_traffic.json")
     if not os.path.exists(p):
@@ -124,216 +136,648 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# ----------------------------------------------------------------- oracle leg
-def cpu_oracle_sample(n=CPU_SAMPLE_N):
-    """Times the oracle's AMG-PCG solve on the same workload at n^3 nodes in a
-    fresh single-threaded process; returns its JSON record."""
+# ---------------------------------------------------------------- workloads
+def config_of(w, small=None):
+    if w == "poisson3d":
+        n = small or N_FULL
+        return {"workload": f"3D Poisson AMG-PCG, ellipsoid (0.7,0.5,0.4) seeded rotation, {n}^3 nodes on [-1,1]^3, "
+                            f"u=exp(x)sin(y+z), rtol {RTOL:g}", "n": n, "rtol": RTOL,
+                "vcycle": "FP32 storage and arithmetic, Chebyshev-2, smoothed aggregation; outer flexible PCG in FP64",
+                "l2": "flushed between timed steps (512 MB write outside the timed events)"}
+    if w == "poisson2d":
+        return {"workload": f"2D Poisson plain FP64 AMG-PCG, circle R=0.5 at (0.02,0.01), 128^2 nodes on [-1,1]^2, "
+                            f"u=sin(2x)cos(3y), rtol {RTOL:g}", "n": 128, "rtol": RTOL,
+                "l2": "flushed between timed steps (512 MB write outside the timed events)"}
+    if w == "wave":
+        n = small or 4096
+        return {"workload": f"2D leapfrog wave, star r=0.5+0.1 sin(5 phi), {n}^2 nodes on [-1,1]^2, "
+                            f"dt=0.9 h/sqrt(2), 10000 steps, seeded Gaussian pulse", "n": n, "steps_per_run": 10000,
+                "precision": "FP32 fields (FP64 timed beside)",
+                "l2": "fields (2 x 67 MB FP32) and the 512 MB flush between runs"}
+    if w == "batched":
+        return {"workload": "batched backward-Euler heat, 64 seeded stars r=0.5+sum a_k sin(k phi+p_k), k=2..6, "
+                            "grids 128^2..1024^2, dt=h, 50 steps of all geometries per bench step, "
+                            "forcing and boundary data of u=exp(-t) sin(2x) cos(3y) frozen at t=0",
+                "geometries": 64, "time_steps": 50, "rtol": RTOL,
+                "vcycle": "FP32 V-cycle on the block-diagonal hierarchy, per-geometry flexible FP64 PCG",
+                "l2": "batch vectors exceed L2 (26M nodes x 8 B)"}
+    if w == "learned":
+        return {"workload": "flexible PCG with V-cycle + learned CNN stage, random star at 2048^2, "
+                            f"u=sin(2x)cos(3y), rtol {RTOL:g}; network trained on 20000 solver pairs at 512^2 "
+                            "(2500 random stars x 8)", "n": 2048, "train_n": 512, "train_pairs": 20000,
+                "network": "6 x conv3x3, 32 channels, BF16 activations, FP32 accumulation",
+                "l2": "flushed between timed steps (512 MB write outside the timed events)"}
+    raise ValueError(w)
+
+
+UNITS = {"poisson3d": "DOF/s", "poisson2d": "DOF/s", "wave": "DOF-steps/s", "batched": "DOF/s",
+         "learned": "DOF/s"}
+
+
+# ------------------------------------------------------------------ oracle
+def _oracle_run(code, timeout=900):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = f"""
-import json, sys, time
-sys.path.insert(0, {ROOT!r})
-import numpy as np
-import eb_inputs as ei
-from oracle import amg, eb, solvers
-g, ls = ei.ellipsoid_k3({n}, 0)
-t0 = time.perf_counter(); s = eb.build(g, ls); t1 = time.perf_counter()
-pts = ei.grid_points(g)
-b = eb.rhs(s, ei.f_k3(*pts), ei.u_k3(*[s.cut_xg[:, a] for a in range(3)]))
-t2 = time.perf_counter(); H = amg.setup(s.A); t3 = time.perf_counter()
-x, st = solvers.pcg(s.A, b, M=lambda r: amg.vcycle(H, r), rtol={RTOL})
-t4 = time.perf_counter()
-print(json.dumps(dict(n={n}, num_cp=s.num_cp, build_s=t1 - t0, setup_s=t3 - t2, solve_s=t4 - t3,
-                      iterations=st.iterations, rel=st.true_rel_residual)))
-"""
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    r = subprocess.run([sys.executable, "-c", f"import sys; sys.path.insert(0, {ROOT!r})\n" + code],
+                       capture_output=True, text=True, env=env, timeout=timeout)
     if r.returncode != 0:
         raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_oracle_sample(w):
+    """Times the oracle on a bounded sample of workload w in a fresh
+    single-threaded process; returns (value, unit-consistent sample text, record)."""
+    if w == "poisson3d":
+        rec = _oracle_run(f"""
+import json, time
+import eb_inputs as ei
+from oracle import amg, eb, solvers
+g, ls = ei.ellipsoid_k3({CPU_SAMPLE_N}, 0)
+s = eb.build(g, ls)
+pts = ei.grid_points(g)
+b = eb.rhs(s, ei.f_k3(*pts), ei.u_k3(*[s.cut_xg[:, a] for a in range(3)]))
+H = amg.setup(s.A)
+t0 = time.perf_counter()
+x, st = solvers.pcg(s.A, b, M=lambda r: amg.vcycle(H, r), rtol={RTOL})
+t1 = time.perf_counter()
+print(json.dumps(dict(dof=s.num_cp, sec=t1 - t0, iterations=st.iterations)))
+""")
+        return rec["dof"] / rec["sec"], (f"oracle AMG-PCG solve to {RTOL:g} of the same ellipsoid at {CPU_SAMPLE_N}^3 "
+                                         f"nodes (N_C={rec['dof']}, {rec['iterations']} its, {rec['sec']:.1f} s)"), rec
+    if w == "poisson2d":
+        rec = _oracle_run(f"""
+import json, time
+import eb_inputs as ei
+from oracle import amg, eb, solvers
+g, ls = ei.circle_k1(128)
+s = eb.build(g, ls)
+X, Y = ei.grid_points(g)
+b = eb.rhs(s, ei.f_k1(X, Y), ei.u_k1(s.cut_xg[:, 0], s.cut_xg[:, 1]))
+H = amg.setup(s.A)
+t0 = time.perf_counter()
+reps = 0
+while time.perf_counter() - t0 < 10.0:
+    x, st = solvers.pcg(s.A, b, M=lambda r: amg.vcycle(H, r), rtol={RTOL})
+    reps += 1
+t1 = time.perf_counter()
+print(json.dumps(dict(dof=s.num_cp, sec=(t1 - t0) / reps, iterations=st.iterations, reps=reps)))
+""")
+        return rec["dof"] / rec["sec"], (f"oracle AMG-PCG solve of the full 128^2 workload (N_C={rec['dof']}, "
+                                         f"{rec['iterations']} its), mean of {rec['reps']} solves"), rec
+    if w == "wave":
+        rec = _oracle_run("""
+import json, math, time
+import eb_inputs as ei
+from oracle import eb, solvers
+g = ei.box_grid(2, 1024)
+ls = ei.star(ei.STAR_CENTER, 0.5, [5], [0.1], [0.0])
+s = eb.build(g, ls)
+X, Y = ei.grid_points(g)
+c, w = ei.pulse_params(0)
+u0 = s.from_grid(ei.pulse(X, Y, c, w))
+dt = 0.9 * g.h / math.sqrt(2.0)
+u1 = u0 - 0.5 * dt * dt * (s.A @ u0)
+t0 = time.perf_counter()
+solvers.leapfrog(s.A, u0, u1, dt, 4000)
+t1 = time.perf_counter()
+print(json.dumps(dict(dof=s.num_cp, steps=4000, sec=t1 - t0)))
+""")
+        return rec["dof"] * rec["steps"] / rec["sec"], (
+            f"oracle leapfrog (scipy CSR matvec) on the same star at 1024^2 nodes, 4000 steps "
+            f"(N_C={rec['dof']}, {rec['sec']:.1f} s)"), rec
+    if w == "batched":
+        rec = _oracle_run(f"""
+import json, time
+import numpy as np
+import scipy.sparse as sp
+import eb_inputs as ei
+from oracle import amg, eb, solvers
+cfg = ei.star_batch(64, 0)
+pick = list(range(12))
+dof, sec, its = 0, 0.0, []
+for i in pick:
+    nb, ls = cfg[i]
+    g = ei.box_grid(2, nb)
+    s = eb.build(g, ls)
+    dt = g.h
+    M0 = (s.A + (1.0 / dt) * sp.identity(s.num_cp, format="csr")).tocsr()
+    H = amg.setup(M0)
+    X, Y = ei.grid_points(g)
+    u = s.from_grid(ei.u_heat(X, Y, 0.0))
+    b = eb.rhs(s, -ei.f_heat(X, Y, 0.0), ei.u_heat(s.cut_xg[:, 0], s.cut_xg[:, 1], 0.0))
+    t0 = time.perf_counter()
+    u, st = solvers.pcg(M0, u / dt + b, x0=u, M=lambda r: amg.vcycle(H, r), rtol={RTOL})
+    sec += time.perf_counter() - t0
+    dof += s.num_cp
+    its.append(st.iterations)
+print(json.dumps(dict(dof=dof, sec=sec, iterations=its, sizes=[cfg[i][0] for i in pick])))
+""")
+        return rec["dof"] / rec["sec"], (
+            f"oracle backward-Euler step (AMG-PCG, warm start) of batch geometries 0-11 (n={rec['sizes']}, "
+            f"N_C={rec['dof']}, iterations {rec['iterations']}, {rec['sec']:.1f} s)"), rec
+    if w == "learned":
+        rec = _oracle_run(f"""
+import json, time
+import numpy as np
+import eb_inputs as ei
+from oracle import amg, cnn, eb
+g = ei.box_grid(2, 128)
+s = eb.build(g, ei.random_star(999))
+X, Y = ei.grid_points(g)
+b = eb.rhs(s, ei.f_k1(X, Y), ei.u_k1(s.cut_xg[:, 0], s.cut_xg[:, 1]))
+H = amg.setup(s.A)
+theta = cnn.init_params(8) * 0.1
+t0 = time.perf_counter()
+x, it = cnn.fpcg(s.A, b, lambda r: cnn.stage(s, s.A, H, theta, r), rtol={RTOL})
+t1 = time.perf_counter()
+print(json.dumps(dict(dof=s.num_cp, sec=t1 - t0, iterations=it)))
+""")
+        return rec["dof"] / rec["sec"], (
+            f"oracle flexible PCG with V-cycle + FP64 CNN stage (untrained weights) on a random star at 128^2 "
+            f"(N_C={rec['dof']}, {rec['iterations']} its, {rec['sec']:.1f} s)"), rec
+    raise ValueError(w)
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    times = []
-    rec = None
+    w = args.workload
+    vals, secs, rec, sample = [], [], None, ""
     for i in range(args.warmup + args.steps):
-        rec = cpu_oracle_sample()
+        v, sample, rec = cpu_oracle_sample(w)
         if i >= args.warmup:
-            times.append(rec["solve_s"])
-    t = sum(times) / len(times)
-    value = rec["num_cp"] / t
-    sample = (f"oracle AMG-PCG solve to {RTOL:g} on the same ellipsoid at {CPU_SAMPLE_N}^3 nodes "
-              f"(N_C={rec['num_cp']}, {rec['iterations']} iterations); DOF/s of that solve")
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(CPU_SAMPLE_N),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            vals.append(v)
+            secs.append(rec["sec"])
+    value = statistics.mean(vals)
+    unit = UNITS[w]
+    small = {"poisson3d": CPU_SAMPLE_N, "wave": 1024}.get(w)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.mean(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(w, small),
+            "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
 # -------------------------------------------------------------------- GPU leg
-def run_gpu(args):
+class Ctx:
+    def __init__(self):
+        import torch
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+            self.dist = dist
+        else:
+            torch.cuda.set_device(0)
+        from paper_2204_06083_gb300 import build as ebuild
+        if self.rank == 0:
+            ebuild.build()
+        self.barrier()
+        ebuild.build()
+        self.dev = torch.device("cuda", torch.cuda.current_device())
+        self.flush_buf = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=self.dev)
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def flush(self):
+        self.flush_buf.fill_(1.0)
+
+    def max_over_ranks(self, v):
+        import torch
+        t = torch.tensor([float(v)], dtype=torch.float64, device=self.dev)
+        if self.dist is not None:
+            self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+
+
+def timed(fn):
+    """Runs fn between CUDA events on torch's current stream; returns (ms, result)."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    r = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), r
+
+
+def loop(ctx, args, step, clocks_index):
+    """warm-up, then exactly args.steps timed steps between barriers; returns
+    (list of per-step results, max-over-ranks mean ms, clock summary)."""
+    import torch
+    for _ in range(args.warmup):
+        ctx.flush()
+        timed(step)
+    res, ms = [], []
+    ctx.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(clocks_index) as clk:
+        for _ in range(args.steps):
+            ctx.flush()
+            t, r = timed(step)
+            ms.append(t)
+            res.append(r)
+    torch.cuda.synchronize()
+    ctx.barrier()
+    return res, ctx.max_over_ranks(sum(ms) / len(ms)), clk.summary()
+
+
+def gpu_poisson(ctx, args, dim):
     import numpy as np
     import torch
-
     import eb_inputs as ei
     import paper_2204_06083_gb300 as eb
-    from paper_2204_06083_gb300 import build as ebuild
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = ctx.dev
+    if dim == 3:
+        grid, ls = ei.ellipsoid_k3(N_FULL, 0)
     else:
-        torch.cuda.set_device(0)
-    if rank == 0:
-        ebuild.build()
-    if dist is not None:
-        dist.barrier()
-    ebuild.build()
-    dev = torch.device("cuda", torch.cuda.current_device())
-
-    grid, ls = ei.ellipsoid_k3(N_FULL, 0)
+        grid, ls = ei.circle_k1(128)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     h = eb.EB(grid, ls)
     torch.cuda.synchronize()
     build_ms = 1000.0 * (time.perf_counter() - t0)
+    prec = eb.EB_F32 if dim == 3 else eb.EB_F64
     t0 = time.perf_counter()
-    solver = eb.AMG(h, 0.0, vcycle_prec=eb.EB_F32)
+    solver = eb.AMG(h, 0.0, vcycle_prec=prec)
     setup_ms = 1000.0 * (time.perf_counter() - t0)
-    solver64 = eb.AMG(h, 0.0)
+    solver64 = eb.AMG(h, 0.0) if dim == 3 else solver
     nc = h.info.num_cp
     pts = ei.grid_points(grid)
-    f = torch.tensor(ei.f_k3(*pts), device=dev)
     _, _, _, xg = h.cuts()
     xg = xg.cpu().numpy()
-    ug = torch.tensor(ei.u_k3(xg[:, 0], xg[:, 1], xg[:, 2]), device=dev)
+    if dim == 3:
+        f = torch.tensor(ei.f_k3(*pts), device=dev)
+        ug = torch.tensor(ei.u_k3(xg[:, 0], xg[:, 1], xg[:, 2]), device=dev)
+        uex = ei.u_k3(*pts)
+    else:
+        f = torch.tensor(ei.f_k1(*pts), device=dev)
+        ug = torch.tensor(ei.u_k1(xg[:, 0], xg[:, 1]), device=dev)
+        uex = ei.u_k1(*pts)
     b = h.rhs(f, ug)
     x = torch.zeros_like(b)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def step(profile):
+    def step():
         x.zero_()
-        flush.fill_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        _, st = solver.solve(b, x=x, rtol=RTOL, maxit=500, profile=profile)
-        e1.record()
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1), st
+        return solver.solve(b, x=x, rtol=RTOL, maxit=500, profile=True)[1]
 
-    for _ in range(args.warmup):
-        step(False)
-    clocks = ClockSampler(torch.cuda.current_device())
-    ms, iters, prof_ms, prof_n, launches = [], [], 0.0, 0, 0
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with clocks:
-        for _ in range(args.steps):
-            t, st = step(True)
-            ms.append(t)
-            iters.append(st.iterations)
-            prof_ms += st.prof_kernel_ms
-            prof_n += st.prof_launches
-            launches += st.launches
-    torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
-    tot = torch.tensor([sum(ms)], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
-    ms_per_step = float(tot.item()) / args.steps
-    value = world * nc / (ms_per_step / 1000.0)
-
-    # the plain FP64 AMG-PCG on the same input, for comparison
-    f64_ms, f64_it = [], 0
-    for i in range(args.warmup + args.steps):
-        x.zero_()
-        flush.fill_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        _, st64 = solver64.solve(b, x=x, rtol=RTOL, maxit=500)
-        e1.record()
-        torch.cuda.synchronize()
-        if i >= args.warmup:
-            f64_ms.append(e0.elapsed_time(e1))
-            f64_it = st64.iterations
-
+    sts, ms_per_step, clocks = loop(ctx, args, step, torch.cuda.current_device())
+    prof_ms = sum(s.prof_kernel_ms for s in sts)
+    prof_n = sum(s.prof_launches for s in sts)
+    launches = sum(s.launches for s in sts) // len(sts)
+    value = ctx.world * nc / (ms_per_step / 1000.0)
+    extra = {}
+    if dim == 3:
+        f64 = []
+        for i in range(args.warmup + args.steps):
+            x.zero_()
+            ctx.flush()
+            t, st64 = timed(lambda: solver64.solve(b, x=x, rtol=RTOL, maxit=500)[1])
+            if i >= args.warmup:
+                f64.append(t)
+        extra["fp64_vcycle"] = {"time_to_tol_ms": statistics.mean(f64), "iterations": st64.iterations,
+                                "dof_per_s": nc / (statistics.mean(f64) / 1000.0)}
     # end to end through the C ABI: pinned host b -> device, solve, x -> pinned host
     hb = b.cpu().pin_memory()
     hx = torch.empty_like(hb).pin_memory()
     db = torch.empty_like(b)
-    e2e_ms = []
-    for i in range(args.warmup + args.steps):
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
+    e2e = []
+
+    def e2e_step():
         db.copy_(hb, non_blocking=True)
         x.zero_()
         solver.solve(db, x=x, rtol=RTOL, maxit=500)
         hx.copy_(x, non_blocking=True)
-        e1.record()
+
+    for i in range(args.warmup + args.steps):
+        ctx.flush()
         torch.cuda.synchronize()
+        t, _ = timed(e2e_step)
         if i >= args.warmup:
-            e2e_ms.append(e0.elapsed_time(e1))
-    e2e_t = torch.tensor([sum(e2e_ms) / len(e2e_ms)], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = world * nc / (float(e2e_t.item()) / 1000.0)
-    # solution check against the manufactured solution (second order)
-    xs = hx.numpy().reshape(-1)
+            e2e.append(t)
+    e2e_value = ctx.world * nc / (ctx.max_over_ranks(statistics.mean(e2e)) / 1000.0)
     nodes, _ = h.cp_data()
     nodes = nodes.cpu().numpy()
-    ue = ei.u_k3(*pts).reshape(-1)[nodes]
-    err_linf = float(np.abs(xs[nodes] - ue).max())
+    err = float(np.abs(hx.numpy().reshape(-1)[nodes] - uex.reshape(-1)[nodes]).max())
+    pk, kind = peaks()
+    avg_s = (prof_ms / prof_n) / 1000.0 if prof_n else float("nan")
+    vb = CHEB_BYTES_PER_DOF["f32" if dim == 3 else "f64"]
+    achieved = vb * nc / avg_s / 1e9 if prof_n else None
+    line = {"value": value, "ms_per_step": ms_per_step,
+            "dtype": "f64 outer, f32 V-cycle" if dim == 3 else "f64",
+            "num_cp": nc, "iterations": sts[-1].iterations, "time_to_tol_ms": ms_per_step,
+            "build_ms": build_ms, "setup_ms": setup_ms, "amg_levels": solver.rows, "max_err_vs_exact": err,
+            "roofline": {"bound": "hbm",
+                         "kernel": f"k_g_cheb_step<{dim}, {'float, float' if dim == 3 else 'double, double'}>",
+                         "achieved": achieved, "peak": pk["hbm_gbs"], "peak_kind": kind, "unit": "GB/s",
+                         "frac": (achieved / pk["hbm_gbs"]) if achieved else None,
+                         "traffic": recorded_traffic() if dim == 3 else None,
+                         "algorithmic_bytes_per_launch": vb * nc, "avg_launch_us": avg_s * 1e6,
+                         "launches_timed": prof_n},
+            "e2e": {"value": e2e_value, "unit": "DOF/s", "h2d_bytes_per_step": hb.numel() * 8,
+                    "d2h_bytes_per_step": hx.numel() * 8},
+            "gpu_launches": launches, "clocks": clocks}
+    line.update(extra)
+    return line
 
-    peak, peak_kind = peaks()
-    avg_launch_s = (prof_ms / prof_n) / 1000.0 if prof_n else float("nan")
-    achieved = CHEB_BYTES_PER_DOF * nc / avg_launch_s / 1e9 if prof_n else None
-    if rank != 0:
-        if dist is not None:
-            dist.destroy_process_group()
+
+def gpu_wave(ctx, args):
+    import torch
+    import eb_inputs as ei
+    import paper_2204_06083_gb300 as eb
+    nsteps = 10000
+    grid, ls = ei.star_wave(4096)
+    h = eb.EB(grid, ls)
+    nc = h.info.num_cp
+    X, Y = ei.grid_points(grid)
+    c, w = ei.pulse_params(0)
+    dt = 0.9 * grid.h / math.sqrt(2.0)
+    u0 = torch.tensor(ei.pulse(X, Y, c, w), device=ctx.dev)
+    u1 = u0 - 0.5 * dt * dt * h.apply(u0)
+    fields = {}
+    for dt_name, dtype in (("f32", torch.float32), ("f64", torch.float64)):
+        fields[dt_name] = (u0.to(dtype), u1.to(dtype))
+    a = torch.empty_like(fields["f32"][0])
+    bfield = torch.empty_like(fields["f32"][0])
+
+    def step():
+        a.copy_(fields["f32"][0])
+        bfield.copy_(fields["f32"][1])
+        return timed(lambda: h.wave_step(a, bfield, dt, nsteps))[0]
+
+    kern_ms, ms_per_step, clocks = loop(ctx, args, step, torch.cuda.current_device())
+    value = ctx.world * nc * nsteps / (ms_per_step / 1000.0)
+    a64 = torch.empty_like(fields["f64"][0])
+    b64 = torch.empty_like(fields["f64"][0])
+    f64 = []
+    for i in range(1 + args.steps):
+        a64.copy_(fields["f64"][0])
+        b64.copy_(fields["f64"][1])
+        ctx.flush()
+        t, _ = timed(lambda: h.wave_step(a64, b64, dt, nsteps))
+        if i >= 1:
+            f64.append(t)
+    diff = float((bfield.double() - b64).abs().max().item() / b64.abs().max().item())
+    # e2e: pinned host fields -> device, 10,000 steps, both fields -> host
+    hu = [fields["f32"][0].cpu().pin_memory(), fields["f32"][1].cpu().pin_memory()]
+    ho = [torch.empty_like(hu[0]).pin_memory(), torch.empty_like(hu[1]).pin_memory()]
+    e2e = []
+
+    def e2e_step():
+        a.copy_(hu[0], non_blocking=True)
+        bfield.copy_(hu[1], non_blocking=True)
+        h.wave_step(a, bfield, dt, nsteps)
+        ho[0].copy_(a, non_blocking=True)
+        ho[1].copy_(bfield, non_blocking=True)
+
+    for i in range(1 + args.steps):
+        ctx.flush()
+        t, _ = timed(e2e_step)
+        if i >= 1:
+            e2e.append(t)
+    e2e_value = ctx.world * nc * nsteps / (ctx.max_over_ranks(statistics.mean(e2e)) / 1000.0)
+    pk, kind = peaks()
+    launch_s = statistics.mean(kern_ms) / 1000.0
+    alg = LEAPFROG_BYTES_PER_DOF["f32"] * nc * nsteps
+    achieved = alg / launch_s / 1e9
+    return {"value": value, "ms_per_step": ms_per_step, "dtype": "f32", "num_cp": nc, "dt": dt,
+            "us_per_time_step": 1000.0 * ms_per_step / nsteps,
+            "fp64": {"ms_per_run": statistics.mean(f64), "us_per_time_step": 1000.0 * statistics.mean(f64) / nsteps,
+                     "dof_steps_per_s": nc * nsteps / (statistics.mean(f64) / 1000.0),
+                     "max_rel_diff_f32_vs_f64_after_run": diff},
+            "roofline": {"bound": "hbm", "kernel": "k_leapfrog<float, 2> (persistent, 10000 steps per launch)",
+                         "achieved": achieved, "peak": pk["hbm_gbs"], "peak_kind": kind, "unit": "GB/s",
+                         "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                         "algorithmic_bytes_per_launch": alg, "avg_launch_us": launch_s * 1e6,
+                         "launches_timed": len(kern_ms)},
+            "e2e": {"value": e2e_value, "unit": "DOF-steps/s", "h2d_bytes_per_step": 2 * hu[0].numel() * 4,
+                    "d2h_bytes_per_step": 2 * hu[0].numel() * 4},
+            "gpu_launches": 3, "clocks": clocks}
+
+
+def gpu_batched(ctx, args):
+    import numpy as np
+    import torch
+    import eb_inputs as ei
+    import paper_2204_06083_gb300 as eb
+    nsteps = 50
+    cfg = ei.star_batch(64, 0)
+    grids = [ei.box_grid(2, nb) for nb, _ in cfg]
+    lss = [ls for _, ls in cfg]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    B = eb.Batch(grids, lss)
+    dts = [g.h for g in grids]
+    B.heat_setup(dts, 1.0, vcycle_prec=eb.EB_F32)
+    torch.cuda.synchronize()
+    setup_ms = 1000.0 * (time.perf_counter() - t0)
+    u0 = B.zeros()
+    f = B.zeros()
+    ug = torch.zeros(max(B.num_cut, 1), dtype=torch.float64, device=ctx.dev)
+    for g in range(B.count):
+        X, Y = ei.grid_points(grids[g])
+        B.view(u0, g).copy_(torch.tensor(ei.u_heat(X, Y, 0.0)))
+        B.view(f, g).copy_(torch.tensor(-ei.f_heat(X, Y, 0.0)))
+        xg = B.geometry(g).cuts()[3].cpu().numpy()
+        ug[B.cut_off[g]:B.cut_off[g + 1]] = torch.tensor(ei.u_heat(xg[:, 0], xg[:, 1], 0.0))
+    b1 = B.rhs(f, ug)
+    u = B.zeros()
+    B.set_profile(True)
+
+    def step():
+        u.copy_(u0)
+        stats = []
+        for _ in range(nsteps):
+            stats.append(B.heat_step(u, b1, rtol=RTOL, maxit=300))
+        return stats
+
+    res, ms_per_step, clocks = loop(ctx, args, step, torch.cuda.current_device())
+    B.set_profile(False)
+    nc = B.num_cp
+    value = ctx.world * nc * nsteps / (ms_per_step / 1000.0)
+    prof_ms = sum(st[0].prof_kernel_ms for r in res for st in r)
+    prof_n = sum(st[0].prof_launches for r in res for st in r)
+    launches = sum(st[0].launches for st in res[-1])
+    iters = [max(s.iterations for s in st) for st in res[-1]]
+    # the plain FP64 AMG-PCG, geometry by geometry, on the first time step
+    hs = [B.geometry(g) for g in range(B.count)]
+    solvers = [eb.AMG(hs[g], 1.0 / dts[g]) for g in range(B.count)]
+    us = [B.view(u0, g).contiguous() for g in range(B.count)]
+    bs = [B.view(b1, g).contiguous() for g in range(B.count)]
+    seq = []
+    for i in range(1 + args.steps):
+        uu = [v.clone() for v in us]
+        ctx.flush()
+        t, _ = timed(lambda: [solvers[g].heat_step(uu[g], bs[g], dts[g], theta=1.0, rtol=RTOL)
+                              for g in range(B.count)])
+        if i >= 1:
+            seq.append(t)
+    # e2e: pinned host u0 and b1 -> device, 50 steps, u -> host
+    hu0 = u0.cpu().pin_memory()
+    hb1 = b1.cpu().pin_memory()
+    hout = torch.empty_like(hu0).pin_memory()
+    db1 = torch.empty_like(b1)
+    e2e = []
+
+    def e2e_step():
+        u.copy_(hu0, non_blocking=True)
+        db1.copy_(hb1, non_blocking=True)
+        for _ in range(nsteps):
+            B.heat_step(u, db1, rtol=RTOL, maxit=300)
+        hout.copy_(u, non_blocking=True)
+
+    for i in range(1 + min(args.steps, 2)):
+        ctx.flush()
+        t, _ = timed(e2e_step)
+        if i >= 1:
+            e2e.append(t)
+    e2e_value = ctx.world * nc * nsteps / (ctx.max_over_ranks(statistics.mean(e2e)) / 1000.0)
+    pk, kind = peaks()
+    avg_s = (prof_ms / prof_n) / 1000.0 if prof_n else float("nan")
+    achieved = CHEB_BYTES_PER_DOF["f32"] * nc / avg_s / 1e9 if prof_n else None
+    return {"value": value, "ms_per_step": ms_per_step, "dtype": "f64 outer, f32 V-cycle", "num_cp": nc,
+            "num_nodes": B.num_nodes, "setup_ms": setup_ms, "ms_per_time_step": ms_per_step / nsteps,
+            "max_iterations_per_time_step": iters,
+            "sequential_fp64": {"ms_per_time_step": statistics.mean(seq),
+                                "dof_per_s": nc / (statistics.mean(seq) / 1000.0)},
+            "roofline": {"bound": "hbm", "kernel": "k_g_cheb_step<2, float, float> (batch view)",
+                         "achieved": achieved, "peak": pk["hbm_gbs"], "peak_kind": kind, "unit": "GB/s",
+                         "frac": (achieved / pk["hbm_gbs"]) if achieved else None, "traffic": None,
+                         "algorithmic_bytes_per_launch": CHEB_BYTES_PER_DOF["f32"] * nc,
+                         "avg_launch_us": avg_s * 1e6, "launches_timed": prof_n},
+            "e2e": {"value": e2e_value, "unit": "DOF/s", "h2d_bytes_per_step": 2 * hu0.numel() * 8,
+                    "d2h_bytes_per_step": hu0.numel() * 8},
+            "gpu_launches": launches, "clocks": clocks}
+
+
+def gpu_learned(ctx, args):
+    import numpy as np
+    import torch
+    import eb_inputs as ei
+    import paper_2204_06083_gb300 as eb
+    from paper_2204_06083_gb300 import learned
+    ntrain, per, npairs, batch = 512, 8, 20000, 16
+    t0 = time.perf_counter()
+    geos = [(ei.box_grid(2, ntrain), ei.random_star(10000 + i)) for i in range(npairs // per)]
+    store = learned.make_pairs(geos, per, seed=1)
+    pairs_s = time.perf_counter() - t0
+    net = eb.Net(learned.init_params(8))
+    t0 = time.perf_counter()
+    log = learned.train(net, store, steps=npairs // batch, batch=batch, lr=1e-3, seed=2, log_every=125)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del store
+    grid, ls = ei.box_grid(2, 2048), ei.random_star(999)
+    h = eb.EB(grid, ls)
+    amg = eb.AMG(h)
+    nc = h.info.num_cp
+    pts = ei.grid_points(grid)
+    xg = h.cuts()[3].cpu().numpy()
+    b = h.rhs(torch.tensor(ei.f_k1(*pts), device=ctx.dev), torch.tensor(ei.u_k1(xg[:, 0], xg[:, 1]), device=ctx.dev))
+    x = torch.zeros_like(b)
+
+    def step():
+        x.zero_()
+        return eb.solve_nn(amg, net, b, x=x, rtol=RTOL, maxit=400, mode=eb.EB_NN_PLAIN, profile=2,
+                           allow_noconv=True)[1]
+
+    sts, ms_per_step, clocks = loop(ctx, args, step, torch.cuda.current_device())
+    value = ctx.world * nc / (ms_per_step / 1000.0)
+    prof_ms = sum(s.prof_kernel_ms for s in sts)
+    prof_n = sum(s.prof_launches for s in sts)
+    compare = {}
+    for name, fn in (("plain_fp64_amg_pcg", lambda: amg.solve(b, x=x, rtol=RTOL, maxit=400)[1]),
+                     ("stage_energy_step", lambda: eb.solve_nn(amg, net, b, x=x, rtol=RTOL, maxit=400,
+                                                               mode=eb.EB_NN_ENERGY, allow_noconv=True)[1])):
+        tt = []
+        for i in range(1 + args.steps):
+            x.zero_()
+            ctx.flush()
+            t, st = timed(fn)
+            if i >= 1:
+                tt.append(t)
+        compare[name] = {"time_to_tol_ms": statistics.mean(tt), "iterations": st.iterations,
+                         "converged": bool(st.converged)}
+    hb = b.cpu().pin_memory()
+    hx = torch.empty_like(hb).pin_memory()
+    db = torch.empty_like(b)
+    e2e = []
+
+    def e2e_step():
+        db.copy_(hb, non_blocking=True)
+        x.zero_()
+        eb.solve_nn(amg, net, db, x=x, rtol=RTOL, maxit=400, allow_noconv=True)
+        hx.copy_(x, non_blocking=True)
+
+    for i in range(1 + args.steps):
+        ctx.flush()
+        t, _ = timed(e2e_step)
+        if i >= 1:
+            e2e.append(t)
+    e2e_value = ctx.world * nc / (ctx.max_over_ranks(statistics.mean(e2e)) / 1000.0)
+    pk, kind = peaks()
+    px = int(grid.n[0]) * int(grid.n[1])
+    avg_s = (prof_ms / prof_n) / 1000.0 if prof_n else float("nan")
+    achieved = CONV_FLOP_PER_PX * px / avg_s / 1e12 if prof_n else None
+    peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+    return {"value": value, "ms_per_step": ms_per_step, "dtype": "f64 outer, bf16 CNN (f32 accumulate)",
+            "num_cp": nc, "iterations": sts[-1].iterations, "converged": bool(sts[-1].converged),
+            "time_to_tol_ms": ms_per_step, "compare": compare,
+            "training": {"pairs": npairs, "pair_generation_s": pairs_s, "train_s": train_s, "adam_steps": npairs // batch,
+                         "batch": batch, "loss_log": log},
+            "roofline": {"bound": "tensor", "kernel": "k_conv32 (32->32 implicit-GEMM conv, mma.sync bf16)",
+                         "achieved": achieved, "peak": peak, "peak_kind": kind + " bf16 sustained", "unit": "TFLOP/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "algorithmic_flops_per_launch": CONV_FLOP_PER_PX * px, "avg_launch_us": avg_s * 1e6,
+                         "launches_timed": prof_n},
+            "e2e": {"value": e2e_value, "unit": "DOF/s", "h2d_bytes_per_step": hb.numel() * 8,
+                    "d2h_bytes_per_step": hx.numel() * 8},
+            "gpu_launches": sts[-1].launches, "clocks": clocks}
+
+
+def run_gpu(args):
+    ctx = Ctx()
+    w = args.workload
+    if w == "poisson3d":
+        body = gpu_poisson(ctx, args, 3)
+    elif w == "poisson2d":
+        body = gpu_poisson(ctx, args, 2)
+    elif w == "wave":
+        body = gpu_wave(ctx, args)
+    elif w == "batched":
+        body = gpu_batched(ctx, args)
+    else:
+        body = gpu_learned(ctx, args)
+    if ctx.rank != 0:
+        ctx.close()
         return 0
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
-        rec = cpu_oracle_sample()
-        cpu = {"value": rec["num_cp"] / rec["solve_s"], "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"oracle AMG-PCG solve to {RTOL:g} of the same ellipsoid at {CPU_SAMPLE_N}^3 nodes "
-                         f"(N_C={rec['num_cp']}, {rec['iterations']} its, {rec['solve_s']:.1f} s), one thread"}
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64 outer, f32 V-cycle", "data": "synthetic",
-            "config": workload_config(),
-            "fp64_vcycle": {"time_to_tol_ms": sum(f64_ms) / len(f64_ms), "iterations": f64_it,
-                            "dof_per_s": nc / (sum(f64_ms) / len(f64_ms) / 1000.0)},
-            "num_cp": nc, "iterations": iters[-1], "time_to_tol_ms": ms_per_step,
-            "build_ms": build_ms, "setup_ms": setup_ms, "amg_levels": solver.rows,
-            "max_err_vs_exact": err_linf,
-            "roofline": {"bound": "hbm", "kernel": ROOFLINE_KERNEL, "achieved": achieved, "peak": peak,
-                         "peak_kind": peak_kind, "unit": "GB/s",
-                         "frac": (achieved / peak) if achieved else None, "traffic": recorded_traffic(),
-                         "algorithmic_bytes_per_launch": CHEB_BYTES_PER_DOF * nc,
-                         "avg_launch_us": avg_launch_s * 1e6, "launches_timed": prof_n},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": hb.numel() * 8,
-                    "d2h_bytes_per_step": hx.numel() * 8},
-            "gpu_launches": launches, "clocks": clocks.summary(), "cpu_baseline": cpu}
+    if ctx.world == 1 and not args.no_cpu_baseline:
+        v, sample, _ = cpu_oracle_sample(w)
+        cpu = {"value": v, "unit": UNITS[w], "cores": 1, "kind": "oracle", "sample": sample + ", one thread"}
+    line = {"metric": METRIC, "value": body.pop("value"), "unit": UNITS[w], "n_gpus": ctx.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": body.pop("ms_per_step"),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": body.pop("dtype"),
+            "data": "synthetic", "config": config_of(w)}
+    line.update(body)
+    line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    ctx.close()
     return 0
 
 
@@ -343,6 +787,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="poisson3d", choices=WORKLOADS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -181,7 +181,8 @@ typedef struct {
   int precond;           /* eb_pc_kind, default EB_PC_AMG */
   int check_every;       /* host convergence check period in iterations (default 1) */
   int use_graph;         /* capture the iteration in a CUDA graph (default 1) */
-  int profile;           /* 1: time every level-0 smoother launch with CUDA events */
+  int profile;           /* 1: time every level-0 smoother launch with CUDA events; 2 (pcg_solve_nn):
+                            time the learned stage's 32 -> 32 convolution launches instead */
 } pcg_opts;
 
 typedef struct {
@@ -190,7 +191,7 @@ typedef struct {
   double true_rel_residual;  /* ||b - A x|| / ||b|| recomputed at exit */
   double solve_ms;
   int converged;
-  double prof_kernel_ms;     /* with opts.profile: summed duration of the level-0 smoother launches */
+  double prof_kernel_ms;     /* with opts.profile: summed duration of the timed launches */
   int prof_launches;         /* with opts.profile: their number */
   int64_t launches;          /* kernel launches this solve issued */
 } pcg_stats;
@@ -259,6 +260,11 @@ int batch_rhs(const batch_handle* b, const double* f_all, const double* ug_all, 
 /* Fixes the time steps dt[g] (host array) and theta of the theta-method and
  * builds the AMG hierarchy of the batch.  Synchronous. */
 int batch_heat_setup(batch_handle* b, const double* dt, double theta, const amg_opts* opts, cudaStream_t stream);
+/* on != 0: later batch_heat_step calls time every level-0 smoother launch of
+ * their captured PCG iterations with CUDA events and report the summed
+ * duration and the launch count in prof_kernel_ms / prof_launches of every
+ * geometry's stats (batch totals). */
+int batch_set_profile(batch_handle* b, int on);
 /* One theta-method step of every geometry (heat_step semantics, warm start
  * from u), u overwritten.  stats: host array of count entries (may be NULL).
  * Returns EB_ERR_NO_CONVERGENCE if any geometry missed rtol.  Synchronous. */

@@ -97,6 +97,7 @@ _SIGS = {
     "batch_rhs": (C.c_int, [_P, _P, _P, _P, _P]),
     "batch_heat_setup": (C.c_int, [_P, _P, C.c_double, C.POINTER(amg_opts), _P]),
     "batch_heat_step": (C.c_int, [_P, _P, _P, _P, C.c_double, C.c_int, _P, _P]),
+    "batch_set_profile": (C.c_int, [_P, C.c_int]),
     "nn_create": (C.c_int, [C.POINTER(_P), _P]),
     "nn_destroy": (None, [_P]),
     "nn_num_params": (C.c_int, []),
@@ -454,6 +455,9 @@ class Batch:
                allow=(EB_ERR_NO_CONVERGENCE,) if allow_noconv else ())
         return list(st)
 
+    def set_profile(self, on: bool):
+        _check(load().batch_set_profile(self._h, int(bool(on))))
+
 
 class Net:
     """Handle of nn_create: the learned preconditioner stage (a 6-layer BF16
@@ -552,12 +556,13 @@ def precondition_nn(amg: AMG, net: Net, r, out=None, mode=EB_NN_PLAIN, stream=No
 
 
 def solve_nn(amg: AMG, net: Net, b, x=None, rtol=1e-10, maxit=1000, mode=EB_NN_PLAIN, check_every=1, use_graph=1,
-             stream=None, allow_noconv=False):
-    """Flexible PCG with the V-cycle followed by the learned stage (pcg_solve_nn)."""
+             stream=None, allow_noconv=False, profile=0):
+    """Flexible PCG with the V-cycle followed by the learned stage (pcg_solve_nn);
+    profile 2 times the stage's 32 -> 32 convolution launches."""
     import torch
     if x is None:
         x = torch.zeros_like(b)
-    o = pcg_opts(EB_PC_AMG_NN, check_every, use_graph, 0)
+    o = pcg_opts(EB_PC_AMG_NN, check_every, use_graph, int(profile))
     st = pcg_stats()
     _check(load().pcg_solve_nn(amg._h, net.handle, int(mode), _ptr(b), _ptr(x), float(rtol), int(maxit), C.byref(o),
                                C.byref(st), _stream(stream)), allow=(EB_ERR_NO_CONVERGENCE,) if allow_noconv else ())

@@ -766,13 +766,18 @@ static void pack(NN& N, cudaStream_t s, int64_t& nl) {
   ++nl;
 }
 
-// out = N(in) over the stack; the activations stay for backward
-static void forward(NN& N, const Image& im, const float2* in, float* out, cudaStream_t s, int64_t& nl) {
+// out = N(in) over the stack; the activations stay for backward.  prof (may be
+// NULL): a solver timing the 32 -> 32 convolution launches.
+static void forward(NN& N, const Image& im, const float2* in, float* out, cudaStream_t s, int64_t& nl,
+                    Solver* prof = nullptr) {
   const int64_t npx = npx_of(im);
   k_l1_fwd<<<blocks_for(npx, 128), 128, 0, s>>>(im, in, N.P, N.act[1]);
-  for (int l = 0; l < NMID; ++l)
+  for (int l = 0; l < NMID; ++l) {
+    if (prof) prof->prof_mark(s, true, PROF_CONV);
     k_conv32<<<conv_grid(im, 3), 128, conv_smem(), s>>>(im, N.act[l + 1], N.wf + (int64_t)l * WM_N,
                                                          N.P + off_wm(l) + WM_N, N.act[l + 2], 1, nullptr);
+    if (prof) prof->prof_mark(s, false, PROF_CONV);
+  }
   k_l6_fwd<<<blocks_for(npx, 128), 128, 0, s>>>(im, N.act[5], N.P, in, out);
   nl += 6;
   EB_CUDA(cudaGetLastError());
@@ -858,7 +863,7 @@ void nn_stage_prepare(nn_handle* h, const EBHandle& eb, cudaStream_t s) {
 // z = z1 + omega h^2 rms(s) N(s / rms(s), m) with s = r - (sigma I + A) z1 and z1 = z on
 // entry; omega = 1 (EB_NN_PLAIN) or the energy-optimal step (EB_NN_ENERGY)
 void nn_stage_apply(nn_handle* h, const EBHandle& eb, double shift, int mode, const double* r, double* z,
-                    int64_t& nl, cudaStream_t s) {
+                    int64_t& nl, Solver* prof, cudaStream_t s) {
   NN& N = h->n;
   const int64_t nn = eb.g.num_nodes;
   const unsigned nb = grid_blocks(nn);
@@ -868,7 +873,7 @@ void nn_stage_apply(nn_handle* h, const EBHandle& eb, double shift, int mode, co
   k_st_norm<<<1, 32, 0, s>>>(N.spart, (int)nb, (double)eb.num_cp, eb.g.h * eb.g.h, N.scal);
   k_st_input<<<nb, 256, 0, s>>>(nn, eb.code, N.s64, N.scal, N.in);
   const Image im{eb.g.n0, eb.g.n1, eb.g.n1};
-  forward(N, im, N.in, N.out, s, nl);
+  forward(N, im, N.in, N.out, s, nl, prof);
   if (mode == EB_NN_ENERGY) {
     k_st_energy<<<nb, 256, 0, s>>>(G, eb.g.h * eb.g.h, nn, eb.code, eb.diag, N.in, N.out, N.spart);
     k_st_omega<<<1, 32, 0, s>>>(N.spart, (int)nb, N.scal);
@@ -1134,7 +1139,7 @@ int nn_precondition(const amg_handle* amg, nn_handle* nn, int mode, const double
     nn_stage_prepare(nn, *S.eb, stream);
     int64_t nl = 0;
     amg_vcycle_grid(S, r_dev, z_dev, stream);
-    nn_stage_apply(nn, *S.eb, S.shift, mode, r_dev, z_dev, nl, stream);
+    nn_stage_apply(nn, *S.eb, S.shift, mode, r_dev, z_dev, nl, nullptr, stream);
     EB_CUDA(cudaGetLastError());
   });
 }

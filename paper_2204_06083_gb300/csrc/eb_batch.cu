@@ -59,6 +59,9 @@ struct Batch {
   const double* g_b = nullptr;
   double* g_x = nullptr;
   int64_t g_launches = 0, nlaunch = 0;
+  // event timing of the level-0 smoother launches inside the captured iteration
+  bool profile = false;
+  int g_prof = -1, g_pairs = 0;
   int ngeo() const { return (int)geo.size(); }
 };
 
@@ -535,7 +538,8 @@ static void b_iteration(Batch& B, double* x, bool flex, cudaStream_t s) {
 }
 
 static void b_graph_prepare(Batch& B, const double* b, double* x, bool flex, cudaStream_t s) {
-  if (B.gexec && B.g_b == b && B.g_x == x) return;
+  if (B.gexec && B.g_b == b && B.g_x == x && B.g_prof == (int)B.profile) return;
+  Solver& S = *B.S;
   if (B.gexec) cudaGraphExecDestroy(B.gexec);
   B.gexec = nullptr;
   if (!B.cap_stream) EB_CUDA(cudaStreamCreateWithFlags(&B.cap_stream, cudaStreamNonBlocking));
@@ -544,10 +548,16 @@ static void b_graph_prepare(Batch& B, const double* b, double* x, bool flex, cud
   EB_CUDA(cudaEventRecord(fork, s));
   EB_CUDA(cudaStreamWaitEvent(B.cap_stream, fork, 0));
   const int64_t n0 = B.nlaunch;
+  // the graph records event pairs 0 .. g_pairs-1 around its level-0 smoother launches
+  S.prof_on = B.profile;
+  S.prof_n = 0;
   EB_CUDA(cudaStreamBeginCapture(B.cap_stream, cudaStreamCaptureModeThreadLocal));
   b_iteration(B, x, flex, B.cap_stream);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(B.cap_stream, &graph);
+  S.prof_on = false;
+  B.g_pairs = S.prof_n;
+  B.g_prof = (int)B.profile;
   cudaEventDestroy(fork);
   EB_CUDA(e);
   e = cudaGraphInstantiate(&B.gexec, graph, 0);
@@ -575,6 +585,10 @@ static int batch_pcg(Batch& B, const double* b, double* x, double rtol, int maxi
   std::vector<int> iters(ng, 0), flags(ng, 0), conv(ng, 0);
   std::vector<double> rel(ng, 0.0);
   B.nlaunch = 0;
+  S.prof_on = false;
+  S.prof_what = PROF_SMOOTHER;
+  S.prof_acc_ms = 0.0;
+  S.prof_acc_n = 0;
   for (int restart = 0; restart < 4; ++restart) {
     EB_CUDA(cudaMemcpyAsync(B.sc, init.data(), sizeof(PcgScalars) * ng, cudaMemcpyHostToDevice, s));
     B.nlaunch += 2;
@@ -596,6 +610,7 @@ static int batch_pcg(Batch& B, const double* b, double* x, double rtol, int maxi
         ++it;
         EB_CUDA(cudaMemcpyAsync(B.sc_host, B.sc, sizeof(PcgScalars) * ng, cudaMemcpyDeviceToHost, s));
         EB_CUDA(cudaStreamSynchronize(s));
+        if (B.profile) S.prof_collect(0, B.g_pairs);
         bool all = true;
         for (int g = 0; g < ng; ++g) all = all && B.sc_host[g].done;
         if (all) break;
@@ -635,6 +650,8 @@ static int batch_pcg(Batch& B, const double* b, double* x, double rtol, int maxi
       stats[g].solve_ms = ms;
       stats[g].converged = conv[g];
       stats[g].launches = B.nlaunch;
+      stats[g].prof_kernel_ms = S.prof_acc_ms;
+      stats[g].prof_launches = S.prof_acc_n;
     }
     if (flags[g] & PCG_FLAG_NONFINITE) worst = EB_ERR_NONFINITE;
     else if ((flags[g] & PCG_FLAG_BREAKDOWN) && worst == EB_OK) worst = EB_ERR_BREAKDOWN;
@@ -802,6 +819,15 @@ int batch_heat_setup(batch_handle* b, const double* dt, double theta, const amg_
     EB_CUDA(cudaStreamSynchronize(stream));
     S.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   });
+}
+
+int batch_set_profile(batch_handle* b, int on) {
+  if (!b) {
+    set_error("batch_set_profile: NULL handle");
+    return EB_ERR_INVALID;
+  }
+  b->b.profile = on != 0;
+  return EB_OK;
 }
 
 int batch_heat_step(batch_handle* b, const double* b1_all, const double* b0_all, double* u_all, double rtol,

@@ -349,7 +349,7 @@ void Solver::precondition(int kind, const double* rin, double* zout, cudaStream_
   const TileView tv = eb->tv();
   if (kind == EB_PC_AMG_NN) {
     amg_vcycle_grid(*this, rin, zout, s);
-    nn_stage_apply(nn, *eb, shift, nn_mode, rin, zout, nlaunch, s);
+    nn_stage_apply(nn, *eb, shift, nn_mode, rin, zout, nlaunch, this, s);
     EB_DIM_LAUNCH(dim, k_dot2, nblk, tv, rin, zout, zold, part);
   } else if (kind == EB_PC_AMG && H) {
     amg_vcycle_grid(*this, rin, zout, s);
@@ -380,7 +380,7 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
   EB_REQUIRE(rtol > 0.0 && maxit >= 0, EB_ERR_INVALID, "rtol must be > 0 and maxit >= 0");
   EB_REQUIRE(b != x, EB_ERR_INVALID, "pcg: b and x must be different buffers");
   const int check = std::max(1, o.check_every);
-  prof_begin(o.profile != 0, s);
+  prof_begin(o.profile, s);
   nlaunch = 0;
   auto t0 = std::chrono::steady_clock::now();
   PcgScalars init{};
@@ -423,7 +423,7 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
       const int nb = std::min(check, maxit - (total_iters + it));
       bool graphed = false;
       if (o.use_graph && nb == check) {
-        graph_prepare(kind, b, x, check, prof_on, s);
+        graph_prepare(kind, b, x, check, prof_on ? prof_what : 0, s);
         EB_CUDA(cudaGraphLaunch(gexec, s));
         nlaunch += g_launches;
         graphed = true;
@@ -512,8 +512,8 @@ void Solver::iteration(int kind, const double* b, double* x, cudaStream_t s) {
 // Captures `iters` iterations into a CUDA graph (once per argument set).  The
 // capture runs on a private stream forked from s, so s may be the legacy
 // default stream.
-void Solver::graph_prepare(int kind, const double* b, double* x, int iters, bool profile, cudaStream_t s) {
-  if (gexec && g_b == b && g_x == x && g_iters == iters && g_kind == kind && g_prof == (int)profile && g_nn == nn &&
+void Solver::graph_prepare(int kind, const double* b, double* x, int iters, int profile, cudaStream_t s) {
+  if (gexec && g_b == b && g_x == x && g_iters == iters && g_kind == kind && g_prof == profile && g_nn == nn &&
       g_nn_mode == nn_mode)
     return;
   if (prof_on) {  // settle event pairs recorded so far before the capture reuses them
@@ -544,7 +544,7 @@ void Solver::graph_prepare(int kind, const double* b, double* x, int iters, bool
   g_x = x;
   g_iters = iters;
   g_kind = kind;
-  g_prof = (int)profile;
+  g_prof = profile;
   g_nn = nn;
   g_nn_mode = nn_mode;
 }
@@ -567,8 +567,9 @@ static bool capturing(cudaStream_t s) {
 // that dominates an AMG-PCG iteration), on the stream they are launched on.
 // Inside a captured iteration the event records are graph nodes, so the
 // pairs time the kernels back to back, without host-enqueue gaps.
-void Solver::prof_begin(bool on, cudaStream_t) {
-  prof_on = on;
+void Solver::prof_begin(int mode, cudaStream_t) {
+  prof_on = mode != 0;
+  prof_what = mode == PROF_CONV ? PROF_CONV : PROF_SMOOTHER;
   prof_n = g_pairs;
   prof_acc_ms = 0.0;
   prof_acc_n = 0;
@@ -583,8 +584,8 @@ void Solver::prof_collect(int first, int count) {
   }
 }
 
-void Solver::prof_mark(cudaStream_t s, bool start) {
-  if (!prof_on) return;
+void Solver::prof_mark(cudaStream_t s, bool start, int what) {
+  if (!prof_on || what != prof_what) return;
   if (start) {
     if (prof_n >= (int)prof_ev.size()) {
       cudaEvent_t a, b;

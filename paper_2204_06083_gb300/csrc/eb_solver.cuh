@@ -11,6 +11,8 @@ namespace ebk {
 // FIN_RZ0F / FIN_BETAF: flexible CG, partials are pairs (r.z, r.z_previous)
 enum { FIN_INIT = 0, FIN_RZ0 = 1, FIN_ALPHA = 2, FIN_RR = 3, FIN_BETA = 4, FIN_RZ0F = 5, FIN_BETAF = 6 };
 enum { PCG_FLAG_NONFINITE = 1, PCG_FLAG_BREAKDOWN = 2 };
+// what pcg_opts.profile times: the level-0 smoother launches or the learned stage's 32 -> 32 convolutions
+enum { PROF_SMOOTHER = 1, PROF_CONV = 2 };
 
 struct PcgScalars {
   double bb, rr, rz, pq, alpha, beta, tol2;
@@ -40,6 +42,7 @@ struct Solver {
   int64_t nlaunch = 0;  // kernel launches issued (reported per solve)
   // event timing of the level-0 smoother launches
   bool prof_on = false;
+  int prof_what = PROF_SMOOTHER;
   int prof_n = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
   double prof_acc_ms = 0.0;
@@ -61,13 +64,13 @@ struct Solver {
   int pcg(const double* b, double* x, double rtol, int maxit, const pcg_opts& o, pcg_stats* stats, cudaStream_t s);
   int heat(double dt, double theta, const double* b1, const double* b0, double* u, double rtol, int maxit,
            pcg_stats* stats, cudaStream_t s);
-  void prof_begin(bool on, cudaStream_t s);
-  void prof_mark(cudaStream_t s, bool start);
+  void prof_begin(int mode, cudaStream_t s);
+  void prof_mark(cudaStream_t s, bool start, int what = PROF_SMOOTHER);
   void prof_collect(int first, int count);
   void prof_end(pcg_stats* st, cudaStream_t s);
   void prof_release();
   void iteration(int kind, const double* b, double* x, cudaStream_t s);
-  void graph_prepare(int kind, const double* b, double* x, int iters, bool profile, cudaStream_t s);
+  void graph_prepare(int kind, const double* b, double* x, int iters, int profile, cudaStream_t s);
   void graph_release();
 };
 
@@ -82,7 +85,7 @@ void amg_copy_level(const Solver& S, int level, int which, int32_t* rowptr, int3
 // then z <- z + omega h^2 rms(s) N(s / rms(s), m), s = r - (shift I + A) z
 void nn_stage_prepare(nn_handle* nn, const EBHandle& eb, cudaStream_t s);
 void nn_stage_apply(nn_handle* nn, const EBHandle& eb, double shift, int mode, const double* r, double* z,
-                    int64_t& nlaunch, cudaStream_t s);
+                    int64_t& nlaunch, Solver* prof, cudaStream_t s);
 
 }  // namespace ebk
 
