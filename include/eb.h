@@ -137,6 +137,30 @@ int eb_rhs(const eb_handle* eb, const double* f_dev, const double* ugamma_dev, d
  * free.  x and y have the element type of prec (double, float, bf16). */
 int eb_apply(const eb_handle* eb, int prec, const void* x_dev, void* y_dev, cudaStream_t stream);
 
+/* --------------------------------------------------------------- tile shapes
+ * The grid kernels walk the "active tiles" of a grid: blocks of 256 nodes,
+ * tile[0] x tile[1] x tile[2] with power-of-two extents, x fastest (eb_info
+ * reports the shape in use; eb_build starts from 32 x 8 in 2D and 16 x 4 x 4
+ * in 3D).  The shape changes how the work is cut into CTAs, never a result.
+ * The paper has no counterpart: this is how the library is fitted to a GPU. */
+typedef struct {
+  int count;         /* candidate shapes timed */
+  int tile[16][3];   /* the candidates */
+  double us[16];     /* mean duration of the timed operation with each (microseconds) */
+  int best;          /* index of the shape in use on return */
+} eb_tune_t;
+
+/* Rebuilds the active-tile list of eb for the given shape (powers of two,
+ * product 256, 2 <= tile[0] <= 128, tile[1], tile[2] <= 128, tile[2] = 1 in
+ * 2D; EB_ERR_INVALID otherwise).  Hierarchies and captured iterations built on
+ * eb stay valid (their next solve captures again).  Do not call while work on
+ * eb is in flight on another stream.  Synchronous. */
+int eb_retile(eb_handle* eb, const int tile[3], cudaStream_t stream);
+/* Autotuner: for each candidate shape, times `reps` eb_apply launches of
+ * precision prec with CUDA events on stream, and keeps the fastest shape.
+ * out (may be NULL) receives the timings.  Synchronous. */
+int eb_autotune(eb_handle* eb, int prec, int reps, eb_tune_t* out, cudaStream_t stream);
+
 /* ---------------------------------------------------------------- AMG + PCG */
 /* EB_PC_AMG_NN (V-cycle followed by the learned stage) is selected by
  * pcg_solve_nn only; pcg_solve rejects it. */
@@ -176,6 +200,10 @@ int amg_level_copy(const amg_handle* amg, int level, int which, int32_t* rowptr_
                    double* val_dev, cudaStream_t stream);
 /* z = M^-1 r: one symmetric V-cycle (Chebyshev pre/post smoothing). */
 int amg_vcycle(const amg_handle* amg, const double* r_dev, double* z_dev, cudaStream_t stream);
+/* Tile-shape autotuner for a solve: retiles the hierarchy's grid with each
+ * candidate shape, times `reps` V-cycles, keeps the fastest (see eb_autotune).
+ * Synchronous. */
+int amg_autotune(amg_handle* amg, int reps, eb_tune_t* out, cudaStream_t stream);
 
 typedef struct {
   int precond;           /* eb_pc_kind, default EB_PC_AMG */
@@ -260,6 +288,10 @@ int batch_rhs(const batch_handle* b, const double* f_all, const double* ug_all, 
 /* Fixes the time steps dt[g] (host array) and theta of the theta-method and
  * builds the AMG hierarchy of the batch.  Synchronous. */
 int batch_heat_setup(batch_handle* b, const double* dt, double theta, const amg_opts* opts, cudaStream_t stream);
+/* Tile-shape autotuner for a batch (after batch_heat_setup): retiles every
+ * geometry and the batch with each candidate 2D shape, times `reps` V-cycles
+ * of the batch hierarchy, keeps the fastest.  Synchronous. */
+int batch_autotune(batch_handle* b, int reps, eb_tune_t* out, cudaStream_t stream);
 /* on != 0: later batch_heat_step calls time every level-0 smoother launch of
  * their captured PCG iterations with CUDA events and report the summed
  * duration and the launch count in prof_kernel_ms / prof_launches of every

@@ -70,6 +70,25 @@ class pcg_stats(C.Structure):
                 ("prof_launches", C.c_int), ("launches", C.c_int64)]
 
 
+class eb_tune_t(C.Structure):
+    _fields_ = [("count", C.c_int), ("tile", (C.c_int * 3) * 16), ("us", C.c_double * 16), ("best", C.c_int)]
+
+
+@dataclass
+class TuneResult:
+    shapes: list
+    us: list
+    best: int
+
+    @property
+    def shape(self):
+        return self.shapes[self.best]
+
+
+def _tune_result(t: eb_tune_t) -> TuneResult:
+    return TuneResult([tuple(t.tile[i]) for i in range(t.count)], [t.us[i] for i in range(t.count)], t.best)
+
+
 _P = C.c_void_p
 _SIGS = {
     "eb_build": (C.c_int, [C.POINTER(eb_grid), C.POINTER(eb_levelset), C.POINTER(_P), _P]),
@@ -80,6 +99,10 @@ _SIGS = {
     "eb_cuts": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "eb_rhs": (C.c_int, [_P, _P, _P, _P, _P]),
     "eb_apply": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "eb_retile": (C.c_int, [_P, _P, _P]),
+    "eb_autotune": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(eb_tune_t), _P]),
+    "amg_autotune": (C.c_int, [_P, C.c_int, C.POINTER(eb_tune_t), _P]),
+    "batch_autotune": (C.c_int, [_P, C.c_int, C.POINTER(eb_tune_t), _P]),
     "amg_setup": (C.c_int, [_P, C.c_double, C.POINTER(amg_opts), C.POINTER(_P), _P]),
     "amg_destroy": (None, [_P]),
     "amg_info": (C.c_int, [_P, C.POINTER(amg_info_t)]),
@@ -282,6 +305,24 @@ class EB:
         _check(load().eb_apply(self._h, prec, _ptr(x), _ptr(out), _stream(stream)))
         return out
 
+    def _refresh_info(self):
+        inf = eb_info_t()
+        _check(load().eb_info(self._h, C.byref(inf)))
+        self.info = Info(inf.num_nodes, inf.num_cp, inf.num_bp, inf.num_cut, inf.num_far, inf.num_tiles,
+                         tuple(inf.tile), inf.max_delta_over_h, inf.min_abs_psi)
+
+    def retile(self, shape, stream=None):
+        t = (C.c_int * 3)(*[int(v) for v in shape])
+        _check(load().eb_retile(self._h, C.cast(t, C.c_void_p), _stream(stream)))
+        self._refresh_info()
+
+    def autotune(self, prec=EB_F64, reps=20, stream=None) -> TuneResult:
+        """Times eb_apply for every candidate tile shape and keeps the fastest."""
+        t = eb_tune_t()
+        _check(load().eb_autotune(self._h, int(prec), int(reps), C.byref(t), _stream(stream)))
+        self._refresh_info()
+        return _tune_result(t)
+
     def wave_step(self, u_prev, u_cur, dt, nsteps, stream=None):
         import torch
         prec = {torch.float64: EB_F64, torch.float32: EB_F32}[u_cur.dtype]
@@ -297,6 +338,7 @@ class AMG:
         lib = load()
         self.eb = eb
         self.shift = shift
+        self.vcycle_prec = vcycle_prec
         o = amg_opts(max_levels, coarse_max, strength, cheb_degree, vcycle_prec)
         self._h = C.c_void_p()
         _check(lib.amg_setup(eb.handle, float(shift), C.byref(o), C.byref(self._h), _stream(stream)))
@@ -361,6 +403,13 @@ class AMG:
         _check(load().pcg_solve(self._h, _ptr(b), _ptr(x), float(rtol), int(maxit), C.byref(o), C.byref(st),
                                 _stream(stream)), allow=(EB_ERR_NO_CONVERGENCE,) if allow_noconv else ())
         return x, st
+
+    def autotune(self, reps=20, stream=None) -> TuneResult:
+        """Times V-cycles for every candidate tile shape of the grid and keeps the fastest."""
+        t = eb_tune_t()
+        _check(load().amg_autotune(self._h, int(reps), C.byref(t), _stream(stream)))
+        self.eb._refresh_info()
+        return _tune_result(t)
 
     def heat_step(self, u, b1, dt, theta=1.0, b0=None, rtol=1e-10, maxit=1000, stream=None):
         st = pcg_stats()
@@ -457,6 +506,12 @@ class Batch:
 
     def set_profile(self, on: bool):
         _check(load().batch_set_profile(self._h, int(bool(on))))
+
+    def autotune(self, reps=10, stream=None) -> TuneResult:
+        """Times batch V-cycles for every candidate 2D tile shape and keeps the fastest."""
+        t = eb_tune_t()
+        _check(load().batch_autotune(self._h, int(reps), C.byref(t), _stream(stream)))
+        return _tune_result(t)
 
 
 class Net:

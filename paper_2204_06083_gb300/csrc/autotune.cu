@@ -1,0 +1,147 @@
+// Tile-shape autotuner.  The active-tile kernels cut the grid into blocks of
+// 256 nodes whose extents are powers of two; the shape only changes how the
+// work is split into CTAs and how far apart in memory the rows of one tile
+// lie, never a result.  The tuner rebuilds the tile list for each candidate
+// shape, times the operation it is asked about with CUDA events on the
+// caller's stream, and keeps the fastest shape.
+#include "eb_solver.cuh"
+
+#include <vector>
+
+namespace ebk {
+
+std::vector<TileDims> tile_candidates(int dim) {
+  if (dim == 2) return {{32, 8, 1}, {64, 4, 1}, {16, 16, 1}, {128, 2, 1}, {8, 32, 1}};
+  return {{16, 4, 4}, {32, 4, 2}, {8, 8, 4}, {16, 8, 2}, {32, 2, 4}, {64, 2, 2},
+          {8, 4, 8}, {16, 2, 8}, {32, 8, 1}, {64, 4, 1}};
+}
+
+double time_us(const std::function<void()>& op, int reps, cudaStream_t s) {
+  for (int i = 0; i < 3; ++i) op();
+  cudaEvent_t a, b;
+  EB_CUDA(cudaEventCreate(&a));
+  cudaError_t e = cudaEventCreate(&b);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(a);
+    EB_CUDA(e);
+  }
+  float ms = 0.0f;
+  try {
+    EB_CUDA(cudaEventRecord(a, s));
+    for (int i = 0; i < reps; ++i) op();
+    EB_CUDA(cudaEventRecord(b, s));
+    EB_CUDA(cudaEventSynchronize(b));
+    EB_CUDA(cudaEventElapsedTime(&ms, a, b));
+  } catch (...) {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    throw;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return 1000.0 * ms / reps;
+}
+
+void run_tuner(int dim, const std::function<void(const TileDims&)>& retile, const std::function<void()>& op,
+               int reps, eb_tune_t* out, cudaStream_t s) {
+  EB_REQUIRE(reps >= 1 && reps <= 100000, EB_ERR_INVALID, "autotune: reps in [1, 100000]");
+  const std::vector<TileDims> cand = tile_candidates(dim);
+  eb_tune_t r{};
+  r.count = (int)cand.size();
+  int best = 0;
+  for (int i = 0; i < r.count; ++i) {
+    retile(cand[i]);
+    r.tile[i][0] = cand[i].x;
+    r.tile[i][1] = cand[i].y;
+    r.tile[i][2] = cand[i].z;
+    r.us[i] = time_us(op, reps, s);
+    if (r.us[i] < r.us[best]) best = i;
+  }
+  if (best != r.count - 1) retile(cand[best]);
+  r.best = best;
+  if (out) *out = r;
+}
+
+}  // namespace ebk
+
+using namespace ebk;
+
+extern "C" {
+
+int eb_retile(eb_handle* eb, const int tile[3], cudaStream_t stream) {
+  if (!eb || !tile) {
+    set_error("eb_retile: NULL argument");
+    return EB_ERR_INVALID;
+  }
+  return guarded([&] {
+    build_tiles(eb->h, tile[0], tile[1], tile[2], stream);
+    EB_CUDA(cudaStreamSynchronize(stream));
+  });
+}
+
+int eb_autotune(eb_handle* eb, int prec, int reps, eb_tune_t* out, cudaStream_t stream) {
+  if (!eb) {
+    set_error("eb_autotune: NULL handle");
+    return EB_ERR_INVALID;
+  }
+  if (prec != EB_F64 && prec != EB_F32 && prec != EB_BF16) {
+    set_error("eb_autotune: prec must be EB_F64, EB_F32 or EB_BF16");
+    return EB_ERR_INVALID;
+  }
+  return guarded([&] {
+    EBHandle& E = eb->h;
+    const int64_t nn = E.g.num_nodes;
+    const size_t es = prec == EB_F64 ? 8 : (prec == EB_F32 ? 4 : 2);
+    uint8_t* x = dalloc<uint8_t>(nn * es, stream);
+    uint8_t* y = nullptr;
+    try {
+      y = dalloc<uint8_t>(nn * es, stream);
+      auto op = [&] {
+        if (prec == EB_F64)
+          launch_apply<double>(E, reinterpret_cast<double*>(x), reinterpret_cast<double*>(y), 0.0, stream);
+        else if (prec == EB_F32)
+          launch_apply<float>(E, reinterpret_cast<float*>(x), reinterpret_cast<float*>(y), 0.0, stream);
+        else
+          launch_apply<__nv_bfloat16>(E, reinterpret_cast<__nv_bfloat16*>(x), reinterpret_cast<__nv_bfloat16*>(y),
+                                      0.0, stream);
+      };
+      run_tuner(E.g.dim, [&](const TileDims& t) { build_tiles(E, t.x, t.y, t.z, stream); }, op, reps, out, stream);
+    } catch (...) {
+      dfree(x, stream);
+      dfree(y, stream);
+      throw;
+    }
+    dfree(x, stream);
+    dfree(y, stream);
+    EB_CUDA(cudaStreamSynchronize(stream));
+  });
+}
+
+int amg_autotune(amg_handle* amg, int reps, eb_tune_t* out, cudaStream_t stream) {
+  if (!amg) {
+    set_error("amg_autotune: NULL handle");
+    return EB_ERR_INVALID;
+  }
+  return guarded([&] {
+    Solver& S = amg->s;
+    EB_REQUIRE(S.H != nullptr, EB_ERR_INVALID, "amg_autotune: handle has no hierarchy");
+    EBHandle& E = *S.eb;
+    const int64_t nn = E.g.num_nodes;
+    double* r = dalloc<double>(nn, stream);
+    double* z = nullptr;
+    try {
+      z = dalloc<double>(nn, stream);
+      run_tuner(E.g.dim, [&](const TileDims& t) { build_tiles(E, t.x, t.y, t.z, stream); },
+                [&] { amg_vcycle_grid(S, r, z, stream); }, reps, out, stream);
+    } catch (...) {
+      dfree(r, stream);
+      dfree(z, stream);
+      throw;
+    }
+    dfree(r, stream);
+    dfree(z, stream);
+    EB_CUDA(cudaStreamSynchronize(stream));
+  });
+}
+
+}  // extern "C"

@@ -105,6 +105,8 @@ __global__ void k_tile_shift(int64_t nt, const int32_t* tile_geo, const GeoConst
   t32[t] = make_float2((float)sig, (float)di);
 }
 
+static void batch_tiles(Batch& B, cudaStream_t s);
+
 static void build_batch(Batch& B, const eb_grid* grids, const eb_levelset* lss, int count, cudaStream_t s) {
   EB_REQUIRE(count >= 1, EB_ERR_INVALID, "batch_build: need at least one geometry");
   B.home = s;
@@ -118,7 +120,6 @@ static void build_batch(Batch& B, const eb_grid* grids, const eb_levelset* lss, 
   B.node_off.assign(count + 1, 0);
   B.cut_off.assign(count + 1, 0);
   B.cp_off.assign(count + 1, 0);
-  B.tile_off.assign(count + 1, 0);
   for (int g = 0; g < count; ++g) {
     eb_handle* e = new eb_handle();
     B.geo.push_back(e);
@@ -126,10 +127,9 @@ static void build_batch(Batch& B, const eb_grid* grids, const eb_levelset* lss, 
     B.node_off[g + 1] = B.node_off[g] + S * (int64_t)grids[g].n[1];
     B.cut_off[g + 1] = B.cut_off[g] + e->h.num_cut;
     B.cp_off[g + 1] = B.cp_off[g] + e->h.num_cp;
-    B.tile_off[g + 1] = B.tile_off[g] + e->h.num_tiles;
     rows += grids[g].n[1];
   }
-  const int64_t nn = B.node_off[count], ncp = B.cp_off[count], ncut = B.cut_off[count], nt = B.tile_off[count];
+  const int64_t nn = B.node_off[count], ncp = B.cp_off[count], ncut = B.cut_off[count];
   EB_REQUIRE(nn < ((int64_t)1 << 31) - 1, EB_ERR_INVALID, "batch_build: batch above 2^31 nodes");
   EBHandle& V = B.view;
   V.home = s;
@@ -141,26 +141,14 @@ static void build_batch(Batch& B, const eb_grid* grids, const eb_levelset* lss, 
   G.num_nodes = nn;
   G.lo[0] = G.lo[1] = G.lo[2] = 0.0;
   G.h = 1.0;
-  G.tx = TileShape<2>::X;
-  G.ty = TileShape<2>::Y;
-  G.tz = 1;
-  G.ntx = (int)((S + G.tx - 1) / G.tx);
-  G.nty = (int)((rows + G.ty - 1) / G.ty);
-  G.ntz = 1;
   V.num_cp = ncp;
   V.num_cut = ncut;
-  V.num_tiles = nt;
   V.code = dalloc<uint8_t>(nn, s);
   V.diag = dalloc<double>(nn, s);
   V.diag32 = dalloc<float>(nn, s);
   V.cp_of_node = dalloc<int32_t>(nn, s, false);
   k_fill_i32<<<blocks_for(nn, 256), 256, 0, s>>>(nn, -1, V.cp_of_node);
   V.cp_node = dalloc<int32_t>(ncp, s, false);
-  V.tile_base = dalloc<int32_t>(nt, s, false);
-  V.tile_lim = dalloc<int32_t>(nt, s, false);
-  V.tile_shift64 = dalloc<double2>(nt, s);
-  V.tile_shift32 = dalloc<float2>(nt, s);
-  B.tile_geo = dalloc<int32_t>(nt, s, false);
   B.cut_off_cp = dalloc<int32_t>(ncp + 1, s, false);
   B.cut_c = dalloc<double>(ncut, s, false);
   for (int g = 0; g < count; ++g) {
@@ -173,30 +161,71 @@ static void build_batch(Batch& B, const eb_grid* grids, const eb_levelset* lss, 
                               cudaMemcpyDeviceToDevice, s));
     k_offset_cp<<<blocks_for(S * n1, 256), 256, 0, s>>>(S * n1, V.cp_of_node + off, (int32_t)B.cp_off[g]);
     k_map_cp<<<blocks_for(h.num_cp, 256), 256, 0, s>>>(h.num_cp, h.cp_node, h.g.n0, S, off, V.cp_node + B.cp_off[g]);
-    k_rebase_tiles<<<blocks_for(h.num_tiles, 256), 256, 0, s>>>(h.num_tiles, h.tile_base, h.g.n0, S, off,
-                                                                V.tile_base + B.tile_off[g]);
-    EB_CUDA(cudaMemcpyAsync(V.tile_lim + B.tile_off[g], h.tile_lim, 4 * h.num_tiles, cudaMemcpyDeviceToDevice, s));
-    k_fill_i32<<<blocks_for(h.num_tiles, 256), 256, 0, s>>>(h.num_tiles, g, B.tile_geo + B.tile_off[g]);
     k_add_i32<<<blocks_for(h.num_cp, 256), 256, 0, s>>>(h.num_cp, h.cut_off, (int32_t)B.cut_off[g],
                                                           B.cut_off_cp + B.cp_off[g]);
     if (h.num_cut)
       EB_CUDA(cudaMemcpyAsync(B.cut_c + B.cut_off[g], h.cut_c, 8 * h.num_cut, cudaMemcpyDeviceToDevice, s));
   }
-  std::vector<int32_t> gt0(count + 1);
-  for (int g = 0; g <= count; ++g) gt0[g] = (int32_t)B.tile_off[g];
   const int32_t ncut32 = (int32_t)ncut;
   EB_CUDA(cudaMemcpyAsync(B.cut_off_cp + ncp, &ncut32, 4, cudaMemcpyHostToDevice, s));
-  B.geo_tile0 = dalloc<int32_t>(count + 1, s, false);
-  EB_CUDA(cudaMemcpyAsync(B.geo_tile0, gt0.data(), 4 * (count + 1), cudaMemcpyHostToDevice, s));
   B.gconst = dalloc<GeoConst>(count, s);
   B.hconst.resize(count);
   for (int g = 0; g < count; ++g) B.hconst[g] = GeoConst{grids[g].h * grids[g].h, 1.0, 1.0};
   EB_CUDA(cudaMemcpyAsync(B.gconst, B.hconst.data(), sizeof(GeoConst) * count, cudaMemcpyHostToDevice, s));
   B.sc = dalloc<PcgScalars>(count, s);
   EB_CUDA(cudaMallocHost((void**)&B.sc_host, sizeof(PcgScalars) * count));
-  B.part = dalloc<double>(2 * std::max<int64_t>(nt, 1), s);
-  EB_CUDA(cudaStreamSynchronize(s));  // the host vectors above are read by the async copies
+  EB_CUDA(cudaStreamSynchronize(s));  // the host values above are read by the async copies
+  batch_tiles(B, s);
   EB_CUDA(cudaGetLastError());
+}
+
+// (Re)builds the batch view's tile list from the geometries' tile lists (all
+// geometries share one tile shape), with the per-tile geometry ids, shifts and
+// reduction partials that depend on it.  Drops the captured iteration.
+static void batch_tiles(Batch& B, cudaStream_t s) {
+  EBHandle& V = B.view;
+  const int count = B.ngeo();
+  const Geometry& g0 = B.geo[0]->h.g;
+  for (int g = 1; g < count; ++g)
+    EB_REQUIRE(B.geo[g]->h.g.tx == g0.tx && B.geo[g]->h.g.ty == g0.ty, EB_ERR_INVALID,
+               "batch: the geometries have different tile shapes");
+  B.tile_off.assign(count + 1, 0);
+  for (int g = 0; g < count; ++g) B.tile_off[g + 1] = B.tile_off[g] + B.geo[g]->h.num_tiles;
+  const int64_t nt = B.tile_off[count];
+  if (B.gexec) cudaGraphExecDestroy(B.gexec);
+  B.gexec = nullptr;
+  dfree(V.tile_base, s); dfree(V.tile_lim, s); dfree(V.tile_shift64, s); dfree(V.tile_shift32, s);
+  dfree(B.tile_geo, s); dfree(B.geo_tile0, s); dfree(B.part, s);
+  V.num_tiles = 0;
+  Geometry& G = V.g;
+  G.tx = g0.tx;
+  G.ty = g0.ty;
+  G.tz = 1;
+  G.ntx = (int)((G.n0 + G.tx - 1) / G.tx);
+  G.nty = (int)((G.n1 + G.ty - 1) / G.ty);
+  G.ntz = 1;
+  V.tile_base = dalloc<int32_t>(nt, s, false);
+  V.tile_lim = dalloc<int32_t>(nt, s, false);
+  V.tile_shift64 = dalloc<double2>(nt, s);
+  V.tile_shift32 = dalloc<float2>(nt, s);
+  B.tile_geo = dalloc<int32_t>(nt, s, false);
+  B.part = dalloc<double>(2 * std::max<int64_t>(nt, 1), s);
+  B.geo_tile0 = dalloc<int32_t>(count + 1, s, false);
+  for (int g = 0; g < count; ++g) {
+    const EBHandle& h = B.geo[g]->h;
+    k_rebase_tiles<<<blocks_for(h.num_tiles, 256), 256, 0, s>>>(h.num_tiles, h.tile_base, h.g.n0, B.stride,
+                                                                B.node_off[g], V.tile_base + B.tile_off[g]);
+    EB_CUDA(cudaMemcpyAsync(V.tile_lim + B.tile_off[g], h.tile_lim, 4 * h.num_tiles, cudaMemcpyDeviceToDevice, s));
+    k_fill_i32<<<blocks_for(h.num_tiles, 256), 256, 0, s>>>(h.num_tiles, g, B.tile_geo + B.tile_off[g]);
+  }
+  std::vector<int32_t> gt0(count + 1);
+  for (int g = 0; g <= count; ++g) gt0[g] = (int32_t)B.tile_off[g];
+  EB_CUDA(cudaMemcpyAsync(B.geo_tile0, gt0.data(), 4 * (count + 1), cudaMemcpyHostToDevice, s));
+  V.num_tiles = nt;
+  k_tile_shift<<<blocks_for(nt, 256), 256, 0, s>>>(nt, B.tile_geo, B.gconst, V.tile_shift64, V.tile_shift32);
+  EB_CUDA(cudaGetLastError());
+  ++V.tile_gen;
+  EB_CUDA(cudaStreamSynchronize(s));  // gt0 is read by the copy above
 }
 
 static void destroy_batch(Batch& B) {
@@ -818,6 +847,35 @@ int batch_heat_setup(batch_handle* b, const double* dt, double theta, const amg_
     amg_build_from(S, A0, stream);
     EB_CUDA(cudaStreamSynchronize(stream));
     S.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  });
+}
+
+int batch_autotune(batch_handle* b, int reps, eb_tune_t* out, cudaStream_t stream) {
+  if (!b) {
+    set_error("batch_autotune: NULL handle");
+    return EB_ERR_INVALID;
+  }
+  return guarded([&] {
+    Batch& B = b->b;
+    EB_REQUIRE(B.S != nullptr, EB_ERR_INVALID, "batch_autotune: call batch_heat_setup first");
+    const int64_t nn = B.view.g.num_nodes;
+    double* r = dalloc<double>(nn, stream);
+    double* z = nullptr;
+    try {
+      z = dalloc<double>(nn, stream);
+      auto retile = [&](const TileDims& t) {
+        for (eb_handle* e : B.geo) build_tiles(e->h, t.x, t.y, t.z, stream);
+        batch_tiles(B, stream);
+      };
+      run_tuner(2, retile, [&] { amg_vcycle_grid(*B.S, r, z, stream); }, reps, out, stream);
+    } catch (...) {
+      dfree(r, stream);
+      dfree(z, stream);
+      throw;
+    }
+    dfree(r, stream);
+    dfree(z, stream);
+    EB_CUDA(cudaStreamSynchronize(stream));
   });
 }
 

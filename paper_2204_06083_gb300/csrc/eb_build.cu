@@ -353,14 +353,6 @@ void build_handle(EBHandle& eb, const eb_grid& grid, const eb_levelset& ls, cuda
   G.num_nodes = nn;
   for (int a = 0; a < 3; ++a) G.lo[a] = grid.lo[a];
   G.h = grid.h;
-  if (grid.dim == 2) {
-    G.tx = TileShape<2>::X; G.ty = TileShape<2>::Y; G.tz = TileShape<2>::Z;
-  } else {
-    G.tx = TileShape<3>::X; G.ty = TileShape<3>::Y; G.tz = TileShape<3>::Z;
-  }
-  G.ntx = (G.n0 + G.tx - 1) / G.tx;
-  G.nty = (G.n1 + G.ty - 1) / G.ty;
-  G.ntz = (G.n2 + G.tz - 1) / G.tz;
   eb.ls = ls;
   eb.home = s;
   LSDev L = to_dev(ls, grid.dim);
@@ -415,30 +407,70 @@ void build_handle(EBHandle& eb, const eb_grid& grid, const eb_levelset& ls, cuda
                                              eb.cut_dir, eb.cut_delta, eb.cut_c, eb.cut_xg, st);
   EB_CUDA(cudaGetLastError());
 
-  int64_t ntiles_all = (int64_t)G.ntx * G.nty * G.ntz;
-  int32_t* tflag = dalloc<int32_t>(ntiles_all, s);
-  int32_t* toff = dalloc<int32_t>(ntiles_all + 1, s, false);
-  k_tile_flags<<<blocks_for(nn, T), T, 0, s>>>(G, eb.code, tflag);
-  exclusive_scan_i32(tflag, toff, ntiles_all, s);
-  int32_t nt = 0;
-  EB_CUDA(cudaMemcpyAsync(&nt, toff + ntiles_all, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  if (grid.dim == 2)
+    build_tiles(eb, TileShape<2>::X, TileShape<2>::Y, TileShape<2>::Z, s);
+  else
+    build_tiles(eb, TileShape<3>::X, TileShape<3>::Y, TileShape<3>::Z, s);
   EB_CUDA(cudaMemcpyAsync(&hst, st, sizeof(hst), cudaMemcpyDeviceToHost, s));
   EB_CUDA(cudaStreamSynchronize(s));
-  eb.num_tiles = nt;
-  eb.tiles = dalloc<int32_t>(nt, s, false);
-  k_compact<<<blocks_for(ntiles_all, T), T, 0, s>>>(tflag, toff, ntiles_all, eb.tiles);
-  eb.tile_base = dalloc<int32_t>(nt, s, false);
-  eb.tile_lim = dalloc<int32_t>(nt, s, false);
-  k_tile_geom<<<blocks_for(nt, T), T, 0, s>>>(G, eb.tiles, nt, eb.tile_base, eb.tile_lim);
   eb.diag32 = dalloc<float>(nn, s, false);
   k_diag32<<<blocks_for(nn, T), T, 0, s>>>(nn, eb.diag, eb.diag32);
   EB_CUDA(cudaGetLastError());
   eb.num_far = (int64_t)hst.num_far;
   eb.max_delta_over_h = hst.max_delta_over_h;
   eb.min_abs_psi = hst.min_abs_psi;
-  dfree(psi, s); dfree(is_cp, s); dfree(cp_off, s); dfree(ncut, s);
-  dfree(tflag, s); dfree(toff, s); dfree(st, s);
+  dfree(psi, s); dfree(is_cp, s); dfree(cp_off, s); dfree(ncut, s); dfree(st, s);
   EB_CUDA(cudaStreamSynchronize(s));
+}
+
+bool tile_shape_ok(int dim, int tx, int ty, int tz) {
+  auto pow2 = [](int v) { return v >= 1 && (v & (v - 1)) == 0; };
+  if (!pow2(tx) || !pow2(ty) || !pow2(tz)) return false;
+  if (tx * ty * tz != TILE_NODES || tx < 2 || tx > 128 || ty > 128 || tz > 128) return false;
+  return dim == 3 || tz == 1;
+}
+
+void build_tiles(EBHandle& eb, int tx, int ty, int tz, cudaStream_t s) {
+  EB_REQUIRE(tile_shape_ok(eb.g.dim, tx, ty, tz), EB_ERR_INVALID,
+             "tile shape: powers of two with product 256, 2 <= x <= 128, y, z <= 128, z = 1 in 2D");
+  Geometry& G = eb.g;
+  G.tx = tx;
+  G.ty = ty;
+  G.tz = tz;
+  G.ntx = (G.n0 + G.tx - 1) / G.tx;
+  G.nty = (G.n1 + G.ty - 1) / G.ty;
+  G.ntz = (G.n2 + G.tz - 1) / G.tz;
+  dfree(eb.tiles, s);
+  dfree(eb.tile_base, s);
+  dfree(eb.tile_lim, s);
+  eb.num_tiles = 0;
+  const int T = 256;
+  const int64_t nn = G.num_nodes;
+  const int64_t ntiles_all = (int64_t)G.ntx * G.nty * G.ntz;
+  int32_t* tflag = dalloc<int32_t>(ntiles_all, s);
+  int32_t* toff = nullptr;
+  try {
+    toff = dalloc<int32_t>(ntiles_all + 1, s, false);
+    k_tile_flags<<<blocks_for(nn, T), T, 0, s>>>(G, eb.code, tflag);
+    exclusive_scan_i32(tflag, toff, ntiles_all, s);
+    int32_t nt = 0;
+    EB_CUDA(cudaMemcpyAsync(&nt, toff + ntiles_all, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    EB_CUDA(cudaStreamSynchronize(s));
+    eb.tiles = dalloc<int32_t>(nt, s, false);
+    k_compact<<<blocks_for(ntiles_all, T), T, 0, s>>>(tflag, toff, ntiles_all, eb.tiles);
+    eb.tile_base = dalloc<int32_t>(nt, s, false);
+    eb.tile_lim = dalloc<int32_t>(nt, s, false);
+    k_tile_geom<<<blocks_for(nt, T), T, 0, s>>>(G, eb.tiles, nt, eb.tile_base, eb.tile_lim);
+    EB_CUDA(cudaGetLastError());
+    eb.num_tiles = nt;
+  } catch (...) {
+    dfree(tflag, s);
+    dfree(toff, s);
+    throw;
+  }
+  dfree(tflag, s);
+  dfree(toff, s);
+  ++eb.tile_gen;
 }
 
 void destroy_handle(EBHandle& eb) {

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <cstdio>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -106,9 +107,17 @@ struct EBHandle {
   int32_t* tile_lim = nullptr;   // [num_tiles] extents x | y << 8 | z << 16
   double2* tile_shift64 = nullptr;  // batched view only: per-tile (sigma, 1 / (sigma + 2 dim))
   float2* tile_shift32 = nullptr;
+  int tile_gen = 0;  // bumped whenever the tile list is rebuilt (captured graphs key on it)
   TileView tv() const {
-    return TileView{tile_base, tile_lim, num_tiles, g.n0, g.n0 * g.n1, (int32_t)g.num_nodes, tile_shift64,
-                    tile_shift32};
+    TileView v{tile_base, tile_lim, num_tiles, g.n0, g.n0 * g.n1, (int32_t)g.num_nodes, tile_shift64, tile_shift32};
+    v.bx = ilog2(g.tx);
+    v.by = ilog2(g.ty);
+    return v;
+  }
+  static int ilog2(int v) {
+    int r = 0;
+    while ((1 << r) < v) ++r;
+    return r;
   }
   int32_t* cut_cp = nullptr;     // [num_cut]
   int32_t* cut_dir = nullptr;    // [num_cut]
@@ -189,6 +198,20 @@ inline unsigned blocks_for(int64_t n, int threads) {
 }  // namespace ebk
 
 namespace ebk {
+// Rebuilds the list of active tiles of eb for tiles of tx x ty x tz nodes
+// (powers of two, product 256, tx >= 2, tz = 1 in 2D); bumps eb.tile_gen.
+void build_tiles(EBHandle& eb, int tx, int ty, int tz, cudaStream_t s);
+// whether (tx, ty, tz) is a valid tile shape for dim
+bool tile_shape_ok(int dim, int tx, int ty, int tz);
+// tile-shape autotuner (autotune.cu): candidate shapes, event timing of an
+// operation on a stream, and the tuning loop (retile, time, keep the fastest)
+struct TileDims {
+  int x, y, z;
+};
+std::vector<TileDims> tile_candidates(int dim);
+double time_us(const std::function<void()>& op, int reps, cudaStream_t s);
+void run_tuner(int dim, const std::function<void(const TileDims&)>& retile, const std::function<void()>& op,
+               int reps, eb_tune_t* out, cudaStream_t s);
 template <class T>
 int launch_leapfrog(const EBHandle& eb, T* ua, T* ub, int nsteps, double dt, cudaStream_t s);
 }

@@ -514,7 +514,7 @@ void Solver::iteration(int kind, const double* b, double* x, cudaStream_t s) {
 // default stream.
 void Solver::graph_prepare(int kind, const double* b, double* x, int iters, int profile, cudaStream_t s) {
   if (gexec && g_b == b && g_x == x && g_iters == iters && g_kind == kind && g_prof == profile && g_nn == nn &&
-      g_nn_mode == nn_mode)
+      g_nn_mode == nn_mode && g_tile_gen == eb->tile_gen)
     return;
   if (prof_on) {  // settle event pairs recorded so far before the capture reuses them
     EB_CUDA(cudaStreamSynchronize(s));
@@ -547,6 +547,7 @@ void Solver::graph_prepare(int kind, const double* b, double* x, int iters, int 
   g_prof = profile;
   g_nn = nn;
   g_nn_mode = nn_mode;
+  g_tile_gen = eb->tile_gen;
 }
 
 void Solver::graph_release() {

@@ -53,6 +53,7 @@ struct Solver {
   const double* g_b = nullptr;
   double* g_x = nullptr;
   const nn_handle* g_nn = nullptr;
+  int g_tile_gen = -1;
   int g_nn_mode = -1;
   int g_iters = 0, g_kind = -1, g_prof = -1, g_pairs = 0;
   int64_t g_launches = 0;

@@ -1,10 +1,11 @@
 // Active-tile traversal shared by every grid kernel.
 //
-// The grid is cut into tiles of 256 nodes (2D: 32 x 8, 3D: 16 x 4 x 4, x
-// fastest); only tiles that hold a CP are listed.  For each listed tile the
-// build stores the node index of its corner and its extents (ragged at the
-// high ends of the grid), so a thread finds its nodes with shifts and one
-// multiply-add -- no integer division in the hot loops.
+// The grid is cut into tiles of 256 nodes, x fastest; the extents are powers
+// of two chosen at run time (default 2D: 32 x 8, 3D: 16 x 4 x 4; eb_retile /
+// the autotuner pick others).  Only tiles that hold a CP are listed.  For each
+// listed tile the build stores the node index of its corner and its extents
+// (ragged at the high ends of the grid), so a thread finds its nodes with
+// shifts and one multiply-add -- no integer division in the hot loops.
 //
 // Hot kernels work on PAIRS of x-adjacent nodes (n0 even, tile origins even,
 // so a pair is 16-byte aligned in FP64): 128 threads cover a tile and a CTA of
@@ -18,6 +19,7 @@ namespace ebk {
 constexpr int TILE_NODES = 256;
 constexpr int PAIR_THREADS = 128;  // threads per tile in the pair layout
 
+// default tile extents
 template <int DIM>
 struct TileShape;
 template <>
@@ -39,14 +41,14 @@ struct TileView {
   // 1 / (sigma + 2 dim) of the unit-spacing operator, FP64 and FP32 copies
   const double2* tshift64 = nullptr;
   const float2* tshift32 = nullptr;
+  int32_t bx = 5, by = 3;  // log2 of the tile extents in x and y (z = 256 >> (bx + by))
 };
 
 // Node of this thread in listed tile tt (one node per thread, 256 threads).
 template <int DIM>
 __device__ __forceinline__ bool tile_node(const TileView& tv, int64_t tt, int32_t& node) {
-  using S = TileShape<DIM>;
   const int l = threadIdx.x;
-  const int lx = l % S::X, ly = (l / S::X) % S::Y, lz = l / (S::X * S::Y);
+  const int lx = l & ((1 << tv.bx) - 1), ly = (l >> tv.bx) & ((1 << tv.by) - 1), lz = l >> (tv.bx + tv.by);
   const int32_t lim = __ldg(tv.lim + tt);
   node = __ldg(tv.base + tt) + lx + ly * tv.sy + lz * tv.sz;
   return lx < (lim & 0xFF) && ly < ((lim >> 8) & 0xFF) && lz < ((lim >> 16) & 0xFF);
@@ -55,9 +57,8 @@ __device__ __forceinline__ bool tile_node(const TileView& tv, int64_t tt, int32_
 // First node of this thread's pair in listed tile tt (pair layout).
 template <int DIM>
 __device__ __forceinline__ bool tile_pair(const TileView& tv, int64_t tt, int t, int32_t& node) {
-  using S = TileShape<DIM>;
-  constexpr int PX = S::X / 2;
-  const int px = t % PX, ly = (t / PX) % S::Y, lz = t / (PX * S::Y);
+  const int bp = tv.bx - 1;  // pairs per tile row: 2^(bx - 1)
+  const int px = t & ((1 << bp) - 1), ly = (t >> bp) & ((1 << tv.by) - 1), lz = t >> (bp + tv.by);
   const int32_t lim = __ldg(tv.lim + tt);
   node = __ldg(tv.base + tt) + 2 * px + ly * tv.sy + lz * tv.sz;
   return 2 * px < (lim & 0xFF) && ly < ((lim >> 8) & 0xFF) && lz < ((lim >> 16) & 0xFF);
