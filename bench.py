@@ -23,8 +23,10 @@ learned    The learned preconditioner stage: trained (outside the timed
            1e-10 on a random star at 2048^2 (u = sin(2x) cos(3y)); the plain
            FP64 AMG-PCG is timed beside it.
 
-L2 (129 MB) is flushed between timed steps by a 512 MB write outside the
-timed events.  Under torchrun every rank runs its own copy (replicas; no
+Before timing, the tile shape of the grid kernels is chosen by the library's
+autotuner (V-cycle or apply timed for each candidate shape; the winner and
+the timings are in the line).  L2 (129 MB) is flushed between timed steps by
+a 512 MB write outside the timed events.  Under torchrun every rank runs its own copy (replicas; no
 collective on the data path) and rank 0 prints the line.
 
 --impl reference runs the FP64 CPU oracle (plain numpy / scipy) of the same
@@ -364,6 +366,14 @@ class Ctx:
             self.dist.destroy_process_group()
 
 
+def tune_tiles(fn):
+    """Runs one of the library's tile autotuners (through its JSON cache);
+    returns (shape in use, {shape: microseconds} when it timed)."""
+    shape, res = fn()
+    tune = None if res is None else {f"{a}x{b}x{c}": round(u, 2) for (a, b, c), u in zip(res.shapes, res.us)}
+    return list(shape), tune
+
+
 def timed(fn):
     """Runs fn between CUDA events on torch's current stream; returns (ms, result)."""
     import torch
@@ -398,6 +408,7 @@ def loop(ctx, args, step, clocks_index):
 
 
 def gpu_poisson(ctx, args, dim):
+    from paper_2204_06083_gb300 import autotune
     import numpy as np
     import torch
     import eb_inputs as ei
@@ -417,6 +428,7 @@ def gpu_poisson(ctx, args, dim):
     solver = eb.AMG(h, 0.0, vcycle_prec=prec)
     setup_ms = 1000.0 * (time.perf_counter() - t0)
     solver64 = eb.AMG(h, 0.0) if dim == 3 else solver
+    tile, tune = tune_tiles(lambda: autotune.tune_amg(solver, reps=10))
     nc = h.info.num_cp
     pts = ei.grid_points(grid)
     _, _, _, xg = h.cuts()
@@ -482,6 +494,7 @@ def gpu_poisson(ctx, args, dim):
             "dtype": "f64 outer, f32 V-cycle" if dim == 3 else "f64",
             "num_cp": nc, "iterations": sts[-1].iterations, "time_to_tol_ms": ms_per_step,
             "build_ms": build_ms, "setup_ms": setup_ms, "amg_levels": solver.rows, "max_err_vs_exact": err,
+            "tile": tile, "autotune_us_per_vcycle": tune,
             "roofline": {"bound": "hbm",
                          "kernel": f"k_g_cheb_step<{dim}, {'float, float' if dim == 3 else 'double, double'}>",
                          "achieved": achieved, "peak": pk["hbm_gbs"], "peak_kind": kind, "unit": "GB/s",
@@ -497,6 +510,7 @@ def gpu_poisson(ctx, args, dim):
 
 
 def gpu_wave(ctx, args):
+    from paper_2204_06083_gb300 import autotune
     import torch
     import eb_inputs as ei
     import paper_2204_06083_gb300 as eb
@@ -504,6 +518,7 @@ def gpu_wave(ctx, args):
     grid, ls = ei.star_wave(4096)
     h = eb.EB(grid, ls)
     nc = h.info.num_cp
+    tile, tune = tune_tiles(lambda: autotune.tune_eb(h, eb.EB_F32, reps=5, op=eb.EB_TUNE_LEAPFROG))
     X, Y = ei.grid_points(grid)
     c, w = ei.pulse_params(0)
     dt = 0.9 * grid.h / math.sqrt(2.0)
@@ -556,6 +571,7 @@ def gpu_wave(ctx, args):
     alg = LEAPFROG_BYTES_PER_DOF["f32"] * nc * nsteps
     achieved = alg / launch_s / 1e9
     return {"value": value, "ms_per_step": ms_per_step, "dtype": "f32", "num_cp": nc, "dt": dt,
+            "tile": tile, "autotune_us_per_16_steps": tune,
             "us_per_time_step": 1000.0 * ms_per_step / nsteps,
             "fp64": {"ms_per_run": statistics.mean(f64), "us_per_time_step": 1000.0 * statistics.mean(f64) / nsteps,
                      "dof_steps_per_s": nc * nsteps / (statistics.mean(f64) / 1000.0),
@@ -571,6 +587,7 @@ def gpu_wave(ctx, args):
 
 
 def gpu_batched(ctx, args):
+    from paper_2204_06083_gb300 import autotune
     import numpy as np
     import torch
     import eb_inputs as ei
@@ -586,6 +603,7 @@ def gpu_batched(ctx, args):
     B.heat_setup(dts, 1.0, vcycle_prec=eb.EB_F32)
     torch.cuda.synchronize()
     setup_ms = 1000.0 * (time.perf_counter() - t0)
+    tile, tune = tune_tiles(lambda: autotune.tune_batch(B, reps=5))
     u0 = B.zeros()
     f = B.zeros()
     ug = torch.zeros(max(B.num_cut, 1), dtype=torch.float64, device=ctx.dev)
@@ -652,6 +670,7 @@ def gpu_batched(ctx, args):
     achieved = CHEB_BYTES_PER_DOF["f32"] * nc / avg_s / 1e9 if prof_n else None
     return {"value": value, "ms_per_step": ms_per_step, "dtype": "f64 outer, f32 V-cycle", "num_cp": nc,
             "num_nodes": B.num_nodes, "setup_ms": setup_ms, "ms_per_time_step": ms_per_step / nsteps,
+            "tile": tile, "autotune_us_per_vcycle": tune,
             "max_iterations_per_time_step": iters,
             "sequential_fp64": {"ms_per_time_step": statistics.mean(seq),
                                 "dof_per_s": nc / (statistics.mean(seq) / 1000.0)},
@@ -666,6 +685,7 @@ def gpu_batched(ctx, args):
 
 
 def gpu_learned(ctx, args):
+    from paper_2204_06083_gb300 import autotune
     import numpy as np
     import torch
     import eb_inputs as ei
@@ -686,6 +706,7 @@ def gpu_learned(ctx, args):
     h = eb.EB(grid, ls)
     amg = eb.AMG(h)
     nc = h.info.num_cp
+    tile, tune = tune_tiles(lambda: autotune.tune_amg(amg, reps=10))
     pts = ei.grid_points(grid)
     xg = h.cuts()[3].cpu().numpy()
     b = h.rhs(torch.tensor(ei.f_k1(*pts), device=ctx.dev), torch.tensor(ei.u_k1(xg[:, 0], xg[:, 1]), device=ctx.dev))
@@ -737,6 +758,7 @@ def gpu_learned(ctx, args):
     peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
     return {"value": value, "ms_per_step": ms_per_step, "dtype": "f64 outer, bf16 CNN (f32 accumulate)",
             "num_cp": nc, "iterations": sts[-1].iterations, "converged": bool(sts[-1].converged),
+            "tile": tile, "autotune_us_per_vcycle": tune,
             "time_to_tol_ms": ms_per_step, "compare": compare,
             "training": {"pairs": npairs, "pair_generation_s": pairs_s, "train_s": train_s, "adam_steps": npairs // batch,
                          "batch": batch, "loss_log": log},

@@ -27,6 +27,8 @@
  *   - Calls that take a cudaStream_t are asynchronous on that stream unless
  *     noted "synchronous" (those read a result back to the host).
  *   - Handles own all their device memory and are released by *_destroy.
+ *     A handle built on another (an AMG hierarchy on its grid, a geometry
+ *     borrowed from a batch) must be destroyed before the one it was built on.
  */
 #ifndef EB_H_
 #define EB_H_
@@ -156,10 +158,14 @@ typedef struct {
  * eb stay valid (their next solve captures again).  Do not call while work on
  * eb is in flight on another stream.  Synchronous. */
 int eb_retile(eb_handle* eb, const int tile[3], cudaStream_t stream);
-/* Autotuner: for each candidate shape, times `reps` eb_apply launches of
- * precision prec with CUDA events on stream, and keeps the fastest shape.
- * out (may be NULL) receives the timings.  Synchronous. */
-int eb_autotune(eb_handle* eb, int prec, int reps, eb_tune_t* out, cudaStream_t stream);
+/* Operations the grid autotuner can time. */
+typedef enum { EB_TUNE_APPLY = 0, EB_TUNE_LEAPFROG = 1 } eb_tune_op;
+/* Autotuner: for each candidate shape, times `reps` calls of the operation
+ * (EB_TUNE_APPLY: one eb_apply launch; EB_TUNE_LEAPFROG: one wave_step of 16
+ * steps) in precision prec (EB_F64, EB_F32; EB_BF16 for apply) with CUDA
+ * events on stream, and keeps the fastest shape.  out (may be NULL) receives
+ * the timings.  Synchronous. */
+int eb_autotune(eb_handle* eb, int op, int prec, int reps, eb_tune_t* out, cudaStream_t stream);
 
 /* ---------------------------------------------------------------- AMG + PCG */
 /* EB_PC_AMG_NN (V-cycle followed by the learned stage) is selected by

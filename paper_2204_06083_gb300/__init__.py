@@ -22,6 +22,7 @@ EB_ERR_NO_CONVERGENCE, EB_ERR_BREAKDOWN, EB_ERR_TIMEOUT, EB_ERR_OOM, EB_ERR_NOT_
 EB_F64, EB_F32, EB_BF16 = 0, 1, 2
 EB_PC_AMG, EB_PC_JACOBI, EB_PC_NONE, EB_PC_AMG_NN = 0, 1, 2, 3
 EB_NN_PLAIN, EB_NN_ENERGY = 0, 1
+EB_TUNE_APPLY, EB_TUNE_LEAPFROG = 0, 1
 STAR_MAX = 16
 
 CODE_BP = 0x40
@@ -100,7 +101,7 @@ _SIGS = {
     "eb_rhs": (C.c_int, [_P, _P, _P, _P, _P]),
     "eb_apply": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "eb_retile": (C.c_int, [_P, _P, _P]),
-    "eb_autotune": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(eb_tune_t), _P]),
+    "eb_autotune": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.POINTER(eb_tune_t), _P]),
     "amg_autotune": (C.c_int, [_P, C.c_int, C.POINTER(eb_tune_t), _P]),
     "batch_autotune": (C.c_int, [_P, C.c_int, C.POINTER(eb_tune_t), _P]),
     "amg_setup": (C.c_int, [_P, C.c_double, C.POINTER(amg_opts), C.POINTER(_P), _P]),
@@ -316,10 +317,10 @@ class EB:
         _check(load().eb_retile(self._h, C.cast(t, C.c_void_p), _stream(stream)))
         self._refresh_info()
 
-    def autotune(self, prec=EB_F64, reps=20, stream=None) -> TuneResult:
-        """Times eb_apply for every candidate tile shape and keeps the fastest."""
+    def autotune(self, prec=EB_F64, reps=20, op=EB_TUNE_APPLY, stream=None) -> TuneResult:
+        """Times eb_apply (or 16 leapfrog steps) for every candidate tile shape and keeps the fastest."""
         t = eb_tune_t()
-        _check(load().eb_autotune(self._h, int(prec), int(reps), C.byref(t), _stream(stream)))
+        _check(load().eb_autotune(self._h, int(op), int(prec), int(reps), C.byref(t), _stream(stream)))
         self._refresh_info()
         return _tune_result(t)
 
@@ -424,9 +425,12 @@ class batch_info_t(C.Structure):
 
 
 class _Borrowed(EB):
-    """EB view of a geometry owned by a batch (never destroyed here)."""
+    """EB view of a geometry owned by a batch (never destroyed here).  It keeps
+    the batch alive, so that handles built on it (an AMG hierarchy reads its
+    geometry when destroyed) never outlive the geometry."""
 
-    def __init__(self, handle, grid):
+    def __init__(self, handle, grid, owner):
+        self._owner = owner
         self._h = C.c_void_p(handle)
         self.grid = grid
         self.dim = grid.dim
@@ -473,7 +477,7 @@ class Batch:
         h = load().batch_geometry(self._h, g)
         if not h:
             raise EBError(EB_ERR_INVALID, load().eb_last_error().decode())
-        return _Borrowed(h, self.grids[g])
+        return _Borrowed(h, self.grids[g], self)
 
     def view(self, v, g):
         """Geometry g's (n1, n0) grid inside a batch-layout vector."""

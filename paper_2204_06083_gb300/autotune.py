@@ -12,7 +12,7 @@ import json
 import os
 from typing import Optional
 
-from . import AMG, EB, EB_F64, Batch, TuneResult
+from . import AMG, EB, EB_F64, EB_TUNE_APPLY, Batch, TuneResult
 
 
 def cache_path() -> str:
@@ -50,15 +50,16 @@ def _grid_key(eb: EB):
     return f"{g.dim}D {'x'.join(str(int(v)) for v in g.n[:g.dim])} cp={eb.info.num_cp}"
 
 
-def tune_eb(eb: EB, prec=EB_F64, reps=20, path: Optional[str] = None, retune=False):
-    """Tile shape for eb_apply-like kernels (apply, leapfrog) on this grid."""
+def tune_eb(eb: EB, prec=EB_F64, reps=20, op=EB_TUNE_APPLY, path: Optional[str] = None, retune=False):
+    """Tile shape for the apply (op EB_TUNE_APPLY) or the leapfrog step
+    (EB_TUNE_LEAPFROG) on this grid."""
     path = path or cache_path()
-    key = f"{_device()} | apply prec={prec} | {_grid_key(eb)}"
+    key = f"{_device()} | {'apply' if op == EB_TUNE_APPLY else 'leapfrog'} prec={prec} | {_grid_key(eb)}"
     hit = None if retune else _load(path).get(key)
     if hit:
         eb.retile(hit["tile"])
         return tuple(hit["tile"]), None
-    res = eb.autotune(prec, reps)
+    res = eb.autotune(prec, reps, op)
     _store(path, key, res.shape, res)
     return res.shape, res
 

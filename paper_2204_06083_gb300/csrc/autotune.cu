@@ -79,13 +79,17 @@ int eb_retile(eb_handle* eb, const int tile[3], cudaStream_t stream) {
   });
 }
 
-int eb_autotune(eb_handle* eb, int prec, int reps, eb_tune_t* out, cudaStream_t stream) {
+int eb_autotune(eb_handle* eb, int op_kind, int prec, int reps, eb_tune_t* out, cudaStream_t stream) {
   if (!eb) {
     set_error("eb_autotune: NULL handle");
     return EB_ERR_INVALID;
   }
-  if (prec != EB_F64 && prec != EB_F32 && prec != EB_BF16) {
-    set_error("eb_autotune: prec must be EB_F64, EB_F32 or EB_BF16");
+  if (op_kind != EB_TUNE_APPLY && op_kind != EB_TUNE_LEAPFROG) {
+    set_error("eb_autotune: op must be EB_TUNE_APPLY or EB_TUNE_LEAPFROG");
+    return EB_ERR_INVALID;
+  }
+  if (prec != EB_F64 && prec != EB_F32 && (prec != EB_BF16 || op_kind == EB_TUNE_LEAPFROG)) {
+    set_error("eb_autotune: prec must be EB_F64, EB_F32 or (apply only) EB_BF16");
     return EB_ERR_INVALID;
   }
   return guarded([&] {
@@ -96,8 +100,19 @@ int eb_autotune(eb_handle* eb, int prec, int reps, eb_tune_t* out, cudaStream_t 
     uint8_t* y = nullptr;
     try {
       y = dalloc<uint8_t>(nn * es, stream);
+      // leapfrog: 16 steps of the persistent kernel per timed call (dt = 0: fields stay finite)
+      auto leap = [&] {
+        int rc = prec == EB_F64
+                     ? launch_leapfrog<double>(E, reinterpret_cast<double*>(x), reinterpret_cast<double*>(y), 16, 0.0,
+                                               stream)
+                     : launch_leapfrog<float>(E, reinterpret_cast<float*>(x), reinterpret_cast<float*>(y), 16, 0.0,
+                                              stream);
+        EB_REQUIRE(rc == EB_OK, rc, "eb_autotune: leapfrog launch failed");
+      };
       auto op = [&] {
-        if (prec == EB_F64)
+        if (op_kind == EB_TUNE_LEAPFROG)
+          leap();
+        else if (prec == EB_F64)
           launch_apply<double>(E, reinterpret_cast<double*>(x), reinterpret_cast<double*>(y), 0.0, stream);
         else if (prec == EB_F32)
           launch_apply<float>(E, reinterpret_cast<float*>(x), reinterpret_cast<float*>(y), 0.0, stream);

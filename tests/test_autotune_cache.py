@@ -19,7 +19,7 @@ class FakeEB:
     def retile(self, shape):
         self.retiled.append(tuple(shape))
 
-    def autotune(self, prec, reps):
+    def autotune(self, prec, reps, op=0):
         self.tuned += 1
         return pkg.TuneResult([(32, 8, 1), (64, 4, 1), (16, 16, 1)], [5.0, 3.0, 4.0], 1)
 

@@ -100,6 +100,9 @@ def test_autotuners():
     h = eb.EB(grid, ls)
     res = h.autotune(eb.EB_F32, reps=5)
     assert len(res.shapes) == 10
+    resw = h.autotune(eb.EB_F32, reps=2, op=eb.EB_TUNE_LEAPFROG)
+    assert h.info.tile == resw.shape and min(resw.us) == resw.us[resw.best]
+    res = h.autotune(eb.EB_F32, reps=5)
     assert h.info.tile == res.shape and min(res.us) == res.us[res.best] and all(u > 0 for u in res.us)
     amg = eb.AMG(h, vcycle_prec=eb.EB_F32)
     b = torch.from_numpy(np.random.default_rng(3).standard_normal(h.shape())).cuda()
@@ -139,3 +142,20 @@ def test_batch_autotune_keeps_results():
         outs.append(torch.cat([B.view(u, g)[(B.geometry(g).classes() & eb.CODE_CP) != 0]
                                for g in range(len(grids))]))
     assert torch.linalg.norm(outs[1] - outs[0]) <= 1e-10 * torch.linalg.norm(outs[0])
+
+
+def test_amg_on_batch_geometry_outlives_batch_variable():
+    """An AMG hierarchy built on a geometry borrowed from a batch keeps the
+    batch alive after the last direct reference to the batch is dropped."""
+    import gc
+    eb = _pkg()
+    grids = [ei.box_grid(2, n) for n in (64, 96)]
+    B = eb.Batch(grids, [ei.random_star(s) for s in (1, 2)])
+    amg = eb.AMG(B.geometry(1), 1.0 / grids[1].h)
+    del B
+    gc.collect()
+    b = torch.ones(amg.eb.shape(), dtype=torch.float64, device="cuda")
+    x, st = amg.solve(b, rtol=1e-10)
+    assert st.converged
+    del amg
+    gc.collect()
