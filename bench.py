@@ -5,7 +5,8 @@
 poisson3d  3D Poisson AMG-PCG: ellipsoid with semi-axes 0.7/0.5/0.4 and a seeded
            rotation, 256^3 nodes on [-1,1]^3, u = exp(x) sin(y+z).  One step =
            one pcg_solve from x = 0 to ||r||/||b|| <= 1e-10 (FP32 V-cycle,
-           flexible FP64 PCG); the plain FP64 V-cycle is timed beside it.
+           flexible FP64 PCG); the plain FP64 V-cycle and the BF16-storage
+           V-cycle are timed beside it.
 poisson2d  2D Poisson, plain FP64 AMG-PCG: circle R = 0.5 at (0.02, 0.01),
            128^2 nodes, u = sin(2x) cos(3y), rtol 1e-10.
 wave       Leapfrog wave equation on the star r = 0.5 + 0.1 sin(5 phi), 4096^2
@@ -464,6 +465,17 @@ def gpu_poisson(ctx, args, dim):
                 f64.append(t)
         extra["fp64_vcycle"] = {"time_to_tol_ms": statistics.mean(f64), "iterations": st64.iterations,
                                 "dof_per_s": nc / (statistics.mean(f64) / 1000.0)}
+        solver16 = eb.AMG(h, 0.0, vcycle_prec=eb.EB_BF16)
+        b16 = []
+        for i in range(args.warmup + args.steps):
+            x.zero_()
+            ctx.flush()
+            t, st16 = timed(lambda: solver16.solve(b, x=x, rtol=RTOL, maxit=500)[1])
+            if i >= args.warmup:
+                b16.append(t)
+        extra["bf16_vcycle"] = {"time_to_tol_ms": statistics.mean(b16), "iterations": st16.iterations,
+                                "dof_per_s": nc / (statistics.mean(b16) / 1000.0)}
+        solver16.close()
     # end to end through the C ABI: pinned host b -> device, solve, x -> pinned host
     hb = b.cpu().pin_memory()
     hx = torch.empty_like(hb).pin_memory()

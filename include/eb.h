@@ -177,7 +177,9 @@ typedef struct {
   int coarse_max;        /* coarsen until n <= coarse_max (default 1024) */
   double strength;       /* theta of |a_ij| >= theta sqrt(a_ii a_jj), default 0.02 */
   int cheb_degree;       /* Chebyshev smoother degree, default 2 */
-  int vcycle_prec;       /* EB_F64 (default) or EB_F32: storage of level vectors/matrices */
+  int vcycle_prec;       /* storage of level vectors/matrices: EB_F64 (default), EB_F32, or EB_BF16
+                            (bfloat16 storage, FP32 sums; the level-0 diagonal stays FP32); the
+                            reduced precisions make pcg_solve use the flexible (Polak-Ribiere) beta */
 } amg_opts;
 
 typedef struct {

@@ -36,8 +36,10 @@ struct Level {
   double rho = 0.0;
   VecSet<double> v64;
   VecSet<float> v32;
-  // FP32 copies of the values for the reduced-precision V-cycle
+  VecSet<__nv_bfloat16> v16;
+  // FP32 / BF16 copies of the values for the reduced-precision V-cycles
   float *A32 = nullptr, *P32 = nullptr, *R32 = nullptr, *dinv32 = nullptr;
+  __nv_bfloat16 *A16 = nullptr, *P16 = nullptr, *R16 = nullptr, *dinv16 = nullptr;
 };
 
 struct Hierarchy {
@@ -46,6 +48,7 @@ struct Hierarchy {
   int64_t nc = 0;
   VecSet<double> g64;            // level-0 grid vectors (full grid)
   VecSet<float> g32;
+  VecSet<__nv_bfloat16> g16;
 };
 
 DCsr level0_csr(const EBHandle& eb, double sigma, cudaStream_t s);

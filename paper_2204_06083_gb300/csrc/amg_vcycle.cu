@@ -1,13 +1,17 @@
 // V-cycle of the smoothed-aggregation hierarchy (AMG preconditioner of
-// Algorithm 1 step 4), in FP64 or in FP32 storage with FP32 arithmetic.
+// Algorithm 1 step 4), in FP64, or in FP32 or BF16 storage with FP32
+// arithmetic.
 //
 // Level 0 is matrix free on the grid (stencil.cuh); coarser levels use CSR.
 // Smoother: Chebyshev polynomial of degree k for D^-1 A on [rho/30, 1.1 rho],
 // one sweep before and one after the coarse correction; the first sweep
 // starts from x = 0 and needs no operator apply.  The coarsest level is solved
-// by its FP64 explicit inverse.  With FP32 storage the right-hand side is
-// rounded to FP32 on entry and the result is widened to FP64 on exit; the
-// outer PCG (eb_solve.cu) then uses the flexible (Polak-Ribiere) beta.
+// by its FP64 explicit inverse.  With FP32 / BF16 storage the right-hand side
+// is rounded on entry and the result is widened to FP64 on exit (the last
+// smoothing step writes FP64 directly); the outer PCG (eb_solve.cu) then uses
+// the flexible (Polak-Ribiere) beta.  BF16 storage: level vectors and the
+// values of A_l, P_l, R_l and D_l^-1 in bfloat16, every sum in FP32; the
+// level-0 diagonal stays FP32.
 #include "amg_internal.cuh"
 #include "stencil.cuh"
 
@@ -57,6 +61,29 @@ __device__ __forceinline__ GOp<double> tile_op(const TileView& tv, int64_t tt, G
 
 __device__ __forceinline__ void st2o(double* p, double a, double b) { st2(p, a, b); }
 __device__ __forceinline__ void st2o(float* p, float a, float b) { st2(p, a, b); }
+__device__ __forceinline__ void st2o(__nv_bfloat16* p, float a, float b) { st2(p, a, b); }
+
+// conversions between the storage type and the arithmetic types
+template <class To, class From>
+__device__ __forceinline__ To cvt(From v) {
+  return static_cast<To>(v);
+}
+template <>
+__device__ __forceinline__ float cvt<float, __nv_bfloat16>(__nv_bfloat16 v) {
+  return __bfloat162float(v);
+}
+template <>
+__device__ __forceinline__ double cvt<double, __nv_bfloat16>(__nv_bfloat16 v) {
+  return (double)__bfloat162float(v);
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16, float>(float v) {
+  return __float2bfloat16_rn(v);
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16, double>(double v) {
+  return __double2bfloat16(v);
+}
 
 // level 0 ----------------------------------------------------------------
 // b_out = (V) r; x = d = D^-1 b / theta
@@ -108,7 +135,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_step(TileView tv, const u
     const A d0 = (k0 & CODE_CP) ? c1 * dv.x + c2 * res0 : (A)0;
     const A d1 = (k1 & CODE_CP) ? c1 * dv.y + c2 * res1 : (A)0;
     st2o(d + node, d0, d1);
-    st2(xo + node, (O)((k0 & CODE_CP) ? xc.x + d0 : (A)0), (O)((k1 & CODE_CP) ? xc.y + d1 : (A)0));
+    st2(xo + node, (k0 & CODE_CP) ? xc.x + d0 : (A)0, (k1 & CODE_CP) ? xc.y + d1 : (A)0);
   }
 }
 
@@ -150,9 +177,9 @@ __global__ void k_restrict0(int64_t n, const int32_t* __restrict__ rp, const int
   const int g = (int)(t % G);
   A s = 0;
   if (i < n)
-    for (int32_t e = rp[i] + g; e < rp[i + 1]; e += G) s += (A)v[e] * (A)r[node_col[e]];
+    for (int32_t e = rp[i] + g; e < rp[i + 1]; e += G) s += cvt<A>(v[e]) * cvt<A>(r[node_col[e]]);
   s = group_reduce<G>(s);
-  if (i < n && g == 0) out[i] = (V)s;
+  if (i < n && g == 0) out[i] = cvt<V>(s);
 }
 
 // x[node(i)] += sum_c P_ic e_c over the CPs i
@@ -166,11 +193,11 @@ __global__ void k_prolong0(int64_t n, const int32_t* __restrict__ rp, const int3
   const int g = (int)(t % G);
   A s = 0;
   if (i < n)
-    for (int32_t f = rp[i] + g; f < rp[i + 1]; f += G) s += (A)v[f] * (A)e[ci[f]];
+    for (int32_t f = rp[i] + g; f < rp[i + 1]; f += G) s += cvt<A>(v[f]) * cvt<A>(e[ci[f]]);
   s = group_reduce<G>(s);
   if (i < n && g == 0) {
     const int32_t node = cp_node[i];
-    x[node] = (V)((A)x[node] + s);
+    x[node] = cvt<V>(cvt<A>(x[node]) + s);
   }
 }
 
@@ -180,7 +207,7 @@ __global__ void k_c_cheb_first(int64_t n, const V* dinv, const V* b, V* x, V* d,
   using A = typename AccOf<V>::type;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const V v = (V)((A)dinv[i] * (A)b[i] / theta);
+  const V v = cvt<V>(cvt<A>(dinv[i]) * cvt<A>(b[i]) / theta);
   x[i] = v;
   d[i] = v;
 }
@@ -190,7 +217,7 @@ __device__ __forceinline__ typename AccOf<V>::type csr_row(const CsrV<V>& M, con
   using A = typename AccOf<V>::type;
   A s = 0;
   if (i < M.n)
-    for (int32_t e = M.rp[i] + g; e < M.rp[i + 1]; e += G) s += (A)M.v[e] * (A)x[M.ci[e]];
+    for (int32_t e = M.rp[i] + g; e < M.rp[i + 1]; e += G) s += cvt<A>(M.v[e]) * cvt<A>(x[M.ci[e]]);
   return group_reduce<G>(s);
 }
 
@@ -203,10 +230,10 @@ __global__ void k_c_cheb_step(CsrV<V> M, const V* dinv, const V* b, const V* x, 
   const int g = (int)(t % G);
   const A ax = csr_row<G>(M, x, i, g);
   if (i >= M.n || g != 0) return;
-  const A res = (A)dinv[i] * ((A)b[i] - ax);
-  const A dv = (c1 == (A)0 ? (A)0 : c1 * (A)d[i]) + c2 * res;
-  d[i] = (V)dv;
-  xo[i] = (V)((A)x[i] + dv);
+  const A res = cvt<A>(dinv[i]) * (cvt<A>(b[i]) - ax);
+  const A dv = (c1 == (A)0 ? (A)0 : c1 * cvt<A>(d[i])) + c2 * res;
+  d[i] = cvt<V>(dv);
+  xo[i] = cvt<V>(cvt<A>(x[i]) + dv);
 }
 
 template <int G, class V>
@@ -216,7 +243,7 @@ __global__ void k_c_resid(CsrV<V> M, const V* b, const V* x, V* r) {
   const int64_t i = t / G;
   const int g = (int)(t % G);
   const A ax = csr_row<G>(M, x, i, g);
-  if (i < M.n && g == 0) r[i] = (V)((A)b[i] - ax);
+  if (i < M.n && g == 0) r[i] = cvt<V>(cvt<A>(b[i]) - ax);
 }
 
 template <int G, class V>
@@ -225,7 +252,7 @@ __global__ void k_c_spmv(CsrV<V> M, const V* x, V* y) {
   const int64_t i = t / G;
   const int g = (int)(t % G);
   const auto s = csr_row<G>(M, x, i, g);
-  if (i < M.n && g == 0) y[i] = (V)s;
+  if (i < M.n && g == 0) y[i] = cvt<V>(s);
 }
 
 template <int G, class V>
@@ -235,7 +262,7 @@ __global__ void k_c_prolong_add(CsrV<V> P, const V* e, V* x) {
   const int64_t i = t / G;
   const int g = (int)(t % G);
   const A s = csr_row<G>(P, e, i, g);
-  if (i < P.n && g == 0) x[i] = (V)((A)x[i] + s);
+  if (i < P.n && g == 0) x[i] = cvt<V>(cvt<A>(x[i]) + s);
 }
 
 // group width for a CSR matrix: the power of two nearest half its mean row
@@ -267,26 +294,31 @@ __global__ void k_dense_gemv(const double* __restrict__ M, int64_t n, const V* _
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
   double s = 0.0;
-  for (int64_t j = lane; j < n; j += 32) s += M[row * n + j] * (double)b[j];
+  for (int64_t j = lane; j < n; j += 32) s += M[row * n + j] * cvt<double>(b[j]);
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) x[row] = (V)s;
+  if (lane == 0) x[row] = cvt<V>(s);
 }
 
 template <class V>
 __global__ void k_gather_cp(int64_t n, const int32_t* cp_node, const double* g, V* out) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = (V)g[cp_node[i]];
+  if (i < n) out[i] = cvt<V>(g[cp_node[i]]);
 }
 
 template <class V>
 __global__ void k_scatter_cp(int64_t n, const int32_t* cp_node, const V* in, double* g) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) g[cp_node[i]] = (double)in[i];
+  if (i < n) g[cp_node[i]] = cvt<double>(in[i]);
 }
 
 __global__ void k_to_f32(int64_t n, const double* a, float* b) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
+}
+
+__global__ void k_to_bf16(int64_t n, const double* a, __nv_bfloat16* b) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = __double2bfloat16(a[i]);
 }
 
 // ------------------------------------------------------------------ host
@@ -333,6 +365,16 @@ struct LevelView<float> {
   static CsrV<float> P(const Level& L) { return {L.P.n, L.P.rp, L.P.ci, L.P32}; }
   static CsrV<float> R(const Level& L) { return {L.R.n, L.R.rp, L.R.ci, L.R32}; }
   static const float* dinv(const Level& L) { return L.dinv32; }
+};
+
+template <>
+struct LevelView<__nv_bfloat16> {
+  static VecSet<__nv_bfloat16>& vec(Level& L) { return L.v16; }
+  static VecSet<__nv_bfloat16>& grid(Hierarchy& H) { return H.g16; }
+  static CsrV<__nv_bfloat16> A(const Level& L) { return {L.A.n, L.A.rp, L.A.ci, L.A16}; }
+  static CsrV<__nv_bfloat16> P(const Level& L) { return {L.P.n, L.P.rp, L.P.ci, L.P16}; }
+  static CsrV<__nv_bfloat16> R(const Level& L) { return {L.R.n, L.R.rp, L.R.ci, L.R16}; }
+  static const __nv_bfloat16* dinv(const Level& L) { return L.dinv16; }
 };
 
 template <class V>
@@ -436,6 +478,9 @@ void amg_vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s) {
   if (S.opts.vcycle_prec == EB_F32) {
     if (dim == 2) vcycle_grid<float, 2>(S, r, z, s);
     else vcycle_grid<float, 3>(S, r, z, s);
+  } else if (S.opts.vcycle_prec == EB_BF16) {
+    if (dim == 2) vcycle_grid<__nv_bfloat16, 2>(S, r, z, s);
+    else vcycle_grid<__nv_bfloat16, 3>(S, r, z, s);
   } else {
     if (dim == 2) vcycle_grid<double, 2>(S, r, z, s);
     else vcycle_grid<double, 3>(S, r, z, s);
@@ -462,6 +507,12 @@ static float* to_f32(const double* a, int64_t n, cudaStream_t s) {
   return b;
 }
 
+static __nv_bfloat16* to_bf16(const double* a, int64_t n, cudaStream_t s) {
+  __nv_bfloat16* b = dalloc<__nv_bfloat16>(n, s, false);
+  if (n > 0) k_to_bf16<<<blocks_for(n, 256), 256, 0, s>>>(n, a, b);
+  return b;
+}
+
 void amg_alloc_vcycle(Solver& S, cudaStream_t s) {
   Hierarchy& H = *S.H;
   const int64_t nn = S.eb->g.num_nodes;
@@ -477,6 +528,16 @@ void amg_alloc_vcycle(Solver& S, cudaStream_t s) {
       if (L.P.v) L.P32 = to_f32(L.P.v, L.P.nnz, s);
       if (L.R.v) L.R32 = to_f32(L.R.v, L.R.nnz, s);
     }
+  } else if (S.opts.vcycle_prec == EB_BF16) {
+    alloc_set(H.g16, nn, true, s);
+    for (size_t l = first; l < H.L.size(); ++l) alloc_set(H.L[l].v16, H.L[l].A.n, true, s);
+    for (size_t l = 0; l < H.L.size(); ++l) {
+      Level& L = H.L[l];
+      L.A16 = to_bf16(L.A.v, L.A.nnz, s);
+      if (L.dinv) L.dinv16 = to_bf16(L.dinv, L.A.n, s);
+      if (L.P.v) L.P16 = to_bf16(L.P.v, L.P.nnz, s);
+      if (L.R.v) L.R16 = to_bf16(L.R.v, L.R.nnz, s);
+    }
   } else {
     alloc_set(H.g64, nn, false, s);
     for (size_t l = first; l < H.L.size(); ++l) alloc_set(H.L[l].v64, H.L[l].A.n, true, s);
@@ -487,10 +548,13 @@ void amg_alloc_vcycle(Solver& S, cudaStream_t s) {
 void amg_free_vcycle(Hierarchy& H, cudaStream_t s) {
   free_set(H.g64, s);
   free_set(H.g32, s);
+  free_set(H.g16, s);
   for (Level& L : H.L) {
     free_set(L.v64, s);
     free_set(L.v32, s);
+    free_set(L.v16, s);
     dfree(L.A32, s); dfree(L.P32, s); dfree(L.R32, s); dfree(L.dinv32, s);
+    dfree(L.A16, s); dfree(L.P16, s); dfree(L.R16, s); dfree(L.dinv16, s);
   }
 }
 

@@ -185,8 +185,8 @@ int amg_setup(const eb_handle* eb, double shift, const amg_opts* opts, amg_handl
     EB_REQUIRE(o.max_levels >= 0 && o.max_levels <= 32, EB_ERR_INVALID, "amg_setup: max_levels out of range");
     EB_REQUIRE(o.coarse_max >= 1 && o.coarse_max <= 4096, EB_ERR_INVALID, "amg_setup: coarse_max in [1, 4096]");
     EB_REQUIRE(o.cheb_degree >= 1 && o.cheb_degree <= 8, EB_ERR_INVALID, "amg_setup: cheb_degree in [1, 8]");
-    EB_REQUIRE(o.vcycle_prec == EB_F64 || o.vcycle_prec == EB_F32, EB_ERR_INVALID,
-               "amg_setup: vcycle_prec must be EB_F64 or EB_F32");
+    EB_REQUIRE(o.vcycle_prec == EB_F64 || o.vcycle_prec == EB_F32 || o.vcycle_prec == EB_BF16, EB_ERR_INVALID,
+               "amg_setup: vcycle_prec must be EB_F64, EB_F32 or EB_BF16");
     auto t0 = std::chrono::steady_clock::now();
     S.alloc_work(stream);
     if (o.max_levels > 0) amg_build(S, stream);

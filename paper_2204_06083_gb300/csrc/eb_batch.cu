@@ -603,7 +603,7 @@ static int batch_pcg(Batch& B, const double* b, double* x, double rtol, int maxi
   const int ng = B.ngeo();
   const TileView tv = B.view.tv();
   const unsigned gb = bgrid(B);
-  const bool flex = S.opts.vcycle_prec == EB_F32;
+  const bool flex = S.opts.vcycle_prec != EB_F64;
   EB_REQUIRE(rtol > 0.0 && maxit >= 0, EB_ERR_INVALID, "batch: rtol must be > 0 and maxit >= 0");
   auto t0 = std::chrono::steady_clock::now();
   std::vector<PcgScalars> init(ng);
@@ -807,15 +807,15 @@ int batch_heat_setup(batch_handle* b, const double* dt, double theta, const amg_
     amg_opts o{25, 1024, 0.02, 2, EB_F64};
     if (opts) o = *opts;
     EB_REQUIRE(o.max_levels >= 1 && o.max_levels <= 32, EB_ERR_INVALID, "batch_heat_setup: max_levels in [1, 32]");
-    EB_REQUIRE(o.vcycle_prec == EB_F64 || o.vcycle_prec == EB_F32, EB_ERR_INVALID,
-               "batch_heat_setup: vcycle_prec must be EB_F64 or EB_F32");
+    EB_REQUIRE(o.vcycle_prec == EB_F64 || o.vcycle_prec == EB_F32 || o.vcycle_prec == EB_BF16, EB_ERR_INVALID,
+               "batch_heat_setup: vcycle_prec must be EB_F64, EB_F32 or EB_BF16");
     B.S = new Solver();
     Solver& S = *B.S;
     S.eb = &B.view;
     S.shift = 0.0;  // per-tile shifts of the view take over
     S.opts = o;
     S.alloc_work(stream);
-    if (o.vcycle_prec == EB_F32) B.zold = dalloc<double>(B.view.g.num_nodes, stream);
+    if (o.vcycle_prec != EB_F64) B.zold = dalloc<double>(B.view.g.num_nodes, stream);
     // block-diagonal level-0 matrix of the scaled operators, geometry by geometry
     std::vector<DCsr> parts(ng);
     int64_t nnz = 0;

@@ -322,7 +322,7 @@ void Solver::alloc_work(cudaStream_t s) {
   p = dalloc<double>(nn, s);
   q = dalloc<double>(nn, s);
   tmp = dalloc<double>(nn, s);
-  if (opts.vcycle_prec == EB_F32) zold = dalloc<double>(nn, s);
+  if (opts.vcycle_prec != EB_F64) zold = dalloc<double>(nn, s);
   nblk = (int)std::min<int64_t>(std::max<int64_t>(eb->num_tiles, 1), (int64_t)num_sms() * 4);
   part = dalloc<double>(2 * (int64_t)nblk, s);
   sc = dalloc<PcgScalars>(1, s);

@@ -30,7 +30,7 @@ struct Solver {
   // full-grid work vectors (touched on the active tiles only)
   double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *tmp = nullptr;
   double* zold = nullptr;  // previous z (flexible CG with a reduced-precision V-cycle)
-  bool flexible() const { return H != nullptr && opts.vcycle_prec == EB_F32; }
+  bool flexible() const { return H != nullptr && (opts.vcycle_prec == EB_F32 || opts.vcycle_prec == EB_BF16); }
   // the flexible (Polak-Ribiere) beta: reduced-precision V-cycle or learned stage
   bool flex_for(int kind) const { return kind == EB_PC_AMG_NN || (kind == EB_PC_AMG && flexible()); }
   nn_handle* nn = nullptr;  // learned stage of EB_PC_AMG_NN (set for one solve)

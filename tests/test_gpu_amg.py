@@ -191,3 +191,41 @@ def test_mixed_precision_vcycle_pcg(name):
     _, s32 = g32.solve(b, rtol=1e-10, maxit=500)
     _, s64 = g64.solve(b, rtol=1e-10, maxit=500)
     assert s32.iterations <= s64.iterations + 2
+
+
+@pytest.mark.parametrize("name", ["circle128", "star258", "ellipsoid64"])
+def test_bf16_vcycle_pcg(name):
+    """Form (1), BF16 variant: level vectors and level matrices stored in
+    bfloat16, every sum in FP32, FP64 outer flexible PCG.  The V-cycle output
+    differs from the FP64 one by the bf16 rounding of the stored values
+    (stated: rel-L2 <= 3e-2); the solution still reaches the FP64 tolerance and
+    matches the oracle, at the cost of a few more iterations."""
+    eb = _eb()
+    grid, ls = CASES[name]()
+    h = eb.EB(grid, ls)
+    ref = oeb.build(grid, ls)
+    H = oamg.setup(ref.A)
+    g16 = eb.AMG(h, 0.0, vcycle_prec=eb.EB_BF16)
+    g64 = eb.AMG(h, 0.0)
+    rng = np.random.default_rng(5)
+    r = torch.tensor(rng.standard_normal(h.shape()), device="cuda")
+    z16 = ref.from_grid(g16.vcycle(r).cpu().numpy())
+    z64 = ref.from_grid(g64.vcycle(r).cpu().numpy())
+    e = np.linalg.norm(z16 - z64) / np.linalg.norm(z64)
+    print(f"{name}: BF16 V-cycle rel-L2 vs FP64 V-cycle {e:.2e}")
+    assert e <= 3e-2
+    pts = ei.grid_points(grid)
+    ufun, ffun = (ei.u_k1, ei.f_k1) if grid.dim == 2 else (ei.u_k3, ei.f_k3)
+    f = ffun(*pts)
+    ug = ufun(*[ref.cut_xg[:, a] for a in range(grid.dim)])
+    b = h.rhs(torch.tensor(f, device="cuda"), torch.tensor(ug, device="cuda"))
+    b_ref = oeb.rhs(ref, f, ug)
+    x, st = g16.solve(b, rtol=1e-13, maxit=500)
+    x_ref, _ = osol.pcg(ref.A, b_ref, M=lambda q: oamg.vcycle(H, q), rtol=1e-13)
+    got = ref.from_grid(x.cpu().numpy())
+    assert st.converged and st.true_rel_residual <= 1e-13
+    assert np.linalg.norm(got - x_ref) / np.linalg.norm(x_ref) <= 1e-10
+    _, s16 = g16.solve(b, rtol=1e-10, maxit=500)
+    _, s64 = g64.solve(b, rtol=1e-10, maxit=500)
+    print(f"{name}: iterations to 1e-10 BF16 {s16.iterations}, FP64 {s64.iterations}")
+    assert s16.iterations <= 2 * s64.iterations + 2
