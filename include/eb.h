@@ -216,7 +216,10 @@ int amg_autotune(amg_handle* amg, int reps, eb_tune_t* out, cudaStream_t stream)
 typedef struct {
   int precond;           /* eb_pc_kind, default EB_PC_AMG */
   int check_every;       /* host convergence check period in iterations (default 1) */
-  int use_graph;         /* capture the iteration in a CUDA graph (default 1) */
+  int use_graph;         /* 1 (default): the whole iteration loop runs on the device in one graph launch (a
+                            conditional WHILE node around one captured iteration; no host round trip per
+                            iteration); with profile set, or 2: captured chunks of check_every iterations
+                            with a host convergence check between them; 0: direct launches */
   int profile;           /* 1: time every level-0 smoother launch with CUDA events; 2 (pcg_solve_nn):
                             time the learned stage's 32 -> 32 convolution launches instead */
 } pcg_opts;

@@ -62,6 +62,11 @@ struct Batch {
   // event timing of the level-0 smoother launches inside the captured iteration
   bool profile = false;
   int g_prof = -1, g_pairs = 0;
+  // the whole loop on the device (conditional WHILE node) when not profiling
+  cudaGraphExec_t lexec = nullptr;
+  const double* l_b = nullptr;
+  double* l_x = nullptr;
+  int64_t l_launches = 0;
   int ngeo() const { return (int)geo.size(); }
 };
 
@@ -194,6 +199,10 @@ static void batch_tiles(Batch& B, cudaStream_t s) {
   const int64_t nt = B.tile_off[count];
   if (B.gexec) cudaGraphExecDestroy(B.gexec);
   B.gexec = nullptr;
+  if (B.lexec) cudaGraphExecDestroy(B.lexec);
+  B.lexec = nullptr;
+  B.l_b = nullptr;
+  B.l_x = nullptr;
   dfree(V.tile_base, s); dfree(V.tile_lim, s); dfree(V.tile_shift64, s); dfree(V.tile_shift32, s);
   dfree(B.tile_geo, s); dfree(B.geo_tile0, s); dfree(B.part, s);
   V.num_tiles = 0;
@@ -231,6 +240,7 @@ static void batch_tiles(Batch& B, cudaStream_t s) {
 static void destroy_batch(Batch& B) {
   cudaStream_t s = B.home;
   if (B.gexec) cudaGraphExecDestroy(B.gexec);
+  if (B.lexec) cudaGraphExecDestroy(B.lexec);
   if (B.cap_stream) cudaStreamDestroy(B.cap_stream);
   if (B.S) {
     amg_free(*B.S);
@@ -598,6 +608,37 @@ static void b_graph_prepare(Batch& B, const double* b, double* x, bool flex, cud
   B.g_x = x;
 }
 
+// continue while some geometry is neither converged nor at its iteration limit
+__global__ void k_b_loop_cond(cudaGraphConditionalHandle h, const PcgScalars* sc, int ng) {
+  int active = 0;
+  for (int g = threadIdx.x; g < ng; g += blockDim.x) active |= (!sc[g].done && sc[g].iters < sc[g].maxit) ? 1 : 0;
+  active = __syncthreads_or(active);
+  if (threadIdx.x == 0) cudaGraphSetConditional(h, active ? 1u : 0u);
+}
+
+static void b_loop_release(Batch& B) {
+  if (B.lexec) cudaGraphExecDestroy(B.lexec);
+  B.lexec = nullptr;
+  B.l_b = nullptr;
+  B.l_x = nullptr;
+}
+
+static void b_loop_prepare(Batch& B, const double* b, double* x, bool flex) {
+  if (B.lexec && B.l_b == b && B.l_x == x) return;
+  b_loop_release(B);
+  if (!B.cap_stream) EB_CUDA(cudaStreamCreateWithFlags(&B.cap_stream, cudaStreamNonBlocking));
+  const int64_t n0 = B.nlaunch;
+  B.lexec = build_while_graph(B.cap_stream, [&](cudaStream_t cs, cudaGraphConditionalHandle h) {
+    b_iteration(B, x, flex, cs);
+    k_b_loop_cond<<<1, 256, 0, cs>>>(h, B.sc, B.ngeo());
+    ++B.nlaunch;
+  });
+  B.l_launches = B.nlaunch - n0;
+  B.nlaunch = n0;
+  B.l_b = b;
+  B.l_x = x;
+}
+
 static int batch_pcg(Batch& B, const double* b, double* x, double rtol, int maxit, pcg_stats* stats, cudaStream_t s) {
   Solver& S = *B.S;
   const int ng = B.ngeo();
@@ -619,6 +660,8 @@ static int batch_pcg(Batch& B, const double* b, double* x, double rtol, int maxi
   S.prof_acc_ms = 0.0;
   S.prof_acc_n = 0;
   for (int restart = 0; restart < 4; ++restart) {
+    const int done_its = *std::max_element(iters.begin(), iters.end());
+    for (auto& p : init) p.maxit = maxit - done_its;
     EB_CUDA(cudaMemcpyAsync(B.sc, init.data(), sizeof(PcgScalars) * ng, cudaMemcpyHostToDevice, s));
     B.nlaunch += 2;
     k_b_mask<<<gb, BT, 0, s>>>(tv, B.view.code, x, x);
@@ -631,6 +674,16 @@ static int batch_pcg(Batch& B, const double* b, double* x, double rtol, int maxi
       ++B.nlaunch;
       k_b_xpby<<<gb, BT, 0, s>>>(tv, B.tile_geo, B.sc, S.z, S.p, flex ? B.zold : nullptr, 1);
       int it = 0;
+      if (!B.profile) {  // the whole loop on the device
+        b_loop_prepare(B, b, x, flex);
+        EB_CUDA(cudaGraphLaunch(B.lexec, s));
+        EB_CUDA(cudaMemcpyAsync(B.sc_host, B.sc, sizeof(PcgScalars) * ng, cudaMemcpyDeviceToHost, s));
+        EB_CUDA(cudaStreamSynchronize(s));
+        int most = 0;
+        for (int g = 0; g < ng; ++g) most = std::max(most, B.sc_host[g].iters);
+        B.nlaunch += B.l_launches * most;
+        it = maxit;  // skip the host loop below
+      }
       while (true) {
         if (its + it >= maxit) break;
         b_graph_prepare(B, b, x, flex, s);
@@ -803,6 +856,7 @@ int batch_heat_setup(batch_handle* b, const double* dt, double theta, const amg_
     }
     if (B.gexec) cudaGraphExecDestroy(B.gexec);
     B.gexec = nullptr;
+    b_loop_release(B);
     dfree(B.zold, stream);
     amg_opts o{25, 1024, 0.02, 2, EB_F64};
     if (opts) o = *opts;

@@ -296,6 +296,12 @@ __global__ void k_finalize(const double* part, int nblk, int op, PcgScalars* sc)
   }
 }
 
+// condition of the device-side iteration loop: continue while not converged
+// (or broken down) and below the iteration limit
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, const PcgScalars* sc) {
+  cudaGraphSetConditional(h, (!sc->done && sc->iters < sc->maxit) ? 1u : 0u);
+}
+
 // ---------------------------------------------------------------- host side
 #define EB_DIM_LAUNCH(dim, kernel, grid, ...)                                 \
   do {                                                                       \
@@ -332,6 +338,7 @@ void Solver::alloc_work(cudaStream_t s) {
 void Solver::free_work() {
   cudaStream_t s = eb->home;
   graph_release();
+  loop_release();
   if (cap_stream) cudaStreamDestroy(cap_stream);
   cap_stream = nullptr;
   dfree(r, s); dfree(z, s); dfree(p, s); dfree(q, s); dfree(tmp, s); dfree(zold, s); dfree(part, s); dfree(sc, s);
@@ -386,10 +393,12 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
   PcgScalars init{};
   init.tol2 = rtol * rtol;
   int total_iters = 0;
+  const int pcg_maxit = maxit;
   bool converged = false;
   int flags = 0;
   double rel = 0.0;
   for (int restart = 0; restart < 4 && !converged; ++restart) {
+    init.maxit = pcg_maxit - total_iters;
     EB_CUDA(cudaMemcpyAsync(sc, &init, sizeof(init), cudaMemcpyHostToDevice, s));
     // x is masked to the CPs (its non-CP entries are ignored on input)
     EB_DIM_LAUNCH(dim, k_mask_copy, nblk, tv, eb->code, x, x);
@@ -419,6 +428,14 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
     EB_DIM_LAUNCH(dim, k_xpby, nblk, tv, sc, z, p, flex ? zold : nullptr, 1);
     int it = 0;
     bool stop = false;
+    if (o.use_graph == 1 && !prof_on) {  // the whole loop on the device
+      loop_prepare(kind, b, x, s);
+      EB_CUDA(cudaGraphLaunch(lexec, s));
+      EB_CUDA(cudaMemcpyAsync(sc_host, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+      EB_CUDA(cudaStreamSynchronize(s));
+      nlaunch += l_launches * sc_host->iters;
+      stop = true;
+    }
     while (!stop) {
       const int nb = std::min(check, maxit - (total_iters + it));
       bool graphed = false;
@@ -556,6 +573,72 @@ void Solver::graph_release() {
   g_pairs = 0;
   g_b = nullptr;
   g_x = nullptr;
+}
+
+cudaGraphExec_t build_while_graph(cudaStream_t cap,
+                                  const std::function<void(cudaStream_t, cudaGraphConditionalHandle)>& body) {
+  cudaGraph_t graph = nullptr;
+  EB_CUDA(cudaGraphCreate(&graph, 0));
+  cudaGraphExec_t exec = nullptr;
+  try {
+    cudaGraphConditionalHandle h;
+    EB_CUDA(cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    EB_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &p));
+    cudaGraph_t bg = p.conditional.phGraph_out[0];
+    EB_CUDA(cudaStreamBeginCaptureToGraph(cap, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    try {
+      body(cap, h);
+    } catch (...) {
+      cudaGraph_t dummy = nullptr;
+      cudaStreamEndCapture(cap, &dummy);
+      throw;
+    }
+    EB_CUDA(cudaStreamEndCapture(cap, &bg));
+    EB_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+  } catch (...) {
+    cudaGraphDestroy(graph);
+    throw;
+  }
+  cudaGraphDestroy(graph);
+  return exec;
+}
+
+// Captures the device-side loop { while (!done && iters < maxit) iteration }
+// (once per argument set).
+void Solver::loop_prepare(int kind, const double* b, double* x, cudaStream_t s) {
+  if (lexec && l_b == b && l_x == x && l_kind == kind && l_nn == nn && l_nn_mode == nn_mode &&
+      l_tile_gen == eb->tile_gen)
+    return;
+  loop_release();
+  (void)s;  // capturing runs nothing; the graph is launched on s
+  if (!cap_stream) EB_CUDA(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+  const int64_t n0 = nlaunch;
+  lexec = build_while_graph(cap_stream, [&](cudaStream_t cs, cudaGraphConditionalHandle h) {
+    iteration(kind, b, x, cs);
+    k_loop_cond<<<1, 1, 0, cs>>>(h, sc);
+    ++nlaunch;
+  });
+  l_launches = nlaunch - n0;
+  nlaunch = n0;
+  l_b = b;
+  l_x = x;
+  l_kind = kind;
+  l_nn = nn;
+  l_nn_mode = nn_mode;
+  l_tile_gen = eb->tile_gen;
+}
+
+void Solver::loop_release() {
+  if (lexec) cudaGraphExecDestroy(lexec);
+  lexec = nullptr;
+  l_b = nullptr;
+  l_x = nullptr;
 }
 
 static bool capturing(cudaStream_t s) {

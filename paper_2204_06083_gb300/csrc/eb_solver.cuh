@@ -16,7 +16,8 @@ enum { PROF_SMOOTHER = 1, PROF_CONV = 2 };
 
 struct PcgScalars {
   double bb, rr, rz, pq, alpha, beta, tol2;
-  int iters, flags, done, pad;
+  int iters, flags, done;
+  int maxit;  // iteration limit of the device-side loop (counted like iters)
 };
 
 struct Hierarchy;  // AMG levels (amg.cu)
@@ -57,6 +58,14 @@ struct Solver {
   int g_nn_mode = -1;
   int g_iters = 0, g_kind = -1, g_prof = -1, g_pairs = 0;
   int64_t g_launches = 0;
+  // the whole iteration loop on the device: a conditional WHILE node whose
+  // body is one iteration (no host round trip per iteration)
+  cudaGraphExec_t lexec = nullptr;
+  const double* l_b = nullptr;
+  double* l_x = nullptr;
+  int l_kind = -1, l_nn_mode = -1, l_tile_gen = -1;
+  const nn_handle* l_nn = nullptr;
+  int64_t l_launches = 0;  // kernel launches per loop iteration
 
   void alloc_work(cudaStream_t s);
   void free_work();
@@ -73,7 +82,16 @@ struct Solver {
   void iteration(int kind, const double* b, double* x, cudaStream_t s);
   void graph_prepare(int kind, const double* b, double* x, int iters, int profile, cudaStream_t s);
   void graph_release();
+  void loop_prepare(int kind, const double* b, double* x, cudaStream_t s);
+  void loop_release();
 };
+
+// Instantiates { while (condition) body } as one executable graph: body(st,
+// h) enqueues one pass on the capture stream st and must end with a kernel
+// that sets the condition handle h (cudaGraphSetConditional); the condition
+// starts at 1.  cap is a non-blocking stream used only for the capture.
+cudaGraphExec_t build_while_graph(cudaStream_t cap,
+                                  const std::function<void(cudaStream_t, cudaGraphConditionalHandle)>& body);
 
 // AMG (amg.cu)
 void amg_build(Solver& S, cudaStream_t s);

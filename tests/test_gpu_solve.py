@@ -181,3 +181,47 @@ def test_wave_energy_conserved_on_gpu():
     h.wave_step(ua, ub, dt, 2001)
     e1 = osol.leapfrog_energy(ref.A, ref.from_grid(ua.cpu().numpy()), ref.from_grid(ub.cpu().numpy()), dt)
     assert abs(e1 - e0) / e0 < 1e-9
+
+
+def test_device_loop_matches_host_checked_loop():
+    """use_graph=1 runs the whole PCG loop on the device (conditional WHILE
+    node); use_graph=2 launches captured single iterations with a host check
+    after each.  Same kernels in the same order: bit-identical iterates,
+    iteration counts, and the maxit limit is honoured on the device."""
+    import paper_2204_06083_gb300 as eb
+    for grid, ls in (ei.circle_k1(128), ei.ellipsoid_k3(48, seed=1)):
+        h = eb.EB(grid, ls)
+        for prec in (eb.EB_F64, eb.EB_F32):
+            amg = eb.AMG(h, vcycle_prec=prec)
+            b = torch.from_numpy(np.random.default_rng(7).standard_normal(h.shape())).cuda()
+            x1, s1 = amg.solve(b, rtol=1e-11, use_graph=1)
+            x2, s2 = amg.solve(b, rtol=1e-11, use_graph=2)
+            assert s1.iterations == s2.iterations and torch.equal(x1, x2)
+            x3, s3 = amg.solve(b, rtol=1e-30, maxit=3, use_graph=1, allow_noconv=True)
+            x4, s4 = amg.solve(b, rtol=1e-30, maxit=3, use_graph=2, allow_noconv=True)
+            assert s3.iterations == 3 and not s3.converged and torch.equal(x3, x4)
+
+
+def test_batch_device_loop_matches_host_checked_loop():
+    import paper_2204_06083_gb300 as eb
+    grids = [ei.box_grid(2, n) for n in (96, 160, 130)]
+    lss = [ei.random_star(s) for s in (51, 52, 53)]
+    outs = []
+    for profile in (False, True):   # profiling runs the host-checked loop
+        B = eb.Batch(grids, lss)
+        B.heat_setup([g.h for g in grids], 1.0, vcycle_prec=eb.EB_F32)
+        B.set_profile(profile)
+        u = B.zeros()
+        for g, gr in enumerate(grids):
+            X, Y = ei.grid_points(gr)
+            B.view(u, g).copy_(torch.tensor(ei.u_heat(X, Y, 0.0)))
+        f = B.zeros()
+        ug = torch.zeros(max(B.num_cut, 1), dtype=torch.float64, device="cuda")
+        b1 = B.rhs(f, ug)
+        its = []
+        for _ in range(3):
+            st = B.heat_step(u, b1, rtol=1e-11)
+            its.append([s.iterations for s in st])
+        outs.append((u, its))
+    assert outs[0][1] == outs[1][1]
+    assert torch.equal(outs[0][0], outs[1][0])
