@@ -421,7 +421,9 @@ def loop(ctx, args, step, clocks_index):
     with ClockSampler(clocks_index) as clk:
         for _ in range(args.steps):
             ctx.flush()
+            torch.cuda.nvtx.range_push("timed")
             t, r = timed(step)
+            torch.cuda.nvtx.range_pop()
             ms.append(t)
             res.append(r)
     torch.cuda.synchronize()
@@ -451,6 +453,9 @@ def gpu_poisson(ctx, args, dim):
     setup_ms = 1000.0 * (time.perf_counter() - t0)
     solver64 = eb.AMG(h, 0.0) if dim == 3 else solver
     tile, tune = tune_tiles(lambda: autotune.tune_amg(solver, reps=10))
+    epl, epl_us = solver.tune_csr(reps=10)
+    if solver64 is not solver:
+        solver64.tune_csr(reps=5)
     nc = h.info.num_cp
     pts = ei.grid_points(grid)
     _, _, _, xg = h.cuts()
@@ -466,9 +471,11 @@ def gpu_poisson(ctx, args, dim):
     b = h.rhs(f, ug)
     x = torch.zeros_like(b)
 
+    loop_kind = 2 if args.host_loop else 1
+
     def step():
         x.zero_()
-        return solver.solve(b, x=x, rtol=RTOL, maxit=500)[1]
+        return solver.solve(b, x=x, rtol=RTOL, maxit=500, use_graph=loop_kind)[1]
 
     sts, ms_per_step, clocks = loop(ctx, args, step, torch.cuda.current_device())
     launches = sum(s.launches for s in sts) // len(sts)
@@ -486,6 +493,7 @@ def gpu_poisson(ctx, args, dim):
         extra["fp64_vcycle"] = {"time_to_tol_ms": statistics.mean(f64), "iterations": st64.iterations,
                                 "dof_per_s": nc / (statistics.mean(f64) / 1000.0)}
         solver16 = eb.AMG(h, 0.0, vcycle_prec=eb.EB_BF16)
+        solver16.tune_csr(reps=5)
         b16 = []
         for i in range(args.warmup + args.steps):
             x.zero_()
@@ -527,6 +535,7 @@ def gpu_poisson(ctx, args, dim):
             "num_cp": nc, "iterations": sts[-1].iterations, "time_to_tol_ms": ms_per_step,
             "build_ms": build_ms, "setup_ms": setup_ms, "amg_levels": solver.rows, "max_err_vs_exact": err,
             "tile": tile, "autotune_us_per_vcycle": tune,
+            "csr_entries_per_lane": epl, "csr_tune_us_per_vcycle": {str(k): round(v, 2) for k, v in epl_us.items()},
             "roofline": {"bound": "hbm",
                          "kernel": f"k_g_cheb_step<{dim}, {'float, float' if dim == 3 else 'double, double'}>",
                          "achieved": achieved, "peak": pk["hbm_gbs"], "peak_kind": kind, "unit": "GB/s",
@@ -844,6 +853,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="poisson3d", choices=WORKLOADS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="poisson workloads: timed solves check convergence on the host after every captured "
+                         "iteration instead of looping on the device (for kernel-level profilers)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -212,6 +212,14 @@ int amg_vcycle(const amg_handle* amg, const double* r_dev, double* z_dev, cudaSt
  * candidate shape, times `reps` V-cycles, keeps the fastest (see eb_autotune).
  * Synchronous. */
 int amg_autotune(amg_handle* amg, int reps, eb_tune_t* out, cudaStream_t stream);
+/* Tunes the row groups of the V-cycle's CSR kernels (coarse levels, level-0
+ * restriction and prolongation): a group of G <= 32 lanes owns one row, G the
+ * largest power of two with G x (entries per lane) <= the mean row length.
+ * Times `reps` V-cycles with 1, 2, 4 and 8 entries per lane, keeps the
+ * fastest.  us_out (4 doubles, may be NULL) receives the timings, best_out
+ * (may be NULL) the entries per lane chosen.  Results do not change (the sums
+ * are grouped differently: FP rounding only).  Synchronous. */
+int amg_tune_csr(amg_handle* amg, int reps, double* us_out, int* best_out, cudaStream_t stream);
 
 typedef struct {
   int precond;           /* eb_pc_kind, default EB_PC_AMG */

@@ -103,6 +103,7 @@ _SIGS = {
     "eb_retile": (C.c_int, [_P, _P, _P]),
     "eb_autotune": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.POINTER(eb_tune_t), _P]),
     "amg_autotune": (C.c_int, [_P, C.c_int, C.POINTER(eb_tune_t), _P]),
+    "amg_tune_csr": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "batch_autotune": (C.c_int, [_P, C.c_int, C.POINTER(eb_tune_t), _P]),
     "amg_setup": (C.c_int, [_P, C.c_double, C.POINTER(amg_opts), C.POINTER(_P), _P]),
     "amg_destroy": (None, [_P]),
@@ -411,6 +412,14 @@ class AMG:
         _check(load().amg_autotune(self._h, int(reps), C.byref(t), _stream(stream)))
         self.eb._refresh_info()
         return _tune_result(t)
+
+    def tune_csr(self, reps=20, stream=None):
+        """Times V-cycles with 1, 2, 4, 8 entries per lane in the CSR kernels; keeps the fastest.
+        Returns (chosen entries per lane, {entries per lane: microseconds})."""
+        us = (C.c_double * 4)()
+        best = C.c_int()
+        _check(load().amg_tune_csr(self._h, int(reps), C.cast(us, C.c_void_p), C.byref(best), _stream(stream)))
+        return best.value, {e: us[i] for i, e in enumerate((1, 2, 4, 8))}
 
     def heat_step(self, u, b1, dt, theta=1.0, b0=None, rtol=1e-10, maxit=1000, stream=None):
         st = pcg_stats()

@@ -265,12 +265,12 @@ __global__ void k_c_prolong_add(CsrV<V> P, const V* e, V* x) {
   if (i < P.n && g == 0) x[i] = cvt<V>(cvt<A>(x[i]) + s);
 }
 
-// group width for a CSR matrix: the power of two nearest half its mean row
-// length, in [1, 32]
-inline int group_width(int64_t nnz, int64_t n) {
+// group width for a CSR matrix: the largest power of two G <= 32 with
+// G * epl <= its mean row length (epl: entries per lane, tuned per solver)
+inline int group_width(int64_t nnz, int64_t n, int epl) {
   const double avg = n > 0 ? (double)nnz / (double)n : 1.0;
   int g = 1;
-  while (g < 32 && 2 * g <= avg) g *= 2;
+  while (g < 32 && 2 * g * epl <= avg) g *= 2;
   return g;
 }
 
@@ -393,7 +393,9 @@ static void vcycle_compact(Solver& S, size_t l, cudaStream_t s) {
   const ChebCoef cc = cheb_coef(L.rho, S.opts.cheb_degree);
   S.nlaunch += 3 + 2 * cc.deg;  // first step, deg-1 steps, residual, restriction, prolongation, deg steps
   const CsrV<V> A = LV::A(L);
-  const int gA = group_width(L.A.nnz, L.A.n), gP = group_width(L.P.nnz, L.P.n), gR = group_width(L.R.nnz, L.R.n);
+  const int e = S.csr_epl;
+  const int gA = group_width(L.A.nnz, L.A.n, e), gP = group_width(L.P.nnz, L.P.n, e),
+            gR = group_width(L.R.nnz, L.R.n, e);
   k_c_cheb_first<V><<<nb, 256, 0, s>>>(n, LV::dinv(L), v.b, v.x, v.d, cc.theta);
   for (int k = 1; k < cc.deg; ++k) {
     EB_GROUP_LAUNCH(gA, k_c_cheb_step, V, n, s, A, LV::dinv(L), v.b, v.x, v.x2, v.d, cc.c1[k], cc.c2[k]);
@@ -454,7 +456,7 @@ static void vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s) {
   Level& C = H.L[1];
   VecSet<V>& cv = LV::vec(C);
   const CsrV<V> R0 = LV::R(L0), P0 = LV::P(L0);
-  const int gR = group_width(L0.R.nnz, L0.R.n), gP = group_width(L0.P.nnz, L0.P.n);
+  const int gR = group_width(L0.R.nnz, L0.R.n, S.csr_epl), gP = group_width(L0.P.nnz, L0.P.n, S.csr_epl);
   EB_GROUP_LAUNCH(gR, k_restrict0, V, C.A.n, s, C.A.n, R0.rp, L0.R0node, R0.v, g.r, cv.b);
   vcycle_compact<V>(S, 1, s);
   EB_GROUP_LAUNCH(gP, k_prolong0, V, P0.n, s, P0.n, P0.rp, P0.ci, P0.v, eb.cp_node, cv.x, x);

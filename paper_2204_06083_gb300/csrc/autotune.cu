@@ -159,4 +159,43 @@ int amg_autotune(amg_handle* amg, int reps, eb_tune_t* out, cudaStream_t stream)
   });
 }
 
+int amg_tune_csr(amg_handle* amg, int reps, double* us_out, int* best_out, cudaStream_t stream) {
+  if (!amg) {
+    set_error("amg_tune_csr: NULL handle");
+    return EB_ERR_INVALID;
+  }
+  return guarded([&] {
+    Solver& S = amg->s;
+    EB_REQUIRE(S.H != nullptr, EB_ERR_INVALID, "amg_tune_csr: handle has no hierarchy");
+    EB_REQUIRE(reps >= 1 && reps <= 100000, EB_ERR_INVALID, "amg_tune_csr: reps in [1, 100000]");
+    const int64_t nn = S.eb->g.num_nodes;
+    double* r = dalloc<double>(nn, stream);
+    double* z = nullptr;
+    try {
+      z = dalloc<double>(nn, stream);
+      const int cand[4] = {1, 2, 4, 8};
+      double us[4];
+      int best = 0;
+      for (int i = 0; i < 4; ++i) {
+        S.csr_epl = cand[i];
+        us[i] = time_us([&] { amg_vcycle_grid(S, r, z, stream); }, reps, stream);
+        if (us[i] < us[best]) best = i;
+      }
+      S.csr_epl = cand[best];
+      S.graph_release();  // captured iterations hold the old launch shapes
+      S.loop_release();
+      if (us_out)
+        for (int i = 0; i < 4; ++i) us_out[i] = us[i];
+      if (best_out) *best_out = cand[best];
+    } catch (...) {
+      dfree(r, stream);
+      dfree(z, stream);
+      throw;
+    }
+    dfree(r, stream);
+    dfree(z, stream);
+    EB_CUDA(cudaStreamSynchronize(stream));
+  });
+}
+
 }  // extern "C"

@@ -28,6 +28,7 @@ struct Solver {
   amg_opts opts{};
   Hierarchy* H = nullptr;
   double setup_ms = 0.0;
+  int csr_epl = 2;  // CSR kernels of the V-cycle: target entries per lane of a row group (amg_tune_csr)
   // full-grid work vectors (touched on the active tiles only)
   double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *tmp = nullptr;
   double* zold = nullptr;  // previous z (flexible CG with a reduced-precision V-cycle)

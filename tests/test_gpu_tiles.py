@@ -159,3 +159,20 @@ def test_amg_on_batch_geometry_outlives_batch_variable():
     assert st.converged
     del amg
     gc.collect()
+
+
+def test_csr_group_tuning_keeps_results():
+    eb = _pkg()
+    grid, ls = ei.ellipsoid_k3(80, seed=2)
+    h = eb.EB(grid, ls)
+    amg = eb.AMG(h, vcycle_prec=eb.EB_F32)
+    b = torch.from_numpy(np.random.default_rng(9).standard_normal(h.shape())).cuda()
+    z0 = amg.vcycle(b)
+    x0, st0 = amg.solve(b, rtol=1e-11)
+    best, us = amg.tune_csr(reps=3)
+    assert best in (1, 2, 4, 8) and min(us.values()) == us[best]
+    z1 = amg.vcycle(b)
+    assert torch.linalg.norm(z1 - z0) <= 1e-5 * torch.linalg.norm(z0)   # FP32 sums regrouped
+    x1, st1 = amg.solve(b, rtol=1e-11)
+    assert abs(st1.iterations - st0.iterations) <= 1
+    assert torch.linalg.norm(x1 - x0) <= 1e-9 * torch.linalg.norm(x0)
