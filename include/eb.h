@@ -334,8 +334,9 @@ int batch_heat_step(batch_handle* b, const double* b1_all, const double* b0_all,
  * Parameters: one float vector of nn_num_params() = 37889 entries,
  *   W1 [32][9][2], b1 [32], 4 x (W [32][9][32], b [32]), W6 [9][32], b6 [1]
  * (W[co][d][ci]).  Hidden activations are stored in bfloat16 (NHWC, 64 bytes
- * per pixel) and the four 32 -> 32 layers run on the tensor cores with bf16
- * weights; every sum is accumulated in float.
+ * per pixel) and the four 32 -> 32 layers run on the tensor cores (tcgen05,
+ * accumulators in tensor memory) with bf16 weights; every sum is accumulated
+ * in float.
  *
  * Images: "images" images of height x width pixels, stored one after the
  * other, row-major (x fastest); each image is zero-padded separately.
@@ -355,6 +356,12 @@ typedef struct nn_handle nn_handle;
 int nn_create(nn_handle** out, cudaStream_t stream);
 void nn_destroy(nn_handle* nn);
 int nn_num_params(void);
+/* The 32 -> 32 layers run on the tensor cores (tcgen05); a wait for them that
+ * gives up (bounded) marks the handle.  nn_status reads and clears the mark:
+ * EB_ERR_TIMEOUT if any convolution since the last check gave up (its
+ * results are invalid), else EB_OK.  nn_get_params and pcg_solve_nn check it
+ * themselves.  Synchronous. */
+int nn_status(nn_handle* nn, cudaStream_t stream);
 /* Copies nn_num_params() floats from HOST memory into the network and resets
  * the Adam state (moments and step count).  Synchronous. */
 int nn_set_params(nn_handle* nn, const float* params_host, cudaStream_t stream);

@@ -126,6 +126,7 @@ _SIGS = {
     "nn_create": (C.c_int, [C.POINTER(_P), _P]),
     "nn_destroy": (None, [_P]),
     "nn_num_params": (C.c_int, []),
+    "nn_status": (C.c_int, [_P, _P]),
     "nn_set_params": (C.c_int, [_P, _P, _P]),
     "nn_get_params": (C.c_int, [_P, _P, _P, _P]),
     "nn_forward": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P]),
@@ -583,6 +584,10 @@ class Net:
             out = torch.empty((nimg, h, w), dtype=torch.float32, device="cuda")
         _check(load().nn_forward(self._h, w, h, nimg, _ptr(inp), _ptr(out), _stream(stream)))
         return out
+
+    def status(self, stream=None):
+        """Raises if a tensor-core wait gave up since the last check."""
+        _check(load().nn_status(self._h, _stream(stream)))
 
     def backward(self, inp, dout, stream=None):
         """Gradient of sum(dout * N(inp)) in the parameters (read with params())."""

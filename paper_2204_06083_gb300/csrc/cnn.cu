@@ -7,12 +7,13 @@
 // Storage: hidden activations BF16 NHWC (32 channels = 64 bytes per pixel);
 // FP32 master parameters, BF16 copies of the 32 -> 32 weights; every sum in
 // FP32.  The four 32 -> 32 layers (99.6 % of the FLOPs) are implicit GEMMs on
-// the tensor cores: a CTA owns 128 pixels of one image row and all 32 output
-// channels; the three input rows it needs (130 pixels x 32 channels) and the
-// 9 x 32 x 32 weights sit in shared memory; K = 9 taps x 32 channels.  Data
-// gradients run through the same kernel with flipped, transposed weights and
-// the ReLU mask of the layer input applied in its epilogue; weight gradients
-// are GEMMs over pixels with per-CTA partials summed in a fixed order.  The
+// the 5th-generation tensor cores (tcgen05.mma, accumulators in tensor memory):
+// a CTA owns 128 pixels of one image row and all 32 output channels; the three
+// input rows it needs (130 pixels x 32 channels) and the 9 x 32 x 32 weights
+// sit in shared memory; K = 9 taps x 32 channels.  Data gradients run through
+// the same kernel with flipped, transposed weights and the ReLU mask of the
+// layer input applied in its epilogue; weight gradients are GEMMs over pixels
+// (mma.sync fragments) with per-CTA partials summed in a fixed order.  The
 // 2 -> 32 and 32 -> 1 layers run on the CUDA cores.
 #include "eb_solver.cuh"
 
@@ -30,8 +31,7 @@ namespace wm = nvcuda::wmma;
 constexpr int NC = 32;    // hidden channels
 constexpr int NMID = 4;   // 32 -> 32 layers
 constexpr int TPX = 128;  // pixels per CTA job (one row segment)
-constexpr int LDA = 48;   // shared-memory pixel stride in bf16 (96 bytes: 32-byte aligned rows)
-constexpr int LDC = 36;   // FP32 epilogue stride
+constexpr int LDA = 48;   // weight-gradient staging: pixel stride in bf16 (96 bytes: 32-byte aligned rows)
 
 // flat parameter vector
 constexpr int W1_N = NC * 9 * 2, B1_N = NC;
@@ -95,62 +95,136 @@ __device__ __forceinline__ void stage_rows(const Image& im, const bf16* __restri
   }
 }
 
-// 32 -> 32 convolution on the tensor cores.  wk: bf16 [9][32 (k)][32 (n)];
-// y = conv + bias (if bias), then ReLU (if relu), then 0 where mask_ref <= 0
-// (if mask_ref: the ReLU derivative of a data gradient).
+// ------------------------------------------- 32 -> 32 convolution (tcgen05)
+// Implicit GEMM on the 5th-generation tensor cores: a CTA owns a job of 128
+// pixels of one image row (M = 128) and all 32 output channels (N = 32); K = 9
+// taps x 32 input channels = 18 MMAs of 128 x 32 x 16 (bf16 in, f32 in TMEM).
+// Shared-memory operands use the no-swizzle K-major layout of "core matrices"
+// (8 rows x 16 bytes stored contiguously):
+//   A: the three input rows of the job, [channel group g (8 ch)][row][pixel][8 ch];
+//      for tap (dy, dx) and channel half kh the operand starts at group 2 kh,
+//      row dy, pixel dx: consecutive pixels are the M rows (SBO = 128 B), the
+//      next channel group the next K core matrix (LBO = one group plane);
+//   B: the weights, [tap][channel group g][n][8 k] (SBO = 128 B between 8-row
+//      blocks of n, LBO = 32 x 16 B between channel groups).
+// One thread issues the MMAs and commits them to an mbarrier; the four warps
+// wait (bounded), read their 32 TMEM lanes (= their 32 pixels) and run the
+// epilogue.  A wait that gives up sets *err and ends the CTA's loop.
+constexpr int TC_PIX = TPX + 2;
+constexpr int TC_GROUP = 3 * TC_PIX * 16;        // one channel group of the three rows (bytes)
+constexpr int TC_A = 4 * TC_GROUP;               // 24,960
+constexpr int TC_WTAP = 4 * NC * 16;             // 2048 per tap
+constexpr int TC_W = 9 * TC_WTAP;                // 18,432
+constexpr int TC_BAR = TC_A + TC_W;              // mbarrier (8 bytes), TMEM address slot after it
+constexpr int TC_SMEM = TC_BAR + 16;
+constexpr uint32_t TC_SPIN = 1u << 22;           // bounded mbarrier polls (~0.1 s)
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start, LBO, SBO (bytes), version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor of kind::f16: D f32, A and B bf16, both K-major, N, M
+__device__ __forceinline__ constexpr uint32_t tc_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok = 0;
+  for (uint32_t it = 0; it < TC_SPIN && !ok; ++it)
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+  return ok != 0;
+}
+
+// y = conv(x; wk) + bias (if bias), then ReLU (if relu), then 0 where mask_ref <= 0
+// (if mask_ref: the ReLU derivative of a data gradient).  wk: bf16 [9][32 (n)][32 (k)].
 __global__ void __launch_bounds__(128) k_conv32(Image im, const bf16* __restrict__ x, const bf16* __restrict__ wk,
                                                 const float* __restrict__ bias, bf16* __restrict__ y, int relu,
-                                                const bf16* __restrict__ mask_ref) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  bf16* sIn = reinterpret_cast<bf16*>(smem_raw);   // [3][TPX + 2][LDA]
-  bf16* sW = sIn + 3 * (TPX + 2) * LDA;            // [9 * 32][LDA]
-  float* sC = reinterpret_cast<float*>(smem_raw);  // [TPX][LDC], aliases sIn after the MMAs
-  const int segs = (im.W + TPX - 1) / TPX;
+                                                const bf16* __restrict__ mask_ref, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* sA = smem_raw;
+  unsigned char* sW = smem_raw + TC_A;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + TC_BAR);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem_raw + TC_BAR + 8);
   const int tid = threadIdx.x, warp = tid >> 5;
-  for (int i = tid; i < 9 * NC * 4; i += blockDim.x) {
-    const int row = i >> 2, q = i & 3;
-    *reinterpret_cast<int4*>(sW + row * LDA + q * 8) = *reinterpret_cast<const int4*>(wk + row * NC + q * 8);
+  const uint32_t a0 = smem_addr(sA), w0 = smem_addr(sW), bar_a = smem_addr(bar);
+  for (int i = tid; i < 9 * NC * 4; i += blockDim.x) {  // weights once per CTA
+    const int g = i & 3, n = (i >> 2) % NC, d = (i >> 2) / NC;
+    *reinterpret_cast<int4*>(sW + d * TC_WTAP + g * (NC * 16) + n * 16) =
+        *reinterpret_cast<const int4*>(wk + (d * NC + n) * NC + g * 8);
   }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_addr(tslot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tslot;
   float bv[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) bv[c] = bias ? bias[c] : 0.0f;
+  const int segs = (im.W + TPX - 1) / TPX;
   const int64_t jobs = (int64_t)segs * im.H;
-  for (int64_t job = blockIdx.x; job < jobs; job += gridDim.x) {
+  uint32_t phase = 0;
+  for (int64_t job = blockIdx.x; job < jobs; job += gridDim.x, phase ^= 1u) {
     const int r = (int)(job / segs), x0 = (int)(job % segs) * TPX;
-    __syncthreads();  // the previous job's epilogue is done with sC / sIn
-    stage_rows(im, x, r, x0, sIn);
-    __syncthreads();
-    wm::fragment<wm::accumulator, 16, 16, 16, float> acc[2][2];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-      for (int b = 0; b < 2; ++b) wm::fill_fragment(acc[a][b], 0.0f);
-#pragma unroll 1
-    for (int d = 0; d < 9; ++d) {
-      const int dy = d / 3, dx = d % 3;
-#pragma unroll
-      for (int cb = 0; cb < 2; ++cb) {
-        wm::fragment<wm::matrix_a, 16, 16, 16, bf16, wm::row_major> fa[2];
-        wm::fragment<wm::matrix_b, 16, 16, 16, bf16, wm::row_major> fb[2];
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-          wm::load_matrix_sync(fa[mt], sIn + (dy * (TPX + 2) + 32 * warp + 16 * mt + dx) * LDA + cb * 16, LDA);
-#pragma unroll
-        for (int nt = 0; nt < 2; ++nt) wm::load_matrix_sync(fb[nt], sW + (d * NC + cb * 16) * LDA + nt * 16, LDA);
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-          for (int nt = 0; nt < 2; ++nt) wm::mma_sync(acc[mt][nt], fa[mt], fb[nt], acc[mt][nt]);
-      }
+    const int lo = (r / im.R) * im.R, hi = lo + im.R;
+    for (int i = tid; i < 3 * TC_PIX * 4; i += blockDim.x) {
+      const int g = i & 3, px = (i >> 2) % TC_PIX, rr = (i >> 2) / TC_PIX;
+      const int gx = x0 - 1 + px, gr = r - 1 + rr;
+      int4 v = make_int4(0, 0, 0, 0);
+      if (gx >= 0 && gx < im.W && gr >= lo && gr < hi)
+        v = *reinterpret_cast<const int4*>(x + ((int64_t)gr * im.W + gx) * NC + g * 8);
+      *reinterpret_cast<int4*>(sA + g * TC_GROUP + (rr * TC_PIX + px) * 16) = v;
     }
-    __syncthreads();  // all warps are done reading sIn before it becomes sC
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-      for (int nt = 0; nt < 2; ++nt)
-        wm::store_matrix_sync(sC + (32 * warp + 16 * mt) * LDC + nt * 16, acc[mt][nt], LDC, wm::mem_row_major);
+    asm volatile("fence.proxy.async.shared::cta;");  // the tensor cores read what the threads wrote
+    asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    const int gx = x0 + tid;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+      constexpr uint32_t idesc = tc_idesc(128, NC);
+#pragma unroll 1
+      for (int k = 0; k < 18; ++k) {
+        const int d = k >> 1, kh = k & 1, dy = d / 3, dx = d % 3;
+        const uint64_t da = tc_desc(a0 + (2 * kh) * TC_GROUP + (dy * TC_PIX + dx) * 16, TC_GROUP, 128);
+        const uint64_t db = tc_desc(w0 + d * TC_WTAP + (2 * kh) * (NC * 16), NC * 16, 128);
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(idesc), "r"((uint32_t)(k > 0)));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_a)
+                   : "memory");
+    }
+    // the CTA decides together, so that every thread leaves the loop or none
+    if (!__syncthreads_and(tc_wait(bar_a, phase) ? 1 : 0)) {
+      if (tid == 0) atomicExch(err, 1);
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    uint32_t v[NC];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+          "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(tmem + ((uint32_t)(warp * 32) << 16)));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int gx = x0 + tid;  // TMEM lane tid = pixel x0 + tid
     if (gx < im.W) {
       const int64_t p = (int64_t)r * im.W + gx;
       __align__(16) bf16 ov[NC];
@@ -162,15 +236,21 @@ __global__ void __launch_bounds__(128) k_conv32(Image im, const bf16* __restrict
       }
 #pragma unroll
       for (int co = 0; co < NC; ++co) {
-        float v = sC[tid * LDC + co] + bv[co];
-        if (relu) v = fmaxf(v, 0.0f);
-        if (mask_ref && !(__bfloat162float(mr[co]) > 0.0f)) v = 0.0f;
-        ov[co] = __float2bfloat16_rn(v);
+        float f = __uint_as_float(v[co]) + bv[co];
+        if (relu) f = fmaxf(f, 0.0f);
+        if (mask_ref && !(__bfloat162float(mr[co]) > 0.0f)) f = 0.0f;
+        ov[co] = __float2bfloat16_rn(f);
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) reinterpret_cast<int4*>(y + p * NC)[q] = reinterpret_cast<const int4*>(ov)[q];
     }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();  // staging buffer and accumulator are free for the next job
+    asm volatile("tcgen05.fence::after_thread_sync;");
   }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
 }
 
 // layer 6 (32 -> 1); out = m * (conv + b6)
@@ -239,77 +319,123 @@ __device__ __forceinline__ void chunk_of(int64_t n, int b, int nb, int64_t& p0, 
   p1 = p0 + c < n ? p0 + c : n;
 }
 
-// layer 6 gradient partials: slot d * 32 + ci: sum g6[p] y5[p + off(d)][ci]; slot 288: sum g6[p]
-__global__ void __launch_bounds__(320) k_l6_wgrad(Image im, const float* __restrict__ dout,
+// layer 6 gradient partials: slot d * 32 + ci: sum g6[p] y5[p + off(d)][ci]; slot 288: sum g6[p].
+// A warp walks pixels of the CTA's chunk (lane = input channel, 9 tap sums in
+// registers); the 8 warps' sums are added in a fixed order.
+__global__ void __launch_bounds__(256) k_l6_wgrad(Image im, const float* __restrict__ dout,
                                                   const float2* __restrict__ in, const bf16* __restrict__ y5,
                                                   float* __restrict__ part) {
-  const int slot = threadIdx.x;
-  if (slot > W6_N) return;
-  const int d = slot / NC, ci = slot % NC;
-  const int dx = d % 3 - 1, dy = d / 3 - 1;
+  __shared__ float sm[8][W6_N + B6_N];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int64_t p0, p1;
   chunk_of(im.npx(), blockIdx.x, gridDim.x, p0, p1);
-  float a = 0.0f;
-  for (int64_t p = p0; p < p1; ++p) {
-    const float g = dout[p] * in[p].y;
-    if (g == 0.0f) continue;
-    if (slot == W6_N) {
-      a += g;
-      continue;
+  float acc[9], bacc = 0.0f;
+#pragma unroll
+  for (int d = 0; d < 9; ++d) acc[d] = 0.0f;
+  // 4 pixels per step, their loads issued before the sums (latency hiding)
+  for (int64_t pb = p0 + w; pb < p1; pb += 32) {
+    float g[4], v[4][9];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t p = pb + 8 * u;
+      g[u] = p < p1 ? dout[p] * in[p].y : 0.0f;
+      const int x = (int)(p % im.W), r = (int)(p / im.W);
+      const int lo = (r / im.R) * im.R, hi = lo + im.R;
+#pragma unroll
+      for (int d = 0; d < 9; ++d) {
+        const int xx = x + d % 3 - 1, rr = r + d / 3 - 1;
+        v[u][d] = (p < p1 && xx >= 0 && xx < im.W && rr >= lo && rr < hi)
+                      ? __bfloat162float(y5[((int64_t)rr * im.W + xx) * NC + lane])
+                      : 0.0f;
+      }
     }
-    const int x = (int)(p % im.W) + dx, r = (int)(p / im.W);
-    const int lo = (r / im.R) * im.R, rr = r + dy;
-    if (x < 0 || x >= im.W || rr < lo || rr >= lo + im.R) continue;
-    a += g * __bfloat162float(y5[((int64_t)rr * im.W + x) * NC + ci]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      bacc += g[u];
+#pragma unroll
+      for (int d = 0; d < 9; ++d) acc[d] += g[u] * v[u][d];
+    }
   }
-  part[(int64_t)blockIdx.x * (W6_N + B6_N) + slot] = a;
+#pragma unroll
+  for (int d = 0; d < 9; ++d) sm[w][d * NC + lane] = acc[d];
+  if (lane == 0) sm[w][W6_N] = bacc;
+  __syncthreads();
+  for (int i = threadIdx.x; i < W6_N + B6_N; i += blockDim.x) {
+    float t = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += sm[k][i];
+    part[(int64_t)blockIdx.x * (W6_N + B6_N) + i] = t;
+  }
 }
 
 // layer 1 gradient partials: slot (co * 9 + d) * 2 + ci: sum dy1[p][co] in[p + off(d)][ci];
-// slot 576 + co: sum dy1[p][co]
-__global__ void __launch_bounds__(640) k_l1_wgrad(Image im, const bf16* __restrict__ dy1,
+// slot 576 + co: sum dy1[p][co].  A warp walks pixels (lane = output channel).
+__global__ void __launch_bounds__(256) k_l1_wgrad(Image im, const bf16* __restrict__ dy1,
                                                   const float2* __restrict__ in, float* __restrict__ part) {
-  const int slot = threadIdx.x;
-  if (slot >= W1_N + B1_N) return;
+  __shared__ float sm[8][W1_N + B1_N];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int64_t p0, p1;
   chunk_of(im.npx(), blockIdx.x, gridDim.x, p0, p1);
-  float a = 0.0f;
-  if (slot < W1_N) {
-    const int co = slot / 18, d = (slot / 2) % 9, ci = slot & 1;
-    const int dx = d % 3 - 1, dy = d / 3 - 1;
-    for (int64_t p = p0; p < p1; ++p) {
-      const float g = __bfloat162float(dy1[p * NC + co]);
-      if (g == 0.0f) continue;
-      const int x = (int)(p % im.W) + dx, r = (int)(p / im.W);
-      const int lo = (r / im.R) * im.R, rr = r + dy;
-      if (x < 0 || x >= im.W || rr < lo || rr >= lo + im.R) continue;
-      const float2 v = in[(int64_t)rr * im.W + x];
-      a += g * (ci ? v.y : v.x);
+  float acc[9][2], bacc = 0.0f;
+#pragma unroll
+  for (int d = 0; d < 9; ++d) acc[d][0] = acc[d][1] = 0.0f;
+  // 4 pixels per step, their loads issued before the sums (latency hiding)
+  for (int64_t pb = p0 + w; pb < p1; pb += 32) {
+    float g[4];
+    float2 v[4][9];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t p = pb + 8 * u;
+      g[u] = p < p1 ? __bfloat162float(dy1[p * NC + lane]) : 0.0f;
+      const int x = (int)(p % im.W), r = (int)(p / im.W);
+      const int lo = (r / im.R) * im.R, hi = lo + im.R;
+#pragma unroll
+      for (int d = 0; d < 9; ++d) {
+        const int xx = x + d % 3 - 1, rr = r + d / 3 - 1;
+        v[u][d] = (p < p1 && xx >= 0 && xx < im.W && rr >= lo && rr < hi) ? in[(int64_t)rr * im.W + xx]
+                                                                            : make_float2(0.0f, 0.0f);
+      }
     }
-  } else {
-    const int co = slot - W1_N;
-    for (int64_t p = p0; p < p1; ++p) a += __bfloat162float(dy1[p * NC + co]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      bacc += g[u];
+#pragma unroll
+      for (int d = 0; d < 9; ++d) {
+        acc[d][0] += g[u] * v[u][d].x;
+        acc[d][1] += g[u] * v[u][d].y;
+      }
+    }
   }
-  part[(int64_t)blockIdx.x * (W1_N + B1_N) + slot] = a;
+#pragma unroll
+  for (int d = 0; d < 9; ++d) {
+    sm[w][(lane * 9 + d) * 2] = acc[d][0];
+    sm[w][(lane * 9 + d) * 2 + 1] = acc[d][1];
+  }
+  sm[w][W1_N + lane] = bacc;
+  __syncthreads();
+  for (int i = threadIdx.x; i < W1_N + B1_N; i += blockDim.x) {
+    float t = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += sm[k][i];
+    part[(int64_t)blockIdx.x * (W1_N + B1_N) + i] = t;
+  }
 }
 
-// 32 -> 32 weight-gradient partials on the tensor cores:
-// part[cta][d][k = ci][n = co] = sum_p x[p + off(d)][ci] dy[p][co]
+// 32 -> 32 weight-gradient partials on the tensor cores (mma.sync fragments):
+// part[cta][d][k = ci][n = co] = sum_p x[p + off(d)][ci] dy[p][co].
+// Warp w owns the 16 x 16 quadrant (ci block w >> 1, co block w & 1) of all 9
+// taps: per 16-pixel step it loads one dy fragment and 9 shifted x fragments.
 __global__ void __launch_bounds__(128) k_conv32_wgrad(Image im, const bf16* __restrict__ x,
                                                       const bf16* __restrict__ dy, float* __restrict__ part) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
   bf16* sIn = reinterpret_cast<bf16*>(smem_raw);  // [3][TPX + 2][LDA]
   bf16* sDy = sIn + 3 * (TPX + 2) * LDA;          // [TPX][LDA]
   const int segs = (im.W + TPX - 1) / TPX;
   const int tid = threadIdx.x, warp = tid >> 5;
-  // warp w owns the taps w, w + 4, w + 8 (< 9)
-  wm::fragment<wm::accumulator, 16, 16, 16, float> acc[3][2][2];
+  const int kb = warp >> 1, nb = warp & 1;
+  wm::fragment<wm::accumulator, 16, 16, 16, float> acc[9];
 #pragma unroll
-  for (int t = 0; t < 3; ++t)
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-      for (int b = 0; b < 2; ++b) wm::fill_fragment(acc[t][a][b], 0.0f);
+  for (int d = 0; d < 9; ++d) wm::fill_fragment(acc[d], 0.0f);
   const int64_t jobs = (int64_t)segs * im.H;
   for (int64_t job = blockIdx.x; job < jobs; job += gridDim.x) {
     const int r = (int)(job / segs), x0 = (int)(job % segs) * TPX;
@@ -322,40 +448,22 @@ __global__ void __launch_bounds__(128) k_conv32_wgrad(Image im, const bf16* __re
       *reinterpret_cast<int4*>(sDy + px * LDA + q * 8) = v;
     }
     __syncthreads();
+#pragma unroll 1
+    for (int ks = 0; ks < TPX / 16; ++ks) {
+      wm::fragment<wm::matrix_b, 16, 16, 16, bf16, wm::row_major> fb;
+      wm::load_matrix_sync(fb, sDy + (16 * ks) * LDA + nb * 16, LDA);
 #pragma unroll
-    for (int t = 0; t < 3; ++t) {
-      const int d = warp + 4 * t;
-      if (d < 9) {
-        const int ty = d / 3, tx = d % 3;
-#pragma unroll 2
-        for (int ks = 0; ks < TPX / 16; ++ks) {
-          wm::fragment<wm::matrix_a, 16, 16, 16, bf16, wm::col_major> fa[2];
-          wm::fragment<wm::matrix_b, 16, 16, 16, bf16, wm::row_major> fb[2];
-#pragma unroll
-          for (int kb = 0; kb < 2; ++kb)
-            wm::load_matrix_sync(fa[kb], sIn + (ty * (TPX + 2) + 16 * ks + tx) * LDA + kb * 16, LDA);
-#pragma unroll
-          for (int nb = 0; nb < 2; ++nb) wm::load_matrix_sync(fb[nb], sDy + (16 * ks) * LDA + nb * 16, LDA);
-#pragma unroll
-          for (int kb = 0; kb < 2; ++kb)
-#pragma unroll
-            for (int nb = 0; nb < 2; ++nb) wm::mma_sync(acc[t][kb][nb], fa[kb], fb[nb], acc[t][kb][nb]);
-        }
+      for (int d = 0; d < 9; ++d) {
+        wm::fragment<wm::matrix_a, 16, 16, 16, bf16, wm::col_major> fa;
+        wm::load_matrix_sync(fa, sIn + ((d / 3) * (TPX + 2) + 16 * ks + d % 3) * LDA + kb * 16, LDA);
+        wm::mma_sync(acc[d], fa, fb, acc[d]);
       }
     }
   }
   float* out = part + (int64_t)blockIdx.x * WM_N;
 #pragma unroll
-  for (int t = 0; t < 3; ++t) {
-    const int d = warp + 4 * t;
-    if (d < 9) {
-#pragma unroll
-      for (int kb = 0; kb < 2; ++kb)
-#pragma unroll
-        for (int nb = 0; nb < 2; ++nb)
-          wm::store_matrix_sync(out + (d * NC + 16 * kb) * NC + 16 * nb, acc[t][kb][nb], NC, wm::mem_row_major);
-    }
-  }
+  for (int d = 0; d < 9; ++d)
+    wm::store_matrix_sync(out + (d * NC + 16 * kb) * NC + 16 * nb, acc[d], NC, wm::mem_row_major);
 }
 
 // bias-gradient partials of a 32-channel gradient: part[cta][c] = sum over the CTA's pixels
@@ -397,16 +505,17 @@ __global__ void k_sum_wgrad(const float* __restrict__ part, int nparts, float* _
 }
 
 // ------------------------------------------------------------- weights
-// forward: wf[l][d][k = ci][n = co] = W_l[co][d][ci]
-// data gradient: wb[l][8 - d][k = co][n = ci] = W_l[co][d][ci]
+// B operands of k_conv32, [tap][n][k]:
+// forward: wf[l][d][n = co][k = ci] = W_l[co][d][ci]
+// data gradient: wb[l][8 - d][n = ci][k = co] = W_l[co][d][ci]
 __global__ void k_pack_weights(const float* __restrict__ P, bf16* __restrict__ wf, bf16* __restrict__ wb) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= NMID * WM_N) return;
   const int l = i / WM_N, rem = i % WM_N;
   const int co = rem / (9 * NC), d = (rem / NC) % 9, ci = rem % NC;
   const bf16 w = __float2bfloat16_rn(P[off_wm(l) + rem]);
-  wf[(int64_t)l * WM_N + (d * NC + ci) * NC + co] = w;
-  wb[(int64_t)l * WM_N + ((8 - d) * NC + co) * NC + ci] = w;
+  wf[(int64_t)l * WM_N + (d * NC + co) * NC + ci] = w;
+  wb[(int64_t)l * WM_N + ((8 - d) * NC + ci) * NC + co] = w;
 }
 
 __global__ void k_adam(int n, float* __restrict__ P, const float* __restrict__ G, float* __restrict__ m,
@@ -686,6 +795,7 @@ struct NN {
   float* G = nullptr;  // gradient
   float* m = nullptr;  // Adam moments
   float* v = nullptr;
+  int* err = nullptr;  // set by a convolution whose tensor-core wait gave up
   bf16* wf = nullptr;  // packed forward weights of the middle layers
   bf16* wb = nullptr;  // packed data-gradient weights
   int64_t steps = 0;
@@ -716,7 +826,7 @@ struct NN {
   int snblk = 0;
 };
 
-static size_t conv_smem() { return (size_t)(3 * (TPX + 2) * LDA + 9 * NC * LDA) * sizeof(bf16); }
+static size_t conv_smem() { return (size_t)TC_SMEM; }
 static size_t wgrad_smem() { return (size_t)(3 * (TPX + 2) * LDA + TPX * LDA) * sizeof(bf16); }
 
 static void set_attrs() {
@@ -774,8 +884,8 @@ static void forward(NN& N, const Image& im, const float2* in, float* out, cudaSt
   k_l1_fwd<<<blocks_for(npx, 128), 128, 0, s>>>(im, in, N.P, N.act[1]);
   for (int l = 0; l < NMID; ++l) {
     if (prof) prof->prof_mark(s, true, PROF_CONV);
-    k_conv32<<<conv_grid(im, 3), 128, conv_smem(), s>>>(im, N.act[l + 1], N.wf + (int64_t)l * WM_N,
-                                                         N.P + off_wm(l) + WM_N, N.act[l + 2], 1, nullptr);
+    k_conv32<<<conv_grid(im, 4), 128, conv_smem(), s>>>(im, N.act[l + 1], N.wf + (int64_t)l * WM_N,
+                                                         N.P + off_wm(l) + WM_N, N.act[l + 2], 1, nullptr, N.err);
     if (prof) prof->prof_mark(s, false, PROF_CONV);
   }
   k_l6_fwd<<<blocks_for(npx, 128), 128, 0, s>>>(im, N.act[5], N.P, in, out);
@@ -790,7 +900,7 @@ static void backward(NN& N, const Image& im, const float2* in, const float* dout
   {
     const int nb = nsm * 4;
     float* part = ensure_part(N, (int64_t)nb * (W6_N + B6_N), s);
-    k_l6_wgrad<<<nb, 320, 0, s>>>(im, dout, in, N.act[5], part);
+    k_l6_wgrad<<<nb, 256, 0, s>>>(im, dout, in, N.act[5], part);
     k_sum_parts<<<blocks_for(W6_N + B6_N, 256), 256, 0, s>>>(part, nb, W6_N + B6_N, N.G + OFF_W6);
     k_l6_bwd<<<blocks_for(npx, 128), 128, 0, s>>>(im, dout, in, N.act[5], N.P, N.gA);
     nl += 3;
@@ -805,15 +915,15 @@ static void backward(NN& N, const Image& im, const float2* in, const float* dout
     k_sum_wgrad<<<blocks_for(WM_N, 256), 256, 0, s>>>(part, (int)gw, N.G + off_wm(l));
     k_bias_grad<<<nbb, 256, 0, s>>>(npx, cur, part);
     k_sum_parts<<<1, 32, 0, s>>>(part, nbb, NC, N.G + off_wm(l) + WM_N);
-    k_conv32<<<conv_grid(im, 3), 128, conv_smem(), s>>>(im, cur, N.wb + (int64_t)l * WM_N, nullptr, nxt, 0,
-                                                         N.act[l + 1]);
+    k_conv32<<<conv_grid(im, 4), 128, conv_smem(), s>>>(im, cur, N.wb + (int64_t)l * WM_N, nullptr, nxt, 0,
+                                                         N.act[l + 1], N.err);
     std::swap(cur, nxt);
     nl += 5;
   }
   {
     const int nb = nsm * 4;
     float* part = ensure_part(N, (int64_t)nb * (W1_N + B1_N), s);
-    k_l1_wgrad<<<nb, 640, 0, s>>>(im, cur, in, part);
+    k_l1_wgrad<<<nb, 256, 0, s>>>(im, cur, in, part);
     k_sum_parts<<<blocks_for(W1_N + B1_N, 256), 256, 0, s>>>(part, nb, W1_N + B1_N, N.G + OFF_W1);
     nl += 2;
   }
@@ -918,6 +1028,7 @@ int nn_create(nn_handle** out, cudaStream_t stream) {
     N.v = dalloc<float>(NPARAM, stream);
     N.wf = dalloc<bf16>(NMID * WM_N, stream);
     N.wb = dalloc<bf16>(NMID * WM_N, stream);
+    N.err = dalloc<int>(1, stream);
     EB_CUDA(cudaStreamSynchronize(stream));
   });
   if (st != EB_OK) {
@@ -932,7 +1043,7 @@ void nn_destroy(nn_handle* h) {
   if (!h) return;
   NN& N = h->n;
   cudaStream_t s = N.home;
-  dfree(N.P, s); dfree(N.G, s); dfree(N.m, s); dfree(N.v, s); dfree(N.wf, s); dfree(N.wb, s);
+  dfree(N.P, s); dfree(N.G, s); dfree(N.m, s); dfree(N.v, s); dfree(N.wf, s); dfree(N.wb, s); dfree(N.err, s);
   for (int l = 1; l <= 5; ++l) dfree(N.act[l], s);
   dfree(N.gA, s); dfree(N.gB, s); dfree(N.out, s); dfree(N.dout, s); dfree(N.in, s); dfree(N.code, s);
   dfree(N.diag, s); dfree(N.part, s); dfree(N.lpart, s); dfree(N.cimg, s); dfree(N.loss, s);
@@ -942,6 +1053,25 @@ void nn_destroy(nn_handle* h) {
 }
 
 int nn_num_params(void) { return NPARAM; }
+
+int nn_status(nn_handle* h, cudaStream_t stream) {
+  if (!h) {
+    set_error("nn_status: NULL handle");
+    return EB_ERR_INVALID;
+  }
+  int flag = 0;
+  int st = guarded([&] {
+    EB_CUDA(cudaMemcpyAsync(&flag, h->n.err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    EB_CUDA(cudaMemsetAsync(h->n.err, 0, sizeof(int), stream));
+    EB_CUDA(cudaStreamSynchronize(stream));
+  });
+  if (st != EB_OK) return st;
+  if (flag) {
+    set_error("nn: a tensor-core wait in a convolution gave up (results of that call are invalid)");
+    return EB_ERR_TIMEOUT;
+  }
+  return EB_OK;
+}
 
 int nn_set_params(nn_handle* h, const float* params_host, cudaStream_t stream) {
   if (!h || !params_host) {
@@ -965,6 +1095,7 @@ int nn_get_params(const nn_handle* h, float* params_host, float* grad_host, cuda
     set_error("nn_get_params: NULL handle");
     return EB_ERR_INVALID;
   }
+  if (int ns = nn_status(const_cast<nn_handle*>(h), stream)) return ns;
   return guarded([&] {
     const NN& N = h->n;
     if (params_host)
@@ -1173,7 +1304,9 @@ int pcg_solve_nn(const amg_handle* amg, nn_handle* nn, int mode, const double* b
     }
     S.nn = nullptr;
   });
-  return st != EB_OK ? st : rc;
+  if (st != EB_OK) return st;
+  const int ns = nn_status(nn, stream);
+  return ns != EB_OK ? ns : rc;
 }
 
 }  // extern "C"
