@@ -145,7 +145,7 @@ __device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
 
 // y = conv(x; wk) + bias (if bias), then ReLU (if relu), then 0 where mask_ref <= 0
 // (if mask_ref: the ReLU derivative of a data gradient).  wk: bf16 [9][32 (n)][32 (k)].
-__global__ void __launch_bounds__(128) k_conv32(Image im, const bf16* __restrict__ x, const bf16* __restrict__ wk,
+__global__ void __launch_bounds__(128, 4) k_conv32(Image im, const bf16* __restrict__ x, const bf16* __restrict__ wk,
                                                 const float* __restrict__ bias, bf16* __restrict__ y, int relu,
                                                 const bf16* __restrict__ mask_ref, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -181,13 +181,26 @@ __global__ void __launch_bounds__(128) k_conv32(Image im, const bf16* __restrict
   for (int64_t job = blockIdx.x; job < jobs; job += gridDim.x, phase ^= 1u) {
     const int r = (int)(job / segs), x0 = (int)(job % segs) * TPX;
     const int lo = (r / im.R) * im.R, hi = lo + im.R;
-    for (int i = tid; i < 3 * TC_PIX * 4; i += blockDim.x) {
-      const int g = i & 3, px = (i >> 2) % TC_PIX, rr = (i >> 2) / TC_PIX;
-      const int gx = x0 - 1 + px, gr = r - 1 + rr;
-      int4 v = make_int4(0, 0, 0, 0);
-      if (gx >= 0 && gx < im.W && gr >= lo && gr < hi)
-        v = *reinterpret_cast<const int4*>(x + ((int64_t)gr * im.W + gx) * NC + g * 8);
-      *reinterpret_cast<int4*>(sA + g * TC_GROUP + (rr * TC_PIX + px) * 16) = v;
+    // stage the three rows: 4 loads in flight per thread before their stores
+    for (int i0 = 0; i0 < 3 * TC_PIX * 4; i0 += 4 * 128) {
+      int4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + tid + 128 * u;
+        const int g = i & 3, px = (i >> 2) % TC_PIX, rr = (i >> 2) / TC_PIX;
+        const int gx = x0 - 1 + px, gr = r - 1 + rr;
+        v[u] = make_int4(0, 0, 0, 0);
+        if (i < 3 * TC_PIX * 4 && gx >= 0 && gx < im.W && gr >= lo && gr < hi)
+          v[u] = *reinterpret_cast<const int4*>(x + ((int64_t)gr * im.W + gx) * NC + g * 8);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + tid + 128 * u;
+        if (i < 3 * TC_PIX * 4) {
+          const int g = i & 3, px = (i >> 2) % TC_PIX, rr = (i >> 2) / TC_PIX;
+          *reinterpret_cast<int4*>(sA + g * TC_GROUP + (rr * TC_PIX + px) * 16) = v[u];
+        }
+      }
     }
     asm volatile("fence.proxy.async.shared::cta;");  // the tensor cores read what the threads wrote
     asm volatile("tcgen05.fence::before_thread_sync;");
