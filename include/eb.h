@@ -28,7 +28,8 @@
  *     noted "synchronous" (those read a result back to the host).
  *   - Handles own all their device memory and are released by *_destroy.
  *     A handle built on another (an AMG hierarchy on its grid, a geometry
- *     borrowed from a batch) must be destroyed before the one it was built on.
+ *     borrowed from a batch) must not be used after the one it was built on
+ *     is destroyed; destroying it is allowed in either order.
  */
 #ifndef EB_H_
 #define EB_H_

@@ -601,6 +601,40 @@ __global__ void k_map_cols(int64_t nnz, const int32_t* ci, const int32_t* map, i
   if (e < nnz) out[e] = map[ci[e]];
 }
 
+// ---------------------------------------- matrix-free level-0 prolongation data
+__global__ void k_agg_node(int64_t ncp, const int32_t* cp_node, const int32_t* agg, int32_t* agg_node) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < ncp) agg_node[cp_node[k]] = agg[k];
+}
+
+__global__ void k_agg_scale(int64_t nc, const int32_t* size, double* sc64, float* sc32) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const double v = __ddiv_rn(1.0, __dsqrt_rn((double)size[c]));  // the P_hat value of k_phat
+  sc64[c] = v;
+  sc32[c] = (float)v;
+}
+
+static void build_mf(MatrixFreeP& M, const EBHandle& eb, const Level& L0, int32_t nc, const int32_t* size,
+                     cudaStream_t s) {
+  const int64_t ncp = eb.num_cp, nn = eb.g.num_nodes;
+  M.omega = 4.0 / (3.0 * L0.rho);
+  M.nc = nc;
+  M.agg_node = dalloc<int32_t>(nn, s, false);
+  EB_CUDA(cudaMemsetAsync(M.agg_node, 0xFF, sizeof(int32_t) * nn, s));
+  k_agg_node<<<blocks_for(ncp, 256), 256, 0, s>>>(ncp, eb.cp_node, L0.agg, M.agg_node);
+  M.sc64 = dalloc<double>(nc, s, false);
+  M.sc32 = dalloc<float>(nc, s, false);
+  k_agg_scale<<<blocks_for(nc, 256), 256, 0, s>>>(nc, size, M.sc64, M.sc32);
+  EB_CUDA(cudaGetLastError());
+  M.on = true;
+}
+
+static void free_mf(MatrixFreeP& M, cudaStream_t s) {
+  dfree(M.agg_node, s); dfree(M.sc64, s); dfree(M.sc32, s);
+  M.on = false;
+}
+
 // level-0 matrix sigma I + A over the CPs of one grid, in CSR
 DCsr level0_csr(const EBHandle& eb, double sigma, cudaStream_t s) {
   const Geometry& G = eb.g;
@@ -704,6 +738,8 @@ void amg_build_from(Solver& S, DCsr A0, cudaStream_t s) {
     EB_CUDA(cudaGetLastError());
     L.P = T;
     csr_free(Ph, s);
+    // a single grid (no per-tile shifts) applies the level-0 P and R matrix free
+    if (lev == 0 && eb.tile_shift64 == nullptr && A.n == eb.num_cp) build_mf(H->mf, eb, L, nc, size, s);
     dfree(size, s);
     L.R = transpose(L.P, s);
     if (lev == 0) {
@@ -725,9 +761,10 @@ void amg_build_from(Solver& S, DCsr A0, cudaStream_t s) {
 
 void amg_free(Solver& S) {
   if (!S.H) return;
-  cudaStream_t s = S.eb->home;
+  cudaStream_t s = S.home;
   Hierarchy* H = S.H;
   amg_free_vcycle(*H, s);
+  free_mf(H->mf, s);
   for (Level& L : H->L) {
     csr_free(L.A, s);
     csr_free(L.P, s);

@@ -42,10 +42,23 @@ struct Level {
   __nv_bfloat16 *A16 = nullptr, *P16 = nullptr, *R16 = nullptr, *dinv16 = nullptr;
 };
 
+// Level-0 prolongation applied matrix free (single grids): with
+// P = (I - omega D^-1 A) P_hat, x += P e is one stencil pass over the tiles on
+// t = P_hat e, t_j = e[agg(j)] / sqrt(|agg(j)|).
+struct MatrixFreeP {
+  bool on = false;
+  double omega = 0.0;             // 4 / (3 rho_0)
+  int32_t* agg_node = nullptr;    // [num_nodes] aggregate of a CP node, -1 elsewhere
+  double* sc64 = nullptr;         // [nc] P_hat value of aggregate c: 1 / sqrt(|c|)
+  float* sc32 = nullptr;
+  int64_t nc = 0;
+};
+
 struct Hierarchy {
   std::vector<Level> L;
   double* coarse_inv = nullptr;  // FP64 inverse of the coarsest matrix
   int64_t nc = 0;
+  MatrixFreeP mf;
   VecSet<double> g64;            // level-0 grid vectors (full grid)
   VecSet<float> g32;
   VecSet<__nv_bfloat16> g16;

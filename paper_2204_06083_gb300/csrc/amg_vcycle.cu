@@ -201,6 +201,47 @@ __global__ void k_prolong0(int64_t n, const int32_t* __restrict__ rp, const int3
   }
 }
 
+// matrix-free level-0 transfers ----------------------------------------------
+// t_j = e[agg(j)] sc[agg(j)] (the tentative prolongation at CP node j)
+template <class V, class SC>
+__device__ __forceinline__ typename AccOf<V>::type t_at(const int32_t* __restrict__ agg_node, const SC* __restrict__ sc,
+                                                       const V* __restrict__ e, int32_t j) {
+  using A = typename AccOf<V>::type;
+  const int32_t c = __ldg(agg_node + j);
+  return cvt<A>(e[c]) * (A)__ldg(sc + c);
+}
+
+// x_i += t_i - omega D_ii^-1 (A t)_i at the CPs (P = (I - omega D^-1 A) P_hat)
+template <int DIM, class V, class SC>
+__global__ void __launch_bounds__(TILE_NODES) k_prolong_mf(TileView tv, const uint8_t* __restrict__ code,
+                                                           const typename DiagOf<V>::type* __restrict__ diag,
+                                                           GOp<typename AccOf<V>::type> o,
+                                                           typename AccOf<V>::type omega,
+                                                           const int32_t* __restrict__ agg_node,
+                                                           const SC* __restrict__ sc, const V* __restrict__ e,
+                                                           V* __restrict__ x) {
+  using A = typename AccOf<V>::type;
+  const int32_t st[3] = {1, tv.sy, tv.sz};
+  EB_PAIR_LOOP(DIM, tv, node) {
+    uint32_t c0, c1;
+    ld_codes(code, node, c0, c1);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t c = h ? c1 : c0;
+      const int32_t i = node + h;
+      if (!(c & CODE_CP)) continue;
+      const A ti = t_at(agg_node, sc, e, i);
+      A sum = 0;
+#pragma unroll
+      for (int sdir = 0; sdir < 2 * DIM; ++sdir)
+        if (!(c & (1u << sdir))) sum += t_at(agg_node, sc, e, i + ((sdir & 1) ? st[sdir >> 1] : -st[sdir >> 1]));
+      const A D = (c & 0x3F) ? (A)__ldg(diag + i) : (A)(2 * DIM);
+      const A at = (o.sigma + D * o.inv_h2) * ti - o.inv_h2 * sum;
+      x[i] = cvt<V>(cvt<A>(x[i]) + ti - omega * inv_diag_t<A>(c, diag, i, o) * at);
+    }
+  }
+}
+
 // compact levels -----------------------------------------------------------
 template <class V>
 __global__ void k_c_cheb_first(int64_t n, const V* dinv, const V* b, V* x, V* d, typename AccOf<V>::type theta) {
@@ -457,9 +498,18 @@ static void vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s) {
   VecSet<V>& cv = LV::vec(C);
   const CsrV<V> R0 = LV::R(L0), P0 = LV::P(L0);
   const int gR = group_width(L0.R.nnz, L0.R.n, S.csr_epl), gP = group_width(L0.P.nnz, L0.P.n, S.csr_epl);
+  const MatrixFreeP& M = H.mf;
+  using SC = typename std::conditional<std::is_same<V, double>::value, double, float>::type;
+  const SC* sc = nullptr;
+  if (M.on) sc = reinterpret_cast<const SC*>(std::is_same<V, double>::value ? (const void*)M.sc64 : (const void*)M.sc32);
+  // restriction through the explicit R (its per-member stencil gathers made a
+  // matrix-free restriction slower); prolongation matrix free
   EB_GROUP_LAUNCH(gR, k_restrict0, V, C.A.n, s, C.A.n, R0.rp, L0.R0node, R0.v, g.r, cv.b);
   vcycle_compact<V>(S, 1, s);
-  EB_GROUP_LAUNCH(gP, k_prolong0, V, P0.n, s, P0.n, P0.rp, P0.ci, P0.v, eb.cp_node, cv.x, x);
+  if (M.on)
+    k_prolong_mf<DIM, V, SC><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, (A)M.omega, M.agg_node, sc, cv.x, x);
+  else
+    EB_GROUP_LAUNCH(gP, k_prolong0, V, P0.n, s, P0.n, P0.rp, P0.ci, P0.v, eb.cp_node, cv.x, x);
   for (int k = 0; k < cc.deg; ++k) {
     S.prof_mark(s, true);
     if (k == cc.deg - 1)

@@ -177,6 +177,7 @@ int amg_setup(const eb_handle* eb, double shift, const amg_opts* opts, amg_handl
   }
   Solver& S = a->s;
   S.eb = const_cast<EBHandle*>(&eb->h);
+  S.home = stream;
   S.shift = shift;
   amg_opts o{25, 1024, 0.02, 2, EB_F64};
   if (opts) o = *opts;
@@ -208,7 +209,7 @@ void amg_destroy(amg_handle* amg) {
   amg_free(amg->s);
   amg->s.free_work();
   amg->s.prof_release();
-  cudaStreamSynchronize(amg->s.eb->home);
+  cudaStreamSynchronize(amg->s.home);
   delete amg;
 }
 

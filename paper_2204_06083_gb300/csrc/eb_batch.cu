@@ -502,7 +502,7 @@ __global__ void k_b_finalize(const double* part, const int32_t* geo_tile0, int o
       break;
     case FIN_RZ0:
     case FIN_RZ0F:
-      S.rz = v;
+      S.rz[0] = v;
       if (!isfinite(v)) {
         S.flags |= PCG_FLAG_NONFINITE;
         S.done = 1;
@@ -515,7 +515,7 @@ __global__ void k_b_finalize(const double* part, const int32_t* geo_tile0, int o
         S.done = 1;
         S.alpha = 0.0;
       } else {
-        S.alpha = S.rz / v;
+        S.alpha = S.rz[0] / v;
       }
       break;
     case FIN_RR:
@@ -535,8 +535,8 @@ __global__ void k_b_finalize(const double* part, const int32_t* geo_tile0, int o
         S.done = 1;
         break;
       }
-      S.beta = (op == FIN_BETAF ? v - w : v) / S.rz;
-      S.rz = v;
+      S.beta = (op == FIN_BETAF ? v - w : v) / S.rz[0];
+      S.rz[0] = v;
       break;
   }
 }
@@ -866,6 +866,7 @@ int batch_heat_setup(batch_handle* b, const double* dt, double theta, const amg_
     B.S = new Solver();
     Solver& S = *B.S;
     S.eb = &B.view;
+    S.home = stream;
     S.shift = 0.0;  // per-tile shifts of the view take over
     S.opts = o;
     S.alloc_work(stream);

@@ -3,10 +3,11 @@
 //
 // Vectors live in the full-grid layout and are touched on the active tiles
 // only.  Every reduction is two-pass and deterministic: each CTA of a fixed
-// grid reduces its nodes in a fixed order to one partial, and a single CTA
-// combines the partials in a fixed tree and advances the scalar recurrences
-// (alpha, beta, ...) in device memory.  No scalar crosses to the host except
-// the convergence flag, read every check_every iterations.
+// grid reduces its nodes in a fixed order to one partial; the partials are
+// combined in a fixed order by the kernel that needs the result -- every CTA
+// of the update kernels (x, r with alpha; p with beta) reduces them itself and
+// CTA 0 records the scalars -- or by one CTA (r'r and the convergence test).
+// No scalar crosses to the host except at the end of the loop.
 #include "eb_solver.cuh"
 #include "stencil.cuh"
 
@@ -87,16 +88,41 @@ __global__ void __launch_bounds__(TILE_NODES) k_apply_dot(TileView tv, const uin
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
-// x += alpha p; r -= alpha q; partial r.r
+// sum of n partials (stride apart) in a fixed order, the same in every CTA
+__device__ __forceinline__ double sum_parts(const double* part, int n, int stride, double* sm) {
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a += part[stride * i];
+  return block_sum(a, sm);  // thread 0 holds the result
+}
+
+// alpha = rz / p'q from the partials of k_apply_dot (every CTA; CTA 0 records
+// pq, alpha and a breakdown); x += alpha p; r -= alpha q; partial r.r
 template <int DIM>
-__global__ void __launch_bounds__(TILE_NODES) k_update_xr(TileView tv, const PcgScalars* sc, double* x, double* r,
-                                                          const double* p, const double* q, double* part) {
+__global__ void __launch_bounds__(TILE_NODES) k_update_xr(TileView tv, PcgScalars* sc, double* x, double* r,
+                                                          const double* p, const double* q, const double* pq_part,
+                                                          int nblk, double* part) {
   __shared__ double sm[32];
+  __shared__ double s_alpha;
   if (sc->done) {
     if (threadIdx.x == 0) part[blockIdx.x] = 0.0;
     return;
   }
-  const double alpha = sc->alpha;
+  const double pq = sum_parts(pq_part, nblk, 1, sm);
+  if (threadIdx.x == 0) {
+    const bool ok = pq > 0.0;  // false for NaN too
+    const double alpha = ok ? sc->rz[sc->iters & 1] / pq : 0.0;
+    s_alpha = alpha;
+    if (blockIdx.x == 0) {
+      sc->pq = pq;
+      sc->alpha = alpha;
+      if (!ok) {
+        sc->flags |= isfinite(pq) ? PCG_FLAG_BREAKDOWN : PCG_FLAG_NONFINITE;
+        sc->done = 1;
+      }
+    }
+  }
+  __syncthreads();
+  const double alpha = s_alpha;
   double s = 0.0;
   EB_PAIR_LOOP(DIM, tv, node) {
     const Two<double> rv = ld2d(r + node), qv = LdRO::ld2(q + node), pv = LdRO::ld2(p + node), xv = ld2d(x + node);
@@ -160,12 +186,38 @@ __global__ void __launch_bounds__(TILE_NODES) k_dot2(TileView tv, const double* 
 }
 
 // p = z + beta p   (p = z on the first iteration of a cycle); zold = z when
-// zold is given (flexible CG)
+// zold is given (flexible CG).  Otherwise beta comes from the partials of the
+// preconditioner's dot kernel (pairs (r.z, r.zold) when flexible): beta =
+// r.z / rz (Fletcher-Reeves) or (r.z - r.zold) / rz (Polak-Ribiere), computed
+// by every CTA; CTA 0 records beta, the next rz (the other slot) and a breakdown.
 template <int DIM>
-__global__ void __launch_bounds__(TILE_NODES) k_xpby(TileView tv, const PcgScalars* sc, const double* z, double* p,
-                                                     double* zold, int first) {
+__global__ void __launch_bounds__(TILE_NODES) k_xpby(TileView tv, PcgScalars* sc, const double* z, double* p,
+                                                     double* zold, int first, const double* rz_part, int nblk) {
+  __shared__ double sm[32];
+  __shared__ double s_beta;
   if (sc->done) return;
-  const double beta = first ? 0.0 : sc->beta;
+  if (!first) {
+    const int stride = zold ? 2 : 1;
+    const double v = sum_parts(rz_part, nblk, stride, sm);
+    __syncthreads();
+    const double t = zold ? sum_parts(rz_part + 1, nblk, 2, sm) : 0.0;
+    if (threadIdx.x == 0) {
+      const int k = sc->iters & 1;
+      const bool ok = v > 0.0;
+      const double beta = ok ? (v - t) / sc->rz[k] : 0.0;
+      s_beta = beta;
+      if (blockIdx.x == 0) {
+        sc->beta = beta;
+        sc->rz[k ^ 1] = v;
+        if (!ok) {
+          sc->flags |= isfinite(v) ? PCG_FLAG_BREAKDOWN : PCG_FLAG_NONFINITE;
+          sc->done = 1;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const double beta = first ? 0.0 : s_beta;
   EB_PAIR_LOOP(DIM, tv, node) {
     const Two<double> zv = LdRO::ld2(z + node);
     if (first) {
@@ -248,29 +300,8 @@ __global__ void k_finalize(const double* part, int nblk, int op, PcgScalars* sc)
       break;
     case FIN_RZ0:
     case FIN_RZ0F:
-      sc->rz = v;
+      sc->rz[sc->iters & 1] = v;
       if (!isfinite(v)) sc->flags |= PCG_FLAG_NONFINITE;
-      break;
-    case FIN_BETAF:  // flexible (Polak-Ribiere): beta = r'(z - zold) / rz_old
-      if (sc->done) break;
-      if (!(v > 0.0)) {
-        sc->flags |= isfinite(v) ? PCG_FLAG_BREAKDOWN : PCG_FLAG_NONFINITE;
-        sc->done = 1;
-        break;
-      }
-      sc->beta = (v - sm[1][0]) / sc->rz;
-      sc->rz = v;
-      break;
-    case FIN_ALPHA:
-      if (sc->done) break;
-      sc->pq = v;
-      if (!(v > 0.0)) {
-        sc->flags |= isfinite(v) ? PCG_FLAG_BREAKDOWN : PCG_FLAG_NONFINITE;
-        sc->done = 1;
-        sc->alpha = 0.0;
-      } else {
-        sc->alpha = sc->rz / v;
-      }
       break;
     case FIN_RR:
       if (sc->done) break;
@@ -283,22 +314,26 @@ __global__ void k_finalize(const double* part, int nblk, int op, PcgScalars* sc)
         sc->done = 1;
       }
       break;
-    case FIN_BETA:
-      if (sc->done) break;
-      if (!(v > 0.0)) {
-        sc->flags |= isfinite(v) ? PCG_FLAG_BREAKDOWN : PCG_FLAG_NONFINITE;
-        sc->done = 1;
-        break;
-      }
-      sc->beta = v / sc->rz;
-      sc->rz = v;
-      break;
   }
 }
 
-// condition of the device-side iteration loop: continue while not converged
-// (or broken down) and below the iteration limit
-__global__ void k_loop_cond(cudaGraphConditionalHandle h, const PcgScalars* sc) {
+// end of a device-side loop iteration: r'r from the partials of k_update_xr
+// (FIN_RR of k_finalize), then the loop condition: continue while not
+// converged (or broken down) and below the iteration limit
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, const double* part, int nblk, PcgScalars* sc) {
+  __shared__ double sm[32];
+  const double v = sum_parts(part, nblk, 1, sm);
+  if (threadIdx.x != 0) return;
+  if (!sc->done) {
+    sc->rr = v;
+    sc->iters += 1;
+    if (!isfinite(v)) {
+      sc->flags |= PCG_FLAG_NONFINITE;
+      sc->done = 1;
+    } else if (v <= sc->tol2 * sc->bb) {
+      sc->done = 1;
+    }
+  }
   cudaGraphSetConditional(h, (!sc->done && sc->iters < sc->maxit) ? 1u : 0u);
 }
 
@@ -330,13 +365,13 @@ void Solver::alloc_work(cudaStream_t s) {
   tmp = dalloc<double>(nn, s);
   if (opts.vcycle_prec != EB_F64) zold = dalloc<double>(nn, s);
   nblk = (int)std::min<int64_t>(std::max<int64_t>(eb->num_tiles, 1), (int64_t)num_sms() * 4);
-  part = dalloc<double>(2 * (int64_t)nblk, s);
+  part = dalloc<double>(6 * (int64_t)nblk, s);  // three regions of 2 nblk: p'q / r'r / r'z partials
   sc = dalloc<PcgScalars>(1, s);
   EB_CUDA(cudaMallocHost((void**)&sc_host, sizeof(PcgScalars)));
 }
 
 void Solver::free_work() {
-  cudaStream_t s = eb->home;
+  cudaStream_t s = home;
   graph_release();
   loop_release();
   if (cap_stream) cudaStreamDestroy(cap_stream);
@@ -346,9 +381,9 @@ void Solver::free_work() {
   sc_host = nullptr;
 }
 
-void Solver::finalize(int op, cudaStream_t s) {
+void Solver::finalize(int op, const double* src, cudaStream_t s) {
   ++nlaunch;
-  k_finalize<<<1, 1024, 0, s>>>(part, nblk, op, sc);
+  k_finalize<<<1, 1024, 0, s>>>(src, nblk, op, sc);
 }
 
 void Solver::precondition(int kind, const double* rin, double* zout, cudaStream_t s) {
@@ -357,18 +392,18 @@ void Solver::precondition(int kind, const double* rin, double* zout, cudaStream_
   if (kind == EB_PC_AMG_NN) {
     amg_vcycle_grid(*this, rin, zout, s);
     nn_stage_apply(nn, *eb, shift, nn_mode, rin, zout, nlaunch, this, s);
-    EB_DIM_LAUNCH(dim, k_dot2, nblk, tv, rin, zout, zold, part);
+    EB_DIM_LAUNCH(dim, k_dot2, nblk, tv, rin, zout, zold, part_rz());
   } else if (kind == EB_PC_AMG && H) {
     amg_vcycle_grid(*this, rin, zout, s);
     if (flexible())
-      EB_DIM_LAUNCH(dim, k_dot2, nblk, tv, rin, zout, zold, part);
+      EB_DIM_LAUNCH(dim, k_dot2, nblk, tv, rin, zout, zold, part_rz());
     else
-      EB_DIM_LAUNCH(dim, k_dot, nblk, tv, rin, zout, part);
+      EB_DIM_LAUNCH(dim, k_dot, nblk, tv, rin, zout, part_rz());
   } else if (kind == EB_PC_NONE) {
     EB_DIM_LAUNCH(dim, k_copy_tiles, nblk, tv, rin, zout);
-    EB_DIM_LAUNCH(dim, k_dot, nblk, tv, rin, zout, part);
+    EB_DIM_LAUNCH(dim, k_dot, nblk, tv, rin, zout, part_rz());
   } else {
-    EB_DIM_LAUNCH(dim, k_jacobi_dot, nblk, tv, eb->code, eb->diag, op_params(*this), rin, zout, part);
+    EB_DIM_LAUNCH(dim, k_jacobi_dot, nblk, tv, eb->code, eb->diag, op_params(*this), rin, zout, part_rz());
   }
 }
 
@@ -402,8 +437,8 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
     EB_CUDA(cudaMemcpyAsync(sc, &init, sizeof(init), cudaMemcpyHostToDevice, s));
     // x is masked to the CPs (its non-CP entries are ignored on input)
     EB_DIM_LAUNCH(dim, k_mask_copy, nblk, tv, eb->code, x, x);
-    EB_DIM_LAUNCH(dim, k_resid, nblk, tv, eb->code, eb->diag, op, b, x, r, part);
-    finalize(FIN_INIT, s);
+    EB_DIM_LAUNCH(dim, k_resid, nblk, tv, eb->code, eb->diag, op, b, x, r, part_pq());
+    finalize(FIN_INIT, part_pq(), s);
     EB_CUDA(cudaMemcpyAsync(sc_host, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
     EB_CUDA(cudaStreamSynchronize(s));
     if (sc_host->flags & PCG_FLAG_NONFINITE) {
@@ -424,8 +459,8 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
     if (total_iters >= maxit) break;
     precondition(kind, r, z, s);
     const bool flex = flex_for(kind);
-    finalize(flex ? FIN_RZ0F : FIN_RZ0, s);
-    EB_DIM_LAUNCH(dim, k_xpby, nblk, tv, sc, z, p, flex ? zold : nullptr, 1);
+    finalize(flex ? FIN_RZ0F : FIN_RZ0, part_rz(), s);
+    EB_DIM_LAUNCH(dim, k_xpby, nblk, tv, sc, z, p, flex ? zold : nullptr, 1, part_rz(), nblk);
     int it = 0;
     bool stop = false;
     if (o.use_graph == 1 && !prof_on) {  // the whole loop on the device
@@ -462,8 +497,8 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
     flags |= sc_host->flags;
     if (flags & (PCG_FLAG_NONFINITE | PCG_FLAG_BREAKDOWN)) break;
     // true residual at exit
-    EB_DIM_LAUNCH(dim, k_resid, nblk, tv, eb->code, eb->diag, op, b, x, r, part);
-    finalize(FIN_INIT, s);
+    EB_DIM_LAUNCH(dim, k_resid, nblk, tv, eb->code, eb->diag, op, b, x, r, part_pq());
+    finalize(FIN_INIT, part_pq(), s);
     EB_CUDA(cudaMemcpyAsync(sc_host, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
     EB_CUDA(cudaStreamSynchronize(s));
     rel = sc_host->bb > 0 ? std::sqrt(sc_host->rr / sc_host->bb) : 0.0;
@@ -511,19 +546,19 @@ int Solver::heat(double dt, double theta, const double* b1, const double* b0, do
 }
 
 // One PCG iteration (device-side scalars; no host synchronisation).
-void Solver::iteration(int kind, const double* b, double* x, cudaStream_t s) {
+void Solver::iteration(int kind, const double* b, double* x, cudaStream_t s, bool loop_end) {
   (void)b;
   const int dim = eb->g.dim;
   const TileView tv = eb->tv();
   const OpParams op = op_params(*this);
-  EB_DIM_LAUNCH(dim, k_apply_dot, nblk, tv, eb->code, eb->diag, op, p, q, part);
-  finalize(FIN_ALPHA, s);
-  EB_DIM_LAUNCH(dim, k_update_xr, nblk, tv, sc, x, r, p, q, part);
-  finalize(FIN_RR, s);
+  EB_DIM_LAUNCH(dim, k_apply_dot, nblk, tv, eb->code, eb->diag, op, p, q, part_pq());
+  EB_DIM_LAUNCH(dim, k_update_xr, nblk, tv, sc, x, r, p, q, part_pq(), nblk, part_rr());
   precondition(kind, r, z, s);
   const bool flex = flex_for(kind);
-  finalize(flex ? FIN_BETAF : FIN_BETA, s);
-  EB_DIM_LAUNCH(dim, k_xpby, nblk, tv, sc, z, p, flex ? zold : nullptr, 0);
+  EB_DIM_LAUNCH(dim, k_xpby, nblk, tv, sc, z, p, flex ? zold : nullptr, 0, part_rz(), nblk);
+  // r'r and the convergence test end the iteration (the device-side loop's
+  // condition kernel does it itself)
+  if (!loop_end) finalize(FIN_RR, part_rr(), s);
 }
 
 // Captures `iters` iterations into a CUDA graph (once per argument set).  The
@@ -620,8 +655,8 @@ void Solver::loop_prepare(int kind, const double* b, double* x, cudaStream_t s) 
   if (!cap_stream) EB_CUDA(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
   const int64_t n0 = nlaunch;
   lexec = build_while_graph(cap_stream, [&](cudaStream_t cs, cudaGraphConditionalHandle h) {
-    iteration(kind, b, x, cs);
-    k_loop_cond<<<1, 1, 0, cs>>>(h, sc);
+    iteration(kind, b, x, cs, true);
+    k_loop_cond<<<1, 256, 0, cs>>>(h, part_rr(), nblk, sc);
     ++nlaunch;
   });
   l_launches = nlaunch - n0;

@@ -8,14 +8,19 @@
 
 namespace ebk {
 
-// FIN_RZ0F / FIN_BETAF: flexible CG, partials are pairs (r.z, r.z_previous)
+// FIN_RZ0F / FIN_BETAF: flexible CG, partials are pairs (r.z, r.z_previous).
+// The single-grid PCG combines FIN_ALPHA and FIN_BETA inside its update
+// kernels; the batch finalizes every op in its per-geometry kernel.
 enum { FIN_INIT = 0, FIN_RZ0 = 1, FIN_ALPHA = 2, FIN_RR = 3, FIN_BETA = 4, FIN_RZ0F = 5, FIN_BETAF = 6 };
 enum { PCG_FLAG_NONFINITE = 1, PCG_FLAG_BREAKDOWN = 2 };
 // what pcg_opts.profile times: the level-0 smoother launches or the learned stage's 32 -> 32 convolutions
 enum { PROF_SMOOTHER = 1, PROF_CONV = 2 };
 
+// rz[iters & 1] holds r'z of the current iteration; the kernel that computes
+// the next one writes the other slot, so that no CTA reads a value another CTA
+// of the same kernel is rewriting (the batch keeps using rz[0])
 struct PcgScalars {
-  double bb, rr, rz, pq, alpha, beta, tol2;
+  double bb, rr, rz[2], pq, alpha, beta, tol2;
   int iters, flags, done;
   int maxit;  // iteration limit of the device-side loop (counted like iters)
 };
@@ -24,6 +29,9 @@ struct Hierarchy;  // AMG levels (amg.cu)
 
 struct Solver {
   EBHandle* eb = nullptr;
+  // stream the solver's memory belongs to (set at setup); destroying a solver
+  // never reads *eb, which may already be gone
+  cudaStream_t home = 0;
   double shift = 0.0;
   amg_opts opts{};
   Hierarchy* H = nullptr;
@@ -37,7 +45,10 @@ struct Solver {
   bool flex_for(int kind) const { return kind == EB_PC_AMG_NN || (kind == EB_PC_AMG && flexible()); }
   nn_handle* nn = nullptr;  // learned stage of EB_PC_AMG_NN (set for one solve)
   int nn_mode = 0;          // eb_nn_mode of that stage
-  double* part = nullptr;
+  double* part = nullptr;  // reduction partials: [p'q | r'r | r'z] regions of 2 nblk each
+  double* part_pq() const { return part; }
+  double* part_rr() const { return part + 2 * (int64_t)nblk; }
+  double* part_rz() const { return part + 4 * (int64_t)nblk; }
   int nblk = 1;
   PcgScalars* sc = nullptr;
   PcgScalars* sc_host = nullptr;
@@ -70,7 +81,7 @@ struct Solver {
 
   void alloc_work(cudaStream_t s);
   void free_work();
-  void finalize(int op, cudaStream_t s);
+  void finalize(int op, const double* src, cudaStream_t s);
   void precondition(int kind, const double* r, double* z, cudaStream_t s);
   int pcg(const double* b, double* x, double rtol, int maxit, const pcg_opts& o, pcg_stats* stats, cudaStream_t s);
   int heat(double dt, double theta, const double* b1, const double* b0, double* u, double rtol, int maxit,
@@ -80,7 +91,7 @@ struct Solver {
   void prof_collect(int first, int count);
   void prof_end(pcg_stats* st, cudaStream_t s);
   void prof_release();
-  void iteration(int kind, const double* b, double* x, cudaStream_t s);
+  void iteration(int kind, const double* b, double* x, cudaStream_t s, bool loop_end = false);
   void graph_prepare(int kind, const double* b, double* x, int iters, int profile, cudaStream_t s);
   void graph_release();
   void loop_prepare(int kind, const double* b, double* x, cudaStream_t s);

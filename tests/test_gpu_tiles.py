@@ -176,3 +176,14 @@ def test_csr_group_tuning_keeps_results():
     x1, st1 = amg.solve(b, rtol=1e-11)
     assert abs(st1.iterations - st0.iterations) <= 1
     assert torch.linalg.norm(x1 - x0) <= 1e-9 * torch.linalg.norm(x0)
+
+
+def test_handles_destroyed_in_any_order():
+    """Cycle collection finalizes objects in any order: a hierarchy destroyed
+    after its grid must not touch the grid."""
+    eb = _pkg()
+    h = eb.EB(ei.box_grid(2, 96), ei.random_star(7))
+    amg = eb.AMG(h)
+    eb.load().eb_destroy(h.handle)   # the grid first ...
+    h._h = type(h._h)()
+    amg.close()                      # ... then the hierarchy
