@@ -18,6 +18,8 @@ batched    64 seeded stars on grids from 128^2 to 1024^2, backward-Euler heat
            batch_heat_step per time step, forcing and boundary data frozen at
            t = 0); the same time step solved geometry by geometry with the
            plain FP64 AMG-PCG is timed beside it.
+conv       The learned stage's network alone: one forward pass (6 layers, the four
+           32 -> 32 layers on tcgen05) over a 2048^2 image of seeded inputs.
 learned    The learned preconditioner stage: trained (outside the timed
            region) on 20,000 solver-generated pairs at 512^2 on random stars,
            then one step = one flexible PCG solve with V-cycle + stage to
@@ -62,7 +64,7 @@ CPU_SAMPLE_N = 112
 PROF_NOTE = ("CUDA events around every launch of the kernel in as many solves (batched: one bench step) run right "
              "after the timed ones on the same input; those use the captured iteration with a host check, since "
              "the timed device-side loop cannot bracket single launches")
-WORKLOADS = ("poisson3d", "poisson2d", "wave", "batched", "learned")
+WORKLOADS = ("poisson3d", "poisson2d", "wave", "batched", "learned", "conv")
 
 
 def peaks():
@@ -167,6 +169,11 @@ def config_of(w, small=None):
                 "geometries": 64, "time_steps": 50, "rtol": RTOL,
                 "vcycle": "FP32 V-cycle on the block-diagonal hierarchy, per-geometry flexible FP64 PCG",
                 "l2": "batch vectors exceed L2 (26M nodes x 8 B)"}
+    if w == "conv":
+        return {"workload": "learned-stage network forward, one 2048^2 image, He-initialised weights (seed 8), "
+                            "seeded normal residual channel, mask of the random star (seed 999)",
+                "n": 2048, "network": "6 x conv3x3, 32 channels, BF16 activations, FP32 accumulation",
+                "l2": "activations 268 MB per layer exceed L2; 512 MB flush between steps"}
     if w == "learned":
         return {"workload": "flexible PCG with V-cycle + learned CNN stage, random star at 2048^2, "
                             f"u=sin(2x)cos(3y), rtol {RTOL:g}; network trained on 20000 solver pairs at 512^2 "
@@ -177,7 +184,7 @@ def config_of(w, small=None):
 
 
 UNITS = {"poisson3d": "DOF/s", "poisson2d": "DOF/s", "wave": "DOF-steps/s", "batched": "DOF/s",
-         "learned": "DOF/s"}
+         "learned": "DOF/s", "conv": "pixels/s"}
 
 
 # ------------------------------------------------------------------ oracle
@@ -301,6 +308,22 @@ print(json.dumps(dict(dof=s.num_cp, sec=t1 - t0, iterations=it)))
         return rec["dof"] / rec["sec"], (
             f"oracle flexible PCG with V-cycle + FP64 CNN stage (untrained weights) on a random star at 128^2 "
             f"(N_C={rec['dof']}, {rec['iterations']} its, {rec['sec']:.1f} s)"), rec
+    if w == "conv":
+        rec = _oracle_run("""
+import json, time
+import numpy as np
+from oracle import cnn
+theta = cnn.init_params(8)
+rng = np.random.default_rng(0)
+s_hat = rng.standard_normal((256, 256))
+m = np.ones((256, 256))
+t0 = time.perf_counter()
+cnn.forward(theta, s_hat, m)
+t1 = time.perf_counter()
+print(json.dumps(dict(px=256 * 256, sec=t1 - t0)))
+""")
+        return rec["px"] / rec["sec"], (f"oracle FP64 network forward (numpy einsum) on a 256^2 image "
+                                        f"({rec['sec']:.1f} s)"), rec
     raise ValueError(w)
 
 
@@ -479,7 +502,9 @@ def gpu_poisson(ctx, args, dim):
 
     sts, ms_per_step, clocks = loop(ctx, args, step, torch.cuda.current_device())
     launches = sum(s.launches for s in sts) // len(sts)
-    prof_ms, prof_n = profiled(ctx, args, lambda: solver.solve(b, x=x.zero_(), rtol=RTOL, maxit=500, profile=True)[1])
+    prof_ms, prof_n = profiled(ctx, args, lambda: solver.solve(b, x=x.zero_(), rtol=RTOL, maxit=500, profile=1)[1])
+    l1_ms, l1_n = (profiled(ctx, args, lambda: solver.solve(b, x=x.zero_(), rtol=RTOL, maxit=500, profile=3)[1])
+                   if solver.num_levels > 2 else (0.0, 0))
     value = ctx.world * nc / (ms_per_step / 1000.0)
     extra = {}
     if dim == 3:
@@ -530,19 +555,38 @@ def gpu_poisson(ctx, args, dim):
     avg_s = (prof_ms / prof_n) / 1000.0 if prof_n else float("nan")
     vb = CHEB_BYTES_PER_DOF["f32" if dim == 3 else "f64"]
     achieved = vb * nc / avg_s / 1e9 if prof_n else None
+    stencil = {"bound": "hbm",
+               "kernel": f"k_g_cheb_step<{dim}, {'float, float' if dim == 3 else 'double, double'}>",
+               "achieved": achieved, "peak": pk["hbm_gbs"], "peak_kind": kind, "unit": "GB/s",
+               "frac": (achieved / pk["hbm_gbs"]) if achieved else None,
+               "traffic": recorded_traffic() if dim == 3 else None,
+               "algorithmic_bytes_per_launch": vb * nc, "avg_launch_us": avg_s * 1e6,
+               "launches_timed": prof_n, "timing": PROF_NOTE}
+    roof = stencil
+    if l1_n:
+        # level-1 Chebyshev step: values + column indices per nonzero, and per row the row
+        # pointer, x gathered once, b, D^-1, d read and written, x written (word size 4 or 8)
+        w = 4 if dim == 3 else 8
+        n1, nnz1 = solver.rows[1], solver.nnz[1]
+        l1_bytes = nnz1 * (w + 4) + n1 * (4 + 6 * w)
+        l1_s = (l1_ms / l1_n) / 1000.0
+        l1_ach = l1_bytes / l1_s / 1e9
+        level1 = {"bound": "hbm", "kernel": f"k_c_cheb_step<G, {'float' if dim == 3 else 'double'}> (level 1, CSR)",
+                  "achieved": l1_ach, "peak": pk["hbm_gbs"], "peak_kind": kind, "unit": "GB/s",
+                  "frac": l1_ach / pk["hbm_gbs"], "traffic": None,
+                  "algorithmic_bytes_per_launch": l1_bytes, "avg_launch_us": l1_s * 1e6, "launches_timed": l1_n,
+                  "rows": n1, "nnz": nnz1, "timing": PROF_NOTE}
+        if l1_ms > prof_ms:  # the line's roofline is the kernel with the larger share of the solve
+            roof = level1
     line = {"value": value, "ms_per_step": ms_per_step,
             "dtype": "f64 outer, f32 V-cycle" if dim == 3 else "f64",
             "num_cp": nc, "iterations": sts[-1].iterations, "time_to_tol_ms": ms_per_step,
             "build_ms": build_ms, "setup_ms": setup_ms, "amg_levels": solver.rows, "max_err_vs_exact": err,
             "tile": tile, "autotune_us_per_vcycle": tune,
             "csr_entries_per_lane": epl, "csr_tune_us_per_vcycle": {str(k): round(v, 2) for k, v in epl_us.items()},
-            "roofline": {"bound": "hbm",
-                         "kernel": f"k_g_cheb_step<{dim}, {'float, float' if dim == 3 else 'double, double'}>",
-                         "achieved": achieved, "peak": pk["hbm_gbs"], "peak_kind": kind, "unit": "GB/s",
-                         "frac": (achieved / pk["hbm_gbs"]) if achieved else None,
-                         "traffic": recorded_traffic() if dim == 3 else None,
-                         "algorithmic_bytes_per_launch": vb * nc, "avg_launch_us": avg_s * 1e6,
-                         "launches_timed": prof_n, "timing": PROF_NOTE},
+            "roofline": roof, "stencil_roofline": stencil,
+            "kernel_time_ms_per_solve": {"level0_smoother": prof_ms / max(args.steps, 1),
+                                         "level1_smoother": l1_ms / max(args.steps, 1)},
             "e2e": {"value": e2e_value, "unit": "DOF/s", "h2d_bytes_per_step": hb.numel() * 8,
                     "d2h_bytes_per_step": hx.numel() * 8},
             "gpu_launches": launches, "clocks": clocks}
@@ -814,6 +858,62 @@ def gpu_learned(ctx, args):
             "gpu_launches": sts[-1].launches, "clocks": clocks}
 
 
+def gpu_conv(ctx, args):
+    import numpy as np
+    import torch
+    import eb_inputs as ei
+    import paper_2204_06083_gb300 as eb
+    from paper_2204_06083_gb300 import learned
+    n = 2048
+    h = eb.EB(ei.box_grid(2, n), ei.random_star(999))
+    cp = ((h.classes() & eb.CODE_CP) != 0).float()
+    rng = np.random.default_rng(0)
+    inp = torch.empty((1, n, n, 2), dtype=torch.float32, device=ctx.dev)
+    inp[0, :, :, 0] = torch.from_numpy(rng.standard_normal((n, n)).astype(np.float32)).cuda() * cp
+    inp[0, :, :, 1] = cp
+    out = torch.empty((1, n, n), dtype=torch.float32, device=ctx.dev)
+    net = eb.Net(learned.init_params(8))
+
+    def step():
+        net.forward(inp, out)
+
+    _, ms_per_step, clocks = loop(ctx, args, step, torch.cuda.current_device())
+    px = n * n
+    value = ctx.world * px / (ms_per_step / 1000.0)
+    net.set_profile(True)  # the convolution launches, in as many forwards right after the timed ones
+    for _ in range(args.steps):
+        ctx.flush()
+        net.forward(inp, out)
+    conv_ms, conv_n = net.profile()
+    net.set_profile(False)
+    net.status()
+    hin = inp.cpu().pin_memory()
+    hout = torch.empty_like(out, device="cpu").pin_memory()
+    din = torch.empty_like(inp)
+    e2e = []
+    for i in range(1 + args.steps):
+        ctx.flush()
+        t, _ = timed(lambda: (din.copy_(hin, non_blocking=True), net.forward(din, out),
+                              hout.copy_(out, non_blocking=True)))
+        if i >= 1:
+            e2e.append(t)
+    e2e_value = ctx.world * px / (ctx.max_over_ranks(statistics.mean(e2e)) / 1000.0)
+    pk, kind = peaks()
+    avg_s = (conv_ms / conv_n) / 1000.0 if conv_n else float("nan")
+    achieved = CONV_FLOP_PER_PX * px / avg_s / 1e12 if conv_n else None
+    peak = pk.get("bf16_tflops", pk.get("bf16_tflops_sustained"))
+    return {"value": value, "ms_per_step": ms_per_step, "dtype": "bf16 (f32 accumulate)",
+            "roofline": {"bound": "tensor", "kernel": "k_conv32 (32->32 implicit-GEMM conv, tcgen05.mma, TMEM)",
+                         "achieved": achieved, "peak": peak, "peak_kind": kind + " bf16 burst", "unit": "TFLOP/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "algorithmic_flops_per_launch": CONV_FLOP_PER_PX * px, "avg_launch_us": avg_s * 1e6,
+                         "launches_timed": conv_n,
+                         "hbm_gbs_equivalent": 128 * px / avg_s / 1e9 if conv_n else None},
+            "e2e": {"value": e2e_value, "unit": "pixels/s", "h2d_bytes_per_step": hin.numel() * 4,
+                    "d2h_bytes_per_step": hout.numel() * 4},
+            "gpu_launches": 6, "clocks": clocks}
+
+
 def run_gpu(args):
     ctx = Ctx()
     w = args.workload
@@ -825,6 +925,8 @@ def run_gpu(args):
         body = gpu_wave(ctx, args)
     elif w == "batched":
         body = gpu_batched(ctx, args)
+    elif w == "conv":
+        body = gpu_conv(ctx, args)
     else:
         body = gpu_learned(ctx, args)
     if ctx.rank != 0:

@@ -230,7 +230,8 @@ typedef struct {
                             iteration); with profile set, or 2: captured chunks of check_every iterations
                             with a host convergence check between them; 0: direct launches */
   int profile;           /* 1: time every level-0 smoother launch with CUDA events; 2 (pcg_solve_nn):
-                            time the learned stage's 32 -> 32 convolution launches instead */
+                            time the learned stage's 32 -> 32 convolution launches instead; 3: time the
+                            level-1 (first coarse level, CSR) Chebyshev-step launches */
 } pcg_opts;
 
 typedef struct {
@@ -363,6 +364,12 @@ int nn_num_params(void);
  * results are invalid), else EB_OK.  nn_get_params and pcg_solve_nn check it
  * themselves.  Synchronous. */
 int nn_status(nn_handle* nn, cudaStream_t stream);
+/* on != 0: later nn_forward / nn_backward / nn_train_step calls time every
+ * 32 -> 32 convolution launch of their forward passes with CUDA events;
+ * nn_profile returns (synchronously) the summed milliseconds and the number
+ * of timed launches since, and restarts the count. */
+int nn_set_profile(nn_handle* nn, int on);
+int nn_profile(nn_handle* nn, double* ms, int* launches, cudaStream_t stream);
 /* Copies nn_num_params() floats from HOST memory into the network and resets
  * the Adam state (moments and step count).  Synchronous. */
 int nn_set_params(nn_handle* nn, const float* params_host, cudaStream_t stream);

@@ -127,6 +127,8 @@ _SIGS = {
     "nn_destroy": (None, [_P]),
     "nn_num_params": (C.c_int, []),
     "nn_status": (C.c_int, [_P, _P]),
+    "nn_set_profile": (C.c_int, [_P, C.c_int]),
+    "nn_profile": (C.c_int, [_P, _P, _P, _P]),
     "nn_set_params": (C.c_int, [_P, _P, _P]),
     "nn_get_params": (C.c_int, [_P, _P, _P, _P]),
     "nn_forward": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P]),
@@ -584,6 +586,16 @@ class Net:
             out = torch.empty((nimg, h, w), dtype=torch.float32, device="cuda")
         _check(load().nn_forward(self._h, w, h, nimg, _ptr(inp), _ptr(out), _stream(stream)))
         return out
+
+    def set_profile(self, on: bool):
+        _check(load().nn_set_profile(self._h, int(bool(on))))
+
+    def profile(self, stream=None):
+        """(summed ms, launches) of the timed 32 -> 32 convolution launches since the last call."""
+        ms = C.c_double()
+        n = C.c_int()
+        _check(load().nn_profile(self._h, C.byref(ms), C.byref(n), _stream(stream)))
+        return ms.value, n.value
 
     def status(self, stream=None):
         """Raises if a tensor-core wait gave up since the last check."""

@@ -438,8 +438,11 @@ static void vcycle_compact(Solver& S, size_t l, cudaStream_t s) {
   const int gA = group_width(L.A.nnz, L.A.n, e), gP = group_width(L.P.nnz, L.P.n, e),
             gR = group_width(L.R.nnz, L.R.n, e);
   k_c_cheb_first<V><<<nb, 256, 0, s>>>(n, LV::dinv(L), v.b, v.x, v.d, cc.theta);
+  const bool mark = l == 1;  // level-1 smoother launches are timed with PROF_LEVEL1
   for (int k = 1; k < cc.deg; ++k) {
+    if (mark) S.prof_mark(s, true, PROF_LEVEL1);
     EB_GROUP_LAUNCH(gA, k_c_cheb_step, V, n, s, A, LV::dinv(L), v.b, v.x, v.x2, v.d, cc.c1[k], cc.c2[k]);
+    if (mark) S.prof_mark(s, false, PROF_LEVEL1);
     std::swap(v.x, v.x2);
   }
   EB_GROUP_LAUNCH(gA, k_c_resid, V, n, s, A, v.b, v.x, v.r);
@@ -449,7 +452,9 @@ static void vcycle_compact(Solver& S, size_t l, cudaStream_t s) {
   vcycle_compact<V>(S, l + 1, s);
   EB_GROUP_LAUNCH(gP, k_c_prolong_add, V, n, s, LV::P(L), cv.x, v.x);
   for (int k = 0; k < cc.deg; ++k) {
+    if (mark) S.prof_mark(s, true, PROF_LEVEL1);
     EB_GROUP_LAUNCH(gA, k_c_cheb_step, V, n, s, A, LV::dinv(L), v.b, v.x, v.x2, v.d, cc.c1[k], cc.c2[k]);
+    if (mark) S.prof_mark(s, false, PROF_LEVEL1);
     std::swap(v.x, v.x2);
   }
 }

@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cmath>
 #include <utility>
+#include <vector>
 
 namespace ebk {
 
@@ -809,6 +810,10 @@ struct NN {
   float* m = nullptr;  // Adam moments
   float* v = nullptr;
   int* err = nullptr;  // set by a convolution whose tensor-core wait gave up
+  // optional CUDA-event timing of the 32 -> 32 convolution launches of forward()
+  bool prof = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
+  int prof_n = 0;
   bf16* wf = nullptr;  // packed forward weights of the middle layers
   bf16* wb = nullptr;  // packed data-gradient weights
   int64_t steps = 0;
@@ -896,10 +901,21 @@ static void forward(NN& N, const Image& im, const float2* in, float* out, cudaSt
   const int64_t npx = npx_of(im);
   k_l1_fwd<<<blocks_for(npx, 128), 128, 0, s>>>(im, in, N.P, N.act[1]);
   for (int l = 0; l < NMID; ++l) {
+    const bool own = N.prof && !prof;  // events of the handle (not inside a solver's graph)
+    if (own) {
+      if (N.prof_n >= (int)N.prof_ev.size()) {
+        cudaEvent_t a, b;
+        EB_CUDA(cudaEventCreate(&a));
+        EB_CUDA(cudaEventCreate(&b));
+        N.prof_ev.push_back({a, b});
+      }
+      EB_CUDA(cudaEventRecord(N.prof_ev[N.prof_n].first, s));
+    }
     if (prof) prof->prof_mark(s, true, PROF_CONV);
     k_conv32<<<conv_grid(im, 4), 128, conv_smem(), s>>>(im, N.act[l + 1], N.wf + (int64_t)l * WM_N,
                                                          N.P + off_wm(l) + WM_N, N.act[l + 2], 1, nullptr, N.err);
     if (prof) prof->prof_mark(s, false, PROF_CONV);
+    if (own) EB_CUDA(cudaEventRecord(N.prof_ev[N.prof_n++].second, s));
   }
   k_l6_fwd<<<blocks_for(npx, 128), 128, 0, s>>>(im, N.act[5], N.P, in, out);
   nl += 6;
@@ -1062,10 +1078,44 @@ void nn_destroy(nn_handle* h) {
   dfree(N.diag, s); dfree(N.part, s); dfree(N.lpart, s); dfree(N.cimg, s); dfree(N.loss, s);
   dfree(N.s64, s); dfree(N.spart, s); dfree(N.scal, s);
   cudaStreamSynchronize(s);
+  for (auto& e : N.prof_ev) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
   delete h;
 }
 
 int nn_num_params(void) { return NPARAM; }
+
+int nn_set_profile(nn_handle* h, int on) {
+  if (!h) {
+    set_error("nn_set_profile: NULL handle");
+    return EB_ERR_INVALID;
+  }
+  h->n.prof = on != 0;
+  h->n.prof_n = 0;
+  return EB_OK;
+}
+
+int nn_profile(nn_handle* h, double* ms, int* launches, cudaStream_t stream) {
+  if (!h || !ms || !launches) {
+    set_error("nn_profile: NULL argument");
+    return EB_ERR_INVALID;
+  }
+  return guarded([&] {
+    NN& N = h->n;
+    EB_CUDA(cudaStreamSynchronize(stream));
+    double t = 0.0;
+    for (int i = 0; i < N.prof_n; ++i) {
+      float m = 0.0f;
+      EB_CUDA(cudaEventElapsedTime(&m, N.prof_ev[i].first, N.prof_ev[i].second));
+      t += m;
+    }
+    *ms = t;
+    *launches = N.prof_n;
+    N.prof_n = 0;
+  });
+}
 
 int nn_status(nn_handle* h, cudaStream_t stream) {
   if (!h) {

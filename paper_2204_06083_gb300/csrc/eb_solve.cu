@@ -688,7 +688,7 @@ static bool capturing(cudaStream_t s) {
 // pairs time the kernels back to back, without host-enqueue gaps.
 void Solver::prof_begin(int mode, cudaStream_t) {
   prof_on = mode != 0;
-  prof_what = mode == PROF_CONV ? PROF_CONV : PROF_SMOOTHER;
+  prof_what = (mode == PROF_CONV || mode == PROF_LEVEL1) ? mode : PROF_SMOOTHER;
   prof_n = g_pairs;
   prof_acc_ms = 0.0;
   prof_acc_n = 0;

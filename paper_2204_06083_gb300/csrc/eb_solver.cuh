@@ -13,8 +13,9 @@ namespace ebk {
 // kernels; the batch finalizes every op in its per-geometry kernel.
 enum { FIN_INIT = 0, FIN_RZ0 = 1, FIN_ALPHA = 2, FIN_RR = 3, FIN_BETA = 4, FIN_RZ0F = 5, FIN_BETAF = 6 };
 enum { PCG_FLAG_NONFINITE = 1, PCG_FLAG_BREAKDOWN = 2 };
-// what pcg_opts.profile times: the level-0 smoother launches or the learned stage's 32 -> 32 convolutions
-enum { PROF_SMOOTHER = 1, PROF_CONV = 2 };
+// what pcg_opts.profile times: the level-0 smoother launches, the learned stage's 32 -> 32
+// convolutions, or the level-1 (first coarse, CSR) smoother launches
+enum { PROF_SMOOTHER = 1, PROF_CONV = 2, PROF_LEVEL1 = 3 };
 
 // rz[iters & 1] holds r'z of the current iteration; the kernel that computes
 // the next one writes the other slot, so that no CTA reads a value another CTA
