@@ -60,6 +60,8 @@ CHEB_BYTES_PER_DOF = {"f32": 20, "f64": 40}
 LEAPFROG_BYTES_PER_DOF = {"f32": 13, "f64": 25}
 # one 32 -> 32 convolution of the learned stage per pixel: 2 x 9 x 32 x 32 FLOP
 CONV_FLOP_PER_PX = 18432
+# and its bytes per pixel: 32 BF16 channels read and 32 written
+CONV_BYTES_PER_PX = 128
 CPU_SAMPLE_N = 112
 PROF_NOTE = ("CUDA events around every launch of the kernel in as many solves (batched: one bench step) run right "
              "after the timed ones on the same input; those use the captured iteration with a host check, since "
@@ -75,21 +77,21 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def kernel_fingerprint():
+def kernel_fingerprint(files):
     h = hashlib.sha256()
-    for f in ("amg_vcycle.cu", "stencil.cuh", "tiles.cuh"):
+    for f in files:
         h.update(open(os.path.join(ROOT, "paper_2204_06083_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
-    """Per-launch DRAM bytes of the 3D roofline kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "cheb_step_3d_256_traffic.json")
+def recorded_traffic(kernel):
+    """Per-launch DRAM bytes (read + write) of a roofline kernel from the
+    committed ncu summaries, if they were taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "kernel_traffic.json")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p))
-    if d.get("fingerprint") != kernel_fingerprint():
+    d = json.load(open(p)).get(kernel)
+    if not d or d.get("fingerprint") != kernel_fingerprint(d["files"]):
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -559,7 +561,7 @@ def gpu_poisson(ctx, args, dim):
                "kernel": f"k_g_cheb_step<{dim}, {'float, float' if dim == 3 else 'double, double'}>",
                "achieved": achieved, "peak": pk["hbm_gbs"], "peak_kind": kind, "unit": "GB/s",
                "frac": (achieved / pk["hbm_gbs"]) if achieved else None,
-               "traffic": recorded_traffic() if dim == 3 else None,
+               "traffic": recorded_traffic("k_g_cheb_step<3, float, float>") if dim == 3 else None,
                "algorithmic_bytes_per_launch": vb * nc, "avg_launch_us": avg_s * 1e6,
                "launches_timed": prof_n, "timing": PROF_NOTE}
     roof = stencil
@@ -573,7 +575,8 @@ def gpu_poisson(ctx, args, dim):
         l1_ach = l1_bytes / l1_s / 1e9
         level1 = {"bound": "hbm", "kernel": f"k_c_cheb_step<G, {'float' if dim == 3 else 'double'}> (level 1, CSR)",
                   "achieved": l1_ach, "peak": pk["hbm_gbs"], "peak_kind": kind, "unit": "GB/s",
-                  "frac": l1_ach / pk["hbm_gbs"], "traffic": None,
+                  "frac": l1_ach / pk["hbm_gbs"],
+                  "traffic": recorded_traffic("k_c_cheb_step<G, float> level 1") if dim == 3 else None,
                   "algorithmic_bytes_per_launch": l1_bytes, "avg_launch_us": l1_s * 1e6, "launches_timed": l1_n,
                   "rows": n1, "nnz": nnz1, "timing": PROF_NOTE}
         if l1_ms > prof_ms:  # the line's roofline is the kernel with the larger share of the solve
@@ -848,67 +851,16 @@ def gpu_learned(ctx, args):
             "time_to_tol_ms": ms_per_step, "compare": compare,
             "training": {"pairs": npairs, "pair_generation_s": pairs_s, "train_s": train_s, "adam_steps": npairs // batch,
                          "batch": batch, "loss_log": log},
-            "roofline": {"bound": "tensor", "kernel": "k_conv32 (32->32 implicit-GEMM conv, mma.sync bf16)",
-                         "achieved": achieved, "peak": peak, "peak_kind": kind + " bf16 sustained", "unit": "TFLOP/s",
-                         "frac": (achieved / peak) if achieved else None, "traffic": None,
-                         "algorithmic_flops_per_launch": CONV_FLOP_PER_PX * px, "avg_launch_us": avg_s * 1e6,
-                         "launches_timed": prof_n, "timing": PROF_NOTE},
-            "e2e": {"value": e2e_value, "unit": "DOF/s", "h2d_bytes_per_step": hb.numel() * 8,
-                    "d2h_bytes_per_step": hx.numel() * 8},
-            "gpu_launches": sts[-1].launches, "clocks": clocks}
-
-
-def gpu_conv(ctx, args):
-    import numpy as np
-    import torch
-    import eb_inputs as ei
-    import paper_2204_06083_gb300 as eb
-    from paper_2204_06083_gb300 import learned
-    n = 2048
-    h = eb.EB(ei.box_grid(2, n), ei.random_star(999))
-    cp = ((h.classes() & eb.CODE_CP) != 0).float()
-    rng = np.random.default_rng(0)
-    inp = torch.empty((1, n, n, 2), dtype=torch.float32, device=ctx.dev)
-    inp[0, :, :, 0] = torch.from_numpy(rng.standard_normal((n, n)).astype(np.float32)).cuda() * cp
-    inp[0, :, :, 1] = cp
-    out = torch.empty((1, n, n), dtype=torch.float32, device=ctx.dev)
-    net = eb.Net(learned.init_params(8))
-
-    def step():
-        net.forward(inp, out)
-
-    _, ms_per_step, clocks = loop(ctx, args, step, torch.cuda.current_device())
-    px = n * n
-    value = ctx.world * px / (ms_per_step / 1000.0)
-    net.set_profile(True)  # the convolution launches, in as many forwards right after the timed ones
-    for _ in range(args.steps):
-        ctx.flush()
-        net.forward(inp, out)
-    conv_ms, conv_n = net.profile()
-    net.set_profile(False)
-    net.status()
-    hin = inp.cpu().pin_memory()
-    hout = torch.empty_like(out, device="cpu").pin_memory()
-    din = torch.empty_like(inp)
-    e2e = []
-    for i in range(1 + args.steps):
-        ctx.flush()
-        t, _ = timed(lambda: (din.copy_(hin, non_blocking=True), net.forward(din, out),
-                              hout.copy_(out, non_blocking=True)))
-        if i >= 1:
-            e2e.append(t)
-    e2e_value = ctx.world * px / (ctx.max_over_ranks(statistics.mean(e2e)) / 1000.0)
-    pk, kind = peaks()
-    avg_s = (conv_ms / conv_n) / 1000.0 if conv_n else float("nan")
-    achieved = CONV_FLOP_PER_PX * px / avg_s / 1e12 if conv_n else None
-    peak = pk.get("bf16_tflops", pk.get("bf16_tflops_sustained"))
-    return {"value": value, "ms_per_step": ms_per_step, "dtype": "bf16 (f32 accumulate)",
-            "roofline": {"bound": "tensor", "kernel": "k_conv32 (32->32 implicit-GEMM conv, tcgen05.mma, TMEM)",
-                         "achieved": achieved, "peak": peak, "peak_kind": kind + " bf16 burst", "unit": "TFLOP/s",
-                         "frac": (achieved / peak) if achieved else None, "traffic": None,
-                         "algorithmic_flops_per_launch": CONV_FLOP_PER_PX * px, "avg_launch_us": avg_s * 1e6,
+            # 144 FLOP per byte moved, below the ridge (peak FLOP/s over peak B/s): HBM is the roof that binds
+            "roofline": {"bound": "hbm", "kernel": "k_conv32 (32->32 implicit-GEMM conv, tcgen05.mma, TMEM)",
+                         "achieved": hbm_ach, "peak": pk["hbm_gbs"], "peak_kind": kind, "unit": "GB/s",
+                         "frac": (hbm_ach / pk["hbm_gbs"]) if hbm_ach else None,
+                         "traffic": recorded_traffic("k_conv32"),
+                         "algorithmic_bytes_per_launch": CONV_BYTES_PER_PX * px, "avg_launch_us": avg_s * 1e6,
                          "launches_timed": conv_n,
-                         "hbm_gbs_equivalent": 128 * px / avg_s / 1e9 if conv_n else None},
+                         "tensor": {"achieved": achieved, "peak": peak, "peak_kind": kind + " bf16 burst",
+                                    "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+                                    "algorithmic_flops_per_launch": CONV_FLOP_PER_PX * px}},
             "e2e": {"value": e2e_value, "unit": "pixels/s", "h2d_bytes_per_step": hin.numel() * 4,
                     "d2h_bytes_per_step": hout.numel() * 4},
             "gpu_launches": 6, "clocks": clocks}

@@ -264,9 +264,11 @@ int heat_step(const amg_handle* amg, double dt, double theta, const double* b1_d
 /* nsteps of the explicit leapfrog scheme (the theta-scheme of Sec. 3.5 with
  * theta = 0): u^{n+1} = 2 u^n - u^{n-1} - dt^2 A u^n (homogeneous Dirichlet
  * data).  On entry (u_prev, u_cur) = (u^{n-1}, u^n); on exit they hold
- * (u^{n+nsteps-1}, u^{n+nsteps}).  One persistent cooperative launch; its
- * grid-wide barrier gives up after a bounded spin and returns EB_ERR_TIMEOUT.
- * prec: EB_F64 or EB_F32 element type of both fields. */
+ * (u^{n+nsteps-1}, u^{n+nsteps}).  One kernel launch per step; whole chunks of
+ * 32 steps run as one launch of a CUDA graph that the handle caches for these
+ * fields, prec, dt and tile list (built on first use, which allocates).
+ * prec: EB_F64 or EB_F32 element type of both fields.  Asynchronous on
+ * stream; the fields must not be touched by other work until it completes. */
 int wave_step(const eb_handle* eb, int prec, double dt, void* u_prev_dev, void* u_cur_dev, int nsteps,
               cudaStream_t stream);
 
@@ -423,23 +425,16 @@ int nn_precondition(const amg_handle* amg, nn_handle* nn, int mode, const double
 int pcg_solve_nn(const amg_handle* amg, nn_handle* nn, int mode, const double* b_dev, double* x_dev, double rtol,
                  int maxit, const pcg_opts* opts, pcg_stats* stats, cudaStream_t stream);
 
-/* The leapfrog step of wave_step for callers that must not allocate device
- * memory during the call.  The paper has no counterpart: this is a service of
- * this library.  wave_step allocates a small barrier record per call; code
+/* The leapfrog steps of wave_step for callers that must not allocate during
+ * the call.  The paper has no counterpart: this is a service of this library.
+ * wave_step builds and caches a CUDA graph on first use, which allocates; code
  * running while a surrounding CUDA graph is being captured, loops that must not
  * touch the allocator after start-up, and programs whose device memory is held
- * by another framework's pool cannot allow that.  This entry point keeps the
- * barrier in a fixed device array of the library instead (one flag per
- * cooperative CTA, at most 2048 CTAs, about 8 KB, held by every GPU that loads
- * the library until the process exits) and calls no cudaMalloc, cudaFree or
- * allocating library routine.  Same arguments, arithmetic and results as
+ * by another framework's pool cannot allow that.  This entry point launches
+ * every step directly on the stream and calls no cudaMalloc, cudaFree, graph
+ * or allocating library routine.  Same arguments, arithmetic and results as
  * wave_step; the handle and the fields are created by the caller beforehand.
- * The first call on each device looks up the array's device address (no
- * allocation); make that first call before any stream capture.  All calls
- * share the array and each clears the part it uses before its launch, so two
- * calls whose kernels overlap on the GPU race and must not be issued.  A launch
- * that would need more than 2048 CTAs is rejected with EB_ERR_INVALID.
- * Synchronous, like wave_step. */
+ * Asynchronous on stream, like wave_step. */
 int wave_step_noalloc(const eb_handle* eb, int prec, double dt, void* u_prev_dev, void* u_cur_dev, int nsteps,
                       cudaStream_t stream);
 

@@ -100,13 +100,13 @@ int eb_autotune(eb_handle* eb, int op_kind, int prec, int reps, eb_tune_t* out, 
     uint8_t* y = nullptr;
     try {
       y = dalloc<uint8_t>(nn * es, stream);
-      // leapfrog: 16 steps of the persistent kernel per timed call (dt = 0: fields stay finite)
+      // leapfrog: 16 step launches per timed call (dt = 0: fields stay finite)
       auto leap = [&] {
         int rc = prec == EB_F64
                      ? launch_leapfrog<double>(E, reinterpret_cast<double*>(x), reinterpret_cast<double*>(y), 16, 0.0,
-                                               stream)
+                                               stream, false)
                      : launch_leapfrog<float>(E, reinterpret_cast<float*>(x), reinterpret_cast<float*>(y), 16, 0.0,
-                                              stream);
+                                              stream, false);
         EB_REQUIRE(rc == EB_OK, rc, "eb_autotune: leapfrog launch failed");
       };
       auto op = [&] {

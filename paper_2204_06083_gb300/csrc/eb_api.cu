@@ -154,9 +154,9 @@ int wave_step(const eb_handle* eb, int prec, double dt, void* u_prev_dev, void* 
   int rc = EB_OK;
   int st = guarded([&] {
     if (prec == EB_F64)
-      rc = launch_leapfrog<double>(eb->h, (double*)u_prev_dev, (double*)u_cur_dev, nsteps, dt, stream);
+      rc = launch_leapfrog<double>(eb->h, (double*)u_prev_dev, (double*)u_cur_dev, nsteps, dt, stream, true);
     else if (prec == EB_F32)
-      rc = launch_leapfrog<float>(eb->h, (float*)u_prev_dev, (float*)u_cur_dev, nsteps, dt, stream);
+      rc = launch_leapfrog<float>(eb->h, (float*)u_prev_dev, (float*)u_cur_dev, nsteps, dt, stream, true);
     else
       throw Failure{EB_ERR_INVALID, "wave_step: precision must be EB_F64 or EB_F32"};
   });

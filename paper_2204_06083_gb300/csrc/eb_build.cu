@@ -475,6 +475,7 @@ void build_tiles(EBHandle& eb, int tx, int ty, int tz, cudaStream_t s) {
 
 void destroy_handle(EBHandle& eb) {
   cudaStream_t s = eb.home;
+  eb.lf_graph.release();
   dfree(eb.code, s); dfree(eb.diag, s); dfree(eb.diag32, s); dfree(eb.cp_of_node, s); dfree(eb.cp_node, s);
   dfree(eb.tiles, s); dfree(eb.tile_base, s); dfree(eb.tile_lim, s); dfree(eb.cut_cp, s); dfree(eb.cut_dir, s); dfree(eb.cut_delta, s);
   dfree(eb.cut_c, s); dfree(eb.cut_xg, s); dfree(eb.cut_off, s);

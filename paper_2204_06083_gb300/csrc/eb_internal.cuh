@@ -92,6 +92,18 @@ struct Geometry {
 };
 
 // ------------------------------------------------------------------ handle
+// CUDA graph of CHUNK consecutive leapfrog launches, cached per handle for
+// the fields, precision, dt and tile list it was built with
+struct LeapfrogGraph {
+  static constexpr int CHUNK = 32;  // even: a chunk leaves the roles of the two fields unchanged
+  cudaGraphExec_t exec = nullptr;
+  const void* ua = nullptr;
+  const void* ub = nullptr;
+  int prec = -1, tile_gen = -1;
+  double c2 = 0.0;
+  void release();
+};
+
 struct EBHandle {
   Geometry g;
   eb_levelset ls;
@@ -126,6 +138,7 @@ struct EBHandle {
   double* cut_xg = nullptr;      // [num_cut * dim]
   int32_t* cut_off = nullptr;    // [num_cp + 1] first cut of CP k
   cudaStream_t home = 0;
+  mutable LeapfrogGraph lf_graph;
 };
 
 }  // namespace ebk
@@ -213,5 +226,5 @@ double time_us(const std::function<void()>& op, int reps, cudaStream_t s);
 void run_tuner(int dim, const std::function<void(const TileDims&)>& retile, const std::function<void()>& op,
                int reps, eb_tune_t* out, cudaStream_t s);
 template <class T>
-int launch_leapfrog(const EBHandle& eb, T* ua, T* ub, int nsteps, double dt, cudaStream_t s);
+int launch_leapfrog(const EBHandle& eb, T* ua, T* ub, int nsteps, double dt, cudaStream_t s, bool use_graph);
 }
