@@ -109,15 +109,22 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_first(TileView tv, const 
   }
 }
 
-// res = D^-1 (b - A x); d = c1 d + c2 res; xo = x + d   (xo may be FP64)
-template <int DIM, class V, class O>
+// res = D^-1 (b - A x); d = c1 d + c2 res; xo = x + d   (xo may be FP64).
+// DOT (xo FP64, the V-cycle's output z): also the CTA's partial r.z and, with
+// zold, r.zold (pairs), summed over its node pairs in loop order exactly as
+// the PCG's own dot kernels do.
+template <int DIM, class V, class O, bool DOT = false>
 __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_step(TileView tv, const uint8_t* __restrict__ code,
                                                             const typename DiagOf<V>::type* __restrict__ diag,
                                                             GOp<typename AccOf<V>::type> o,
                                                             const V* __restrict__ b, const V* __restrict__ x,
                                                             O* __restrict__ xo, V* __restrict__ d,
-                                                            typename AccOf<V>::type c1, typename AccOf<V>::type c2) {
+                                                            typename AccOf<V>::type c1, typename AccOf<V>::type c2,
+                                                            const double* __restrict__ r64 = nullptr,
+                                                            const double* __restrict__ zold = nullptr,
+                                                            double* __restrict__ part = nullptr) {
   using A = typename AccOf<V>::type;
+  double srz = 0.0, srzo = 0.0;
   EB_PAIR_LOOP(DIM, tv, node) {
     const GOp<A> ot = tile_op(tv, tt_, o);
     uint32_t k0, k1;
@@ -135,7 +142,29 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_step(TileView tv, const u
     const A d0 = (k0 & CODE_CP) ? c1 * dv.x + c2 * res0 : (A)0;
     const A d1 = (k1 & CODE_CP) ? c1 * dv.y + c2 * res1 : (A)0;
     st2o(d + node, d0, d1);
-    st2(xo + node, (k0 & CODE_CP) ? xc.x + d0 : (A)0, (k1 & CODE_CP) ? xc.y + d1 : (A)0);
+    const A z0 = (k0 & CODE_CP) ? xc.x + d0 : (A)0, z1 = (k1 & CODE_CP) ? xc.y + d1 : (A)0;
+    st2(xo + node, z0, z1);
+    if (DOT) {
+      const Two<double> rv = LdRO::ld2(r64 + node);
+      srz += rv.x * (double)z0 + rv.y * (double)z1;
+      if (zold) {
+        const Two<double> ov = LdRO::ld2(zold + node);
+        srzo += rv.x * ov.x + rv.y * ov.y;
+      }
+    }
+  }
+  if (DOT) {
+    __shared__ double sm[32];
+    const double a = block_sum(srz, sm);
+    if (zold) {
+      const double t = block_sum(srzo, sm);
+      if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = t;
+      }
+    } else if (threadIdx.x == 0) {
+      part[blockIdx.x] = a;
+    }
   }
 }
 
@@ -167,6 +196,34 @@ __device__ __forceinline__ A group_reduce(A s) {
   return s;
 }
 
+// Lane g's part of sum_e v[e] x[col[e]] over entries beg..end-1 of a row:
+// entries g, g+G, g+2G, ... summed in that order.  The column indices and
+// values of CSR_UNROLL entries are loaded before their x gathers, so a row
+// costs two dependent memory round trips per CSR_UNROLL * G entries instead of
+// two per G; the summation order, hence the rounding, is that of the plain
+// loop.
+constexpr int CSR_UNROLL = 4;
+template <int G, class V, class X>
+__device__ __forceinline__ typename AccOf<V>::type csr_dot(const int32_t* __restrict__ col, const V* __restrict__ v,
+                                                           const X* x, int32_t beg, int32_t end, int g) {
+  using A = typename AccOf<V>::type;
+  A s = 0;
+  for (int32_t e0 = beg + g; e0 < end; e0 += CSR_UNROLL * G) {
+    int32_t c[CSR_UNROLL];
+    A w[CSR_UNROLL];
+#pragma unroll
+    for (int u = 0; u < CSR_UNROLL; ++u) {
+      const int32_t e = e0 + u * G;
+      c[u] = e < end ? __ldg(col + e) : -1;
+      w[u] = e < end ? cvt<A>(v[e]) : (A)0;
+    }
+#pragma unroll
+    for (int u = 0; u < CSR_UNROLL; ++u)
+      if (c[u] >= 0) s += w[u] * cvt<A>(x[c[u]]);
+  }
+  return s;
+}
+
 // out = R r with R's columns given as grid nodes
 template <int G, class V>
 __global__ void k_restrict0(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ node_col,
@@ -176,8 +233,7 @@ __global__ void k_restrict0(int64_t n, const int32_t* __restrict__ rp, const int
   const int64_t i = t / G;
   const int g = (int)(t % G);
   A s = 0;
-  if (i < n)
-    for (int32_t e = rp[i] + g; e < rp[i + 1]; e += G) s += cvt<A>(v[e]) * cvt<A>(r[node_col[e]]);
+  if (i < n) s = csr_dot<G>(node_col, v, r, rp[i], rp[i + 1], g);
   s = group_reduce<G>(s);
   if (i < n && g == 0) out[i] = cvt<V>(s);
 }
@@ -192,8 +248,7 @@ __global__ void k_prolong0(int64_t n, const int32_t* __restrict__ rp, const int3
   const int64_t i = t / G;
   const int g = (int)(t % G);
   A s = 0;
-  if (i < n)
-    for (int32_t f = rp[i] + g; f < rp[i + 1]; f += G) s += cvt<A>(v[f]) * cvt<A>(e[ci[f]]);
+  if (i < n) s = csr_dot<G>(ci, v, e, rp[i], rp[i + 1], g);
   s = group_reduce<G>(s);
   if (i < n && g == 0) {
     const int32_t node = cp_node[i];
@@ -257,11 +312,11 @@ template <int G, class V>
 __device__ __forceinline__ typename AccOf<V>::type csr_row(const CsrV<V>& M, const V* x, int64_t i, int g) {
   using A = typename AccOf<V>::type;
   A s = 0;
-  if (i < M.n)
-    for (int32_t e = M.rp[i] + g; e < M.rp[i + 1]; e += G) s += cvt<A>(M.v[e]) * cvt<A>(x[M.ci[e]]);
+  if (i < M.n) s = csr_dot<G>(M.ci, M.v, x, M.rp[i], M.rp[i + 1], g);
   return group_reduce<G>(s);
 }
 
+// the row's own values are loaded first, alongside the row pointers
 template <int G, class V>
 __global__ void k_c_cheb_step(CsrV<V> M, const V* dinv, const V* b, const V* x, V* xo, V* d,
                               typename AccOf<V>::type c1, typename AccOf<V>::type c2) {
@@ -269,12 +324,19 @@ __global__ void k_c_cheb_step(CsrV<V> M, const V* dinv, const V* b, const V* x, 
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t i = t / G;
   const int g = (int)(t % G);
+  A di = 0, bi = 0, dd = 0, xi = 0;
+  if (i < M.n && g == 0) {
+    di = cvt<A>(dinv[i]);
+    bi = cvt<A>(b[i]);
+    if (c1 != (A)0) dd = cvt<A>(d[i]);
+    xi = cvt<A>(x[i]);
+  }
   const A ax = csr_row<G>(M, x, i, g);
   if (i >= M.n || g != 0) return;
-  const A res = cvt<A>(dinv[i]) * (cvt<A>(b[i]) - ax);
-  const A dv = (c1 == (A)0 ? (A)0 : c1 * cvt<A>(d[i])) + c2 * res;
+  const A res = di * (bi - ax);
+  const A dv = (c1 == (A)0 ? (A)0 : c1 * dd) + c2 * res;
   d[i] = cvt<V>(dv);
-  xo[i] = cvt<V>(cvt<A>(x[i]) + dv);
+  xo[i] = cvt<V>(xi + dv);
 }
 
 template <int G, class V>
@@ -460,7 +522,7 @@ static void vcycle_compact(Solver& S, size_t l, cudaStream_t s) {
 }
 
 template <class V, int DIM>
-static void vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s) {
+static int vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, const VcycleDot* dot) {
   using LV = LevelView<V>;
   Hierarchy& H = *S.H;
   const EBHandle& eb = *S.eb;
@@ -475,7 +537,7 @@ static void vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s) {
     k_scatter_cp<V><<<blocks_for(n, 256), 256, 0, s>>>(n, eb.cp_node, v.x, z);
     EB_CUDA(cudaGetLastError());
     S.nlaunch += 3;
-    return;
+    return 0;
   }
   const double inv_h2 = 1.0 / (G.h * G.h);
   const unsigned gb = tile_grid(eb);
@@ -516,32 +578,34 @@ static void vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s) {
   else
     EB_GROUP_LAUNCH(gP, k_prolong0, V, P0.n, s, P0.n, P0.rp, P0.ci, P0.v, eb.cp_node, cv.x, x);
   for (int k = 0; k < cc.deg; ++k) {
-    S.prof_mark(s, true);
-    if (k == cc.deg - 1)
+    // the launch that also forms the r'z partials is a different kernel: not
+    // part of the smoother-step timing
+    const bool mark = !(k == cc.deg - 1 && dot);
+    if (mark) S.prof_mark(s, true);
+    if (k == cc.deg - 1 && dot)
+      k_g_cheb_step<DIM, V, double, true><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, x, z, g.d, (A)cc.c1[k],
+                                                                    (A)cc.c2[k], dot->r, dot->zold, dot->part);
+    else if (k == cc.deg - 1)
       k_g_cheb_step<DIM, V, double>
           <<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, x, z, g.d, (A)cc.c1[k], (A)cc.c2[k]);
     else
       k_g_cheb_step<DIM, V, V><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, x, x2, g.d, (A)cc.c1[k], (A)cc.c2[k]);
-    S.prof_mark(s, false);
+    if (mark) S.prof_mark(s, false);
     if (k != cc.deg - 1) std::swap(x, x2);
   }
   g.x = x;
   g.x2 = x2;
   EB_CUDA(cudaGetLastError());
+  return dot ? (int)gb : 0;
 }
 
-void amg_vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s) {
+int amg_vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, const VcycleDot* dot) {
   const int dim = S.eb->g.dim;
-  if (S.opts.vcycle_prec == EB_F32) {
-    if (dim == 2) vcycle_grid<float, 2>(S, r, z, s);
-    else vcycle_grid<float, 3>(S, r, z, s);
-  } else if (S.opts.vcycle_prec == EB_BF16) {
-    if (dim == 2) vcycle_grid<__nv_bfloat16, 2>(S, r, z, s);
-    else vcycle_grid<__nv_bfloat16, 3>(S, r, z, s);
-  } else {
-    if (dim == 2) vcycle_grid<double, 2>(S, r, z, s);
-    else vcycle_grid<double, 3>(S, r, z, s);
-  }
+  if (S.opts.vcycle_prec == EB_F32)
+    return dim == 2 ? vcycle_grid<float, 2>(S, r, z, s, dot) : vcycle_grid<float, 3>(S, r, z, s, dot);
+  if (S.opts.vcycle_prec == EB_BF16)
+    return dim == 2 ? vcycle_grid<__nv_bfloat16, 2>(S, r, z, s, dot) : vcycle_grid<__nv_bfloat16, 3>(S, r, z, s, dot);
+  return dim == 2 ? vcycle_grid<double, 2>(S, r, z, s, dot) : vcycle_grid<double, 3>(S, r, z, s, dot);
 }
 
 template <class V>

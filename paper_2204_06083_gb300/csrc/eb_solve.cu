@@ -17,18 +17,6 @@
 
 namespace ebk {
 
-__device__ __forceinline__ double block_sum(double v, double* sm) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0) sm[w] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0)
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sm[i];
-  return s;
-}
-
 struct OpParams {
   double inv_h2, sigma, dinv_int;
 };
@@ -365,7 +353,9 @@ void Solver::alloc_work(cudaStream_t s) {
   tmp = dalloc<double>(nn, s);
   if (opts.vcycle_prec != EB_F64) zold = dalloc<double>(nn, s);
   nblk = (int)std::min<int64_t>(std::max<int64_t>(eb->num_tiles, 1), (int64_t)num_sms() * 4);
-  part = dalloc<double>(6 * (int64_t)nblk, s);  // three regions of 2 nblk: p'q / r'r / r'z partials
+  // p'q and r'r regions of 2 nblk, then r'z of 2 max(nblk, 8 SMs) (the V-cycle's
+  // grid sweeps use at most 8 CTAs per SM)
+  part = dalloc<double>(4 * (int64_t)nblk + 2 * std::max<int64_t>(nblk, (int64_t)num_sms() * 8), s);
   sc = dalloc<PcgScalars>(1, s);
   EB_CUDA(cudaMallocHost((void**)&sc_host, sizeof(PcgScalars)));
 }
@@ -381,20 +371,27 @@ void Solver::free_work() {
   sc_host = nullptr;
 }
 
-void Solver::finalize(int op, const double* src, cudaStream_t s) {
+void Solver::finalize(int op, const double* src, cudaStream_t s, int count) {
   ++nlaunch;
-  k_finalize<<<1, 1024, 0, s>>>(src, nblk, op, sc);
+  k_finalize<<<1, 1024, 0, s>>>(src, count < 0 ? nblk : count, op, sc);
 }
 
 void Solver::precondition(int kind, const double* rin, double* zout, cudaStream_t s) {
   const int dim = eb->g.dim;
   const TileView tv = eb->tv();
+  rz_n = nblk;
   if (kind == EB_PC_AMG_NN) {
     amg_vcycle_grid(*this, rin, zout, s);
     nn_stage_apply(nn, *eb, shift, nn_mode, rin, zout, nlaunch, this, s);
     EB_DIM_LAUNCH(dim, k_dot2, nblk, tv, rin, zout, zold, part_rz());
   } else if (kind == EB_PC_AMG && H) {
-    amg_vcycle_grid(*this, rin, zout, s);
+    // the V-cycle's last smoothing launch forms the r'z partials itself
+    VcycleDot dot;
+    dot.r = rin;
+    dot.zold = flexible() ? zold : nullptr;
+    dot.part = part_rz();
+    rz_n = amg_vcycle_grid(*this, rin, zout, s, &dot);
+    if (rz_n) return;
     if (flexible())
       EB_DIM_LAUNCH(dim, k_dot2, nblk, tv, rin, zout, zold, part_rz());
     else
@@ -459,8 +456,8 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
     if (total_iters >= maxit) break;
     precondition(kind, r, z, s);
     const bool flex = flex_for(kind);
-    finalize(flex ? FIN_RZ0F : FIN_RZ0, part_rz(), s);
-    EB_DIM_LAUNCH(dim, k_xpby, nblk, tv, sc, z, p, flex ? zold : nullptr, 1, part_rz(), nblk);
+    finalize(flex ? FIN_RZ0F : FIN_RZ0, part_rz(), s, rz_n);
+    EB_DIM_LAUNCH(dim, k_xpby, nblk, tv, sc, z, p, flex ? zold : nullptr, 1, part_rz(), rz_n);
     int it = 0;
     bool stop = false;
     if (o.use_graph == 1 && !prof_on) {  // the whole loop on the device
@@ -555,7 +552,7 @@ void Solver::iteration(int kind, const double* b, double* x, cudaStream_t s, boo
   EB_DIM_LAUNCH(dim, k_update_xr, nblk, tv, sc, x, r, p, q, part_pq(), nblk, part_rr());
   precondition(kind, r, z, s);
   const bool flex = flex_for(kind);
-  EB_DIM_LAUNCH(dim, k_xpby, nblk, tv, sc, z, p, flex ? zold : nullptr, 0, part_rz(), nblk);
+  EB_DIM_LAUNCH(dim, k_xpby, nblk, tv, sc, z, p, flex ? zold : nullptr, 0, part_rz(), rz_n);
   // r'r and the convergence test end the iteration (the device-side loop's
   // condition kernel does it itself)
   if (!loop_end) finalize(FIN_RR, part_rr(), s);

@@ -46,11 +46,15 @@ struct Solver {
   bool flex_for(int kind) const { return kind == EB_PC_AMG_NN || (kind == EB_PC_AMG && flexible()); }
   nn_handle* nn = nullptr;  // learned stage of EB_PC_AMG_NN (set for one solve)
   int nn_mode = 0;          // eb_nn_mode of that stage
-  double* part = nullptr;  // reduction partials: [p'q | r'r | r'z] regions of 2 nblk each
+  // reduction partials: [p'q | r'r] regions of 2 nblk each, then the r'z region
+  // of 2 max(nblk, 8 SMs): r'z comes from the PCG's own dot kernel (nblk
+  // partials) or from the V-cycle's last smoothing launch (one per CTA of it)
+  double* part = nullptr;
   double* part_pq() const { return part; }
   double* part_rr() const { return part + 2 * (int64_t)nblk; }
   double* part_rz() const { return part + 4 * (int64_t)nblk; }
   int nblk = 1;
+  int rz_n = 1;  // r'z partials written by the last precondition()
   PcgScalars* sc = nullptr;
   PcgScalars* sc_host = nullptr;
   int64_t nlaunch = 0;  // kernel launches issued (reported per solve)
@@ -82,7 +86,7 @@ struct Solver {
 
   void alloc_work(cudaStream_t s);
   void free_work();
-  void finalize(int op, const double* src, cudaStream_t s);
+  void finalize(int op, const double* src, cudaStream_t s, int count = -1);  // count < 0: nblk partials
   void precondition(int kind, const double* r, double* z, cudaStream_t s);
   int pcg(const double* b, double* x, double rtol, int maxit, const pcg_opts& o, pcg_stats* stats, cudaStream_t s);
   int heat(double dt, double theta, const double* b1, const double* b0, double* u, double rtol, int maxit,
@@ -109,7 +113,30 @@ cudaGraphExec_t build_while_graph(cudaStream_t cap,
 // AMG (amg.cu)
 void amg_build(Solver& S, cudaStream_t s);
 void amg_free(Solver& S);
-void amg_vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s);
+// Sum of v over the CTA (warp shuffles, then the warps in order); thread 0
+// holds the result.  Every reduction partial of the PCG is formed this way.
+__device__ __forceinline__ double block_sum(double v, double* sm) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sm[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sm[i];
+  return s;
+}
+
+// z = V r.  With dot, the last level-0 smoothing launch also writes per-CTA
+// partials of r.z (and of r.zold when dot->zold is set, as pairs) to
+// dot->part; returns their count, or 0 if no launch wrote them (single-level
+// hierarchy), in which case the caller computes the dot itself.
+struct VcycleDot {
+  const double* r = nullptr;
+  const double* zold = nullptr;
+  double* part = nullptr;
+};
+int amg_vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, const VcycleDot* dot = nullptr);
 void amg_fill_info(const Solver& S, amg_info_t* out);
 void amg_copy_level(const Solver& S, int level, int which, int32_t* rowptr, int32_t* col, double* val, cudaStream_t s);
 
