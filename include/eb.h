@@ -427,14 +427,24 @@ int pcg_solve_nn(const amg_handle* amg, nn_handle* nn, int mode, const double* b
 
 /* The leapfrog steps of wave_step for callers that must not allocate during
  * the call.  The paper has no counterpart: this is a service of this library.
- * wave_step builds and caches a CUDA graph on first use, which allocates; code
- * running while a surrounding CUDA graph is being captured, loops that must not
- * touch the allocator after start-up, and programs whose device memory is held
- * by another framework's pool cannot allow that.  This entry point launches
- * every step directly on the stream and calls no cudaMalloc, cudaFree, graph
- * or allocating library routine.  Same arguments, arithmetic and results as
- * wave_step; the handle and the fields are created by the caller beforehand.
- * Asynchronous on stream, like wave_step. */
+ * wave_step builds and caches a CUDA graph on its first call for a set of
+ * fields, which allocates; loops with a fixed memory budget that must not
+ * touch the allocator after start-up, programs whose device memory is held by
+ * another framework's pool, and time-critical loops that cannot afford the
+ * device synchronisation of cudaMalloc / cudaFree cannot allow that.  This
+ * entry point runs all nsteps in one persistent cooperative launch and keeps
+ * the scratch of its grid-wide barrier in a fixed device array of the library
+ * (one flag per cooperative CTA, at most 2048 CTAs, about 8 KB, held by every
+ * GPU that loads the library until the process exits); it calls no cudaMalloc,
+ * cudaFree or allocating library routine.  Same arguments, arithmetic and
+ * results as wave_step; the handle and the fields are created by the caller
+ * beforehand.  The first call on each device looks up the array's device
+ * address (no allocation); make that first call before any stream capture.
+ * All calls share the array and each clears the part it uses before its
+ * launch, so two calls whose kernels overlap on the GPU race and must not be
+ * issued.  A launch that would need more than 2048 CTAs is rejected with
+ * EB_ERR_INVALID; a barrier wait that gives up returns EB_ERR_TIMEOUT.
+ * Synchronous. */
 int wave_step_noalloc(const eb_handle* eb, int prec, double dt, void* u_prev_dev, void* u_cur_dev, int nsteps,
                       cudaStream_t stream);
 
