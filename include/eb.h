@@ -221,6 +221,24 @@ int amg_autotune(amg_handle* amg, int reps, eb_tune_t* out, cudaStream_t stream)
  * (may be NULL) the entries per lane chosen.  Results do not change (the sums
  * are grouped differently: FP rounding only).  Synchronous. */
 int amg_tune_csr(amg_handle* amg, int reps, double* us_out, int* best_out, cudaStream_t stream);
+/* Times one V-cycle kernel on its own (instrumentation; the paper has no
+ * counterpart).  kernel EB_TK_SMOOTH_STEP: one Chebyshev smoothing step of
+ * level `level` (level 0: the stencil kernel of Sec. 2 over the active tiles;
+ * coarser levels: the CSR kernel with the tuned row groups), in its V-cycle
+ * launch configuration, on the hierarchy's own matrices and level vectors.
+ * `launches` (1..10000) back-to-back launches are captured in one CUDA graph
+ * and timed by events around the graph, so no per-launch event enters the
+ * figure.  clear_bytes > 0: each launch is preceded by a read of a buffer of
+ * that many bytes (choose more than the L2 size), so that the kernel finds
+ * none of its data in L2 and no dirty lines to write back, as after a cache
+ * flush; the time of the reads alone, measured the same way, is subtracted.
+ * The buffer is allocated for the call.
+ * level must have a coarser level below it.  Overwrites the level's smoother
+ * vectors: call between solves.  us_out: microseconds per launch.
+ * Synchronous. */
+enum { EB_TK_SMOOTH_STEP = 0 };
+int amg_time_kernel(const amg_handle* amg, int kernel, int level, int launches, int64_t clear_bytes, double* us_out,
+                    cudaStream_t stream);
 
 typedef struct {
   int precond;           /* eb_pc_kind, default EB_PC_AMG */

@@ -23,6 +23,7 @@ EB_F64, EB_F32, EB_BF16 = 0, 1, 2
 EB_PC_AMG, EB_PC_JACOBI, EB_PC_NONE, EB_PC_AMG_NN = 0, 1, 2, 3
 EB_NN_PLAIN, EB_NN_ENERGY = 0, 1
 EB_TUNE_APPLY, EB_TUNE_LEAPFROG = 0, 1
+EB_TK_SMOOTH_STEP = 0
 STAR_MAX = 16
 
 CODE_BP = 0x40
@@ -104,6 +105,7 @@ _SIGS = {
     "eb_autotune": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.POINTER(eb_tune_t), _P]),
     "amg_autotune": (C.c_int, [_P, C.c_int, C.POINTER(eb_tune_t), _P]),
     "amg_tune_csr": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "amg_time_kernel": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int64, _P, _P]),
     "batch_autotune": (C.c_int, [_P, C.c_int, C.POINTER(eb_tune_t), _P]),
     "amg_setup": (C.c_int, [_P, C.c_double, C.POINTER(amg_opts), C.POINTER(_P), _P]),
     "amg_destroy": (None, [_P]),
@@ -423,6 +425,15 @@ class AMG:
         best = C.c_int()
         _check(load().amg_tune_csr(self._h, int(reps), C.cast(us, C.c_void_p), C.byref(best), _stream(stream)))
         return best.value, {e: us[i] for i, e in enumerate((1, 2, 4, 8))}
+
+    def time_smoother_step(self, level, launches=50, clear_bytes=0, stream=None):
+        """Microseconds per launch of level `level`'s Chebyshev smoothing step
+        timed on its own (amg_time_kernel); clear_bytes > 0 clears L2 before
+        every launch.  Overwrites the level's smoother vectors."""
+        us = C.c_double()
+        _check(load().amg_time_kernel(self._h, EB_TK_SMOOTH_STEP, int(level), int(launches), int(clear_bytes),
+                                      C.byref(us), _stream(stream)))
+        return us.value
 
     def heat_step(self, u, b1, dt, theta=1.0, b0=None, rtol=1e-10, maxit=1000, stream=None):
         st = pcg_stats()

@@ -680,3 +680,139 @@ void amg_free_vcycle(Hierarchy& H, cudaStream_t s) {
 }
 
 }  // namespace ebk
+
+// ------------------------------------------------------- kernel timing alone
+namespace ebk {
+
+// Reads n 16-byte words (a buffer larger than L2), so that L2 then holds only
+// clean lines of that buffer: the next kernel misses without write-backs, as
+// after a cache flush.  The store never happens for a buffer of zeros
+// (flag = 1); it only keeps the reads from being dropped.
+__global__ void k_l2_clear(const uint4* __restrict__ p, int64_t n, int flag, unsigned* sink) {
+  unsigned acc = 0u;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 v = __ldcg(p + i);
+    acc |= v.x | v.y | v.z | v.w;
+  }
+  if (acc == 0u && flag == 0) *sink = acc;
+}
+
+// One Chebyshev smoothing step of level `level` (k = 1 coefficients, so that
+// the step reads its previous direction), launched as in a V-cycle.
+template <class V>
+static void smoother_step(Solver& S, int level, cudaStream_t s) {
+  using LV = LevelView<V>;
+  using A = typename AccOf<V>::type;
+  Hierarchy& H = *S.H;
+  Level& L = H.L[level];
+  const ChebCoef cc = cheb_coef(L.rho, S.opts.cheb_degree);
+  const int k = cc.deg > 1 ? 1 : 0;
+  if (level == 0) {
+    const EBHandle& eb = *S.eb;
+    const Geometry& G = eb.g;
+    const double inv_h2 = 1.0 / (G.h * G.h);
+    const GOp<A> o{(A)inv_h2, (A)S.shift, (A)(1.0 / (S.shift + 2.0 * G.dim * inv_h2))};
+    VecSet<V>& g = LV::grid(H);
+    const V* b = std::is_same<V, double>::value ? reinterpret_cast<const V*>(S.r) : g.b;
+    if (G.dim == 2)
+      k_g_cheb_step<2, V, V><<<tile_grid(eb), TILE_NODES, 0, s>>>(eb.tv(), eb.code, diag_of<V>(eb), o, b, g.x, g.x2,
+                                                                    g.d, (A)cc.c1[k], (A)cc.c2[k]);
+    else
+      k_g_cheb_step<3, V, V><<<tile_grid(eb), TILE_NODES, 0, s>>>(eb.tv(), eb.code, diag_of<V>(eb), o, b, g.x, g.x2,
+                                                                    g.d, (A)cc.c1[k], (A)cc.c2[k]);
+  } else {
+    VecSet<V>& v = LV::vec(L);
+    const int gA = group_width(L.A.nnz, L.A.n, S.csr_epl);
+    EB_GROUP_LAUNCH(gA, k_c_cheb_step, V, L.A.n, s, LV::A(L), LV::dinv(L), v.b, v.x, v.x2, v.d, (A)cc.c1[k],
+                    (A)cc.c2[k]);
+  }
+}
+
+// microseconds per launch of `launches` back-to-back launches captured in one
+// graph (each preceded by an L2-clearing write when clear is given, whose own
+// time, measured the same way, is subtracted)
+static double time_alone(const std::function<void(cudaStream_t)>& launch, int launches, const uint4* clear,
+                         int64_t nclear, cudaStream_t s) {
+  cudaStream_t cap = nullptr;
+  EB_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto graph_us = [&](bool with_kernel) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    EB_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < launches; ++i) {
+      if (clear) k_l2_clear<<<num_sms() * 4, 512, 0, cap>>>(clear, nclear, 1, nullptr);
+      if (with_kernel) launch(cap);
+    }
+    EB_CUDA(cudaStreamEndCapture(cap, &g));
+    const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) throw Failure{EB_ERR_CUDA, std::string("amg_time_kernel: ") + cudaGetErrorString(ie)};
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      EB_CUDA(cudaEventRecord(e0, s));
+      EB_CUDA(cudaGraphLaunch(ge, s));
+      EB_CUDA(cudaEventRecord(e1, s));
+      EB_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      EB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      best = std::min(best, ms);
+    }
+    cudaGraphExecDestroy(ge);
+    return 1000.0 * best / launches;
+  };
+  double us = 0.0;
+  try {
+    EB_CUDA(cudaEventCreate(&e0));
+    EB_CUDA(cudaEventCreate(&e1));
+    us = graph_us(true);
+    if (clear) us -= graph_us(false);
+  } catch (...) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamDestroy(cap);
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(cap);
+  return us;
+}
+
+}  // namespace ebk
+
+using namespace ebk;
+
+extern "C" int amg_time_kernel(const amg_handle* amg, int kernel, int level, int launches, int64_t clear_bytes,
+                               double* us_out, cudaStream_t stream) {
+  if (!amg || !us_out || launches < 1 || launches > 10000 || clear_bytes < 0) {
+    set_error("amg_time_kernel: invalid argument");
+    return EB_ERR_INVALID;
+  }
+  return guarded([&] {
+    Solver& S = const_cast<Solver&>(amg->s);
+    EB_REQUIRE(S.H != nullptr, EB_ERR_INVALID, "amg_time_kernel: handle has no hierarchy");
+    EB_REQUIRE(kernel == EB_TK_SMOOTH_STEP, EB_ERR_INVALID, "amg_time_kernel: unknown kernel");
+    EB_REQUIRE(level >= 0 && level + 1 < (int)S.H->L.size(), EB_ERR_INVALID,
+               "amg_time_kernel: level must have a coarser level below it");
+    EB_REQUIRE(S.r != nullptr, EB_ERR_INVALID, "amg_time_kernel: no work vectors");
+    const int64_t nclear = clear_bytes / (int64_t)sizeof(uint4);
+    uint4* clear = nclear > 0 ? dalloc<uint4>(nclear, stream) : nullptr;  // zero-filled
+    double us = 0.0;
+    try {
+      auto launch = [&](cudaStream_t s) {
+        if (S.opts.vcycle_prec == EB_F32) smoother_step<float>(S, level, s);
+        else if (S.opts.vcycle_prec == EB_BF16) smoother_step<__nv_bfloat16>(S, level, s);
+        else smoother_step<double>(S, level, s);
+      };
+      EB_CUDA(cudaStreamSynchronize(stream));
+      us = time_alone(launch, launches, clear, nclear, stream);
+    } catch (...) {
+      dfree(clear, stream);
+      throw;
+    }
+    dfree(clear, stream);
+    EB_CUDA(cudaStreamSynchronize(stream));
+    *us_out = us;
+  });
+}

@@ -229,3 +229,26 @@ def test_bf16_vcycle_pcg(name):
     _, s64 = g64.solve(b, rtol=1e-10, maxit=500)
     print(f"{name}: iterations to 1e-10 BF16 {s16.iterations}, FP64 {s64.iterations}")
     assert s16.iterations <= 2 * s64.iterations + 2
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+def test_time_kernel_alone(prec):
+    """amg_time_kernel times a smoothing step of levels 0 and 1 on their own
+    (with and without the L2-clearing writes), leaves the solver usable and
+    rejects levels without a coarser level below them."""
+    eb = _eb()
+    grid, ls = CASES["ellipsoid64"]()
+    h = eb.EB(grid, ls)
+    vp = {"f64": eb.EB_F64, "f32": eb.EB_F32, "bf16": eb.EB_BF16}[prec]
+    amg = eb.AMG(h, 0.0, vcycle_prec=vp)
+    b = torch.tensor(np.random.default_rng(7).standard_normal(h.shape()), device="cuda")
+    x0, st0 = amg.solve(b, rtol=1e-10)
+    assert amg.num_levels >= 3
+    for lev in (0, 1):
+        warm = amg.time_smoother_step(lev, 10, 0)
+        cold = amg.time_smoother_step(lev, 4, 256 << 20)
+        assert 0.0 < warm < 1e4 and -5.0 < cold < 1e4
+    with pytest.raises(eb.EBError):
+        amg.time_smoother_step(amg.num_levels - 1, 4, 0)
+    x1, st1 = amg.solve(b, rtol=1e-10)
+    assert st1.iterations == st0.iterations and torch.equal(x1, x0)
