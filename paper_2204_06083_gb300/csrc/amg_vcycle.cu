@@ -202,7 +202,7 @@ __device__ __forceinline__ A group_reduce(A s) {
 // costs two dependent memory round trips per CSR_UNROLL * G entries instead of
 // two per G; the summation order, hence the rounding, is that of the plain
 // loop.
-constexpr int CSR_UNROLL = 4;
+constexpr int CSR_UNROLL = 8;
 template <int G, class V, class X>
 __device__ __forceinline__ typename AccOf<V>::type csr_dot(const int32_t* __restrict__ col, const V* __restrict__ v,
                                                            const X* x, int32_t beg, int32_t end, int g) {
