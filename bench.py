@@ -867,6 +867,7 @@ def gpu_learned(ctx, args):
     px = int(grid.n[0]) * int(grid.n[1])
     avg_s = (prof_ms / prof_n) / 1000.0 if prof_n else float("nan")
     achieved = CONV_FLOP_PER_PX * px / avg_s / 1e12 if prof_n else None
+    hbm_ach = CONV_BYTES_PER_PX * px / avg_s / 1e9 if prof_n else None
     peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
     return {"value": value, "ms_per_step": ms_per_step, "dtype": "f64 outer, bf16 CNN (f32 accumulate)",
             "num_cp": nc, "iterations": sts[-1].iterations, "converged": bool(sts[-1].converged),
@@ -874,6 +875,66 @@ def gpu_learned(ctx, args):
             "time_to_tol_ms": ms_per_step, "compare": compare,
             "training": {"pairs": npairs, "pair_generation_s": pairs_s, "train_s": train_s, "adam_steps": npairs // batch,
                          "batch": batch, "loss_log": log},
+            # the stage's 32 -> 32 convolutions: 144 FLOP per byte, below the ridge, so the HBM roof binds
+            "roofline": {"bound": "hbm", "kernel": "k_conv32 (32->32 implicit-GEMM conv, tcgen05.mma, TMEM)",
+                         "achieved": hbm_ach, "peak": pk["hbm_gbs"], "peak_kind": kind, "unit": "GB/s",
+                         "frac": (hbm_ach / pk["hbm_gbs"]) if hbm_ach else None, "traffic": recorded_traffic("k_conv32"),
+                         "algorithmic_bytes_per_launch": CONV_BYTES_PER_PX * px, "avg_launch_us": avg_s * 1e6,
+                         "launches_timed": prof_n, "timing": PROF_NOTE,
+                         "tensor": {"achieved": achieved, "peak": peak, "peak_kind": kind + " bf16 sustained",
+                                    "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+                                    "algorithmic_flops_per_launch": CONV_FLOP_PER_PX * px}},
+            "e2e": {"value": e2e_value, "unit": "DOF/s", "h2d_bytes_per_step": hb.numel() * 8,
+                    "d2h_bytes_per_step": hx.numel() * 8},
+            "gpu_launches": sts[-1].launches, "clocks": clocks}
+
+
+def gpu_conv(ctx, args):
+    import numpy as np
+    import torch
+    import eb_inputs as ei
+    import paper_2204_06083_gb300 as eb
+    from paper_2204_06083_gb300 import learned
+    n = 2048
+    h = eb.EB(ei.box_grid(2, n), ei.random_star(999))
+    cp = ((h.classes() & eb.CODE_CP) != 0).float()
+    rng = np.random.default_rng(0)
+    inp = torch.empty((1, n, n, 2), dtype=torch.float32, device=ctx.dev)
+    inp[0, :, :, 0] = torch.from_numpy(rng.standard_normal((n, n)).astype(np.float32)).cuda() * cp
+    inp[0, :, :, 1] = cp
+    out = torch.empty((1, n, n), dtype=torch.float32, device=ctx.dev)
+    net = eb.Net(learned.init_params(8))
+
+    def step():
+        net.forward(inp, out)
+
+    _, ms_per_step, clocks = loop(ctx, args, step, torch.cuda.current_device())
+    px = n * n
+    value = ctx.world * px / (ms_per_step / 1000.0)
+    net.set_profile(True)  # the convolution launches, in as many forwards right after the timed ones
+    for _ in range(args.steps):
+        ctx.flush()
+        net.forward(inp, out)
+    conv_ms, conv_n = net.profile()
+    net.set_profile(False)
+    net.status()
+    hin = inp.cpu().pin_memory()
+    hout = torch.empty_like(out, device="cpu").pin_memory()
+    din = torch.empty_like(inp)
+    e2e = []
+    for i in range(1 + args.steps):
+        ctx.flush()
+        t, _ = timed(lambda: (din.copy_(hin, non_blocking=True), net.forward(din, out),
+                              hout.copy_(out, non_blocking=True)))
+        if i >= 1:
+            e2e.append(t)
+    e2e_value = ctx.world * px / (ctx.max_over_ranks(statistics.mean(e2e)) / 1000.0)
+    pk, kind = peaks()
+    avg_s = (conv_ms / conv_n) / 1000.0 if conv_n else float("nan")
+    achieved = CONV_FLOP_PER_PX * px / avg_s / 1e12 if conv_n else None
+    peak = pk.get("bf16_tflops", pk.get("bf16_tflops_sustained"))
+    hbm_ach = CONV_BYTES_PER_PX * px / avg_s / 1e9 if conv_n else None
+    return {"value": value, "ms_per_step": ms_per_step, "dtype": "bf16 (f32 accumulate)",
             # 144 FLOP per byte moved, below the ridge (peak FLOP/s over peak B/s): HBM is the roof that binds
             "roofline": {"bound": "hbm", "kernel": "k_conv32 (32->32 implicit-GEMM conv, tcgen05.mma, TMEM)",
                          "achieved": hbm_ach, "peak": pk["hbm_gbs"], "peak_kind": kind, "unit": "GB/s",
