@@ -221,6 +221,10 @@ int amg_autotune(amg_handle* amg, int reps, eb_tune_t* out, cudaStream_t stream)
  * (may be NULL) the entries per lane chosen.  Results do not change (the sums
  * are grouped differently: FP rounding only).  Synchronous. */
 int amg_tune_csr(amg_handle* amg, int reps, double* us_out, int* best_out, cudaStream_t stream);
+/* Sets the entries per lane of the CSR kernels' row groups (1, 2, 4 or 8; see
+ * amg_tune_csr) without timing, e.g. to a value a previous tuning found.  The
+ * paper has no counterpart.  EB_ERR_INVALID for other values. */
+int amg_set_csr_epl(amg_handle* amg, int epl);
 /* Times one V-cycle kernel on its own (instrumentation; the paper has no
  * counterpart).  kernel EB_TK_SMOOTH_STEP: one Chebyshev smoothing step of
  * level `level` (level 0: the stencil kernel of Sec. 2 over the active tiles;

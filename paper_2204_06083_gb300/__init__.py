@@ -106,6 +106,7 @@ _SIGS = {
     "amg_autotune": (C.c_int, [_P, C.c_int, C.POINTER(eb_tune_t), _P]),
     "amg_tune_csr": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "amg_time_kernel": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int64, _P, _P]),
+    "amg_set_csr_epl": (C.c_int, [_P, C.c_int]),
     "batch_autotune": (C.c_int, [_P, C.c_int, C.POINTER(eb_tune_t), _P]),
     "amg_setup": (C.c_int, [_P, C.c_double, C.POINTER(amg_opts), C.POINTER(_P), _P]),
     "amg_destroy": (None, [_P]),
@@ -425,6 +426,10 @@ class AMG:
         best = C.c_int()
         _check(load().amg_tune_csr(self._h, int(reps), C.cast(us, C.c_void_p), C.byref(best), _stream(stream)))
         return best.value, {e: us[i] for i, e in enumerate((1, 2, 4, 8))}
+
+    def set_csr_epl(self, epl):
+        """Entries per lane of the CSR row groups (1, 2, 4 or 8), e.g. a cached tuning result."""
+        _check(load().amg_set_csr_epl(self._h, int(epl)))
 
     def time_smoother_step(self, level, launches=50, clear_bytes=0, stream=None):
         """Microseconds per launch of level `level`'s Chebyshev smoothing step

@@ -1,9 +1,10 @@
-"""Tile-shape autotuning with a persistent cache.
+"""Tile-shape and CSR row-group autotuning with a persistent cache.
 
-The library's tuners (eb_autotune, amg_autotune, batch_autotune) time the
-candidate tile shapes on the GPU and keep the fastest.  This module remembers
-the winner per (GPU, operation, problem) in a JSON file so that later runs
-retile directly (eb_retile) instead of timing again.  The cache file is
+The library's tuners (eb_autotune, amg_autotune, batch_autotune,
+amg_tune_csr) time the candidates on the GPU and keep the fastest.  This
+module remembers the winner per (GPU, operation, problem) in a JSON file so
+that later runs apply it directly (eb_retile, amg_set_csr_epl) instead of
+timing again.  The cache file is
 ``$EB_TUNE_CACHE`` if set, else ``~/.cache/paper_2204_06083_gb300/tiles.json``.
 """
 from __future__ import annotations
@@ -86,3 +87,24 @@ def tune_batch(batch: Batch, reps=10, path: Optional[str] = None, retune=False):
     res = batch.autotune(reps)
     _store(path, key, res.shape, res)
     return res.shape, res
+
+
+def tune_csr(amg: AMG, reps=10, path: Optional[str] = None, retune=False):
+    """Entries per lane of the CSR kernels of this hierarchy (amg_tune_csr);
+    returns (entries per lane, {entries per lane: microseconds per V-cycle} or
+    None when taken from the cache)."""
+    path = path or cache_path()
+    key = f"{_device()} | csr vcycle prec={amg.vcycle_prec} | {_grid_key(amg.eb)}"
+    hit = None if retune else _load(path).get(key)
+    if hit:
+        amg.set_csr_epl(hit["epl"])
+        return int(hit["epl"]), None
+    epl, us = amg.tune_csr(reps)
+    d = _load(path)
+    d[key] = {"epl": epl, "us": {str(k): v for k, v in us.items()}}
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+    return epl, us

@@ -198,4 +198,18 @@ int amg_tune_csr(amg_handle* amg, int reps, double* us_out, int* best_out, cudaS
   });
 }
 
+int amg_set_csr_epl(amg_handle* amg, int epl) {
+  if (!amg || (epl != 1 && epl != 2 && epl != 4 && epl != 8)) {
+    set_error("amg_set_csr_epl: NULL handle or entries per lane not 1, 2, 4 or 8");
+    return EB_ERR_INVALID;
+  }
+  return guarded([&] {
+    Solver& S = amg->s;
+    if (S.csr_epl == epl) return;
+    S.csr_epl = epl;
+    S.graph_release();  // captured iterations hold the old launch shapes
+    S.loop_release();
+  });
+}
+
 }  // extern "C"

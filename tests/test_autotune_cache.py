@@ -43,3 +43,31 @@ def test_cache_roundtrip(tmp_path, monkeypatch):
 def test_cache_path_env(monkeypatch, tmp_path):
     monkeypatch.setenv("EB_TUNE_CACHE", str(tmp_path / "x.json"))
     assert autotune.cache_path() == str(tmp_path / "x.json")
+
+
+class FakeAMG:
+    def __init__(self):
+        self.eb = FakeEB()
+        self.vcycle_prec = 1
+        self.tuned = 0
+        self.set_to = []
+
+    def tune_csr(self, reps):
+        self.tuned += 1
+        return 4, {1: 9.0, 2: 7.0, 4: 5.0, 8: 6.0}
+
+    def set_csr_epl(self, epl):
+        self.set_to.append(epl)
+
+
+def test_csr_cache_roundtrip(tmp_path, monkeypatch):
+    monkeypatch.setattr(autotune, "_device", lambda: "FakeGPU")
+    path = str(tmp_path / "tiles.json")
+    amg = FakeAMG()
+    assert autotune.tune_csr(amg, path=path) == (4, {1: 9.0, 2: 7.0, 4: 5.0, 8: 6.0})
+    assert amg.tuned == 1 and amg.set_to == []
+    assert autotune.tune_csr(amg, path=path) == (4, None)
+    assert amg.tuned == 1 and amg.set_to == [4]
+    d = json.load(open(path))
+    (key,) = d.keys()
+    assert key.startswith("FakeGPU | csr vcycle prec=1 | 2D 64x64 cp=777") and d[key]["epl"] == 4

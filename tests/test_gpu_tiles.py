@@ -176,6 +176,15 @@ def test_csr_group_tuning_keeps_results():
     x1, st1 = amg.solve(b, rtol=1e-11)
     assert abs(st1.iterations - st0.iterations) <= 1
     assert torch.linalg.norm(x1 - x0) <= 1e-9 * torch.linalg.norm(x0)
+    # a cached choice is applied without timing; other values are rejected
+    other = 8 if best != 8 else 1
+    amg.set_csr_epl(other)
+    x2, st2 = amg.solve(b, rtol=1e-11)
+    assert abs(st2.iterations - st0.iterations) <= 1
+    assert torch.linalg.norm(x2 - x0) <= 1e-9 * torch.linalg.norm(x0)
+    with pytest.raises(eb.EBError) as e:
+        amg.set_csr_epl(3)
+    assert e.value.code == eb.EB_ERR_INVALID
 
 
 def test_handles_destroyed_in_any_order():
