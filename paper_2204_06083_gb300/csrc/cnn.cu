@@ -17,6 +17,8 @@
 // 2 -> 32 and 32 -> 1 layers run on the CUDA cores.
 #include "eb_solver.cuh"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <mma.h>
 
 #include <algorithm>
@@ -265,6 +267,207 @@ __global__ void __launch_bounds__(128, 4) k_conv32(Image im, const bf16* __restr
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
+}
+
+// ------------------------- 32 -> 32 convolution, TMA-fed warp-specialised pipeline
+// The same implicit GEMM as k_conv32 (identical shared-memory operand layout,
+// descriptors and MMA sequence, so the results are bit-identical), with the
+// staging taken off the critical path: one thread issues, per job, one 5D
+// tensor copy (cp.async.bulk.tensor) of the job's 3 rows x 130 pixels x 32
+// channels straight into the core-matrix layout, into a ring of CP_STAGES
+// buffers; one thread issues the 18 MMAs of each job into one of two TMEM
+// accumulators; four warps drain the accumulators (tcgen05.ld) and run the
+// epilogue while the next jobs load and multiply.  The tensor map views the
+// activations as (8 channels, pixel, row in image, channel group, image), so
+// the copied box lands as [group][row][pixel][8 channels] and the rows outside
+// an image and the pixels outside a row are filled with zeros by the copy.
+// Barriers: full[s] (copy -> MMA, transaction bytes), empty[s] (MMA commit ->
+// copy), tfull[a] (MMA commit -> epilogue), tempty[a] (4 epilogue warps ->
+// MMA).  Every wait is bounded; a wait that gives up raises a shared abort
+// flag that ends every role's loop, sets *err, and the CTA waits (bounded) for
+// its copies and MMAs in flight before freeing TMEM.
+constexpr int CP_STAGES = 3;
+constexpr int CP_STAGE = 25600;                        // TC_A rounded up to 1 KB
+constexpr int CP_W = CP_STAGES * CP_STAGE;             // weights after the stages
+constexpr int CP_BAR = CP_W + TC_W;                    // barriers after the weights
+constexpr int CP_NBAR = 2 * CP_STAGES + 4;
+constexpr int CP_SMEM = CP_BAR + 8 * CP_NBAR + 16;     // + TMEM slot and abort flag
+constexpr int CP_THREADS = 192;                        // warps 0-3 epilogue, 4 copies, 5 MMAs
+constexpr uint32_t CP_BOX_BYTES = 3 * TC_PIX * NC * 2;  // 24,960
+static_assert(CP_BOX_BYTES == TC_A, "box = staged operand");
+
+__device__ __forceinline__ bool cp_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+  for (uint32_t it = 0; it < TC_SPIN; ++it) {
+    uint32_t ok = 0;
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 63) == 63 && *abort) return false;
+  }
+  *abort = 1;
+  return false;
+}
+
+__global__ void __launch_bounds__(CP_THREADS, 2) k_conv32_tma(const __grid_constant__ CUtensorMap xmap, Image im,
+                                                               const bf16* __restrict__ wk,
+                                                               const float* __restrict__ bias, bf16* __restrict__ y,
+                                                               int relu, const bf16* __restrict__ mask_ref,
+                                                               int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* sW = smem_raw + CP_W;
+  const uint32_t base = smem_addr(smem_raw);
+  const uint32_t a0 = base, w0 = base + CP_W, bars = base + CP_BAR;
+  auto full = [&](int st) { return bars + 8 * st; };
+  auto empty = [&](int st) { return bars + 8 * (CP_STAGES + st); };
+  auto tfull = [&](int a) { return bars + 8 * (2 * CP_STAGES + a); };
+  auto tempty = [&](int a) { return bars + 8 * (2 * CP_STAGES + 2 + a); };
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem_raw + CP_BAR + 8 * CP_NBAR);
+  volatile int* abort = reinterpret_cast<volatile int*>(smem_raw + CP_BAR + 8 * CP_NBAR + 8);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int i = tid; i < 9 * NC * 4; i += CP_THREADS) {  // weights once per CTA
+    const int g = i & 3, n = (i >> 2) % NC, d = (i >> 2) / NC;
+    *reinterpret_cast<int4*>(sW + d * TC_WTAP + g * (NC * 16) + n * 16) =
+        *reinterpret_cast<const int4*>(wk + (d * NC + n) * NC + g * 8);
+  }
+  if (tid == 0) {
+    for (int b = 0; b < CP_NBAR; ++b) {
+      const uint32_t cnt = (b >= 2 * CP_STAGES + 2) ? 4u : 1u;  // tempty: one arrive per epilogue warp
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bars + 8 * b), "r"(cnt));
+    }
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 5) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_addr(tslot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;");  // weights (generic stores) are read by the tensor cores
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tslot;
+  const int segs = (im.W + TPX - 1) / TPX;
+  const int64_t jobs = (int64_t)segs * im.H;
+  const int64_t njob = jobs > (int64_t)blockIdx.x ? (jobs - 1 - blockIdx.x) / gridDim.x + 1 : 0;  // this CTA's jobs
+  if (warp == 4) {
+    // copies: stage s = k mod S, its u-th use waits for the MMAs of use u - 1
+    if (lane == 0) {
+      const uint64_t map = reinterpret_cast<uint64_t>(&xmap);
+      asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
+      int64_t k = 0;
+      for (; k < njob; ++k) {
+        const int st = (int)(k % CP_STAGES);
+        const uint32_t u = (uint32_t)(k / CP_STAGES);
+        if (u > 0 && !cp_wait(empty(st), (u - 1) & 1u, abort)) break;
+        const int64_t job = blockIdx.x + k * gridDim.x;
+        const int r = (int)(job / segs), x0 = (int)(job % segs) * TPX;
+        const int img = r / im.R, rin = r - img * im.R;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full(st)), "r"(CP_BOX_BYTES)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+            "%5, %6}], [%7];" ::"r"(a0 + st * CP_STAGE),
+            "l"(map), "r"(0), "r"(x0 - 1), "r"(rin - 1), "r"(0), "r"(img), "r"(full(st))
+            : "memory");
+      }
+      // copies still in flight (an aborted run) land before the CTA ends
+      for (int64_t q = k > CP_STAGES ? k - CP_STAGES : 0; q < k; ++q) {
+        volatile int never = 0;
+        cp_wait(full((int)(q % CP_STAGES)), (uint32_t)(q / CP_STAGES) & 1u, &never);
+      }
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc_idesc(128, NC);
+      int64_t k = 0;
+      for (; k < njob; ++k) {
+        const int st = (int)(k % CP_STAGES);
+        const int a = (int)(k & 1);
+        if (!cp_wait(full(st), (uint32_t)(k / CP_STAGES) & 1u, abort)) break;
+        if (k >= 2 && !cp_wait(tempty(a), (uint32_t)((k >> 1) - 1) & 1u, abort)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t sa = a0 + st * CP_STAGE;
+#pragma unroll 1
+        for (int q = 0; q < 18; ++q) {
+          const int d = q >> 1, kh = q & 1, dy = d / 3, dx = d % 3;
+          const uint64_t da = tc_desc(sa + (2 * kh) * TC_GROUP + (dy * TC_PIX + dx) * 16, TC_GROUP, 128);
+          const uint64_t db = tc_desc(w0 + d * TC_WTAP + (2 * kh) * (NC * 16), NC * 16, 128);
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem + (uint32_t)(a * NC)),
+              "l"(da), "l"(db), "r"(idesc), "r"((uint32_t)(q > 0)));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty(st))
+                     : "memory");
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tfull(a))
+                     : "memory");
+      }
+      if (k > 0) {  // the last MMAs complete before TMEM is freed
+        volatile int never = 0;
+        cp_wait(tfull((int)((k - 1) & 1)), (uint32_t)(((k - 1) >> 1) & 1), &never);
+      }
+    }
+  } else {
+    // epilogue: warp w drains TMEM lanes 32 w .. 32 w + 31 (pixels x0 + 32 w + lane)
+    float bv[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) bv[c] = bias ? bias[c] : 0.0f;
+    for (int64_t k = 0; k < njob; ++k) {
+      const int a = (int)(k & 1);
+      // the warp leaves together or not at all (tcgen05.ld is warp-collective)
+      const bool okl = cp_wait(tfull(a), (uint32_t)(k >> 1) & 1u, abort);
+      if (!__all_sync(0xffffffffu, okl)) {
+        *abort = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      uint32_t v[NC];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+          "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+            "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+          : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * NC)));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tempty(a)) : "memory");
+      const int64_t job = blockIdx.x + k * gridDim.x;
+      const int r = (int)(job / segs), x0 = (int)(job % segs) * TPX;
+      const int gx = x0 + warp * 32 + lane;
+      if (gx < im.W) {
+        const int64_t p = (int64_t)r * im.W + gx;
+        __align__(16) bf16 ov[NC];
+        __align__(16) bf16 mr[NC];
+        if (mask_ref) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            reinterpret_cast<int4*>(mr)[q] = reinterpret_cast<const int4*>(mask_ref + p * NC)[q];
+        }
+#pragma unroll
+        for (int co = 0; co < NC; ++co) {
+          float f = __uint_as_float(v[co]) + bv[co];
+          if (relu) f = fmaxf(f, 0.0f);
+          if (mask_ref && !(__bfloat162float(mr[co]) > 0.0f)) f = 0.0f;
+          ov[co] = __float2bfloat16_rn(f);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) reinterpret_cast<int4*>(y + p * NC)[q] = reinterpret_cast<const int4*>(ov)[q];
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (tid == 0 && *abort) atomicExch(err, 1);
+  if (warp == 5) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
+  }
 }
 
 // layer 6 (32 -> 1); out = m * (conv + b6)
@@ -851,8 +1054,51 @@ static void set_attrs() {
   static bool done = false;
   if (done) return;
   EB_CUDA(cudaFuncSetAttribute(k_conv32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem()));
+  EB_CUDA(cudaFuncSetAttribute(k_conv32_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CP_SMEM));
   EB_CUDA(cudaFuncSetAttribute(k_conv32_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wgrad_smem()));
   done = true;
+}
+
+// Tensor map of a BF16 NHWC activation stack for k_conv32_tma: dimensions
+// (8 channels, pixel, row in image, channel group, image), strides 64 B,
+// W * 64 B, 16 B, R * W * 64 B; box (8, 130, 3, 4, 1); out-of-range elements
+// read as zero.  The encode entry point comes from the driver through the
+// runtime (no link to libcuda).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    EB_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    EB_REQUIRE(q == cudaDriverEntryPointSuccess && p, EB_ERR_CUDA, "cuTensorMapEncodeTiled not available");
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+static CUtensorMap conv_map(const bf16* x, const Image& im) {
+  EB_REQUIRE(((uintptr_t)x & 15) == 0, EB_ERR_INVALID, "conv: activations not 16-byte aligned");
+  EB_REQUIRE(im.R > 0 && im.H % im.R == 0, EB_ERR_INVALID, "conv: rows are not whole images");
+  CUtensorMap m;
+  const cuuint64_t dims[5] = {8, (cuuint64_t)im.W, (cuuint64_t)im.R, 4, (cuuint64_t)(im.H / im.R)};
+  const cuuint64_t strides[4] = {64, (cuuint64_t)im.W * 64, 16, (cuuint64_t)im.R * im.W * 64};
+  const cuuint32_t box[5] = {8, (cuuint32_t)TC_PIX, 3, 4, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  const CUresult r = tensor_map_encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16*>(x), dims,
+                                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  EB_REQUIRE(r == CUDA_SUCCESS, EB_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return m;
+}
+
+// y = conv(x; wk) (+ bias, ReLU, mask as in k_conv32) through the pipelined kernel
+static void conv32(const Image& im, const bf16* x, const bf16* wk, const float* bias, bf16* y, int relu,
+                   const bf16* mask_ref, int* err, cudaStream_t s) {
+  const CUtensorMap m = conv_map(x, im);
+  const int64_t jobs = (int64_t)((im.W + TPX - 1) / TPX) * im.H;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(jobs, (int64_t)num_sms() * 2));
+  k_conv32_tma<<<grid, CP_THREADS, CP_SMEM, s>>>(m, im, wk, bias, y, relu, mask_ref, err);
 }
 
 static void ensure_act(NN& N, int64_t px, cudaStream_t s) {
@@ -912,8 +1158,7 @@ static void forward(NN& N, const Image& im, const float2* in, float* out, cudaSt
       EB_CUDA(cudaEventRecord(N.prof_ev[N.prof_n].first, s));
     }
     if (prof) prof->prof_mark(s, true, PROF_CONV);
-    k_conv32<<<conv_grid(im, 4), 128, conv_smem(), s>>>(im, N.act[l + 1], N.wf + (int64_t)l * WM_N,
-                                                         N.P + off_wm(l) + WM_N, N.act[l + 2], 1, nullptr, N.err);
+    conv32(im, N.act[l + 1], N.wf + (int64_t)l * WM_N, N.P + off_wm(l) + WM_N, N.act[l + 2], 1, nullptr, N.err, s);
     if (prof) prof->prof_mark(s, false, PROF_CONV);
     if (own) EB_CUDA(cudaEventRecord(N.prof_ev[N.prof_n++].second, s));
   }
@@ -944,8 +1189,7 @@ static void backward(NN& N, const Image& im, const float2* in, const float* dout
     k_sum_wgrad<<<blocks_for(WM_N, 256), 256, 0, s>>>(part, (int)gw, N.G + off_wm(l));
     k_bias_grad<<<nbb, 256, 0, s>>>(npx, cur, part);
     k_sum_parts<<<1, 32, 0, s>>>(part, nbb, NC, N.G + off_wm(l) + WM_N);
-    k_conv32<<<conv_grid(im, 4), 128, conv_smem(), s>>>(im, cur, N.wb + (int64_t)l * WM_N, nullptr, nxt, 0,
-                                                         N.act[l + 1], N.err);
+    conv32(im, cur, N.wb + (int64_t)l * WM_N, nullptr, nxt, 0, N.act[l + 1], N.err, s);
     std::swap(cur, nxt);
     nl += 5;
   }
