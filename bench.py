@@ -880,9 +880,9 @@ def gpu_learned(ctx, args):
             "training": {"pairs": npairs, "pair_generation_s": pairs_s, "train_s": train_s, "adam_steps": npairs // batch,
                          "batch": batch, "loss_log": log},
             # the stage's 32 -> 32 convolutions: 144 FLOP per byte, below the ridge, so the HBM roof binds
-            "roofline": {"bound": "hbm", "kernel": "k_conv32 (32->32 implicit-GEMM conv, tcgen05.mma, TMEM)",
+            "roofline": {"bound": "hbm", "kernel": "k_conv32_tma (32->32 implicit-GEMM conv: TMA-fed tcgen05 pipeline, TMEM)",
                          "achieved": hbm_ach, "peak": pk["hbm_gbs"], "peak_kind": kind, "unit": "GB/s",
-                         "frac": (hbm_ach / pk["hbm_gbs"]) if hbm_ach else None, "traffic": recorded_traffic("k_conv32"),
+                         "frac": (hbm_ach / pk["hbm_gbs"]) if hbm_ach else None, "traffic": recorded_traffic("k_conv32_tma"),
                          "algorithmic_bytes_per_launch": CONV_BYTES_PER_PX * px, "avg_launch_us": avg_s * 1e6,
                          "launches_timed": prof_n, "timing": PROF_NOTE,
                          "tensor": {"achieved": achieved, "peak": peak, "peak_kind": kind + " bf16 sustained",
@@ -940,10 +940,10 @@ def gpu_conv(ctx, args):
     hbm_ach = CONV_BYTES_PER_PX * px / avg_s / 1e9 if conv_n else None
     return {"value": value, "ms_per_step": ms_per_step, "dtype": "bf16 (f32 accumulate)",
             # 144 FLOP per byte moved, below the ridge (peak FLOP/s over peak B/s): HBM is the roof that binds
-            "roofline": {"bound": "hbm", "kernel": "k_conv32 (32->32 implicit-GEMM conv, tcgen05.mma, TMEM)",
+            "roofline": {"bound": "hbm", "kernel": "k_conv32_tma (32->32 implicit-GEMM conv: TMA-fed tcgen05 pipeline, TMEM)",
                          "achieved": hbm_ach, "peak": pk["hbm_gbs"], "peak_kind": kind, "unit": "GB/s",
                          "frac": (hbm_ach / pk["hbm_gbs"]) if hbm_ach else None,
-                         "traffic": recorded_traffic("k_conv32"),
+                         "traffic": recorded_traffic("k_conv32_tma"),
                          "algorithmic_bytes_per_launch": CONV_BYTES_PER_PX * px, "avg_launch_us": avg_s * 1e6,
                          "launches_timed": conv_n,
                          "tensor": {"achieved": achieved, "peak": peak, "peak_kind": kind + " bf16 burst",
