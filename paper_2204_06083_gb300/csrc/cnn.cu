@@ -130,6 +130,16 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
 
+// shared-memory matrix descriptor of a K-major operand in the 64-byte swizzled
+// layout: rows of 64 bytes (32 bf16 along K), the 16-byte chunks of a row
+// permuted by the address bits 7-8 as the tensor copies write them, 8-row
+// groups 512 bytes apart (SBO); LBO unused (the K extent of one MMA, 32 bytes,
+// lies inside a row); swizzle mode 4 (64 bytes) in bits 61-63
+__device__ __forceinline__ uint64_t tc_desc_sw64(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+
 // instruction descriptor of kind::f16: D f32, A and B bf16, both K-major, N, M
 __device__ __forceinline__ constexpr uint32_t tc_idesc(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
@@ -368,9 +378,9 @@ __global__ void __launch_bounds__(CP_THREADS, 2) k_conv32_tma(const __grid_const
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full(st)), "r"(CP_BOX_BYTES)
                      : "memory");
         asm volatile(
-            "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
-            "%5, %6}], [%7];" ::"r"(a0 + st * CP_STAGE),
-            "l"(map), "r"(0), "r"(x0 - 1), "r"(rin - 1), "r"(0), "r"(img), "r"(full(st))
+            "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+            "%5}], [%6];" ::"r"(a0 + st * CP_STAGE),
+            "l"(map), "r"(0), "r"(x0 - 1), "r"(rin - 1), "r"(img), "r"(full(st))
             : "memory");
       }
       // copies still in flight (an aborted run) land before the CTA ends
@@ -393,7 +403,7 @@ __global__ void __launch_bounds__(CP_THREADS, 2) k_conv32_tma(const __grid_const
 #pragma unroll 1
         for (int q = 0; q < 18; ++q) {
           const int d = q >> 1, kh = q & 1, dy = d / 3, dx = d % 3;
-          const uint64_t da = tc_desc(sa + (2 * kh) * TC_GROUP + (dy * TC_PIX + dx) * 16, TC_GROUP, 128);
+          const uint64_t da = tc_desc_sw64(sa + (dy * TC_PIX + dx) * 64 + kh * 32);
           const uint64_t db = tc_desc(w0 + d * TC_WTAP + (2 * kh) * (NC * 16), NC * 16, 128);
           asm volatile(
               "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -1080,13 +1090,13 @@ static CUtensorMap conv_map(const bf16* x, const Image& im) {
   EB_REQUIRE(((uintptr_t)x & 15) == 0, EB_ERR_INVALID, "conv: activations not 16-byte aligned");
   EB_REQUIRE(im.R > 0 && im.H % im.R == 0, EB_ERR_INVALID, "conv: rows are not whole images");
   CUtensorMap m;
-  const cuuint64_t dims[5] = {8, (cuuint64_t)im.W, (cuuint64_t)im.R, 4, (cuuint64_t)(im.H / im.R)};
-  const cuuint64_t strides[4] = {64, (cuuint64_t)im.W * 64, 16, (cuuint64_t)im.R * im.W * 64};
-  const cuuint32_t box[5] = {8, (cuuint32_t)TC_PIX, 3, 4, 1};
-  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-  const CUresult r = tensor_map_encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16*>(x), dims,
+  const cuuint64_t dims[4] = {(cuuint64_t)NC, (cuuint64_t)im.W, (cuuint64_t)im.R, (cuuint64_t)(im.H / im.R)};
+  const cuuint64_t strides[3] = {(cuuint64_t)NC * 2, (cuuint64_t)im.W * NC * 2, (cuuint64_t)im.R * im.W * NC * 2};
+  const cuuint32_t box[4] = {(cuuint32_t)NC, (cuuint32_t)TC_PIX, 3, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = tensor_map_encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(x), dims,
                                           strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                          CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   EB_REQUIRE(r == CUDA_SUCCESS, EB_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
   return m;
