@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(128, 4) k_conv32(Image im, const bf16* __restr
 // MMA).  Every wait is bounded; a wait that gives up raises a shared abort
 // flag that ends every role's loop, sets *err, and the CTA waits (bounded) for
 // its copies and MMAs in flight before freeing TMEM.
-constexpr int CP_STAGES = 3;
+constexpr int CP_STAGES = 2;
 constexpr int CP_STAGE = 25600;                        // TC_A rounded up to 1 KB
 constexpr int CP_W = CP_STAGES * CP_STAGE;             // weights after the stages
 constexpr int CP_BAR = CP_W + TC_W;                    // barriers after the weights
@@ -321,7 +321,7 @@ __device__ __forceinline__ bool cp_wait(uint32_t bar, uint32_t parity, volatile 
   return false;
 }
 
-__global__ void __launch_bounds__(CP_THREADS, 2) k_conv32_tma(const __grid_constant__ CUtensorMap xmap, Image im,
+__global__ void __launch_bounds__(CP_THREADS, 3) k_conv32_tma(const __grid_constant__ CUtensorMap xmap, Image im,
                                                                const bf16* __restrict__ wk,
                                                                const float* __restrict__ bias, bf16* __restrict__ y,
                                                                int relu, const bf16* __restrict__ mask_ref,
@@ -1107,7 +1107,7 @@ static void conv32(const Image& im, const bf16* x, const bf16* wk, const float* 
                    const bf16* mask_ref, int* err, cudaStream_t s) {
   const CUtensorMap m = conv_map(x, im);
   const int64_t jobs = (int64_t)((im.W + TPX - 1) / TPX) * im.H;
-  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(jobs, (int64_t)num_sms() * 2));
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(jobs, (int64_t)num_sms() * 3));
   k_conv32_tma<<<grid, CP_THREADS, CP_SMEM, s>>>(m, im, wk, bias, y, relu, mask_ref, err);
 }
 
