@@ -7,10 +7,11 @@
 // Storage: hidden activations BF16 NHWC (32 channels = 64 bytes per pixel);
 // FP32 master parameters, BF16 copies of the 32 -> 32 weights; every sum in
 // FP32.  The four 32 -> 32 layers (99.6 % of the FLOPs) are implicit GEMMs on
-// the 5th-generation tensor cores (tcgen05.mma, accumulators in tensor memory):
-// a CTA owns 128 pixels of one image row and all 32 output channels; the three
-// input rows it needs (130 pixels x 32 channels) and the 9 x 32 x 32 weights
-// sit in shared memory; K = 9 taps x 32 channels.  Data gradients run through
+// the 5th-generation tensor cores (tcgen05.mma, accumulators in tensor memory),
+// fed by tensor copies (TMA) in a warp-specialised pipeline: a job is 128
+// pixels of one image row and all 32 output channels; its three input rows
+// (130 pixels x 32 channels) and the 9 x 32 x 32 weights sit in shared memory;
+// K = 9 taps x 32 channels.  Data gradients run through
 // the same kernel with flipped, transposed weights and the ReLU mask of the
 // layer input applied in its epilogue; weight gradients are GEMMs over pixels
 // (mma.sync fragments) with per-CTA partials summed in a fixed order.  The
@@ -99,27 +100,16 @@ __device__ __forceinline__ void stage_rows(const Image& im, const bf16* __restri
 }
 
 // ------------------------------------------- 32 -> 32 convolution (tcgen05)
-// Implicit GEMM on the 5th-generation tensor cores: a CTA owns a job of 128
-// pixels of one image row (M = 128) and all 32 output channels (N = 32); K = 9
-// taps x 32 input channels = 18 MMAs of 128 x 32 x 16 (bf16 in, f32 in TMEM).
-// Shared-memory operands use the no-swizzle K-major layout of "core matrices"
-// (8 rows x 16 bytes stored contiguously):
-//   A: the three input rows of the job, [channel group g (8 ch)][row][pixel][8 ch];
-//      for tap (dy, dx) and channel half kh the operand starts at group 2 kh,
-//      row dy, pixel dx: consecutive pixels are the M rows (SBO = 128 B), the
-//      next channel group the next K core matrix (LBO = one group plane);
-//   B: the weights, [tap][channel group g][n][8 k] (SBO = 128 B between 8-row
-//      blocks of n, LBO = 32 x 16 B between channel groups).
-// One thread issues the MMAs and commits them to an mbarrier; the four warps
-// wait (bounded), read their 32 TMEM lanes (= their 32 pixels) and run the
-// epilogue.  A wait that gives up sets *err and ends the CTA's loop.
-constexpr int TC_PIX = TPX + 2;
-constexpr int TC_GROUP = 3 * TC_PIX * 16;        // one channel group of the three rows (bytes)
-constexpr int TC_A = 4 * TC_GROUP;               // 24,960
+// Implicit GEMM on the 5th-generation tensor cores (kernel k_conv32_tma below).
+// The B operand, the weights, sits in shared memory in the no-swizzle K-major
+// layout of "core matrices" (8 rows x 16 bytes stored contiguously):
+// [tap][channel group g][n][8 k] (SBO = 128 B between 8-row blocks of n,
+// LBO = 32 x 16 B between channel groups).  The A operand (activations) uses the
+// 64-byte swizzled layout written by the tensor copies (tc_desc_sw64).
+constexpr int TC_PIX = TPX + 2;                  // pixels of a job's rows with their two halo pixels
+constexpr int TC_A = 3 * TC_PIX * NC * 2;        // a job's three rows: 24,960 bytes
 constexpr int TC_WTAP = 4 * NC * 16;             // 2048 per tap
 constexpr int TC_W = 9 * TC_WTAP;                // 18,432
-constexpr int TC_BAR = TC_A + TC_W;              // mbarrier (8 bytes), TMEM address slot after it
-constexpr int TC_SMEM = TC_BAR + 16;
 constexpr uint32_t TC_SPIN = 1u << 22;           // bounded mbarrier polls (~0.1 s)
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -145,159 +135,29 @@ __device__ __forceinline__ constexpr uint32_t tc_idesc(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok = 0;
-  for (uint32_t it = 0; it < TC_SPIN && !ok; ++it)
-    asm volatile(
-        "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-  return ok != 0;
-}
-
-// y = conv(x; wk) + bias (if bias), then ReLU (if relu), then 0 where mask_ref <= 0
-// (if mask_ref: the ReLU derivative of a data gradient).  wk: bf16 [9][32 (n)][32 (k)].
-__global__ void __launch_bounds__(128, 4) k_conv32(Image im, const bf16* __restrict__ x, const bf16* __restrict__ wk,
-                                                const float* __restrict__ bias, bf16* __restrict__ y, int relu,
-                                                const bf16* __restrict__ mask_ref, int* __restrict__ err) {
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char* sA = smem_raw;
-  unsigned char* sW = smem_raw + TC_A;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + TC_BAR);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem_raw + TC_BAR + 8);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const uint32_t a0 = smem_addr(sA), w0 = smem_addr(sW), bar_a = smem_addr(bar);
-  for (int i = tid; i < 9 * NC * 4; i += blockDim.x) {  // weights once per CTA
-    const int g = i & 3, n = (i >> 2) % NC, d = (i >> 2) / NC;
-    *reinterpret_cast<int4*>(sW + d * TC_WTAP + g * (NC * 16) + n * 16) =
-        *reinterpret_cast<const int4*>(wk + (d * NC + n) * NC + g * 8);
-  }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a));
-    asm volatile("fence.mbarrier_init.release.cluster;");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_addr(tslot)));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tmem = *tslot;
-  float bv[NC];
-#pragma unroll
-  for (int c = 0; c < NC; ++c) bv[c] = bias ? bias[c] : 0.0f;
-  const int segs = (im.W + TPX - 1) / TPX;
-  const int64_t jobs = (int64_t)segs * im.H;
-  uint32_t phase = 0;
-  for (int64_t job = blockIdx.x; job < jobs; job += gridDim.x, phase ^= 1u) {
-    const int r = (int)(job / segs), x0 = (int)(job % segs) * TPX;
-    const int lo = (r / im.R) * im.R, hi = lo + im.R;
-    // stage the three rows: 4 loads in flight per thread before their stores
-    for (int i0 = 0; i0 < 3 * TC_PIX * 4; i0 += 4 * 128) {
-      int4 v[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int i = i0 + tid + 128 * u;
-        const int g = i & 3, px = (i >> 2) % TC_PIX, rr = (i >> 2) / TC_PIX;
-        const int gx = x0 - 1 + px, gr = r - 1 + rr;
-        v[u] = make_int4(0, 0, 0, 0);
-        if (i < 3 * TC_PIX * 4 && gx >= 0 && gx < im.W && gr >= lo && gr < hi)
-          v[u] = *reinterpret_cast<const int4*>(x + ((int64_t)gr * im.W + gx) * NC + g * 8);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int i = i0 + tid + 128 * u;
-        if (i < 3 * TC_PIX * 4) {
-          const int g = i & 3, px = (i >> 2) % TC_PIX, rr = (i >> 2) / TC_PIX;
-          *reinterpret_cast<int4*>(sA + g * TC_GROUP + (rr * TC_PIX + px) * 16) = v[u];
-        }
-      }
-    }
-    asm volatile("fence.proxy.async.shared::cta;");  // the tensor cores read what the threads wrote
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (tid == 0) {
-      constexpr uint32_t idesc = tc_idesc(128, NC);
-#pragma unroll 1
-      for (int k = 0; k < 18; ++k) {
-        const int d = k >> 1, kh = k & 1, dy = d / 3, dx = d % 3;
-        const uint64_t da = tc_desc(a0 + (2 * kh) * TC_GROUP + (dy * TC_PIX + dx) * 16, TC_GROUP, 128);
-        const uint64_t db = tc_desc(w0 + d * TC_WTAP + (2 * kh) * (NC * 16), NC * 16, 128);
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
-            "l"(da), "l"(db), "r"(idesc), "r"((uint32_t)(k > 0)));
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_a)
-                   : "memory");
-    }
-    // the CTA decides together, so that every thread leaves the loop or none
-    if (!__syncthreads_and(tc_wait(bar_a, phase) ? 1 : 0)) {
-      if (tid == 0) atomicExch(err, 1);
-      break;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    uint32_t v[NC];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
-        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
-          "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(tmem + ((uint32_t)(warp * 32) << 16)));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    const int gx = x0 + tid;  // TMEM lane tid = pixel x0 + tid
-    if (gx < im.W) {
-      const int64_t p = (int64_t)r * im.W + gx;
-      __align__(16) bf16 ov[NC];
-      __align__(16) bf16 mr[NC];
-      if (mask_ref) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          reinterpret_cast<int4*>(mr)[q] = reinterpret_cast<const int4*>(mask_ref + p * NC)[q];
-      }
-#pragma unroll
-      for (int co = 0; co < NC; ++co) {
-        float f = __uint_as_float(v[co]) + bv[co];
-        if (relu) f = fmaxf(f, 0.0f);
-        if (mask_ref && !(__bfloat162float(mr[co]) > 0.0f)) f = 0.0f;
-        ov[co] = __float2bfloat16_rn(f);
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) reinterpret_cast<int4*>(y + p * NC)[q] = reinterpret_cast<const int4*>(ov)[q];
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();  // staging buffer and accumulator are free for the next job
-    asm volatile("tcgen05.fence::after_thread_sync;");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
-}
-
 // ------------------------- 32 -> 32 convolution, TMA-fed warp-specialised pipeline
-// The same implicit GEMM as k_conv32 (identical shared-memory operand layout,
-// descriptors and MMA sequence, so the results are bit-identical), with the
-// staging taken off the critical path: one thread issues, per job, one 5D
+// y = conv(x; wk) + bias (if bias), then ReLU (if relu), then 0 where
+// mask_ref <= 0 (if mask_ref: the ReLU derivative of a data gradient).
+// wk: bf16 [9][32 (n)][32 (k)].  A job is 128 pixels of one image row and all
+// 32 output channels: M = 128, N = 32, K = 9 taps x 32 channels = 18 MMAs of
+// 128 x 32 x 16 (bf16 in, f32 in TMEM).  One thread issues, per job, one 4D
 // tensor copy (cp.async.bulk.tensor) of the job's 3 rows x 130 pixels x 32
-// channels straight into the core-matrix layout, into a ring of CP_STAGES
-// buffers; one thread issues the 18 MMAs of each job into one of two TMEM
-// accumulators; four warps drain the accumulators (tcgen05.ld) and run the
-// epilogue while the next jobs load and multiply.  The tensor map views the
-// activations as (8 channels, pixel, row in image, channel group, image), so
-// the copied box lands as [group][row][pixel][8 channels] and the rows outside
-// an image and the pixels outside a row are filled with zeros by the copy.
+// channels into a ring of CP_STAGES buffers, in the 64-byte swizzled K-major
+// layout (a pixel's 32 channels are one 64-byte row); the operand of tap
+// (dy, dx) and channel half kh starts at row dy * 130 + dx, byte 32 kh.  One
+// thread issues the 18 MMAs of each job into one of two TMEM accumulators;
+// four warps drain the accumulators (tcgen05.ld: warp w reads TMEM lanes
+// 32 w .. 32 w + 31, its 32 pixels) and run the epilogue while the next jobs
+// load and multiply.  The tensor map views the activations as (32 channels,
+// pixel, row in image, image), so the rows outside an image and the pixels
+// outside a row are filled with zeros by the copy.
 // Barriers: full[s] (copy -> MMA, transaction bytes), empty[s] (MMA commit ->
 // copy), tfull[a] (MMA commit -> epilogue), tempty[a] (4 epilogue warps ->
 // MMA).  Every wait is bounded; a wait that gives up raises a shared abort
 // flag that ends every role's loop, sets *err, and the CTA waits (bounded) for
 // its copies and MMAs in flight before freeing TMEM.
 constexpr int CP_STAGES = 2;
-constexpr int CP_STAGE = 25600;                        // TC_A rounded up to 1 KB
+constexpr int CP_STAGE = 25600;                        // TC_A rounded up to 1 KB (swizzle atoms stay aligned)
 constexpr int CP_W = CP_STAGES * CP_STAGE;             // weights after the stages
 constexpr int CP_BAR = CP_W + TC_W;                    // barriers after the weights
 constexpr int CP_NBAR = 2 * CP_STAGES + 4;
@@ -732,7 +592,7 @@ __global__ void k_sum_wgrad(const float* __restrict__ part, int nparts, float* _
 }
 
 // ------------------------------------------------------------- weights
-// B operands of k_conv32, [tap][n][k]:
+// B operands of k_conv32_tma, [tap][n][k]:
 // forward: wf[l][d][n = co][k = ci] = W_l[co][d][ci]
 // data gradient: wb[l][8 - d][n = ci][k = co] = W_l[co][d][ci]
 __global__ void k_pack_weights(const float* __restrict__ P, bf16* __restrict__ wf, bf16* __restrict__ wb) {
@@ -1057,23 +917,21 @@ struct NN {
   int snblk = 0;
 };
 
-static size_t conv_smem() { return (size_t)TC_SMEM; }
 static size_t wgrad_smem() { return (size_t)(3 * (TPX + 2) * LDA + TPX * LDA) * sizeof(bf16); }
 
 static void set_attrs() {
   static bool done = false;
   if (done) return;
-  EB_CUDA(cudaFuncSetAttribute(k_conv32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem()));
   EB_CUDA(cudaFuncSetAttribute(k_conv32_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CP_SMEM));
   EB_CUDA(cudaFuncSetAttribute(k_conv32_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wgrad_smem()));
   done = true;
 }
 
 // Tensor map of a BF16 NHWC activation stack for k_conv32_tma: dimensions
-// (8 channels, pixel, row in image, channel group, image), strides 64 B,
-// W * 64 B, 16 B, R * W * 64 B; box (8, 130, 3, 4, 1); out-of-range elements
-// read as zero.  The encode entry point comes from the driver through the
-// runtime (no link to libcuda).
+// (32 channels, pixel, row in image, image), strides 64 B, W * 64 B,
+// R * W * 64 B; box (32, 130, 3, 1) written in the 64-byte swizzled layout;
+// out-of-range elements read as zero.  The encode entry point comes from the
+// driver through the runtime (no link to libcuda).
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -1102,7 +960,7 @@ static CUtensorMap conv_map(const bf16* x, const Image& im) {
   return m;
 }
 
-// y = conv(x; wk) (+ bias, ReLU, mask as in k_conv32) through the pipelined kernel
+// y = conv(x; wk) (+ bias, ReLU, mask) through k_conv32_tma
 static void conv32(const Image& im, const bf16* x, const bf16* wk, const float* bias, bf16* y, int relu,
                    const bf16* mask_ref, int* err, cudaStream_t s) {
   const CUtensorMap m = conv_map(x, im);
