@@ -390,8 +390,11 @@ void Solver::precondition(int kind, const double* rin, double* zout, cudaStream_
     dot.r = rin;
     dot.zold = flexible() ? zold : nullptr;
     dot.part = part_rz();
-    rz_n = amg_vcycle_grid(*this, rin, zout, s, &dot);
-    if (rz_n) return;
+    const int fused = amg_vcycle_grid(*this, rin, zout, s, &dot);
+    if (fused) {
+      rz_n = fused;
+      return;
+    }  // single-level hierarchy: no smoothing launch formed them
     if (flexible())
       EB_DIM_LAUNCH(dim, k_dot2, nblk, tv, rin, zout, zold, part_rz());
     else
