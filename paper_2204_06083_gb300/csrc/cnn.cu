@@ -17,9 +17,8 @@
 // (mma.sync fragments) with per-CTA partials summed in a fixed order.  The
 // 2 -> 32 and 32 -> 1 layers run on the CUDA cores.
 #include "eb_solver.cuh"
+#include "tma.cuh"
 
-#include <cuda.h>
-#include <cudaTypedefs.h>
 #include <mma.h>
 
 #include <algorithm>
@@ -930,20 +929,7 @@ static void set_attrs() {
 // Tensor map of a BF16 NHWC activation stack for k_conv32_tma: dimensions
 // (32 channels, pixel, row in image, image), strides 64 B, W * 64 B,
 // R * W * 64 B; box (32, 130, 3, 1) written in the 64-byte swizzled layout;
-// out-of-range elements read as zero.  The encode entry point comes from the
-// driver through the runtime (no link to libcuda).
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    EB_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
-    EB_REQUIRE(q == cudaDriverEntryPointSuccess && p, EB_ERR_CUDA, "cuTensorMapEncodeTiled not available");
-    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
+// out-of-range elements read as zero.
 static CUtensorMap conv_map(const bf16* x, const Image& im) {
   EB_REQUIRE(((uintptr_t)x & 15) == 0, EB_ERR_INVALID, "conv: activations not 16-byte aligned");
   EB_REQUIRE(im.R > 0 && im.H % im.R == 0, EB_ERR_INVALID, "conv: rows are not whole images");
