@@ -224,10 +224,33 @@ __device__ __forceinline__ typename AccOf<V>::type csr_dot(const int32_t* __rest
   return s;
 }
 
+// The first Chebyshev step of a coarse level, x = d = D^-1 b / theta, done by
+// the restriction that produces its b (the values of a separate first-step
+// launch: the same expression on the stored b); dinv == nullptr: not done.
+template <class V>
+struct CoarseFirst {
+  const V* dinv = nullptr;
+  V* x = nullptr;
+  V* d = nullptr;
+  typename AccOf<V>::type theta = 1;
+};
+
+template <class V>
+__device__ __forceinline__ void store_restricted(V* out, int64_t i, typename AccOf<V>::type s, const CoarseFirst<V>& f) {
+  using A = typename AccOf<V>::type;
+  const V b = cvt<V>(s);
+  out[i] = b;
+  if (f.dinv) {
+    const V v = cvt<V>(cvt<A>(f.dinv[i]) * cvt<A>(b) / f.theta);
+    f.x[i] = v;
+    f.d[i] = v;
+  }
+}
+
 // out = R r with R's columns given as grid nodes
 template <int G, class V>
 __global__ void k_restrict0(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ node_col,
-                            const V* __restrict__ v, const V* __restrict__ r, V* __restrict__ out) {
+                            const V* __restrict__ v, const V* __restrict__ r, V* __restrict__ out, CoarseFirst<V> f) {
   using A = typename AccOf<V>::type;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t i = t / G;
@@ -235,7 +258,7 @@ __global__ void k_restrict0(int64_t n, const int32_t* __restrict__ rp, const int
   A s = 0;
   if (i < n) s = csr_dot<G>(node_col, v, r, rp[i], rp[i + 1], g);
   s = group_reduce<G>(s);
-  if (i < n && g == 0) out[i] = cvt<V>(s);
+  if (i < n && g == 0) store_restricted(out, i, s, f);
 }
 
 // x[node(i)] += sum_c P_ic e_c over the CPs i
@@ -298,16 +321,6 @@ __global__ void __launch_bounds__(TILE_NODES) k_prolong_mf(TileView tv, const ui
 }
 
 // compact levels -----------------------------------------------------------
-template <class V>
-__global__ void k_c_cheb_first(int64_t n, const V* dinv, const V* b, V* x, V* d, typename AccOf<V>::type theta) {
-  using A = typename AccOf<V>::type;
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const V v = cvt<V>(cvt<A>(dinv[i]) * cvt<A>(b[i]) / theta);
-  x[i] = v;
-  d[i] = v;
-}
-
 template <int G, class V>
 __device__ __forceinline__ typename AccOf<V>::type csr_row(const CsrV<V>& M, const V* x, int64_t i, int g) {
   using A = typename AccOf<V>::type;
@@ -349,13 +362,15 @@ __global__ void k_c_resid(CsrV<V> M, const V* b, const V* x, V* r) {
   if (i < M.n && g == 0) r[i] = cvt<V>(cvt<A>(b[i]) - ax);
 }
 
+// y = M x (the restriction of the compact levels), with the coarse level's
+// first smoothing step when f.dinv is set
 template <int G, class V>
-__global__ void k_c_spmv(CsrV<V> M, const V* x, V* y) {
+__global__ void k_c_spmv(CsrV<V> M, const V* x, V* y, CoarseFirst<V> f) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t i = t / G;
   const int g = (int)(t % G);
   const auto s = csr_row<G>(M, x, i, g);
-  if (i < M.n && g == 0) y[i] = cvt<V>(s);
+  if (i < M.n && g == 0) store_restricted(y, i, s, f);
 }
 
 template <int G, class V>
@@ -480,6 +495,25 @@ struct LevelView<__nv_bfloat16> {
   static const __nv_bfloat16* dinv(const Level& L) { return L.dinv16; }
 };
 
+// the first-step outputs for compact level l, or none if l is the coarsest
+// (its dense solve replaces smoothing)
+template <class V>
+static CoarseFirst<V> coarse_first(Solver& S, size_t l) {
+  using LV = LevelView<V>;
+  Hierarchy& H = *S.H;
+  CoarseFirst<V> f;
+  if (l + 1 >= H.L.size()) return f;
+  Level& L = H.L[l];
+  VecSet<V>& v = LV::vec(L);
+  f.dinv = LV::dinv(L);
+  f.x = v.x;
+  f.d = v.d;
+  f.theta = (typename AccOf<V>::type)cheb_coef(L.rho, S.opts.cheb_degree).theta;
+  return f;
+}
+
+// V-cycle from compact level l down; the restriction into l already did its
+// first smoothing step (coarse_first)
 template <class V>
 static void vcycle_compact(Solver& S, size_t l, cudaStream_t s) {
   using LV = LevelView<V>;
@@ -487,19 +521,17 @@ static void vcycle_compact(Solver& S, size_t l, cudaStream_t s) {
   Level& L = H.L[l];
   VecSet<V>& v = LV::vec(L);
   const int64_t n = L.A.n;
-  const unsigned nb = blocks_for(n, 256);
   if (l + 1 == H.L.size()) {
     S.nlaunch += 1;
     k_dense_gemv<V><<<blocks_for(n * 32, 256), 256, 0, s>>>(H.coarse_inv, n, v.b, v.x);
     return;
   }
   const ChebCoef cc = cheb_coef(L.rho, S.opts.cheb_degree);
-  S.nlaunch += 3 + 2 * cc.deg;  // first step, deg-1 steps, residual, restriction, prolongation, deg steps
+  S.nlaunch += 2 + 2 * cc.deg;  // deg-1 steps, residual, restriction, prolongation, deg steps
   const CsrV<V> A = LV::A(L);
   const int e = S.csr_epl;
   const int gA = group_width(L.A.nnz, L.A.n, e), gP = group_width(L.P.nnz, L.P.n, e),
             gR = group_width(L.R.nnz, L.R.n, e);
-  k_c_cheb_first<V><<<nb, 256, 0, s>>>(n, LV::dinv(L), v.b, v.x, v.d, cc.theta);
   const bool mark = l == 1;  // level-1 smoother launches are timed with PROF_LEVEL1
   for (int k = 1; k < cc.deg; ++k) {
     if (mark) S.prof_mark(s, true, PROF_LEVEL1);
@@ -510,7 +542,7 @@ static void vcycle_compact(Solver& S, size_t l, cudaStream_t s) {
   EB_GROUP_LAUNCH(gA, k_c_resid, V, n, s, A, v.b, v.x, v.r);
   Level& C = H.L[l + 1];
   VecSet<V>& cv = LV::vec(C);
-  EB_GROUP_LAUNCH(gR, k_c_spmv, V, C.A.n, s, LV::R(L), v.r, cv.b);
+  EB_GROUP_LAUNCH(gR, k_c_spmv, V, C.A.n, s, LV::R(L), v.r, cv.b, coarse_first<V>(S, l + 1));
   vcycle_compact<V>(S, l + 1, s);
   EB_GROUP_LAUNCH(gP, k_c_prolong_add, V, n, s, LV::P(L), cv.x, v.x);
   for (int k = 0; k < cc.deg; ++k) {
@@ -571,7 +603,7 @@ static int vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, co
   if (M.on) sc = reinterpret_cast<const SC*>(std::is_same<V, double>::value ? (const void*)M.sc64 : (const void*)M.sc32);
   // restriction through the explicit R (its per-member stencil gathers made a
   // matrix-free restriction slower); prolongation matrix free
-  EB_GROUP_LAUNCH(gR, k_restrict0, V, C.A.n, s, C.A.n, R0.rp, L0.R0node, R0.v, g.r, cv.b);
+  EB_GROUP_LAUNCH(gR, k_restrict0, V, C.A.n, s, C.A.n, R0.rp, L0.R0node, R0.v, g.r, cv.b, coarse_first<V>(S, 1));
   vcycle_compact<V>(S, 1, s);
   if (M.on)
     k_prolong_mf<DIM, V, SC><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, (A)M.omega, M.agg_node, sc, cv.x, x);
