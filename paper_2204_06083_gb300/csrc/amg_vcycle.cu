@@ -109,6 +109,45 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_first(TileView tv, const 
   }
 }
 
+// The PCG's x += alpha p, r -= alpha q and r'r partials (k_update_xr, same
+// grid, same loop order: the same values and partials) followed, per node
+// pair, by k_g_cheb_first on the new r: b_out = (V) r; x = d = D^-1 b / theta.
+template <int DIM, class V>
+__global__ void __launch_bounds__(TILE_NODES) k_update_first(TileView tv, PcgUpdate u, const uint8_t* __restrict__ code,
+                                                             const typename DiagOf<V>::type* __restrict__ diag,
+                                                             GOp<typename AccOf<V>::type> o, V* __restrict__ b_out,
+                                                             V* __restrict__ x0, V* __restrict__ d,
+                                                             typename AccOf<V>::type theta) {
+  using A = typename AccOf<V>::type;
+  __shared__ double sm[32];
+  __shared__ double s_alpha;
+  if (u.sc->done) {
+    if (threadIdx.x == 0) u.rr_part[blockIdx.x] = 0.0;
+    return;
+  }
+  const double alpha = pcg_alpha(u.sc, u.pq_part, u.nblk, sm, &s_alpha);
+  double srr = 0.0;
+  EB_PAIR_LOOP(DIM, tv, node) {
+    const Two<double> rv = ld2d(u.r + node), qv = LdRO::ld2(u.q + node), pv = LdRO::ld2(u.p + node),
+                      xv = ld2d(u.x + node);
+    const double r0 = rv.x - alpha * qv.x, r1 = rv.y - alpha * qv.y;
+    st2(u.x + node, xv.x + alpha * pv.x, xv.y + alpha * pv.y);
+    st2(u.r + node, r0, r1);
+    srr += r0 * r0 + r1 * r1;
+    const GOp<A> ot = tile_op(tv, tt_, o);
+    uint32_t c0, c1;
+    ld_codes(code, node, c0, c1);
+    const A b0 = (c0 & CODE_CP) ? (A)r0 : (A)0, b1 = (c1 & CODE_CP) ? (A)r1 : (A)0;
+    if (b_out) st2o(b_out + node, b0, b1);
+    const A v0 = (c0 & CODE_CP) ? inv_diag_t<A>(c0, diag, node, ot) * b0 / theta : (A)0;
+    const A v1 = (c1 & CODE_CP) ? inv_diag_t<A>(c1, diag, node + 1, ot) * b1 / theta : (A)0;
+    st2o(x0 + node, v0, v1);
+    st2o(d + node, v0, v1);
+  }
+  const double t = block_sum(srr, sm);
+  if (threadIdx.x == 0) u.rr_part[blockIdx.x] = t;
+}
+
 // res = D^-1 (b - A x); d = c1 d + c2 res; xo = x + d   (xo may be FP64).
 // DOT (xo FP64, the V-cycle's output z): also the CTA's partial r.z and, with
 // zold, r.zold (pairs), summed over its node pairs in loop order exactly as
@@ -554,7 +593,7 @@ static void vcycle_compact(Solver& S, size_t l, cudaStream_t s) {
 }
 
 template <class V, int DIM>
-static int vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, const VcycleDot* dot) {
+static int vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, const VcycleDot* dot, bool first_done) {
   using LV = LevelView<V>;
   Hierarchy& H = *S.H;
   const EBHandle& eb = *S.eb;
@@ -585,7 +624,10 @@ static int vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, co
   const V* b = std::is_same<V, double>::value ? reinterpret_cast<const V*>(r) : g.b;
   V* x = g.x;
   V* x2 = g.x2;
-  k_g_cheb_first<DIM, V><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, r, bcopy, x, g.d, (A)cc.theta);
+  if (first_done)
+    S.nlaunch -= 1;  // amg_update_first did it
+  else
+    k_g_cheb_first<DIM, V><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, r, bcopy, x, g.d, (A)cc.theta);
   for (int k = 1; k < cc.deg; ++k) {
     S.prof_mark(s, true);
     k_g_cheb_step<DIM, V, V><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, x, x2, g.d, (A)cc.c1[k], (A)cc.c2[k]);
@@ -631,13 +673,49 @@ static int vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, co
   return dot ? (int)gb : 0;
 }
 
-int amg_vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, const VcycleDot* dot) {
+int amg_vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, const VcycleDot* dot, bool first_done) {
   const int dim = S.eb->g.dim;
   if (S.opts.vcycle_prec == EB_F32)
-    return dim == 2 ? vcycle_grid<float, 2>(S, r, z, s, dot) : vcycle_grid<float, 3>(S, r, z, s, dot);
+    return dim == 2 ? vcycle_grid<float, 2>(S, r, z, s, dot, first_done)
+                    : vcycle_grid<float, 3>(S, r, z, s, dot, first_done);
   if (S.opts.vcycle_prec == EB_BF16)
-    return dim == 2 ? vcycle_grid<__nv_bfloat16, 2>(S, r, z, s, dot) : vcycle_grid<__nv_bfloat16, 3>(S, r, z, s, dot);
-  return dim == 2 ? vcycle_grid<double, 2>(S, r, z, s, dot) : vcycle_grid<double, 3>(S, r, z, s, dot);
+    return dim == 2 ? vcycle_grid<__nv_bfloat16, 2>(S, r, z, s, dot, first_done)
+                    : vcycle_grid<__nv_bfloat16, 3>(S, r, z, s, dot, first_done);
+  return dim == 2 ? vcycle_grid<double, 2>(S, r, z, s, dot, first_done)
+                  : vcycle_grid<double, 3>(S, r, z, s, dot, first_done);
+}
+
+template <class V, int DIM>
+static void update_first(Solver& S, const PcgUpdate& u, cudaStream_t s) {
+  using LV = LevelView<V>;
+  using A = typename AccOf<V>::type;
+  Hierarchy& H = *S.H;
+  const EBHandle& eb = *S.eb;
+  const Geometry& G = eb.g;
+  const double inv_h2 = 1.0 / (G.h * G.h);
+  const ChebCoef cc = cheb_coef(H.L[0].rho, S.opts.cheb_degree);
+  const GOp<A> o{(A)inv_h2, (A)S.shift, (A)(1.0 / (S.shift + 2.0 * G.dim * inv_h2))};
+  VecSet<V>& g = LV::grid(H);
+  V* bcopy = std::is_same<V, double>::value ? nullptr : g.b;
+  k_update_first<DIM, V><<<(unsigned)u.nblk, TILE_NODES, 0, s>>>(eb.tv(), u, eb.code, diag_of<V>(eb), o, bcopy, g.x,
+                                                                 g.d, (A)cc.theta);
+}
+
+int amg_update_first(Solver& S, const PcgUpdate& u, cudaStream_t s) {
+  if (!S.H || S.H->L.size() == 1) return 0;  // a single level has no smoothing step
+  const int dim = S.eb->g.dim;
+  if (S.opts.vcycle_prec == EB_F32) {
+    if (dim == 2) update_first<float, 2>(S, u, s);
+    else update_first<float, 3>(S, u, s);
+  } else if (S.opts.vcycle_prec == EB_BF16) {
+    if (dim == 2) update_first<__nv_bfloat16, 2>(S, u, s);
+    else update_first<__nv_bfloat16, 3>(S, u, s);
+  } else {
+    if (dim == 2) update_first<double, 2>(S, u, s);
+    else update_first<double, 3>(S, u, s);
+  }
+  EB_CUDA(cudaGetLastError());
+  return 1;
 }
 
 template <class V>

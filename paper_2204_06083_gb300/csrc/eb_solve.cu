@@ -76,12 +76,6 @@ __global__ void __launch_bounds__(TILE_NODES) k_apply_dot(TileView tv, const uin
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
-// sum of n partials (stride apart) in a fixed order, the same in every CTA
-__device__ __forceinline__ double sum_parts(const double* part, int n, int stride, double* sm) {
-  double a = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) a += part[stride * i];
-  return block_sum(a, sm);  // thread 0 holds the result
-}
 
 // alpha = rz / p'q from the partials of k_apply_dot (every CTA; CTA 0 records
 // pq, alpha and a breakdown); x += alpha p; r -= alpha q; partial r.r
@@ -95,22 +89,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_update_xr(TileView tv, PcgScalar
     if (threadIdx.x == 0) part[blockIdx.x] = 0.0;
     return;
   }
-  const double pq = sum_parts(pq_part, nblk, 1, sm);
-  if (threadIdx.x == 0) {
-    const bool ok = pq > 0.0;  // false for NaN too
-    const double alpha = ok ? sc->rz[sc->iters & 1] / pq : 0.0;
-    s_alpha = alpha;
-    if (blockIdx.x == 0) {
-      sc->pq = pq;
-      sc->alpha = alpha;
-      if (!ok) {
-        sc->flags |= isfinite(pq) ? PCG_FLAG_BREAKDOWN : PCG_FLAG_NONFINITE;
-        sc->done = 1;
-      }
-    }
-  }
-  __syncthreads();
-  const double alpha = s_alpha;
+  const double alpha = pcg_alpha(sc, pq_part, nblk, sm, &s_alpha);
   double s = 0.0;
   EB_PAIR_LOOP(DIM, tv, node) {
     const Two<double> rv = ld2d(r + node), qv = LdRO::ld2(q + node), pv = LdRO::ld2(p + node), xv = ld2d(x + node);
@@ -376,7 +355,7 @@ void Solver::finalize(int op, const double* src, cudaStream_t s, int count) {
   k_finalize<<<1, 1024, 0, s>>>(src, count < 0 ? nblk : count, op, sc);
 }
 
-void Solver::precondition(int kind, const double* rin, double* zout, cudaStream_t s) {
+void Solver::precondition(int kind, const double* rin, double* zout, cudaStream_t s, bool first_done) {
   const int dim = eb->g.dim;
   const TileView tv = eb->tv();
   rz_n = nblk;
@@ -390,7 +369,7 @@ void Solver::precondition(int kind, const double* rin, double* zout, cudaStream_
     dot.r = rin;
     dot.zold = flexible() ? zold : nullptr;
     dot.part = part_rz();
-    const int fused = amg_vcycle_grid(*this, rin, zout, s, &dot);
+    const int fused = amg_vcycle_grid(*this, rin, zout, s, &dot, first_done);
     if (fused) {
       rz_n = fused;
       return;
@@ -552,8 +531,23 @@ void Solver::iteration(int kind, const double* b, double* x, cudaStream_t s, boo
   const TileView tv = eb->tv();
   const OpParams op = op_params(*this);
   EB_DIM_LAUNCH(dim, k_apply_dot, nblk, tv, eb->code, eb->diag, op, p, q, part_pq());
-  EB_DIM_LAUNCH(dim, k_update_xr, nblk, tv, sc, x, r, p, q, part_pq(), nblk, part_rr());
-  precondition(kind, r, z, s);
+  // with an AMG V-cycle next, the x/r update also does its first level-0 step
+  bool fused = false;
+  if (kind == EB_PC_AMG && H) {
+    PcgUpdate u;
+    u.sc = sc;
+    u.x = x;
+    u.r = r;
+    u.p = p;
+    u.q = q;
+    u.pq_part = part_pq();
+    u.nblk = nblk;
+    u.rr_part = part_rr();
+    fused = amg_update_first(*this, u, s) != 0;
+    if (fused) ++nlaunch;
+  }
+  if (!fused) EB_DIM_LAUNCH(dim, k_update_xr, nblk, tv, sc, x, r, p, q, part_pq(), nblk, part_rr());
+  precondition(kind, r, z, s, fused);
   const bool flex = flex_for(kind);
   EB_DIM_LAUNCH(dim, k_xpby, nblk, tv, sc, z, p, flex ? zold : nullptr, 0, part_rz(), rz_n);
   // r'r and the convergence test end the iteration (the device-side loop's

@@ -87,7 +87,8 @@ struct Solver {
   void alloc_work(cudaStream_t s);
   void free_work();
   void finalize(int op, const double* src, cudaStream_t s, int count = -1);  // count < 0: nblk partials
-  void precondition(int kind, const double* r, double* z, cudaStream_t s);
+  // first_done: amg_update_first did the V-cycle's first level-0 step for r
+  void precondition(int kind, const double* r, double* z, cudaStream_t s, bool first_done = false);
   int pcg(const double* b, double* x, double rtol, int maxit, const pcg_opts& o, pcg_stats* stats, cudaStream_t s);
   int heat(double dt, double theta, const double* b1, const double* b0, double* u, double rtol, int maxit,
            pcg_stats* stats, cudaStream_t s);
@@ -127,6 +128,50 @@ __device__ __forceinline__ double block_sum(double v, double* sm) {
   return s;
 }
 
+// sum of n partials (stride apart) in a fixed order, the same in every CTA;
+// thread 0 holds the result
+__device__ __forceinline__ double sum_parts(const double* part, int n, int stride, double* sm) {
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a += part[stride * i];
+  return block_sum(a, sm);
+}
+
+// alpha = rz / p'q from the nblk partials of k_apply_dot, formed by every CTA in
+// the same order; CTA 0 records p'q, alpha and a breakdown (p'q <= 0 or not
+// finite).  All threads of the CTA call it; returns alpha to every thread.
+__device__ __forceinline__ double pcg_alpha(PcgScalars* sc, const double* pq_part, int nblk, double* sm,
+                                            double* s_alpha) {
+  const double pq = sum_parts(pq_part, nblk, 1, sm);
+  if (threadIdx.x == 0) {
+    const bool ok = pq > 0.0;  // false for NaN too
+    const double alpha = ok ? sc->rz[sc->iters & 1] / pq : 0.0;
+    *s_alpha = alpha;
+    if (blockIdx.x == 0) {
+      sc->pq = pq;
+      sc->alpha = alpha;
+      if (!ok) {
+        sc->flags |= isfinite(pq) ? PCG_FLAG_BREAKDOWN : PCG_FLAG_NONFINITE;
+        sc->done = 1;
+      }
+    }
+  }
+  __syncthreads();
+  return *s_alpha;
+}
+
+// The PCG update x += alpha p, r -= alpha q (with the r'r partials of
+// k_update_xr) fused with the first level-0 smoothing step of the V-cycle that
+// follows (which then starts at its second step); 0 if the hierarchy has no
+// such step (a single level), else the launch was issued.
+struct PcgUpdate {
+  PcgScalars* sc = nullptr;
+  double *x = nullptr, *r = nullptr;
+  const double *p = nullptr, *q = nullptr, *pq_part = nullptr;
+  int nblk = 0;
+  double* rr_part = nullptr;
+};
+int amg_update_first(Solver& S, const PcgUpdate& u, cudaStream_t s);
+
 // z = V r.  With dot, the last level-0 smoothing launch also writes per-CTA
 // partials of r.z (and of r.zold when dot->zold is set, as pairs) to
 // dot->part; returns their count, or 0 if no launch wrote them (single-level
@@ -136,7 +181,9 @@ struct VcycleDot {
   const double* zold = nullptr;
   double* part = nullptr;
 };
-int amg_vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, const VcycleDot* dot = nullptr);
+// first_done: amg_update_first already did the first level-0 step for this r.
+int amg_vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, const VcycleDot* dot = nullptr,
+                    bool first_done = false);
 void amg_fill_info(const Solver& S, amg_info_t* out);
 void amg_copy_level(const Solver& S, int level, int which, int32_t* rowptr, int32_t* col, double* val, cudaStream_t s);
 
