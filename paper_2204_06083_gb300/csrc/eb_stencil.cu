@@ -1,5 +1,5 @@
 // Matrix-free EB stencil (eq. 3 with the line-by-line diagonal of Sec. 2.1),
-// device prefix scan, and the persistent leapfrog kernel (theta-scheme of
+// device prefix scan, and the leapfrog step kernel (theta-scheme of
 // Sec. 3.5 at theta = 0).
 //
 // Layout: full grid, x fastest; work is distributed over the active tiles
