@@ -361,12 +361,25 @@ def run_reference(args):
 
 # -------------------------------------------------------------------- GPU leg
 class Ctx:
-    def __init__(self):
+    """One rank of the run: rank and world size from the torchrun environment,
+    NCCL between the ranks' GPUs (replicas: only the barrier and the max over
+    ranks of the timings cross ranks).  cpu=True: gloo on host tensors and no
+    GPU, for testing the multi-rank logic."""
+
+    def __init__(self, cpu=False):
         import torch
         self.world = int(os.environ.get("WORLD_SIZE", "1"))
         self.rank = int(os.environ.get("RANK", "0"))
         local = int(os.environ.get("LOCAL_RANK", "0"))
         self.dist = None
+        if cpu:
+            if self.world > 1:
+                import torch.distributed as dist
+                dist.init_process_group("gloo")
+                self.dist = dist
+            self.dev = torch.device("cpu")
+            self.flush_buf = None
+            return
         if self.world > 1:
             import torch.distributed as dist
             torch.cuda.set_device(local)
