@@ -57,27 +57,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_resid(TileView tv, const uint8_t
   }
 }
 
-// q = (sigma I + A) p; partial p.q
-template <int DIM>
-__global__ void __launch_bounds__(TILE_NODES) k_apply_dot(TileView tv, const uint8_t* code, const double* diag,
-                                                          OpParams o, const double* p, double* q, double* part) {
-  __shared__ double sm[32];
-  double s = 0.0;
-  EB_PAIR_LOOP(DIM, tv, node) {
-    uint32_t c0, c1;
-    ld_codes(code, node, c0, c1);
-    Two<double> xc, ax;
-    op_pair<DIM>(tv, p, node, c0, c1, diag, o, xc, ax);
-    const double q0 = (c0 & CODE_CP) ? ax.x : 0.0, q1 = (c1 & CODE_CP) ? ax.y : 0.0;
-    s += xc.x * q0 + xc.y * q1;
-    st2(q + node, q0, q1);
-  }
-  const double t = block_sum(s, sm);
-  if (threadIdx.x == 0) part[blockIdx.x] = t;
-}
-
-
-// alpha = rz / p'q from the partials of k_apply_dot (every CTA; CTA 0 records
+// alpha = rz / p'q from the partials of k_xpby_apply (every CTA; CTA 0 records
 // pq, alpha and a breakdown); x += alpha p; r -= alpha q; partial r.r
 template <int DIM>
 __global__ void __launch_bounds__(TILE_NODES) k_update_xr(TileView tv, PcgScalars* sc, double* x, double* r,
@@ -155,11 +135,20 @@ __global__ void __launch_bounds__(TILE_NODES) k_dot2(TileView tv, const double* 
 // p = z + beta p   (p = z on the first iteration of a cycle); zold = z when
 // zold is given (flexible CG).  Otherwise beta comes from the partials of the
 // preconditioner's dot kernel (pairs (r.z, r.zold) when flexible): beta =
-// r.z / rz (Fletcher-Reeves) or (r.z - r.zold) / rz (Polak-Ribiere), computed
-// by every CTA; CTA 0 records beta, the next rz (the other slot) and a breakdown.
+// The end of a PCG iteration in one pass: beta = r.z / rz (Fletcher-Reeves) or
+// (r.z - r.zold) / rz (Polak-Ribiere), computed by every CTA (CTA 0 records
+// beta, the next rz and a breakdown), p = z + beta p, zold = z (flexible CG), and the operator apply
+// of the next iteration formed as q = (sigma I + A) z + beta q -- in exact
+// arithmetic (sigma I + A)(z + beta p), since q holds (sigma I + A) p -- with
+// the partials of p.q.  The stencil then reads z, which the preconditioner
+// launch before has completed, instead of the p this launch writes, so the
+// p update and the apply need no launch boundary between them.  first: beta =
+// 0, p = z, q = (sigma I + A) z (the old p and q are not read).
 template <int DIM>
-__global__ void __launch_bounds__(TILE_NODES) k_xpby(TileView tv, PcgScalars* sc, const double* z, double* p,
-                                                     double* zold, int first, const double* rz_part, int nblk) {
+__global__ void __launch_bounds__(TILE_NODES) k_xpby_apply(TileView tv, PcgScalars* sc, const uint8_t* code,
+                                                           const double* diag, OpParams o, const double* z,
+                                                           double* p, double* q, double* zold, int first,
+                                                           const double* rz_part, int nblk, double* pq_part) {
   __shared__ double sm[32];
   __shared__ double s_beta;
   if (sc->done) return;
@@ -185,16 +174,29 @@ __global__ void __launch_bounds__(TILE_NODES) k_xpby(TileView tv, PcgScalars* sc
     __syncthreads();
   }
   const double beta = first ? 0.0 : s_beta;
+  double s = 0.0;
   EB_PAIR_LOOP(DIM, tv, node) {
-    const Two<double> zv = LdRO::ld2(z + node);
-    if (first) {
-      st2(p + node, zv.x, zv.y);
-    } else {
-      const Two<double> pv = ld2d(p + node);
-      st2(p + node, zv.x + beta * pv.x, zv.y + beta * pv.y);
+    uint32_t c0, c1;
+    ld_codes(code, node, c0, c1);
+    Two<double> zc, az;
+    op_pair<DIM>(tv, z, node, c0, c1, diag, o, zc, az);
+    double p0 = zc.x, p1 = zc.y, q0 = az.x, q1 = az.y;
+    if (!first) {
+      const Two<double> pv = ld2d(p + node), qv = ld2d(q + node);
+      p0 = zc.x + beta * pv.x;
+      p1 = zc.y + beta * pv.y;
+      q0 = az.x + beta * qv.x;
+      q1 = az.y + beta * qv.y;
     }
-    if (zold) st2(zold + node, zv.x, zv.y);
+    q0 = (c0 & CODE_CP) ? q0 : 0.0;
+    q1 = (c1 & CODE_CP) ? q1 : 0.0;
+    st2(p + node, p0, p1);
+    st2(q + node, q0, q1);
+    if (zold) st2(zold + node, zc.x, zc.y);
+    s += p0 * q0 + p1 * q1;
   }
+  const double t = block_sum(s, sm);
+  if (threadIdx.x == 0) pq_part[blockIdx.x] = t;
 }
 
 template <int DIM>
@@ -439,7 +441,8 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
     precondition(kind, r, z, s);
     const bool flex = flex_for(kind);
     finalize(flex ? FIN_RZ0F : FIN_RZ0, part_rz(), s, rz_n);
-    EB_DIM_LAUNCH(dim, k_xpby, nblk, tv, sc, z, p, flex ? zold : nullptr, 1, part_rz(), rz_n);
+    EB_DIM_LAUNCH(dim, k_xpby_apply, nblk, tv, sc, eb->code, eb->diag, op, z, p, q, flex ? zold : nullptr, 1,
+                  part_rz(), rz_n, part_pq());
     int it = 0;
     bool stop = false;
     if (o.use_graph == 1 && !prof_on) {  // the whole loop on the device
@@ -530,8 +533,9 @@ void Solver::iteration(int kind, const double* b, double* x, cudaStream_t s, boo
   const int dim = eb->g.dim;
   const TileView tv = eb->tv();
   const OpParams op = op_params(*this);
-  EB_DIM_LAUNCH(dim, k_apply_dot, nblk, tv, eb->code, eb->diag, op, p, q, part_pq());
-  // with an AMG V-cycle next, the x/r update also does its first level-0 step
+  // q = (sigma I + A) p and the p.q partials come from the previous
+  // k_xpby_apply; with an AMG V-cycle next, the x/r update also does its first
+  // level-0 step
   bool fused = false;
   if (kind == EB_PC_AMG && H) {
     PcgUpdate u;
@@ -549,7 +553,8 @@ void Solver::iteration(int kind, const double* b, double* x, cudaStream_t s, boo
   if (!fused) EB_DIM_LAUNCH(dim, k_update_xr, nblk, tv, sc, x, r, p, q, part_pq(), nblk, part_rr());
   precondition(kind, r, z, s, fused);
   const bool flex = flex_for(kind);
-  EB_DIM_LAUNCH(dim, k_xpby, nblk, tv, sc, z, p, flex ? zold : nullptr, 0, part_rz(), rz_n);
+  EB_DIM_LAUNCH(dim, k_xpby_apply, nblk, tv, sc, eb->code, eb->diag, op, z, p, q, flex ? zold : nullptr, 0,
+                part_rz(), rz_n, part_pq());
   // r'r and the convergence test end the iteration (the device-side loop's
   // condition kernel does it itself)
   if (!loop_end) finalize(FIN_RR, part_rr(), s);

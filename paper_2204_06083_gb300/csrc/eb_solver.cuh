@@ -136,7 +136,7 @@ __device__ __forceinline__ double sum_parts(const double* part, int n, int strid
   return block_sum(a, sm);
 }
 
-// alpha = rz / p'q from the nblk partials of k_apply_dot, formed by every CTA in
+// alpha = rz / p'q from the nblk partials of k_xpby_apply, formed by every CTA in
 // the same order; CTA 0 records p'q, alpha and a breakdown (p'q <= 0 or not
 // finite).  All threads of the CTA call it; returns alpha to every thread.
 __device__ __forceinline__ double pcg_alpha(PcgScalars* sc, const double* pq_part, int nblk, double* sm,
