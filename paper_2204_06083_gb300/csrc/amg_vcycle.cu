@@ -110,10 +110,12 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_first(TileView tv, const 
 }
 
 // The PCG's x += alpha p, r -= alpha q and r'r partials (k_update_xr, same
-// grid, same loop order: the same values and partials) followed, per node
-// pair, by k_g_cheb_first on the new r: b_out = (V) r; x = d = D^-1 b / theta.
+// grid, same pair list and order: the same values and partials) followed, per
+// node pair, by k_g_cheb_first on the new r: b_out = (V) r; x = d = D^-1 b /
+// theta.  It runs over the CP pairs only (single grids): the entries of pairs
+// without a CP are never read at a CP.
 template <int DIM, class V>
-__global__ void __launch_bounds__(TILE_NODES) k_update_first(TileView tv, PcgUpdate u, const uint8_t* __restrict__ code,
+__global__ void __launch_bounds__(TILE_NODES) k_update_first(PairList pl, PcgUpdate u, const uint8_t* __restrict__ code,
                                                              const typename DiagOf<V>::type* __restrict__ diag,
                                                              GOp<typename AccOf<V>::type> o, V* __restrict__ b_out,
                                                              V* __restrict__ x0, V* __restrict__ d,
@@ -127,14 +129,14 @@ __global__ void __launch_bounds__(TILE_NODES) k_update_first(TileView tv, PcgUpd
   }
   const double alpha = pcg_alpha(u.sc, u.pq_part, u.nblk, sm, &s_alpha);
   double srr = 0.0;
-  EB_PAIR_LOOP(DIM, tv, node) {
+  EB_LIST_LOOP(pl, node) {
     const Two<double> rv = ld2d(u.r + node), qv = LdRO::ld2(u.q + node), pv = LdRO::ld2(u.p + node),
                       xv = ld2d(u.x + node);
     const double r0 = rv.x - alpha * qv.x, r1 = rv.y - alpha * qv.y;
     st2(u.x + node, xv.x + alpha * pv.x, xv.y + alpha * pv.y);
     st2(u.r + node, r0, r1);
     srr += r0 * r0 + r1 * r1;
-    const GOp<A> ot = tile_op(tv, tt_, o);
+    const GOp<A>& ot = o;
     uint32_t c0, c1;
     ld_codes(code, node, c0, c1);
     const A b0 = (c0 & CODE_CP) ? (A)r0 : (A)0, b1 = (c1 & CODE_CP) ? (A)r1 : (A)0;
@@ -697,8 +699,8 @@ static void update_first(Solver& S, const PcgUpdate& u, cudaStream_t s) {
   const GOp<A> o{(A)inv_h2, (A)S.shift, (A)(1.0 / (S.shift + 2.0 * G.dim * inv_h2))};
   VecSet<V>& g = LV::grid(H);
   V* bcopy = std::is_same<V, double>::value ? nullptr : g.b;
-  k_update_first<DIM, V><<<(unsigned)u.nblk, TILE_NODES, 0, s>>>(eb.tv(), u, eb.code, diag_of<V>(eb), o, bcopy, g.x,
-                                                                 g.d, (A)cc.theta);
+  k_update_first<DIM, V><<<(unsigned)u.nblk, TILE_NODES, 0, s>>>(eb.pairs(), u, eb.code, diag_of<V>(eb), o, bcopy,
+                                                                 g.x, g.d, (A)cc.theta);
 }
 
 int amg_update_first(Solver& S, const PcgUpdate& u, cudaStream_t s) {

@@ -312,6 +312,32 @@ __global__ void k_tile_geom(Geometry G, const int32_t* tiles, int64_t nt, int32_
   lim[k] = lx | (ly << 8) | (lz << 16);
 }
 
+// Node pairs of listed tile blockIdx.x (128 threads, pair layout) that hold a
+// CP: their count (fill == false) or their first nodes written from off[tile]
+// on in pair order (fill == true).
+__global__ void __launch_bounds__(128) k_cp_pairs(TileView tv, const uint8_t* __restrict__ code, bool fill,
+                                                  int32_t* cnt, const int32_t* off, int32_t* list) {
+  __shared__ int wc[4];
+  const int64_t tt = blockIdx.x;
+  int32_t node = 0;
+  bool ok = tile_pair<3>(tv, tt, threadIdx.x, node);
+  if (ok) {
+    const uint32_t v = __ldg(reinterpret_cast<const unsigned short*>(code + node));
+    ok = ((v | (v >> 8)) & CODE_CP) != 0;
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, ok);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) wc[w] = __popc(m);
+  __syncthreads();
+  if (!fill) {
+    if (threadIdx.x == 0) cnt[tt] = wc[0] + wc[1] + wc[2] + wc[3];
+    return;
+  }
+  int before = 0;
+  for (int k = 0; k < w; ++k) before += wc[k];
+  if (ok) list[off[tt] + before + __popc(m & ((1u << lane) - 1u))] = node;
+}
+
 static LSDev to_dev(const eb_levelset& ls, int dim) {
   LSDev L{};
   L.kind = ls.kind;
@@ -470,14 +496,46 @@ void build_tiles(EBHandle& eb, int tx, int ty, int tz, cudaStream_t s) {
   }
   dfree(tflag, s);
   dfree(toff, s);
+  build_cp_pairs(eb, s);
   ++eb.tile_gen;
+}
+
+// the CP pair list of the current tile view (EBHandle::pairs)
+void build_cp_pairs(EBHandle& eb, cudaStream_t s) {
+  dfree(eb.pair_node, s);
+  eb.num_pairs = 0;
+  const int64_t nt = eb.num_tiles;
+  if (nt == 0) return;
+  int32_t* cnt = dalloc<int32_t>(nt, s, false);
+  int32_t* off = nullptr;
+  try {
+    off = dalloc<int32_t>(nt + 1, s, false);
+    const TileView tv = eb.tv();
+    k_cp_pairs<<<(unsigned)nt, 128, 0, s>>>(tv, eb.code, false, cnt, nullptr, nullptr);
+    exclusive_scan_i32(cnt, off, nt, s);
+    int32_t np = 0;
+    EB_CUDA(cudaMemcpyAsync(&np, off + nt, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    EB_CUDA(cudaStreamSynchronize(s));
+    if (np > 0) {
+      eb.pair_node = dalloc<int32_t>(np, s, false);
+      k_cp_pairs<<<(unsigned)nt, 128, 0, s>>>(tv, eb.code, true, nullptr, off, eb.pair_node);
+      EB_CUDA(cudaGetLastError());
+    }
+    eb.num_pairs = np;
+  } catch (...) {
+    dfree(cnt, s);
+    dfree(off, s);
+    throw;
+  }
+  dfree(cnt, s);
+  dfree(off, s);
 }
 
 void destroy_handle(EBHandle& eb) {
   cudaStream_t s = eb.home;
   eb.lf_graph.release();
   dfree(eb.code, s); dfree(eb.diag, s); dfree(eb.diag32, s); dfree(eb.cp_of_node, s); dfree(eb.cp_node, s);
-  dfree(eb.tiles, s); dfree(eb.tile_base, s); dfree(eb.tile_lim, s); dfree(eb.cut_cp, s); dfree(eb.cut_dir, s); dfree(eb.cut_delta, s);
+  dfree(eb.tiles, s); dfree(eb.tile_base, s); dfree(eb.tile_lim, s); dfree(eb.pair_node, s); dfree(eb.cut_cp, s); dfree(eb.cut_dir, s); dfree(eb.cut_delta, s);
   dfree(eb.cut_c, s); dfree(eb.cut_xg, s); dfree(eb.cut_off, s);
   cudaStreamSynchronize(s);
 }

@@ -120,6 +120,11 @@ struct EBHandle {
   double2* tile_shift64 = nullptr;  // batched view only: per-tile (sigma, 1 / (sigma + 2 dim))
   float2* tile_shift32 = nullptr;
   int tile_gen = 0;  // bumped whenever the tile list is rebuilt (captured graphs key on it)
+  // node pairs of the tile view holding a CP (rebuilt with the tiles; single
+  // grids only): the PCG's FP64 update kernels run over these
+  int32_t* pair_node = nullptr;
+  int64_t num_pairs = 0;
+  PairList pairs() const { return PairList{pair_node, num_pairs}; }
   TileView tv() const {
     TileView v{tile_base, tile_lim, num_tiles, g.n0, g.n0 * g.n1, (int32_t)g.num_nodes, tile_shift64, tile_shift32};
     v.bx = ilog2(g.tx);
@@ -214,6 +219,7 @@ namespace ebk {
 // Rebuilds the list of active tiles of eb for tiles of tx x ty x tz nodes
 // (powers of two, product 256, tx >= 2, tz = 1 in 2D); bumps eb.tile_gen.
 void build_tiles(EBHandle& eb, int tx, int ty, int tz, cudaStream_t s);
+void build_cp_pairs(EBHandle& eb, cudaStream_t s);
 // whether (tx, ty, tz) is a valid tile shape for dim
 bool tile_shape_ok(int dim, int tx, int ty, int tz);
 // tile-shape autotuner (autotune.cu): candidate shapes, event timing of an

@@ -2,7 +2,9 @@
 // and the theta-method heat step (Sec. 3.4).
 //
 // Vectors live in the full-grid layout and are touched on the active tiles
-// only.  Every reduction is two-pass and deterministic: each CTA of a fixed
+// only; the FP64 update kernels (x, r, p, q) run over the node pairs of the
+// tiles that hold a CP (EBHandle::pairs): the other pairs' entries are never
+// read at a CP, and GB300's narrow FP64 pipe makes the skipped pairs count.  Every reduction is two-pass and deterministic: each CTA of a fixed
 // grid reduces its nodes in a fixed order to one partial; the partials are
 // combined in a fixed order by the kernel that needs the result -- every CTA
 // of the update kernels (x, r with alpha; p with beta) reduces them itself and
@@ -60,7 +62,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_resid(TileView tv, const uint8_t
 // alpha = rz / p'q from the partials of k_xpby_apply (every CTA; CTA 0 records
 // pq, alpha and a breakdown); x += alpha p; r -= alpha q; partial r.r
 template <int DIM>
-__global__ void __launch_bounds__(TILE_NODES) k_update_xr(TileView tv, PcgScalars* sc, double* x, double* r,
+__global__ void __launch_bounds__(TILE_NODES) k_update_xr(PairList pl, PcgScalars* sc, double* x, double* r,
                                                           const double* p, const double* q, const double* pq_part,
                                                           int nblk, double* part) {
   __shared__ double sm[32];
@@ -71,7 +73,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_update_xr(TileView tv, PcgScalar
   }
   const double alpha = pcg_alpha(sc, pq_part, nblk, sm, &s_alpha);
   double s = 0.0;
-  EB_PAIR_LOOP(DIM, tv, node) {
+  EB_LIST_LOOP(pl, node) {
     const Two<double> rv = ld2d(r + node), qv = LdRO::ld2(q + node), pv = LdRO::ld2(p + node), xv = ld2d(x + node);
     const double r0 = rv.x - alpha * qv.x, r1 = rv.y - alpha * qv.y;
     st2(x + node, xv.x + alpha * pv.x, xv.y + alpha * pv.y);
@@ -135,20 +137,22 @@ __global__ void __launch_bounds__(TILE_NODES) k_dot2(TileView tv, const double* 
 // p = z + beta p   (p = z on the first iteration of a cycle); zold = z when
 // zold is given (flexible CG).  Otherwise beta comes from the partials of the
 // preconditioner's dot kernel (pairs (r.z, r.zold) when flexible): beta =
-// The end of a PCG iteration in one pass: beta = r.z / rz (Fletcher-Reeves) or
-// (r.z - r.zold) / rz (Polak-Ribiere), computed by every CTA (CTA 0 records
-// beta, the next rz and a breakdown), p = z + beta p, zold = z (flexible CG), and the operator apply
-// of the next iteration formed as q = (sigma I + A) z + beta q -- in exact
-// arithmetic (sigma I + A)(z + beta p), since q holds (sigma I + A) p -- with
-// the partials of p.q.  The stencil then reads z, which the preconditioner
-// launch before has completed, instead of the p this launch writes, so the
-// p update and the apply need no launch boundary between them.  first: beta =
-// 0, p = z, q = (sigma I + A) z (the old p and q are not read).
+// The end of a PCG iteration in one pass over the CP pairs: beta = r.z / rz
+// (Fletcher-Reeves) or (r.z - r.zold) / rz (Polak-Ribiere), computed by every
+// CTA (CTA 0 records beta, the next rz and a breakdown), p = z + beta p, zold
+// = z (flexible CG), and the operator apply of the next iteration formed as
+// q = (sigma I + A) z + beta q -- in exact arithmetic (sigma I + A)(z + beta
+// p), since q holds (sigma I + A) p -- with the partials of p.q.  The stencil
+// then reads z, which the preconditioner launch before has completed, instead
+// of the p this launch writes, so the p update and the apply need no launch
+// boundary between them.  first: beta = 0, p = z, q = (sigma I + A) z (the
+// old p and q are not read).
 template <int DIM>
-__global__ void __launch_bounds__(TILE_NODES) k_xpby_apply(TileView tv, PcgScalars* sc, const uint8_t* code,
-                                                           const double* diag, OpParams o, const double* z,
-                                                           double* p, double* q, double* zold, int first,
-                                                           const double* rz_part, int nblk, double* pq_part) {
+__global__ void __launch_bounds__(TILE_NODES) k_xpby_apply(TileView tv, PairList pl, PcgScalars* sc,
+                                                           const uint8_t* code, const double* diag, OpParams o,
+                                                           const double* z, double* p, double* q, double* zold,
+                                                           int first, const double* rz_part, int nblk,
+                                                           double* pq_part) {
   __shared__ double sm[32];
   __shared__ double s_beta;
   if (sc->done) return;
@@ -175,7 +179,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_xpby_apply(TileView tv, PcgScala
   }
   const double beta = first ? 0.0 : s_beta;
   double s = 0.0;
-  EB_PAIR_LOOP(DIM, tv, node) {
+  EB_LIST_LOOP(pl, node) {
     uint32_t c0, c1;
     ld_codes(code, node, c0, c1);
     Two<double> zc, az;
@@ -402,6 +406,7 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
              "AMG preconditioner requested without a hierarchy");
   EB_REQUIRE(rtol > 0.0 && maxit >= 0, EB_ERR_INVALID, "rtol must be > 0 and maxit >= 0");
   EB_REQUIRE(b != x, EB_ERR_INVALID, "pcg: b and x must be different buffers");
+  EB_REQUIRE(eb->pair_node != nullptr || eb->num_cp == 0, EB_ERR_INVALID, "pcg: the handle has no CP pair list");
   const int check = std::max(1, o.check_every);
   prof_begin(o.profile, s);
   nlaunch = 0;
@@ -441,8 +446,8 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
     precondition(kind, r, z, s);
     const bool flex = flex_for(kind);
     finalize(flex ? FIN_RZ0F : FIN_RZ0, part_rz(), s, rz_n);
-    EB_DIM_LAUNCH(dim, k_xpby_apply, nblk, tv, sc, eb->code, eb->diag, op, z, p, q, flex ? zold : nullptr, 1,
-                  part_rz(), rz_n, part_pq());
+    EB_DIM_LAUNCH(dim, k_xpby_apply, nblk, tv, eb->pairs(), sc, eb->code, eb->diag, op, z, p, q,
+                  flex ? zold : nullptr, 1, part_rz(), rz_n, part_pq());
     int it = 0;
     bool stop = false;
     if (o.use_graph == 1 && !prof_on) {  // the whole loop on the device
@@ -550,11 +555,11 @@ void Solver::iteration(int kind, const double* b, double* x, cudaStream_t s, boo
     fused = amg_update_first(*this, u, s) != 0;
     if (fused) ++nlaunch;
   }
-  if (!fused) EB_DIM_LAUNCH(dim, k_update_xr, nblk, tv, sc, x, r, p, q, part_pq(), nblk, part_rr());
+  if (!fused) EB_DIM_LAUNCH(dim, k_update_xr, nblk, eb->pairs(), sc, x, r, p, q, part_pq(), nblk, part_rr());
   precondition(kind, r, z, s, fused);
   const bool flex = flex_for(kind);
-  EB_DIM_LAUNCH(dim, k_xpby_apply, nblk, tv, sc, eb->code, eb->diag, op, z, p, q, flex ? zold : nullptr, 0,
-                part_rz(), rz_n, part_pq());
+  EB_DIM_LAUNCH(dim, k_xpby_apply, nblk, tv, eb->pairs(), sc, eb->code, eb->diag, op, z, p, q,
+                flex ? zold : nullptr, 0, part_rz(), rz_n, part_pq());
   // r'r and the convergence test end the iteration (the device-side loop's
   // condition kernel does it itself)
   if (!loop_end) finalize(FIN_RR, part_rr(), s);

@@ -64,6 +64,13 @@ __device__ __forceinline__ bool tile_pair(const TileView& tv, int64_t tt, int t,
   return 2 * px < (lim & 0xFF) && ly < ((lim >> 8) & 0xFF) && lz < ((lim >> 16) & 0xFF);
 }
 
+// The node pairs of the tile view (pair layout, first node even) that hold
+// at least one CP, in tile order and, within a tile, in pair order.
+struct PairList {
+  const int32_t* node = nullptr;
+  int64_t n = 0;
+};
+
 }  // namespace ebk
 
 // for (each listed tile of this CTA) if (this thread's node is in the grid) body
@@ -75,3 +82,10 @@ __device__ __forceinline__ bool tile_pair(const TileView& tv, int64_t tt, int t,
 #define EB_PAIR_LOOP(DIM, tv, node)                                                                      \
   for (int64_t tt_ = 2 * (int64_t)blockIdx.x + (threadIdx.x >> 7); tt_ < (tv).ntiles; tt_ += 2 * (int64_t)gridDim.x) \
     if (int32_t node = 0; ::ebk::tile_pair<DIM>((tv), tt_, threadIdx.x & 127, node))
+
+// for (each pair of the list given to this thread: grid-stride) body; node
+// and node + 1 belong to this thread
+#define EB_LIST_LOOP(pl, node)                                                                              \
+  for (int64_t li_ = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li_ < (pl).n;                          \
+       li_ += (int64_t)gridDim.x * blockDim.x)                                                              \
+    if (const int32_t node = __ldg((pl).node + li_); true)
