@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_first(TileView tv, const 
   }
 }
 
-// The PCG's x += alpha p, r -= alpha q and r'r partials (k_update_xr, same
+// The PCG's x += alpha h2 p, r -= alpha q and r'r partials (k_update_xr, same
 // grid, same pair list and order: the same values and partials) followed, per
 // node pair, by k_g_cheb_first on the new r: b_out = (V) r; x = d = D^-1 b /
 // theta.  It runs over the CP pairs only (single grids): the entries of pairs
@@ -128,12 +128,13 @@ __global__ void __launch_bounds__(TILE_NODES) k_update_first(PairList pl, PcgUpd
     return;
   }
   const double alpha = pcg_alpha(u.sc, u.pq_part, u.nblk, sm, &s_alpha);
+  const double ax = alpha * u.h2;  // q holds h^2 (sigma I + A) p
   double srr = 0.0;
   EB_LIST_LOOP(pl, node) {
     const Two<double> rv = ld2d(u.r + node), qv = LdRO::ld2(u.q + node), pv = LdRO::ld2(u.p + node),
                       xv = ld2d(u.x + node);
     const double r0 = rv.x - alpha * qv.x, r1 = rv.y - alpha * qv.y;
-    st2(u.x + node, xv.x + alpha * pv.x, xv.y + alpha * pv.y);
+    st2(u.x + node, xv.x + ax * pv.x, xv.y + ax * pv.y);
     st2(u.r + node, r0, r1);
     srr += r0 * r0 + r1 * r1;
     const GOp<A>& ot = o;

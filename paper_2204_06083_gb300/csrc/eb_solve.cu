@@ -21,6 +21,7 @@ namespace ebk {
 
 struct OpParams {
   double inv_h2, sigma, dinv_int;
+  double sigma_h2;  // sigma h^2: the shift of the unit stencil h^2 (sigma I + A)
 };
 
 // (sigma I + A) x for the pair at node
@@ -31,6 +32,19 @@ __device__ __forceinline__ void op_pair(const TileView& tv, const double* x, int
   stencil_pair<DIM, LdRO>(x, node, tv.nn, c0, c1, diag, tv.sy, tv.sz, xc, core);
   ax.x = core.x * o.inv_h2 + o.sigma * xc.x;
   ax.y = core.y * o.inv_h2 + o.sigma * xc.y;
+}
+
+// h^2 (sigma I + A) x for the pair at node: the unit stencil D_k x_k - sum of
+// the CP-neighbour values, plus sigma h^2 x_k when SHIFT
+template <int DIM, bool SHIFT>
+__device__ __forceinline__ void op_pair_unit(const TileView& tv, const double* x, int32_t node, uint32_t c0,
+                                             uint32_t c1, const double* diag, double sigma_h2, Two<double>& xc,
+                                             Two<double>& ax) {
+  stencil_pair<DIM, LdRO>(x, node, tv.nn, c0, c1, diag, tv.sy, tv.sz, xc, ax);
+  if (SHIFT) {
+    ax.x += sigma_h2 * xc.x;
+    ax.y += sigma_h2 * xc.y;
+  }
 }
 
 // r = b - (sigma I + A) x  (b masked to the CPs); partials (b.b, r.r)
@@ -60,11 +74,13 @@ __global__ void __launch_bounds__(TILE_NODES) k_resid(TileView tv, const uint8_t
 }
 
 // alpha = rz / p'q from the partials of k_xpby_apply (every CTA; CTA 0 records
-// pq, alpha and a breakdown); x += alpha p; r -= alpha q; partial r.r
+// pq, alpha and a breakdown); x += alpha h2 p; r -= alpha q; partial r.r.  q
+// holds h^2 (sigma I + A) p (k_xpby_apply), so this alpha is the CG step
+// length divided by h2 = h^2.
 template <int DIM>
 __global__ void __launch_bounds__(TILE_NODES) k_update_xr(PairList pl, PcgScalars* sc, double* x, double* r,
                                                           const double* p, const double* q, const double* pq_part,
-                                                          int nblk, double* part) {
+                                                          int nblk, double* part, double h2) {
   __shared__ double sm[32];
   __shared__ double s_alpha;
   if (sc->done) {
@@ -72,11 +88,12 @@ __global__ void __launch_bounds__(TILE_NODES) k_update_xr(PairList pl, PcgScalar
     return;
   }
   const double alpha = pcg_alpha(sc, pq_part, nblk, sm, &s_alpha);
+  const double ax = alpha * h2;
   double s = 0.0;
   EB_LIST_LOOP(pl, node) {
     const Two<double> rv = ld2d(r + node), qv = LdRO::ld2(q + node), pv = LdRO::ld2(p + node), xv = ld2d(x + node);
     const double r0 = rv.x - alpha * qv.x, r1 = rv.y - alpha * qv.y;
-    st2(x + node, xv.x + alpha * pv.x, xv.y + alpha * pv.y);
+    st2(x + node, xv.x + ax * pv.x, xv.y + ax * pv.y);
     st2(r + node, r0, r1);
     s += r0 * r0 + r1 * r1;
   }
@@ -141,13 +158,16 @@ __global__ void __launch_bounds__(TILE_NODES) k_dot2(TileView tv, const double* 
 // (Fletcher-Reeves) or (r.z - r.zold) / rz (Polak-Ribiere), computed by every
 // CTA (CTA 0 records beta, the next rz and a breakdown), p = z + beta p, zold
 // = z (flexible CG), and the operator apply of the next iteration formed as
-// q = (sigma I + A) z + beta q -- in exact arithmetic (sigma I + A)(z + beta
-// p), since q holds (sigma I + A) p -- with the partials of p.q.  The stencil
-// then reads z, which the preconditioner launch before has completed, instead
-// of the p this launch writes, so the p update and the apply need no launch
-// boundary between them.  first: beta = 0, p = z, q = (sigma I + A) z (the
-// old p and q are not read).
-template <int DIM>
+// q = B z + beta q with B = h^2 (sigma I + A) -- in exact arithmetic B (z +
+// beta p), since q holds B p -- with the partials of p.q.  The stencil then
+// reads z, which the preconditioner launch before has completed, instead of
+// the p this launch writes, so the p update and the apply need no launch
+// boundary between them.  B is the unit stencil (no 1/h^2 multiply; the
+// update kernels take the step as alpha h^2 for x), and SHIFT = false drops
+// its sigma term for Poisson: two FP64 operations fewer per node on GB300's
+// narrow FP64 pipe.  first: beta = 0, p = z, q = B z (the old p and q are not
+// read).
+template <int DIM, bool SHIFT>
 __global__ void __launch_bounds__(TILE_NODES) k_xpby_apply(TileView tv, PairList pl, PcgScalars* sc,
                                                            const uint8_t* code, const double* diag, OpParams o,
                                                            const double* z, double* p, double* q, double* zold,
@@ -183,7 +203,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_xpby_apply(TileView tv, PairList
     uint32_t c0, c1;
     ld_codes(code, node, c0, c1);
     Two<double> zc, az;
-    op_pair<DIM>(tv, z, node, c0, c1, diag, o, zc, az);
+    op_pair_unit<DIM, SHIFT>(tv, z, node, c0, c1, diag, o.sigma_h2, zc, az);
     double p0 = zc.x, p1 = zc.y, q0 = az.x, q1 = az.y;
     if (!first) {
       const Two<double> pv = ld2d(p + node), qv = ld2d(q + node);
@@ -326,6 +346,7 @@ static OpParams op_params(const Solver& S) {
   o.inv_h2 = 1.0 / (G.h * G.h);
   o.sigma = S.shift;
   o.dinv_int = 1.0 / (S.shift + 2.0 * G.dim * o.inv_h2);
+  o.sigma_h2 = S.shift * G.h * G.h;
   return o;
 }
 
@@ -446,8 +467,7 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
     precondition(kind, r, z, s);
     const bool flex = flex_for(kind);
     finalize(flex ? FIN_RZ0F : FIN_RZ0, part_rz(), s, rz_n);
-    EB_DIM_LAUNCH(dim, k_xpby_apply, nblk, tv, eb->pairs(), sc, eb->code, eb->diag, op, z, p, q,
-                  flex ? zold : nullptr, 1, part_rz(), rz_n, part_pq());
+    xpby_apply(op, flex ? zold : nullptr, 1, s);
     int it = 0;
     bool stop = false;
     if (o.use_graph == 1 && !prof_on) {  // the whole loop on the device
@@ -533,6 +553,29 @@ int Solver::heat(double dt, double theta, const double* b1, const double* b0, do
 }
 
 // One PCG iteration (device-side scalars; no host synchronisation).
+void Solver::xpby_apply(const OpParams& op, double* zo, int first, cudaStream_t s) {
+  const TileView tv = eb->tv();
+  const PairList pl = eb->pairs();
+  const unsigned g = (unsigned)nblk;
+  const bool shift = op.sigma_h2 != 0.0;
+  ++nlaunch;
+  if (eb->g.dim == 2) {
+    if (shift)
+      k_xpby_apply<2, true><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, eb->code, eb->diag, op, z, p, q, zo, first, part_rz(),
+                                                     rz_n, part_pq());
+    else
+      k_xpby_apply<2, false><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, eb->code, eb->diag, op, z, p, q, zo, first,
+                                                      part_rz(), rz_n, part_pq());
+  } else {
+    if (shift)
+      k_xpby_apply<3, true><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, eb->code, eb->diag, op, z, p, q, zo, first, part_rz(),
+                                                     rz_n, part_pq());
+    else
+      k_xpby_apply<3, false><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, eb->code, eb->diag, op, z, p, q, zo, first,
+                                                      part_rz(), rz_n, part_pq());
+  }
+}
+
 void Solver::iteration(int kind, const double* b, double* x, cudaStream_t s, bool loop_end) {
   (void)b;
   const int dim = eb->g.dim;
@@ -552,14 +595,15 @@ void Solver::iteration(int kind, const double* b, double* x, cudaStream_t s, boo
     u.pq_part = part_pq();
     u.nblk = nblk;
     u.rr_part = part_rr();
+    u.h2 = eb->g.h * eb->g.h;
     fused = amg_update_first(*this, u, s) != 0;
     if (fused) ++nlaunch;
   }
-  if (!fused) EB_DIM_LAUNCH(dim, k_update_xr, nblk, eb->pairs(), sc, x, r, p, q, part_pq(), nblk, part_rr());
+  if (!fused)
+    EB_DIM_LAUNCH(dim, k_update_xr, nblk, eb->pairs(), sc, x, r, p, q, part_pq(), nblk, part_rr(), eb->g.h * eb->g.h);
   precondition(kind, r, z, s, fused);
   const bool flex = flex_for(kind);
-  EB_DIM_LAUNCH(dim, k_xpby_apply, nblk, tv, eb->pairs(), sc, eb->code, eb->diag, op, z, p, q,
-                flex ? zold : nullptr, 0, part_rz(), rz_n, part_pq());
+  xpby_apply(op, flex ? zold : nullptr, 0, s);
   // r'r and the convergence test end the iteration (the device-side loop's
   // condition kernel does it itself)
   if (!loop_end) finalize(FIN_RR, part_rr(), s);

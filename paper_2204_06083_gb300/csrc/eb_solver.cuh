@@ -27,6 +27,7 @@ struct PcgScalars {
 };
 
 struct Hierarchy;  // AMG levels (amg.cu)
+struct OpParams;   // operator constants of the PCG kernels (eb_solve.cu)
 
 struct Solver {
   EBHandle* eb = nullptr;
@@ -98,6 +99,9 @@ struct Solver {
   void prof_end(pcg_stats* st, cudaStream_t s);
   void prof_release();
   void iteration(int kind, const double* b, double* x, cudaStream_t s, bool loop_end = false);
+  // p = z + beta p and q = h^2 (sigma I + A) z + beta q with the p.q partials
+  // (eb_solve.cu); zo: the zold buffer of the flexible beta, or null
+  void xpby_apply(const OpParams& op, double* zo, int first, cudaStream_t s);
   void graph_prepare(int kind, const double* b, double* x, int iters, int profile, cudaStream_t s);
   void graph_release();
   void loop_prepare(int kind, const double* b, double* x, cudaStream_t s);
@@ -136,7 +140,8 @@ __device__ __forceinline__ double sum_parts(const double* part, int n, int strid
   return block_sum(a, sm);
 }
 
-// alpha = rz / p'q from the nblk partials of k_xpby_apply, formed by every CTA in
+// alpha = rz / p'q from the nblk partials of k_xpby_apply (q scaled by h^2:
+// the CG step length over h^2), formed by every CTA in
 // the same order; CTA 0 records p'q, alpha and a breakdown (p'q <= 0 or not
 // finite).  All threads of the CTA call it; returns alpha to every thread.
 __device__ __forceinline__ double pcg_alpha(PcgScalars* sc, const double* pq_part, int nblk, double* sm,
@@ -169,6 +174,7 @@ struct PcgUpdate {
   const double *p = nullptr, *q = nullptr, *pq_part = nullptr;
   int nblk = 0;
   double* rr_part = nullptr;
+  double h2 = 1.0;  // q holds h2 (sigma I + A) p: x takes the step alpha h2
 };
 int amg_update_first(Solver& S, const PcgUpdate& u, cudaStream_t s);
 
