@@ -109,7 +109,8 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_first(TileView tv, const 
   }
 }
 
-// The PCG's x += alpha h2 p, r -= alpha q and r'r partials (k_update_xr, same
+// The PCG's x += alpha h2 p, r -= alpha q, r'r (and, flexible, r'zold)
+// partials (k_update_xr, same
 // grid, same pair list and order: the same values and partials) followed, per
 // node pair, by k_g_cheb_first on the new r: b_out = (V) r; x = d = D^-1 b /
 // theta.  It runs over the CP pairs only (single grids): the entries of pairs
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_update_first(PairList pl, PcgUpd
   }
   const double alpha = pcg_alpha(u.sc, u.pq_part, u.nblk, sm, &s_alpha);
   const double ax = alpha * u.h2;  // q holds h^2 (sigma I + A) p
-  double srr = 0.0;
+  double srr = 0.0, srzo = 0.0;
   EB_LIST_LOOP(pl, node) {
     const Two<double> rv = ld2d(u.r + node), qv = LdRO::ld2(u.q + node), pv = LdRO::ld2(u.p + node),
                       xv = ld2d(u.x + node);
@@ -137,6 +138,10 @@ __global__ void __launch_bounds__(TILE_NODES) k_update_first(PairList pl, PcgUpd
     st2(u.x + node, xv.x + ax * pv.x, xv.y + ax * pv.y);
     st2(u.r + node, r0, r1);
     srr += r0 * r0 + r1 * r1;
+    if (u.rzo_part) {
+      const Two<double> zv = LdRO::ld2(u.z + node);
+      srzo += r0 * zv.x + r1 * zv.y;
+    }
     const GOp<A>& ot = o;
     uint32_t c0, c1;
     ld_codes(code, node, c0, c1);
@@ -147,14 +152,17 @@ __global__ void __launch_bounds__(TILE_NODES) k_update_first(PairList pl, PcgUpd
     st2o(x0 + node, v0, v1);
     st2o(d + node, v0, v1);
   }
+  if (u.rzo_part) {
+    const double t = block_sum(srzo, sm);
+    if (threadIdx.x == 0) u.rzo_part[blockIdx.x] = t;
+  }
   const double t = block_sum(srr, sm);
   if (threadIdx.x == 0) u.rr_part[blockIdx.x] = t;
 }
 
 // res = D^-1 (b - A x); d = c1 d + c2 res; xo = x + d   (xo may be FP64).
-// DOT (xo FP64, the V-cycle's output z): also the CTA's partial r.z and, with
-// zold, r.zold (pairs), summed over its node pairs in loop order exactly as
-// the PCG's own dot kernels do.
+// DOT (xo FP64, the V-cycle's output z): also the CTA's partial r.z, summed
+// over its node pairs in loop order exactly as the PCG's own dot kernel does.
 template <int DIM, class V, class O, bool DOT = false>
 __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_step(TileView tv, const uint8_t* __restrict__ code,
                                                             const typename DiagOf<V>::type* __restrict__ diag,
@@ -163,10 +171,9 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_step(TileView tv, const u
                                                             O* __restrict__ xo, V* __restrict__ d,
                                                             typename AccOf<V>::type c1, typename AccOf<V>::type c2,
                                                             const double* __restrict__ r64 = nullptr,
-                                                            const double* __restrict__ zold = nullptr,
                                                             double* __restrict__ part = nullptr) {
   using A = typename AccOf<V>::type;
-  double srz = 0.0, srzo = 0.0;
+  double srz = 0.0;
   EB_PAIR_LOOP(DIM, tv, node) {
     const GOp<A> ot = tile_op(tv, tt_, o);
     uint32_t k0, k1;
@@ -189,24 +196,12 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_step(TileView tv, const u
     if (DOT) {
       const Two<double> rv = LdRO::ld2(r64 + node);
       srz += rv.x * (double)z0 + rv.y * (double)z1;
-      if (zold) {
-        const Two<double> ov = LdRO::ld2(zold + node);
-        srzo += rv.x * ov.x + rv.y * ov.y;
-      }
     }
   }
   if (DOT) {
     __shared__ double sm[32];
     const double a = block_sum(srz, sm);
-    if (zold) {
-      const double t = block_sum(srzo, sm);
-      if (threadIdx.x == 0) {
-        part[2 * blockIdx.x] = a;
-        part[2 * blockIdx.x + 1] = t;
-      }
-    } else if (threadIdx.x == 0) {
-      part[blockIdx.x] = a;
-    }
+    if (threadIdx.x == 0) part[blockIdx.x] = a;
   }
 }
 
@@ -661,7 +656,7 @@ static int vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, co
     if (mark) S.prof_mark(s, true);
     if (k == cc.deg - 1 && dot)
       k_g_cheb_step<DIM, V, double, true><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, x, z, g.d, (A)cc.c1[k],
-                                                                    (A)cc.c2[k], dot->r, dot->zold, dot->part);
+                                                                    (A)cc.c2[k], dot->r, dot->part);
     else if (k == cc.deg - 1)
       k_g_cheb_step<DIM, V, double>
           <<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, x, z, g.d, (A)cc.c1[k], (A)cc.c2[k]);

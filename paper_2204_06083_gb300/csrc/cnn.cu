@@ -1454,7 +1454,6 @@ int pcg_solve_nn(const amg_handle* amg, nn_handle* nn, int mode, const double* b
     Solver& S = const_cast<Solver&>(amg->s);
     EB_REQUIRE(S.H != nullptr, EB_ERR_INVALID, "pcg_solve_nn: handle has no hierarchy");
     nn_stage_prepare(nn, *S.eb, stream);
-    if (!S.zold) S.zold = dalloc<double>(S.eb->g.num_nodes, stream);
     S.nn = nn;
     S.nn_mode = mode;
     try {

@@ -76,11 +76,14 @@ __global__ void __launch_bounds__(TILE_NODES) k_resid(TileView tv, const uint8_t
 // alpha = rz / p'q from the partials of k_xpby_apply (every CTA; CTA 0 records
 // pq, alpha and a breakdown); x += alpha h2 p; r -= alpha q; partial r.r.  q
 // holds h^2 (sigma I + A) p (k_xpby_apply), so this alpha is the CG step
-// length divided by h2 = h^2.
+// length divided by h2 = h^2.  With rzo_part (flexible CG), also the partial
+// of r.z for the new r and the z of the iteration ending (still in z): the
+// r.zold term of the Polak-Ribiere beta.
 template <int DIM>
 __global__ void __launch_bounds__(TILE_NODES) k_update_xr(PairList pl, PcgScalars* sc, double* x, double* r,
                                                           const double* p, const double* q, const double* pq_part,
-                                                          int nblk, double* part, double h2) {
+                                                          int nblk, double* part, double h2, const double* z,
+                                                          double* rzo_part) {
   __shared__ double sm[32];
   __shared__ double s_alpha;
   if (sc->done) {
@@ -89,13 +92,21 @@ __global__ void __launch_bounds__(TILE_NODES) k_update_xr(PairList pl, PcgScalar
   }
   const double alpha = pcg_alpha(sc, pq_part, nblk, sm, &s_alpha);
   const double ax = alpha * h2;
-  double s = 0.0;
+  double s = 0.0, so = 0.0;
   EB_LIST_LOOP(pl, node) {
     const Two<double> rv = ld2d(r + node), qv = LdRO::ld2(q + node), pv = LdRO::ld2(p + node), xv = ld2d(x + node);
     const double r0 = rv.x - alpha * qv.x, r1 = rv.y - alpha * qv.y;
     st2(x + node, xv.x + ax * pv.x, xv.y + ax * pv.y);
     st2(r + node, r0, r1);
     s += r0 * r0 + r1 * r1;
+    if (rzo_part) {
+      const Two<double> zv = LdRO::ld2(z + node);
+      so += r0 * zv.x + r1 * zv.y;
+    }
+  }
+  if (rzo_part) {
+    const double t = block_sum(so, sm);
+    if (threadIdx.x == 0) rzo_part[blockIdx.x] = t;
   }
   const double t = block_sum(s, sm);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
@@ -132,32 +143,11 @@ __global__ void __launch_bounds__(TILE_NODES) k_dot(TileView tv, const double* a
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
-// partials (r.z, r.zold) for the flexible beta
-template <int DIM>
-__global__ void __launch_bounds__(TILE_NODES) k_dot2(TileView tv, const double* r, const double* z, const double* zo,
-                                                     double* part) {
-  __shared__ double sm[32];
-  double s = 0.0, t = 0.0;
-  EB_PAIR_LOOP(DIM, tv, node) {
-    const Two<double> rv = LdRO::ld2(r + node), zv = LdRO::ld2(z + node), ov = LdRO::ld2(zo + node);
-    s += rv.x * zv.x + rv.y * zv.y;
-    t += rv.x * ov.x + rv.y * ov.y;
-  }
-  const double a = block_sum(s, sm);
-  const double b = block_sum(t, sm);
-  if (threadIdx.x == 0) {
-    part[2 * blockIdx.x] = a;
-    part[2 * blockIdx.x + 1] = b;
-  }
-}
-
-// p = z + beta p   (p = z on the first iteration of a cycle); zold = z when
-// zold is given (flexible CG).  Otherwise beta comes from the partials of the
-// preconditioner's dot kernel (pairs (r.z, r.zold) when flexible): beta =
 // The end of a PCG iteration in one pass over the CP pairs: beta = r.z / rz
-// (Fletcher-Reeves) or (r.z - r.zold) / rz (Polak-Ribiere), computed by every
-// CTA (CTA 0 records beta, the next rz and a breakdown), p = z + beta p, zold
-// = z (flexible CG), and the operator apply of the next iteration formed as
+// (Fletcher-Reeves), or (r.z - r.zold) / rz (Polak-Ribiere, flexible CG: the
+// r.zold partials come from the x/r update), computed by every CTA (CTA 0
+// records beta, the next rz and a breakdown), p = z + beta p, and the
+// operator apply of the next iteration formed as
 // q = B z + beta q with B = h^2 (sigma I + A) -- in exact arithmetic B (z +
 // beta p), since q holds B p -- with the partials of p.q.  The stencil then
 // reads z, which the preconditioner launch before has completed, instead of
@@ -170,17 +160,16 @@ __global__ void __launch_bounds__(TILE_NODES) k_dot2(TileView tv, const double* 
 template <int DIM, bool SHIFT>
 __global__ void __launch_bounds__(TILE_NODES) k_xpby_apply(TileView tv, PairList pl, PcgScalars* sc,
                                                            const uint8_t* code, const double* diag, OpParams o,
-                                                           const double* z, double* p, double* q, double* zold,
-                                                           int first, const double* rz_part, int nblk,
-                                                           double* pq_part) {
+                                                           const double* z, double* p, double* q, int first,
+                                                           const double* rz_part, int nrz, const double* rzo_part,
+                                                           int nrzo, double* pq_part) {
   __shared__ double sm[32];
   __shared__ double s_beta;
   if (sc->done) return;
   if (!first) {
-    const int stride = zold ? 2 : 1;
-    const double v = sum_parts(rz_part, nblk, stride, sm);
+    const double v = sum_parts(rz_part, nrz, 1, sm);
     __syncthreads();
-    const double t = zold ? sum_parts(rz_part + 1, nblk, 2, sm) : 0.0;
+    const double t = rzo_part ? sum_parts(rzo_part, nrzo, 1, sm) : 0.0;
     if (threadIdx.x == 0) {
       const int k = sc->iters & 1;
       const bool ok = v > 0.0;
@@ -216,7 +205,6 @@ __global__ void __launch_bounds__(TILE_NODES) k_xpby_apply(TileView tv, PairList
     q1 = (c1 & CODE_CP) ? q1 : 0.0;
     st2(p + node, p0, p1);
     st2(q + node, q0, q1);
-    if (zold) st2(zold + node, zc.x, zc.y);
     s += p0 * q0 + p1 * q1;
   }
   const double t = block_sum(s, sm);
@@ -266,7 +254,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_mask_copy(TileView tv, const uin
 __global__ void k_finalize(const double* part, int nblk, int op, PcgScalars* sc) {
   __shared__ double sm[2][1024];
   double a = 0.0, b = 0.0;
-  const bool pairs = op == FIN_INIT || op == FIN_RZ0F || op == FIN_BETAF;
+  const bool pairs = op == FIN_INIT;
   const int stride = pairs ? 2 : 1;
   for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
     a += part[stride * i];
@@ -292,7 +280,6 @@ __global__ void k_finalize(const double* part, int nblk, int op, PcgScalars* sc)
       sc->done = (sm[1][0] <= sc->tol2 * v) ? 1 : 0;
       break;
     case FIN_RZ0:
-    case FIN_RZ0F:
       sc->rz[sc->iters & 1] = v;
       if (!isfinite(v)) sc->flags |= PCG_FLAG_NONFINITE;
       break;
@@ -357,11 +344,11 @@ void Solver::alloc_work(cudaStream_t s) {
   p = dalloc<double>(nn, s);
   q = dalloc<double>(nn, s);
   tmp = dalloc<double>(nn, s);
-  if (opts.vcycle_prec != EB_F64) zold = dalloc<double>(nn, s);
   nblk = (int)std::min<int64_t>(std::max<int64_t>(eb->num_tiles, 1), (int64_t)num_sms() * 4);
-  // p'q and r'r regions of 2 nblk, then r'z of 2 max(nblk, 8 SMs) (the V-cycle's
-  // grid sweeps use at most 8 CTAs per SM)
-  part = dalloc<double>(4 * (int64_t)nblk + 2 * std::max<int64_t>(nblk, (int64_t)num_sms() * 8), s);
+  // p'q and r'r regions of 2 nblk, r'z of 2 max(nblk, 8 SMs) (the V-cycle's
+  // grid sweeps use at most 8 CTAs per SM), then r'zold of nblk
+  rz_cap = 2 * std::max<int64_t>(nblk, (int64_t)num_sms() * 8);
+  part = dalloc<double>(5 * (int64_t)nblk + rz_cap, s);
   sc = dalloc<PcgScalars>(1, s);
   EB_CUDA(cudaMallocHost((void**)&sc_host, sizeof(PcgScalars)));
 }
@@ -372,7 +359,7 @@ void Solver::free_work() {
   loop_release();
   if (cap_stream) cudaStreamDestroy(cap_stream);
   cap_stream = nullptr;
-  dfree(r, s); dfree(z, s); dfree(p, s); dfree(q, s); dfree(tmp, s); dfree(zold, s); dfree(part, s); dfree(sc, s);
+  dfree(r, s); dfree(z, s); dfree(p, s); dfree(q, s); dfree(tmp, s); dfree(part, s); dfree(sc, s);
   if (sc_host) cudaFreeHost(sc_host);
   sc_host = nullptr;
 }
@@ -389,22 +376,18 @@ void Solver::precondition(int kind, const double* rin, double* zout, cudaStream_
   if (kind == EB_PC_AMG_NN) {
     amg_vcycle_grid(*this, rin, zout, s);
     nn_stage_apply(nn, *eb, shift, nn_mode, rin, zout, nlaunch, this, s);
-    EB_DIM_LAUNCH(dim, k_dot2, nblk, tv, rin, zout, zold, part_rz());
+    EB_DIM_LAUNCH(dim, k_dot, nblk, tv, rin, zout, part_rz());
   } else if (kind == EB_PC_AMG && H) {
     // the V-cycle's last smoothing launch forms the r'z partials itself
     VcycleDot dot;
     dot.r = rin;
-    dot.zold = flexible() ? zold : nullptr;
     dot.part = part_rz();
     const int fused = amg_vcycle_grid(*this, rin, zout, s, &dot, first_done);
     if (fused) {
       rz_n = fused;
       return;
     }  // single-level hierarchy: no smoothing launch formed them
-    if (flexible())
-      EB_DIM_LAUNCH(dim, k_dot2, nblk, tv, rin, zout, zold, part_rz());
-    else
-      EB_DIM_LAUNCH(dim, k_dot, nblk, tv, rin, zout, part_rz());
+    EB_DIM_LAUNCH(dim, k_dot, nblk, tv, rin, zout, part_rz());
   } else if (kind == EB_PC_NONE) {
     EB_DIM_LAUNCH(dim, k_copy_tiles, nblk, tv, rin, zout);
     EB_DIM_LAUNCH(dim, k_dot, nblk, tv, rin, zout, part_rz());
@@ -421,7 +404,7 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
   const int kind = o.precond;
   EB_REQUIRE(kind == EB_PC_AMG || kind == EB_PC_JACOBI || kind == EB_PC_NONE || kind == EB_PC_AMG_NN,
              EB_ERR_INVALID, "bad preconditioner");
-  EB_REQUIRE(kind != EB_PC_AMG_NN || (nn != nullptr && zold != nullptr), EB_ERR_INVALID,
+  EB_REQUIRE(kind != EB_PC_AMG_NN || nn != nullptr, EB_ERR_INVALID,
              "the learned stage is selected by pcg_solve_nn");
   EB_REQUIRE((kind != EB_PC_AMG && kind != EB_PC_AMG_NN) || H != nullptr, EB_ERR_INVALID,
              "AMG preconditioner requested without a hierarchy");
@@ -466,8 +449,8 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
     if (total_iters >= maxit) break;
     precondition(kind, r, z, s);
     const bool flex = flex_for(kind);
-    finalize(flex ? FIN_RZ0F : FIN_RZ0, part_rz(), s, rz_n);
-    xpby_apply(op, flex ? zold : nullptr, 1, s);
+    finalize(FIN_RZ0, part_rz(), s, rz_n);
+    xpby_apply(op, flex, 1, s);
     int it = 0;
     bool stop = false;
     if (o.use_graph == 1 && !prof_on) {  // the whole loop on the device
@@ -553,26 +536,27 @@ int Solver::heat(double dt, double theta, const double* b1, const double* b0, do
 }
 
 // One PCG iteration (device-side scalars; no host synchronisation).
-void Solver::xpby_apply(const OpParams& op, double* zo, int first, cudaStream_t s) {
+void Solver::xpby_apply(const OpParams& op, bool flex, int first, cudaStream_t s) {
   const TileView tv = eb->tv();
   const PairList pl = eb->pairs();
   const unsigned g = (unsigned)nblk;
   const bool shift = op.sigma_h2 != 0.0;
+  const double* rzo = flex ? part_rzo() : nullptr;
   ++nlaunch;
   if (eb->g.dim == 2) {
     if (shift)
-      k_xpby_apply<2, true><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, eb->code, eb->diag, op, z, p, q, zo, first, part_rz(),
-                                                     rz_n, part_pq());
+      k_xpby_apply<2, true><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, eb->code, eb->diag, op, z, p, q, first, part_rz(),
+                                                     rz_n, rzo, nblk, part_pq());
     else
-      k_xpby_apply<2, false><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, eb->code, eb->diag, op, z, p, q, zo, first,
-                                                      part_rz(), rz_n, part_pq());
+      k_xpby_apply<2, false><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, eb->code, eb->diag, op, z, p, q, first, part_rz(),
+                                                      rz_n, rzo, nblk, part_pq());
   } else {
     if (shift)
-      k_xpby_apply<3, true><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, eb->code, eb->diag, op, z, p, q, zo, first, part_rz(),
-                                                     rz_n, part_pq());
+      k_xpby_apply<3, true><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, eb->code, eb->diag, op, z, p, q, first, part_rz(),
+                                                     rz_n, rzo, nblk, part_pq());
     else
-      k_xpby_apply<3, false><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, eb->code, eb->diag, op, z, p, q, zo, first,
-                                                      part_rz(), rz_n, part_pq());
+      k_xpby_apply<3, false><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, eb->code, eb->diag, op, z, p, q, first, part_rz(),
+                                                      rz_n, rzo, nblk, part_pq());
   }
 }
 
@@ -596,14 +580,17 @@ void Solver::iteration(int kind, const double* b, double* x, cudaStream_t s, boo
     u.nblk = nblk;
     u.rr_part = part_rr();
     u.h2 = eb->g.h * eb->g.h;
+    u.z = z;
+    u.rzo_part = flex_for(kind) ? part_rzo() : nullptr;
     fused = amg_update_first(*this, u, s) != 0;
     if (fused) ++nlaunch;
   }
   if (!fused)
-    EB_DIM_LAUNCH(dim, k_update_xr, nblk, eb->pairs(), sc, x, r, p, q, part_pq(), nblk, part_rr(), eb->g.h * eb->g.h);
+    EB_DIM_LAUNCH(dim, k_update_xr, nblk, eb->pairs(), sc, x, r, p, q, part_pq(), nblk, part_rr(), eb->g.h * eb->g.h, z,
+                  flex_for(kind) ? part_rzo() : nullptr);
   precondition(kind, r, z, s, fused);
   const bool flex = flex_for(kind);
-  xpby_apply(op, flex ? zold : nullptr, 0, s);
+  xpby_apply(op, flex, 0, s);
   // r'r and the convergence test end the iteration (the device-side loop's
   // condition kernel does it itself)
   if (!loop_end) finalize(FIN_RR, part_rr(), s);

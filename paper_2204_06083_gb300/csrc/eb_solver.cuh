@@ -8,7 +8,8 @@
 
 namespace ebk {
 
-// FIN_RZ0F / FIN_BETAF: flexible CG, partials are pairs (r.z, r.z_previous).
+// FIN_RZ0F / FIN_BETAF: flexible CG, partials are pairs (r.z, r.z_previous)
+// (the batched PCG; the single-grid PCG forms r.z_previous in its x/r update).
 // The single-grid PCG combines FIN_ALPHA and FIN_BETA inside its update
 // kernels; the batch finalizes every op in its per-geometry kernel.
 enum { FIN_INIT = 0, FIN_RZ0 = 1, FIN_ALPHA = 2, FIN_RR = 3, FIN_BETA = 4, FIN_RZ0F = 5, FIN_BETAF = 6 };
@@ -41,7 +42,6 @@ struct Solver {
   int csr_epl = 2;  // CSR kernels of the V-cycle: target entries per lane of a row group (amg_tune_csr)
   // full-grid work vectors (touched on the active tiles only)
   double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *tmp = nullptr;
-  double* zold = nullptr;  // previous z (flexible CG with a reduced-precision V-cycle)
   bool flexible() const { return H != nullptr && (opts.vcycle_prec == EB_F32 || opts.vcycle_prec == EB_BF16); }
   // the flexible (Polak-Ribiere) beta: reduced-precision V-cycle or learned stage
   bool flex_for(int kind) const { return kind == EB_PC_AMG_NN || (kind == EB_PC_AMG && flexible()); }
@@ -54,6 +54,9 @@ struct Solver {
   double* part_pq() const { return part; }
   double* part_rr() const { return part + 2 * (int64_t)nblk; }
   double* part_rz() const { return part + 4 * (int64_t)nblk; }
+  // r'zold partials of the flexible beta (nblk, from the x/r update)
+  double* part_rzo() const { return part + 4 * (int64_t)nblk + rz_cap; }
+  int64_t rz_cap = 0;
   int nblk = 1;
   int rz_n = 1;  // r'z partials written by the last precondition()
   PcgScalars* sc = nullptr;
@@ -100,8 +103,8 @@ struct Solver {
   void prof_release();
   void iteration(int kind, const double* b, double* x, cudaStream_t s, bool loop_end = false);
   // p = z + beta p and q = h^2 (sigma I + A) z + beta q with the p.q partials
-  // (eb_solve.cu); zo: the zold buffer of the flexible beta, or null
-  void xpby_apply(const OpParams& op, double* zo, int first, cudaStream_t s);
+  // (eb_solve.cu); flex: the Polak-Ribiere beta (r'zold partials in part_rzo)
+  void xpby_apply(const OpParams& op, bool flex, int first, cudaStream_t s);
   void graph_prepare(int kind, const double* b, double* x, int iters, int profile, cudaStream_t s);
   void graph_release();
   void loop_prepare(int kind, const double* b, double* x, cudaStream_t s);
@@ -175,16 +178,18 @@ struct PcgUpdate {
   int nblk = 0;
   double* rr_part = nullptr;
   double h2 = 1.0;  // q holds h2 (sigma I + A) p: x takes the step alpha h2
+  // flexible CG: partials of (new r).z with the z still in z (r'zold)
+  const double* z = nullptr;
+  double* rzo_part = nullptr;
 };
 int amg_update_first(Solver& S, const PcgUpdate& u, cudaStream_t s);
 
 // z = V r.  With dot, the last level-0 smoothing launch also writes per-CTA
-// partials of r.z (and of r.zold when dot->zold is set, as pairs) to
-// dot->part; returns their count, or 0 if no launch wrote them (single-level
-// hierarchy), in which case the caller computes the dot itself.
+// partials of r.z to dot->part; returns their count, or 0 if no launch wrote
+// them (single-level hierarchy), in which case the caller computes the dot
+// itself.
 struct VcycleDot {
   const double* r = nullptr;
-  const double* zold = nullptr;
   double* part = nullptr;
 };
 // first_done: amg_update_first already did the first level-0 step for this r.
