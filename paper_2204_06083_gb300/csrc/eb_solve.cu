@@ -152,7 +152,9 @@ __global__ void __launch_bounds__(TILE_NODES) k_dot(TileView tv, const double* a
 // beta p), since q holds B p -- with the partials of p.q.  The stencil then
 // reads z, which the preconditioner launch before has completed, instead of
 // the p this launch writes, so the p update and the apply need no launch
-// boundary between them.  B is the unit stencil (no 1/h^2 multiply; the
+// boundary between them.  nupd: partials per array of the x/r update (r'r,
+// r'zold).  set_cond (device-side loop): CTA 0 also does the loop test and
+// sets the loop condition h.  B is the unit stencil (no 1/h^2 multiply; the
 // update kernels take the step as alpha h^2 for x), and SHIFT = false drops
 // its sigma term for Poisson: two FP64 operations fewer per node on GB300's
 // narrow FP64 pipe.  first: beta = 0, p = z, q = B z (the old p and q are not
@@ -162,16 +164,20 @@ __global__ void __launch_bounds__(TILE_NODES) k_xpby_apply(TileView tv, PairList
                                                            const uint8_t* code, const double* diag, OpParams o,
                                                            const double* z, double* p, double* q, int first,
                                                            const double* rz_part, int nrz, const double* rzo_part,
-                                                           int nrzo, double* pq_part) {
+                                                           int nupd, double* pq_part, const double* rr_part,
+                                                           int set_cond, cudaGraphConditionalHandle h) {
   __shared__ double sm[32];
   __shared__ double s_beta;
-  if (sc->done) return;
+  if (sc->done) {
+    if (set_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+    return;
+  }
   if (!first) {
     const double v = sum_parts(rz_part, nrz, 1, sm);
     __syncthreads();
-    const double t = rzo_part ? sum_parts(rzo_part, nrzo, 1, sm) : 0.0;
+    const double t = rzo_part ? sum_parts(rzo_part, nupd, 1, sm) : 0.0;
     if (threadIdx.x == 0) {
-      const int k = sc->iters & 1;
+      const int k = sc->slot;  // not sc->iters: CTA 0 of this launch may advance it
       const bool ok = v > 0.0;
       const double beta = ok ? (v - t) / sc->rz[k] : 0.0;
       s_beta = beta;
@@ -187,6 +193,26 @@ __global__ void __launch_bounds__(TILE_NODES) k_xpby_apply(TileView tv, PairList
     __syncthreads();
   }
   const double beta = first ? 0.0 : s_beta;
+  if (set_cond && blockIdx.x == 0) {
+    // the device-side loop's test, after the beta breakdown check: r'r of
+    // this iteration's update, then continue while not converged (or broken
+    // down) and below the iteration limit.  CTAs that start after it and see
+    // done skip the p, q update, which a finished loop does not use.
+    const double v = sum_parts(rr_part, nupd, 1, sm);
+    if (threadIdx.x == 0) {
+      if (!sc->done) {
+        sc->rr = v;
+        sc->iters += 1;
+        if (!isfinite(v)) {
+          sc->flags |= PCG_FLAG_NONFINITE;
+          sc->done = 1;
+        } else if (v <= sc->tol2 * sc->bb) {
+          sc->done = 1;
+        }
+      }
+      cudaGraphSetConditional(h, (!sc->done && sc->iters < sc->maxit) ? 1u : 0u);
+    }
+  }
   double s = 0.0;
   EB_LIST_LOOP(pl, node) {
     uint32_t c0, c1;
@@ -295,26 +321,6 @@ __global__ void k_finalize(const double* part, int nblk, int op, PcgScalars* sc)
       }
       break;
   }
-}
-
-// end of a device-side loop iteration: r'r from the partials of k_update_xr
-// (FIN_RR of k_finalize), then the loop condition: continue while not
-// converged (or broken down) and below the iteration limit
-__global__ void k_loop_cond(cudaGraphConditionalHandle h, const double* part, int nblk, PcgScalars* sc) {
-  __shared__ double sm[32];
-  const double v = sum_parts(part, nblk, 1, sm);
-  if (threadIdx.x != 0) return;
-  if (!sc->done) {
-    sc->rr = v;
-    sc->iters += 1;
-    if (!isfinite(v)) {
-      sc->flags |= PCG_FLAG_NONFINITE;
-      sc->done = 1;
-    } else if (v <= sc->tol2 * sc->bb) {
-      sc->done = 1;
-    }
-  }
-  cudaGraphSetConditional(h, (!sc->done && sc->iters < sc->maxit) ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------- host side
@@ -536,31 +542,35 @@ int Solver::heat(double dt, double theta, const double* b1, const double* b0, do
 }
 
 // One PCG iteration (device-side scalars; no host synchronisation).
-void Solver::xpby_apply(const OpParams& op, bool flex, int first, cudaStream_t s) {
+void Solver::xpby_apply(const OpParams& op, bool flex, int first, cudaStream_t s,
+                        const cudaGraphConditionalHandle* cond) {
   const TileView tv = eb->tv();
   const PairList pl = eb->pairs();
   const unsigned g = (unsigned)nblk;
   const bool shift = op.sigma_h2 != 0.0;
   const double* rzo = flex ? part_rzo() : nullptr;
+  const int sc_ = cond ? 1 : 0;
+  const cudaGraphConditionalHandle h = cond ? *cond : cudaGraphConditionalHandle{};
   ++nlaunch;
   if (eb->g.dim == 2) {
     if (shift)
       k_xpby_apply<2, true><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, eb->code, eb->diag, op, z, p, q, first, part_rz(),
-                                                     rz_n, rzo, nblk, part_pq());
+                                                     rz_n, rzo, nblk, part_pq(), part_rr(), sc_, h);
     else
       k_xpby_apply<2, false><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, eb->code, eb->diag, op, z, p, q, first, part_rz(),
-                                                      rz_n, rzo, nblk, part_pq());
+                                                      rz_n, rzo, nblk, part_pq(), part_rr(), sc_, h);
   } else {
     if (shift)
       k_xpby_apply<3, true><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, eb->code, eb->diag, op, z, p, q, first, part_rz(),
-                                                     rz_n, rzo, nblk, part_pq());
+                                                     rz_n, rzo, nblk, part_pq(), part_rr(), sc_, h);
     else
       k_xpby_apply<3, false><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, eb->code, eb->diag, op, z, p, q, first, part_rz(),
-                                                      rz_n, rzo, nblk, part_pq());
+                                                      rz_n, rzo, nblk, part_pq(), part_rr(), sc_, h);
   }
 }
 
-void Solver::iteration(int kind, const double* b, double* x, cudaStream_t s, bool loop_end) {
+void Solver::iteration(int kind, const double* b, double* x, cudaStream_t s,
+                       const cudaGraphConditionalHandle* cond) {
   (void)b;
   const int dim = eb->g.dim;
   const TileView tv = eb->tv();
@@ -590,10 +600,10 @@ void Solver::iteration(int kind, const double* b, double* x, cudaStream_t s, boo
                   flex_for(kind) ? part_rzo() : nullptr);
   precondition(kind, r, z, s, fused);
   const bool flex = flex_for(kind);
-  xpby_apply(op, flex, 0, s);
-  // r'r and the convergence test end the iteration (the device-side loop's
-  // condition kernel does it itself)
-  if (!loop_end) finalize(FIN_RR, part_rr(), s);
+  // r'r and the convergence test end the iteration: in the device-side loop
+  // the p, q launch does them and sets the loop condition
+  xpby_apply(op, flex, 0, s, cond);
+  if (!cond) finalize(FIN_RR, part_rr(), s);
 }
 
 // Captures `iters` iterations into a CUDA graph (once per argument set).  The
@@ -689,11 +699,8 @@ void Solver::loop_prepare(int kind, const double* b, double* x, cudaStream_t s) 
   (void)s;  // capturing runs nothing; the graph is launched on s
   if (!cap_stream) EB_CUDA(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
   const int64_t n0 = nlaunch;
-  lexec = build_while_graph(cap_stream, [&](cudaStream_t cs, cudaGraphConditionalHandle h) {
-    iteration(kind, b, x, cs, true);
-    k_loop_cond<<<1, 256, 0, cs>>>(h, part_rr(), nblk, sc);
-    ++nlaunch;
-  });
+  lexec = build_while_graph(cap_stream,
+                            [&](cudaStream_t cs, cudaGraphConditionalHandle h) { iteration(kind, b, x, cs, &h); });
   l_launches = nlaunch - n0;
   nlaunch = n0;
   l_b = b;

@@ -25,6 +25,9 @@ struct PcgScalars {
   double bb, rr, rz[2], pq, alpha, beta, tol2;
   int iters, flags, done;
   int maxit;  // iteration limit of the device-side loop (counted like iters)
+  // iters & 1 as the x/r update of the iteration saw it: the r'z slot of the
+  // p update, whose launch may also advance iters (device-side loop)
+  int slot;
 };
 
 struct Hierarchy;  // AMG levels (amg.cu)
@@ -101,10 +104,13 @@ struct Solver {
   void prof_collect(int first, int count);
   void prof_end(pcg_stats* st, cudaStream_t s);
   void prof_release();
-  void iteration(int kind, const double* b, double* x, cudaStream_t s, bool loop_end = false);
+  // cond: inside the device-side loop, the handle its last launch sets
+  void iteration(int kind, const double* b, double* x, cudaStream_t s,
+                 const cudaGraphConditionalHandle* cond = nullptr);
   // p = z + beta p and q = h^2 (sigma I + A) z + beta q with the p.q partials
   // (eb_solve.cu); flex: the Polak-Ribiere beta (r'zold partials in part_rzo)
-  void xpby_apply(const OpParams& op, bool flex, int first, cudaStream_t s);
+  void xpby_apply(const OpParams& op, bool flex, int first, cudaStream_t s,
+                  const cudaGraphConditionalHandle* cond = nullptr);
   void graph_prepare(int kind, const double* b, double* x, int iters, int profile, cudaStream_t s);
   void graph_release();
   void loop_prepare(int kind, const double* b, double* x, cudaStream_t s);
@@ -157,6 +163,7 @@ __device__ __forceinline__ double pcg_alpha(PcgScalars* sc, const double* pq_par
     if (blockIdx.x == 0) {
       sc->pq = pq;
       sc->alpha = alpha;
+      sc->slot = sc->iters & 1;
       if (!ok) {
         sc->flags |= isfinite(pq) ? PCG_FLAG_BREAKDOWN : PCG_FLAG_NONFINITE;
         sc->done = 1;
