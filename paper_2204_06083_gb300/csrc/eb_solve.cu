@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <type_traits>
 
 namespace ebk {
 
@@ -153,23 +154,24 @@ __global__ void __launch_bounds__(TILE_NODES) k_dot(TileView tv, const double* a
 // reads z, which the preconditioner launch before has completed, instead of
 // the p this launch writes, so the p update and the apply need no launch
 // boundary between them.  nupd: partials per array of the x/r update (r'r,
-// r'zold).  set_cond (device-side loop): CTA 0 also does the loop test and
-// sets the loop condition h.  B is the unit stencil (no 1/h^2 multiply; the
+// r'zold).  COND (device-side loop): CTA 0 also does the loop test and sets
+// the loop condition h (a separate instance: profilers cannot replay graph
+// kernel nodes that may set a condition).  B is the unit stencil (no 1/h^2 multiply; the
 // update kernels take the step as alpha h^2 for x), and SHIFT = false drops
 // its sigma term for Poisson: two FP64 operations fewer per node on GB300's
 // narrow FP64 pipe.  first: beta = 0, p = z, q = B z (the old p and q are not
 // read).
-template <int DIM, bool SHIFT>
+template <int DIM, bool SHIFT, bool COND>
 __global__ void __launch_bounds__(TILE_NODES) k_xpby_apply(TileView tv, PairList pl, PcgScalars* sc,
                                                            const uint8_t* code, const double* diag, OpParams o,
                                                            const double* z, double* p, double* q, int first,
                                                            const double* rz_part, int nrz, const double* rzo_part,
                                                            int nupd, double* pq_part, const double* rr_part,
-                                                           int set_cond, cudaGraphConditionalHandle h) {
+                                                           cudaGraphConditionalHandle h) {
   __shared__ double sm[32];
   __shared__ double s_beta;
   if (sc->done) {
-    if (set_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+    if (COND && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
     return;
   }
   if (!first) {
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_xpby_apply(TileView tv, PairList
     __syncthreads();
   }
   const double beta = first ? 0.0 : s_beta;
-  if (set_cond && blockIdx.x == 0) {
+  if (COND && blockIdx.x == 0) {
     // the device-side loop's test, after the beta breakdown check: r'r of
     // this iteration's update, then continue while not converged (or broken
     // down) and below the iteration limit.  CTAs that start after it and see
@@ -542,30 +544,43 @@ int Solver::heat(double dt, double theta, const double* b1, const double* b0, do
 }
 
 // One PCG iteration (device-side scalars; no host synchronisation).
+// the k_xpby_apply instance for the dimension, the shift and the loop test
+template <bool SHIFT, bool COND>
+static void launch_xpby_apply(int dim, unsigned g, cudaStream_t s, const TileView& tv, const PairList& pl,
+                              PcgScalars* sc, const uint8_t* code, const double* diag, const OpParams& op,
+                              const double* z, double* p, double* q, int first, const double* rz, int nrz,
+                              const double* rzo, int nupd, double* pq, const double* rr,
+                              cudaGraphConditionalHandle h) {
+  if (dim == 2)
+    k_xpby_apply<2, SHIFT, COND><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, code, diag, op, z, p, q, first, rz, nrz, rzo,
+                                                          nupd, pq, rr, h);
+  else
+    k_xpby_apply<3, SHIFT, COND><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, code, diag, op, z, p, q, first, rz, nrz, rzo,
+                                                          nupd, pq, rr, h);
+}
+
 void Solver::xpby_apply(const OpParams& op, bool flex, int first, cudaStream_t s,
                         const cudaGraphConditionalHandle* cond) {
   const TileView tv = eb->tv();
   const PairList pl = eb->pairs();
   const unsigned g = (unsigned)nblk;
-  const bool shift = op.sigma_h2 != 0.0;
+  const int dim = eb->g.dim;
   const double* rzo = flex ? part_rzo() : nullptr;
-  const int sc_ = cond ? 1 : 0;
   const cudaGraphConditionalHandle h = cond ? *cond : cudaGraphConditionalHandle{};
   ++nlaunch;
-  if (eb->g.dim == 2) {
-    if (shift)
-      k_xpby_apply<2, true><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, eb->code, eb->diag, op, z, p, q, first, part_rz(),
-                                                     rz_n, rzo, nblk, part_pq(), part_rr(), sc_, h);
-    else
-      k_xpby_apply<2, false><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, eb->code, eb->diag, op, z, p, q, first, part_rz(),
-                                                      rz_n, rzo, nblk, part_pq(), part_rr(), sc_, h);
+  auto go = [&](auto shift, auto with_cond) {
+    launch_xpby_apply<decltype(shift)::value, decltype(with_cond)::value>(
+        dim, g, s, tv, pl, sc, eb->code, eb->diag, op, z, p, q, first, part_rz(), rz_n, rzo, nblk, part_pq(),
+        part_rr(), h);
+  };
+  using T = std::true_type;
+  using F = std::false_type;
+  if (op.sigma_h2 != 0.0) {
+    if (cond) go(T{}, T{});
+    else go(T{}, F{});
   } else {
-    if (shift)
-      k_xpby_apply<3, true><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, eb->code, eb->diag, op, z, p, q, first, part_rz(),
-                                                     rz_n, rzo, nblk, part_pq(), part_rr(), sc_, h);
-    else
-      k_xpby_apply<3, false><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, eb->code, eb->diag, op, z, p, q, first, part_rz(),
-                                                      rz_n, rzo, nblk, part_pq(), part_rr(), sc_, h);
+    if (cond) go(F{}, T{});
+    else go(F{}, F{});
   }
 }
 
