@@ -52,7 +52,6 @@ struct Batch {
   PcgScalars* sc = nullptr;      // [ngeo]
   PcgScalars* sc_host = nullptr;
   double* part = nullptr;        // [2 ntiles]
-  double* zold = nullptr;
   cudaStream_t home = 0;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -253,7 +252,7 @@ static void destroy_batch(Batch& B) {
   dfree(V.code, s); dfree(V.diag, s); dfree(V.diag32, s); dfree(V.cp_of_node, s); dfree(V.cp_node, s);
   dfree(V.tile_base, s); dfree(V.tile_lim, s); dfree(V.tile_shift64, s); dfree(V.tile_shift32, s);
   dfree(B.tile_geo, s); dfree(B.geo_tile0, s); dfree(B.cut_off_cp, s); dfree(B.cut_c, s); dfree(B.gconst, s);
-  dfree(B.sc, s); dfree(B.part, s); dfree(B.zold, s);
+  dfree(B.sc, s); dfree(B.part, s);
   if (B.sc_host) cudaFreeHost(B.sc_host);
   B.sc_host = nullptr;
   for (eb_handle* e : B.geo) {
@@ -341,92 +340,102 @@ __global__ void __launch_bounds__(BT) k_b_resid(TileView tv, const uint8_t* code
   }
 }
 
-// q = B p; per-tile partial p.q (tiles of converged geometries skipped)
-__global__ void __launch_bounds__(BT) k_b_apply_dot(TileView tv, const int32_t* tile_geo, const PcgScalars* sc,
-                                                    const uint8_t* code, const double* diag, const double* p,
-                                                    double* q, double* part) {
+// The end of a batched PCG iteration in one pass (tiles of converged
+// geometries skipped): p = z + beta p and q = B z + beta q -- in exact
+// arithmetic B (z + beta p), since q holds B p -- with the per-tile p.q
+// partials, beta the geometry's (k_b_finalize FIN_BETA / FIN_BETAF).  The
+// stencil reads z, which the preconditioner launch before completed, so the p
+// update and the apply of the next iteration share one launch.  first: beta =
+// 0, p = z, q = B z (the old p and q are not read).
+__global__ void __launch_bounds__(BT) k_b_xpby_apply(TileView tv, const int32_t* tile_geo, const PcgScalars* sc,
+                                                     const uint8_t* code, const double* diag, const double* z,
+                                                     double* p, double* q, int first, double* part) {
   __shared__ double sm[BT / 32];
   for (int64_t tt = blockIdx.x; tt < tv.ntiles; tt += gridDim.x) {
-    if (sc[tile_geo[tt]].done) continue;
+    const PcgScalars& S = sc[tile_geo[tt]];
+    if (S.done) continue;
+    const double beta = first ? 0.0 : S.beta;
     int32_t node;
     double s = 0.0;
     if (tile_pair<2>(tv, tt, threadIdx.x, node)) {
       uint32_t c0, c1;
       ld_codes(code, node, c0, c1);
-      Two<double> xc, ax;
-      b_op(tv, tt, p, node, c0, c1, diag, xc, ax);
-      const double q0 = (c0 & CODE_CP) ? ax.x : 0.0, q1 = (c1 & CODE_CP) ? ax.y : 0.0;
-      s = xc.x * q0 + xc.y * q1;
+      Two<double> zc, az;
+      b_op(tv, tt, z, node, c0, c1, diag, zc, az);
+      double p0 = zc.x, p1 = zc.y, q0 = az.x, q1 = az.y;
+      if (!first) {
+        const Two<double> pv = ld2d(p + node), qv = ld2d(q + node);
+        p0 = zc.x + beta * pv.x;
+        p1 = zc.y + beta * pv.y;
+        q0 = az.x + beta * qv.x;
+        q1 = az.y + beta * qv.y;
+      }
+      q0 = (c0 & CODE_CP) ? q0 : 0.0;
+      q1 = (c1 & CODE_CP) ? q1 : 0.0;
+      st2(p + node, p0, p1);
       st2(q + node, q0, q1);
+      s = p0 * q0 + p1 * q1;
     }
     const double t = tile_sum(s, sm);
     if (threadIdx.x == 0) part[tt] = t;
   }
 }
 
+// x += alpha p, r -= alpha q; per-tile partials r.r and, with z (flexible
+// CG), r.z for the new r and the z still in place (the r.zold term of the
+// Polak-Ribiere beta), as pairs; without z, single r.r partials
 __global__ void __launch_bounds__(BT) k_b_update_xr(TileView tv, const int32_t* tile_geo, const PcgScalars* sc,
                                                     double* x, double* r, const double* p, const double* q,
-                                                    double* part) {
+                                                    const double* z, double* part) {
   __shared__ double sm[BT / 32];
   for (int64_t tt = blockIdx.x; tt < tv.ntiles; tt += gridDim.x) {
     const PcgScalars& S = sc[tile_geo[tt]];
     if (S.done) continue;
     const double alpha = S.alpha;
     int32_t node;
-    double s = 0.0;
+    double s = 0.0, so = 0.0;
     if (tile_pair<2>(tv, tt, threadIdx.x, node)) {
       const Two<double> rv = ld2d(r + node), qv = LdRO::ld2(q + node), pv = LdRO::ld2(p + node), xv = ld2d(x + node);
       const double r0 = rv.x - alpha * qv.x, r1 = rv.y - alpha * qv.y;
       st2(x + node, xv.x + alpha * pv.x, xv.y + alpha * pv.y);
       st2(r + node, r0, r1);
       s = r0 * r0 + r1 * r1;
+      if (z) {
+        const Two<double> zv = LdRO::ld2(z + node);
+        so = r0 * zv.x + r1 * zv.y;
+      }
     }
     const double t = tile_sum(s, sm);
-    if (threadIdx.x == 0) part[tt] = t;
+    if (z) {
+      const double u = tile_sum(so, sm);
+      if (threadIdx.x == 0) {
+        part[2 * tt] = t;
+        part[2 * tt + 1] = u;
+      }
+    } else if (threadIdx.x == 0) {
+      part[tt] = t;
+    }
   }
 }
 
-// per-tile partials (r.z, r.zold); zold may be null (then only r.z)
-__global__ void __launch_bounds__(BT) k_b_dot2(TileView tv, const int32_t* tile_geo, const PcgScalars* sc,
-                                               const double* r, const double* z, const double* zo, double* part) {
+// per-tile partials r.z (pairs (r.z, 0), the layout k_b_finalize reads for
+// FIN_RZ0 / FIN_BETA)
+__global__ void __launch_bounds__(BT) k_b_dot(TileView tv, const int32_t* tile_geo, const PcgScalars* sc,
+                                              const double* r, const double* z, double* part) {
   __shared__ double sm[BT / 32];
   for (int64_t tt = blockIdx.x; tt < tv.ntiles; tt += gridDim.x) {
     if (sc[tile_geo[tt]].done) continue;
     int32_t node;
-    double a = 0.0, b = 0.0;
+    double a = 0.0;
     if (tile_pair<2>(tv, tt, threadIdx.x, node)) {
       const Two<double> rv = LdRO::ld2(r + node), zv = LdRO::ld2(z + node);
       a = rv.x * zv.x + rv.y * zv.y;
-      if (zo) {
-        const Two<double> ov = LdRO::ld2(zo + node);
-        b = rv.x * ov.x + rv.y * ov.y;
-      }
     }
     const double u = tile_sum(a, sm);
-    const double v = tile_sum(b, sm);
     if (threadIdx.x == 0) {
       part[2 * tt] = u;
-      part[2 * tt + 1] = v;
+      part[2 * tt + 1] = 0.0;
     }
-  }
-}
-
-__global__ void __launch_bounds__(BT) k_b_xpby(TileView tv, const int32_t* tile_geo, const PcgScalars* sc,
-                                               const double* z, double* p, double* zold, int first) {
-  for (int64_t tt = blockIdx.x; tt < tv.ntiles; tt += gridDim.x) {
-    const PcgScalars& S = sc[tile_geo[tt]];
-    if (S.done) continue;
-    const double beta = S.beta;
-    int32_t node;
-    if (!tile_pair<2>(tv, tt, threadIdx.x, node)) continue;
-    const Two<double> zv = LdRO::ld2(z + node);
-    if (first) {
-      st2(p + node, zv.x, zv.y);
-    } else {
-      const Two<double> pv = ld2d(p + node);
-      st2(p + node, zv.x + beta * pv.x, zv.y + beta * pv.y);
-    }
-    if (zold) st2(zold + node, zv.x, zv.y);
   }
 }
 
@@ -472,7 +481,8 @@ __global__ void k_b_finalize(const double* part, const int32_t* geo_tile0, int o
   __shared__ double sm[2][256];
   const int g = blockIdx.x;
   const int t0 = geo_tile0[g], t1 = geo_tile0[g + 1];
-  // k_b_resid and k_b_dot2 write pairs of partials, the others single ones
+  // k_b_resid, k_b_dot and the flexible x/r update (FIN_RRF) write pairs of
+  // partials, the others single ones
   const bool pairs = op != FIN_ALPHA && op != FIN_RR;
   PcgScalars& S = sc[g];
   if (op != FIN_INIT && op != FIN_RZ0 && op != FIN_RZ0F && S.done) return;
@@ -519,6 +529,8 @@ __global__ void k_b_finalize(const double* part, const int32_t* geo_tile0, int o
       }
       break;
     case FIN_RR:
+    case FIN_RRF:
+      if (op == FIN_RRF) S.rzo = w;
       S.rr = v;
       S.iters += 1;
       if (!isfinite(v)) {
@@ -535,7 +547,7 @@ __global__ void k_b_finalize(const double* part, const int32_t* geo_tile0, int o
         S.done = 1;
         break;
       }
-      S.beta = (op == FIN_BETAF ? v - w : v) / S.rz[0];
+      S.beta = (op == FIN_BETAF ? v - S.rzo : v) / S.rz[0];
       S.rz[0] = v;
       break;
   }
@@ -553,27 +565,29 @@ static void b_finalize(Batch& B, int op, cudaStream_t s) {
 
 // z = M^-1 r for all geometries at once (block-diagonal V-cycle), then the
 // per-tile dot partials for beta
-static void b_precondition(Batch& B, const double* r, double* z, bool flex, cudaStream_t s) {
+static void b_precondition(Batch& B, const double* r, double* z, cudaStream_t s) {
   Solver& S = *B.S;
   const int64_t n0 = S.nlaunch;
   amg_vcycle_grid(S, r, z, s);
   B.nlaunch += S.nlaunch - n0;
   ++B.nlaunch;
-  k_b_dot2<<<bgrid(B), BT, 0, s>>>(B.view.tv(), B.tile_geo, B.sc, r, z, flex ? B.zold : nullptr, B.part);
+  k_b_dot<<<bgrid(B), BT, 0, s>>>(B.view.tv(), B.tile_geo, B.sc, r, z, B.part);
 }
 
+// One batched iteration: alpha from the p.q partials of the previous
+// k_b_xpby_apply, the x/r update (with r.zold when flexible), r.r and the
+// convergence test, the V-cycle and r.z, beta, then p and the next q.
 static void b_iteration(Batch& B, double* x, bool flex, cudaStream_t s) {
   Solver& S = *B.S;
   const TileView tv = B.view.tv();
   const unsigned gb = bgrid(B);
-  B.nlaunch += 3;
-  k_b_apply_dot<<<gb, BT, 0, s>>>(tv, B.tile_geo, B.sc, B.view.code, B.view.diag, S.p, S.q, B.part);
+  B.nlaunch += 2;
   b_finalize(B, FIN_ALPHA, s);
-  k_b_update_xr<<<gb, BT, 0, s>>>(tv, B.tile_geo, B.sc, x, S.r, S.p, S.q, B.part);
-  b_finalize(B, FIN_RR, s);
-  b_precondition(B, S.r, S.z, flex, s);
+  k_b_update_xr<<<gb, BT, 0, s>>>(tv, B.tile_geo, B.sc, x, S.r, S.p, S.q, flex ? S.z : nullptr, B.part);
+  b_finalize(B, flex ? FIN_RRF : FIN_RR, s);
+  b_precondition(B, S.r, S.z, s);
   b_finalize(B, flex ? FIN_BETAF : FIN_BETA, s);
-  k_b_xpby<<<gb, BT, 0, s>>>(tv, B.tile_geo, B.sc, S.z, S.p, flex ? B.zold : nullptr, 0);
+  k_b_xpby_apply<<<gb, BT, 0, s>>>(tv, B.tile_geo, B.sc, B.view.code, B.view.diag, S.z, S.p, S.q, 0, B.part);
 }
 
 static void b_graph_prepare(Batch& B, const double* b, double* x, bool flex, cudaStream_t s) {
@@ -669,10 +683,10 @@ static int batch_pcg(Batch& B, const double* b, double* x, double rtol, int maxi
     b_finalize(B, FIN_INIT, s);
     int its = *std::max_element(iters.begin(), iters.end());
     if (its < maxit) {
-      b_precondition(B, S.r, S.z, flex, s);
-      b_finalize(B, flex ? FIN_RZ0F : FIN_RZ0, s);
+      b_precondition(B, S.r, S.z, s);
+      b_finalize(B, FIN_RZ0, s);
       ++B.nlaunch;
-      k_b_xpby<<<gb, BT, 0, s>>>(tv, B.tile_geo, B.sc, S.z, S.p, flex ? B.zold : nullptr, 1);
+      k_b_xpby_apply<<<gb, BT, 0, s>>>(tv, B.tile_geo, B.sc, B.view.code, B.view.diag, S.z, S.p, S.q, 1, B.part);
       int it = 0;
       if (!B.profile) {  // the whole loop on the device
         b_loop_prepare(B, b, x, flex);
@@ -857,7 +871,6 @@ int batch_heat_setup(batch_handle* b, const double* dt, double theta, const amg_
     if (B.gexec) cudaGraphExecDestroy(B.gexec);
     B.gexec = nullptr;
     b_loop_release(B);
-    dfree(B.zold, stream);
     amg_opts o{25, 1024, 0.02, 2, EB_F64};
     if (opts) o = *opts;
     EB_REQUIRE(o.max_levels >= 1 && o.max_levels <= 32, EB_ERR_INVALID, "batch_heat_setup: max_levels in [1, 32]");
@@ -870,7 +883,6 @@ int batch_heat_setup(batch_handle* b, const double* dt, double theta, const amg_
     S.shift = 0.0;  // per-tile shifts of the view take over
     S.opts = o;
     S.alloc_work(stream);
-    if (o.vcycle_prec != EB_F64) B.zold = dalloc<double>(B.view.g.num_nodes, stream);
     // block-diagonal level-0 matrix of the scaled operators, geometry by geometry
     std::vector<DCsr> parts(ng);
     int64_t nnz = 0;

@@ -8,11 +8,13 @@
 
 namespace ebk {
 
-// FIN_RZ0F / FIN_BETAF: flexible CG, partials are pairs (r.z, r.z_previous)
-// (the batched PCG; the single-grid PCG forms r.z_previous in its x/r update).
-// The single-grid PCG combines FIN_ALPHA and FIN_BETA inside its update
-// kernels; the batch finalizes every op in its per-geometry kernel.
-enum { FIN_INIT = 0, FIN_RZ0 = 1, FIN_ALPHA = 2, FIN_RR = 3, FIN_BETA = 4, FIN_RZ0F = 5, FIN_BETAF = 6 };
+// Flexible CG (Polak-Ribiere beta): the x/r update also forms r.z_previous
+// (the r'zold term) from the z still in place.  FIN_RRF: the batch's (r.r,
+// r.z_previous) pairs, recorded per geometry; FIN_BETAF then takes r.z_previous
+// from there; FIN_RZ0F is FIN_RZ0.  The single-grid PCG combines FIN_ALPHA and
+// FIN_BETA inside its update kernels; the batch finalizes every op in its
+// per-geometry kernel.
+enum { FIN_INIT = 0, FIN_RZ0 = 1, FIN_ALPHA = 2, FIN_RR = 3, FIN_BETA = 4, FIN_RZ0F = 5, FIN_BETAF = 6, FIN_RRF = 7 };
 enum { PCG_FLAG_NONFINITE = 1, PCG_FLAG_BREAKDOWN = 2 };
 // what pcg_opts.profile times: the level-0 smoother launches, the learned stage's 32 -> 32
 // convolutions, or the level-1 (first coarse, CSR) smoother launches
@@ -28,6 +30,7 @@ struct PcgScalars {
   // iters & 1 as the x/r update of the iteration saw it: the r'z slot of the
   // p update, whose launch may also advance iters (device-side loop)
   int slot;
+  double rzo;  // batched flexible PCG: r'zold of the iteration (FIN_RRF)
 };
 
 struct Hierarchy;  // AMG levels (amg.cu)
