@@ -85,26 +85,6 @@ __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16, double>(double v) {
   return __double2bfloat16(v);
 }
 
-// Exact float -> double from the bits, in integer operations (the value of
-// the hardware conversion, without issuing to GB300's narrow FP64 pipe); zero
-// is formed from its sign, subnormal, infinite and NaN inputs take the
-// hardware conversion.
-__device__ __forceinline__ double widen(float f) {
-  const uint32_t u = __float_as_uint(f);
-  const uint32_t e = (u >> 23) & 0xFFu;
-  if ((u & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
-  if (e == 0u || e == 0xFFu) return (double)f;
-  const uint32_t hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
-  return __hiloint2double((int)hi, (int)((u & 7u) << 29));
-}
-template <class O, class A>
-__device__ __forceinline__ O to_out(A v) {
-  if constexpr (std::is_same<O, double>::value && std::is_same<A, float>::value)
-    return widen(v);
-  else
-    return (O)v;
-}
-
 // level 0 ----------------------------------------------------------------
 // b_out = (V) r; x = d = D^-1 b / theta
 template <int DIM, class V>
@@ -212,12 +192,10 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_step(TileView tv, const u
     const A d1 = (k1 & CODE_CP) ? c1 * dv.y + c2 * res1 : (A)0;
     st2o(d + node, d0, d1);
     const A z0 = (k0 & CODE_CP) ? xc.x + d0 : (A)0, z1 = (k1 & CODE_CP) ? xc.y + d1 : (A)0;
-    using W = typename std::conditional<std::is_same<O, double>::value, double, A>::type;
-    const W w0 = to_out<W>(z0), w1 = to_out<W>(z1);
-    st2(xo + node, w0, w1);
+    st2(xo + node, z0, z1);
     if (DOT) {
       const Two<double> rv = LdRO::ld2(r64 + node);
-      srz += rv.x * (double)w0 + rv.y * (double)w1;
+      srz += rv.x * (double)z0 + rv.y * (double)z1;
     }
   }
   if (DOT) {
