@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_update_first(PairList pl, PcgUpd
   using A = typename AccOf<V>::type;
   __shared__ double sm[32];
   __shared__ double s_alpha;
-  if (u.sc->done) {
+  if (cta_done(u.sc)) {
     if (threadIdx.x == 0) u.rr_part[blockIdx.x] = 0.0;
     return;
   }

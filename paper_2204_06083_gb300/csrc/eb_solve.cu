@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_update_xr(PairList pl, PcgScalar
                                                           double* rzo_part) {
   __shared__ double sm[32];
   __shared__ double s_alpha;
-  if (sc->done) {
+  if (cta_done(sc)) {
     if (threadIdx.x == 0) part[blockIdx.x] = 0.0;
     return;
   }
@@ -156,11 +156,11 @@ __global__ void __launch_bounds__(TILE_NODES) k_dot(TileView tv, const double* a
 // boundary between them.  nupd: partials per array of the x/r update (r'r,
 // r'zold).  COND (device-side loop): CTA 0 also does the loop test and sets
 // the loop condition h (a separate instance: profilers cannot replay graph
-// kernel nodes that may set a condition).  B is the unit stencil (no 1/h^2 multiply; the
-// update kernels take the step as alpha h^2 for x), and SHIFT = false drops
-// its sigma term for Poisson: two FP64 operations fewer per node on GB300's
-// narrow FP64 pipe.  first: beta = 0, p = z, q = B z (the old p and q are not
-// read).
+// kernel nodes that may set a condition).  B is the unit stencil (no 1/h^2
+// multiply; the update kernels take the step as alpha h^2 for x), and SHIFT =
+// false drops its sigma term for Poisson: two FP64 operations fewer per node
+// on GB300's narrow FP64 pipe.  first: beta = 0, p = z, q = B z (the old p and
+// q are not read).
 template <int DIM, bool SHIFT, bool COND>
 __global__ void __launch_bounds__(TILE_NODES) k_xpby_apply(TileView tv, PairList pl, PcgScalars* sc,
                                                            const uint8_t* code, const double* diag, OpParams o,
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_xpby_apply(TileView tv, PairList
                                                            cudaGraphConditionalHandle h) {
   __shared__ double sm[32];
   __shared__ double s_beta;
-  if (sc->done) {
+  if (cta_done(sc)) {
     if (COND && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
     return;
   }

@@ -144,6 +144,17 @@ __device__ __forceinline__ double block_sum(double v, double* sm) {
   return s;
 }
 
+// sc->done as thread 0 of the CTA reads it, the same for all its threads (CTA
+// 0 of the launch may set it meanwhile, so threads reading it themselves could
+// disagree and part of the CTA skip the barriers the rest waits at); all
+// threads call it.
+__device__ __forceinline__ bool cta_done(const PcgScalars* sc) {
+  __shared__ int s_done;
+  if (threadIdx.x == 0) s_done = *(volatile const int*)&sc->done;
+  __syncthreads();
+  return s_done != 0;
+}
+
 // sum of n partials (stride apart) in a fixed order, the same in every CTA;
 // thread 0 holds the result
 __device__ __forceinline__ double sum_parts(const double* part, int n, int stride, double* sm) {
