@@ -588,9 +588,9 @@ void Solver::iteration(int kind, const double* b, double* x, cudaStream_t s,
                        const cudaGraphConditionalHandle* cond) {
   (void)b;
   const int dim = eb->g.dim;
-  const TileView tv = eb->tv();
   const OpParams op = op_params(*this);
-  // q = (sigma I + A) p and the p.q partials come from the previous
+  const bool flex = flex_for(kind);
+  // q = h^2 (sigma I + A) p and the p.q partials come from the previous
   // k_xpby_apply; with an AMG V-cycle next, the x/r update also does its first
   // level-0 step
   bool fused = false;
@@ -606,15 +606,14 @@ void Solver::iteration(int kind, const double* b, double* x, cudaStream_t s,
     u.rr_part = part_rr();
     u.h2 = eb->g.h * eb->g.h;
     u.z = z;
-    u.rzo_part = flex_for(kind) ? part_rzo() : nullptr;
+    u.rzo_part = flex ? part_rzo() : nullptr;
     fused = amg_update_first(*this, u, s) != 0;
     if (fused) ++nlaunch;
   }
   if (!fused)
     EB_DIM_LAUNCH(dim, k_update_xr, nblk, eb->pairs(), sc, x, r, p, q, part_pq(), nblk, part_rr(), eb->g.h * eb->g.h, z,
-                  flex_for(kind) ? part_rzo() : nullptr);
+                  flex ? part_rzo() : nullptr);
   precondition(kind, r, z, s, fused);
-  const bool flex = flex_for(kind);
   // r'r and the convergence test end the iteration: in the device-side loop
   // the p, q launch does them and sets the loop condition
   xpby_apply(op, flex, 0, s, cond);
