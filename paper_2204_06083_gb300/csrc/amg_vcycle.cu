@@ -2,7 +2,8 @@
 // Algorithm 1 step 4), in FP64, or in FP32 or BF16 storage with FP32
 // arithmetic.
 //
-// Level 0 is matrix free on the grid (stencil.cuh); coarser levels use CSR.
+// Level 0 is matrix free on the grid (stencil.cuh), swept over the node pairs
+// that hold a CP (EB_SWEEP); coarser levels use CSR.
 // Smoother: Chebyshev polynomial of degree k for D^-1 A on [rho/30, 1.1 rho],
 // one sweep before and one after the coarse correction; the first sweep
 // starts from x = 0 and needs no operator apply.  The coarsest level is solved
@@ -85,6 +86,14 @@ __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16, double>(double v) {
   return __double2bfloat16(v);
 }
 
+// the view without its CP pair list: EB_SWEEP then visits every pair of the
+// active tiles
+inline TileView tiles_only(TileView tv) {
+  tv.pair_node = nullptr;
+  tv.npairs = 0;
+  return tv;
+}
+
 // level 0 ----------------------------------------------------------------
 // b_out = (V) r; x = d = D^-1 b / theta
 template <int DIM, class V>
@@ -95,7 +104,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_first(TileView tv, const 
                                                              V* __restrict__ x, V* __restrict__ d,
                                                              typename AccOf<V>::type theta) {
   using A = typename AccOf<V>::type;
-  EB_PAIR_LOOP(DIM, tv, node) {
+  EB_SWEEP(DIM, tv, node) {
     const GOp<A> ot = tile_op(tv, tt_, o);
     uint32_t c0, c1;
     ld_codes(code, node, c0, c1);
@@ -174,7 +183,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_step(TileView tv, const u
                                                             double* __restrict__ part = nullptr) {
   using A = typename AccOf<V>::type;
   double srz = 0.0;
-  EB_PAIR_LOOP(DIM, tv, node) {
+  EB_SWEEP(DIM, tv, node) {
     const GOp<A> ot = tile_op(tv, tt_, o);
     uint32_t k0, k1;
     ld_codes(code, node, k0, k1);
@@ -212,7 +221,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_resid(TileView tv, const uint8
                                                         const V* __restrict__ b, const V* __restrict__ x,
                                                         V* __restrict__ r) {
   using A = typename AccOf<V>::type;
-  EB_PAIR_LOOP(DIM, tv, node) {
+  EB_SWEEP(DIM, tv, node) {
     const GOp<A> ot = tile_op(tv, tt_, o);
     uint32_t c0, c1;
     ld_codes(code, node, c0, c1);
@@ -337,7 +346,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_prolong_mf(TileView tv, const ui
                                                            V* __restrict__ x) {
   using A = typename AccOf<V>::type;
   const int32_t st[3] = {1, tv.sy, tv.sz};
-  EB_PAIR_LOOP(DIM, tv, node) {
+  EB_SWEEP(DIM, tv, node) {
     uint32_t c0, c1;
     ld_codes(code, node, c0, c1);
 #pragma unroll
@@ -657,9 +666,9 @@ static int vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, co
     if (k == cc.deg - 1 && dot)
       k_g_cheb_step<DIM, V, double, true><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, x, z, g.d, (A)cc.c1[k],
                                                                     (A)cc.c2[k], dot->r, dot->part);
-    else if (k == cc.deg - 1)
+    else if (k == cc.deg - 1)  // z for a caller (amg_vcycle): every node of the active tiles, 0 off the CPs
       k_g_cheb_step<DIM, V, double>
-          <<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, x, z, g.d, (A)cc.c1[k], (A)cc.c2[k]);
+          <<<gb, TILE_NODES, 0, s>>>(tiles_only(tv), eb.code, diag, o, b, x, z, g.d, (A)cc.c1[k], (A)cc.c2[k]);
     else
       k_g_cheb_step<DIM, V, V><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, x, x2, g.d, (A)cc.c1[k], (A)cc.c2[k]);
     if (mark) S.prof_mark(s, false);

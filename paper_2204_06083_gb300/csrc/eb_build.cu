@@ -505,7 +505,9 @@ void build_cp_pairs(EBHandle& eb, cudaStream_t s) {
   dfree(eb.pair_node, s);
   eb.num_pairs = 0;
   const int64_t nt = eb.num_tiles;
-  if (nt == 0) return;
+  // views with per-tile shifts (batches) keep sweeping tiles: EB_SWEEP's list
+  // mode has no tile index to read a shift with
+  if (nt == 0 || eb.tile_shift64 || eb.tile_shift32) return;
   int32_t* cnt = dalloc<int32_t>(nt, s, false);
   int32_t* off = nullptr;
   try {

@@ -129,6 +129,8 @@ struct EBHandle {
     TileView v{tile_base, tile_lim, num_tiles, g.n0, g.n0 * g.n1, (int32_t)g.num_nodes, tile_shift64, tile_shift32};
     v.bx = ilog2(g.tx);
     v.by = ilog2(g.ty);
+    v.pair_node = pair_node;
+    v.npairs = num_pairs;
     return v;
   }
   static int ilog2(int v) {

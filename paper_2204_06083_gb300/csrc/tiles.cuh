@@ -42,6 +42,10 @@ struct TileView {
   const double2* tshift64 = nullptr;
   const float2* tshift32 = nullptr;
   int32_t bx = 5, by = 3;  // log2 of the tile extents in x and y (z = 256 >> (bx + by))
+  // single grids: the pairs of the tiles that hold a CP (EBHandle::pairs), in
+  // tile order; null for batched views
+  const int32_t* pair_node = nullptr;
+  int64_t npairs = 0;
 };
 
 // Node of this thread in listed tile tt (one node per thread, 256 threads).
@@ -89,3 +93,27 @@ struct PairList {
   for (int64_t li_ = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li_ < (pl).n;                          \
        li_ += (int64_t)gridDim.x * blockDim.x)                                                              \
     if (const int32_t node = __ldg((pl).node + li_); true)
+
+namespace ebk {
+// item it_ of EB_SWEEP: a CP pair of the list, or pair t of listed tile it_
+template <int DIM>
+__device__ __forceinline__ bool sweep_pair(const TileView& tv, int64_t it, int t, int32_t& node) {
+  if (tv.pair_node) {
+    node = __ldg(tv.pair_node + it);
+    return true;
+  }
+  return tile_pair<DIM>(tv, it, t, node);
+}
+}  // namespace ebk
+
+// for (each pair this thread handles) body: the CP pairs of the view's list
+// when it has one (values at the nodes of the other pairs are never read at a
+// CP), else every pair of every listed tile as EB_PAIR_LOOP (tt_ is then the
+// tile; with a list it is the list index and the view has no per-tile shifts)
+#define EB_SWEEP(DIM, tv, node)                                                                             \
+  for (int64_t tt_ = (tv).pair_node ? (int64_t)blockIdx.x * blockDim.x + threadIdx.x                        \
+                                    : 2 * (int64_t)blockIdx.x + (threadIdx.x >> 7),                         \
+               end_ = (tv).pair_node ? (tv).npairs : (tv).ntiles,                                           \
+               step_ = (tv).pair_node ? (int64_t)gridDim.x * blockDim.x : 2 * (int64_t)gridDim.x;           \
+       tt_ < end_; tt_ += step_)                                                                            \
+    if (int32_t node = 0; ::ebk::sweep_pair<DIM>((tv), tt_, threadIdx.x & 127, node))
