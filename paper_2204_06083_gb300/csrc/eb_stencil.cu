@@ -156,10 +156,7 @@ __global__ void __launch_bounds__(LF_THREADS) k_leapfrog(TileView tv, const uint
                                                          const T* __restrict__ cur, T* __restrict__ prev,
                                                          typename AccOf<T>::type c2) {
   using A = typename AccOf<T>::type;
-  constexpr int TPP = LF_THREADS / PAIR_THREADS;
-  for (int64_t tt = (int64_t)TPP * blockIdx.x + (threadIdx.x >> 7); tt < tv.ntiles; tt += (int64_t)TPP * gridDim.x) {
-    int32_t node;
-    if (!tile_pair<DIM>(tv, tt, threadIdx.x & (PAIR_THREADS - 1), node)) continue;
+  auto step = [&](int32_t node) {
     uint32_t c0, c1;
     ld_codes(code, node, c0, c1);
     Two<A> xc, core;
@@ -168,6 +165,38 @@ __global__ void __launch_bounds__(LF_THREADS) k_leapfrog(TileView tv, const uint
     const A n0 = (c0 & CODE_CP) ? (A)2 * xc.x - po.x - c2 * core.x : (A)0;
     const A n1 = (c1 & CODE_CP) ? (A)2 * xc.y - po.y - c2 * core.y : (A)0;
     st2(prev + node, n0, n1);
+  };
+  if (tv.pair_node) {  // the CP pairs (the others hold 0 in both fields: k_field_mask)
+    for (int64_t li = (int64_t)blockIdx.x * LF_THREADS + threadIdx.x; li < tv.npairs;
+         li += (int64_t)gridDim.x * LF_THREADS)
+      step(__ldg(tv.pair_node + li));
+    return;
+  }
+  constexpr int TPP = LF_THREADS / PAIR_THREADS;
+  for (int64_t tt = (int64_t)TPP * blockIdx.x + (threadIdx.x >> 7); tt < tv.ntiles; tt += (int64_t)TPP * gridDim.x) {
+    int32_t node;
+    if (!tile_pair<DIM>(tv, tt, threadIdx.x & (PAIR_THREADS - 1), node)) continue;
+    step(node);
+  }
+}
+
+// 0 at the non-CP nodes of every pair of the active tiles, in both fields: the
+// values a step over every tile pair writes there, so that stepping only the
+// CP pairs leaves the same fields
+template <class T, int DIM>
+__global__ void __launch_bounds__(LF_THREADS) k_field_mask(TileView tv, const uint8_t* __restrict__ code, T* ua,
+                                                           T* ub) {
+  constexpr int TPP = LF_THREADS / PAIR_THREADS;
+  for (int64_t tt = (int64_t)TPP * blockIdx.x + (threadIdx.x >> 7); tt < tv.ntiles; tt += (int64_t)TPP * gridDim.x) {
+    int32_t node;
+    if (!tile_pair<DIM>(tv, tt, threadIdx.x & (PAIR_THREADS - 1), node)) continue;
+    uint32_t c0, c1;
+    ld_codes(code, node, c0, c1);
+    if ((c0 & c1 & CODE_CP) != 0) continue;  // both CPs: nothing to clear
+    const bool k0 = (c0 & CODE_CP) != 0, k1 = (c1 & CODE_CP) != 0;
+    const Two<T> a{ua[node], ua[node + 1]}, b{ub[node], ub[node + 1]};
+    st2(ua + node, k0 ? a.x : (T)0, k1 ? a.y : (T)0);
+    st2(ub + node, k0 ? b.x : (T)0, k1 ? b.y : (T)0);
   }
 }
 
@@ -225,6 +254,12 @@ int launch_leapfrog(const EBHandle& eb, T* ua, T* ub, int nsteps, double dt, cud
     cur = (k & 1) ? ua : ub;
     prev = (k & 1) ? ub : ua;
   };
+  if (tv.pair_node) {  // the steps touch only the CP pairs
+    if (G.dim == 2)
+      k_field_mask<T, 2><<<blocks, LF_THREADS, 0, s>>>(tv, code, ua, ub);
+    else
+      k_field_mask<T, 3><<<blocks, LF_THREADS, 0, s>>>(tv, code, ua, ub);
+  }
   int done = 0;
   if (use_graph && nsteps >= LeapfrogGraph::CHUNK) {
     LeapfrogGraph& lg = eb.lf_graph;
