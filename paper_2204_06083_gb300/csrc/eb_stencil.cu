@@ -3,7 +3,7 @@
 // Sec. 3.5 at theta = 0).
 //
 // Layout: full grid, x fastest; work is distributed over the active tiles
-// (tiles.cuh).  The node code byte carries the CP flag and the mask of
+// (tiles.cuh), the leapfrog steps over their node pairs that hold a CP.  The node code byte carries the CP flag and the mask of
 // directions whose neighbour is a BP, so a CP never reads a non-CP value:
 // interior CPs (code 0x80) use D = 2 dim, cut CPs read D_k (stencil.cuh).
 #include "eb_internal.cuh"
@@ -146,8 +146,9 @@ template void launch_apply<__nv_bfloat16>(const EBHandle&, const __nv_bfloat16*,
 // overwriting u_old in place.  A launch boundary is the cheapest grid-wide
 // barrier on this part: a persistent cooperative kernel with a software grid
 // barrier between its steps measured 9.6-14.8 us per step at 4096^2 against
-// 8.3 us for one launch per step inside a CUDA graph.  512-thread CTAs (four
-// tiles per pass) sized to one resident wave.
+// 8.3 us for one launch per step inside a CUDA graph.  512-thread CTAs sized
+// to one resident wave, over the view's CP pair list (four tiles per pass over
+// every tile pair for a view without one).
 constexpr int LF_THREADS = 512;
 
 template <class T, int DIM>
