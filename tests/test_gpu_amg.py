@@ -274,3 +274,32 @@ def test_time_kernel_alone(prec):
         amg.time_smoother_step(amg.num_levels - 1, 4, 0)
     x1, st1 = amg.solve(b, rtol=1e-10)
     assert st1.iterations == st0.iterations and torch.equal(x1, x0)
+
+
+def test_full_size_pcg_256_benchmark_configuration():
+    """The default benchmark's solve at its full size (256^3 ellipsoid, FP32
+    V-cycle, flexible FP64 PCG on the device-side loop, rtol 1e-10), checked by
+    properties the oracle computes at this size: the right-hand side equals the
+    oracle's (eq. 3 with the boundary terms) to 1e-12, the true residual of the
+    GPU solution with the oracle's assembled matrix is <= 1e-10 (one sparse
+    product on the CPU), and the solution is within the discretisation error
+    of the exact u at the CPs (max <= 2e-4; about 9e-5 at this size)."""
+    eb = _eb()
+    grid, ls = ei.ellipsoid_k3(256, seed=0)
+    h = eb.EB(grid, ls)
+    ref = oeb.build(grid, ls)
+    pts = ei.grid_points(grid)
+    f = ei.f_k3(*pts)
+    ug = ei.u_k3(*[ref.cut_xg[:, a] for a in range(3)])
+    b = h.rhs(torch.tensor(f, device="cuda"), torch.tensor(ug, device="cuda"))
+    b_ref = oeb.rhs(ref, f, ug)
+    b_cp = ref.from_grid(b.cpu().numpy())
+    assert np.linalg.norm(b_cp - b_ref) <= 1e-12 * np.linalg.norm(b_ref)
+    amg = eb.AMG(h, 0.0, vcycle_prec=eb.EB_F32)
+    x, st = amg.solve(b, rtol=1e-10, maxit=200)
+    assert st.converged and 15 <= st.iterations <= 30
+    x_cp = ref.from_grid(x.cpu().numpy())
+    res = np.linalg.norm(b_ref - ref.A @ x_cp) / np.linalg.norm(b_ref)
+    assert res <= 1e-10, res
+    err = np.abs(x_cp - ei.u_k3(*[p.reshape(-1)[ref.cp_nodes] for p in pts])).max()
+    assert err <= 2e-4, err
