@@ -4,11 +4,14 @@
 // Vectors live in the full-grid layout and are touched on the active tiles
 // only; the FP64 update kernels (x, r, p, q) run over the node pairs of the
 // tiles that hold a CP (EBHandle::pairs): the other pairs' entries are never
-// read at a CP, and GB300's narrow FP64 pipe makes the skipped pairs count.  Every reduction is two-pass and deterministic: each CTA of a fixed
-// grid reduces its nodes in a fixed order to one partial; the partials are
-// combined in a fixed order by the kernel that needs the result -- every CTA
-// of the update kernels (x, r with alpha; p with beta) reduces them itself and
-// CTA 0 records the scalars -- or by one CTA (r'r and the convergence test).
+// read at a CP, and GB300's narrow FP64 pipe makes the skipped pairs count.
+// One iteration is the x/r update, the preconditioner and k_xpby_apply (the
+// p update with the next operator apply).  Every reduction is two-pass and
+// deterministic: each CTA of a fixed grid reduces its nodes in a fixed order
+// to one partial; the partials are combined in a fixed order by the kernel
+// that needs the result -- every CTA of the update kernels (x, r with alpha;
+// p with beta) reduces them itself and CTA 0 records the scalars and, in the
+// device-side loop, runs the convergence test -- or by one CTA (k_finalize).
 // No scalar crosses to the host except at the end of the loop.
 #include "eb_solver.cuh"
 #include "stencil.cuh"
