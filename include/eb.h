@@ -196,8 +196,10 @@ typedef struct {
  * (Sec. 3, first paragraph); this hierarchy is deterministic: strength
  * |a_ij| >= theta sqrt(a_ii a_jj); distance-2 maximal independent set with
  * priorities (lowbias32 hash of the index, index); aggregates grown from its
- * nodes; P = (I - 4/(3 rho) D^-1 A) P_hat; Galerkin A_c = P^T A P; dense
- * Cholesky on the coarsest level.  opts may be NULL for the defaults.
+ * nodes; P = (I - 4/(3 rho) D^-1 A) P_hat; Galerkin A_c = P^T A P; on the
+ * coarsest level an explicit dense inverse formed by Gauss-Jordan elimination
+ * without pivoting (the coarsest matrix is SPD), applied as a dense
+ * matrix-vector product.  opts may be NULL for the defaults.
  * Synchronous. */
 int amg_setup(const eb_handle* eb, double shift, const amg_opts* opts, amg_handle** out, cudaStream_t stream);
 void amg_destroy(amg_handle* amg);
@@ -456,16 +458,16 @@ int pcg_solve_nn(const amg_handle* amg, nn_handle* nn, int mode, const double* b
  * device synchronisation of cudaMalloc / cudaFree cannot allow that.  This
  * entry point runs all nsteps in one persistent cooperative launch and keeps
  * the scratch of its grid-wide barrier in a fixed device array of the library
- * (one flag per cooperative CTA, at most 2048 CTAs, about 8 KB, held by every
- * GPU that loads the library until the process exits); it calls no cudaMalloc,
+ * (one flag per cooperative CTA, at most 2048 CTAs -- larger grids are capped
+ * at 2048, which limits parallelism, not the result -- about 8 KB, held by
+ * every GPU that loads the library until the process exits); it calls no cudaMalloc,
  * cudaFree or allocating library routine.  Same arguments, arithmetic and
  * results as wave_step; the handle and the fields are created by the caller
  * beforehand.  The first call on each device looks up the array's device
  * address (no allocation); make that first call before any stream capture.
  * All calls share the array and each clears the part it uses before its
  * launch, so two calls whose kernels overlap on the GPU race and must not be
- * issued.  A launch that would need more than 2048 CTAs is rejected with
- * EB_ERR_INVALID; a barrier wait that gives up returns EB_ERR_TIMEOUT.
+ * issued.  A barrier wait that gives up returns EB_ERR_TIMEOUT.
  * Synchronous. */
 int wave_step_noalloc(const eb_handle* eb, int prec, double dt, void* u_prev_dev, void* u_cur_dev, int nsteps,
                       cudaStream_t stream);

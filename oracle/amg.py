@@ -21,7 +21,15 @@ so that a parallel implementation can reproduce it exactly:
                  neighbour joins it (at most one exists); every other node
                  joins the aggregate of the strong neighbour (assigned in the
                  first pass) with the largest |a_ij| (compared rounded to
-                 single precision), ties to the lowest aggregate id.
+                 single precision), ties to the lowest aggregate id.  The
+                 single-precision comparison is part of this specification:
+                 below the finest level the entries are Galerkin sums whose
+                 summation order is an implementation choice, and near-equal
+                 couplings (symmetric stencils, mirrored cut cells) are common;
+                 comparing them at 24 bits makes the choice independent of
+                 the last FP64 bits, so that any correct summation order
+                 builds the same aggregates except for weights that straddle
+                 an FP32 rounding boundary.
 * prolongation   P_hat = normalised constant vector per aggregate
                  (1/sqrt(|agg|)); P = (I - omega D^-1 A) P_hat with omega =
                  4/(3 rho), rho = max_i sum_j |a_ij| / a_ii (Gershgorin bound of
@@ -107,8 +115,13 @@ def mis2(S: sp.csr_matrix) -> np.ndarray:
 def aggregate(A: sp.csr_matrix):
     """Aggregate id per node and the number of aggregates."""
     S = strength_graph(A)
-    n = A.shape[0]
-    roots = mis2(S)
+    return aggregate_from_roots(S, mis2(S))
+
+
+def aggregate_from_roots(S: sp.csr_matrix, roots: np.ndarray):
+    """The two aggregation passes around given roots on the strength graph S
+    (values |a_ij|): aggregate id per node and the number of aggregates."""
+    n = S.shape[0]
     agg = np.full(n, -1, dtype=np.int64)
     agg[roots] = np.arange(int(roots.sum()))
     rows = np.repeat(np.arange(n), np.diff(S.indptr))

@@ -14,7 +14,8 @@
 // The fields and the eb handle are the caller's, created beforehand.
 //
 // Scratch: one flag per cooperative CTA plus a release counter and an error
-// word, at most EB_NOALLOC_MAX_CTAS CTAs (8 KB of flags).  Every GPU that
+// word, at most EB_NOALLOC_MAX_CTAS CTAs (8 KB of flags); the grid is capped
+// at that many CTAs.  Every GPU that
 // loads the library holds this array until the process exits.  The first call
 // on a device looks up the array's device address with that device current
 // (cudaGetSymbolAddress, no allocation); make that first call before any
@@ -47,10 +48,10 @@ constexpr long long NOALLOC_SPIN_LIMIT = 20000000;  // ~ a second of polling
 // waits for all flags and then publishes k in gen, the others wait for gen.
 // Every wait is bounded; on timeout err is set and all later barriers return.
 __device__ bool noalloc_sync(NoAllocWaveScratch* sc, unsigned int k) {
-  __syncthreads();
   __shared__ int failed;
+  if (threadIdx.x == 0) failed = 0;  // before the barrier: pollers below may set it
+  __syncthreads();
   if (threadIdx.x == 0) {
-    failed = 0;
     __threadfence();
     atomicExch(&sc->arrive[blockIdx.x], k);
   }
@@ -68,6 +69,7 @@ __device__ bool noalloc_sync(NoAllocWaveScratch* sc, unsigned int k) {
         __nanosleep(32);
       }
     }
+    __threadfence();  // acquire: order this thread's observations before the release below
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
@@ -114,12 +116,19 @@ __global__ void __launch_bounds__(TILE_NODES) k_leapfrog_noalloc(TileView tv, co
     }
     if (!noalloc_sync(sc, (unsigned int)s + 1u)) return;
   }
+  // After an odd number of steps the newest field sits in ua: swap.  With a
+  // single step ub was never written, so its non-CP entries still hold the
+  // caller's input; both fields are masked here (0 off the CPs), as wave_step's
+  // masking pass leaves them.
   if (nsteps & 1) {
     EB_PAIR_LOOP(DIM, tv, node) {
+      uint32_t c0, c1;
+      ld_codes(code, node, c0, c1);
+      const bool k0 = (c0 & CODE_CP) != 0, k1 = (c1 & CODE_CP) != 0;
       const Two<A> a = LdCG::ld2(ua + node);
       const Two<A> b = LdCG::ld2(ub + node);
-      st2(ua + node, b.x, b.y);
-      st2(ub + node, a.x, a.y);
+      st2(ua + node, k0 ? b.x : (A)0, k1 ? b.y : (A)0);
+      st2(ub + node, k0 ? a.x : (A)0, k1 ? a.y : (A)0);
     }
   }
 }
@@ -152,11 +161,11 @@ static int leapfrog_noalloc(const EBHandle& eb, T* ua, T* ub, int nsteps, double
   int per_sm = 0;
   EB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TILE_NODES, 0));
   EB_REQUIRE(per_sm > 0, EB_ERR_INVALID, "wave_step_noalloc: kernel cannot be resident");
-  const int64_t nb = std::max<int64_t>(1, std::min<int64_t>(eb.num_tiles, (int64_t)per_sm * num_sms()));
-  if (nb > EB_NOALLOC_MAX_CTAS)
-    throw Failure{EB_ERR_INVALID, "wave_step_noalloc: the launch needs " + std::to_string(nb) +
-                                      " cooperative CTAs, above the scratch limit of " +
-                                      std::to_string(EB_NOALLOC_MAX_CTAS)};
+  // the step body is a grid-stride loop over the tile pairs, so a grid capped
+  // at the scratch's flag count gives the same fields (the cap limits
+  // parallelism on parts with more resident CTAs, never the result)
+  const int64_t nb = std::max<int64_t>(
+      1, std::min<int64_t>({eb.num_tiles, (int64_t)per_sm * num_sms(), (int64_t)EB_NOALLOC_MAX_CTAS}));
   // clear the counter, the error word and the flags this launch uses
   EB_CUDA(cudaMemsetAsync(sc, 0, offsetof(NoAllocWaveScratch, arrive) + sizeof(unsigned int) * (size_t)nb, s));
   typename AccOf<T>::type c2 = (typename AccOf<T>::type)(dt * dt / (G.h * G.h));

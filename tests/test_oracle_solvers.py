@@ -2,8 +2,9 @@
 
 P4  CG and AMG-PCG agree with a dense Cholesky solve on tiny grids
 P5  leapfrog on the Bessel J_7 standing mode: second-order rates as in
-    Table 1 (theta = 0 column); magnitudes within a factor 4 of the table
-    (the interior phase error of the 5-point / leapfrog pair dominates)
+    Table 1 (theta = 0 column); at 10.2 periods the error is the predicted
+    phase drift of the mode (~2.7x the table); at 10 and 10.5 periods, where
+    the drift is invisible, within a factor 1.5 of the table
 P6  leapfrog conserves the discrete energy; stable at 0.9 of the periodic
     CFL limit although cut cells are tiny; the ghost-point closure is not
     leapfrog on a discrete eigenvector follows the closed form
@@ -50,27 +51,57 @@ def test_p4_amg_multilevel_vs_direct():
     assert st.iterations < 40
 
 
-def _bessel_error(N):
+def _bessel_error(N, periods=10.2, with_prediction=False):
     grid, ls = ei.disk_bessel(N + 1)
     s = eb.build(grid, ls)
     X, Y = ei.grid_points(grid)
-    T = 10.2 * 2.0 * math.pi / ei.KAPPA_77
+    T = periods * 2.0 * math.pi / ei.KAPPA_77
     nsteps = math.ceil(T / (0.7 * grid.h))
     dt = T / nsteps
     xs = X.reshape(-1)[s.cp_nodes]
     ys = Y.reshape(-1)[s.cp_nodes]
-    _, u = solvers.leapfrog(s.A, ei.bessel_mode(xs, ys, -dt), ei.bessel_mode(xs, ys, 0.0), dt, nsteps)
-    return float(np.abs(u - ei.bessel_mode(xs, ys, nsteps * dt)).max()), grid.h
+    u0 = ei.bessel_mode(xs, ys, 0.0)
+    _, u = solvers.leapfrog(s.A, ei.bessel_mode(xs, ys, -dt), u0, dt, nsteps)
+    err = float(np.abs(u - ei.bessel_mode(xs, ys, nsteps * dt)).max())
+    if not with_prediction:
+        return err, grid.h
+    # phase drift of the standing mode: the discrete frequency w of the mode
+    # under leapfrog, 1 - lam dt^2 / 2 = cos(w dt), lam the Rayleigh quotient
+    # of the sampled mode on the EB operator
+    lam = float(u0 @ (s.A @ u0) / (u0 @ u0))
+    w = math.acos(1.0 - lam * dt * dt / 2.0) / dt
+    pred = float(np.abs(u0).max()) * abs(math.cos(w * nsteps * dt) - math.cos(ei.KAPPA_77 * nsteps * dt))
+    return err, pred
+
+
+TABLE1_THETA0 = {100: 3.6e-2, 200: 9.2e-3, 400: 2.5e-3}   # Table 1, theta = 0 column, N = 2.2 / h
 
 
 def test_p5_bessel_table1():
-    table = {100: 3.6e-2, 200: 9.2e-3, 400: 2.5e-3}
-    errs = {N: _bessel_error(N)[0] for N in (100, 200, 400)}
-    for N, ref in table.items():
-        assert ref / 4 < errs[N] < ref * 4, (N, errs[N], ref)
+    """At the stated 10.2 periods the leapfrog errors are ~2.7x Table 1's theta
+    = 0 column, with the table's rates; that excess is the phase drift of the
+    standing mode, which the dispersion relation of the discrete mode predicts
+    (the drift alone already exceeds the table at N = 100)."""
+    errs = {}
+    for N in (100, 200, 400):
+        err, pred = _bessel_error(N, with_prediction=True)
+        errs[N] = err
+        assert TABLE1_THETA0[N] / 4 < err < TABLE1_THETA0[N] * 4, (N, err)
+        assert 0.6 * err < pred < err, (N, err, pred)
     r1 = math.log2(errs[100] / errs[200])
     r2 = math.log2(errs[200] / errs[400])
     assert 1.6 < r1 < 2.4 and 1.6 < r2 < 2.4
+
+
+@pytest.mark.parametrize("periods", [10.0, 10.5])
+def test_p5_bessel_table1_at_phase_neutral_times(periods):
+    """At 10 or 10.5 periods cos(kappa t) = +-1, where a phase drift of the
+    standing mode shows only to second order: there the errors agree with
+    Table 1's theta = 0 column within a factor 1.5 on every grid."""
+    errs = {N: _bessel_error(N, periods)[0] for N in (100, 200, 400)}
+    for N, ref in TABLE1_THETA0.items():
+        assert ref / 1.5 < errs[N] < ref * 1.5, (N, errs[N], ref)
+    assert 1.7 < math.log2(errs[100] / errs[400]) / 2 < 2.3
 
 
 def test_p6_energy_and_cfl_stability():
@@ -225,3 +256,61 @@ def test_hash32_is_a_bijection_sample():
     x = np.arange(1 << 20)
     h = amg.hash32(x)
     assert np.unique(h).size == x.size
+
+
+def _lowbias32_inverse(y):
+    """The inverse of lowbias32 as its author published it beside the hash
+    (xorshift 16; multiply by 0x43021123; x ^= x >> 15 ^ x >> 30; multiply by
+    0x1d69e2a5; xorshift 16), written out independently of oracle.amg."""
+    y = np.asarray(y, dtype=np.uint64) & np.uint64(0xFFFFFFFF)
+    m = np.uint64(0xFFFFFFFF)
+    y ^= y >> np.uint64(16)
+    y = (y * np.uint64(0x43021123)) & m
+    y ^= (y >> np.uint64(15)) ^ (y >> np.uint64(30))
+    y = (y * np.uint64(0x1D69E2A5)) & m
+    y ^= y >> np.uint64(16)
+    return y
+
+
+def test_hash32_is_lowbias32_by_its_published_inverse():
+    """hash32 composed with the published inverse is the identity in both
+    orders; a wrong multiplier or shift anywhere in hash32 breaks it."""
+    rng = np.random.default_rng(3)
+    x = np.concatenate([np.arange(4096, dtype=np.uint64),
+                        rng.integers(0, 1 << 32, size=1 << 16, dtype=np.uint64)])
+    h = amg.hash32(x.astype(np.uint32)).astype(np.uint64)
+    assert np.array_equal(_lowbias32_inverse(h), x)
+    y = rng.integers(0, 1 << 32, size=1 << 16, dtype=np.uint64)
+    assert np.array_equal(amg.hash32(_lowbias32_inverse(y).astype(np.uint32)).astype(np.uint64), y)
+    # a low-bias hash spreads consecutive integers: about half of the output
+    # bits flip between i and i + 1
+    flips = np.unpackbits((h[1:4096] ^ h[:4095]).astype(">u4").view(np.uint8)).mean() * 32
+    assert 14.0 < flips < 18.0
+
+
+def _chain(w_left, w_right):
+    """Strength graph of the path 0-1-2-3-4 whose middle node 2 couples to 1
+    with weight w_left and to 3 with weight w_right."""
+    rows = [0, 1, 1, 2, 2, 3, 3, 4]
+    cols = [1, 0, 2, 1, 3, 2, 4, 3]
+    vals = [1.0, 1.0, w_left, w_left, w_right, w_right, 1.0, 1.0]
+    S = sp.csr_matrix((vals, (rows, cols)), shape=(5, 5))
+    S.sort_indices()
+    return S
+
+
+def test_aggregation_tie_break_in_single_precision():
+    """Roots 0 and 4: pass 1 puts 1 in aggregate 0 and 3 in aggregate 1; node 2
+    joins the aggregate of its strongest neighbour.  Weights that differ only
+    below single precision (one FP64 ulp) tie, and the tie goes to the lowest
+    aggregate id; a difference above FP32 resolution decides."""
+    roots = np.array([True, False, False, False, True])
+    one_ulp_up = np.nextafter(1.0, 2.0)
+    agg, nc = amg.aggregate_from_roots(_chain(1.0, one_ulp_up), roots)
+    assert nc == 2 and list(agg) == [0, 0, 0, 1, 1]
+    agg, _ = amg.aggregate_from_roots(_chain(one_ulp_up, 1.0), roots)
+    assert agg[2] == 0
+    agg, _ = amg.aggregate_from_roots(_chain(1.0, 1.0 + 1e-6), roots)
+    assert list(agg) == [0, 0, 1, 1, 1]
+    agg, _ = amg.aggregate_from_roots(_chain(1.0 + 1e-6, 1.0), roots)
+    assert agg[2] == 0
