@@ -27,13 +27,14 @@ from __future__ import annotations
 
 import math
 from dataclasses import dataclass, field
-from typing import List, Sequence, Tuple
+from typing import List, Optional, Sequence, Tuple
 
 import numpy as np
 
 # level-set kinds (values match the C enum eb_ls_kind)
 LS_QUADRIC = 0   # (rotated) ellipsoid / sphere / circle: sum_a (y_a/s_a)^2 - 1
 LS_STAR2D = 1    # rho - r(phi), r(phi) = r0 + sum_k a_k sin(k phi + p_k)
+LS_SAMPLED = 2   # psi given at every grid node (full-grid array)
 
 
 @dataclass
@@ -77,6 +78,7 @@ class LevelSet:
     ks: List[int] = field(default_factory=list)
     amps: List[float] = field(default_factory=list)
     phases: List[float] = field(default_factory=list)
+    psi: Optional[np.ndarray] = None   # LS_SAMPLED: psi at the nodes, shape Grid.shape()
 
 
 def sphere(center: Sequence[float], radius: float) -> LevelSet:
@@ -94,6 +96,26 @@ def star(center, r0, ks, amps, phases) -> LevelSet:
     c = tuple(center) + (0.0,) * (3 - len(center))
     return LevelSet(kind=LS_STAR2D, center=c, r0=float(r0), ks=[int(k) for k in ks],
                     amps=[float(a) for a in amps], phases=[float(p) for p in phases])
+
+
+def sampled(psi_nodes) -> LevelSet:
+    """A level set known only through its values at the grid nodes."""
+    return LevelSet(kind=LS_SAMPLED, psi=np.ascontiguousarray(psi_nodes, dtype=np.float64))
+
+
+def circle_distance_values(grid: "Grid", center, radius: float) -> np.ndarray:
+    """Signed distance |x - c| - R to a circle (2D) or sphere (3D), sampled at
+    the nodes: a smooth level set for the sampled-psi path."""
+    pts = grid_points(grid)
+    r2 = sum((pts[a] - center[a]) ** 2 for a in range(grid.dim))
+    return np.sqrt(r2) - radius
+
+
+def diamond_values(grid: "Grid", center, radius: float) -> np.ndarray:
+    """|x - c_x| + |y - c_y| (+ |z - c_z|) - R sampled at the nodes: linear
+    along every grid line except where the line crosses the diamond's axis."""
+    pts = grid_points(grid)
+    return sum(np.abs(pts[a] - center[a]) for a in range(grid.dim)) - radius
 
 
 # ---------------------------------------------------------------- workloads

@@ -73,8 +73,16 @@ typedef struct {
  *  EB_LS_STAR2D:  psi = |x - c| - r(phi), r(phi) = r0 + sum_k a[k] sin(k[k]
  *                 phi + p[k]), phi = atan2(y - c_y, x - c_x); 2D only.  Grid-
  *                 line roots by the Illinois (safeguarded secant) iteration,
- *                 the secant root finder named in Sec. 2.1. */
-typedef enum { EB_LS_QUADRIC = 0, EB_LS_STAR2D = 1 } eb_ls_kind;
+ *                 the secant root finder named in Sec. 2.1.
+ *  EB_LS_SAMPLED: psi known only at the grid nodes: psi points to a caller-
+ *                 owned DEVICE array of n0 n1 n2 doubles in the full-grid
+ *                 layout, read during eb_build only (not kept).  The crossing
+ *                 beyond a BP is the linear-ratio distance of Sec. 3.3 between
+ *                 the last inside node (psi_in < 0, m nodes beyond the BP) and
+ *                 the next node (psi_out >= 0): delta = m h + psi_in /
+ *                 (psi_in - psi_out) h.  Second-order accurate for a smooth
+ *                 psi; 2D and 3D.  The other fields are ignored. */
+typedef enum { EB_LS_QUADRIC = 0, EB_LS_STAR2D = 1, EB_LS_SAMPLED = 2 } eb_ls_kind;
 
 #define EB_STAR_MAX_TERMS 16
 typedef struct {
@@ -87,6 +95,7 @@ typedef struct {
   int k[EB_STAR_MAX_TERMS];
   double a[EB_STAR_MAX_TERMS];
   double p[EB_STAR_MAX_TERMS];
+  const double* psi;     /* EB_LS_SAMPLED only: psi at the nodes (device); NULL otherwise */
 } eb_levelset;
 
 typedef struct eb_handle eb_handle;
@@ -102,6 +111,10 @@ typedef struct {
   int tile[3];           /* tile extents in nodes */
   double max_delta_over_h;
   double min_abs_psi;    /* smallest |psi| over all nodes: the classification margin */
+  double min_dominance_margin;  /* smallest D_k - sum_j |h^2 a_kj| over the rows with a cut, i.e. the
+                                   smallest sum of c_s over the BP directions of a CP (h^2 units): > 0
+                                   means strict diagonal dominance of every cut row (Sec. 2.1); interior
+                                   rows have margin 0 */
 } eb_info_t;
 
 /* Algorithm 1 steps 1-3 on the device: classifies every node (mask, BP, CP),
@@ -111,7 +124,8 @@ typedef struct {
  * diagonal D_k = sum_s c_s with c_s = 1 towards a CP and c_s = h/(h+delta)
  * towards a BP (Sec. 2.1: g_Gamma of eq. 6 evaluated at the BP).
  * Synchronous (reads N_C back).  EB_ERR_GEOMETRY when an inside node lies on
- * the outermost ring of the grid or when there is no CP. */
+ * the outermost ring of the grid or when there is no CP; EB_ERR_INVALID for
+ * an EB_LS_SAMPLED level set without psi. */
 int eb_build(const eb_grid* grid, const eb_levelset* ls, eb_handle** out, cudaStream_t stream);
 void eb_destroy(eb_handle* eb);
 int eb_info(const eb_handle* eb, eb_info_t* out);

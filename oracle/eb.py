@@ -146,6 +146,8 @@ def build(grid: ei.Grid, ls: ei.LevelSet) -> EBSystem:
                     p.append(grid.lo[a2] + ia.astype(np.float64) * h)
                 if ls.kind == ei.LS_QUADRIC:
                     delta = geo.quadric_line_root(ls, dim, p, ax, float(sgn))
+                elif ls.kind == ei.LS_SAMPLED:
+                    delta = geo.sampled_line_distance(flat_psi[cur - sgn * st[ax]], flat_psi[cur], m - 1, h)
                 else:
                     ta = (m - 1).astype(np.float64) * h
                     tb = m.astype(np.float64) * h
@@ -207,6 +209,22 @@ def assemble(grid, cp_nodes, cp_of_node, flat_cls, diag) -> sp.csr_matrix:
     A = sp.csr_matrix((v, (r, c)), shape=(cp_nodes.size, cp_nodes.size))
     A.sort_indices()
     return A
+
+
+def dominance_margin(eb: EBSystem) -> float:
+    """Smallest strict diagonal-dominance margin of the cut rows of h^2 A:
+    D_k - sum_j |h^2 a_kj| = sum of c_s over the BP directions of CP k (Sec.
+    2.1: only the diagonal changes and |g| <= 1).  Positive for the line-by-
+    line closure (every c_s lies in (0, 1)); interior rows have margin 0."""
+    if eb.cut_cp.size == 0:
+        return 0.0
+    acc = np.zeros(eb.num_cp)
+    has = np.zeros(eb.num_cp, dtype=bool)
+    for s in range(2 * eb.grid.dim):   # direction order, as D_k is summed
+        m = eb.cut_dir == s
+        acc[eb.cut_cp[m]] += eb.cut_c[m]
+        has[eb.cut_cp[m]] = True
+    return float(acc[has].min())
 
 
 def rhs(eb: EBSystem, f_nodes: np.ndarray, ugamma: np.ndarray) -> np.ndarray:

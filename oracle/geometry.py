@@ -66,8 +66,28 @@ def psi_points(ls: ei.LevelSet, dim: int, pts):
 
 def psi_nodes(grid: ei.Grid, ls: ei.LevelSet) -> np.ndarray:
     """psi on the full grid, numpy shape grid.shape() (x fastest)."""
+    if ls.kind == ei.LS_SAMPLED:
+        psi = np.asarray(ls.psi, dtype=np.float64)
+        if psi.shape != grid.shape():
+            raise ValueError("sampled level set: psi must have the grid's shape")
+        return psi.copy()
     pts = ei.grid_points(grid)
     return psi_points(ls, grid.dim, list(pts))
+
+
+def sampled_line_distance(psi_in, psi_out, steps_in, h):
+    """Distance from a BP to Gamma along its grid line when psi is known only at
+    the nodes (Sec. 3.3, the linear-ratio distance of two grid points that
+    border x_Gamma): psi is taken linear between the last inside node psi_in
+    < 0, which lies steps_in nodes beyond the BP (0: the BP itself), and the
+    next node psi_out >= 0, so the crossing lies psi_in / (psi_in - psi_out) h
+    beyond the last inside node: delta = steps_in h + psi_in / (psi_in -
+    psi_out) h.  Second-order accurate for a smooth psi, exact where psi is
+    linear between the two nodes."""
+    psi_in = np.asarray(psi_in, dtype=np.float64)
+    psi_out = np.asarray(psi_out, dtype=np.float64)
+    steps = np.asarray(steps_in).astype(np.float64)
+    return steps * h + (psi_in / (psi_in - psi_out)) * h
 
 
 def quadric_line_root(ls: ei.LevelSet, dim: int, p, axis: int, sign):

@@ -43,13 +43,14 @@ class eb_grid(C.Structure):
 class eb_levelset(C.Structure):
     _fields_ = [("kind", C.c_int), ("center", C.c_double * 3), ("semi", C.c_double * 3), ("rot", C.c_double * 9),
                 ("r0", C.c_double), ("nk", C.c_int), ("k", C.c_int * STAR_MAX), ("a", C.c_double * STAR_MAX),
-                ("p", C.c_double * STAR_MAX)]
+                ("p", C.c_double * STAR_MAX), ("psi", C.c_void_p)]
 
 
 class eb_info_t(C.Structure):
     _fields_ = [("num_nodes", C.c_int64), ("num_cp", C.c_int64), ("num_bp", C.c_int64), ("num_cut", C.c_int64),
                 ("num_far", C.c_int64), ("num_tiles", C.c_int64), ("tile", C.c_int * 3),
-                ("max_delta_over_h", C.c_double), ("min_abs_psi", C.c_double)]
+                ("max_delta_over_h", C.c_double), ("min_abs_psi", C.c_double),
+                ("min_dominance_margin", C.c_double)]
 
 
 class amg_opts(C.Structure):
@@ -206,8 +207,25 @@ def make_grid(g) -> eb_grid:
     return out
 
 
-def make_levelset(ls) -> eb_levelset:
-    """eb_levelset from an ``eb_inputs.LevelSet``-like descriptor."""
+EB_LS_QUADRIC, EB_LS_STAR2D, EB_LS_SAMPLED = 0, 1, 2
+
+
+def sampled_psi_on_device(ls):
+    """The node values of a sampled level set as a contiguous CUDA float64
+    tensor (the caller keeps it alive while eb_build / batch_build run)."""
+    import numpy as np
+    import torch
+    if getattr(ls, "psi", None) is None:
+        raise ValueError("sampled level set without psi values")
+    psi = ls.psi
+    if not isinstance(psi, torch.Tensor):
+        psi = torch.from_numpy(np.ascontiguousarray(psi, dtype=np.float64))
+    return psi.to(device="cuda", dtype=torch.float64).contiguous()
+
+
+def make_levelset(ls, psi_dev=None) -> eb_levelset:
+    """eb_levelset from an ``eb_inputs.LevelSet``-like descriptor; psi_dev: the
+    CUDA tensor of node values of a sampled level set."""
     out = eb_levelset()
     out.kind = int(ls.kind)
     for a in range(3):
@@ -223,6 +241,10 @@ def make_levelset(ls) -> eb_levelset:
         out.k[j] = int(k)
         out.a[j] = float(a)
         out.p[j] = float(p)
+    if int(ls.kind) == EB_LS_SAMPLED:
+        if psi_dev is None:
+            raise ValueError("sampled level set: pass its node values on the device")
+        out.psi = C.c_void_p(psi_dev.data_ptr())
     return out
 
 
@@ -237,6 +259,7 @@ class Info:
     tile: tuple
     max_delta_over_h: float
     min_abs_psi: float
+    min_dominance_margin: float
 
 
 class EB:
@@ -248,12 +271,13 @@ class EB:
         self.grid = grid
         self.dim = grid.dim
         g = make_grid(grid)
-        ls = make_levelset(levelset)
+        psi_dev = sampled_psi_on_device(levelset) if int(levelset.kind) == EB_LS_SAMPLED else None
+        ls = make_levelset(levelset, psi_dev)
         _check(lib.eb_build(C.byref(g), C.byref(ls), C.byref(self._h), _stream(stream)))
         inf = eb_info_t()
         _check(lib.eb_info(self._h, C.byref(inf)))
         self.info = Info(inf.num_nodes, inf.num_cp, inf.num_bp, inf.num_cut, inf.num_far, inf.num_tiles,
-                         tuple(inf.tile), inf.max_delta_over_h, inf.min_abs_psi)
+                         tuple(inf.tile), inf.max_delta_over_h, inf.min_abs_psi, inf.min_dominance_margin)
 
     def close(self):
         if self._h:
@@ -317,7 +341,7 @@ class EB:
         inf = eb_info_t()
         _check(load().eb_info(self._h, C.byref(inf)))
         self.info = Info(inf.num_nodes, inf.num_cp, inf.num_bp, inf.num_cut, inf.num_far, inf.num_tiles,
-                         tuple(inf.tile), inf.max_delta_over_h, inf.min_abs_psi)
+                         tuple(inf.tile), inf.max_delta_over_h, inf.min_abs_psi, inf.min_dominance_margin)
 
     def retile(self, shape, stream=None):
         t = (C.c_int * 3)(*[int(v) for v in shape])
@@ -465,7 +489,7 @@ class _Borrowed(EB):
         inf = eb_info_t()
         _check(load().eb_info(self._h, C.byref(inf)))
         self.info = Info(inf.num_nodes, inf.num_cp, inf.num_bp, inf.num_cut, inf.num_far, inf.num_tiles,
-                         tuple(inf.tile), inf.max_delta_over_h, inf.min_abs_psi)
+                         tuple(inf.tile), inf.max_delta_over_h, inf.min_abs_psi, inf.min_dominance_margin)
 
     def close(self):
         self._h = C.c_void_p()
@@ -478,7 +502,8 @@ class Batch:
         lib = load()
         n = len(grids)
         G = (eb_grid * n)(*[make_grid(g) for g in grids])
-        L = (eb_levelset * n)(*[make_levelset(l) for l in levelsets])
+        psis = [sampled_psi_on_device(l) if int(l.kind) == EB_LS_SAMPLED else None for l in levelsets]
+        L = (eb_levelset * n)(*[make_levelset(l, p) for l, p in zip(levelsets, psis)])
         self._h = C.c_void_p()
         self.grids = list(grids)
         _check(lib.batch_build(C.cast(G, C.c_void_p), C.cast(L, C.c_void_p), n, C.byref(self._h), _stream(stream)))

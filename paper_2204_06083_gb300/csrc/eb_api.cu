@@ -63,6 +63,7 @@ int eb_info(const eb_handle* eb, eb_info_t* out) {
   out->tile[2] = h.g.tz;
   out->max_delta_over_h = h.max_delta_over_h;
   out->min_abs_psi = h.min_abs_psi;
+  out->min_dominance_margin = h.min_margin;
   return EB_OK;
 }
 

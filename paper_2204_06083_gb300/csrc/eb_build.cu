@@ -19,6 +19,7 @@ struct LSDev {
   int nk;
   int k[EB_STAR_MAX_TERMS];
   double a[EB_STAR_MAX_TERMS], p[EB_STAR_MAX_TERMS];
+  const double* psi;  // EB_LS_SAMPLED: psi at the nodes
 };
 
 __device__ __forceinline__ double node_coord(double lo, int64_t i, double h) {
@@ -154,6 +155,7 @@ struct BuildStats {
   unsigned long long num_far;
   double min_abs_psi;
   double max_delta_over_h;
+  double min_margin;   // smallest sum of c_s over the BP directions of a CP
 };
 
 // pass 1: psi at every node; border check; |psi| margin
@@ -163,9 +165,14 @@ __global__ void k_psi(Geometry G, LSDev L, double* psi, BuildStats* st) {
   if (!live) node = G.num_nodes - 1;   // keep the warp whole for the shuffle reduction
   int64_t i[3];
   unflatten(G, node, i);
-  double x[3];
-  for (int a = 0; a < 3; ++a) x[a] = a < G.dim ? node_coord(G.lo[a], i[a], G.h) : 0.0;
-  double v = psi_at(L, x);
+  double v;
+  if (L.kind == EB_LS_SAMPLED) {
+    v = L.psi[node];
+  } else {
+    double x[3];
+    for (int a = 0; a < 3; ++a) x[a] = a < G.dim ? node_coord(G.lo[a], i[a], G.h) : 0.0;
+    v = psi_at(L, x);
+  }
   if (live) psi[node] = v;
   if (v < 0.0 && on_border(G, i)) atomicExch(&st->border_inside, 1);
   double av = fabs(v);
@@ -232,7 +239,7 @@ __global__ void k_cut(Geometry G, LSDev L, const double* psi, const uint8_t* cod
   if (k >= num_cp) return;
   int64_t node = cp_node[k];
   uint8_t m = code[node] & 0x3F;
-  double D = 0.0;
+  double D = 0.0, margin = 0.0;
   int j = cut_off[k];
   int64_t i[3];
   unflatten(G, node, i);
@@ -258,6 +265,11 @@ __global__ void k_cut(Geometry G, LSDev L, const double* psi, const uint8_t* cod
       double delta;
       if (L.kind == EB_LS_QUADRIC) {
         delta = quadric_root(L, p, axis, (double)sg);
+      } else if (L.kind == EB_LS_SAMPLED) {
+        // linear ratio between the last inside node and the first outside one
+        // (Sec. 3.3): delta = (mm - 1) h + psi_in / (psi_in - psi_out) h
+        const double pin = psi[cur - st_ax], pout = psi[cur];
+        delta = __dadd_rn(__dmul_rn((double)(mm - 1), h), __dmul_rn(__ddiv_rn(pin, __dsub_rn(pin, pout)), h));
       } else {
         double ta = __dmul_rn((double)(mm - 1), h);
         double tb = __dmul_rn((double)mm, h);
@@ -272,11 +284,13 @@ __global__ void k_cut(Geometry G, LSDev L, const double* psi, const uint8_t* cod
         cut_xg[(int64_t)j * G.dim + a] = (a == axis) ? __dadd_rn(p[a], __dmul_rn((double)sg, delta)) : p[a];
       if (delta > h) atomicAdd(&st->num_far, 1ull);
       atomic_max_pos(&st->max_delta_over_h, fabs(delta / h));
+      margin = __dadd_rn(margin, cs);
       ++j;
     }
     D = (s == 0) ? cs : __dadd_rn(D, cs);
   }
   diag[node] = D;
+  if (m) atomic_min_pos(&st->min_margin, margin);
 }
 
 __global__ void k_tile_flags(Geometry G, const uint8_t* code, int32_t* tflag) {
@@ -349,11 +363,12 @@ static LSDev to_dev(const eb_levelset& ls, int dim) {
   for (int a = 0; a < 9; ++a) L.q[a] = ls.rot[a];
   L.r0 = ls.r0;
   L.nk = ls.nk;
-  for (int j = 0; j < ls.nk; ++j) {
+  for (int j = 0; j < ls.nk && j < EB_STAR_MAX_TERMS; ++j) {
     L.k[j] = ls.k[j];
     L.a[j] = ls.a[j];
     L.p[j] = ls.p[j];
   }
+  L.psi = ls.psi;
   return L;
 }
 
@@ -363,9 +378,11 @@ void build_handle(EBHandle& eb, const eb_grid& grid, const eb_levelset& ls, cuda
              EB_ERR_INVALID, "grid needs >= 3 nodes per used axis (and n[2] == 1 in 2D)");
   EB_REQUIRE(grid.n[0] % 2 == 0, EB_ERR_INVALID, "n[0] must be even");
   EB_REQUIRE(grid.h > 0.0 && std::isfinite(grid.h), EB_ERR_INVALID, "h must be positive");
-  EB_REQUIRE(ls.kind == EB_LS_QUADRIC || (ls.kind == EB_LS_STAR2D && grid.dim == 2), EB_ERR_INVALID,
-             "unknown level-set kind (STAR2D is 2D only)");
-  EB_REQUIRE(ls.nk >= 0 && ls.nk <= EB_STAR_MAX_TERMS, EB_ERR_INVALID, "star: nk out of range");
+  EB_REQUIRE(ls.kind == EB_LS_QUADRIC || (ls.kind == EB_LS_STAR2D && grid.dim == 2) || ls.kind == EB_LS_SAMPLED,
+             EB_ERR_INVALID, "unknown level-set kind (STAR2D is 2D only)");
+  EB_REQUIRE(ls.kind != EB_LS_SAMPLED || ls.psi != nullptr, EB_ERR_INVALID, "sampled level set: psi is NULL");
+  EB_REQUIRE(ls.kind != EB_LS_STAR2D || (ls.nk >= 0 && ls.nk <= EB_STAR_MAX_TERMS), EB_ERR_INVALID,
+             "star: nk out of range");
   if (ls.kind == EB_LS_QUADRIC)
     for (int a = 0; a < grid.dim; ++a) EB_REQUIRE(ls.semi[a] > 0.0, EB_ERR_INVALID, "quadric semi-axes must be > 0");
   int64_t nn = (int64_t)grid.n[0] * grid.n[1] * grid.n[2];
@@ -380,6 +397,7 @@ void build_handle(EBHandle& eb, const eb_grid& grid, const eb_levelset& ls, cuda
   for (int a = 0; a < 3; ++a) G.lo[a] = grid.lo[a];
   G.h = grid.h;
   eb.ls = ls;
+  eb.ls.psi = nullptr;  // the sampled values are read during the build only
   eb.home = s;
   LSDev L = to_dev(ls, grid.dim);
 
@@ -387,6 +405,7 @@ void build_handle(EBHandle& eb, const eb_grid& grid, const eb_levelset& ls, cuda
   BuildStats init{};
   init.min_abs_psi = 1e300;
   init.max_delta_over_h = 0.0;
+  init.min_margin = 1e300;
   EB_CUDA(cudaMemcpyAsync(st, &init, sizeof(init), cudaMemcpyHostToDevice, s));
 
   double* psi = dalloc<double>(nn, s, false);
@@ -445,6 +464,7 @@ void build_handle(EBHandle& eb, const eb_grid& grid, const eb_levelset& ls, cuda
   eb.num_far = (int64_t)hst.num_far;
   eb.max_delta_over_h = hst.max_delta_over_h;
   eb.min_abs_psi = hst.min_abs_psi;
+  eb.min_margin = eb.num_cut > 0 ? hst.min_margin : 0.0;
   dfree(psi, s); dfree(is_cp, s); dfree(cp_off, s); dfree(ncut, s); dfree(st, s);
   EB_CUDA(cudaStreamSynchronize(s));
 }

@@ -108,7 +108,7 @@ struct EBHandle {
   Geometry g;
   eb_levelset ls;
   int64_t num_cp = 0, num_bp = 0, num_cut = 0, num_far = 0, num_tiles = 0;
-  double max_delta_over_h = 0.0, min_abs_psi = 0.0;
+  double max_delta_over_h = 0.0, min_abs_psi = 0.0, min_margin = 0.0;
   uint8_t* code = nullptr;       // [num_nodes]
   double* diag = nullptr;        // [num_nodes] D_k (h^2 units) at CPs, 0 elsewhere
   float* diag32 = nullptr;       // [num_nodes] FP32 copy for the FP32 / BF16 kernels

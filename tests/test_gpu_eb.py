@@ -80,7 +80,61 @@ def _compare_build(grid, ls, exact):
 @pytest.mark.parametrize("name", list(CASES))
 def test_build_parity(name):
     grid, ls = CASES[name]()
-    _compare_build(grid, ls, exact=(ls.kind == ei.LS_QUADRIC))
+    h, ref = _compare_build(grid, ls, exact=(ls.kind == ei.LS_QUADRIC))
+    margin = oeb.dominance_margin(ref)
+    if ls.kind == ei.LS_QUADRIC:
+        assert h.info.min_dominance_margin == margin
+    else:
+        assert abs(h.info.min_dominance_margin - margin) <= 1e-12
+    assert h.info.min_dominance_margin > 0
+
+
+def _sampled_cases():
+    """Level sets known only at the nodes (Sec. 3.3): psi values are inputs, so
+    both sides run the same IEEE operations on the same numbers."""
+    g2 = ei.box_grid(2, 258)
+    g3 = ei.box_grid(3, 66)
+    g2b = ei.box_grid(2, 1026)
+    star_vals = lambda g: (np.hypot(*(p - c for p, c in zip(ei.grid_points(g), ei.STAR_CENTER)))
+                           - (0.5 + 0.1 * np.sin(5 * np.arctan2(ei.grid_points(g)[1] - ei.STAR_CENTER[1],
+                                                                  ei.grid_points(g)[0] - ei.STAR_CENTER[0]))))
+    return {
+        "circle_sdf_258": (g2, ei.sampled(ei.circle_distance_values(g2, (0.02, 0.01), 0.5))),
+        "diamond_258": (g2, ei.sampled(ei.diamond_values(g2, (0.0123, 0.0071), 0.71))),
+        "sphere_sdf_66": (g3, ei.sampled(ei.circle_distance_values(g3, (0.013, -0.021, 0.017), 0.6))),
+        "star_samples_1026": (g2b, ei.sampled(star_vals(g2b))),
+    }
+
+
+@pytest.mark.parametrize("name", list(_sampled_cases()))
+def test_sampled_levelset_build_parity(name):
+    """EB_LS_SAMPLED: classes, cuts, delta (linear ratio), D_k, crossing points
+    and the dominance margin bit-exact against the oracle; then a solve on the
+    sampled geometry against the oracle's."""
+    grid, ls = _sampled_cases()[name]
+    h, ref = _compare_build(grid, ls, exact=True)
+    assert h.info.min_dominance_margin == oeb.dominance_margin(ref)
+    eb = _eb()
+    rng = np.random.default_rng(11)
+    b = rng.standard_normal(grid.shape())
+    x_ref = __import__("scipy.sparse.linalg", fromlist=["spsolve"]).spsolve(ref.A.tocsc(), ref.from_grid(b))
+    solver = eb.AMG(h, 0.0)
+    x, st = solver.solve(torch.tensor(b, device="cuda"), rtol=1e-13, maxit=500)
+    err = np.linalg.norm(ref.from_grid(x.cpu().numpy()) - x_ref) / np.linalg.norm(x_ref)
+    assert err <= 1e-10, err
+
+
+def test_sampled_levelset_requires_values():
+    import ctypes as C
+    eb = _eb()
+    L = eb.load()
+    grid = ei.box_grid(2, 66)
+    g = eb.make_grid(grid)
+    ls = eb.eb_levelset()
+    ls.kind = eb.EB_LS_SAMPLED
+    out = C.c_void_p()
+    rc = L.eb_build(C.byref(g), C.byref(ls), C.byref(out), C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == eb.EB_ERR_INVALID
 
 
 @pytest.mark.parametrize("name", ["circle130", "randstar_300", "ellipsoid42"])

@@ -251,3 +251,104 @@ def test_unit_operator_is_scaled_operator():
     off = off.tocsr()
     off.eliminate_zeros()
     assert np.all(off.data == -1.0)
+
+
+# ------------------------------------------------ sampled level set (Sec. 3.3)
+
+def test_sampled_distance_is_second_order():
+    """psi given only at the nodes (signed distance to the K1 circle): the
+    linear-ratio distance of Sec. 3.3 approaches the exact crossing (closed
+    form of the same circle) as O(h^2) where the grid line crosses Gamma at an
+    angle, with the interpolation bound h^2 max|psi''| / (8 |psi'|), psi'' <= 1/rho
+    along a line; classes and cuts are those of the analytic circle.  Near
+    tangency |psi'| -> 0 and the error is larger (bounded here by h^1.5)."""
+    c, R = (0.02, 0.01), 0.5
+    errs, errs_all = [], []
+    for n in (64, 128, 256, 512):
+        grid = ei.box_grid(2, n)
+        h = grid.h
+        s_exact = eb.build(grid, ei.sphere(c, R))
+        s_samp = eb.build(grid, ei.sampled(ei.circle_distance_values(grid, c, R)))
+        assert np.array_equal(s_exact.cls, s_samp.cls)
+        assert np.array_equal(s_exact.cut_cp, s_samp.cut_cp) and np.array_equal(s_exact.cut_dir, s_samp.cut_dir)
+        err = np.abs(s_samp.cut_delta - s_exact.cut_delta)
+        ax = s_exact.cut_dir // 2
+        normal_ax = np.abs(s_exact.cut_xg[np.arange(ax.size), ax] - np.asarray(c)[ax]) / R   # |psi'| along the line
+        steep = normal_ax >= 0.5
+        assert steep.mean() > 0.6
+        assert err[steep].max() <= h * h / (8.0 * (R - 2 * h) * 0.5)
+        errs.append(err[steep].max())
+        errs_all.append(err.max())
+        assert err.max() <= 2.0 * h ** 1.5
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert min(rates) > 1.8, (errs, rates)
+
+
+def _diamond_exact_delta(s, center, R):
+    """Exact BP -> Gamma distance of every cut of the diamond sum |x_a - c_a| = R
+    and whether the linear-ratio segment holds no kink (last inside node and
+    first outside node on the same side of the diamond's axis)."""
+    grid = s.grid
+    dim, h = grid.dim, grid.h
+    ax = s.cut_dir // 2
+    sgn = np.where(s.cut_dir % 2 == 1, 1.0, -1.0)
+    bp = s.cut_xg.copy()
+    bp[np.arange(bp.shape[0]), ax] -= sgn * s.cut_delta
+    other = np.zeros(bp.shape[0])
+    for a in range(dim):
+        other += np.where(ax == a, 0.0, np.abs(bp[:, a] - center[a]))
+    x_bp = bp[np.arange(bp.shape[0]), ax]
+    c_ax = np.asarray(center)[ax]
+    x_gamma = c_ax + sgn * (R - other)          # the crossing on the outward side
+    exact = np.abs(x_gamma - x_bp)
+    last_in = x_bp + sgn * (np.floor(s.cut_delta / h + 1e-12) * h)
+    first_out = last_in + sgn * h
+    no_kink = np.sign(last_in - c_ax) == np.sign(first_out - c_ax)
+    return exact, no_kink
+
+
+@pytest.mark.parametrize("dim,n", [(2, 96), (3, 40)])
+def test_sampled_distance_exact_where_psi_is_linear(dim, n):
+    """On the diamond psi = sum |x_a - c_a| - R, psi is linear along a grid line
+    between two nodes on the same side of the axis: there the linear-ratio
+    distance is the exact crossing (round-off only)."""
+    grid = ei.box_grid(dim, n)
+    center = (0.0123, 0.0071, -0.0047)[:dim]
+    s = eb.build(grid, ei.sampled(ei.diamond_values(grid, center, 0.71)))
+    exact, ok = _diamond_exact_delta(s, center, 0.71)
+    assert ok.mean() > 0.9
+    assert np.abs(s.cut_delta[ok] - exact[ok]).max() < 1e-13
+
+
+def test_sampled_diamond_multilinear_exactness():
+    """P2 on the sampled diamond: every cut's segment is kink-free here (a BP
+    next to a CP leaves at least two inside nodes on its line), so every
+    crossing is exact and the discrete solution equals a grid-line-linear
+    harmonic u at every CP up to round-off."""
+    grid = ei.box_grid(2, 96)
+    center = (0.0123, 0.0071)
+    s = eb.build(grid, ei.sampled(ei.diamond_values(grid, center, 0.71)))
+    exact, ok = _diamond_exact_delta(s, center, 0.71)
+    assert ok.all()
+    xg = s.cut_xg
+    ug = ei.u_bilinear(xg[:, 0], xg[:, 1])
+    b = eb.rhs(s, np.zeros(grid.shape()), ug)
+    x = spla.spsolve(s.A.tocsc(), b)
+    X, Y = ei.grid_points(grid)
+    ue = ei.u_bilinear(X, Y).reshape(-1)[s.cp_nodes]
+    assert np.abs(x - ue).max() < 1e-10 * np.abs(ue).max()
+
+
+def test_dominance_margin_matches_rows():
+    """The reported margin is the smallest D_k - sum_j |off-diagonal| over the
+    cut rows of h^2 A, computed here from the assembled matrix."""
+    for grid, ls in (ei.circle_k1(64), (ei.box_grid(2, 80), ei.random_star(7)), ei.ellipsoid_k3(24, seed=0)):
+        s = eb.build(grid, ls)
+        H = (s.A * grid.h ** 2).tocsr()
+        d = H.diagonal()
+        off = np.asarray(abs(H).sum(axis=1)).ravel() - np.abs(d)
+        cut_rows = np.unique(s.cut_cp)
+        want = (d - off)[cut_rows].min()
+        got = eb.dominance_margin(s)
+        assert got > 0 and abs(got - want) < 1e-14
+        assert np.all((d - off)[np.setdiff1d(np.arange(s.num_cp), cut_rows)] == 0.0)
