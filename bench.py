@@ -63,7 +63,6 @@ LEAPFROG_BYTES_PER_DOF = {"f32": 13, "f64": 25}
 CONV_FLOP_PER_PX = 18432
 # and its bytes per pixel: 32 BF16 channels read and 32 written
 CONV_BYTES_PER_PX = 128
-CPU_SAMPLE_N = 112
 ALONE_LAUNCHES = 20
 L2_CLEAR_BYTES = 512 << 20
 ALONE_NOTE = ("amg_time_kernel: back-to-back launches of the kernel on the solver's own level data in one CUDA "
@@ -74,6 +73,10 @@ PROF_NOTE = ("CUDA events around every launch of the kernel in as many solves (b
              "after the timed ones on the same input; those use the captured iteration with a host check, since "
              "the timed device-side loop cannot bracket single launches")
 WORKLOADS = ("poisson3d", "poisson2d", "wave", "batched", "learned", "conv")
+
+
+def pk_hbm():
+    return peaks()[0]["hbm_gbs"]
 
 
 def peaks():
@@ -201,34 +204,102 @@ UNITS = {"poisson3d": "DOF/s", "poisson2d": "DOF/s", "wave": "DOF-steps/s", "bat
 
 # ------------------------------------------------------------------ oracle
 def _oracle_run(code, timeout=900):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-c", f"import sys; sys.path.insert(0, {ROOT!r})\n" + code],
-                       capture_output=True, text=True, env=env, timeout=timeout)
+                       capture_output=True, text=True, env=_oracle_env(), timeout=timeout)
     if r.returncode != 0:
         raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def host_cpu():
+    """Core count and CPU model of the host the oracle runs on."""
+    fields = {}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ":" in ln:
+                k, v = ln.split(":", 1)
+                fields.setdefault(k.strip(), v.strip())
+    except Exception:
+        pass
+    model = fields.get("Model name") or fields.get("Vendor ID")
+    import platform
+    return {"nproc": os.cpu_count(), "model": model or platform.processor() or platform.machine(),
+            "machine": platform.machine()}
+
+
+# The oracle on the full default workload: build, AMG setup (not timed), then
+# `reps` solves from x = 0, each timed.  READY / stdin: the all-cores run starts
+# every process's timed solves together.
+POISSON3D_ORACLE = """
+import json, sys, time
+import eb_inputs as ei
+from oracle import amg, eb, solvers
+g, ls = ei.ellipsoid_k3({n}, 0)
+s = eb.build(g, ls)
+pts = ei.grid_points(g)
+b = eb.rhs(s, ei.f_k3(*pts), ei.u_k3(*[s.cut_xg[:, a] for a in range(3)]))
+H = amg.setup(s.A)
+if {wait}:
+    print("READY", flush=True)
+    sys.stdin.readline()
+secs = []
+for _ in range({reps}):
+    t0 = time.perf_counter()
+    x, st = solvers.pcg(s.A, b, M=lambda r: amg.vcycle(H, r), rtol={rtol})
+    secs.append(time.perf_counter() - t0)
+print(json.dumps(dict(dof=s.num_cp, secs=secs, sec=sum(secs) / len(secs), iterations=st.iterations)))
+"""
+
+
+def _oracle_env():
+    return dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+
+
+def oracle_poisson3d(reps, n=N_FULL):
+    return _oracle_run(POISSON3D_ORACLE.format(n=n, wait=False, reps=reps, rtol=RTOL), timeout=1800)
+
+
+def oracle_poisson3d_all_cores(n=N_FULL, max_procs=16):
+    """One single-threaded oracle process per host core (at most max_procs),
+    each solving the full workload once, all timed solves started together
+    after every process has built its system and hierarchy: the host's
+    aggregate oracle throughput.  Returns (DOF/s, processes, record)."""
+    procs_n = max(1, min(os.cpu_count() or 1, max_procs))
+    code = f"import sys; sys.path.insert(0, {ROOT!r})\n" + POISSON3D_ORACLE.format(n=n, wait=True, reps=1, rtol=RTOL)
+    procs = [subprocess.Popen([sys.executable, "-c", code], stdin=subprocess.PIPE, stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True, env=_oracle_env()) for _ in range(procs_n)]
+    try:
+        for p in procs:
+            line = p.stdout.readline()
+            if line.strip() != "READY":
+                raise RuntimeError("oracle process failed: " + p.stderr.read()[-2000:])
+        for p in procs:
+            p.stdin.write("go\n")
+            p.stdin.flush()
+        recs = []
+        for p in procs:
+            out, err = p.communicate(timeout=1800)
+            if p.returncode != 0:
+                raise RuntimeError("oracle process failed: " + err[-2000:])
+            recs.append(json.loads(out.strip().splitlines()[-1]))
+    finally:
+        for p in procs:
+            if p.poll() is None:
+                p.kill()
+    wall = max(r["sec"] for r in recs)
+    return sum(r["dof"] for r in recs) / wall, procs_n, {"dof": recs[0]["dof"], "wall_s": wall,
+                                                         "iterations": recs[0]["iterations"]}
 
 
 def cpu_oracle_sample(w):
     """Times the oracle on a bounded sample of workload w in a fresh
     single-threaded process; returns (value, unit-consistent sample text, record)."""
     if w == "poisson3d":
-        rec = _oracle_run(f"""
-import json, time
-import eb_inputs as ei
-from oracle import amg, eb, solvers
-g, ls = ei.ellipsoid_k3({CPU_SAMPLE_N}, 0)
-s = eb.build(g, ls)
-pts = ei.grid_points(g)
-b = eb.rhs(s, ei.f_k3(*pts), ei.u_k3(*[s.cut_xg[:, a] for a in range(3)]))
-H = amg.setup(s.A)
-t0 = time.perf_counter()
-x, st = solvers.pcg(s.A, b, M=lambda r: amg.vcycle(H, r), rtol={RTOL})
-t1 = time.perf_counter()
-print(json.dumps(dict(dof=s.num_cp, sec=t1 - t0, iterations=st.iterations)))
-""")
-        return rec["dof"] / rec["sec"], (f"oracle AMG-PCG solve to {RTOL:g} of the same ellipsoid at {CPU_SAMPLE_N}^3 "
-                                         f"nodes (N_C={rec['dof']}, {rec['iterations']} its, {rec['sec']:.1f} s)"), rec
+        rec = oracle_poisson3d(1)
+        return rec["dof"] / rec["sec"], (f"oracle AMG-PCG solve to {RTOL:g} of the full workload ({N_FULL}^3 nodes, "
+                                         f"N_C={rec['dof']}, {rec['iterations']} its, {rec['sec']:.1f} s; "
+                                         f"build and AMG setup not timed)"), rec
     if w == "poisson2d":
         rec = _oracle_run(f"""
 import json, time
@@ -345,19 +416,34 @@ def run_reference(args):
         return 0
     w = args.workload
     vals, secs, rec, sample = [], [], None, ""
-    for i in range(args.warmup + args.steps):
-        v, sample, rec = cpu_oracle_sample(w)
-        if i >= args.warmup:
-            vals.append(v)
-            secs.append(rec["sec"])
+    if w == "poisson3d":
+        # the full workload: one build and AMG setup, then warm-up and timed solves
+        rec = oracle_poisson3d(args.warmup + args.steps)
+        secs = rec["secs"][args.warmup:]
+        vals = [rec["dof"] / t for t in secs]
+        sample = (f"oracle AMG-PCG solves to {RTOL:g} of the full workload ({N_FULL}^3 nodes, N_C={rec['dof']}, "
+                  f"{rec['iterations']} its each); one step = one solve; build and AMG setup not timed")
+    else:
+        for i in range(args.warmup + args.steps):
+            v, sample, rec = cpu_oracle_sample(w)
+            if i >= args.warmup:
+                vals.append(v)
+                secs.append(rec["sec"])
     value = statistics.mean(vals)
     unit = UNITS[w]
-    small = {"poisson3d": CPU_SAMPLE_N, "wave": 1024}.get(w)
+    small = {"wave": 1024}.get(w)
+    cfg = config_of(w, small)
+    cfg["same_config"] = small is None and w in ("poisson3d", "poisson2d")
+    cfg["l2"] = "not applicable: the oracle runs on the host cores"
+    if w == "poisson3d":
+        cfg["vcycle"] = ("FP64 oracle: Chebyshev-2 smoothed-aggregation V-cycle (numpy / scipy), plain FP64 PCG; "
+                         "the same hierarchy specification as the GPU path")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.mean(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_of(w, small),
-            "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample},
+            "config": cfg,
+            "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample,
+                             "host": host_cpu()},
             "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -532,6 +618,8 @@ def gpu_poisson(ctx, args, dim):
     prof_ms, prof_n = profiled(ctx, args, lambda: solver.solve(b, x=x.zero_(), rtol=RTOL, maxit=500, profile=1)[1])
     l1_ms, l1_n = (profiled(ctx, args, lambda: solver.solve(b, x=x.zero_(), rtol=RTOL, maxit=500, profile=3)[1])
                    if solver.num_levels > 2 else (0.0, 0))
+    xp_ms, xp_n = profiled(ctx, args, lambda: solver.solve(b, x=x.zero_(), rtol=RTOL, maxit=500, profile=4)[1])
+    up_ms, up_n = profiled(ctx, args, lambda: solver.solve(b, x=x.zero_(), rtol=RTOL, maxit=500, profile=5)[1])
     value = ctx.world * nc / (ms_per_step / 1000.0)
     extra = {}
     if dim == 3:
@@ -621,8 +709,38 @@ def gpu_poisson(ctx, args, dim):
                   "warm_l2_frac": l1_bytes / (alone[1]["warm_us"] * 1e-6) / 1e9 / pk["hbm_gbs"],
                   "in_solve_event_us": (l1_ms / l1_n) * 1000.0 if l1_n else None, "in_solve_launches_timed": l1_n,
                   "in_solve_timing": PROF_NOTE}
-        if l1_ms > prof_ms:  # the line's roofline is the kernel with the larger share of the solve
-            roof = level1
+    # the PCG's FP64 kernels, against the measured FP64 FMA peak (k_xpby_apply:
+    # per DOF the 7-point sum, 5 adds, and D x - sum, one FMA, then p = z + beta
+    # p, q = B z + beta q and the p.q partial, three FMAs: 13 FLOP; 41 B: z read,
+    # p and q read and written, the code byte) and the HBM peak (k_update_first:
+    # per DOF r, q, p, x, z read, x and r written in FP64, the level-0 right-hand
+    # side, iterate and direction written in the V-cycle's precision, the code
+    # byte: 69 B with FP32 V-cycle vectors, 81 B with FP64)
+    fp64_tflops = eb.fp64_peak_tflops(reps=20)
+    share = {"level0_smoother": prof_ms, "level1_smoother": l1_ms, "pcg_p_update_apply": xp_ms,
+             "pcg_xr_update": up_ms}
+    xp_flop = (13 if dim == 3 else 11) * nc
+    xp_s = (xp_ms / xp_n) / 1000.0 if xp_n else float("nan")
+    pcg_apply = {"bound": "alu", "kernel": f"k_xpby_apply<{dim}, false, true> (p update + next operator apply, FP64)",
+                 "achieved": xp_flop / xp_s / 1e12, "peak": fp64_tflops,
+                 "peak_kind": "measured FP64 FMA throughput (eb_fp64_peak, this run)", "unit": "TFLOP/s",
+                 "frac": xp_flop / xp_s / 1e12 / fp64_tflops, "traffic": None,
+                 "algorithmic_flop_per_launch": xp_flop, "algorithmic_bytes_per_launch": 41 * nc,
+                 "hbm_frac": 41 * nc / xp_s / 1e9 / pk_hbm(), "avg_launch_us": xp_s * 1e6, "launches_timed": xp_n,
+                 "timing": PROF_NOTE + "; each bracketed launch carries the event pair's few microseconds"}
+    up_bytes = (69 if dim == 3 else 81) * nc
+    up_s = (up_ms / up_n) / 1000.0 if up_n else float("nan")
+    pcg_update = {"bound": "hbm", "kernel": f"k_update_first<{dim}, {'float' if dim == 3 else 'double'}> "
+                                           "(x/r update + first level-0 smoothing step)",
+                  "achieved": up_bytes / up_s / 1e9, "peak": pk_hbm(), "peak_kind": "measured HBM copy (burst)",
+                  "unit": "GB/s", "frac": up_bytes / up_s / 1e9 / pk_hbm(), "traffic": None,
+                  "algorithmic_bytes_per_launch": up_bytes, "avg_launch_us": up_s * 1e6, "launches_timed": up_n,
+                  "timing": PROF_NOTE + "; each bracketed launch carries the event pair's few microseconds"}
+    if 1 in alone:
+        by_kernel = {"level0_smoother": stencil, "level1_smoother": level1, "pcg_p_update_apply": pcg_apply,
+                     "pcg_xr_update": pcg_update}
+        # the line's roofline is the kernel with the largest share of the solve
+        roof = by_kernel[max(share, key=share.get)]
     line = {"value": value, "ms_per_step": ms_per_step,
             "dtype": "f64 outer, f32 V-cycle" if dim == 3 else "f64",
             "num_cp": nc, "iterations": sts[-1].iterations, "time_to_tol_ms": ms_per_step,
@@ -630,13 +748,93 @@ def gpu_poisson(ctx, args, dim):
             "tile": tile, "autotune_us_per_vcycle": tune,
             "csr_entries_per_lane": epl, "csr_tune_us_per_vcycle": ({str(k): round(v, 2) for k, v in epl_us.items()} if epl_us else None),
             "roofline": roof, "stencil_roofline": stencil,
-            "kernel_time_ms_per_solve": {"level0_smoother": prof_ms / max(args.steps, 1),
-                                         "level1_smoother": l1_ms / max(args.steps, 1)},
+            "kernel_time_ms_per_solve": {k: v / max(args.steps, 1) for k, v in share.items()},
+            "pcg_rooflines": {"p_update_apply": pcg_apply, "xr_update": pcg_update},
+            "fp64_peak_tflops": fp64_tflops,
             "e2e": {"value": e2e_value, "unit": "DOF/s", "h2d_bytes_per_step": hb.numel() * 8,
                     "d2h_bytes_per_step": hx.numel() * 8},
             "gpu_launches": launches, "clocks": clocks}
     line.update(extra)
+    if dim == 3:
+        line["stencil_subrecords"] = stencil_subrecords(ctx, args, h)
     return line
+
+
+SUB_WAVE_STEPS = 320
+
+
+def stencil_subrecords(ctx, args, h3):
+    """The metric's stencil GB/s beside the solve: eb_apply on the solve's own
+    256^3 grid (FP64 and FP32) and the leapfrog step of the 4096^2 star wave
+    workload (FP32 and FP64, 320 steps = 10 graph chunks per timed call), each
+    against the measured HBM peak.  Algorithmic bytes per DOF: apply 16 (FP64)
+    / 8 (FP32): x read, y written; leapfrog 25 / 13: u^n, u^{n-1} read, u^{n+1}
+    written, the code byte."""
+    from paper_2204_06083_gb300 import autotune
+    import torch
+    import eb_inputs as ei
+    import paper_2204_06083_gb300 as eb
+    hbm = pk_hbm()
+    out = {}
+    nc = h3.info.num_cp
+    rng = torch.Generator(device=ctx.dev).manual_seed(5)
+    for name, dtype, bpd in (("apply_256cubed_f64", torch.float64, 16), ("apply_256cubed_f32", torch.float32, 8)):
+        xin = torch.randn(h3.shape(), generator=rng, device=ctx.dev, dtype=torch.float64).to(dtype)
+        y = torch.zeros_like(xin)
+        for _ in range(3):
+            h3.apply(xin, out=y)
+        cold = []
+        for i in range(3 + args.steps):
+            ctx.flush()
+            torch.cuda.synchronize()
+            t, _ = timed(lambda: h3.apply(xin, out=y))
+            if i >= 3:
+                cold.append(t)
+        reps = 50
+        tw, _ = timed(lambda: [h3.apply(xin, out=y) for _ in range(reps)])
+        cold_s = statistics.mean(cold) / 1000.0
+        warm_s = tw / reps / 1000.0
+        out[name] = {"bound": "hbm", "kernel": "k_apply (eb_apply, matrix free, active tiles)",
+                     "achieved": bpd * nc / cold_s / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": bpd * nc / cold_s / 1e9 / hbm, "algorithmic_bytes_per_launch": bpd * nc,
+                     "avg_launch_us": cold_s * 1e6,
+                     "timing": "one launch between CUDA events after a 512 MB L2 flush (DRAM-cold; the event "
+                               "pair's few microseconds included)",
+                     "warm_us": warm_s * 1e6, "warm_frac": bpd * nc / warm_s / 1e9 / hbm}
+        del xin, y
+    grid, ls = ei.star_wave(4096)
+    hw = eb.EB(grid, ls)
+    ncw = hw.info.num_cp
+    tile, _ = tune_tiles(lambda: autotune.tune_eb(hw, eb.EB_F32, reps=5, op=eb.EB_TUNE_LEAPFROG))
+    X, Y = ei.grid_points(grid)
+    c, w = ei.pulse_params(0)
+    dt = 0.9 * grid.h / math.sqrt(2.0)
+    u0 = torch.tensor(ei.pulse(X, Y, c, w), device=ctx.dev)
+    u1 = u0 - 0.5 * dt * dt * hw.apply(u0)
+    for name, dtype, bpd in (("leapfrog_4096sq_f32", torch.float32, 13), ("leapfrog_4096sq_f64", torch.float64, 25)):
+        a0, b0 = u0.to(dtype), u1.to(dtype)
+        a, bb = torch.empty_like(a0), torch.empty_like(b0)
+        ts = []
+        for i in range(3 + args.steps):
+            a.copy_(a0)
+            bb.copy_(b0)
+            ctx.flush()
+            torch.cuda.synchronize()
+            t, _ = timed(lambda: hw.wave_step(a, bb, dt, SUB_WAVE_STEPS))
+            if i >= 3:
+                ts.append(t)
+        step_s = statistics.mean(ts) / 1000.0 / SUB_WAVE_STEPS
+        out[name] = {"bound": "hbm", "kernel": f"k_leapfrog<{'float' if dtype == torch.float32 else 'double'}, 2> "
+                                               "(one launch per step, 32-step CUDA-graph chunks)",
+                     "achieved": bpd * ncw / step_s / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": bpd * ncw / step_s / 1e9 / hbm, "algorithmic_bytes_per_launch": bpd * ncw,
+                     "avg_launch_us": step_s * 1e6, "num_cp": ncw, "tile": tile,
+                     "timing": f"CUDA events around a {SUB_WAVE_STEPS}-step wave_step call (L2 flushed before it); "
+                               "per-step time = call time / steps; the two fields of the active tiles fit in L2, so "
+                               "the figure can exceed what DRAM alone would allow"}
+        del a, bb, a0, b0
+    hw.close()
+    return out
 
 
 def gpu_wave(ctx, args):
@@ -992,7 +1190,14 @@ def run_gpu(args):
     cpu = None
     if ctx.world == 1 and not args.no_cpu_baseline:
         v, sample, _ = cpu_oracle_sample(w)
-        cpu = {"value": v, "unit": UNITS[w], "cores": 1, "kind": "oracle", "sample": sample + ", one thread"}
+        cpu = {"value": v, "unit": UNITS[w], "cores": 1, "kind": "oracle", "sample": sample + ", one thread",
+               "same_config": w in ("poisson3d", "poisson2d"), "host": host_cpu()}
+        if w == "poisson3d":
+            va, procs, rec = oracle_poisson3d_all_cores()
+            cpu["all_cores"] = {"value": va, "unit": UNITS[w], "cores": procs, "kind": "oracle",
+                                "sample": (f"{procs} single-threaded oracle processes (one per host core, at most 16), "
+                                           f"each solving the full workload once, timed solves started together; "
+                                           f"aggregate DOF/s = sum N_C / slowest solve ({rec['wall_s']:.1f} s)")}
     line = {"metric": METRIC, "value": body.pop("value"), "unit": UNITS[w], "n_gpus": ctx.world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": body.pop("ms_per_step"),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": body.pop("dtype"),

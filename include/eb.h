@@ -260,6 +260,13 @@ enum { EB_TK_SMOOTH_STEP = 0 };
 int amg_time_kernel(const amg_handle* amg, int kernel, int level, int launches, int64_t clear_bytes, double* us_out,
                     cudaStream_t stream);
 
+/* Measured FP64 arithmetic peak of the current GPU (instrumentation; the paper
+ * has no counterpart): a kernel of independent fused multiply-add chains with
+ * no memory traffic, `reps` launches (1..10000) timed by CUDA events on
+ * stream; *tflops_out = FP64 TFLOP/s (an FMA counts 2).  The roof of the FP64
+ * kernels whose time is spent in the FP64 pipe.  Synchronous. */
+int eb_fp64_peak(int reps, double* tflops_out, cudaStream_t stream);
+
 typedef struct {
   int precond;           /* eb_pc_kind, default EB_PC_AMG */
   int check_every;       /* host convergence check period in iterations (default 1) */
@@ -269,7 +276,9 @@ typedef struct {
                             with a host convergence check between them; 0: direct launches */
   int profile;           /* 1: time every level-0 smoother launch with CUDA events; 2 (pcg_solve_nn):
                             time the learned stage's 32 -> 32 convolution launches instead; 3: time the
-                            level-1 (first coarse level, CSR) Chebyshev-step launches */
+                            level-1 (first coarse level, CSR) Chebyshev-step launches; 4: the PCG's
+                            p update + operator apply launches; 5: its x/r update launches (with an AMG
+                            V-cycle, fused with the first level-0 smoothing step) */
 } pcg_opts;
 
 typedef struct {

@@ -30,6 +30,13 @@ CODE_BP = 0x40
 CODE_CP = 0x80
 
 
+def fp64_peak_tflops(reps: int = 20, stream=None) -> float:
+    """Measured FP64 FMA throughput of the current GPU in TFLOP/s."""
+    out = C.c_double()
+    _check(load().eb_fp64_peak(int(reps), C.byref(out), _stream(stream)))
+    return out.value
+
+
 class EBError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"[eb status {code}] {msg}")
@@ -143,6 +150,7 @@ _SIGS = {
     "nn_precondition": (C.c_int, [_P, _P, C.c_int, _P, _P, _P]),
     "pcg_solve_nn": (C.c_int, [_P, _P, C.c_int, _P, _P, C.c_double, C.c_int, C.POINTER(pcg_opts),
                                C.POINTER(pcg_stats), _P]),
+    "eb_fp64_peak": (C.c_int, [C.c_int, _P, _P]),
     "eb_last_error": (C.c_char_p, []),
 }
 

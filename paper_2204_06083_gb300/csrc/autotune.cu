@@ -6,6 +6,7 @@
 // caller's stream, and keeps the fastest shape.
 #include "eb_solver.cuh"
 
+#include <algorithm>
 #include <vector>
 
 namespace ebk {
@@ -194,6 +195,58 @@ int amg_tune_csr(amg_handle* amg, int reps, double* us_out, int* best_out, cudaS
     }
     dfree(r, stream);
     dfree(z, stream);
+    EB_CUDA(cudaStreamSynchronize(stream));
+  });
+}
+
+}  // extern "C"
+
+namespace ebk {
+// FP64 arithmetic peak: every thread runs 8 independent chains of fused
+// multiply-adds (no memory traffic in the loop), so the FP64 pipes, not
+// latency, bound it.  The result is stored only if it were NaN (never), which
+// keeps the chains alive without a store per thread.
+constexpr int FP64_PEAK_ITERS = 2048;
+constexpr int FP64_PEAK_CHAINS = 8;
+__global__ void __launch_bounds__(256) k_fp64_fma_peak(double seed, double* sink) {
+  double a[FP64_PEAK_CHAINS];
+  const double m = 1.0 - 1e-9 * (threadIdx.x & 7);
+  const double c = 1e-9 * seed;
+#pragma unroll
+  for (int k = 0; k < FP64_PEAK_CHAINS; ++k) a[k] = seed + k;
+  for (int i = 0; i < FP64_PEAK_ITERS; ++i) {
+#pragma unroll
+    for (int k = 0; k < FP64_PEAK_CHAINS; ++k) a[k] = fma(a[k], m, c);
+  }
+  double t = 0.0;
+#pragma unroll
+  for (int k = 0; k < FP64_PEAK_CHAINS; ++k) t += a[k];
+  if (t != t) sink[0] = t;
+}
+}  // namespace ebk
+
+extern "C" {
+
+int eb_fp64_peak(int reps, double* tflops_out, cudaStream_t stream) {
+  if (!tflops_out || reps < 1 || reps > 10000) {
+    set_error("eb_fp64_peak: NULL output or reps not in [1, 10000]");
+    return EB_ERR_INVALID;
+  }
+  return guarded([&] {
+    double* sink = dalloc<double>(1, stream);
+    try {
+      int per_sm = 0;
+      EB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fp64_fma_peak, 256, 0));
+      const unsigned blocks = (unsigned)(std::max(per_sm, 1) * num_sms() * 4);
+      const double us = time_us([&] { k_fp64_fma_peak<<<blocks, 256, 0, stream>>>(1.0, sink); }, reps, stream);
+      EB_CUDA(cudaGetLastError());
+      const double flop = 2.0 * FP64_PEAK_ITERS * FP64_PEAK_CHAINS * 256.0 * blocks;
+      *tflops_out = flop / (us * 1e-6) / 1e12;
+    } catch (...) {
+      dfree(sink, stream);
+      throw;
+    }
+    dfree(sink, stream);
     EB_CUDA(cudaStreamSynchronize(stream));
   });
 }

@@ -596,6 +596,7 @@ void Solver::iteration(int kind, const double* b, double* x, cudaStream_t s,
   // q = h^2 (sigma I + A) p and the p.q partials come from the previous
   // k_xpby_apply; with an AMG V-cycle next, the x/r update also does its first
   // level-0 step
+  prof_mark(s, true, PROF_UPDATE);  // exactly one launch until the matching mark: fused or not
   bool fused = false;
   if (kind == EB_PC_AMG && H) {
     PcgUpdate u;
@@ -616,10 +617,13 @@ void Solver::iteration(int kind, const double* b, double* x, cudaStream_t s,
   if (!fused)
     EB_DIM_LAUNCH(dim, k_update_xr, nblk, eb->pairs(), sc, x, r, p, q, part_pq(), nblk, part_rr(), eb->g.h * eb->g.h, z,
                   flex ? part_rzo() : nullptr);
+  prof_mark(s, false, PROF_UPDATE);
   precondition(kind, r, z, s, fused);
   // r'r and the convergence test end the iteration: in the device-side loop
   // the p, q launch does them and sets the loop condition
+  prof_mark(s, true, PROF_XPBY);
   xpby_apply(op, flex, 0, s, cond);
+  prof_mark(s, false, PROF_XPBY);
   if (!cond) finalize(FIN_RR, part_rr(), s);
 }
 
@@ -747,7 +751,7 @@ static bool capturing(cudaStream_t s) {
 // pairs time the kernels back to back, without host-enqueue gaps.
 void Solver::prof_begin(int mode, cudaStream_t) {
   prof_on = mode != 0;
-  prof_what = (mode == PROF_CONV || mode == PROF_LEVEL1) ? mode : PROF_SMOOTHER;
+  prof_what = (mode >= PROF_CONV && mode <= PROF_UPDATE) ? mode : PROF_SMOOTHER;
   prof_n = g_pairs;
   prof_acc_ms = 0.0;
   prof_acc_n = 0;

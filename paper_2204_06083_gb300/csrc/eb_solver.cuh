@@ -17,8 +17,10 @@ namespace ebk {
 enum { FIN_INIT = 0, FIN_RZ0 = 1, FIN_ALPHA = 2, FIN_RR = 3, FIN_BETA = 4, FIN_RZ0F = 5, FIN_BETAF = 6, FIN_RRF = 7 };
 enum { PCG_FLAG_NONFINITE = 1, PCG_FLAG_BREAKDOWN = 2 };
 // what pcg_opts.profile times: the level-0 smoother launches, the learned stage's 32 -> 32
-// convolutions, or the level-1 (first coarse, CSR) smoother launches
-enum { PROF_SMOOTHER = 1, PROF_CONV = 2, PROF_LEVEL1 = 3 };
+// convolutions, the level-1 (first coarse, CSR) smoother launches, the PCG's p update +
+// apply launches (k_xpby_apply) or its x/r update launches (fused with the first level-0
+// smoothing step when an AMG V-cycle follows)
+enum { PROF_SMOOTHER = 1, PROF_CONV = 2, PROF_LEVEL1 = 3, PROF_XPBY = 4, PROF_UPDATE = 5 };
 
 // rz[iters & 1] holds r'z of the current iteration; the kernel that computes
 // the next one writes the other slot, so that no CTA reads a value another CTA

@@ -303,3 +303,50 @@ def test_full_size_pcg_256_benchmark_configuration():
     assert res <= 1e-10, res
     err = np.abs(x_cp - ei.u_k3(*[p.reshape(-1)[ref.cp_nodes] for p in pts])).max()
     assert err <= 2e-4, err
+
+
+def test_full_size_hierarchy_256_matches_oracle():
+    """The default benchmark's hierarchy at its full size (256^3 ellipsoid,
+    1.17M CPs): every level size and sparsity pattern, the aggregate ids of
+    every aggregation and P, A_l per row within 1e-13 of the oracle's
+    sequential smoothed aggregation (the same deterministic rules).  The FP32
+    V-cycle of the benchmark uses this hierarchy's values rounded to FP32."""
+    eb = _eb()
+    grid, ls = ei.ellipsoid_k3(256, seed=0)
+    h = eb.EB(grid, ls)
+    ref = oeb.build(grid, ls)
+    H = oamg.setup(ref.A)
+    g = eb.AMG(h, 0.0)
+    assert g.num_levels == len(H.levels) >= 3
+    for l, lev in enumerate(H.levels):
+        n = lev.A.shape[0]
+        assert g.rows[l] == n and g.nnz[l] == lev.A.nnz
+        rp, ci, v = g.level(l, 0)
+        M = _csr(rp, ci, v, n, n)
+        if l == 0:
+            assert np.array_equal(M.indices, lev.A.indices) and np.array_equal(M.data, lev.A.data)
+        else:
+            _close_rows(M, lev.A, 1e-13)
+        if l < len(H.levels) - 1:
+            assert np.array_equal(g.level(l, 2).cpu().numpy(), lev.agg), l
+            rp, ci, v = g.level(l, 1)
+            _close_rows(_csr(rp, ci, v, n, lev.P.shape[1]), lev.P, 1e-13)
+
+
+def test_pcg_kernel_profiling_modes_and_fp64_peak():
+    """pcg_opts.profile 4 / 5 time one launch of the p update + apply and of the
+    x/r update per iteration without changing the solve; the FP64 peak probe
+    returns a plausible figure (GB300: about 1.2 TFLOP/s FP64)."""
+    eb = _eb()
+    grid, ls = CASES["ellipsoid64"]()
+    h = eb.EB(grid, ls)
+    amg = eb.AMG(h, 0.0, vcycle_prec=eb.EB_F32)
+    b = torch.tensor(np.random.default_rng(4).standard_normal(h.shape()), device="cuda")
+    x0, st0 = amg.solve(b, rtol=1e-10)
+    for mode in (4, 5):
+        x, st = amg.solve(b, rtol=1e-10, profile=mode)
+        assert st.iterations == st0.iterations
+        assert torch.equal(x, x0)
+        assert st.iterations <= st.prof_launches <= st.iterations + 2 and st.prof_kernel_ms > 0.0
+    peak = eb.fp64_peak_tflops(reps=5)
+    assert 0.1 < peak < 100.0, peak
