@@ -206,6 +206,46 @@ def f_heat(x, y, t):
     return 12.0 * math.exp(-t) * np.sin(2.0 * x) * np.cos(3.0 * y)
 
 
+# ------------------------------------------- variable coefficient beta (eq. 3)
+
+def beta_half_points(grid: "Grid", beta_fn):
+    """beta at the half points of eq. 3: one full-grid array per axis a whose
+    entry at node i is beta(x_i + h/2 e_a) (the beta_{i+1/2} of that axis)."""
+    pts = grid_points(grid)
+    out = []
+    for a in range(grid.dim):
+        shifted = [p + (0.5 * grid.h if b == a else 0.0) for b, p in enumerate(pts)]
+        out.append(np.ascontiguousarray(beta_fn(*shifted), dtype=np.float64))
+    return out
+
+
+def beta_bone(x, y, z=None):
+    """beta = 2 + sin(x y) (the bone-shaped example of Sec. 3.3.1)."""
+    return 2.0 + np.sin(x * y)
+
+
+def heat_disk(n: int) -> Tuple["Grid", LevelSet]:
+    """The heat example of Sec. 3.4: disk of radius 0.5 about the origin in
+    [-1,1]^2 (psi = x^2 + y^2 - 0.25 < 0 inside)."""
+    return box_grid(2, n), sphere((0.0, 0.0), 0.5)
+
+
+def beta_heat_disk(x, y):
+    """beta = 0.25 - x^2 - y^2 (Sec. 3.4), positive inside the disk."""
+    return 0.25 - x * x - y * y
+
+
+def u_heat_disk(x, y, t):
+    """u = exp(-t) (x^2 + y^2 - 0.25): zero on the circle (Sec. 3.4)."""
+    return math.exp(-t) * (x * x + y * y - 0.25)
+
+
+def f_heat_disk(x, y, t):
+    """Source F of u_t = div(beta grad u) + F for u_heat_disk and
+    beta_heat_disk: F = u_t - div(beta grad u) = exp(-t) (7 r^2 - 0.75)."""
+    return math.exp(-t) * (7.0 * (x * x + y * y) - 0.75)
+
+
 KAPPA_77 = 31.4227941922
 
 

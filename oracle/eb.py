@@ -55,8 +55,10 @@ class EBSystem:
     cut_delta: np.ndarray    # float64 [n_cut], distance BP -> Gamma
     cut_xg: np.ndarray       # float64 [n_cut, dim], intersection point
     cut_c: np.ndarray        # float64 [n_cut], c_s = h/(h+delta)
-    diag: np.ndarray         # float64 [N_C], D_k = sum_s c_s (h^2 units)
+    diag: np.ndarray         # float64 [N_C], D_k = sum_s beta_s c_s (h^2 units)
     A: sp.csr_matrix         # [N_C, N_C], A = -L
+    beta: tuple = None       # None (beta = 1) or per axis a full-grid array: beta at node + h/2 e_axis
+    cut_beta: np.ndarray = None  # float64 [n_cut], beta at the half point between the CP and its BP
 
     @property
     def num_cp(self) -> int:
@@ -99,8 +101,21 @@ def classify(grid: ei.Grid, psi: np.ndarray) -> np.ndarray:
     return cls
 
 
-def build(grid: ei.Grid, ls: ei.LevelSet) -> EBSystem:
-    """Algorithm 1, steps 1-3, for beta = 1."""
+def half_point_beta(eb_or_beta, grid, cp_nodes, ax, sgn):
+    """beta at the half point between each CP and its neighbour in direction
+    (ax, sgn): beta_{i+1/2} is stored at node i (eq. 3), so the -x half point
+    of node i is beta_x[i - 1]."""
+    b = np.asarray(eb_or_beta[ax], dtype=np.float64).reshape(-1)
+    st = strides(grid)[ax]
+    return b[cp_nodes] if sgn > 0 else b[cp_nodes - st]
+
+
+def build(grid: ei.Grid, ls: ei.LevelSet, beta=None) -> EBSystem:
+    """Algorithm 1, steps 1-3.  beta: None for beta = 1, else one full-grid
+    array per axis holding beta at the half points node + h/2 e_axis (eq. 3).
+    With beta the stencil of eq. 3 weights each neighbour difference by the
+    beta of its half point; the closure of Sec. 2.1 then leaves beta_s c_s on
+    the diagonal and beta_s c_s u_Gamma / h^2 on the right-hand side."""
     dim, h = grid.dim, grid.h
     psi = geo.psi_nodes(grid, ls)
     cls = classify(grid, psi)
@@ -161,8 +176,10 @@ def build(grid: ei.Grid, ls: ei.LevelSet) -> EBSystem:
                 cut_dir.append(np.full(k.size, 2 * ax + sgn_bit))
                 cut_delta.append(delta)
                 cut_xg.append(xg)
+            if beta is not None:
+                cs = half_point_beta(beta, grid, cp_nodes, ax, sgn) * cs
             cs_per_dir.append(cs)
-    # D_k = sum_s c_s, summed in direction order (-x, +x, -y, +y, -z, +z)
+    # D_k = sum_s (beta_s) c_s, summed in direction order (-x, +x, -y, +y, -z, +z)
     for cs in cs_per_dir:
         diag = diag + cs
 
@@ -180,16 +197,23 @@ def build(grid: ei.Grid, ls: ei.LevelSet) -> EBSystem:
         cut_delta_a = np.zeros(0)
         cut_xg_a = np.zeros((0, dim))
     cut_c_a = h / (h + cut_delta_a)
+    cut_beta = np.ones(cut_cp_a.size)
+    if beta is not None:
+        beta = tuple(np.ascontiguousarray(b, dtype=np.float64).reshape(grid.shape()) for b in beta)
+        for ax in range(dim):
+            for sgn_bit, sgn in ((0, -1), (1, 1)):
+                m = cut_dir_a == 2 * ax + sgn_bit
+                cut_beta[m] = half_point_beta(beta, grid, cp_nodes[cut_cp_a[m]], ax, sgn)
 
-    A = assemble(grid, cp_nodes, cp_of_node, flat_cls, diag)
+    A = assemble(grid, cp_nodes, cp_of_node, flat_cls, diag, beta)
     return EBSystem(grid, ls, psi, cls, cp_nodes, cp_of_node, cut_cp_a, cut_dir_a,
-                    cut_delta_a, cut_xg_a, cut_c_a, diag, A)
+                    cut_delta_a, cut_xg_a, cut_c_a, diag, A, beta, cut_beta)
 
 
-def assemble(grid, cp_nodes, cp_of_node, flat_cls, diag) -> sp.csr_matrix:
-    """Eq. (3) with beta = 1 at the CPs (Algorithm 1 step 2); BP neighbours are
-    dropped from the off-diagonal pattern (their value is eliminated by the
-    closure, step 3), CP neighbours give -1/h^2."""
+def assemble(grid, cp_nodes, cp_of_node, flat_cls, diag, beta=None) -> sp.csr_matrix:
+    """Eq. (3) at the CPs (Algorithm 1 step 2); BP neighbours are dropped from
+    the off-diagonal pattern (their value is eliminated by the closure, step
+    3), CP neighbours give -beta_{half point}/h^2 (-1/h^2 for beta = 1)."""
     h2 = grid.h * grid.h
     st = strides(grid)
     rows = [np.arange(cp_nodes.size)]
@@ -202,7 +226,10 @@ def assemble(grid, cp_nodes, cp_of_node, flat_cls, diag) -> sp.csr_matrix:
             k = np.flatnonzero(j >= 0)
             rows.append(k)
             cols.append(j[k])
-            vals.append(np.full(k.size, -1.0 / h2))
+            if beta is None:
+                vals.append(np.full(k.size, -1.0 / h2))
+            else:
+                vals.append(-half_point_beta(beta, grid, cp_nodes[k], ax, sgn) / h2)
     r = np.concatenate(rows)
     c = np.concatenate(cols)
     v = np.concatenate(vals)
@@ -220,9 +247,10 @@ def dominance_margin(eb: EBSystem) -> float:
         return 0.0
     acc = np.zeros(eb.num_cp)
     has = np.zeros(eb.num_cp, dtype=bool)
+    w = eb.cut_c if eb.beta is None else eb.cut_beta * eb.cut_c
     for s in range(2 * eb.grid.dim):   # direction order, as D_k is summed
         m = eb.cut_dir == s
-        acc[eb.cut_cp[m]] += eb.cut_c[m]
+        acc[eb.cut_cp[m]] += w[m]
         has[eb.cut_cp[m]] = True
     return float(acc[has].min())
 
@@ -233,7 +261,8 @@ def rhs(eb: EBSystem, f_nodes: np.ndarray, ugamma: np.ndarray) -> np.ndarray:
     h2 = eb.grid.h * eb.grid.h
     b = -eb.from_grid(f_nodes)
     add = np.zeros(eb.num_cp)
-    np.add.at(add, eb.cut_cp, eb.cut_c * ugamma / h2)
+    w = eb.cut_c if eb.beta is None else eb.cut_beta * eb.cut_c
+    np.add.at(add, eb.cut_cp, w * ugamma / h2)
     return b + add
 
 

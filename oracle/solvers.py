@@ -9,6 +9,10 @@
   and Sec. 3.1 (eigenvalues bounded like the periodic problem).
 * Leapfrog: the theta-scheme of Sec. 3.5 at theta = 0,
   u^{n+1} = 2 u^n - u^{n-1} - dt^2 A u^n (homogeneous Dirichlet data).
+* theta-scheme for the wave equation (Sec. 3.5) with theta > 0; the printed
+  scheme lacks the Laplacian on its (1 - 2 theta) term, read as
+  (I + theta dt^2 A) u^{n+1} = 2 u^n - (1 - 2 theta) dt^2 A u^n - u^{n-1}
+  - theta dt^2 A u^{n-1}  (A = -L; theta = 0 is the leapfrog).
 * theta-method heat step (Sec. 3.4 uses Crank-Nicolson, theta = 1/2; theta = 1
   is backward Euler):
   (I/dt + theta A) u^{n+1} = (I/dt - (1-theta) A) u^n + theta b^{n+1}
@@ -110,3 +114,21 @@ def theta_heat_step(A, u, dt, theta, b_next, b_cur, M=None, rtol=1e-10, maxit=10
     lhs = (I / dt + theta * A).tocsr()
     r = u / dt - (1.0 - theta) * (A @ u) + theta * b_next + (1.0 - theta) * b_cur
     return pcg(lhs, r, x0=u, M=M, rtol=rtol, maxit=maxit)
+
+
+def theta_wave(A, u_prev, u_cur, dt, theta, nsteps, solve=None):
+    """nsteps of the theta-scheme of Sec. 3.5 (theta > 0, homogeneous
+    Dirichlet data) from (u^{-1}, u^0); returns (u^{N-1}, u^N).  solve(rhs,
+    guess) solves (I + theta dt^2 A) x = rhs; default: a sparse LU
+    factorisation computed once."""
+    n = A.shape[0]
+    dt2 = dt * dt
+    M = (sp.identity(n, format="csc") + (theta * dt2) * A).tocsc()
+    if solve is None:
+        lu = spla.splu(M)
+        solve = lambda rhs, guess: lu.solve(rhs)
+    a, b = np.array(u_prev, dtype=np.float64), np.array(u_cur, dtype=np.float64)
+    for _ in range(nsteps):
+        rhs = 2.0 * b - (1.0 - 2.0 * theta) * dt2 * (A @ b) - a - theta * dt2 * (A @ a)
+        a, b = b, solve(rhs, 2.0 * b - a)
+    return a, b
