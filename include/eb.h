@@ -130,6 +130,23 @@ int eb_build(const eb_grid* grid, const eb_levelset* ls, eb_handle** out, cudaSt
 void eb_destroy(eb_handle* eb);
 int eb_info(const eb_handle* eb, eb_info_t* out);
 
+/* Variable coefficient of eq. 3: div(beta grad u) = f.  beta_a_dev (a = x, y
+ * and, in 3D, z) are caller-owned DEVICE arrays of n0 n1 n2 doubles in the
+ * full-grid layout holding beta at the half point node + h/2 e_a of every
+ * node (the beta_{i+1/2} of eq. 3 on axis a); they are copied (FP64 and FP32)
+ * and may be freed on return.  Every operator of the handle then uses the
+ * beta-weighted stencil: the coupling of neighbours k, j is -beta/h^2 with the
+ * beta of their half point, and the closure of Sec. 2.1 leaves beta_s c_s on
+ * the diagonal and beta_s c_s u_Gamma / h^2 in eb_rhs, so D_k = sum_s beta_s
+ * c_s (eb_cp_data).  beta must be positive and finite at every half point a
+ * CP uses (EB_ERR_INVALID otherwise; for a negative constant beta solve the
+ * negated equation); beta_z_dev is ignored in 2D.  Call once, before
+ * amg_setup (hierarchies built earlier describe beta = 1 and must not be used
+ * with the handle afterwards).  EB_ERR_NOT_IMPLEMENTED for a geometry
+ * borrowed from a batch; the learned stage rejects such grids.  Synchronous. */
+int eb_set_beta(eb_handle* eb, const double* beta_x_dev, const double* beta_y_dev, const double* beta_z_dev,
+                cudaStream_t stream);
+
 /* Node classes as one byte per node (full grid), written to a device buffer
  * of num_nodes bytes: 0 outside, 0x40 BP, 0x80|m CP where bit s of m (s = 2
  * axis + (0 for -, 1 for +)) marks a BP neighbour in direction s. */

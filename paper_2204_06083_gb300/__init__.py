@@ -151,6 +151,7 @@ _SIGS = {
     "pcg_solve_nn": (C.c_int, [_P, _P, C.c_int, _P, _P, C.c_double, C.c_int, C.POINTER(pcg_opts),
                                C.POINTER(pcg_stats), _P]),
     "eb_fp64_peak": (C.c_int, [C.c_int, _P, _P]),
+    "eb_set_beta": (C.c_int, [_P, _P, _P, _P, _P]),
     "eb_last_error": (C.c_char_p, []),
 }
 
@@ -344,6 +345,19 @@ class EB:
             out = torch.zeros_like(x)
         _check(load().eb_apply(self._h, prec, _ptr(x), _ptr(out), _stream(stream)))
         return out
+
+    def set_beta(self, betas, stream=None):
+        """Variable coefficient of eq. 3: betas = one full-grid array per axis
+        (numpy or torch), beta at node + h/2 e_axis (eb_set_beta)."""
+        import numpy as np
+        import torch
+        dev = []
+        for b in betas:
+            t = b if isinstance(b, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(b, dtype=np.float64))
+            dev.append(t.to(device="cuda", dtype=torch.float64).contiguous())
+        ptrs = [_ptr(t) for t in dev] + [None] * (3 - len(dev))
+        _check(load().eb_set_beta(self._h, ptrs[0], ptrs[1], ptrs[2], _stream(stream)))
+        self._refresh_info()
 
     def _refresh_info(self):
         inf = eb_info_t()

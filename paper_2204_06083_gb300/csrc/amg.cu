@@ -43,8 +43,14 @@ __global__ void k_l0_count(Geometry G, const int32_t* cp_node, const uint8_t* co
   cnt[k] = 1 + 2 * G.dim - __popc((unsigned)m);
 }
 
+// beta pointers of a variable-coefficient grid (all null for beta = 1)
+struct BetaArgs {
+  const double* b[3];
+};
+
 __global__ void k_l0_fill(Geometry G, const int32_t* cp_node, const int32_t* cp_of_node, const uint8_t* code,
-                          const double* diag, int64_t ncp, double sigma, const int32_t* rp, int32_t* ci, double* v) {
+                          const double* diag, int64_t ncp, double sigma, const int32_t* rp, int32_t* ci, double* v,
+                          BetaArgs beta) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= ncp) return;
   const int64_t node = cp_node[k];
@@ -54,19 +60,20 @@ __global__ void k_l0_fill(Geometry G, const int32_t* cp_node, const int32_t* cp_
   const double off = __ddiv_rn(-1.0, h2);
   const int64_t st[3] = {1, (int64_t)G.n0, (int64_t)G.n0 * G.n1};
   int32_t e = rp[k];
-  // neighbours in ascending node order: -z, -y, -x, self, +x, +y, +z
+  // neighbours in ascending node order: -z, -y, -x, self, +x, +y, +z; with a
+  // variable beta the coupling is -beta(half point) / h^2 (eq. 3)
   for (int a = G.dim - 1; a >= 0; --a)
     if (!(m & (1u << (2 * a)))) {
       ci[e] = cp_of_node[node - st[a]];
-      v[e++] = off;
+      v[e++] = beta.b[0] ? __ddiv_rn(-beta.b[a][node - st[a]], h2) : off;
     }
-  const double D = m ? diag[node] : (double)(2 * G.dim);
+  const double D = (c & 0x7F) ? diag[node] : (double)(2 * G.dim);
   ci[e] = (int32_t)k;
   v[e++] = sigma == 0.0 ? __ddiv_rn(D, h2) : __dadd_rn(__ddiv_rn(D, h2), sigma);
   for (int a = 0; a < G.dim; ++a)
     if (!(m & (1u << (2 * a + 1)))) {
       ci[e] = cp_of_node[node + st[a]];
-      v[e++] = off;
+      v[e++] = beta.b[0] ? __ddiv_rn(-beta.b[a][node], h2) : off;
     }
 }
 
@@ -651,8 +658,9 @@ DCsr level0_csr(const EBHandle& eb, double sigma, cudaStream_t s) {
   A0.nnz = nnz;
   A0.ci = dalloc<int32_t>(nnz, s, false);
   A0.v = dalloc<double>(nnz, s, false);
+  const BetaArgs beta{{eb.beta64[0], eb.beta64[1], eb.beta64[2]}};
   k_l0_fill<<<blocks_for(ncp, 256), 256, 0, s>>>(G, eb.cp_node, eb.cp_of_node, eb.code, eb.diag, ncp, sigma, A0.rp,
-                                                  A0.ci, A0.v);
+                                                  A0.ci, A0.v, beta);
   EB_CUDA(cudaGetLastError());
   dfree(cnt, s);
   return A0;

@@ -38,7 +38,7 @@ struct GOp {
 
 template <class A, class DT>
 __device__ __forceinline__ A inv_diag_t(uint32_t c, const DT* __restrict__ diag, int32_t node, const GOp<A>& o) {
-  if (!(c & 0x3F)) return o.dinv_int;
+  if (!(c & 0x7F)) return o.dinv_int;
   return (A)1 / (o.sigma + (A)__ldg(diag + node) * o.inv_h2);
 }
 
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_step(TileView tv, const u
     uint32_t k0, k1;
     ld_codes(code, node, k0, k1);
     Two<A> xc, core;
-    stencil_pair<DIM, LdRO>(x, node, tv.nn, k0, k1, diag, tv.sy, tv.sz, xc, core);
+    stencil_tv<DIM, LdRO>(tv, x, node, k0, k1, diag, xc, core);
     const Two<A> bv = LdRO::ld2(b + node);
     Two<A> dv{0, 0};
     if (c1 != (A)0) {
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_resid(TileView tv, const uint8
     uint32_t c0, c1;
     ld_codes(code, node, c0, c1);
     Two<A> xc, core;
-    stencil_pair<DIM, LdRO>(x, node, tv.nn, c0, c1, diag, tv.sy, tv.sz, xc, core);
+    stencil_tv<DIM, LdRO>(tv, x, node, c0, c1, diag, xc, core);
     const Two<A> bv = LdRO::ld2(b + node);
     st2o(r + node, (c0 & CODE_CP) ? bv.x - (core.x * ot.inv_h2 + ot.sigma * xc.x) : (A)0,
          (c1 & CODE_CP) ? bv.y - (core.y * ot.inv_h2 + ot.sigma * xc.y) : (A)0);
@@ -357,9 +357,17 @@ __global__ void __launch_bounds__(TILE_NODES) k_prolong_mf(TileView tv, const ui
       const A ti = t_at(agg_node, sc, e, i);
       A sum = 0;
 #pragma unroll
-      for (int sdir = 0; sdir < 2 * DIM; ++sdir)
-        if (!(c & (1u << sdir))) sum += t_at(agg_node, sc, e, i + ((sdir & 1) ? st[sdir >> 1] : -st[sdir >> 1]));
-      const A D = (c & 0x3F) ? (A)__ldg(diag + i) : (A)(2 * DIM);
+      for (int sdir = 0; sdir < 2 * dim_of(DIM); ++sdir)
+        if (!(c & (1u << sdir))) {
+          const int32_t j = i + ((sdir & 1) ? st[sdir >> 1] : -st[sdir >> 1]);
+          const A tj = t_at(agg_node, sc, e, j);
+          // variable beta: each neighbour weighted by the beta of its half point
+          if constexpr ((DIM & DIM_VB) != 0)
+            sum += (A)__ldg(beta_ptrs(tv, diag)[sdir >> 1] + ((sdir & 1) ? i : j)) * tj;
+          else
+            sum += tj;
+        }
+      const A D = (c & 0x7F) ? (A)__ldg(diag + i) : (A)(2 * dim_of(DIM));
       const A at = (o.sigma + D * o.inv_h2) * ti - o.inv_h2 * sum;
       x[i] = cvt<V>(cvt<A>(x[i]) + ti - omega * inv_diag_t<A>(c, diag, i, o) * at);
     }
@@ -681,15 +689,16 @@ static int vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, co
 }
 
 int amg_vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, const VcycleDot* dot, bool first_done) {
-  const int dim = S.eb->g.dim;
-  if (S.opts.vcycle_prec == EB_F32)
-    return dim == 2 ? vcycle_grid<float, 2>(S, r, z, s, dot, first_done)
-                    : vcycle_grid<float, 3>(S, r, z, s, dot, first_done);
-  if (S.opts.vcycle_prec == EB_BF16)
-    return dim == 2 ? vcycle_grid<__nv_bfloat16, 2>(S, r, z, s, dot, first_done)
-                    : vcycle_grid<__nv_bfloat16, 3>(S, r, z, s, dot, first_done);
-  return dim == 2 ? vcycle_grid<double, 2>(S, r, z, s, dot, first_done)
-                  : vcycle_grid<double, 3>(S, r, z, s, dot, first_done);
+  int ret = 0;
+  dim_dispatch(*S.eb, [&](auto D) {
+    if (S.opts.vcycle_prec == EB_F32)
+      ret = vcycle_grid<float, D.value>(S, r, z, s, dot, first_done);
+    else if (S.opts.vcycle_prec == EB_BF16)
+      ret = vcycle_grid<__nv_bfloat16, D.value>(S, r, z, s, dot, first_done);
+    else
+      ret = vcycle_grid<double, D.value>(S, r, z, s, dot, first_done);
+  });
+  return ret;
 }
 
 template <class V, int DIM>
@@ -831,12 +840,10 @@ static void smoother_step(Solver& S, int level, cudaStream_t s) {
     const GOp<A> o{(A)inv_h2, (A)S.shift, (A)(1.0 / (S.shift + 2.0 * G.dim * inv_h2))};
     VecSet<V>& g = LV::grid(H);
     const V* b = std::is_same<V, double>::value ? reinterpret_cast<const V*>(S.r) : g.b;
-    if (G.dim == 2)
-      k_g_cheb_step<2, V, V><<<tile_grid(eb), TILE_NODES, 0, s>>>(eb.tv(), eb.code, diag_of<V>(eb), o, b, g.x, g.x2,
-                                                                    g.d, (A)cc.c1[k], (A)cc.c2[k]);
-    else
-      k_g_cheb_step<3, V, V><<<tile_grid(eb), TILE_NODES, 0, s>>>(eb.tv(), eb.code, diag_of<V>(eb), o, b, g.x, g.x2,
-                                                                    g.d, (A)cc.c1[k], (A)cc.c2[k]);
+    dim_dispatch(eb, [&](auto D) {
+      k_g_cheb_step<D.value, V, V><<<tile_grid(eb), TILE_NODES, 0, s>>>(eb.tv(), eb.code, diag_of<V>(eb), o, b, g.x,
+                                                                          g.x2, g.d, (A)cc.c1[k], (A)cc.c2[k]);
+    });
   } else {
     VecSet<V>& v = LV::vec(L);
     const int gA = group_width(L.A.nnz, L.A.n, S.csr_epl);

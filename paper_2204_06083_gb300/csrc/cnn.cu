@@ -1315,6 +1315,7 @@ int nn_geometry(const eb_handle* eb, uint8_t* code_dev, float* diag_dev, cudaStr
   }
   return guarded([&] {
     const EBHandle& E = eb->h;
+    EB_REQUIRE(!E.has_beta(), EB_ERR_NOT_IMPLEMENTED, "nn_geometry: the learned stage needs beta = 1");
     EB_CUDA(cudaMemcpyAsync(code_dev, E.code, (size_t)E.g.num_nodes, cudaMemcpyDeviceToDevice, stream));
     EB_CUDA(cudaMemcpyAsync(diag_dev, E.diag32, sizeof(float) * E.g.num_nodes, cudaMemcpyDeviceToDevice, stream));
   });
@@ -1329,6 +1330,7 @@ int nn_pairs(const amg_handle* amg, const double* b_dev, const double* xstar_dev
   return guarded([&] {
     Solver& S = const_cast<Solver&>(amg->s);
     EB_REQUIRE(S.H != nullptr, EB_ERR_INVALID, "nn_pairs: handle has no hierarchy");
+    EB_REQUIRE(!S.eb->has_beta(), EB_ERR_NOT_IMPLEMENTED, "nn_pairs: the learned stage needs beta = 1");
     const EBHandle& eb = *S.eb;
     const int64_t nn = eb.g.num_nodes;
     const unsigned nb = grid_blocks(nn);
@@ -1428,6 +1430,7 @@ int nn_precondition(const amg_handle* amg, nn_handle* nn, int mode, const double
   return guarded([&] {
     Solver& S = const_cast<Solver&>(amg->s);
     EB_REQUIRE(S.H != nullptr, EB_ERR_INVALID, "nn_precondition: handle has no hierarchy");
+    EB_REQUIRE(!S.eb->has_beta(), EB_ERR_NOT_IMPLEMENTED, "nn_precondition: the learned stage needs beta = 1");
     nn_stage_prepare(nn, *S.eb, stream);
     int64_t nl = 0;
     amg_vcycle_grid(S, r_dev, z_dev, stream);
@@ -1453,6 +1456,7 @@ int pcg_solve_nn(const amg_handle* amg, nn_handle* nn, int mode, const double* b
   int st = guarded([&] {
     Solver& S = const_cast<Solver&>(amg->s);
     EB_REQUIRE(S.H != nullptr, EB_ERR_INVALID, "pcg_solve_nn: handle has no hierarchy");
+    EB_REQUIRE(!S.eb->has_beta(), EB_ERR_NOT_IMPLEMENTED, "pcg_solve_nn: the learned stage needs beta = 1");
     nn_stage_prepare(nn, *S.eb, stream);
     S.nn = nn;
     S.nn_mode = mode;

@@ -67,14 +67,38 @@ int eb_info(const eb_handle* eb, eb_info_t* out) {
   return EB_OK;
 }
 
+// the public code bytes: the internal CODE_DIAG flag of CPs cleared
+__global__ void k_public_codes(int64_t n, const uint8_t* in, uint8_t* out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const uint8_t c = in[i];
+    out[i] = (c & CODE_CP) ? (uint8_t)(c & ~CODE_DIAG) : c;
+  }
+}
+
 int eb_classes(const eb_handle* eb, uint8_t* code_dev, cudaStream_t stream) {
   if (!eb || !code_dev) {
     set_error("eb_classes: NULL argument");
     return EB_ERR_INVALID;
   }
   return guarded([&] {
-    EB_CUDA(cudaMemcpyAsync(code_dev, eb->h.code, eb->h.g.num_nodes, cudaMemcpyDeviceToDevice, stream));
+    if (eb->h.has_beta()) {
+      k_public_codes<<<blocks_for(eb->h.g.num_nodes, 256), 256, 0, stream>>>(eb->h.g.num_nodes, eb->h.code, code_dev);
+      EB_CUDA(cudaGetLastError());
+    } else {
+      EB_CUDA(cudaMemcpyAsync(code_dev, eb->h.code, eb->h.g.num_nodes, cudaMemcpyDeviceToDevice, stream));
+    }
   });
+}
+
+int eb_set_beta(eb_handle* eb, const double* beta_x_dev, const double* beta_y_dev, const double* beta_z_dev,
+                cudaStream_t stream) {
+  if (!eb) {
+    set_error("eb_set_beta: NULL handle");
+    return EB_ERR_INVALID;
+  }
+  const double* b[3] = {beta_x_dev, beta_y_dev, beta_z_dev};
+  return guarded([&] { set_beta(eb->h, b, stream); });
 }
 
 __global__ void k_gather_diag(const int32_t* cp_node, const double* diag, int64_t n, double* out) {

@@ -558,7 +558,11 @@ void destroy_handle(EBHandle& eb) {
   eb.lf_graph.release();
   dfree(eb.code, s); dfree(eb.diag, s); dfree(eb.diag32, s); dfree(eb.cp_of_node, s); dfree(eb.cp_node, s);
   dfree(eb.tiles, s); dfree(eb.tile_base, s); dfree(eb.tile_lim, s); dfree(eb.pair_node, s); dfree(eb.cut_cp, s); dfree(eb.cut_dir, s); dfree(eb.cut_delta, s);
-  dfree(eb.cut_c, s); dfree(eb.cut_xg, s); dfree(eb.cut_off, s);
+  dfree(eb.cut_c, s); dfree(eb.cut_xg, s); dfree(eb.cut_off, s); dfree(eb.cut_bc, s);
+  for (int a = 0; a < 3; ++a) {
+    dfree(eb.beta64[a], s);
+    dfree(eb.beta32[a], s);
+  }
   cudaStreamSynchronize(s);
 }
 
@@ -588,11 +592,118 @@ void launch_rhs(const EBHandle& eb, const double* f, const double* ug, double* b
   const Geometry& G = eb.g;
   const double h2 = G.h * G.h;
   const unsigned blocks = tile_grid(eb);
+  const double* w = eb.cut_bc ? eb.cut_bc : eb.cut_c;  // beta_s c_s with a variable beta
   if (G.dim == 2)
-    k_rhs<2><<<blocks, TILE_NODES, 0, s>>>(eb.tv(), eb.code, eb.cp_of_node, eb.cut_off, eb.cut_c, f, ug, b, h2);
+    k_rhs<2><<<blocks, TILE_NODES, 0, s>>>(eb.tv(), eb.code, eb.cp_of_node, eb.cut_off, w, f, ug, b, h2);
   else
-    k_rhs<3><<<blocks, TILE_NODES, 0, s>>>(eb.tv(), eb.code, eb.cp_of_node, eb.cut_off, eb.cut_c, f, ug, b, h2);
+    k_rhs<3><<<blocks, TILE_NODES, 0, s>>>(eb.tv(), eb.code, eb.cp_of_node, eb.cut_off, w, f, ug, b, h2);
   EB_CUDA(cudaGetLastError());
+}
+
+// ------------------------------------------------------------ variable beta
+// bad = 1 if a beta some CP uses (the half points between it and its 2 dim
+// neighbours) is not positive and finite
+__global__ void k_beta_check(Geometry G, const double* bx, const double* by, const double* bz, const int32_t* cp_node,
+                             int64_t num_cp, int* bad) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= num_cp) return;
+  const int64_t node = cp_node[k];
+  const double* b[3] = {bx, by, bz};
+  for (int sdir = 0; sdir < 2 * G.dim; ++sdir) {
+    const int a = sdir >> 1;
+    const double beta = b[a][(sdir & 1) ? node : node - stride_of(G, a)];
+    if (!(beta > 0.0) || !isfinite(beta)) *bad = 1;
+  }
+}
+
+// D_k = sum_s beta_s c_s (c_s = 1 towards a CP, h/(h+delta) towards a BP),
+// summed in direction order with every product rounded (the same operations
+// as the assembled definition); cut_bc[j] = beta_s c_s of each cut (the
+// right-hand-side weights of Sec. 2.1 with beta); CODE_DIAG set on every CP;
+// the dominance margin of the cut rows.
+__global__ void k_beta_diag(Geometry G, const double* bx, const double* by, const double* bz, const int32_t* cp_node,
+                            const int32_t* cut_off, const double* cut_c, int64_t num_cp, uint8_t* code, double* diag,
+                            double* cut_bc, double* margin_min) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= num_cp) return;
+  const int64_t node = cp_node[k];
+  const uint8_t c = code[node];
+  const uint8_t m = c & 0x3F;
+  const double* b[3] = {bx, by, bz};
+  int j = cut_off[k];
+  double D = 0.0, margin = 0.0;
+  for (int sdir = 0; sdir < 2 * G.dim; ++sdir) {
+    const int a = sdir >> 1;
+    const int64_t st = stride_of(G, a);
+    const double beta = b[a][(sdir & 1) ? node : node - st];
+    double w = beta;
+    if (m & (1u << sdir)) {
+      w = __dmul_rn(beta, cut_c[j]);
+      cut_bc[j] = w;
+      margin = __dadd_rn(margin, w);
+      ++j;
+    } else {
+      w = __dmul_rn(beta, 1.0);
+    }
+    D = sdir == 0 ? w : __dadd_rn(D, w);
+  }
+  diag[node] = D;
+  code[node] = (uint8_t)(c | CODE_DIAG);
+  if (m) atomic_min_pos(margin_min, margin);
+}
+
+void set_beta(EBHandle& eb, const double* const* beta, cudaStream_t s) {
+  const Geometry& G = eb.g;
+  EB_REQUIRE(!eb.has_beta(), EB_ERR_INVALID, "eb_set_beta: beta is already set on this grid");
+  EB_REQUIRE(eb.tile_shift64 == nullptr, EB_ERR_NOT_IMPLEMENTED, "eb_set_beta: not available on batched grids");
+  for (int a = 0; a < G.dim; ++a) EB_REQUIRE(beta[a] != nullptr, EB_ERR_INVALID, "eb_set_beta: NULL beta array");
+  const int64_t nn = G.num_nodes;
+  const int T = 256;
+  double* bmin = dalloc<double>(1, s, false);
+  int* bad = dalloc<int>(1, s);
+  try {
+    // validate before anything of the handle changes
+    k_beta_check<<<blocks_for(eb.num_cp, 128), 128, 0, s>>>(G, beta[0], beta[1], G.dim == 3 ? beta[2] : nullptr,
+                                                             eb.cp_node, eb.num_cp, bad);
+    EB_CUDA(cudaGetLastError());
+    int hb = 0;
+    EB_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    EB_CUDA(cudaStreamSynchronize(s));
+    if (hb) throw Failure{EB_ERR_INVALID, "eb_set_beta: beta must be positive and finite at every half point a CP uses"};
+    const double init = 1e300;
+    EB_CUDA(cudaMemcpyAsync(bmin, &init, sizeof(double), cudaMemcpyHostToDevice, s));
+    for (int a = 0; a < G.dim; ++a) {
+      eb.beta64[a] = dalloc<double>(nn, s, false);
+      EB_CUDA(cudaMemcpyAsync(eb.beta64[a], beta[a], sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+      eb.beta32[a] = dalloc<float>(nn, s, false);
+      k_diag32<<<blocks_for(nn, T), T, 0, s>>>(nn, eb.beta64[a], eb.beta32[a]);
+    }
+    eb.cut_bc = dalloc<double>(eb.num_cut, s, false);
+    k_beta_diag<<<blocks_for(eb.num_cp, 128), 128, 0, s>>>(G, eb.beta64[0], eb.beta64[1],
+                                                            G.dim == 3 ? eb.beta64[2] : nullptr, eb.cp_node,
+                                                            eb.cut_off, eb.cut_c, eb.num_cp, eb.code, eb.diag,
+                                                            eb.cut_bc, bmin);
+    k_diag32<<<blocks_for(nn, T), T, 0, s>>>(nn, eb.diag, eb.diag32);
+    EB_CUDA(cudaGetLastError());
+    double hm = 0.0;
+    EB_CUDA(cudaMemcpyAsync(&hm, bmin, sizeof(double), cudaMemcpyDeviceToHost, s));
+    EB_CUDA(cudaStreamSynchronize(s));
+    eb.min_margin = eb.num_cut > 0 ? hm : 0.0;
+  } catch (...) {
+    dfree(bmin, s);
+    dfree(bad, s);
+    for (int a = 0; a < 3; ++a) {  // leave the handle without beta
+      dfree(eb.beta64[a], s);
+      dfree(eb.beta32[a], s);
+    }
+    dfree(eb.cut_bc, s);
+    throw;
+  }
+  dfree(bmin, s);
+  dfree(bad, s);
+  eb.lf_graph.release();
+  ++eb.tile_gen;  // captured graphs hold the view without beta
+  EB_CUDA(cudaStreamSynchronize(s));
 }
 
 }  // namespace ebk

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <functional>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/eb.h"
@@ -79,6 +80,9 @@ void dfree(T*& p, cudaStream_t s) {
 constexpr uint8_t CODE_OUT = 0x00;
 constexpr uint8_t CODE_BP = 0x40;
 constexpr uint8_t CODE_CP = 0x80;   // | mask of BP-neighbour directions
+// set on every CP once a variable beta is given: D_k is then read from the
+// diagonal array at every CP (interior CPs no longer have D = 2 dim)
+constexpr uint8_t CODE_DIAG = 0x40;
 
 // --------------------------------------------------------------- geometry
 struct Geometry {
@@ -131,8 +135,17 @@ struct EBHandle {
     v.by = ilog2(g.ty);
     v.pair_node = pair_node;
     v.npairs = num_pairs;
+    for (int a = 0; a < 3; ++a) {
+      v.beta64[a] = beta64[a];
+      v.beta32[a] = beta32[a];
+    }
     return v;
   }
+  // variable beta (eq. 3): null for beta = 1
+  double* beta64[3] = {nullptr, nullptr, nullptr};
+  float* beta32[3] = {nullptr, nullptr, nullptr};
+  double* cut_bc = nullptr;      // [num_cut] beta of the cut's half point times c_s (right-hand side weights)
+  bool has_beta() const { return beta64[0] != nullptr; }
   static int ilog2(int v) {
     int r = 0;
     while ((1 << r) < v) ++r;
@@ -176,6 +189,21 @@ inline const double* diag_of<double>(const EBHandle& eb) {
   return eb.diag;
 }
 
+// Calls f(std::integral_constant<int, D>{}) with the DIM template argument of
+// the grid kernels for eb: its dimension, with DIM_VB added when the grid has
+// a variable beta (the kernels then instantiate the weighted stencil).
+template <class F>
+inline void dim_dispatch(const EBHandle& eb, F&& f) {
+  const bool vb = eb.has_beta();
+  if (eb.g.dim == 2) {
+    if (vb) f(std::integral_constant<int, 2 | DIM_VB>{});
+    else f(std::integral_constant<int, 2>{});
+  } else {
+    if (vb) f(std::integral_constant<int, 3 | DIM_VB>{});
+    else f(std::integral_constant<int, 3>{});
+  }
+}
+
 // ----------------------------------------------------------- build / apply
 void build_handle(EBHandle& eb, const eb_grid& grid, const eb_levelset& ls, cudaStream_t s);
 void destroy_handle(EBHandle& eb);
@@ -185,6 +213,8 @@ template <class T>
 void launch_apply(const EBHandle& eb, const T* x, T* y, double sigma, cudaStream_t s);
 
 void launch_rhs(const EBHandle& eb, const double* f, const double* ug, double* b, cudaStream_t s);
+// variable beta of eq. 3 (device arrays, one per axis, beta at node + h/2 e_a)
+void set_beta(EBHandle& eb, const double* const* beta, cudaStream_t s);
 
 // Scans: exclusive prefix sum of n int32 values into out (out[n] = total).
 void exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s);

@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_leapfrog_noalloc(TileView tv, co
       uint32_t c0, c1;
       ld_codes(code, node, c0, c1);
       Two<A> xc, core;
-      stencil_pair<DIM, LdCG>(cur, node, tv.nn, c0, c1, diag, tv.sy, tv.sz, xc, core);
+      stencil_tv<DIM, LdCG>(tv, cur, node, c0, c1, diag, xc, core);
       const Two<A> po = LdCG::ld2(prev + node);
       const A n0 = (c0 & CODE_CP) ? (A)2 * xc.x - po.x - c2 * core.x : (A)0;
       const A n1 = (c1 & CODE_CP) ? (A)2 * xc.y - po.y - c2 * core.y : (A)0;
@@ -157,7 +157,8 @@ static int leapfrog_noalloc(const EBHandle& eb, T* ua, T* ub, int nsteps, double
   NoAllocWaveScratch* sc = scratch_for_current_device();
   if (nsteps <= 0) return EB_OK;
   const Geometry& G = eb.g;
-  void* fn = G.dim == 2 ? (void*)k_leapfrog_noalloc<T, 2> : (void*)k_leapfrog_noalloc<T, 3>;
+  void* fn = nullptr;
+  dim_dispatch(eb, [&](auto D) { fn = (void*)k_leapfrog_noalloc<T, D.value>; });
   int per_sm = 0;
   EB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TILE_NODES, 0));
   EB_REQUIRE(per_sm > 0, EB_ERR_INVALID, "wave_step_noalloc: kernel cannot be resident");

@@ -33,7 +33,7 @@ template <int DIM>
 __device__ __forceinline__ void op_pair(const TileView& tv, const double* x, int32_t node, uint32_t c0, uint32_t c1,
                                         const double* diag, const OpParams& o, Two<double>& xc, Two<double>& ax) {
   Two<double> core;
-  stencil_pair<DIM, LdRO>(x, node, tv.nn, c0, c1, diag, tv.sy, tv.sz, xc, core);
+  stencil_tv<DIM, LdRO>(tv, x, node, c0, c1, diag, xc, core);
   ax.x = core.x * o.inv_h2 + o.sigma * xc.x;
   ax.y = core.y * o.inv_h2 + o.sigma * xc.y;
 }
@@ -44,7 +44,7 @@ template <int DIM, bool SHIFT>
 __device__ __forceinline__ void op_pair_unit(const TileView& tv, const double* x, int32_t node, uint32_t c0,
                                              uint32_t c1, const double* diag, double sigma_h2, Two<double>& xc,
                                              Two<double>& ax) {
-  stencil_pair<DIM, LdRO>(x, node, tv.nn, c0, c1, diag, tv.sy, tv.sz, xc, ax);
+  stencil_tv<DIM, LdRO>(tv, x, node, c0, c1, diag, xc, ax);
   if (SHIFT) {
     ax.x += sigma_h2 * xc.x;
     ax.y += sigma_h2 * xc.y;
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_heat_rhs(TileView tv, const uint
     uint32_t c0, c1;
     ld_codes(code, node, c0, c1);
     Two<double> uc, core;
-    stencil_pair<DIM, LdRO>(u, node, tv.nn, c0, c1, diag, tv.sy, tv.sz, uc, core);
+    stencil_tv<DIM, LdRO>(tv, u, node, c0, c1, diag, uc, core);
     const Two<double> b1v = LdRO::ld2(b1 + node), b0v = LdRO::ld2(b0 + node);
     double v0 = uc.x / dt + theta * b1v.x, v1 = uc.y / dt + theta * b1v.y;
     if (theta < 1.0) {
@@ -336,6 +336,14 @@ __global__ void k_finalize(const double* part, int nblk, int op, PcgScalars* sc)
       kernel<2><<<(grid), TILE_NODES, 0, s>>>(__VA_ARGS__);                  \
     else                                                                     \
       kernel<3><<<(grid), TILE_NODES, 0, s>>>(__VA_ARGS__);                  \
+  } while (0)
+
+// EB_DIM_LAUNCH for the kernels that apply the stencil: the grid's dimension
+// with DIM_VB for a variable beta (dim_dispatch)
+#define EB_DIMV_LAUNCH(ebh, kernel, grid, ...)                                        \
+  do {                                                                                \
+    ++nlaunch;                                                                        \
+    dim_dispatch((ebh), [&](auto D_) { kernel<D_.value><<<(grid), TILE_NODES, 0, s>>>(__VA_ARGS__); }); \
   } while (0)
 
 static OpParams op_params(const Solver& S) {
@@ -438,7 +446,7 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
     EB_CUDA(cudaMemcpyAsync(sc, &init, sizeof(init), cudaMemcpyHostToDevice, s));
     // x is masked to the CPs (its non-CP entries are ignored on input)
     EB_DIM_LAUNCH(dim, k_mask_copy, nblk, tv, eb->code, x, x);
-    EB_DIM_LAUNCH(dim, k_resid, nblk, tv, eb->code, eb->diag, op, b, x, r, part_pq());
+    EB_DIMV_LAUNCH(*eb, k_resid, nblk, tv, eb->code, eb->diag, op, b, x, r, part_pq());
     finalize(FIN_INIT, part_pq(), s);
     EB_CUDA(cudaMemcpyAsync(sc_host, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
     EB_CUDA(cudaStreamSynchronize(s));
@@ -498,7 +506,7 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
     flags |= sc_host->flags;
     if (flags & (PCG_FLAG_NONFINITE | PCG_FLAG_BREAKDOWN)) break;
     // true residual at exit
-    EB_DIM_LAUNCH(dim, k_resid, nblk, tv, eb->code, eb->diag, op, b, x, r, part_pq());
+    EB_DIMV_LAUNCH(*eb, k_resid, nblk, tv, eb->code, eb->diag, op, b, x, r, part_pq());
     finalize(FIN_INIT, part_pq(), s);
     EB_CUDA(cudaMemcpyAsync(sc_host, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
     EB_CUDA(cudaStreamSynchronize(s));
@@ -539,7 +547,7 @@ int Solver::heat(double dt, double theta, const double* b1, const double* b0, do
   EB_REQUIRE(std::fabs(want - shift) <= 1e-12 * want, EB_ERR_INVALID,
              "heat: the hierarchy shift must equal 1/(theta dt)");
   const Geometry& G = eb->g;
-  EB_DIM_LAUNCH(G.dim, k_heat_rhs, nblk, eb->tv(), eb->code, eb->diag, 1.0 / (G.h * G.h), dt, theta, u, b1,
+  EB_DIMV_LAUNCH(*eb, k_heat_rhs, nblk, eb->tv(), eb->code, eb->diag, 1.0 / (G.h * G.h), dt, theta, u, b1,
                 b0 ? b0 : b1, tmp);
   EB_CUDA(cudaGetLastError());
   pcg_opts o{H ? EB_PC_AMG : EB_PC_JACOBI, 1, 0, 0};
@@ -549,17 +557,15 @@ int Solver::heat(double dt, double theta, const double* b1, const double* b0, do
 // One PCG iteration (device-side scalars; no host synchronisation).
 // the k_xpby_apply instance for the dimension, the shift and the loop test
 template <bool SHIFT, bool COND>
-static void launch_xpby_apply(int dim, unsigned g, cudaStream_t s, const TileView& tv, const PairList& pl,
+static void launch_xpby_apply(const EBHandle& eb, unsigned g, cudaStream_t s, const TileView& tv, const PairList& pl,
                               PcgScalars* sc, const uint8_t* code, const double* diag, const OpParams& op,
                               const double* z, double* p, double* q, int first, const double* rz, int nrz,
                               const double* rzo, int nupd, double* pq, const double* rr,
                               cudaGraphConditionalHandle h) {
-  if (dim == 2)
-    k_xpby_apply<2, SHIFT, COND><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, code, diag, op, z, p, q, first, rz, nrz, rzo,
-                                                          nupd, pq, rr, h);
-  else
-    k_xpby_apply<3, SHIFT, COND><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, code, diag, op, z, p, q, first, rz, nrz, rzo,
-                                                          nupd, pq, rr, h);
+  dim_dispatch(eb, [&](auto D) {
+    k_xpby_apply<D.value, SHIFT, COND><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, code, diag, op, z, p, q, first, rz, nrz,
+                                                                rzo, nupd, pq, rr, h);
+  });
 }
 
 void Solver::xpby_apply(const OpParams& op, bool flex, int first, cudaStream_t s,
@@ -573,7 +579,7 @@ void Solver::xpby_apply(const OpParams& op, bool flex, int first, cudaStream_t s
   ++nlaunch;
   auto go = [&](auto shift, auto with_cond) {
     launch_xpby_apply<decltype(shift)::value, decltype(with_cond)::value>(
-        dim, g, s, tv, pl, sc, eb->code, eb->diag, op, z, p, q, first, part_rz(), rz_n, rzo, nblk, part_pq(),
+        *eb, g, s, tv, pl, sc, eb->code, eb->diag, op, z, p, q, first, part_rz(), rz_n, rzo, nblk, part_pq(),
         part_rr(), h);
   };
   using T = std::true_type;

@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_apply(TileView tv, const uint8_t
     uint32_t c0, c1;
     ld_codes(code, node, c0, c1);
     Two<A> xc, core;
-    stencil_pair<DIM, LdRO>(x, node, tv.nn, c0, c1, diag, tv.sy, tv.sz, xc, core);
+    stencil_tv<DIM, LdRO>(tv, x, node, c0, c1, diag, xc, core);
     const A v0 = (c0 & CODE_CP) ? core.x * inv_h2 + sigma * xc.x : (A)0;
     const A v1 = (c1 & CODE_CP) ? core.y * inv_h2 + sigma * xc.y : (A)0;
     st2(y + node, v0, v1);
@@ -130,10 +130,9 @@ template <class T>
 void launch_apply(const EBHandle& eb, const T* x, T* y, double sigma, cudaStream_t s) {
   using A = typename AccOf<T>::type;
   const A inv_h2 = (A)(1.0 / (eb.g.h * eb.g.h));
-  if (eb.g.dim == 2)
-    k_apply<T, 2><<<tile_grid(eb), TILE_NODES, 0, s>>>(eb.tv(), eb.code, diag_of<T>(eb), x, y, (A)sigma, inv_h2);
-  else
-    k_apply<T, 3><<<tile_grid(eb), TILE_NODES, 0, s>>>(eb.tv(), eb.code, diag_of<T>(eb), x, y, (A)sigma, inv_h2);
+  dim_dispatch(eb, [&](auto D) {
+    k_apply<T, D.value><<<tile_grid(eb), TILE_NODES, 0, s>>>(eb.tv(), eb.code, diag_of<T>(eb), x, y, (A)sigma, inv_h2);
+  });
   EB_CUDA(cudaGetLastError());
 }
 
@@ -161,7 +160,7 @@ __global__ void __launch_bounds__(LF_THREADS) k_leapfrog(TileView tv, const uint
     uint32_t c0, c1;
     ld_codes(code, node, c0, c1);
     Two<A> xc, core;
-    stencil_pair<DIM, LdRO>(cur, node, tv.nn, c0, c1, diag, tv.sy, tv.sz, xc, core);
+    stencil_tv<DIM, LdRO>(tv, cur, node, c0, c1, diag, xc, core);
     const Two<A> po = LdCG::ld2(prev + node);  // read, then overwritten, by this thread only
     const A n0 = (c0 & CODE_CP) ? (A)2 * xc.x - po.x - c2 * core.x : (A)0;
     const A n1 = (c1 & CODE_CP) ? (A)2 * xc.y - po.y - c2 * core.y : (A)0;
@@ -245,7 +244,8 @@ int launch_leapfrog(const EBHandle& eb, T* ua, T* ub, int nsteps, double dt, cud
   if (nsteps <= 0) return EB_OK;
   const Geometry& G = eb.g;
   using A = typename AccOf<T>::type;
-  const void* fn = G.dim == 2 ? (const void*)k_leapfrog<T, 2> : (const void*)k_leapfrog<T, 3>;
+  const void* fn = nullptr;
+  dim_dispatch(eb, [&](auto D) { fn = (const void*)k_leapfrog<T, D.value>; });
   const unsigned blocks = leapfrog_grid<T>(eb, fn);
   A c2 = (A)(dt * dt / (G.h * G.h));  // dt^2 / h^2, the only constant of the step
   TileView tv = eb.tv();
@@ -306,10 +306,7 @@ int launch_leapfrog(const EBHandle& eb, T* ua, T* ub, int nsteps, double dt, cud
     const T* cur;
     T* prev;
     step_args(k, cur, prev);  // CHUNK is even: step k has the parity of k
-    if (G.dim == 2)
-      k_leapfrog<T, 2><<<blocks, LF_THREADS, 0, s>>>(tv, code, diag, cur, prev, c2);
-    else
-      k_leapfrog<T, 3><<<blocks, LF_THREADS, 0, s>>>(tv, code, diag, cur, prev, c2);
+    dim_dispatch(eb, [&](auto D) { k_leapfrog<T, D.value><<<blocks, LF_THREADS, 0, s>>>(tv, code, diag, cur, prev, c2); });
   }
   if (nsteps & 1) {
     if (G.dim == 2)

@@ -17,6 +17,10 @@
 namespace ebk {
 
 constexpr int TILE_NODES = 256;
+// flag in the DIM template argument of a grid kernel: the variable-coefficient
+// stencil (beta of eq. 3 read from the view); dim_of strips it
+constexpr int DIM_VB = 8;
+__host__ __device__ constexpr int dim_of(int d) { return d & 3; }
 constexpr int PAIR_THREADS = 128;  // threads per tile in the pair layout
 
 // default tile extents
@@ -46,6 +50,10 @@ struct TileView {
   // tile order; null for batched views
   const int32_t* pair_node = nullptr;
   int64_t npairs = 0;
+  // variable coefficient of eq. 3 (null for beta = 1): beta at the half point
+  // node + h/2 e_a of every node, per axis a, FP64 and FP32 copies
+  const double* beta64[3] = {nullptr, nullptr, nullptr};
+  const float* beta32[3] = {nullptr, nullptr, nullptr};
 };
 
 // Node of this thread in listed tile tt (one node per thread, 256 threads).
