@@ -325,6 +325,23 @@ int pcg_solve(const amg_handle* amg, const double* b_dev, double* x_dev, double 
 int heat_step(const amg_handle* amg, double dt, double theta, const double* b1_dev, const double* b0_dev,
               double* u_dev, double rtol, int maxit, pcg_stats* stats, cudaStream_t stream);
 
+/* nsteps of the implicit theta-scheme of Sec. 3.5 for u_tt = div(beta grad u)
+ * with homogeneous Dirichlet data, theta > 0 (theta = 1/2, 1/4: second-order
+ * unconditionally stable; theta = 1/12: fourth order in time), the printed
+ * scheme read with the Laplacian on its (1 - 2 theta) term:
+ *   (I + theta dt^2 A) u^{n+1} = 2 u^n - (1 - 2 theta) dt^2 A u^n - u^{n-1}
+ *                                - theta dt^2 A u^{n-1}.
+ * Each step solves (sigma I + A) u^{n+1} = sigma (2 u^n - u^{n-1}) - ((1 -
+ * 2 theta)/theta) A u^n - A u^{n-1} by PCG with amg's preconditioner from the
+ * guess 2 u^n - u^{n-1}; amg must have been set up with shift sigma = 1 /
+ * (theta dt^2).  On entry (u_prev, u_cur) = (u^{n-1}, u^n) (FP64 device
+ * fields), on exit (u^{n+nsteps-1}, u^{n+nsteps}).  stats (may be NULL):
+ * iterations summed over the steps, the largest residuals, converged = all
+ * steps converged.  Returns the first failing step's status (the fields then
+ * hold a partial run).  Synchronous. */
+int wave_theta_step(const amg_handle* amg, double dt, double theta, double* u_prev_dev, double* u_cur_dev,
+                    int nsteps, double rtol, int maxit, pcg_stats* stats, cudaStream_t stream);
+
 /* nsteps of the explicit leapfrog scheme (the theta-scheme of Sec. 3.5 with
  * theta = 0): u^{n+1} = 2 u^n - u^{n-1} - dt^2 A u^n (homogeneous Dirichlet
  * data).  On entry (u_prev, u_cur) = (u^{n-1}, u^n); on exit they hold

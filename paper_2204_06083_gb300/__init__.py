@@ -152,6 +152,8 @@ _SIGS = {
                                C.POINTER(pcg_stats), _P]),
     "eb_fp64_peak": (C.c_int, [C.c_int, _P, _P]),
     "eb_set_beta": (C.c_int, [_P, _P, _P, _P, _P]),
+    "wave_theta_step": (C.c_int, [_P, C.c_double, C.c_double, _P, _P, C.c_int, C.c_double, C.c_int,
+                                  C.POINTER(pcg_stats), _P]),
     "eb_last_error": (C.c_char_p, []),
 }
 
@@ -485,6 +487,14 @@ class AMG:
         _check(load().amg_time_kernel(self._h, EB_TK_SMOOTH_STEP, int(level), int(launches), int(clear_bytes),
                                       C.byref(us), _stream(stream)))
         return us.value
+
+    def wave_theta_step(self, u_prev, u_cur, dt, theta, nsteps, rtol=1e-10, maxit=1000, stream=None):
+        """nsteps implicit theta-scheme wave steps (the hierarchy's shift must be
+        1 / (theta dt^2)); (u_prev, u_cur) advanced in place."""
+        st = pcg_stats()
+        _check(load().wave_theta_step(self._h, float(dt), float(theta), _ptr(u_prev), _ptr(u_cur), int(nsteps),
+                                      float(rtol), int(maxit), C.byref(st), _stream(stream)))
+        return st
 
     def heat_step(self, u, b1, dt, theta=1.0, b0=None, rtol=1e-10, maxit=1000, stream=None):
         st = pcg_stats()

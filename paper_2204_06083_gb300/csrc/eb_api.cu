@@ -282,6 +282,19 @@ int pcg_solve(const amg_handle* amg, const double* b_dev, double* x_dev, double 
   return st != EB_OK ? st : rc;
 }
 
+int wave_theta_step(const amg_handle* amg, double dt, double theta, double* u_prev_dev, double* u_cur_dev,
+                    int nsteps, double rtol, int maxit, pcg_stats* stats, cudaStream_t stream) {
+  if (!amg || !u_prev_dev || !u_cur_dev || u_prev_dev == u_cur_dev) {
+    set_error("wave_theta_step: NULL or aliased argument");
+    return EB_ERR_INVALID;
+  }
+  int rc = EB_OK;
+  int st = guarded([&] {
+    rc = const_cast<Solver&>(amg->s).wave_theta(dt, theta, u_prev_dev, u_cur_dev, nsteps, rtol, maxit, stats, stream);
+  });
+  return st != EB_OK ? st : rc;
+}
+
 int heat_step(const amg_handle* amg, double dt, double theta, const double* b1_dev, const double* b0_dev,
               double* u_dev, double rtol, int maxit, pcg_stats* stats, cudaStream_t stream) {
   if (!amg || !b1_dev || !u_dev) {

@@ -242,6 +242,39 @@ __global__ void __launch_bounds__(TILE_NODES) k_xpby_apply(TileView tv, PairList
   if (threadIdx.x == 0) pq_part[blockIdx.x] = t;
 }
 
+// Right-hand side and guess of one implicit theta-scheme wave step (Sec. 3.5,
+// theta > 0): (sigma I + A) u^{n+1} = sigma (2 u^n - u^{n-1}) - c A u^n -
+// A u^{n-1}, sigma = 1 / (theta dt^2), c = (1 - 2 theta) / theta (the scheme
+// divided by theta dt^2); guess = 2 u^n - u^{n-1} (0 off the CPs).
+template <int DIM>
+__global__ void __launch_bounds__(TILE_NODES) k_wave_theta_rhs(TileView tv, const uint8_t* code, const double* diag,
+                                                               double inv_h2, double sigma, double c,
+                                                               const double* un, const double* um, double* rhs,
+                                                               double* guess) {
+  EB_PAIR_LOOP(DIM, tv, node) {
+    uint32_t c0, c1;
+    ld_codes(code, node, c0, c1);
+    Two<double> uc, ucore, mc, mcore;
+    stencil_tv<DIM, LdRO>(tv, un, node, c0, c1, diag, uc, ucore);
+    stencil_tv<DIM, LdRO>(tv, um, node, c0, c1, diag, mc, mcore);
+    const double g0 = 2.0 * uc.x - mc.x, g1 = 2.0 * uc.y - mc.y;
+    const double r0 = sigma * g0 - c * (ucore.x * inv_h2) - mcore.x * inv_h2;
+    const double r1 = sigma * g1 - c * (ucore.y * inv_h2) - mcore.y * inv_h2;
+    st2(rhs + node, (c0 & CODE_CP) ? r0 : 0.0, (c1 & CODE_CP) ? r1 : 0.0);
+    st2(guess + node, (c0 & CODE_CP) ? g0 : 0.0, (c1 & CODE_CP) ? g1 : 0.0);
+  }
+}
+
+// (a, b) <- (b, a) over the active tiles
+template <int DIM>
+__global__ void __launch_bounds__(TILE_NODES) k_swap_tiles(TileView tv, double* a, double* b) {
+  EB_PAIR_LOOP(DIM, tv, node) {
+    const Two<double> va = ld2d(a + node), vb = ld2d(b + node);
+    st2(a + node, vb.x, vb.y);
+    st2(b + node, va.x, va.y);
+  }
+}
+
 template <int DIM>
 __global__ void __launch_bounds__(TILE_NODES) k_copy_tiles(TileView tv, const double* a, double* b) {
   EB_PAIR_LOOP(DIM, tv, node) {
@@ -378,7 +411,7 @@ void Solver::free_work() {
   loop_release();
   if (cap_stream) cudaStreamDestroy(cap_stream);
   cap_stream = nullptr;
-  dfree(r, s); dfree(z, s); dfree(p, s); dfree(q, s); dfree(tmp, s); dfree(part, s); dfree(sc, s);
+  dfree(r, s); dfree(z, s); dfree(p, s); dfree(q, s); dfree(tmp, s); dfree(part, s); dfree(sc, s); dfree(wx, s);
   if (sc_host) cudaFreeHost(sc_host);
   sc_host = nullptr;
 }
@@ -552,6 +585,47 @@ int Solver::heat(double dt, double theta, const double* b1, const double* b0, do
   EB_CUDA(cudaGetLastError());
   pcg_opts o{H ? EB_PC_AMG : EB_PC_JACOBI, 1, 0, 0};
   return pcg(tmp, u, rtol, maxit, o, stats, s);
+}
+
+// nsteps implicit theta-scheme wave steps (Sec. 3.5): per step the right-hand
+// side and the guess 2 u^n - u^{n-1} in one pass, AMG-PCG (device loop) into
+// the solver's own x vector (fixed, so the captured loop is reused), and the
+// result copied over u^{n-1}, whose buffer then plays u^n.
+int Solver::wave_theta(double dt, double theta, double* ua, double* ub, int nsteps, double rtol, int maxit,
+                       pcg_stats* stats, cudaStream_t s) {
+  EB_REQUIRE(dt > 0.0 && theta > 0.0 && nsteps >= 0, EB_ERR_INVALID, "wave_theta_step: need dt > 0, theta > 0");
+  const double sigma = 1.0 / (theta * dt * dt);
+  EB_REQUIRE(std::fabs(sigma - shift) <= 1e-12 * sigma, EB_ERR_INVALID,
+             "wave_theta_step: the hierarchy shift must equal 1/(theta dt^2)");
+  const Geometry& G = eb->g;
+  if (!wx) wx = dalloc<double>(G.num_nodes, s);
+  const double c = (1.0 - 2.0 * theta) / theta;
+  const double inv_h2 = 1.0 / (G.h * G.h);
+  const TileView tv = eb->tv();
+  pcg_opts o{H ? EB_PC_AMG : EB_PC_JACOBI, 1, 1, 0};
+  pcg_stats total{};
+  total.converged = 1;
+  int rc = EB_OK;
+  for (int k = 0; k < nsteps && rc == EB_OK; ++k) {
+    double* prev = (k & 1) ? ub : ua;
+    const double* cur = (k & 1) ? ua : ub;
+    EB_DIMV_LAUNCH(*eb, k_wave_theta_rhs, nblk, tv, eb->code, eb->diag, inv_h2, sigma, c, cur, prev, tmp, wx);
+    EB_CUDA(cudaGetLastError());
+    pcg_stats st{};
+    rc = pcg(tmp, wx, rtol, maxit, o, &st, s);
+    EB_DIM_LAUNCH(G.dim, k_copy_tiles, nblk, tv, wx, prev);
+    total.iterations += st.iterations;
+    total.rel_residual = std::max(total.rel_residual, st.rel_residual);
+    total.true_rel_residual = std::max(total.true_rel_residual, st.true_rel_residual);
+    total.solve_ms += st.solve_ms;
+    total.launches += st.launches + 2;
+    total.converged = total.converged && st.converged;
+  }
+  if (rc == EB_OK && (nsteps & 1)) EB_DIM_LAUNCH(G.dim, k_swap_tiles, nblk, tv, ua, ub);
+  EB_CUDA(cudaGetLastError());
+  EB_CUDA(cudaStreamSynchronize(s));
+  if (stats) *stats = total;
+  return rc;
 }
 
 // One PCG iteration (device-side scalars; no host synchronisation).

@@ -50,6 +50,7 @@ struct Solver {
   int csr_epl = 2;  // CSR kernels of the V-cycle: target entries per lane of a row group (amg_tune_csr)
   // full-grid work vectors (touched on the active tiles only)
   double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *tmp = nullptr;
+  double* wx = nullptr;  // the implicit wave step's solution vector (allocated on first use)
   bool flexible() const { return H != nullptr && (opts.vcycle_prec == EB_F32 || opts.vcycle_prec == EB_BF16); }
   // the flexible (Polak-Ribiere) beta: reduced-precision V-cycle or learned stage
   bool flex_for(int kind) const { return kind == EB_PC_AMG_NN || (kind == EB_PC_AMG && flexible()); }
@@ -104,6 +105,8 @@ struct Solver {
   int pcg(const double* b, double* x, double rtol, int maxit, const pcg_opts& o, pcg_stats* stats, cudaStream_t s);
   int heat(double dt, double theta, const double* b1, const double* b0, double* u, double rtol, int maxit,
            pcg_stats* stats, cudaStream_t s);
+  int wave_theta(double dt, double theta, double* ua, double* ub, int nsteps, double rtol, int maxit,
+                 pcg_stats* stats, cudaStream_t s);
   void prof_begin(int mode, cudaStream_t s);
   void prof_mark(cudaStream_t s, bool start, int what = PROF_SMOOTHER);
   void prof_collect(int first, int count);
