@@ -246,6 +246,28 @@ def f_heat_disk(x, y, t):
     return math.exp(-t) * (7.0 * (x * x + y * y) - 0.75)
 
 
+# ------------------------------------------------- Helmholtz (Sec. 3.3.2)
+
+HELMHOLTZ_OMEGA = 50.0
+HELMHOLTZ_SOURCE = (-0.375, 0.125)
+
+
+def helmholtz_star(n: int) -> Tuple["Grid", LevelSet]:
+    """The Helmholtz example of Sec. 3.3.2: star r = 0.5 + 0.2 sin(5 theta)
+    about (0.02 sqrt5, 0.02 sqrt5) in [-1,1]^2, n nodes per axis."""
+    return box_grid(2, n), star(STAR_CENTER, 0.5, [5], [0.2], [0.0])
+
+
+def hat_source(grid: "Grid", center=HELMHOLTZ_SOURCE, amplitude: float = 1000.0, width_h: float = 2.0):
+    """amplitude times a 2D hat function of unit integral about center:
+    phi(dx / e) phi(dy / e) / e^2 with phi(t) = max(0, 1 - |t|) and e = width_h h
+    (the approximate delta of Sec. 3.3.2)."""
+    X, Y = grid_points(grid)
+    e = width_h * grid.h
+    phi = lambda t: np.maximum(0.0, 1.0 - np.abs(t))
+    return amplitude * phi((X - center[0]) / e) * phi((Y - center[1]) / e) / (e * e)
+
+
 KAPPA_77 = 31.4227941922
 
 

@@ -317,6 +317,20 @@ typedef struct {
 int pcg_solve(const amg_handle* amg, const double* b_dev, double* x_dev, double rtol, int maxit,
               const pcg_opts* opts, pcg_stats* stats, cudaStream_t stream);
 
+/* Solves (sigma I + A) x = b for any real sigma by preconditioned MINRES:
+ * the Helmholtz problem omega^2 u + Lap u = f of Sec. 3.3.2 is sigma =
+ * -omega^2 with b from eb_rhs (indefinite; the paper solves it by MINRES).
+ * precond: EB_PC_AMG (amg's V-cycle, built for amg's own shift, which must be
+ * positive definite -- e.g. shift 0: the Laplacian), EB_PC_JACOBI or
+ * EB_PC_NONE.  Stops when the preconditioned residual norm (the M^-1 norm
+ * MINRES minimises) falls to rtol times its initial value; stats report the
+ * iterations, that ratio (rel_residual) and the true ||b - (sigma I + A) x|| /
+ * ||b|| (true_rel_residual).  x holds the initial guess on entry.  Allocates
+ * its work vectors for the call.  EB_ERR_BREAKDOWN if the preconditioner is
+ * not positive definite, EB_ERR_NO_CONVERGENCE after maxit.  Synchronous. */
+int minres_solve(const amg_handle* amg, double sigma, int precond, const double* b_dev, double* x_dev, double rtol,
+                 int maxit, pcg_stats* stats, cudaStream_t stream);
+
 /* One theta-method step of u_t = L u + F (Sec. 3.4 uses theta = 1/2; theta = 1
  * is backward Euler): (I/dt + theta A) u1 = (I/dt - (1-theta) A) u0 + theta
  * b1 + (1-theta) b0, where b = eb_rhs(-F, u_Gamma) at the two times.  amg

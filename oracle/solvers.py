@@ -21,6 +21,7 @@
 """
 from __future__ import annotations
 
+import math
 from dataclasses import dataclass
 
 import numpy as np
@@ -132,3 +133,54 @@ def theta_wave(A, u_prev, u_cur, dt, theta, nsteps, solve=None):
         rhs = 2.0 * b - (1.0 - 2.0 * theta) * dt2 * (A @ b) - a - theta * dt2 * (A @ a)
         a, b = b, solve(rhs, 2.0 * b - a)
     return a, b
+
+
+def minres(A, b, x0=None, M=None, rtol=1e-10, maxit=10000):
+    """Preconditioned MINRES for symmetric (indefinite) A with a symmetric
+    positive definite preconditioner M (M maps r -> M^-1 r; None = identity):
+    the Lanczos process in the M-inner product with Givens rotations (Paige &
+    Saunders 1975; the three-term form of Elman, Silvester & Wathen, Finite
+    Elements and Fast Iterative Solvers, ch. 6).  Sec. 3.3.2 solves the
+    Helmholtz problem with MINRES.  Stops when the M^-1-norm of the residual
+    |eta| drops below rtol times its initial value gamma_1; returns (x, stats)
+    with the true relative residual ||b - A x|| / ||b|| at exit."""
+    n = b.size
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64)
+    bnorm = float(np.linalg.norm(b))
+    if bnorm == 0.0:
+        return np.zeros(n), SolveStats(0, 0.0, 0.0, True)
+    Mi = (lambda r: r.copy()) if M is None else M
+    v_prev = np.zeros(n)
+    v = b - A @ x
+    z = Mi(v)
+    gamma = math.sqrt(float(z @ v))
+    gamma1, gamma_prev = gamma, 1.0
+    eta = gamma
+    c_prev, c, s_prev, s = 1.0, 1.0, 0.0, 0.0
+    w_prev, w = np.zeros(n), np.zeros(n)
+    it = 0
+    conv = gamma == 0.0
+    while not conv and it < maxit:
+        z = z / gamma
+        Az = A @ z
+        delta = float(Az @ z)
+        v_next = Az - (delta / gamma) * v - (gamma / gamma_prev) * v_prev
+        z_next = Mi(v_next)
+        gamma_next = math.sqrt(max(float(z_next @ v_next), 0.0))
+        a0 = c * delta - c_prev * s * gamma
+        a1 = math.sqrt(a0 * a0 + gamma_next * gamma_next)
+        a2 = s * delta + c_prev * c * gamma
+        a3 = s_prev * gamma
+        c_prev, s_prev = c, s
+        c, s = a0 / a1, gamma_next / a1
+        w_next = (z - a3 * w_prev - a2 * w) / a1
+        x = x + (c * eta) * w_next
+        eta = -s * eta
+        w_prev, w = w, w_next
+        v_prev, v = v, v_next
+        z = z_next
+        gamma_prev, gamma = gamma, gamma_next
+        it += 1
+        conv = abs(eta) <= rtol * gamma1 or gamma == 0.0
+    tr = float(np.linalg.norm(b - A @ x)) / bnorm
+    return x, SolveStats(it, abs(eta) / gamma1 if gamma1 else 0.0, tr, conv)

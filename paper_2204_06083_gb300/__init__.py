@@ -152,6 +152,7 @@ _SIGS = {
                                C.POINTER(pcg_stats), _P]),
     "eb_fp64_peak": (C.c_int, [C.c_int, _P, _P]),
     "eb_set_beta": (C.c_int, [_P, _P, _P, _P, _P]),
+    "minres_solve": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.c_double, C.c_int, C.POINTER(pcg_stats), _P]),
     "wave_theta_step": (C.c_int, [_P, C.c_double, C.c_double, _P, _P, C.c_int, C.c_double, C.c_int,
                                   C.POINTER(pcg_stats), _P]),
     "eb_last_error": (C.c_char_p, []),
@@ -487,6 +488,17 @@ class AMG:
         _check(load().amg_time_kernel(self._h, EB_TK_SMOOTH_STEP, int(level), int(launches), int(clear_bytes),
                                       C.byref(us), _stream(stream)))
         return us.value
+
+    def minres(self, b, sigma, x=None, rtol=1e-10, maxit=5000, precond=EB_PC_AMG, stream=None, allow_noconv=False):
+        """(sigma I + A) x = b by preconditioned MINRES (sigma = -omega^2: Helmholtz)."""
+        import torch
+        if x is None:
+            x = torch.zeros_like(b)
+        st = pcg_stats()
+        _check(load().minres_solve(self._h, float(sigma), int(precond), _ptr(b), _ptr(x), float(rtol), int(maxit),
+                                   C.byref(st), _stream(stream)),
+               allow=(EB_ERR_NO_CONVERGENCE,) if allow_noconv else ())
+        return x, st
 
     def wave_theta_step(self, u_prev, u_cur, dt, theta, nsteps, rtol=1e-10, maxit=1000, stream=None):
         """nsteps implicit theta-scheme wave steps (the hierarchy's shift must be
