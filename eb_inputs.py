@@ -268,6 +268,66 @@ def hat_source(grid: "Grid", center=HELMHOLTZ_SOURCE, amplitude: float = 1000.0,
     return amplitude * phi((X - center[0]) / e) * phi((Y - center[1]) / e) / (e * e)
 
 
+# ------------------------------------ quantities of interest (Sec. 3.6)
+
+QOI_F = 3.0   # the source of both examples: Lap u = 3, u = 0 on the boundary
+
+
+def qoi_ellipse(semi_x: float, semi_y: float, n: int = 256, L: float = 2.25) -> Tuple["Grid", LevelSet]:
+    """First example of Sec. 3.6: the ellipse x^2/a^2 + y^2 a^2 = 1 (semi-axes
+    a and 1/a, area pi) in [-L, L]^2; the semi-axes are given explicitly so that
+    a parameter and its mirror 1/a can use exactly swapped values."""
+    return box_grid(2, n, -L, L), ellipsoid((0.0, 0.0), (semi_x, semi_y), np.eye(3))
+
+
+def qoi_rotated(theta: float, n: int = 502) -> Tuple["Grid", LevelSet]:
+    """Second example of Sec. 3.6: the ellipse (x cos t - y sin t)^2/16 +
+    (x sin t + y cos t)^2/4 < 1 in [-5, 5]^2 (the paper's 501^2 grid; n even
+    here)."""
+    c, s = math.cos(theta), math.sin(theta)
+    Q = np.array([[c, s, 0.0], [-s, c, 0.0], [0.0, 0.0, 1.0]])
+    return box_grid(2, n, -5.0, 5.0), ellipsoid((0.0, 0.0), (4.0, 2.0), Q)
+
+
+def qoi_point_weights(grid: "Grid", x0: float, y0: float) -> np.ndarray:
+    """Bilinear interpolation weights of the point (x0, y0) on the grid nodes."""
+    w = np.zeros(grid.shape())
+    fx = (x0 - grid.lo[0]) / grid.h
+    fy = (y0 - grid.lo[1]) / grid.h
+    i, j = int(math.floor(fx)), int(math.floor(fy))
+    tx, ty = fx - i, fy - j
+    w[j, i] = (1 - tx) * (1 - ty)
+    w[j, i + 1] = tx * (1 - ty)
+    w[j + 1, i] = (1 - tx) * ty
+    w[j + 1, i + 1] = tx * ty
+    return w
+
+
+def qoi_rect_weights(grid: "Grid", xr=(-1.0, 1.0), yr=(-0.5, 0.5)) -> np.ndarray:
+    """h^2 at the nodes inside the rectangle: the sum of u times these is the
+    integral of u over it (node rule)."""
+    X, Y = grid_points(grid)
+    inside = (X >= xr[0]) & (X <= xr[1]) & (Y >= yr[0]) & (Y <= yr[1])
+    return np.where(inside, grid.h * grid.h, 0.0)
+
+
+def qoi_ellipse_exact(semi_x: float, semi_y: float) -> float:
+    """u(0, 0) of Lap u = 3 in an ellipse with u = 0 on it: u = C (x^2/p^2 +
+    y^2/q^2 - 1) with 2 C (1/p^2 + 1/q^2) = 3."""
+    return -QOI_F / (2.0 * (1.0 / semi_x ** 2 + 1.0 / semi_y ** 2))
+
+
+def qoi_rotated_exact(theta: float) -> float:
+    """The integral of u over [-1,1] x [-0.5,0.5] for the rotated ellipse:
+    u = C (x'^2/16 + y'^2/4 - 1), C = 3 / (2 (1/16 + 1/4)) = 4.8; over the
+    rectangle the mixed moment vanishes, int x^2 = 2/3, int y^2 = 1/6, area 2."""
+    c2, s2 = math.cos(theta) ** 2, math.sin(theta) ** 2
+    C = QOI_F / (2.0 * (1.0 / 16.0 + 1.0 / 4.0))
+    ix = c2 * (2.0 / 3.0) + s2 / 6.0
+    iy = s2 * (2.0 / 3.0) + c2 / 6.0
+    return C * (ix / 16.0 + iy / 4.0 - 2.0)
+
+
 KAPPA_77 = 31.4227941922
 
 

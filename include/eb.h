@@ -404,12 +404,22 @@ const eb_handle* batch_geometry(const batch_handle* b, int g);
 /* eb_rhs for every geometry, in the batch layout. */
 int batch_rhs(const batch_handle* b, const double* f_all, const double* ug_all, double* b_all, cudaStream_t stream);
 /* Fixes the time steps dt[g] (host array) and theta of the theta-method and
- * builds the AMG hierarchy of the batch.  Synchronous. */
+ * builds the AMG hierarchy of the batch.  dt[g] = +INFINITY (with theta = 1)
+ * drops the time derivative: batch_heat_step then solves the steady problem
+ * A u = b1 of every such geometry (a batch of Poisson solves, e.g. a sweep of
+ * a geometry parameter as in Sec. 3.6).  Synchronous. */
 int batch_heat_setup(batch_handle* b, const double* dt, double theta, const amg_opts* opts, cudaStream_t stream);
 /* Tile-shape autotuner for a batch (after batch_heat_setup): retiles every
  * geometry and the batch with each candidate 2D shape, times `reps` V-cycles
  * of the batch hierarchy, keeps the fastest.  Synchronous. */
 int batch_autotune(batch_handle* b, int reps, eb_tune_t* out, cudaStream_t stream);
+/* Quantities of interest of a batch (Sec. 3.6): out_dev[g] = sum over the
+ * nodes of geometry g of w u (w_all, u_all: batch vectors; out_dev: count
+ * doubles on the device), each sum in a fixed order (deterministic).  With w
+ * the interpolation weights of a point, this is u at that point; with h^2 on
+ * the nodes of a region, the integral of u over it.  Synchronous. */
+int batch_weighted_sum(const batch_handle* b, const double* w_all, const double* u_all, double* out_dev,
+                       cudaStream_t stream);
 /* on != 0: later batch_heat_step calls time every level-0 smoother launch of
  * their captured PCG iterations with CUDA events and report the summed
  * duration and the launch count in prof_kernel_ms / prof_launches of every

@@ -152,6 +152,7 @@ _SIGS = {
                                C.POINTER(pcg_stats), _P]),
     "eb_fp64_peak": (C.c_int, [C.c_int, _P, _P]),
     "eb_set_beta": (C.c_int, [_P, _P, _P, _P, _P]),
+    "batch_weighted_sum": (C.c_int, [_P, _P, _P, _P, _P]),
     "minres_solve": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.c_double, C.c_int, C.POINTER(pcg_stats), _P]),
     "wave_theta_step": (C.c_int, [_P, C.c_double, C.c_double, _P, _P, C.c_int, C.c_double, C.c_int,
                                   C.POINTER(pcg_stats), _P]),
@@ -607,6 +608,13 @@ class Batch:
 
     def set_profile(self, on: bool):
         _check(load().batch_set_profile(self._h, int(bool(on))))
+
+    def weighted_sum(self, w_all, u_all, stream=None):
+        """Per-geometry sum of w u (batch_weighted_sum): a device tensor of count doubles."""
+        import torch
+        out = torch.empty(self.count, dtype=torch.float64, device="cuda")
+        _check(load().batch_weighted_sum(self._h, _ptr(w_all), _ptr(u_all), _ptr(out), _stream(stream)))
+        return out
 
     def autotune(self, reps=10, stream=None) -> TuneResult:
         """Times batch V-cycles for every candidate 2D tile shape and keeps the fastest."""

@@ -844,6 +844,53 @@ int batch_rhs(const batch_handle* b, const double* f_all, const double* ug_all, 
   });
 }
 
+// out[g] = sum over geometry g's nodes of w u (one CTA per geometry, a fixed
+// summation order: deterministic)
+__global__ void __launch_bounds__(256) k_b_wsum(const int64_t* node_off, const int32_t* n0, const int32_t* n1,
+                                                int64_t stride, const double* w, const double* u, double* out) {
+  __shared__ double sm[32];
+  const int g = blockIdx.x;
+  const int64_t base = node_off[g];
+  const int64_t nx = n0[g], cnt = nx * n1[g];
+  double acc = 0.0;
+  for (int64_t k = threadIdx.x; k < cnt; k += blockDim.x) {
+    const int64_t node = base + (k / nx) * stride + (k % nx);
+    acc += w[node] * u[node];
+  }
+  const double t = block_sum(acc, sm);
+  if (threadIdx.x == 0) out[g] = t;
+}
+
+int batch_weighted_sum(const batch_handle* b, const double* w_all, const double* u_all, double* out_dev,
+                       cudaStream_t stream) {
+  if (!b || !w_all || !u_all || !out_dev) {
+    set_error("batch_weighted_sum: NULL argument");
+    return EB_ERR_INVALID;
+  }
+  return guarded([&] {
+    const Batch& B = b->b;
+    const int ng = B.ngeo();
+    std::vector<int32_t> nx(ng), ny(ng);
+    for (int g = 0; g < ng; ++g) {
+      nx[g] = B.geo[g]->h.g.n0;
+      ny[g] = B.geo[g]->h.g.n1;
+    }
+    int64_t* off = dalloc<int64_t>(ng, stream, false);
+    int32_t* d0 = dalloc<int32_t>(ng, stream, false);
+    int32_t* d1 = dalloc<int32_t>(ng, stream, false);
+    EB_CUDA(cudaMemcpyAsync(off, B.node_off.data(), sizeof(int64_t) * ng, cudaMemcpyHostToDevice, stream));
+    EB_CUDA(cudaMemcpyAsync(d0, nx.data(), sizeof(int32_t) * ng, cudaMemcpyHostToDevice, stream));
+    EB_CUDA(cudaMemcpyAsync(d1, ny.data(), sizeof(int32_t) * ng, cudaMemcpyHostToDevice, stream));
+    k_b_wsum<<<ng, 256, 0, stream>>>(off, d0, d1, B.stride, w_all, u_all, out_dev);
+    const cudaError_t e = cudaGetLastError();
+    EB_CUDA(cudaStreamSynchronize(stream));
+    dfree(off, stream);
+    dfree(d0, stream);
+    dfree(d1, stream);
+    EB_CUDA(e);
+  });
+}
+
 int batch_heat_setup(batch_handle* b, const double* dt, double theta, const amg_opts* opts, cudaStream_t stream) {
   if (!b || !dt || !(theta > 0.0 && theta <= 1.0)) {
     set_error("batch_heat_setup: invalid argument");
@@ -854,7 +901,8 @@ int batch_heat_setup(batch_handle* b, const double* dt, double theta, const amg_
     const int ng = B.ngeo();
     B.hconst.resize(ng);
     for (int g = 0; g < ng; ++g) {
-      EB_REQUIRE(dt[g] > 0.0 && std::isfinite(dt[g]), EB_ERR_INVALID, "batch_heat_setup: dt must be > 0");
+      EB_REQUIRE(dt[g] > 0.0 && (std::isfinite(dt[g]) || (std::isinf(dt[g]) && theta == 1.0)), EB_ERR_INVALID,
+                 "batch_heat_setup: dt must be > 0 (+infinity only with theta = 1)");
       const double h = B.geo[g]->h.g.h;
       B.hconst[g] = GeoConst{h * h, dt[g], theta};
     }
