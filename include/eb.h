@@ -204,6 +204,12 @@ int eb_autotune(eb_handle* eb, int op, int prec, int reps, eb_tune_t* out, cudaS
  * pcg_solve_nn only; pcg_solve rejects it. */
 typedef enum { EB_PC_AMG = 0, EB_PC_JACOBI = 1, EB_PC_NONE = 2, EB_PC_AMG_NN = 3 } eb_pc_kind;
 
+/* Coarsening of amg_setup: smoothed aggregation (the default) or the classical
+ * Ruge-Stueben method the paper uses (Sec. 3): strength -a_ij >= 0.25
+ * max_k(-a_ik), the independent-set (PMIS) form of its C/F splitting with
+ * measure |S_i^T| and lowbias32 tie-break, direct interpolation. */
+typedef enum { EB_AMG_SA = 0, EB_AMG_RS = 1 } eb_amg_coarsening;
+
 typedef struct {
   int max_levels;        /* default 25 */
   int coarse_max;        /* coarsen until n <= coarse_max (default 1024) */
@@ -212,6 +218,9 @@ typedef struct {
   int vcycle_prec;       /* storage of level vectors/matrices: EB_F64 (default), EB_F32, or EB_BF16
                             (bfloat16 storage, FP32 sums; the level-0 diagonal stays FP32); the
                             reduced precisions make pcg_solve use the flexible (Polak-Ribiere) beta */
+  int coarsening;        /* eb_amg_coarsening, default EB_AMG_SA (strength then ignored for EB_AMG_RS) */
+  int cycle;             /* 1 (default): V-cycle; 2: W-cycle (every coarse-grid correction is two cycles
+                            of the coarser level, the second from the first one's result; Sec. 3) */
 } amg_opts;
 
 typedef struct {

@@ -197,7 +197,123 @@ def gershgorin_rho(A: sp.csr_matrix) -> float:
     return float(np.max(s / d))
 
 
-def setup(A0: sp.csr_matrix) -> Hierarchy:
+# ---------------------------------------------- classical (Ruge-Stueben) AMG
+# The paper's preconditioner is classical AMG (Ruge & Stueben) from a library,
+# with V and W cycles (Sec. 3).  Its sequential first-pass C/F splitting is
+# replaced by the parallel independent-set form of the same coarsening
+# (PMIS, De Sterck, Yang & Heys 2006), with the strength, measure and direct
+# interpolation of the classical method (Stueben 2001, "A review of algebraic
+# multigrid", Sec. 4):
+#   strength    j in S_i iff -a_ij >= theta_rs max_{k != i} (-a_ik), theta_rs = 0.25
+#               (both sides rounded to single precision before comparing)
+#   measure     lambda_i = |S_i^T| (how many points depend strongly on i);
+#               key_i = (lambda_i << 32) | hash32(i): distinct, a fixed order
+#   splitting   points no one depends on are F; then synchronous rounds over
+#               the undecided set U: i in U becomes C if its key exceeds the
+#               keys of every undecided j with j in S_i or i in S_j; then every
+#               undecided point with a C point in its S becomes F
+#   interpolation (direct) for an F point i with strong C neighbours P_i:
+#               w_ij = -alpha_i a_ij / a_ii (a_ij < 0), -beta_i a_ij / a_ii
+#               (a_ij > 0), alpha_i = sum_{k != i} a_ik^- / sum_{j in P_i}
+#               a_ij^-, beta_i likewise for the positive parts; positive
+#               couplings with no positive entry in P_i are added to a_ii.
+#               C points inject (w = 1); an F point without strong C
+#               neighbours gets an empty row.
+RS_THETA = 0.25
+
+
+def strength_rs(A: sp.csr_matrix) -> sp.csr_matrix:
+    """Boolean CSR of the classical strength S (row i: the j in S_i)."""
+    A = A.tocsr()
+    n = A.shape[0]
+    rows = np.repeat(np.arange(n), np.diff(A.indptr))
+    off = rows != A.indices
+    neg = np.where(off, -A.data, -np.inf)
+    mrow = np.full(n, -np.inf)
+    np.maximum.at(mrow, rows, neg)
+    # compared in single precision, as the aggregation weights: coarse-level
+    # entries are sums whose rounding order is an implementation choice
+    lhs = (-A.data).astype(np.float32)
+    rhs = (RS_THETA * mrow[rows]).astype(np.float32)
+    keep = off & (mrow[rows] > 0) & (lhs >= rhs)
+    S = sp.csr_matrix((np.ones(int(keep.sum())), (rows[keep], A.indices[keep])), shape=A.shape)
+    S.sort_indices()
+    return S
+
+
+def pmis(S: sp.csr_matrix) -> np.ndarray:
+    """C/F splitting: 1 = C, 0 = F."""
+    n = S.shape[0]
+    ST = S.T.tocsr()
+    lam = np.diff(ST.indptr).astype(np.uint64)          # |S_i^T|
+    key = (lam << np.uint64(32)) | hash32(np.arange(n)).astype(np.uint64)
+    N = ((S + ST) > 0).tocsr()                          # j in S_i or i in S_j
+    N.setdiag(0)
+    N.eliminate_zeros()
+    state = np.full(n, -1, dtype=np.int64)              # -1 undecided, 1 C, 0 F
+    state[lam == 0] = 0
+    rows = np.repeat(np.arange(n), np.diff(N.indptr))
+    srows = np.repeat(np.arange(n), np.diff(S.indptr))
+    while (state < 0).any():
+        und = state < 0
+        nbmax = np.zeros(n, dtype=np.uint64)
+        m = und[N.indices]
+        np.maximum.at(nbmax, rows[m], key[N.indices[m]])
+        newc = und & (key > nbmax)
+        state[newc] = 1
+        dep = np.zeros(n, dtype=bool)
+        mc = state[S.indices] == 1
+        dep[srows[mc]] = True
+        state[(state < 0) & dep] = 0
+        if not newc.any() and not (dep & und).any():
+            raise RuntimeError("PMIS made no progress")
+    return state.astype(np.int8)
+
+
+def direct_interpolation(A: sp.csr_matrix, S: sp.csr_matrix, cf: np.ndarray) -> sp.csr_matrix:
+    A = A.tocsr()
+    n = A.shape[0]
+    cidx = np.cumsum(cf) - 1
+    nc = int(cf.sum())
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        if cf[i] == 1:
+            rows.append(i); cols.append(cidx[i]); vals.append(1.0)
+            continue
+        a = A.data[A.indptr[i]:A.indptr[i + 1]]
+        c = A.indices[A.indptr[i]:A.indptr[i + 1]]
+        sc = set(S.indices[S.indptr[i]:S.indptr[i + 1]].tolist())
+        aii = 0.0
+        sneg = spos = pneg = ppos = 0.0
+        for j, v in zip(c, a):
+            if j == i:
+                aii = v
+                continue
+            if v < 0:
+                sneg += v
+            else:
+                spos += v
+            if j in sc and cf[j] == 1:
+                if v < 0:
+                    pneg += v
+                else:
+                    ppos += v
+        if ppos == 0.0:
+            aii = aii + spos
+        alpha = sneg / pneg if pneg != 0.0 else 0.0
+        beta = spos / ppos if ppos != 0.0 else 0.0
+        for j, v in zip(c, a):
+            if j != i and j in sc and cf[j] == 1:
+                w = -(alpha if v < 0 else beta) * v / aii
+                rows.append(i); cols.append(cidx[j]); vals.append(w)
+    P = sp.csr_matrix((vals, (rows, cols)), shape=(n, nc))
+    P.sort_indices()
+    return P
+
+
+def setup(A0: sp.csr_matrix, coarsening: str = "sa") -> Hierarchy:
+    """The hierarchy of A0: smoothed aggregation ("sa", the default) or
+    classical Ruge-Stueben coarsening with direct interpolation ("rs")."""
     levels = []
     A = A0.tocsr()
     A.sort_indices()
@@ -208,6 +324,20 @@ def setup(A0: sp.csr_matrix) -> Hierarchy:
         n = A.shape[0]
         if n <= COARSE_MAX or len(levels) >= MAX_LEVELS:
             break
+        if coarsening == "rs":
+            S = strength_rs(A)
+            cf = pmis(S)
+            nc = int(cf.sum())
+            if nc >= n or nc == 0:
+                break
+            P = direct_interpolation(A, S, cf)
+            lev.agg = np.where(cf == 1, np.cumsum(cf) - 1, -1)
+            AP = A @ P
+            Ac_val = P.T.tocsr() @ AP
+            Ac = _on_pattern(_abs(P).T.tocsr() @ _abs(A) @ _abs(P), Ac_val)
+            lev.P, lev.R = P, P.T.tocsr()
+            A = Ac
+            continue
         agg, nc = aggregate(A)
         if nc >= n:
             break
@@ -247,14 +377,19 @@ def chebyshev(lev: Level, b: np.ndarray, x: np.ndarray, degree: int = 2) -> np.n
     return x
 
 
-def vcycle(H: Hierarchy, b: np.ndarray, level: int = 0) -> np.ndarray:
-    """One symmetric V-cycle M^-1 b."""
+def vcycle(H: Hierarchy, b: np.ndarray, level: int = 0, gamma: int = 1, x0: np.ndarray = None) -> np.ndarray:
+    """One symmetric cycle M^-1 b: a V-cycle (gamma = 1) or a W-cycle (gamma =
+    2: the coarse-grid correction of every level is itself two cycles, the
+    second starting from the first one's result); x0: initial guess (zero)."""
     if level == len(H.levels) - 1:
         return sla.cho_solve(H.coarse_chol, b)
     lev = H.levels[level]
-    x = chebyshev(lev, b, np.zeros_like(b))
+    x = chebyshev(lev, b, np.zeros_like(b) if x0 is None else x0)
     r = b - lev.A @ x
-    e = vcycle(H, lev.R @ r, level + 1)
+    bc = lev.R @ r
+    e = vcycle(H, bc, level + 1, gamma)
+    if gamma == 2 and level + 1 < len(H.levels) - 1:
+        e = vcycle(H, bc, level + 1, gamma, x0=e)
     x = x + lev.P @ e
     x = chebyshev(lev, b, x)
     return x

@@ -62,7 +62,10 @@ class eb_info_t(C.Structure):
 
 class amg_opts(C.Structure):
     _fields_ = [("max_levels", C.c_int), ("coarse_max", C.c_int), ("strength", C.c_double),
-                ("cheb_degree", C.c_int), ("vcycle_prec", C.c_int)]
+                ("cheb_degree", C.c_int), ("vcycle_prec", C.c_int), ("coarsening", C.c_int), ("cycle", C.c_int)]
+
+
+EB_AMG_SA, EB_AMG_RS = 0, 1
 
 
 class amg_info_t(C.Structure):
@@ -392,12 +395,13 @@ class AMG:
     """Handle of amg_setup: AMG hierarchy (or Jacobi only) for sigma I + A."""
 
     def __init__(self, eb: EB, shift: float = 0.0, max_levels: int = 25, coarse_max: int = 1024,
-                 strength: float = 0.02, cheb_degree: int = 2, vcycle_prec: int = EB_F64, stream=None):
+                 strength: float = 0.02, cheb_degree: int = 2, vcycle_prec: int = EB_F64, coarsening: int = EB_AMG_SA,
+                 cycle: int = 1, stream=None):
         lib = load()
         self.eb = eb
         self.shift = shift
         self.vcycle_prec = vcycle_prec
-        o = amg_opts(max_levels, coarse_max, strength, cheb_degree, vcycle_prec)
+        o = amg_opts(max_levels, coarse_max, strength, cheb_degree, vcycle_prec, coarsening, cycle)
         self._h = C.c_void_p()
         _check(lib.amg_setup(eb.handle, float(shift), C.byref(o), C.byref(self._h), _stream(stream)))
         inf = amg_info_t()
@@ -596,7 +600,7 @@ class Batch:
     def heat_setup(self, dt, theta=1.0, max_levels=25, coarse_max=1024, strength=0.02, cheb_degree=2,
                    vcycle_prec=EB_F64, stream=None):
         d = (C.c_double * self.count)(*[float(v) for v in dt])
-        o = amg_opts(max_levels, coarse_max, strength, cheb_degree, vcycle_prec)
+        o = amg_opts(max_levels, coarse_max, strength, cheb_degree, vcycle_prec, EB_AMG_SA, 1)
         _check(load().batch_heat_setup(self._h, C.cast(d, C.c_void_p), float(theta), C.byref(o), _stream(stream)))
 
     def heat_step(self, u_all, b1_all, b0_all=None, rtol=1e-10, maxit=500, stream=None, allow_noconv=False):

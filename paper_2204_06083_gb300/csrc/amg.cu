@@ -204,6 +204,161 @@ __global__ void k_agg_pass2(DCsr A, const uint8_t* strong, const int32_t* agg1, 
   agg[i] = a;
 }
 
+// ------------------------------------------------- classical (RS) coarsening
+// Strength, PMIS splitting and direct interpolation of the classical method
+// (the specification the sequential reference implementation states in its
+// header): S_i = {j != i : -a_ij >= 0.25 max_k(-a_ik)}, compared in single
+// precision; lambda_i = |S_i^T|; key (lambda << 32 | lowbias32(i)).
+constexpr double RS_THETA = 0.25;
+
+__global__ void k_rs_strength(DCsr A, uint8_t* strong) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  double m = -INFINITY;
+  for (int32_t e = A.rp[i]; e < A.rp[i + 1]; ++e)
+    if (A.ci[e] != i) m = fmax(m, -A.v[e]);
+  const float thr = __double2float_rn(__dmul_rn(RS_THETA, m));
+  for (int32_t e = A.rp[i]; e < A.rp[i + 1]; ++e)
+    strong[e] = (A.ci[e] != i) && m > 0.0 && __double2float_rn(-A.v[e]) >= thr;
+}
+
+// strongT[e] for entry e = (i, j): whether i is in S_j (the strength flag of
+// the transposed entry (j, i), found by binary search in row j; the pattern of
+// every level is symmetric); lambda_i = sum over row i of strongT
+__global__ void k_rs_transpose(DCsr A, const uint8_t* strong, uint8_t* strongT, int32_t* lambda) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  int32_t lam = 0;
+  for (int32_t e = A.rp[i]; e < A.rp[i + 1]; ++e) {
+    const int32_t j = A.ci[e];
+    uint8_t t = 0;
+    if (j != i) {
+      int32_t lo = A.rp[j], hi = A.rp[j + 1];
+      while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (A.ci[mid] < i) lo = mid + 1;
+        else hi = mid;
+      }
+      if (lo < A.rp[j + 1] && A.ci[lo] == i) t = strong[lo];
+    }
+    strongT[e] = t;
+    lam += t;
+  }
+  lambda[i] = lam;
+}
+
+__device__ __forceinline__ uint64_t rs_key(int32_t lam, int64_t i) {
+  return ((uint64_t)(uint32_t)lam << 32) | (uint64_t)lowbias32((uint32_t)i);
+}
+
+// state: -1 undecided, 1 C, 0 F; points no one depends on start as F
+__global__ void k_rs_init(int64_t n, const int32_t* lambda, int8_t* state) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) state[i] = lambda[i] == 0 ? 0 : -1;
+}
+
+// a PMIS round, part 1: undecided i whose key exceeds those of all undecided
+// strong neighbours (either direction) is marked for C (state unchanged)
+__global__ void k_rs_select(DCsr A, const uint8_t* strong, const uint8_t* strongT, const int32_t* lambda,
+                            const int8_t* state, uint8_t* newc) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  uint8_t c = 0;
+  if (state[i] < 0) {
+    const uint64_t ki = rs_key(lambda[i], i);
+    c = 1;
+    for (int32_t e = A.rp[i]; e < A.rp[i + 1]; ++e) {
+      const int32_t j = A.ci[e];
+      if (j == i || !(strong[e] || strongT[e]) || state[j] >= 0) continue;
+      if (rs_key(lambda[j], j) > ki) {
+        c = 0;
+        break;
+      }
+    }
+  }
+  newc[i] = c;
+}
+
+__global__ void k_rs_apply(int64_t n, const uint8_t* newc, int8_t* state) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && newc[i]) state[i] = 1;
+}
+
+// part 2: undecided points with a C point in their S become F; counts the
+// points still undecided
+__global__ void k_rs_fassign(DCsr A, const uint8_t* strong, int8_t* state, int* undecided) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int und = 0;
+  if (i < A.n && state[i] < 0) {
+    bool dep = false;
+    for (int32_t e = A.rp[i]; e < A.rp[i + 1] && !dep; ++e) dep = strong[e] && state[A.ci[e]] == 1;
+    if (dep) state[i] = 0;
+    else und = 1;
+  }
+  unsigned bal = __ballot_sync(0xffffffffu, und);
+  if ((threadIdx.x & 31) == 0 && bal) atomicAdd(undecided, __popc(bal));
+}
+
+__global__ void k_rs_cflag(int64_t n, const int8_t* state, int32_t* flag) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) flag[i] = state[i] == 1;
+}
+
+// entries of P's row i: 1 for a C point, its strong C neighbours for an F point
+__global__ void k_rs_pcount(DCsr A, const uint8_t* strong, const int8_t* state, int32_t* cnt) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  int32_t c = 0;
+  if (state[i] == 1) {
+    c = 1;
+  } else {
+    for (int32_t e = A.rp[i]; e < A.rp[i + 1]; ++e) c += strong[e] && state[A.ci[e]] == 1;
+  }
+  cnt[i] = c;
+}
+
+// direct interpolation (the sums in the row's column order, as the sequential
+// definition); agg records the coarse index of C points, -1 for F points
+__global__ void k_rs_pfill(DCsr A, const uint8_t* strong, const int8_t* state, const int32_t* cidx, DCsr P,
+                           int32_t* agg) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  int32_t o = P.rp[i];
+  if (state[i] == 1) {
+    P.ci[o] = cidx[i];
+    P.v[o] = 1.0;
+    agg[i] = cidx[i];
+    return;
+  }
+  agg[i] = -1;
+  double aii = 0.0, sneg = 0.0, spos = 0.0, pneg = 0.0, ppos = 0.0;
+  for (int32_t e = A.rp[i]; e < A.rp[i + 1]; ++e) {
+    const int32_t j = A.ci[e];
+    const double v = A.v[e];
+    if (j == i) {
+      aii = v;
+      continue;
+    }
+    if (v < 0.0) sneg = __dadd_rn(sneg, v);
+    else spos = __dadd_rn(spos, v);
+    if (strong[e] && state[j] == 1) {
+      if (v < 0.0) pneg = __dadd_rn(pneg, v);
+      else ppos = __dadd_rn(ppos, v);
+    }
+  }
+  if (ppos == 0.0) aii = __dadd_rn(aii, spos);
+  const double alpha = pneg != 0.0 ? __ddiv_rn(sneg, pneg) : 0.0;
+  const double beta = ppos != 0.0 ? __ddiv_rn(spos, ppos) : 0.0;
+  for (int32_t e = A.rp[i]; e < A.rp[i + 1]; ++e) {
+    const int32_t j = A.ci[e];
+    if (j == i || !(strong[e] && state[j] == 1)) continue;
+    const double v = A.v[e];
+    P.ci[o] = cidx[j];
+    P.v[o] = __ddiv_rn(__dmul_rn(-(v < 0.0 ? alpha : beta), v), aii);
+    ++o;
+  }
+}
+
 __global__ void k_agg_sizes(int64_t n, const int32_t* agg, int32_t* size) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) atomicAdd(&size[agg[i]], 1);
@@ -692,6 +847,74 @@ void amg_build_from(Solver& S, DCsr A0, cudaStream_t s) {
     if (A.n <= S.opts.coarse_max || (int)H->L.size() >= max_levels) {
       dfree(d, s);
       break;
+    }
+    if (S.opts.coarsening == EB_AMG_RS) {
+      // classical coarsening: strength, PMIS splitting, direct interpolation
+      uint8_t* strong = dalloc<uint8_t>(A.nnz, s, false);
+      uint8_t* strongT = dalloc<uint8_t>(A.nnz, s, false);
+      int32_t* lam = dalloc<int32_t>(A.n, s, false);
+      int8_t* state = dalloc<int8_t>(A.n, s, false);
+      uint8_t* newc = dalloc<uint8_t>(A.n, s, false);
+      int* und = dalloc<int>(1, s);
+      const unsigned bn = blocks_for(A.n, 256);
+      k_rs_strength<<<bn, 256, 0, s>>>(A, strong);
+      k_rs_transpose<<<bn, 256, 0, s>>>(A, strong, strongT, lam);
+      k_rs_init<<<bn, 256, 0, s>>>(A.n, lam, state);
+      for (int round = 0;; ++round) {
+        EB_REQUIRE(round < 1000, EB_ERR_INVALID, "amg_setup: PMIS did not terminate");
+        EB_CUDA(cudaMemsetAsync(und, 0, sizeof(int), s));
+        k_rs_select<<<bn, 256, 0, s>>>(A, strong, strongT, lam, state, newc);
+        k_rs_apply<<<bn, 256, 0, s>>>(A.n, newc, state);
+        k_rs_fassign<<<bn, 256, 0, s>>>(A, strong, state, und);
+        int hund = 0;
+        EB_CUDA(cudaMemcpyAsync(&hund, und, sizeof(int), cudaMemcpyDeviceToHost, s));
+        EB_CUDA(cudaStreamSynchronize(s));
+        if (hund == 0) break;
+      }
+      int32_t* cflag = dalloc<int32_t>(A.n + 1, s);
+      int32_t* cidx = dalloc<int32_t>(A.n + 1, s, false);
+      k_rs_cflag<<<bn, 256, 0, s>>>(A.n, state, cflag);
+      exclusive_scan_i32(cflag, cidx, A.n, s);
+      int32_t nc = 0;
+      EB_CUDA(cudaMemcpyAsync(&nc, cidx + A.n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      EB_CUDA(cudaStreamSynchronize(s));
+      auto release = [&] {
+        dfree(strong, s); dfree(strongT, s); dfree(lam, s); dfree(state, s); dfree(newc, s); dfree(und, s);
+        dfree(cflag, s); dfree(cidx, s); dfree(d, s);
+      };
+      if (nc >= A.n || nc == 0) {
+        release();
+        break;
+      }
+      int32_t* pc = dalloc<int32_t>(A.n + 1, s);
+      DCsr P;
+      P.n = A.n;
+      P.m = nc;
+      P.rp = dalloc<int32_t>(A.n + 1, s, false);
+      k_rs_pcount<<<bn, 256, 0, s>>>(A, strong, state, pc);
+      exclusive_scan_i32(pc, P.rp, A.n, s);
+      int32_t pnnz = 0;
+      EB_CUDA(cudaMemcpyAsync(&pnnz, P.rp + A.n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      EB_CUDA(cudaStreamSynchronize(s));
+      P.nnz = pnnz;
+      P.ci = dalloc<int32_t>(pnnz, s, false);
+      P.v = dalloc<double>(pnnz, s, false);
+      L.agg = dalloc<int32_t>(A.n, s, false);
+      k_rs_pfill<<<bn, 256, 0, s>>>(A, strong, state, cidx, P, L.agg);
+      EB_CUDA(cudaGetLastError());
+      dfree(pc, s);
+      release();
+      L.P = P;
+      L.R = transpose(L.P, s);
+      if (lev == 0) {
+        L.R0node = dalloc<int32_t>(L.R.nnz, s, false);
+        k_map_cols<<<blocks_for(L.R.nnz, 256), 256, 0, s>>>(L.R.nnz, L.R.ci, eb.cp_node, L.R0node);
+      }
+      DCsr AP = spgemm(A, L.P, s);
+      DCsr Ac = spgemm(L.R, AP, s);
+      csr_free(AP, s);
+      A = Ac;
+      continue;
     }
     // strength + MIS-2
     uint8_t* strong = dalloc<uint8_t>(A.nnz, s, false);

@@ -566,10 +566,13 @@ static CoarseFirst<V> coarse_first(Solver& S, size_t l) {
   return f;
 }
 
-// V-cycle from compact level l down; the restriction into l already did its
-// first smoothing step (coarse_first)
+// Cycle from compact level l down; the restriction into l already did its
+// first smoothing step (coarse_first) unless warm: then the cycle starts from
+// the level's current x (the second coarse-grid cycle of a W-cycle) and runs
+// all its pre-smoothing steps.  With opts.cycle = 2 every coarse-grid
+// correction is two cycles of the coarser level (W-cycle).
 template <class V>
-static void vcycle_compact(Solver& S, size_t l, cudaStream_t s) {
+static void vcycle_compact(Solver& S, size_t l, cudaStream_t s, bool warm = false) {
   using LV = LevelView<V>;
   Hierarchy& H = *S.H;
   Level& L = H.L[l];
@@ -581,13 +584,13 @@ static void vcycle_compact(Solver& S, size_t l, cudaStream_t s) {
     return;
   }
   const ChebCoef cc = cheb_coef(L.rho, S.opts.cheb_degree);
-  S.nlaunch += 2 + 2 * cc.deg;  // deg-1 steps, residual, restriction, prolongation, deg steps
+  S.nlaunch += 2 + 2 * cc.deg + (warm ? 1 : 0);  // pre steps, residual, restriction, prolongation, deg steps
   const CsrV<V> A = LV::A(L);
   const int e = S.csr_epl;
   const int gA = group_width(L.A.nnz, L.A.n, e), gP = group_width(L.P.nnz, L.P.n, e),
             gR = group_width(L.R.nnz, L.R.n, e);
   const bool mark = l == 1;  // level-1 smoother launches are timed with PROF_LEVEL1
-  for (int k = 1; k < cc.deg; ++k) {
+  for (int k = warm ? 0 : 1; k < cc.deg; ++k) {
     if (mark) S.prof_mark(s, true, PROF_LEVEL1);
     EB_GROUP_LAUNCH(gA, k_c_cheb_step, V, n, s, A, LV::dinv(L), v.b, v.x, v.x2, v.d, cc.c1[k], cc.c2[k]);
     if (mark) S.prof_mark(s, false, PROF_LEVEL1);
@@ -598,6 +601,7 @@ static void vcycle_compact(Solver& S, size_t l, cudaStream_t s) {
   VecSet<V>& cv = LV::vec(C);
   EB_GROUP_LAUNCH(gR, k_c_spmv, V, C.A.n, s, LV::R(L), v.r, cv.b, coarse_first<V>(S, l + 1));
   vcycle_compact<V>(S, l + 1, s);
+  if (S.opts.cycle == 2 && l + 2 < H.L.size()) vcycle_compact<V>(S, l + 1, s, true);
   EB_GROUP_LAUNCH(gP, k_c_prolong_add, V, n, s, LV::P(L), cv.x, v.x);
   for (int k = 0; k < cc.deg; ++k) {
     if (mark) S.prof_mark(s, true, PROF_LEVEL1);
@@ -662,6 +666,7 @@ static int vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, co
   // matrix-free restriction slower); prolongation matrix free
   EB_GROUP_LAUNCH(gR, k_restrict0, V, C.A.n, s, C.A.n, R0.rp, L0.R0node, R0.v, g.r, cv.b, coarse_first<V>(S, 1));
   vcycle_compact<V>(S, 1, s);
+  if (S.opts.cycle == 2 && H.L.size() > 2) vcycle_compact<V>(S, 1, s, true);  // W-cycle
   if (M.on)
     k_prolong_mf<DIM, V, SC><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, (A)M.omega, M.agg_node, sc, cv.x, x);
   else

@@ -204,7 +204,7 @@ int amg_setup(const eb_handle* eb, double shift, const amg_opts* opts, amg_handl
   S.eb = const_cast<EBHandle*>(&eb->h);
   S.home = stream;
   S.shift = shift;
-  amg_opts o{25, 1024, 0.02, 2, EB_F64};
+  amg_opts o{25, 1024, 0.02, 2, EB_F64, EB_AMG_SA, 1};
   if (opts) o = *opts;
   S.opts = o;
   int st = guarded([&] {
@@ -213,6 +213,9 @@ int amg_setup(const eb_handle* eb, double shift, const amg_opts* opts, amg_handl
     EB_REQUIRE(o.cheb_degree >= 1 && o.cheb_degree <= 8, EB_ERR_INVALID, "amg_setup: cheb_degree in [1, 8]");
     EB_REQUIRE(o.vcycle_prec == EB_F64 || o.vcycle_prec == EB_F32 || o.vcycle_prec == EB_BF16, EB_ERR_INVALID,
                "amg_setup: vcycle_prec must be EB_F64, EB_F32 or EB_BF16");
+    EB_REQUIRE(o.coarsening == EB_AMG_SA || o.coarsening == EB_AMG_RS, EB_ERR_INVALID,
+               "amg_setup: coarsening must be EB_AMG_SA or EB_AMG_RS");
+    EB_REQUIRE(o.cycle == 1 || o.cycle == 2, EB_ERR_INVALID, "amg_setup: cycle must be 1 (V) or 2 (W)");
     auto t0 = std::chrono::steady_clock::now();
     S.alloc_work(stream);
     if (o.max_levels > 0) amg_build(S, stream);

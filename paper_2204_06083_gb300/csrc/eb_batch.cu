@@ -919,11 +919,13 @@ int batch_heat_setup(batch_handle* b, const double* dt, double theta, const amg_
     if (B.gexec) cudaGraphExecDestroy(B.gexec);
     B.gexec = nullptr;
     b_loop_release(B);
-    amg_opts o{25, 1024, 0.02, 2, EB_F64};
+    amg_opts o{25, 1024, 0.02, 2, EB_F64, EB_AMG_SA, 1};
     if (opts) o = *opts;
     EB_REQUIRE(o.max_levels >= 1 && o.max_levels <= 32, EB_ERR_INVALID, "batch_heat_setup: max_levels in [1, 32]");
     EB_REQUIRE(o.vcycle_prec == EB_F64 || o.vcycle_prec == EB_F32 || o.vcycle_prec == EB_BF16, EB_ERR_INVALID,
                "batch_heat_setup: vcycle_prec must be EB_F64, EB_F32 or EB_BF16");
+    EB_REQUIRE((o.coarsening == EB_AMG_SA || o.coarsening == EB_AMG_RS) && (o.cycle == 1 || o.cycle == 2),
+               EB_ERR_INVALID, "batch_heat_setup: coarsening EB_AMG_SA / EB_AMG_RS, cycle 1 or 2");
     B.S = new Solver();
     Solver& S = *B.S;
     S.eb = &B.view;
