@@ -27,6 +27,7 @@ Readings of the paper taken here:
 """
 from __future__ import annotations
 
+import math
 from dataclasses import dataclass
 
 import numpy as np
@@ -59,6 +60,23 @@ class EBSystem:
     A: sp.csr_matrix         # [N_C, N_C], A = -L
     beta: tuple = None       # None (beta = 1) or per axis a full-grid array: beta at node + h/2 e_axis
     cut_beta: np.ndarray = None  # float64 [n_cut], beta at the half point between the CP and its BP
+    cut_w1: np.ndarray = None    # float64 [n_cut], right-hand-side weight of the first boundary value
+    rbf_cut: np.ndarray = None   # int64 [n_rbf], the cuts closed by RBF interpolation (ascending)
+    rbf_xg2: np.ndarray = None   # float64 [n_rbf, 2], their second boundary point G2
+    rbf_w2: np.ndarray = None    # float64 [n_rbf], its weight
+    rbf_rot: np.ndarray = None   # bool [n_rbf], G2 from the rotated line (Algorithm 2's second branch)
+
+    @property
+    def num_samples(self) -> int:
+        """Boundary values the right-hand side needs: one per cut, then the
+        second point of every RBF cut."""
+        return int(self.cut_cp.size + (0 if self.rbf_cut is None else self.rbf_cut.size))
+
+    def sample_points(self) -> np.ndarray:
+        """The boundary points of the right-hand side's values, in order."""
+        if self.rbf_cut is None or self.rbf_cut.size == 0:
+            return self.cut_xg
+        return np.concatenate([self.cut_xg, self.rbf_xg2], axis=0)
 
     @property
     def num_cp(self) -> int:
@@ -110,12 +128,59 @@ def half_point_beta(eb_or_beta, grid, cp_nodes, ax, sgn):
     return b[cp_nodes] if sgn > 0 else b[cp_nodes - st]
 
 
-def build(grid: ei.Grid, ls: ei.LevelSet, beta=None) -> EBSystem:
+RBF_EPS = 0.025   # Algorithm 2's tolerance (Sec. 2.3: distinct points for eps = 0.025)
+
+
+def rbf_weights(x_ij, x_g1, x_g2, x_bp, h):
+    """Weights (w_ij, w_1, w_2) of u_BP = w_ij u_ij + w_1 u_G1 + w_2 u_G2 from
+    the cubic polyharmonic RBF interpolant with linear augmentation of eqs.
+    (7)-(9): B c = (phi_BP; pi_BP), B = [[Phi, Pi^T], [Pi, 0]], phi(r) = r^3
+    (Sec. 3).  Coordinates are taken relative to x_BP and scaled by 1/h (the
+    interpolant is invariant under translation and scaling)."""
+    pts = np.array([x_ij, x_g1, x_g2], dtype=np.float64)
+    loc = (pts - np.asarray(x_bp, dtype=np.float64)[None, :]) / h
+    B = np.zeros((6, 6))
+    for a in range(3):
+        for b in range(3):
+            B[a, b] = np.linalg.norm(loc[a] - loc[b]) ** 3
+    B[3, :3] = 1.0
+    B[4, :3] = loc[:, 0]
+    B[5, :3] = loc[:, 1]
+    B[:3, 3:] = B[3:, :3].T
+    rhs = np.zeros(6)
+    rhs[:3] = np.linalg.norm(loc, axis=1) ** 3
+    rhs[3] = 1.0                      # pi_BP = (1, 0, 0) at the local origin
+    c = np.linalg.solve(B, rhs)
+    return c[0], c[1], c[2]
+
+
+def rbf_points(ls, x_ij, x_bp, h, eps=RBF_EPS):
+    """Algorithm 2: x_G1 nearest to x_BP on Gamma, x_G2 nearest to x_ij if the
+    two are more than eps h apart, else the crossing of Gamma with the line
+    x_BP -> x_G1 turned counterclockwise by pi/4 about x_BP.  Returns
+    (x_G1, x_G2, rotated)."""
+    g1 = geo.closest_point(ls, x_bp)[:2]
+    g2 = geo.closest_point(ls, x_ij)[:2]
+    if math.hypot(g1[0] - g2[0], g1[1] - g2[1]) > eps * h:
+        return g1, g2, False
+    v = (g1[0] - x_bp[0], g1[1] - x_bp[1])
+    nv = math.hypot(*v)
+    c, s_ = math.cos(math.pi / 4.0), math.sin(math.pi / 4.0)
+    d = ((c * v[0] - s_ * v[1]) / nv, (s_ * v[0] + c * v[1]) / nv)
+    t = geo.ray_boundary(ls, x_bp, d, h)
+    return g1, (x_bp[0] + t * d[0], x_bp[1] + t * d[1]), True
+
+
+def build(grid: ei.Grid, ls: ei.LevelSet, beta=None, closure: str = "line", rbf_eps: float = RBF_EPS) -> EBSystem:
     """Algorithm 1, steps 1-3.  beta: None for beta = 1, else one full-grid
     array per axis holding beta at the half points node + h/2 e_axis (eq. 3).
     With beta the stencil of eq. 3 weights each neighbour difference by the
     beta of its half point; the closure of Sec. 2.1 then leaves beta_s c_s on
-    the diagonal and beta_s c_s u_Gamma / h^2 on the right-hand side."""
+    the diagonal and beta_s c_s u_Gamma / h^2 on the right-hand side.
+    closure: "line" (line-by-line everywhere, the far crossing beyond the BP
+    when the node past it is inside), "mixed" (Sec. 2.3: line-by-line where
+    the node past the BP is outside, the RBF interpolation of Sec. 2.2
+    otherwise) or "rbf" (RBF everywhere); the RBF forms are 2D."""
     dim, h = grid.dim, grid.h
     psi = geo.psi_nodes(grid, ls)
     cls = classify(grid, psi)
@@ -135,7 +200,7 @@ def build(grid: ei.Grid, ls: ei.LevelSet, beta=None) -> EBSystem:
         idx[ax] = rem % grid.n[ax]
         rem = rem // grid.n[ax]
 
-    cut_cp, cut_dir, cut_delta, cut_xg = [], [], [], []
+    cut_cp, cut_dir, cut_delta, cut_xg, cut_far = [], [], [], [], []
     diag = np.zeros(cp_nodes.size, dtype=np.float64)
     cs_per_dir = []
     for ax in range(dim):
@@ -176,6 +241,7 @@ def build(grid: ei.Grid, ls: ei.LevelSet, beta=None) -> EBSystem:
                 cut_dir.append(np.full(k.size, 2 * ax + sgn_bit))
                 cut_delta.append(delta)
                 cut_xg.append(xg)
+                cut_far.append(m > 1)
             if beta is not None:
                 cs = half_point_beta(beta, grid, cp_nodes, ax, sgn) * cs
             cs_per_dir.append(cs)
@@ -188,15 +254,62 @@ def build(grid: ei.Grid, ls: ei.LevelSet, beta=None) -> EBSystem:
         cut_dir_a = np.concatenate(cut_dir)
         cut_delta_a = np.concatenate(cut_delta)
         cut_xg_a = np.concatenate(cut_xg, axis=0)
+        cut_far_a = np.concatenate(cut_far)
         order = np.lexsort((cut_dir_a, cut_cp_a))
         cut_cp_a, cut_dir_a = cut_cp_a[order], cut_dir_a[order]
         cut_delta_a, cut_xg_a = cut_delta_a[order], cut_xg_a[order]
+        cut_far_a = cut_far_a[order]
     else:
         cut_cp_a = np.zeros(0, np.int64)
         cut_dir_a = np.zeros(0, np.int64)
         cut_delta_a = np.zeros(0)
         cut_xg_a = np.zeros((0, dim))
+        cut_far_a = np.zeros(0, dtype=bool)
     cut_c_a = h / (h + cut_delta_a)
+    # the RBF closure (Sec. 2.2, Algorithm 2) of the selected cuts: u_BP = w_ij
+    # u_ij + w_1 u_G1 + w_2 u_G2 leaves 1 - w_ij on the diagonal (in h^2 units)
+    # and w_1 u_G1 + w_2 u_G2 on the right-hand side; the cut's crossing
+    # becomes G1, its distance |x_BP - G1|, and G2 a second boundary sample
+    cut_w1 = cut_c_a.copy()
+    rbf_cut = np.zeros(0, dtype=np.int64)
+    rbf_xg2 = np.zeros((0, dim))
+    rbf_w2 = np.zeros(0)
+    rbf_rot = np.zeros(0, dtype=bool)
+    if closure not in ("line", "mixed", "rbf"):
+        raise ValueError("closure must be line, mixed or rbf")
+    if closure != "line":
+        if dim != 2:
+            raise ValueError("the RBF closure is two-dimensional (Sec. 2.2)")
+        sel = np.flatnonzero(cut_far_a if closure == "mixed" else np.ones(cut_cp_a.size, dtype=bool))
+        rbf_cut = sel
+        rbf_xg2 = np.zeros((sel.size, 2))
+        rbf_w2 = np.zeros(sel.size)
+        rbf_rot = np.zeros(sel.size, dtype=bool)
+        for r, j in enumerate(sel):
+            node = cp_nodes[cut_cp_a[j]]
+            ax, sg = cut_dir_a[j] // 2, (1 if cut_dir_a[j] % 2 else -1)
+            ij = [int(node % grid.n[0]), int(node // grid.n[0])]
+            x_ij = (grid.lo[0] + float(ij[0]) * h, grid.lo[1] + float(ij[1]) * h)
+            ij[ax] += sg
+            x_bp = (grid.lo[0] + float(ij[0]) * h, grid.lo[1] + float(ij[1]) * h)
+            g1, g2, rot = rbf_points(ls, x_ij, x_bp, h, rbf_eps)
+            w_ij, w1, w2 = rbf_weights(x_ij, g1, g2, x_bp, h)
+            cut_c_a[j] = 1.0 - w_ij
+            cut_w1[j] = w1
+            cut_xg_a[j] = g1
+            cut_delta_a[j] = math.hypot(g1[0] - x_bp[0], g1[1] - x_bp[1])
+            rbf_xg2[r] = g2
+            rbf_w2[r] = w2
+            rbf_rot[r] = rot
+        # D_k = sum_s beta_s c_s again, with the RBF diagonal contributions
+        cdir = np.ones((cp_nodes.size, 2 * dim))
+        cdir[cut_cp_a, cut_dir_a] = cut_c_a
+        diag = np.zeros(cp_nodes.size)
+        for sdir in range(2 * dim):
+            w = cdir[:, sdir]
+            if beta is not None:
+                w = half_point_beta(beta, grid, cp_nodes, sdir // 2, 1 if sdir % 2 else -1) * w
+            diag = diag + w
     cut_beta = np.ones(cut_cp_a.size)
     if beta is not None:
         beta = tuple(np.ascontiguousarray(b, dtype=np.float64).reshape(grid.shape()) for b in beta)
@@ -207,7 +320,8 @@ def build(grid: ei.Grid, ls: ei.LevelSet, beta=None) -> EBSystem:
 
     A = assemble(grid, cp_nodes, cp_of_node, flat_cls, diag, beta)
     return EBSystem(grid, ls, psi, cls, cp_nodes, cp_of_node, cut_cp_a, cut_dir_a,
-                    cut_delta_a, cut_xg_a, cut_c_a, diag, A, beta, cut_beta)
+                    cut_delta_a, cut_xg_a, cut_c_a, diag, A, beta, cut_beta, cut_w1, rbf_cut, rbf_xg2,
+                    rbf_w2, rbf_rot)
 
 
 def assemble(grid, cp_nodes, cp_of_node, flat_cls, diag, beta=None) -> sp.csr_matrix:
@@ -261,8 +375,15 @@ def rhs(eb: EBSystem, f_nodes: np.ndarray, ugamma: np.ndarray) -> np.ndarray:
     h2 = eb.grid.h * eb.grid.h
     b = -eb.from_grid(f_nodes)
     add = np.zeros(eb.num_cp)
-    w = eb.cut_c if eb.beta is None else eb.cut_beta * eb.cut_c
-    np.add.at(add, eb.cut_cp, w * ugamma / h2)
+    w1 = eb.cut_c if eb.cut_w1 is None else eb.cut_w1
+    w = w1 if eb.beta is None else eb.cut_beta * w1
+    ugamma = np.asarray(ugamma, dtype=np.float64)
+    nc = eb.cut_cp.size
+    np.add.at(add, eb.cut_cp, w * ugamma[:nc] / h2)
+    if eb.rbf_cut is not None and eb.rbf_cut.size:
+        j = eb.rbf_cut
+        w2 = eb.rbf_w2 if eb.beta is None else eb.cut_beta[j] * eb.rbf_w2
+        np.add.at(add, eb.cut_cp[j], w2 * ugamma[nc:nc + j.size] / h2)
     return b + add
 
 

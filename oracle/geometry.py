@@ -175,3 +175,100 @@ def star_line_root(ls: ei.LevelSet, p, axis, sign, ta, tb, h, maxit: int = 100):
         told = np.where(act, tn, told)
         done = done | hit0 | conv
     return t
+
+
+# ------------------------------------------------ the boundary as a curve (2D)
+# Sec. 2.2 (RBF closure) needs points ON Gamma nearest to given points and the
+# intersection of a rotated line with Gamma.  Both 2D descriptor families are
+# parameterised curves: the quadric y = Q^T (x - c) has y(t) = (s0 cos t,
+# s1 sin t); the star has x(phi) = c + r(phi) (cos phi, sin phi).
+
+def curve(ls: ei.LevelSet, t):
+    """Gamma(t), Gamma'(t), Gamma''(t) as (x, y) pairs of arrays."""
+    t = np.asarray(t, dtype=np.float64)
+    if ls.kind == ei.LS_QUADRIC:
+        Q, c, s = quadric_parts(ls, 2)
+        # y = Q2^T (x - c) for the leading 2 x 2 block Q2, so x = c + M y with M = (Q2^T)^-1
+        M = np.linalg.inv(Q[:2, :2].T)
+        y = (s[0] * np.cos(t), s[1] * np.sin(t))
+        y1 = (-s[0] * np.sin(t), s[1] * np.cos(t))
+        y2 = (-y[0], -y[1])
+        f = lambda v, off: (off[0] + M[0][0] * v[0] + M[0][1] * v[1], off[1] + M[1][0] * v[0] + M[1][1] * v[1])
+        return f(y, c[:2]), f(y1, (0.0, 0.0)), f(y2, (0.0, 0.0))
+    if ls.kind == ei.LS_STAR2D:
+        r = np.full_like(t, ls.r0)
+        r1 = np.zeros_like(t)
+        r2 = np.zeros_like(t)
+        for k, a, p in zip(ls.ks, ls.amps, ls.phases):
+            r = r + a * np.sin(k * t + p)
+            r1 = r1 + a * k * np.cos(k * t + p)
+            r2 = r2 - a * k * k * np.sin(k * t + p)
+        ct, st = np.cos(t), np.sin(t)
+        g = (ls.center[0] + r * ct, ls.center[1] + r * st)
+        g1 = (r1 * ct - r * st, r1 * st + r * ct)
+        g2 = (r2 * ct - 2.0 * r1 * st - r * ct, r2 * st + 2.0 * r1 * ct - r * st)
+        return g, g1, g2
+    raise ValueError("the RBF closure needs a quadric or star boundary (2D)")
+
+
+def closest_point(ls: ei.LevelSet, p, n_guess: int = 256, maxit: int = 60):
+    """The point of Gamma nearest to p (Sec. 3.3's procedure for parametric
+    curves): the nearest of n_guess uniform parameter samples, then Newton's
+    method on (Gamma(t) - p) . Gamma'(t) = 0 with steps limited to one sample
+    spacing.  Returns (x, y, t)."""
+    ts = 2.0 * np.pi * np.arange(n_guess) / n_guess
+    (gx, gy), _, _ = curve(ls, ts)
+    t = float(ts[int(np.argmin((gx - p[0]) ** 2 + (gy - p[1]) ** 2))])
+    dmax = 2.0 * np.pi / n_guess
+    for _ in range(maxit):
+        (x, y), (x1, y1), (x2, y2) = curve(ls, t)
+        g = (x - p[0]) * x1 + (y - p[1]) * y1
+        dg = x1 * x1 + y1 * y1 + (x - p[0]) * x2 + (y - p[1]) * y2
+        step = -g / dg if dg > 0 else -np.sign(g) * dmax
+        step = float(np.clip(step, -dmax, dmax))
+        t = t + step
+        if abs(step) <= 1e-15:
+            break
+    (x, y), _, _ = curve(ls, t)
+    return float(x), float(y), t
+
+
+def ray_boundary(ls: ei.LevelSet, p, d, h):
+    """First crossing of Gamma on the ray p + s d (s > 0, |d| = 1, p inside):
+    march in steps of h/4 to the first point with psi >= 0, then the Illinois
+    iteration of star_line_root's kind on that bracket."""
+    def psi_at(s):
+        return float(psi_points(ls, 2, [np.array([p[0] + s * d[0]]), np.array([p[1] + s * d[1]])])[0])
+    step = 0.25 * h
+    s0, f0 = 0.0, psi_at(0.0)
+    s1 = step
+    f1 = psi_at(s1)
+    n = 0
+    while f1 < 0.0:
+        s0, f0 = s1, f1
+        s1 = s1 + step
+        f1 = psi_at(s1)
+        n += 1
+        if n > 10 ** 6:
+            raise RuntimeError("ray does not leave the domain")
+    if f1 == 0.0:
+        return s1
+    a, fa, b, fb = s0, f0, s1, f1
+    side, told, t = 0, a, b
+    for _ in range(100):
+        t = (a * fb - b * fa) / (fb - fa)
+        ft = psi_at(t)
+        if ft == 0.0:
+            break
+        if ft < 0.0:
+            if side == -1:
+                fb = 0.5 * fb
+            a, fa, side = t, ft, -1
+        else:
+            if side == 1:
+                fa = 0.5 * fa
+            b, fb, side = t, ft, 1
+        if abs(t - told) <= 1e-15 * h:
+            break
+        told = t
+    return t
