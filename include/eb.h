@@ -114,8 +114,33 @@ typedef struct {
   double min_dominance_margin;  /* smallest D_k - sum_j |h^2 a_kj| over the rows with a cut, i.e. the
                                    smallest sum of c_s over the BP directions of a CP (h^2 units): > 0
                                    means strict diagonal dominance of every cut row (Sec. 2.1); interior
-                                   rows have margin 0 */
+                                   rows have margin 0 (RBF cuts may make it negative, Sec. 2.4) */
+  int64_t num_rbf;       /* cuts closed by RBF interpolation (mixed / RBF-based closures) */
+  int64_t num_rbf_rotated;  /* of those, with G2 from Algorithm 2's rotated line */
 } eb_info_t;
+
+/* Closure of the boundary points (Sec. 2.3).
+ *  EB_CLOSURE_LINE:  line-by-line interpolation everywhere (Sec. 2.1); when the
+ *                    node past the BP is inside, the crossing is the first one
+ *                    walking outward along the grid line (delta may exceed h).
+ *  EB_CLOSURE_MIXED: line-by-line where the node past the BP is outside, the
+ *                    RBF interpolation of Sec. 2.2 elsewhere (the paper's
+ *                    "mixed" method, Algorithm 1 step 3).
+ *  EB_CLOSURE_RBF:   RBF interpolation at every cut ("RBF-based").
+ * RBF cuts: u_BP = w_ij u_ij + w_1 u_G1 + w_2 u_G2 from the cubic polyharmonic
+ * RBF with linear augmentation (eqs. 7-9) through the CP and two boundary
+ * points chosen by Algorithm 2 (G1 nearest to x_BP; G2 nearest to the CP if
+ * more than rbf_eps h from G1, else the crossing of the line x_BP -> G1 turned
+ * counterclockwise by pi/4).  The cut's diagonal term becomes 1 - w_ij, its
+ * crossing point G1; its second value u_G2 is an extra boundary sample.  The
+ * RBF forms need a 2D quadric or star level set (EB_ERR_NOT_IMPLEMENTED
+ * otherwise); their nearest points are found on the descriptor's curve by 256
+ * parameter samples and Newton's method (Sec. 3.3). */
+typedef enum { EB_CLOSURE_LINE = 0, EB_CLOSURE_MIXED = 1, EB_CLOSURE_RBF = 2 } eb_closure;
+typedef struct {
+  int closure;           /* eb_closure, default EB_CLOSURE_LINE */
+  double rbf_eps;        /* Algorithm 2's epsilon, default 0.025 */
+} eb_build_opts;
 
 /* Algorithm 1 steps 1-3 on the device: classifies every node (mask, BP, CP),
  * numbers the CPs lexicographically, finds for every CP and axis direction
@@ -127,6 +152,16 @@ typedef struct {
  * the outermost ring of the grid or when there is no CP; EB_ERR_INVALID for
  * an EB_LS_SAMPLED level set without psi. */
 int eb_build(const eb_grid* grid, const eb_levelset* ls, eb_handle** out, cudaStream_t stream);
+/* eb_build with a closure (opts may be NULL: EB_CLOSURE_LINE).  With RBF cuts
+ * the right-hand side takes num_cut + num_rbf boundary values (eb_rhs). */
+int eb_build_ex(const eb_grid* grid, const eb_levelset* ls, const eb_build_opts* opts, eb_handle** out,
+                cudaStream_t stream);
+/* The RBF cuts (device buffers of num_rbf entries, any may be NULL): the cut
+ * index of each (ascending), its second boundary point G2 (num_rbf x 2), its
+ * weights (w_ij, w_1, w_2) (num_rbf x 3) and whether G2 came from the rotated
+ * line (1) or is the point nearest to the CP (0). */
+int eb_rbf_cuts(const eb_handle* eb, int32_t* cut_index_dev, double* xg2_dev, double* weights_dev,
+                int32_t* rotated_dev, cudaStream_t stream);
 void eb_destroy(eb_handle* eb);
 int eb_info(const eb_handle* eb, eb_info_t* out);
 
@@ -162,8 +197,10 @@ int eb_cuts(const eb_handle* eb, int32_t* cut_cp_dev, int32_t* cut_dir_dev, doub
 
 /* Right-hand side of A u = b for div(grad u) = f with u = u_Gamma on Gamma:
  * b_k = -f_k + sum_s c_s u_Gamma,s / h^2 (the g_Gamma u_Gamma term of
- * Sec. 2.1).  f: full grid; ugamma: one value per cut (eb_cuts order);
- * b: full grid output. */
+ * Sec. 2.1).  f: full grid; ugamma: one value per cut (eb_cuts order, at the
+ * cut's crossing point), followed, with RBF cuts, by one value per RBF cut at
+ * its G2 (eb_rbf_cuts order): num_cut + num_rbf values; an RBF cut adds
+ * (w_1 u_G1 + w_2 u_G2) / h^2.  b: full grid output. */
 int eb_rhs(const eb_handle* eb, const double* f_dev, const double* ugamma_dev, double* b_dev,
            cudaStream_t stream);
 

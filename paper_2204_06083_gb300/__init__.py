@@ -57,7 +57,14 @@ class eb_info_t(C.Structure):
     _fields_ = [("num_nodes", C.c_int64), ("num_cp", C.c_int64), ("num_bp", C.c_int64), ("num_cut", C.c_int64),
                 ("num_far", C.c_int64), ("num_tiles", C.c_int64), ("tile", C.c_int * 3),
                 ("max_delta_over_h", C.c_double), ("min_abs_psi", C.c_double),
-                ("min_dominance_margin", C.c_double)]
+                ("min_dominance_margin", C.c_double), ("num_rbf", C.c_int64), ("num_rbf_rotated", C.c_int64)]
+
+
+class eb_build_opts(C.Structure):
+    _fields_ = [("closure", C.c_int), ("rbf_eps", C.c_double)]
+
+
+EB_CLOSURE_LINE, EB_CLOSURE_MIXED, EB_CLOSURE_RBF = 0, 1, 2
 
 
 class amg_opts(C.Structure):
@@ -106,6 +113,9 @@ _P = C.c_void_p
 _SIGS = {
     "eb_build": (C.c_int, [C.POINTER(eb_grid), C.POINTER(eb_levelset), C.POINTER(_P), _P]),
     "eb_destroy": (None, [_P]),
+    "eb_build_ex": (C.c_int, [C.POINTER(eb_grid), C.POINTER(eb_levelset), C.POINTER(eb_build_opts), C.POINTER(_P),
+                              _P]),
+    "eb_rbf_cuts": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "eb_info": (C.c_int, [_P, C.POINTER(eb_info_t)]),
     "eb_classes": (C.c_int, [_P, _P, _P]),
     "eb_cp_data": (C.c_int, [_P, _P, _P, _P]),
@@ -276,12 +286,14 @@ class Info:
     max_delta_over_h: float
     min_abs_psi: float
     min_dominance_margin: float
+    num_rbf: int = 0
+    num_rbf_rotated: int = 0
 
 
 class EB:
     """Handle of eb_build: the classified grid, cuts and diagonal."""
 
-    def __init__(self, grid, levelset, stream=None):
+    def __init__(self, grid, levelset, stream=None, closure=EB_CLOSURE_LINE, rbf_eps=0.025):
         lib = load()
         self._h = C.c_void_p()
         self.grid = grid
@@ -289,11 +301,13 @@ class EB:
         g = make_grid(grid)
         psi_dev = sampled_psi_on_device(levelset) if int(levelset.kind) == EB_LS_SAMPLED else None
         ls = make_levelset(levelset, psi_dev)
-        _check(lib.eb_build(C.byref(g), C.byref(ls), C.byref(self._h), _stream(stream)))
+        o = eb_build_opts(int(closure), float(rbf_eps))
+        _check(lib.eb_build_ex(C.byref(g), C.byref(ls), C.byref(o), C.byref(self._h), _stream(stream)))
         inf = eb_info_t()
         _check(lib.eb_info(self._h, C.byref(inf)))
         self.info = Info(inf.num_nodes, inf.num_cp, inf.num_bp, inf.num_cut, inf.num_far, inf.num_tiles,
-                         tuple(inf.tile), inf.max_delta_over_h, inf.min_abs_psi, inf.min_dominance_margin)
+                         tuple(inf.tile), inf.max_delta_over_h, inf.min_abs_psi, inf.min_dominance_margin,
+                         inf.num_rbf, inf.num_rbf_rotated)
 
     def close(self):
         if self._h:
@@ -338,6 +352,26 @@ class EB:
         _check(load().eb_cuts(self._h, _ptr(cp), _ptr(d), _ptr(delta), _ptr(xg), _stream(stream)))
         return cp, d, delta, xg
 
+    def rbf_cuts(self, stream=None):
+        """(cut index, G2 [n, 2], weights (w_ij, w_1, w_2) [n, 3], rotated) of the RBF cuts."""
+        import torch
+        n = self.info.num_rbf
+        idx = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+        xg2 = torch.empty((max(n, 1), 2), dtype=torch.float64, device="cuda")
+        w = torch.empty((max(n, 1), 3), dtype=torch.float64, device="cuda")
+        rot = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+        _check(load().eb_rbf_cuts(self._h, _ptr(idx), _ptr(xg2), _ptr(w), _ptr(rot), _stream(stream)))
+        return idx[:n], xg2[:n], w[:n], rot[:n]
+
+    def sample_points(self, stream=None):
+        """The boundary points whose values eb_rhs takes, in its order: each
+        cut's crossing, then the second point of every RBF cut."""
+        import torch
+        _, _, _, xg = self.cuts(stream)
+        if self.info.num_rbf == 0:
+            return xg
+        return torch.cat([xg, self.rbf_cuts(stream)[1]], dim=0)
+
     def rhs(self, f, ugamma, out=None, stream=None):
         import torch
         if out is None:
@@ -370,7 +404,8 @@ class EB:
         inf = eb_info_t()
         _check(load().eb_info(self._h, C.byref(inf)))
         self.info = Info(inf.num_nodes, inf.num_cp, inf.num_bp, inf.num_cut, inf.num_far, inf.num_tiles,
-                         tuple(inf.tile), inf.max_delta_over_h, inf.min_abs_psi, inf.min_dominance_margin)
+                         tuple(inf.tile), inf.max_delta_over_h, inf.min_abs_psi, inf.min_dominance_margin,
+                         inf.num_rbf, inf.num_rbf_rotated)
 
     def retile(self, shape, stream=None):
         t = (C.c_int * 3)(*[int(v) for v in shape])
@@ -538,7 +573,8 @@ class _Borrowed(EB):
         inf = eb_info_t()
         _check(load().eb_info(self._h, C.byref(inf)))
         self.info = Info(inf.num_nodes, inf.num_cp, inf.num_bp, inf.num_cut, inf.num_far, inf.num_tiles,
-                         tuple(inf.tile), inf.max_delta_over_h, inf.min_abs_psi, inf.min_dominance_margin)
+                         tuple(inf.tile), inf.max_delta_over_h, inf.min_abs_psi, inf.min_dominance_margin,
+                         inf.num_rbf, inf.num_rbf_rotated)
 
     def close(self):
         self._h = C.c_void_p()

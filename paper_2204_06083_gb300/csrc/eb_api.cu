@@ -20,6 +20,11 @@ extern "C" {
 const char* eb_last_error(void) { return ebk::last_error(); }
 
 int eb_build(const eb_grid* grid, const eb_levelset* ls, eb_handle** out, cudaStream_t stream) {
+  return eb_build_ex(grid, ls, nullptr, out, stream);
+}
+
+int eb_build_ex(const eb_grid* grid, const eb_levelset* ls, const eb_build_opts* opts, eb_handle** out,
+                cudaStream_t stream) {
   if (!grid || !ls || !out) {
     set_error("eb_build: NULL argument");
     return EB_ERR_INVALID;
@@ -30,7 +35,7 @@ int eb_build(const eb_grid* grid, const eb_levelset* ls, eb_handle** out, cudaSt
     set_error("eb_build: host allocation failed");
     return EB_ERR_OOM;
   }
-  int st = guarded([&] { build_handle(e->h, *grid, *ls, stream); });
+  int st = guarded([&] { build_handle(e->h, *grid, *ls, stream, opts); });
   if (st != EB_OK) {
     destroy_handle(e->h);
     delete e;
@@ -64,7 +69,26 @@ int eb_info(const eb_handle* eb, eb_info_t* out) {
   out->max_delta_over_h = h.max_delta_over_h;
   out->min_abs_psi = h.min_abs_psi;
   out->min_dominance_margin = h.min_margin;
+  out->num_rbf = h.num_rbf;
+  out->num_rbf_rotated = h.num_rbf_rot;
   return EB_OK;
+}
+
+int eb_rbf_cuts(const eb_handle* eb, int32_t* cut_index_dev, double* xg2_dev, double* weights_dev,
+                int32_t* rotated_dev, cudaStream_t stream) {
+  if (!eb) {
+    set_error("eb_rbf_cuts: NULL handle");
+    return EB_ERR_INVALID;
+  }
+  return guarded([&] {
+    const EBHandle& h = eb->h;
+    const size_t n = (size_t)h.num_rbf;
+    if (n == 0) return;
+    if (cut_index_dev) EB_CUDA(cudaMemcpyAsync(cut_index_dev, h.rbf_cut, 4 * n, cudaMemcpyDeviceToDevice, stream));
+    if (xg2_dev) EB_CUDA(cudaMemcpyAsync(xg2_dev, h.rbf_xg2, 16 * n, cudaMemcpyDeviceToDevice, stream));
+    if (weights_dev) EB_CUDA(cudaMemcpyAsync(weights_dev, h.rbf_w, 24 * n, cudaMemcpyDeviceToDevice, stream));
+    if (rotated_dev) EB_CUDA(cudaMemcpyAsync(rotated_dev, h.rbf_rot, 4 * n, cudaMemcpyDeviceToDevice, stream));
+  });
 }
 
 // the public code bytes: the internal CODE_DIAG flag of CPs cleared
@@ -141,7 +165,7 @@ int eb_cuts(const eb_handle* eb, int32_t* cut_cp_dev, int32_t* cut_dir_dev, doub
 }
 
 int eb_rhs(const eb_handle* eb, const double* f_dev, const double* ugamma_dev, double* b_dev, cudaStream_t stream) {
-  if (!eb || !f_dev || !b_dev || (!ugamma_dev && eb->h.num_cut > 0)) {
+  if (!eb || !f_dev || !b_dev || (!ugamma_dev && eb->h.num_cut + eb->h.num_rbf > 0)) {
     set_error("eb_rhs: NULL argument");
     return EB_ERR_INVALID;
   }

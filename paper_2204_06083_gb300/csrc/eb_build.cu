@@ -8,6 +8,8 @@
 #include "eb_internal.cuh"
 
 #include <cmath>
+#include <cstring>
+#include <vector>
 
 namespace ebk {
 
@@ -20,6 +22,7 @@ struct LSDev {
   int k[EB_STAR_MAX_TERMS];
   double a[EB_STAR_MAX_TERMS], p[EB_STAR_MAX_TERMS];
   const double* psi;  // EB_LS_SAMPLED: psi at the nodes
+  double m[4];        // 2D quadric: x = c + M y on the boundary, M = (Q2^T)^-1 (row-major 2 x 2)
 };
 
 __device__ __forceinline__ double node_coord(double lo, int64_t i, double h) {
@@ -144,6 +147,17 @@ __device__ __forceinline__ bool on_border(const Geometry& G, const int64_t* i) {
 __device__ __forceinline__ void atomic_min_pos(double* addr, double v) {
   atomicMin(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
+// minimum of signed doubles through an order-preserving 64-bit key (init ~0)
+__device__ __forceinline__ void atomic_min_signed(unsigned long long* key, double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  atomicMin(key, (u >> 63) ? ~u : (u | 0x8000000000000000ull));
+}
+static double decode_signed_key(unsigned long long k) {
+  const unsigned long long u = (k & 0x8000000000000000ull) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+  double v;
+  std::memcpy(&v, &u, sizeof(v));
+  return v;
+}
 __device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
@@ -234,7 +248,7 @@ __global__ void k_cp_mask(Geometry G, uint8_t* code, const int32_t* cp_off, int3
 // pass 4: per CP, its cuts (walk + root) and the diagonal D_k = sum_s c_s
 __global__ void k_cut(Geometry G, LSDev L, const double* psi, const uint8_t* code, const int32_t* cp_node,
                       const int32_t* cut_off, int64_t num_cp, double* diag, int32_t* cut_cp, int32_t* cut_dir,
-                      double* cut_delta, double* cut_c, double* cut_xg, BuildStats* st) {
+                      double* cut_delta, double* cut_c, double* cut_xg, int32_t* cut_far, BuildStats* st) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= num_cp) return;
   int64_t node = cp_node[k];
@@ -279,6 +293,7 @@ __global__ void k_cut(Geometry G, LSDev L, const double* psi, const uint8_t* cod
       cut_cp[j] = (int32_t)k;
       cut_dir[j] = s;
       cut_delta[j] = delta;
+      cut_far[j] = mm > 1;  // the node past the BP is inside
       cut_c[j] = cs;
       for (int a = 0; a < G.dim; ++a)
         cut_xg[(int64_t)j * G.dim + a] = (a == axis) ? __dadd_rn(p[a], __dmul_rn((double)sg, delta)) : p[a];
@@ -352,6 +367,255 @@ __global__ void __launch_bounds__(128) k_cp_pairs(TileView tv, const uint8_t* __
   if (ok) list[off[tt] + before + __popc(m & ((1u << lane) - 1u))] = node;
 }
 
+// ------------------------------------------------------- RBF closure (2D)
+// Sec. 2.2: u_BP = w_ij u_ij + w_1 u_G1 + w_2 u_G2 from the cubic polyharmonic
+// RBF interpolant with linear augmentation (eqs. 7-9) through the CP and two
+// boundary points chosen by Algorithm 2.  The boundary is the parameterised
+// curve of the descriptor: quadric x = c + M (s0 cos t, s1 sin t), star x =
+// c + r(t) (cos t, sin t).
+struct Pt {
+  double x, y;
+};
+
+__device__ void rbf_curve(const LSDev& L, double t, Pt& g, Pt& g1, Pt& g2) {
+  if (L.kind == EB_LS_QUADRIC) {
+    const double ct = cos(t), st = sin(t);
+    const double y0 = L.s[0] * ct, y1 = L.s[1] * st, d0 = -L.s[0] * st, d1 = L.s[1] * ct;
+    g = {L.c[0] + L.m[0] * y0 + L.m[1] * y1, L.c[1] + L.m[2] * y0 + L.m[3] * y1};
+    g1 = {L.m[0] * d0 + L.m[1] * d1, L.m[2] * d0 + L.m[3] * d1};
+    g2 = {-(L.m[0] * y0 + L.m[1] * y1), -(L.m[2] * y0 + L.m[3] * y1)};
+    return;
+  }
+  double r = L.r0, r1 = 0.0, r2 = 0.0;
+  for (int j = 0; j < L.nk; ++j) {
+    const double a = L.a[j], k = (double)L.k[j];
+    const double sv = sin(k * t + L.p[j]), cv = cos(k * t + L.p[j]);
+    r += a * sv;
+    r1 += a * k * cv;
+    r2 -= a * k * k * sv;
+  }
+  const double ct = cos(t), st = sin(t);
+  g = {L.c[0] + r * ct, L.c[1] + r * st};
+  g1 = {r1 * ct - r * st, r1 * st + r * ct};
+  g2 = {r2 * ct - 2.0 * r1 * st - r * ct, r2 * st + 2.0 * r1 * ct - r * st};
+}
+
+// nearest point of Gamma to p: the nearest of RBF_GUESS uniform parameter
+// samples, then Newton on (Gamma(t) - p) . Gamma'(t) = 0, steps limited to one
+// sample spacing
+constexpr int RBF_GUESS = 256;
+__device__ Pt rbf_closest(const LSDev& L, Pt p) {
+  const double two_pi = 6.283185307179586;
+  const double dmax = two_pi / RBF_GUESS;
+  double best = 1e300, t = 0.0;
+  Pt g, g1, g2;
+  for (int k = 0; k < RBF_GUESS; ++k) {
+    const double tk = two_pi * k / RBF_GUESS;
+    rbf_curve(L, tk, g, g1, g2);
+    const double d = (g.x - p.x) * (g.x - p.x) + (g.y - p.y) * (g.y - p.y);
+    if (d < best) {
+      best = d;
+      t = tk;
+    }
+  }
+  for (int it = 0; it < 60; ++it) {
+    rbf_curve(L, t, g, g1, g2);
+    const double f = (g.x - p.x) * g1.x + (g.y - p.y) * g1.y;
+    const double df = g1.x * g1.x + g1.y * g1.y + (g.x - p.x) * g2.x + (g.y - p.y) * g2.y;
+    double step = df > 0.0 ? -f / df : (f > 0.0 ? -dmax : dmax);
+    step = fmin(fmax(step, -dmax), dmax);
+    t += step;
+    if (fabs(step) <= 1e-15) break;
+  }
+  rbf_curve(L, t, g, g1, g2);
+  return g;
+}
+
+__device__ double rbf_psi(const LSDev& L, double x, double y) {
+  const double xx[3] = {x, y, 0.0};
+  return psi_at(L, xx);
+}
+
+// first crossing of Gamma on the ray p + s d (p inside): march in steps of
+// h/4, then the Illinois iteration on the bracket; -1 if none within the limit
+constexpr int RBF_MARCH_LIMIT = 1 << 20;
+__device__ double rbf_ray(const LSDev& L, Pt p, Pt d, double h) {
+  const double step = 0.25 * h;
+  double a = 0.0, fa = rbf_psi(L, p.x, p.y), b = step, fb = rbf_psi(L, p.x + b * d.x, p.y + b * d.y);
+  int n = 0;
+  while (fb < 0.0) {
+    a = b;
+    fa = fb;
+    b += step;
+    fb = rbf_psi(L, p.x + b * d.x, p.y + b * d.y);
+    if (++n > RBF_MARCH_LIMIT) return -1.0;
+  }
+  if (fb == 0.0) return b;
+  int side = 0;
+  double told = a, t = b;
+  for (int it = 0; it < 100; ++it) {
+    t = (a * fb - b * fa) / (fb - fa);
+    const double ft = rbf_psi(L, p.x + t * d.x, p.y + t * d.y);
+    if (ft == 0.0) break;
+    if (ft < 0.0) {
+      if (side == -1) fb *= 0.5;
+      a = t;
+      fa = ft;
+      side = -1;
+    } else {
+      if (side == 1) fa *= 0.5;
+      b = t;
+      fb = ft;
+      side = 1;
+    }
+    if (fabs(t - told) <= 1e-15 * h) break;
+    told = t;
+  }
+  return t;
+}
+
+// weights of eqs. 7-9 in coordinates relative to x_BP scaled by 1/h: the 6 x 6
+// saddle system by Gaussian elimination with partial pivoting; false if it is
+// singular
+__device__ bool rbf_weights(const Pt* q, double* w) {
+  double B[6][7];
+  for (int a = 0; a < 6; ++a)
+    for (int b = 0; b < 7; ++b) B[a][b] = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    for (int b = 0; b < 3; ++b) {
+      const double r = hypot(q[a].x - q[b].x, q[a].y - q[b].y);
+      B[a][b] = r * r * r;
+    }
+    B[3][a] = B[a][3] = 1.0;
+    B[4][a] = B[a][4] = q[a].x;
+    B[5][a] = B[a][5] = q[a].y;
+    const double r = hypot(q[a].x, q[a].y);
+    B[a][6] = r * r * r;
+  }
+  B[3][6] = 1.0;
+  for (int c = 0; c < 6; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < 6; ++r)
+      if (fabs(B[r][c]) > fabs(B[piv][c])) piv = r;
+    if (!(fabs(B[piv][c]) > 0.0)) return false;
+    if (piv != c)
+      for (int b = 0; b < 7; ++b) {
+        const double t = B[c][b];
+        B[c][b] = B[piv][b];
+        B[piv][b] = t;
+      }
+    for (int r = c + 1; r < 6; ++r) {
+      const double f = B[r][c] / B[c][c];
+      for (int b = c; b < 7; ++b) B[r][b] -= f * B[c][b];
+    }
+  }
+  double x[6];
+  for (int r = 5; r >= 0; --r) {
+    double acc = B[r][6];
+    for (int b = r + 1; b < 6; ++b) acc -= B[r][b] * x[b];
+    x[r] = acc / B[r][r];
+  }
+  w[0] = x[0];
+  w[1] = x[1];
+  w[2] = x[2];
+  return isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]);
+}
+
+// One thread per RBF cut r (cut j = rbf_cut[r]): Algorithm 2 and the weights;
+// the cut's diagonal contribution becomes 1 - w_ij, its crossing G1 (distance
+// |x_BP - G1|), its first right-hand-side weight w_1; the second point G2 and
+// weight w_2 are stored per RBF cut.  bad = 1 if a system was singular or a
+// rotated line did not meet Gamma.
+__global__ void k_rbf(Geometry G, LSDev L, double eps, const int32_t* cp_node, const int32_t* rbf_cut, int64_t nrbf,
+                      const int32_t* cut_cp, const int32_t* cut_dir, double* cut_c, double* cut_w1, double* cut_delta,
+                      double* cut_xg, double* rbf_xg2, double* rbf_w, int32_t* rbf_rot, int* bad) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrbf) return;
+  const int j = rbf_cut[r];
+  const int64_t node = cp_node[cut_cp[j]];
+  const int s = cut_dir[j];
+  const int axis = s >> 1, sg = (s & 1) ? 1 : -1;
+  int64_t ij[2] = {node % G.n0, node / G.n0};
+  const Pt xij{node_coord(G.lo[0], ij[0], G.h), node_coord(G.lo[1], ij[1], G.h)};
+  ij[axis] += sg;
+  const Pt xbp{node_coord(G.lo[0], ij[0], G.h), node_coord(G.lo[1], ij[1], G.h)};
+  const double h = G.h;
+  const Pt g1 = rbf_closest(L, xbp);
+  Pt g2 = rbf_closest(L, xij);
+  int rot = 0;
+  if (!(hypot(g1.x - g2.x, g1.y - g2.y) > eps * h)) {
+    const Pt v{g1.x - xbp.x, g1.y - xbp.y};
+    const double nv = hypot(v.x, v.y);
+    const double c = cos(0.7853981633974483), sn = sin(0.7853981633974483);
+    const Pt d{(c * v.x - sn * v.y) / nv, (sn * v.x + c * v.y) / nv};
+    const double t = rbf_ray(L, xbp, d, h);
+    if (t < 0.0) atomicExch(bad, 1);
+    g2 = {xbp.x + t * d.x, xbp.y + t * d.y};
+    rot = 1;
+  }
+  const Pt q[3] = {{(xij.x - xbp.x) / h, (xij.y - xbp.y) / h}, {(g1.x - xbp.x) / h, (g1.y - xbp.y) / h},
+                   {(g2.x - xbp.x) / h, (g2.y - xbp.y) / h}};
+  double w[3];
+  if (!rbf_weights(q, w)) {
+    atomicExch(bad, 1);
+    w[0] = 0.0;
+    w[1] = 1.0;
+    w[2] = 0.0;
+  }
+  cut_c[j] = 1.0 - w[0];
+  cut_w1[j] = w[1];
+  cut_delta[j] = hypot(g1.x - xbp.x, g1.y - xbp.y);
+  cut_xg[2 * (int64_t)j] = g1.x;
+  cut_xg[2 * (int64_t)j + 1] = g1.y;
+  rbf_xg2[2 * r] = g2.x;
+  rbf_xg2[2 * r + 1] = g2.y;
+  rbf_w[3 * r] = w[0];
+  rbf_w[3 * r + 1] = w[1];
+  rbf_w[3 * r + 2] = w[2];
+  rbf_rot[r] = rot;
+}
+
+// RBF cuts of the closure mode (mixed: the far ones; rbf: all)
+__global__ void k_rbf_flag(int64_t nc, const int32_t* cut_far, int all, int32_t* flag) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < nc) flag[j] = all ? 1 : (cut_far[j] != 0);
+}
+
+__global__ void k_rbf_list(int64_t nc, const int32_t* flag, const int32_t* off, int32_t* rbf_cut, int32_t* cut_rbf) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nc) return;
+  cut_rbf[j] = flag[j] ? off[j] : -1;
+  if (flag[j]) rbf_cut[off[j]] = (int32_t)j;
+}
+
+__global__ void k_copy_f64(int64_t n, const double* a, double* b) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = a[i];
+}
+
+// D_k = sum_s c_s (1 towards a CP) in direction order, after the RBF cuts
+// changed their c_s; the dominance margin of the cut rows (signed: an RBF
+// weight w_ij > 1 makes it negative)
+__global__ void k_diag_from_cuts(Geometry G, const int32_t* cp_node, const uint8_t* code, const int32_t* cut_off,
+                                 const double* cut_c, int64_t num_cp, double* diag, unsigned long long* margin_min) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= num_cp) return;
+  const int64_t node = cp_node[k];
+  const uint8_t m = code[node] & 0x3F;
+  int j = cut_off[k];
+  double D = 0.0, margin = 0.0;
+  for (int sdir = 0; sdir < 2 * G.dim; ++sdir) {
+    double cs = 1.0;
+    if (m & (1u << sdir)) {
+      cs = cut_c[j++];
+      margin = __dadd_rn(margin, cs);
+    }
+    D = sdir == 0 ? cs : __dadd_rn(D, cs);
+  }
+  diag[node] = D;
+  if (m) atomic_min_signed(margin_min, margin);
+}
+
 static LSDev to_dev(const eb_levelset& ls, int dim) {
   LSDev L{};
   L.kind = ls.kind;
@@ -369,10 +633,28 @@ static LSDev to_dev(const eb_levelset& ls, int dim) {
     L.p[j] = ls.p[j];
   }
   L.psi = ls.psi;
+  if (dim == 2 && ls.kind == EB_LS_QUADRIC) {
+    // y = Q2^T (x - c): x = c + M y with M the inverse of Q2^T
+    const double a = ls.rot[0], b = ls.rot[3], c = ls.rot[1], d = ls.rot[4];  // Q2^T = [[a, b], [c, d]]
+    const double det = a * d - b * c;
+    L.m[0] = d / det;
+    L.m[1] = -b / det;
+    L.m[2] = -c / det;
+    L.m[3] = a / det;
+  }
   return L;
 }
 
-void build_handle(EBHandle& eb, const eb_grid& grid, const eb_levelset& ls, cudaStream_t s) {
+void build_handle(EBHandle& eb, const eb_grid& grid, const eb_levelset& ls, cudaStream_t s,
+                  const eb_build_opts* opts) {
+  const int closure = opts ? opts->closure : EB_CLOSURE_LINE;
+  const double rbf_eps = opts ? opts->rbf_eps : 0.025;
+  EB_REQUIRE(closure == EB_CLOSURE_LINE || closure == EB_CLOSURE_MIXED || closure == EB_CLOSURE_RBF, EB_ERR_INVALID,
+             "eb_build: closure must be EB_CLOSURE_LINE, EB_CLOSURE_MIXED or EB_CLOSURE_RBF");
+  EB_REQUIRE(closure == EB_CLOSURE_LINE || (grid.dim == 2 && (ls.kind == EB_LS_QUADRIC || ls.kind == EB_LS_STAR2D)),
+             EB_ERR_NOT_IMPLEMENTED, "eb_build: the RBF closure needs a 2D quadric or star level set");
+  EB_REQUIRE(closure == EB_CLOSURE_LINE || (rbf_eps > 0.0 && std::isfinite(rbf_eps)), EB_ERR_INVALID,
+             "eb_build: rbf_eps must be positive");
   EB_REQUIRE(grid.dim == 2 || grid.dim == 3, EB_ERR_INVALID, "grid.dim must be 2 or 3");
   EB_REQUIRE(grid.n[0] >= 3 && grid.n[1] >= 3 && (grid.dim == 2 ? grid.n[2] == 1 : grid.n[2] >= 3),
              EB_ERR_INVALID, "grid needs >= 3 nodes per used axis (and n[2] == 1 in 2D)");
@@ -448,9 +730,61 @@ void build_handle(EBHandle& eb, const eb_grid& grid, const eb_levelset& ls, cuda
   eb.cut_delta = dalloc<double>(nc, s, false);
   eb.cut_c = dalloc<double>(nc, s, false);
   eb.cut_xg = dalloc<double>((int64_t)nc * G.dim, s, false);
+  int32_t* cut_far = dalloc<int32_t>(nc, s, false);
   k_cut<<<blocks_for(ncp, 128), 128, 0, s>>>(G, L, psi, eb.code, eb.cp_node, eb.cut_off, ncp, eb.diag, eb.cut_cp,
-                                             eb.cut_dir, eb.cut_delta, eb.cut_c, eb.cut_xg, st);
+                                             eb.cut_dir, eb.cut_delta, eb.cut_c, eb.cut_xg, cut_far, st);
   EB_CUDA(cudaGetLastError());
+  eb.closure = closure;
+  double rbf_margin = 0.0;
+  if (closure != EB_CLOSURE_LINE && nc > 0) {
+    // Sec. 2.3: the RBF interpolation of Sec. 2.2 where the node past the BP
+    // is inside (mixed) or at every cut (RBF-based)
+    int32_t* flag = dalloc<int32_t>(nc + 1, s);
+    int32_t* off = dalloc<int32_t>(nc + 1, s, false);
+    int* bad = dalloc<int>(1, s);
+    unsigned long long* mkey = dalloc<unsigned long long>(1, s, false);
+    try {
+      k_rbf_flag<<<blocks_for(nc, T), T, 0, s>>>(nc, cut_far, closure == EB_CLOSURE_RBF ? 1 : 0, flag);
+      exclusive_scan_i32(flag, off, nc, s);
+      int32_t nr = 0;
+      EB_CUDA(cudaMemcpyAsync(&nr, off + nc, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      EB_CUDA(cudaStreamSynchronize(s));
+      eb.num_rbf = nr;
+      eb.rbf_cut = dalloc<int32_t>(nr, s, false);
+      eb.cut_rbf = dalloc<int32_t>(nc, s, false);
+      eb.rbf_xg2 = dalloc<double>(2 * (int64_t)nr, s, false);
+      eb.rbf_w = dalloc<double>(3 * (int64_t)nr, s, false);
+      eb.rbf_rot = dalloc<int32_t>(nr, s, false);
+      eb.cut_w1 = dalloc<double>(nc, s, false);
+      k_rbf_list<<<blocks_for(nc, T), T, 0, s>>>(nc, flag, off, eb.rbf_cut, eb.cut_rbf);
+      k_copy_f64<<<blocks_for(nc, T), T, 0, s>>>(nc, eb.cut_c, eb.cut_w1);  // w_1 = c_s on line-by-line cuts
+      if (nr > 0)
+        k_rbf<<<blocks_for(nr, 64), 64, 0, s>>>(G, L, rbf_eps, eb.cp_node, eb.rbf_cut, nr, eb.cut_cp, eb.cut_dir,
+                                                eb.cut_c, eb.cut_w1, eb.cut_delta, eb.cut_xg, eb.rbf_xg2, eb.rbf_w,
+                                                eb.rbf_rot, bad);
+      const unsigned long long init = ~0ull;
+      EB_CUDA(cudaMemcpyAsync(mkey, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+      k_diag_from_cuts<<<blocks_for(ncp, 128), 128, 0, s>>>(G, eb.cp_node, eb.code, eb.cut_off, eb.cut_c, ncp,
+                                                            eb.diag, mkey);
+      EB_CUDA(cudaGetLastError());
+      int hb = 0;
+      unsigned long long hk = 0;
+      EB_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+      EB_CUDA(cudaMemcpyAsync(&hk, mkey, sizeof(hk), cudaMemcpyDeviceToHost, s));
+      EB_CUDA(cudaStreamSynchronize(s));
+      EB_REQUIRE(hb == 0, EB_ERR_GEOMETRY, "eb_build: an RBF closure found no usable boundary points");
+      rbf_margin = decode_signed_key(hk);
+      std::vector<int32_t> rot(nr);
+      if (nr > 0) EB_CUDA(cudaMemcpy(rot.data(), eb.rbf_rot, sizeof(int32_t) * nr, cudaMemcpyDeviceToHost));
+      eb.num_rbf_rot = 0;
+      for (int32_t v : rot) eb.num_rbf_rot += v;
+    } catch (...) {
+      dfree(flag, s); dfree(off, s); dfree(bad, s); dfree(mkey, s); dfree(cut_far, s);
+      throw;
+    }
+    dfree(flag, s); dfree(off, s); dfree(bad, s); dfree(mkey, s);
+  }
+  dfree(cut_far, s);
 
   if (grid.dim == 2)
     build_tiles(eb, TileShape<2>::X, TileShape<2>::Y, TileShape<2>::Z, s);
@@ -464,7 +798,7 @@ void build_handle(EBHandle& eb, const eb_grid& grid, const eb_levelset& ls, cuda
   eb.num_far = (int64_t)hst.num_far;
   eb.max_delta_over_h = hst.max_delta_over_h;
   eb.min_abs_psi = hst.min_abs_psi;
-  eb.min_margin = eb.num_cut > 0 ? hst.min_margin : 0.0;
+  eb.min_margin = eb.num_cut > 0 ? (closure != EB_CLOSURE_LINE ? rbf_margin : hst.min_margin) : 0.0;
   dfree(psi, s); dfree(is_cp, s); dfree(cp_off, s); dfree(ncut, s); dfree(st, s);
   EB_CUDA(cudaStreamSynchronize(s));
 }
@@ -559,6 +893,8 @@ void destroy_handle(EBHandle& eb) {
   dfree(eb.code, s); dfree(eb.diag, s); dfree(eb.diag32, s); dfree(eb.cp_of_node, s); dfree(eb.cp_node, s);
   dfree(eb.tiles, s); dfree(eb.tile_base, s); dfree(eb.tile_lim, s); dfree(eb.pair_node, s); dfree(eb.cut_cp, s); dfree(eb.cut_dir, s); dfree(eb.cut_delta, s);
   dfree(eb.cut_c, s); dfree(eb.cut_xg, s); dfree(eb.cut_off, s); dfree(eb.cut_bc, s);
+  dfree(eb.rbf_cut, s); dfree(eb.cut_rbf, s); dfree(eb.rbf_xg2, s); dfree(eb.rbf_w, s); dfree(eb.rbf_rot, s);
+  dfree(eb.cut_w1, s); dfree(eb.cut_bw1, s); dfree(eb.rbf_bw2, s);
   for (int a = 0; a < 3; ++a) {
     dfree(eb.beta64[a], s);
     dfree(eb.beta32[a], s);
@@ -569,10 +905,14 @@ void destroy_handle(EBHandle& eb) {
 // ------------------------------------------------------------------- RHS
 // b_k = -f_k + sum over the cuts of k of (c_s u_Gamma) / h^2, summed in cut
 // order; 0 at the non-CP nodes of the active tiles.
+// RBF cuts (cut_rbf[j] = r >= 0) add their second value ug[num_cut + r] with
+// weight w2[r * w2_stride] after all first values of the CP (the order of the
+// assembled definition).
 template <int DIM>
 __global__ void __launch_bounds__(TILE_NODES) k_rhs(TileView tv, const uint8_t* code, const int32_t* cp_of_node,
                                                     const int32_t* cut_off, const double* cut_c, const double* f,
-                                                    const double* ug, double* b, double h2) {
+                                                    const double* ug, double* b, double h2, const int32_t* cut_rbf,
+                                                    const double* w2, int w2_stride, int64_t num_cut) {
   EB_TILE_LOOP(DIM, tv, node) {
     const uint8_t c = code[node];
     double v = 0.0;
@@ -581,6 +921,12 @@ __global__ void __launch_bounds__(TILE_NODES) k_rhs(TileView tv, const uint8_t* 
       if (c & 0x3F) {
         const int32_t k = cp_of_node[node];
         for (int j = cut_off[k]; j < cut_off[k + 1]; ++j) acc = __dadd_rn(acc, __ddiv_rn(__dmul_rn(cut_c[j], ug[j]), h2));
+        if (cut_rbf)
+          for (int j = cut_off[k]; j < cut_off[k + 1]; ++j) {
+            const int32_t r = cut_rbf[j];
+            if (r >= 0)
+              acc = __dadd_rn(acc, __ddiv_rn(__dmul_rn(w2[(int64_t)r * w2_stride], ug[num_cut + r]), h2));
+          }
       }
       v = __dadd_rn(-f[node], acc);
     }
@@ -592,11 +938,18 @@ void launch_rhs(const EBHandle& eb, const double* f, const double* ug, double* b
   const Geometry& G = eb.g;
   const double h2 = G.h * G.h;
   const unsigned blocks = tile_grid(eb);
-  const double* w = eb.cut_bc ? eb.cut_bc : eb.cut_c;  // beta_s c_s with a variable beta
+  // weight of each cut's first value: c_s (line-by-line) or w_1 (RBF), times beta with a variable beta
+  const double* w = eb.cut_bw1 ? eb.cut_bw1 : (eb.cut_bc && !eb.cut_w1) ? eb.cut_bc : eb.cut_w1 ? eb.cut_w1 : eb.cut_c;
+  const bool rbf = eb.num_rbf > 0;
+  const double* w2 = !rbf ? nullptr : eb.rbf_bw2 ? eb.rbf_bw2 : eb.rbf_w + 2;
+  const int w2s = eb.rbf_bw2 ? 1 : 3;
+  const int32_t* crbf = rbf ? eb.cut_rbf : nullptr;
   if (G.dim == 2)
-    k_rhs<2><<<blocks, TILE_NODES, 0, s>>>(eb.tv(), eb.code, eb.cp_of_node, eb.cut_off, w, f, ug, b, h2);
+    k_rhs<2><<<blocks, TILE_NODES, 0, s>>>(eb.tv(), eb.code, eb.cp_of_node, eb.cut_off, w, f, ug, b, h2, crbf, w2, w2s,
+                                           eb.num_cut);
   else
-    k_rhs<3><<<blocks, TILE_NODES, 0, s>>>(eb.tv(), eb.code, eb.cp_of_node, eb.cut_off, w, f, ug, b, h2);
+    k_rhs<3><<<blocks, TILE_NODES, 0, s>>>(eb.tv(), eb.code, eb.cp_of_node, eb.cut_off, w, f, ug, b, h2, crbf, w2, w2s,
+                                           eb.num_cut);
   EB_CUDA(cudaGetLastError());
 }
 
@@ -623,7 +976,7 @@ __global__ void k_beta_check(Geometry G, const double* bx, const double* by, con
 // the dominance margin of the cut rows.
 __global__ void k_beta_diag(Geometry G, const double* bx, const double* by, const double* bz, const int32_t* cp_node,
                             const int32_t* cut_off, const double* cut_c, int64_t num_cp, uint8_t* code, double* diag,
-                            double* cut_bc, double* margin_min) {
+                            double* cut_bc, unsigned long long* margin_min) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= num_cp) return;
   const int64_t node = cp_node[k];
@@ -649,7 +1002,23 @@ __global__ void k_beta_diag(Geometry G, const double* bx, const double* by, cons
   }
   diag[node] = D;
   code[node] = (uint8_t)(c | CODE_DIAG);
-  if (m) atomic_min_pos(margin_min, margin);
+  if (m) atomic_min_signed(margin_min, margin);
+}
+
+// beta of each cut's half point times its first right-hand-side weight, and
+// times the second weight of RBF cuts
+__global__ void k_beta_rbf(Geometry G, const double* bx, const double* by, const int32_t* cp_node,
+                           const int32_t* cut_cp, const int32_t* cut_dir, const double* cut_w1, const int32_t* cut_rbf,
+                           const double* rbf_w, int64_t nc, double* cut_bw1, double* rbf_bw2) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nc) return;
+  const int64_t node = cp_node[cut_cp[j]];
+  const int sdir = cut_dir[j], a = sdir >> 1;
+  const double* b = a == 0 ? bx : by;
+  const double beta = b[(sdir & 1) ? node : node - stride_of(G, a)];
+  cut_bw1[j] = __dmul_rn(beta, cut_w1[j]);
+  const int32_t r = cut_rbf[j];
+  if (r >= 0) rbf_bw2[r] = __dmul_rn(beta, rbf_w[3 * (int64_t)r + 2]);
 }
 
 void set_beta(EBHandle& eb, const double* const* beta, cudaStream_t s) {
@@ -659,7 +1028,7 @@ void set_beta(EBHandle& eb, const double* const* beta, cudaStream_t s) {
   for (int a = 0; a < G.dim; ++a) EB_REQUIRE(beta[a] != nullptr, EB_ERR_INVALID, "eb_set_beta: NULL beta array");
   const int64_t nn = G.num_nodes;
   const int T = 256;
-  double* bmin = dalloc<double>(1, s, false);
+  unsigned long long* bmin = dalloc<unsigned long long>(1, s, false);
   int* bad = dalloc<int>(1, s);
   try {
     // validate before anything of the handle changes
@@ -670,8 +1039,8 @@ void set_beta(EBHandle& eb, const double* const* beta, cudaStream_t s) {
     EB_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
     EB_CUDA(cudaStreamSynchronize(s));
     if (hb) throw Failure{EB_ERR_INVALID, "eb_set_beta: beta must be positive and finite at every half point a CP uses"};
-    const double init = 1e300;
-    EB_CUDA(cudaMemcpyAsync(bmin, &init, sizeof(double), cudaMemcpyHostToDevice, s));
+    const unsigned long long init = ~0ull;
+    EB_CUDA(cudaMemcpyAsync(bmin, &init, sizeof(init), cudaMemcpyHostToDevice, s));
     for (int a = 0; a < G.dim; ++a) {
       eb.beta64[a] = dalloc<double>(nn, s, false);
       EB_CUDA(cudaMemcpyAsync(eb.beta64[a], beta[a], sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
@@ -684,11 +1053,18 @@ void set_beta(EBHandle& eb, const double* const* beta, cudaStream_t s) {
                                                             eb.cut_off, eb.cut_c, eb.num_cp, eb.code, eb.diag,
                                                             eb.cut_bc, bmin);
     k_diag32<<<blocks_for(nn, T), T, 0, s>>>(nn, eb.diag, eb.diag32);
+    if (eb.num_rbf > 0) {
+      eb.cut_bw1 = dalloc<double>(eb.num_cut, s, false);
+      eb.rbf_bw2 = dalloc<double>(eb.num_rbf, s, false);
+      k_beta_rbf<<<blocks_for(eb.num_cut, 128), 128, 0, s>>>(G, eb.beta64[0], eb.beta64[1], eb.cp_node, eb.cut_cp,
+                                                              eb.cut_dir, eb.cut_w1, eb.cut_rbf, eb.rbf_w, eb.num_cut,
+                                                              eb.cut_bw1, eb.rbf_bw2);
+    }
     EB_CUDA(cudaGetLastError());
-    double hm = 0.0;
-    EB_CUDA(cudaMemcpyAsync(&hm, bmin, sizeof(double), cudaMemcpyDeviceToHost, s));
+    unsigned long long hk = 0;
+    EB_CUDA(cudaMemcpyAsync(&hk, bmin, sizeof(hk), cudaMemcpyDeviceToHost, s));
     EB_CUDA(cudaStreamSynchronize(s));
-    eb.min_margin = eb.num_cut > 0 ? hm : 0.0;
+    eb.min_margin = eb.num_cut > 0 ? decode_signed_key(hk) : 0.0;
   } catch (...) {
     dfree(bmin, s);
     dfree(bad, s);

@@ -144,7 +144,18 @@ struct EBHandle {
   // variable beta (eq. 3): null for beta = 1
   double* beta64[3] = {nullptr, nullptr, nullptr};
   float* beta32[3] = {nullptr, nullptr, nullptr};
-  double* cut_bc = nullptr;      // [num_cut] beta of the cut's half point times c_s (right-hand side weights)
+  double* cut_bc = nullptr;      // [num_cut] beta of the cut's half point times c_s (the diagonal's terms)
+  // RBF closure (Sec. 2.2) of the mixed / RBF-based methods: null for the line-by-line closure
+  int closure = EB_CLOSURE_LINE;
+  int64_t num_rbf = 0, num_rbf_rot = 0;
+  int32_t* rbf_cut = nullptr;    // [num_rbf] the cuts closed by RBF interpolation (ascending)
+  int32_t* cut_rbf = nullptr;    // [num_cut] index in rbf_cut, -1 for line-by-line cuts
+  double* rbf_xg2 = nullptr;     // [num_rbf x 2] second boundary point G2
+  double* rbf_w = nullptr;       // [num_rbf x 3] weights (w_ij, w_1, w_2)
+  int32_t* rbf_rot = nullptr;    // [num_rbf] G2 from Algorithm 2's rotated line
+  double* cut_w1 = nullptr;      // [num_cut] right-hand-side weight of the first value (c_s on line cuts)
+  double* cut_bw1 = nullptr;     // [num_cut] beta times cut_w1 (variable beta with RBF cuts)
+  double* rbf_bw2 = nullptr;     // [num_rbf] beta times w_2
   bool has_beta() const { return beta64[0] != nullptr; }
   static int ilog2(int v) {
     int r = 0;
@@ -205,7 +216,8 @@ inline void dim_dispatch(const EBHandle& eb, F&& f) {
 }
 
 // ----------------------------------------------------------- build / apply
-void build_handle(EBHandle& eb, const eb_grid& grid, const eb_levelset& ls, cudaStream_t s);
+void build_handle(EBHandle& eb, const eb_grid& grid, const eb_levelset& ls, cudaStream_t s,
+                  const eb_build_opts* opts = nullptr);
 void destroy_handle(EBHandle& eb);
 
 // y = (sigma I + A) x over the active tiles (masked, non-CP outputs 0).
