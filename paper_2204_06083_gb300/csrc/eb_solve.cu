@@ -583,7 +583,7 @@ int Solver::heat(double dt, double theta, const double* b1, const double* b0, do
   EB_DIMV_LAUNCH(*eb, k_heat_rhs, nblk, eb->tv(), eb->code, eb->diag, 1.0 / (G.h * G.h), dt, theta, u, b1,
                 b0 ? b0 : b1, tmp);
   EB_CUDA(cudaGetLastError());
-  pcg_opts o{H ? EB_PC_AMG : EB_PC_JACOBI, 1, 0, 0};
+  pcg_opts o{H ? EB_PC_AMG : EB_PC_JACOBI, 1, 1, 0};  // the loop on the device (tmp and u keep their addresses)
   return pcg(tmp, u, rtol, maxit, o, stats, s);
 }
 

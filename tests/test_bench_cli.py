@@ -14,6 +14,7 @@ def test_every_workload_has_a_gpu_body():
     import bench
     names = {"poisson3d": "gpu_poisson", "poisson2d": "gpu_poisson", "wave": "gpu_wave", "batched": "gpu_batched",
              "learned": "gpu_learned", "conv": "gpu_conv"}
+    names.update({w: "gpu_paper" for w in bench.PAPER_WORKLOADS})
     assert set(bench.WORKLOADS) == set(names)
     for w, fn in names.items():
         assert callable(getattr(bench, fn)), w
@@ -29,3 +30,13 @@ def test_reference_arm_line():
         assert k in line, k
     assert line["impl"] == "reference" and line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+
+def test_paper_workload_oracle_samples_run():
+    """Every paper workload's CPU oracle sample runs and reports its units."""
+    sys.path.insert(0, str(ROOT))
+    import bench
+    for w in ("rs_w", "qoi"):
+        v, sample, rec = bench.cpu_oracle_sample(w)
+        assert v > 0 and rec["units"] > 0 and sample
