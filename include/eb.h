@@ -320,6 +320,14 @@ int amg_set_csr_epl(amg_handle* amg, int epl);
  * vectors: call between solves.  us_out: microseconds per launch.
  * Synchronous. */
 enum { EB_TK_SMOOTH_STEP = 0 };
+/* The size-matched reference of amg_time_kernel (instrumentation; the paper
+ * has no counterpart): a plain streaming copy that reads bytes/2 and writes
+ * bytes/2 (16-byte accesses, grid-stride), timed the same way -- `launches`
+ * back-to-back launches in one graph, each preceded by a read of clear_bytes
+ * when > 0, whose time is subtracted -- so that a kernel moving the same bytes
+ * can be compared with the best a single launch of that size achieves.  The
+ * buffers are allocated for the call.  Synchronous. */
+int eb_time_copy(int64_t bytes, int launches, int64_t clear_bytes, double* us_out, cudaStream_t stream);
 int amg_time_kernel(const amg_handle* amg, int kernel, int level, int launches, int64_t clear_bytes, double* us_out,
                     cudaStream_t stream);
 

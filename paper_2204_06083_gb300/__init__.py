@@ -30,6 +30,14 @@ CODE_BP = 0x40
 CODE_CP = 0x80
 
 
+def time_copy_us(nbytes: int, launches: int = 20, clear_bytes: int = 0, stream=None) -> float:
+    """Microseconds per launch of a plain copy moving nbytes (half read, half
+    written), timed like amg_time_kernel (eb_time_copy)."""
+    out = C.c_double()
+    _check(load().eb_time_copy(int(nbytes), int(launches), int(clear_bytes), C.byref(out), _stream(stream)))
+    return out.value
+
+
 def fp64_peak_tflops(reps: int = 20, stream=None) -> float:
     """Measured FP64 FMA throughput of the current GPU in TFLOP/s."""
     out = C.c_double()
@@ -165,6 +173,7 @@ _SIGS = {
                                C.POINTER(pcg_stats), _P]),
     "eb_fp64_peak": (C.c_int, [C.c_int, _P, _P]),
     "eb_set_beta": (C.c_int, [_P, _P, _P, _P, _P]),
+    "eb_time_copy": (C.c_int, [C.c_int64, C.c_int, C.c_int64, _P, _P]),
     "batch_weighted_sum": (C.c_int, [_P, _P, _P, _P, _P]),
     "minres_solve": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.c_double, C.c_int, C.POINTER(pcg_stats), _P]),
     "wave_theta_step": (C.c_int, [_P, C.c_double, C.c_double, _P, _P, C.c_int, C.c_double, C.c_int,

@@ -908,9 +908,47 @@ static double time_alone(const std::function<void(cudaStream_t)>& launch, int la
   return us;
 }
 
+// plain streaming copy (16-byte loads and stores, grid-stride): the size-matched
+// reference of eb_time_copy
+__global__ void __launch_bounds__(256) k_stream_copy(const uint4* __restrict__ a, uint4* __restrict__ b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = __ldcs(a + i);
+}
+
 }  // namespace ebk
 
 using namespace ebk;
+
+extern "C" int eb_time_copy(int64_t bytes, int launches, int64_t clear_bytes, double* us_out, cudaStream_t stream) {
+  if (!us_out || bytes < 32 || launches < 1 || launches > 10000 || clear_bytes < 0) {
+    set_error("eb_time_copy: invalid argument");
+    return EB_ERR_INVALID;
+  }
+  return guarded([&] {
+    const int64_t n = bytes / 2 / (int64_t)sizeof(uint4);  // half read, half written
+    uint4* a = dalloc<uint4>(n, stream);
+    uint4* b = nullptr;
+    const int64_t nclear = clear_bytes / (int64_t)sizeof(uint4);
+    uint4* clear = nullptr;
+    try {
+      b = dalloc<uint4>(n, stream);
+      clear = nclear > 0 ? dalloc<uint4>(nclear, stream) : nullptr;
+      const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8);
+      auto launch = [&](cudaStream_t s) { k_stream_copy<<<grid, 256, 0, s>>>(a, b, n); };
+      EB_CUDA(cudaStreamSynchronize(stream));
+      *us_out = time_alone(launch, launches, clear, nclear, stream);
+    } catch (...) {
+      dfree(a, stream);
+      dfree(b, stream);
+      dfree(clear, stream);
+      throw;
+    }
+    dfree(a, stream);
+    dfree(b, stream);
+    dfree(clear, stream);
+    EB_CUDA(cudaStreamSynchronize(stream));
+  });
+}
 
 extern "C" int amg_time_kernel(const amg_handle* amg, int kernel, int level, int launches, int64_t clear_bytes,
                                double* us_out, cudaStream_t stream) {
