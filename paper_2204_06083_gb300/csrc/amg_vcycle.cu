@@ -86,6 +86,13 @@ __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16, double>(double v) {
   return __double2bfloat16(v);
 }
 
+// the operator constants at item tt_ of EB_SWEEP: per tile for a batched view
+template <int DIM, class A>
+__device__ __forceinline__ GOp<A> sweep_op(const TileView& tv, int64_t tt, const GOp<A>& o) {
+  if constexpr ((DIM & DIM_LIST) != 0) return o;
+  else return tile_op(tv, tt, o);
+}
+
 // the view without its CP pair list: EB_SWEEP then visits every pair of the
 // active tiles
 inline TileView tiles_only(TileView tv) {
@@ -105,7 +112,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_first(TileView tv, const 
                                                              typename AccOf<V>::type theta) {
   using A = typename AccOf<V>::type;
   EB_SWEEP(DIM, tv, node) {
-    const GOp<A> ot = tile_op(tv, tt_, o);
+    const GOp<A> ot = sweep_op<DIM>(tv, tt_, o);
     uint32_t c0, c1;
     ld_codes(code, node, c0, c1);
     const Two<double> rv = LdRO::ld2(r + node);
@@ -184,7 +191,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_step(TileView tv, const u
   using A = typename AccOf<V>::type;
   double srz = 0.0;
   EB_SWEEP(DIM, tv, node) {
-    const GOp<A> ot = tile_op(tv, tt_, o);
+    const GOp<A> ot = sweep_op<DIM>(tv, tt_, o);
     uint32_t k0, k1;
     ld_codes(code, node, k0, k1);
     Two<A> xc, core;
@@ -222,7 +229,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_resid(TileView tv, const uint8
                                                         V* __restrict__ r) {
   using A = typename AccOf<V>::type;
   EB_SWEEP(DIM, tv, node) {
-    const GOp<A> ot = tile_op(tv, tt_, o);
+    const GOp<A> ot = sweep_op<DIM>(tv, tt_, o);
     uint32_t c0, c1;
     ld_codes(code, node, c0, c1);
     Two<A> xc, core;
@@ -631,6 +638,10 @@ static int vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, co
   }
   const double inv_h2 = 1.0 / (G.h * G.h);
   const unsigned gb = tile_grid(eb);
+  // list sweeps: one CP pair per thread (the partial-forming launch keeps the
+  // fixed grid gb, whose CTA count is the number of partials)
+  constexpr bool LIST = (DIM & DIM_LIST) != 0;
+  const unsigned gl = LIST ? blocks_for(eb.num_pairs, TILE_NODES) : gb;
   const ChebCoef cc = cheb_coef(L0.rho, S.opts.cheb_degree);
   const TileView tv = eb.tv();
   using A = typename AccOf<V>::type;
@@ -646,14 +657,14 @@ static int vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, co
   if (first_done)
     S.nlaunch -= 1;  // amg_update_first did it
   else
-    k_g_cheb_first<DIM, V><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, r, bcopy, x, g.d, (A)cc.theta);
+    k_g_cheb_first<DIM, V><<<gl, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, r, bcopy, x, g.d, (A)cc.theta);
   for (int k = 1; k < cc.deg; ++k) {
     S.prof_mark(s, true);
-    k_g_cheb_step<DIM, V, V><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, x, x2, g.d, (A)cc.c1[k], (A)cc.c2[k]);
+    k_g_cheb_step<DIM, V, V><<<gl, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, x, x2, g.d, (A)cc.c1[k], (A)cc.c2[k]);
     S.prof_mark(s, false);
     std::swap(x, x2);
   }
-  k_g_resid<DIM, V><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, x, g.r);
+  k_g_resid<DIM, V><<<gl, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, x, g.r);
   Level& C = H.L[1];
   VecSet<V>& cv = LV::vec(C);
   const CsrV<V> R0 = LV::R(L0), P0 = LV::P(L0);
@@ -668,7 +679,7 @@ static int vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, co
   vcycle_compact<V>(S, 1, s);
   if (S.opts.cycle == 2 && H.L.size() > 2) vcycle_compact<V>(S, 1, s, true);  // W-cycle
   if (M.on)
-    k_prolong_mf<DIM, V, SC><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, (A)M.omega, M.agg_node, sc, cv.x, x);
+    k_prolong_mf<DIM, V, SC><<<gl, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, (A)M.omega, M.agg_node, sc, cv.x, x);
   else
     EB_GROUP_LAUNCH(gP, k_prolong0, V, P0.n, s, P0.n, P0.rp, P0.ci, P0.v, eb.cp_node, cv.x, x);
   for (int k = 0; k < cc.deg; ++k) {
@@ -680,10 +691,10 @@ static int vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, co
       k_g_cheb_step<DIM, V, double, true><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, x, z, g.d, (A)cc.c1[k],
                                                                     (A)cc.c2[k], dot->r, dot->part);
     else if (k == cc.deg - 1)  // z for a caller (amg_vcycle): every node of the active tiles, 0 off the CPs
-      k_g_cheb_step<DIM, V, double>
+      k_g_cheb_step<(DIM & ~DIM_LIST), V, double>
           <<<gb, TILE_NODES, 0, s>>>(tiles_only(tv), eb.code, diag, o, b, x, z, g.d, (A)cc.c1[k], (A)cc.c2[k]);
     else
-      k_g_cheb_step<DIM, V, V><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, x, x2, g.d, (A)cc.c1[k], (A)cc.c2[k]);
+      k_g_cheb_step<DIM, V, V><<<gl, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, x, x2, g.d, (A)cc.c1[k], (A)cc.c2[k]);
     if (mark) S.prof_mark(s, false);
     if (k != cc.deg - 1) std::swap(x, x2);
   }
@@ -696,12 +707,17 @@ static int vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, co
 int amg_vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, const VcycleDot* dot, bool first_done) {
   int ret = 0;
   dim_dispatch(*S.eb, [&](auto D) {
+    constexpr int DL = D.value | DIM_LIST;
+    const bool list = S.eb->pair_node != nullptr;
     if (S.opts.vcycle_prec == EB_F32)
-      ret = vcycle_grid<float, D.value>(S, r, z, s, dot, first_done);
+      ret = list ? vcycle_grid<float, DL>(S, r, z, s, dot, first_done)
+                 : vcycle_grid<float, D.value>(S, r, z, s, dot, first_done);
     else if (S.opts.vcycle_prec == EB_BF16)
-      ret = vcycle_grid<__nv_bfloat16, D.value>(S, r, z, s, dot, first_done);
+      ret = list ? vcycle_grid<__nv_bfloat16, DL>(S, r, z, s, dot, first_done)
+                 : vcycle_grid<__nv_bfloat16, D.value>(S, r, z, s, dot, first_done);
     else
-      ret = vcycle_grid<double, D.value>(S, r, z, s, dot, first_done);
+      ret = list ? vcycle_grid<double, DL>(S, r, z, s, dot, first_done)
+                 : vcycle_grid<double, D.value>(S, r, z, s, dot, first_done);
   });
   return ret;
 }
@@ -846,8 +862,12 @@ static void smoother_step(Solver& S, int level, cudaStream_t s) {
     VecSet<V>& g = LV::grid(H);
     const V* b = std::is_same<V, double>::value ? reinterpret_cast<const V*>(S.r) : g.b;
     dim_dispatch(eb, [&](auto D) {
-      k_g_cheb_step<D.value, V, V><<<tile_grid(eb), TILE_NODES, 0, s>>>(eb.tv(), eb.code, diag_of<V>(eb), o, b, g.x,
-                                                                          g.x2, g.d, (A)cc.c1[k], (A)cc.c2[k]);
+      if (eb.pair_node)
+        k_g_cheb_step<D.value | DIM_LIST, V, V><<<blocks_for(eb.num_pairs, TILE_NODES), TILE_NODES, 0, s>>>(
+            eb.tv(), eb.code, diag_of<V>(eb), o, b, g.x, g.x2, g.d, (A)cc.c1[k], (A)cc.c2[k]);
+      else
+        k_g_cheb_step<D.value, V, V><<<tile_grid(eb), TILE_NODES, 0, s>>>(eb.tv(), eb.code, diag_of<V>(eb), o, b,
+                                                                            g.x, g.x2, g.d, (A)cc.c1[k], (A)cc.c2[k]);
     });
   } else {
     VecSet<V>& v = LV::vec(L);

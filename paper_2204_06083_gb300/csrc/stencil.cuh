@@ -168,7 +168,7 @@ __device__ __forceinline__ void stencil_tv(const TileView& tv, const T* __restri
   if constexpr ((DIM & DIM_VB) != 0)
     stencil_pair_beta<dim_of(DIM), L>(x, node, tv.nn, c0, c1, diag, tv.sy, tv.sz, beta_ptrs(tv, diag), xc, core);
   else
-    stencil_pair<DIM, L>(x, node, tv.nn, c0, c1, diag, tv.sy, tv.sz, xc, core);
+    stencil_pair<dim_of(DIM), L>(x, node, tv.nn, c0, c1, diag, tv.sy, tv.sz, xc, core);
 }
 
 // the two code bytes of a pair

@@ -20,6 +20,9 @@ constexpr int TILE_NODES = 256;
 // flag in the DIM template argument of a grid kernel: the variable-coefficient
 // stencil (beta of eq. 3 read from the view); dim_of strips it
 constexpr int DIM_VB = 8;
+// flag in the DIM template argument: the view has a CP pair list and EB_SWEEP
+// visits its pairs, one per thread and grid-stride, with no tile-mode code
+constexpr int DIM_LIST = 16;
 __host__ __device__ constexpr int dim_of(int d) { return d & 3; }
 constexpr int PAIR_THREADS = 128;  // threads per tile in the pair layout
 
@@ -106,22 +109,39 @@ namespace ebk {
 // item it_ of EB_SWEEP: a CP pair of the list, or pair t of listed tile it_
 template <int DIM>
 __device__ __forceinline__ bool sweep_pair(const TileView& tv, int64_t it, int t, int32_t& node) {
-  if (tv.pair_node) {
+  if ((DIM & DIM_LIST) != 0 || tv.pair_node) {
     node = __ldg(tv.pair_node + it);
     return true;
   }
   return tile_pair<DIM>(tv, it, t, node);
 }
+// first item, end and stride of EB_SWEEP
+template <int DIM>
+__device__ __forceinline__ bool sweep_list(const TileView& tv) {
+  return (DIM & DIM_LIST) != 0 || tv.pair_node != nullptr;
+}
+template <int DIM>
+__device__ __forceinline__ int64_t sweep_begin(const TileView& tv) {
+  return sweep_list<DIM>(tv) ? (int64_t)blockIdx.x * blockDim.x + threadIdx.x
+                             : 2 * (int64_t)blockIdx.x + (threadIdx.x >> 7);
+}
+template <int DIM>
+__device__ __forceinline__ int64_t sweep_end(const TileView& tv) {
+  return sweep_list<DIM>(tv) ? tv.npairs : tv.ntiles;
+}
+template <int DIM>
+__device__ __forceinline__ int64_t sweep_step(const TileView& tv) {
+  return sweep_list<DIM>(tv) ? (int64_t)gridDim.x * blockDim.x : 2 * (int64_t)gridDim.x;
+}
 }  // namespace ebk
 
 // for (each pair this thread handles) body: the CP pairs of the view's list
 // when it has one (values at the nodes of the other pairs are never read at a
-// CP), else every pair of every listed tile as EB_PAIR_LOOP (tt_ is then the
-// tile; with a list it is the list index and the view has no per-tile shifts)
+// CP) or DIM carries DIM_LIST, else every pair of every listed tile as
+// EB_PAIR_LOOP (tt_ is then the tile; with a list it is the list index and the
+// view has no per-tile shifts)
 #define EB_SWEEP(DIM, tv, node)                                                                             \
-  for (int64_t tt_ = (tv).pair_node ? (int64_t)blockIdx.x * blockDim.x + threadIdx.x                        \
-                                    : 2 * (int64_t)blockIdx.x + (threadIdx.x >> 7),                         \
-               end_ = (tv).pair_node ? (tv).npairs : (tv).ntiles,                                           \
-               step_ = (tv).pair_node ? (int64_t)gridDim.x * blockDim.x : 2 * (int64_t)gridDim.x;           \
+  for (int64_t tt_ = ::ebk::sweep_begin<DIM>(tv), end_ = ::ebk::sweep_end<DIM>(tv),                         \
+               step_ = ::ebk::sweep_step<DIM>(tv);                                                          \
        tt_ < end_; tt_ += step_)                                                                            \
     if (int32_t node = 0; ::ebk::sweep_pair<DIM>((tv), tt_, threadIdx.x & 127, node))
