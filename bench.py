@@ -5,8 +5,9 @@
 poisson3d  3D Poisson AMG-PCG: ellipsoid with semi-axes 0.7/0.5/0.4 and a seeded
            rotation, 256^3 nodes on [-1,1]^3, u = exp(x) sin(y+z).  One step =
            one pcg_solve from x = 0 to ||r||/||b|| <= 1e-10 (FP32 V-cycle,
-           flexible FP64 PCG); the plain FP64 V-cycle and the BF16-storage
-           V-cycle are timed beside it.
+           flexible PCG with its vectors in double-float, the exit test on the
+           FP64 true residual); the FP64 outer iteration, the plain FP64
+           V-cycle and the BF16-storage V-cycle are timed beside it.
 poisson2d  2D Poisson, plain FP64 AMG-PCG: circle R = 0.5 at (0.02, 0.01),
            128^2 nodes, u = sin(2x) cos(3y), rtol 1e-10.
 wave       Leapfrog wave equation on the star r = 0.5 + 0.1 sin(5 phi), 4096^2
@@ -166,7 +167,8 @@ def config_of(w, small=None):
         n = small or N_FULL
         return {"workload": f"3D Poisson AMG-PCG, ellipsoid (0.7,0.5,0.4) seeded rotation, {n}^3 nodes on [-1,1]^3, "
                             f"u=exp(x)sin(y+z), rtol {RTOL:g}", "n": n, "rtol": RTOL,
-                "vcycle": "FP32 storage and arithmetic, Chebyshev-2, smoothed aggregation; outer flexible PCG in FP64",
+                "vcycle": "FP32 storage and arithmetic, Chebyshev-2, smoothed aggregation; outer flexible PCG with "
+                          "double-float vectors (pcg_opts.outer_prec = EB_DF64), FP64 scalars and exit test",
                 "l2": "flushed between timed steps (512 MB write outside the timed events)"}
     if w == "poisson2d":
         return {"workload": f"2D Poisson plain FP64 AMG-PCG, circle R=0.5 at (0.02,0.01), 128^2 nodes on [-1,1]^2, "
@@ -744,21 +746,41 @@ def gpu_poisson(ctx, args, dim):
     x = torch.zeros_like(b)
 
     loop_kind = 2 if args.host_loop else 1
+    # 3D (FP32 V-cycle): the outer iteration in double-float (pcg_opts.outer_prec);
+    # the FP64 outer iteration is timed beside it
+    outer = eb.EB_DF64 if dim == 3 else eb.EB_F64
 
     def step():
         x.zero_()
-        return solver.solve(b, x=x, rtol=RTOL, maxit=500, use_graph=loop_kind)[1]
+        return solver.solve(b, x=x, rtol=RTOL, maxit=500, use_graph=loop_kind, outer=outer)[1]
 
     sts, ms_per_step, clocks = loop(ctx, args, step, torch.cuda.current_device())
     launches = sum(s.launches for s in sts) // len(sts)
-    prof_ms, prof_n = profiled(ctx, args, lambda: solver.solve(b, x=x.zero_(), rtol=RTOL, maxit=500, profile=1)[1])
-    l1_ms, l1_n = (profiled(ctx, args, lambda: solver.solve(b, x=x.zero_(), rtol=RTOL, maxit=500, profile=3)[1])
-                   if solver.num_levels > 2 else (0.0, 0))
-    xp_ms, xp_n = profiled(ctx, args, lambda: solver.solve(b, x=x.zero_(), rtol=RTOL, maxit=500, profile=4)[1])
-    up_ms, up_n = profiled(ctx, args, lambda: solver.solve(b, x=x.zero_(), rtol=RTOL, maxit=500, profile=5)[1])
+
+    def prof(mode, o=outer):
+        return profiled(ctx, args, lambda: solver.solve(b, x=x.zero_(), rtol=RTOL, maxit=500, profile=mode,
+                                                        outer=o)[1])
+    prof_ms, prof_n = prof(1)
+    l1_ms, l1_n = prof(3) if solver.num_levels > 2 else (0.0, 0)
+    xp_ms, xp_n = prof(4)
+    up_ms, up_n = prof(5)
     value = ctx.world * nc / (ms_per_step / 1000.0)
     extra = {}
     if dim == 3:
+        o64 = []
+        for i in range(args.warmup + args.steps):
+            x.zero_()
+            ctx.flush()
+            t, sto = timed(lambda: solver.solve(b, x=x, rtol=RTOL, maxit=500)[1])
+            if i >= args.warmup:
+                o64.append(t)
+        xp64_ms, xp64_n = prof(4, eb.EB_F64)
+        up64_ms, up64_n = prof(5, eb.EB_F64)
+        extra["fp64_outer"] = {"time_to_tol_ms": statistics.mean(o64), "iterations": sto.iterations,
+                               "true_rel_residual": sto.true_rel_residual,
+                               "dof_per_s": nc / (statistics.mean(o64) / 1000.0),
+                               "kernel_time_ms_per_solve": {"pcg_p_update_apply": xp64_ms / max(args.steps, 1),
+                                                            "pcg_xr_update": up64_ms / max(args.steps, 1)}}
         f64 = []
         for i in range(args.warmup + args.steps):
             x.zero_()
@@ -789,7 +811,7 @@ def gpu_poisson(ctx, args, dim):
     def e2e_step():
         db.copy_(hb, non_blocking=True)
         x.zero_()
-        solver.solve(db, x=x, rtol=RTOL, maxit=500)
+        solver.solve(db, x=x, rtol=RTOL, maxit=500, outer=outer)
         hx.copy_(x, non_blocking=True)
 
     for i in range(args.warmup + args.steps):
@@ -853,40 +875,60 @@ def gpu_poisson(ctx, args, dim):
                   "warm_l2_frac": l1_bytes / (alone[1]["warm_us"] * 1e-6) / 1e9 / pk["hbm_gbs"],
                   "in_solve_event_us": (l1_ms / l1_n) * 1000.0 if l1_n else None, "in_solve_launches_timed": l1_n,
                   "in_solve_timing": PROF_NOTE, "size_matched_copy": size_matched(l1_bytes, alone[1]["cold_us"])}
-    # the PCG's FP64 kernels, against the measured FP64 FMA peak (k_xpby_apply:
-    # per DOF the 7-point sum, 5 adds, and D x - sum, one FMA, then p = z + beta
-    # p, q = B z + beta q and the p.q partial, three FMAs: 13 FLOP; 41 B: z read,
-    # p and q read and written, the code byte) and the HBM peak (k_update_first:
-    # per DOF r, q, p, x, z read, x and r written in FP64, the level-0 right-hand
-    # side, iterate and direction written in the V-cycle's precision, the code
-    # byte: 69 B with FP32 V-cycle vectors, 81 B with FP64)
+    # The PCG's kernels.  DF outer iteration (3D): both are memory passes,
+    # against HBM -- k_xpby_apply_df: per DOF z read (FP32), p and q read and
+    # written (DF, 8 B each), the code byte: 37 B; k_update_first_df: r, q, p,
+    # x read and x, r written (DF), z read, the level-0 right-hand side,
+    # iterate and direction written (FP32), the code byte: 65 B.  FP64 outer
+    # iteration: k_xpby_apply against the measured FP64 FMA peak (per DOF the
+    # 7-point sum, 5 adds, and D x - sum, one FMA, then p = z + beta p, q = B z
+    # + beta q and the p.q partial, three FMAs: 13 FLOP), k_update_first against
+    # HBM (69 B with FP32 V-cycle vectors, 81 B with FP64).
     fp64_tflops = eb.fp64_peak_tflops(reps=20)
     share = {"level0_smoother": prof_ms, "level1_smoother": l1_ms, "pcg_p_update_apply": xp_ms,
              "pcg_xr_update": up_ms}
     xp_flop = (13 if dim == 3 else 11) * nc
-    xp_s = (xp_ms / xp_n) / 1000.0 if xp_n else float("nan")
-    pcg_apply = {"bound": "alu", "kernel": f"k_xpby_apply<{dim}, false, true> (p update + next operator apply, FP64)",
-                 "achieved": xp_flop / xp_s / 1e12, "peak": fp64_tflops,
-                 "peak_kind": "measured FP64 FMA throughput (eb_fp64_peak, this run)", "unit": "TFLOP/s",
-                 "frac": xp_flop / xp_s / 1e12 / fp64_tflops, "traffic": None,
-                 "algorithmic_flop_per_launch": xp_flop, "algorithmic_bytes_per_launch": 41 * nc,
-                 "hbm_frac": 41 * nc / xp_s / 1e9 / pk_hbm(), "avg_launch_us": xp_s * 1e6, "launches_timed": xp_n,
-                 "timing": PROF_NOTE + "; each bracketed launch carries the event pair's few microseconds"}
-    up_bytes = (69 if dim == 3 else 81) * nc
-    up_s = (up_ms / up_n) / 1000.0 if up_n else float("nan")
-    pcg_update = {"bound": "hbm", "kernel": f"k_update_first<{dim}, {'float' if dim == 3 else 'double'}> "
-                                           "(x/r update + first level-0 smoothing step)",
-                  "achieved": up_bytes / up_s / 1e9, "peak": pk_hbm(), "peak_kind": "measured HBM copy (burst)",
-                  "unit": "GB/s", "frac": up_bytes / up_s / 1e9 / pk_hbm(), "traffic": None,
-                  "algorithmic_bytes_per_launch": up_bytes, "avg_launch_us": up_s * 1e6, "launches_timed": up_n,
-                  "timing": PROF_NOTE + "; each bracketed launch carries the event pair's few microseconds"}
+
+    def fp64_apply_roof(ms, n):
+        sec = (ms / n) / 1000.0 if n else float("nan")
+        return {"bound": "alu", "kernel": f"k_xpby_apply<{dim}, false, true> (p update + next operator apply, FP64)",
+                "achieved": xp_flop / sec / 1e12, "peak": fp64_tflops,
+                "peak_kind": "measured FP64 FMA throughput (eb_fp64_peak, this run)", "unit": "TFLOP/s",
+                "frac": xp_flop / sec / 1e12 / fp64_tflops, "traffic": None,
+                "algorithmic_flop_per_launch": xp_flop, "algorithmic_bytes_per_launch": 41 * nc,
+                "hbm_frac": 41 * nc / sec / 1e9 / pk_hbm(), "avg_launch_us": sec * 1e6, "launches_timed": n,
+                "timing": PROF_NOTE + "; each bracketed launch carries the event pair's few microseconds"}
+
+    def hbm_roof(kernel, nbytes, ms, n):
+        sec = (ms / n) / 1000.0 if n else float("nan")
+        return {"bound": "hbm", "kernel": kernel, "achieved": nbytes / sec / 1e9, "peak": pk_hbm(),
+                "peak_kind": "measured HBM copy (burst)", "unit": "GB/s", "frac": nbytes / sec / 1e9 / pk_hbm(),
+                "traffic": None, "algorithmic_bytes_per_launch": nbytes, "avg_launch_us": sec * 1e6,
+                "launches_timed": n,
+                "timing": PROF_NOTE + "; each bracketed launch carries the event pair's few microseconds"}
+    if outer == eb.EB_DF64:
+        pcg_apply = hbm_roof(f"k_xpby_apply_df<{dim}, false, true> (p update + next operator apply, double-float)",
+                             37 * nc, xp_ms, xp_n)
+        pcg_update = hbm_roof(f"k_update_first_df<{dim}, float> (x/r update in double-float + first level-0 "
+                              "smoothing step)", 65 * nc, up_ms, up_n)
+        extra["fp64_outer"]["p_update_apply_roofline"] = fp64_apply_roof(xp64_ms, xp64_n)
+        extra["fp64_outer"]["xr_update_roofline"] = hbm_roof(
+            f"k_update_first<{dim}, float> (x/r update + first level-0 smoothing step, FP64)", 69 * nc,
+            up64_ms, up64_n)
+    else:
+        pcg_apply = fp64_apply_roof(xp_ms, xp_n)
+        up_bytes = (69 if dim == 3 else 81) * nc
+        pcg_update = hbm_roof(f"k_update_first<{dim}, {'float' if dim == 3 else 'double'}> "
+                              "(x/r update + first level-0 smoothing step)", up_bytes, up_ms, up_n)
     if 1 in alone:
         by_kernel = {"level0_smoother": stencil, "level1_smoother": level1, "pcg_p_update_apply": pcg_apply,
                      "pcg_xr_update": pcg_update}
         # the line's roofline is the kernel with the largest share of the solve
         roof = by_kernel[max(share, key=share.get)]
     line = {"value": value, "ms_per_step": ms_per_step,
-            "dtype": "f64 outer, f32 V-cycle" if dim == 3 else "f64",
+            "dtype": ("df64 outer (double-float: FP32 pairs, ~48-bit; exit test on the FP64 true residual), "
+                      "f32 V-cycle") if dim == 3 else "f64",
+            "true_rel_residual": sts[-1].true_rel_residual,
             "num_cp": nc, "iterations": sts[-1].iterations, "time_to_tol_ms": ms_per_step,
             "build_ms": build_ms, "setup_ms": setup_ms, "amg_levels": solver.rows, "max_err_vs_exact": err,
             "tile": tile, "autotune_us_per_vcycle": tune,

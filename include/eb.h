@@ -54,7 +54,10 @@ typedef enum {
   EB_ERR_NOT_IMPLEMENTED = 9
 } eb_status;
 
-typedef enum { EB_F64 = 0, EB_F32 = 1, EB_BF16 = 2 } eb_prec;
+/* EB_DF64 (pcg_opts.outer_prec only): double-float, a value held as the
+ * unevaluated sum of two FP32 numbers (about 48 significant bits) and computed
+ * with error-free FP32 transformations */
+typedef enum { EB_F64 = 0, EB_F32 = 1, EB_BF16 = 2, EB_DF64 = 3 } eb_prec;
 
 /* Uniform grid: n[a] nodes on axis a at lo[a] + i h, i = 0..n[a]-1 (Sec. 2).
  * dim is 2 or 3; for dim 2, n[2] must be 1.  n[0] must be a multiple of 2. */
@@ -350,6 +353,15 @@ typedef struct {
                             level-1 (first coarse level, CSR) Chebyshev-step launches; 4: the PCG's
                             p update + operator apply launches; 5: its x/r update launches (with an AMG
                             V-cycle, fused with the first level-0 smoothing step) */
+  int outer_prec;        /* arithmetic of the outer iteration's vectors x, r, p, q: EB_F64 (default) or
+                            EB_DF64 -- double-float pairs in the same 8 bytes per entry, updated on the FP32
+                            pipe (GB300 issues FP64 and float <-> double conversions at under 2 lanes per
+                            clock per SM, FP32 at about 116); z is then the V-cycle's FP32 output, the
+                            reductions are summed in DF and rounded to FP64 once per CTA, the scalars are
+                            FP64, and b and x cross to DF scaled by a power of two (the scaled b has a
+                            unit root mean square).  The exit test is the FP64 true residual, as for
+                            EB_F64.  EB_DF64 needs EB_PC_AMG with an FP32 or BF16 V-cycle of two or more
+                            levels and beta = 1 (EB_ERR_NOT_IMPLEMENTED otherwise) */
 } pcg_opts;
 
 typedef struct {

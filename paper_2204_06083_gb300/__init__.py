@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libeb.so")
 
 EB_OK, EB_ERR_INVALID, EB_ERR_GEOMETRY, EB_ERR_CUDA, EB_ERR_NONFINITE = 0, 1, 2, 3, 4
 EB_ERR_NO_CONVERGENCE, EB_ERR_BREAKDOWN, EB_ERR_TIMEOUT, EB_ERR_OOM, EB_ERR_NOT_IMPLEMENTED = 5, 6, 7, 8, 9
-EB_F64, EB_F32, EB_BF16 = 0, 1, 2
+EB_F64, EB_F32, EB_BF16, EB_DF64 = 0, 1, 2, 3
 EB_PC_AMG, EB_PC_JACOBI, EB_PC_NONE, EB_PC_AMG_NN = 0, 1, 2, 3
 EB_NN_PLAIN, EB_NN_ENERGY = 0, 1
 EB_TUNE_APPLY, EB_TUNE_LEAPFROG = 0, 1
@@ -89,7 +89,8 @@ class amg_info_t(C.Structure):
 
 
 class pcg_opts(C.Structure):
-    _fields_ = [("precond", C.c_int), ("check_every", C.c_int), ("use_graph", C.c_int), ("profile", C.c_int)]
+    _fields_ = [("precond", C.c_int), ("check_every", C.c_int), ("use_graph", C.c_int), ("profile", C.c_int),
+                ("outer_prec", C.c_int)]
 
 
 class pcg_stats(C.Structure):
@@ -499,12 +500,13 @@ class AMG:
         return out
 
     def solve(self, b, x=None, rtol=1e-10, maxit=1000, precond=None, check_every=1, use_graph=1,
-              stream=None, allow_noconv=False, profile=False):
+              stream=None, allow_noconv=False, profile=False, outer=EB_F64):
+        """pcg_solve; outer = EB_DF64 keeps the outer iteration in double-float."""
         import torch
         if x is None:
             x = torch.zeros_like(b)
         o = pcg_opts(EB_PC_AMG if (precond is None and self.num_levels > 0) else
-                     (EB_PC_JACOBI if precond is None else precond), check_every, use_graph, int(profile))
+                     (EB_PC_JACOBI if precond is None else precond), check_every, use_graph, int(profile), int(outer))
         st = pcg_stats()
         _check(load().pcg_solve(self._h, _ptr(b), _ptr(x), float(rtol), int(maxit), C.byref(o), C.byref(st),
                                 _stream(stream)), allow=(EB_ERR_NO_CONVERGENCE,) if allow_noconv else ())

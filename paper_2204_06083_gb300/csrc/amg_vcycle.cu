@@ -14,6 +14,7 @@
 // values of A_l, P_l, R_l and D_l^-1 in bfloat16, every sum in FP32; the
 // level-0 diagonal stays FP32.
 #include "amg_internal.cuh"
+#include "df.cuh"
 #include "stencil.cuh"
 
 #include <algorithm>
@@ -102,8 +103,9 @@ inline TileView tiles_only(TileView tv) {
 }
 
 // level 0 ----------------------------------------------------------------
-// b_out = (V) r; x = d = D^-1 b / theta
-template <int DIM, class V>
+// b_out = (V) r; x = d = D^-1 b / theta.  RDF: r is a double-float vector
+// (the DF outer iteration), of which the V-cycle takes the FP32 high part.
+template <int DIM, class V, bool RDF = false>
 __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_first(TileView tv, const uint8_t* __restrict__ code,
                                                              const typename DiagOf<V>::type* __restrict__ diag,
                                                              GOp<typename AccOf<V>::type> o,
@@ -115,8 +117,18 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_first(TileView tv, const 
     const GOp<A> ot = sweep_op<DIM>(tv, tt_, o);
     uint32_t c0, c1;
     ld_codes(code, node, c0, c1);
-    const Two<double> rv = LdRO::ld2(r + node);
-    const A b0 = (c0 & CODE_CP) ? (A)rv.x : (A)0, b1 = (c1 & CODE_CP) ? (A)rv.y : (A)0;
+    A r0, r1;
+    if constexpr (RDF) {
+      DF a, b;
+      df_ld2(r, node, a, b);
+      r0 = (A)a.hi;
+      r1 = (A)b.hi;
+    } else {
+      const Two<double> rv = LdRO::ld2(r + node);
+      r0 = (A)rv.x;
+      r1 = (A)rv.y;
+    }
+    const A b0 = (c0 & CODE_CP) ? r0 : (A)0, b1 = (c1 & CODE_CP) ? r1 : (A)0;
     if (b_out) st2o(b_out + node, b0, b1);
     const A v0 = (c0 & CODE_CP) ? inv_diag_t<A>(c0, diag, node, ot) * b0 / theta : (A)0;
     const A v1 = (c1 & CODE_CP) ? inv_diag_t<A>(c1, diag, node + 1, ot) * b1 / theta : (A)0;
@@ -176,10 +188,78 @@ __global__ void __launch_bounds__(TILE_NODES) k_update_first(PairList pl, PcgUpd
   if (threadIdx.x == 0) u.rr_part[blockIdx.x] = t;
 }
 
+// k_update_first for the DF outer iteration: x, r, p, q are double-float
+// vectors (DF pairs in the buffers of doubles), z the FP32 output of the
+// V-cycle, the reduction partials DF.  x += (alpha h2) p, r -= alpha q in DF,
+// the r'r and r'zold partials summed in DF; the V-cycle's first step then
+// takes the FP32 high part of the new r (x = d = D^-1 b (1 / theta)).
+template <int DIM, class V>
+__global__ void __launch_bounds__(TILE_NODES) k_update_first_df(PairList pl, PcgUpdate u, const uint8_t* __restrict__ code,
+                                                                const typename DiagOf<V>::type* __restrict__ diag,
+                                                                GOp<float> o, V* __restrict__ b_out,
+                                                                V* __restrict__ x0, V* __restrict__ d,
+                                                                float inv_theta) {
+  __shared__ DF dsm[32];
+  __shared__ DF s_a[2];
+  if (cta_done(u.sc)) {
+    if (threadIdx.x == 0) {
+      df_part_store(u.rr_part, blockIdx.x, DF{0.0f, 0.0f});
+      if (u.rzo_part) df_part_store(u.rzo_part, blockIdx.x, DF{0.0f, 0.0f});
+    }
+    return;
+  }
+  // alpha from the DF p'q partials (FP64 scalars), split into DF once per CTA
+  const double pq = df_sum_parts(u.pq_part, u.nblk, dsm);
+  if (threadIdx.x == 0) {
+    const double alpha = pcg_alpha_from(u.sc, pq);
+    s_a[0] = df_from_double(alpha);
+    s_a[1] = df_from_double(alpha * u.h2);
+  }
+  __syncthreads();
+  const DF a_df = s_a[0], ax_df = s_a[1];
+  const float* zf = reinterpret_cast<const float*>(u.z);
+  DF srr{0.0f, 0.0f}, srzo{0.0f, 0.0f};
+  EB_LIST_LOOP(pl, node) {
+    DF r0, r1, q0, q1, p0, p1, xa, xb;
+    df_ld2_rw(u.r, node, r0, r1);
+    df_ld2(u.q, node, q0, q1);
+    df_ld2(u.p, node, p0, p1);
+    df_ld2_rw(u.x, node, xa, xb);
+    // the residual update cancels by design: the accurate DF sum
+    r0 = df_sub(r0, df_mul(a_df, q0));
+    r1 = df_sub(r1, df_mul(a_df, q1));
+    df_st2(u.x, node, df_add_fast(xa, df_mul(ax_df, p0)), df_add_fast(xb, df_mul(ax_df, p1)));
+    df_st2(u.r, node, r0, r1);
+    df_acc_prod(srr, r0, r0);
+    df_acc_prod(srr, r1, r1);
+    if (u.rzo_part) {
+      const float2 zv = __ldg(reinterpret_cast<const float2*>(zf + node));
+      df_acc_prod_f(srzo, r0, zv.x);
+      df_acc_prod_f(srzo, r1, zv.y);
+    }
+    uint32_t c0, c1;
+    ld_codes(code, node, c0, c1);
+    const float b0 = (c0 & CODE_CP) ? r0.hi : 0.0f, b1 = (c1 & CODE_CP) ? r1.hi : 0.0f;
+    if (b_out) st2o(b_out + node, b0, b1);
+    const float v0 = (c0 & CODE_CP) ? inv_diag_t<float>(c0, diag, node, o) * b0 * inv_theta : 0.0f;
+    const float v1 = (c1 & CODE_CP) ? inv_diag_t<float>(c1, diag, node + 1, o) * b1 * inv_theta : 0.0f;
+    st2o(x0 + node, v0, v1);
+    st2o(d + node, v0, v1);
+  }
+  if (u.rzo_part) {
+    const DF t = df_block_sum_df(srzo, dsm);
+    if (threadIdx.x == 0) df_part_store(u.rzo_part, blockIdx.x, t);
+  }
+  const DF t = df_block_sum_df(srr, dsm);
+  if (threadIdx.x == 0) df_part_store(u.rr_part, blockIdx.x, t);
+}
+
 // res = D^-1 (b - A x); d = c1 d + c2 res; xo = x + d   (xo may be FP64).
-// DOT (xo FP64, the V-cycle's output z): also the CTA's partial r.z, summed
-// over its node pairs in loop order exactly as the PCG's own dot kernel does.
-template <int DIM, class V, class O, bool DOT = false>
+// DOT = 1 (xo FP64, the V-cycle's output z): also the CTA's partial r.z,
+// summed over its node pairs in loop order exactly as the PCG's own dot kernel
+// does; DOT = 2 (xo FP32, r a double-float vector): the same partial summed
+// and stored in DF.
+template <int DIM, class V, class O, int DOT = 0>
 __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_step(TileView tv, const uint8_t* __restrict__ code,
                                                             const typename DiagOf<V>::type* __restrict__ diag,
                                                             GOp<typename AccOf<V>::type> o,
@@ -190,6 +270,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_step(TileView tv, const u
                                                             double* __restrict__ part = nullptr) {
   using A = typename AccOf<V>::type;
   double srz = 0.0;
+  DF srz_df{0.0f, 0.0f};
   EB_SWEEP(DIM, tv, node) {
     const GOp<A> ot = sweep_op<DIM>(tv, tt_, o);
     uint32_t k0, k1;
@@ -209,15 +290,24 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_step(TileView tv, const u
     st2o(d + node, d0, d1);
     const A z0 = (k0 & CODE_CP) ? xc.x + d0 : (A)0, z1 = (k1 & CODE_CP) ? xc.y + d1 : (A)0;
     st2(xo + node, z0, z1);
-    if (DOT) {
+    if constexpr (DOT == 1) {
       const Two<double> rv = LdRO::ld2(r64 + node);
       srz += rv.x * (double)z0 + rv.y * (double)z1;
+    } else if constexpr (DOT == 2) {
+      DF ra, rb;
+      df_ld2(r64, node, ra, rb);
+      df_acc_prod_f(srz_df, ra, (float)z0);
+      df_acc_prod_f(srz_df, rb, (float)z1);
     }
   }
-  if (DOT) {
+  if constexpr (DOT == 1) {
     __shared__ double sm[32];
     const double a = block_sum(srz, sm);
     if (threadIdx.x == 0) part[blockIdx.x] = a;
+  } else if constexpr (DOT == 2) {
+    __shared__ DF dsm[32];
+    const DF a = df_block_sum_df(srz_df, dsm);
+    if (threadIdx.x == 0) df_part_store(part, blockIdx.x, a);
   }
 }
 
@@ -654,8 +744,11 @@ static int vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, co
   const V* b = std::is_same<V, double>::value ? reinterpret_cast<const V*>(r) : g.b;
   V* x = g.x;
   V* x2 = g.x2;
+  const bool rdf = dot && dot->df;
   if (first_done)
     S.nlaunch -= 1;  // amg_update_first did it
+  else if (rdf)
+    k_g_cheb_first<DIM, V, true><<<gl, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, r, bcopy, x, g.d, (A)cc.theta);
   else
     k_g_cheb_first<DIM, V><<<gl, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, r, bcopy, x, g.d, (A)cc.theta);
   for (int k = 1; k < cc.deg; ++k) {
@@ -687,9 +780,13 @@ static int vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, co
     // part of the smoother-step timing
     const bool mark = !(k == cc.deg - 1 && dot);
     if (mark) S.prof_mark(s, true);
-    if (k == cc.deg - 1 && dot)
-      k_g_cheb_step<DIM, V, double, true><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, x, z, g.d, (A)cc.c1[k],
-                                                                    (A)cc.c2[k], dot->r, dot->part);
+    if (k == cc.deg - 1 && rdf)  // z in FP32 for the DF outer iteration
+      k_g_cheb_step<DIM, V, float, 2><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, x,
+                                                                reinterpret_cast<float*>(z), g.d, (A)cc.c1[k],
+                                                                (A)cc.c2[k], dot->r, dot->part);
+    else if (k == cc.deg - 1 && dot)
+      k_g_cheb_step<DIM, V, double, 1><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, x, z, g.d, (A)cc.c1[k],
+                                                                 (A)cc.c2[k], dot->r, dot->part);
     else if (k == cc.deg - 1)  // z for a caller (amg_vcycle): every node of the active tiles, 0 off the CPs
       k_g_cheb_step<(DIM & ~DIM_LIST), V, double>
           <<<gb, TILE_NODES, 0, s>>>(tiles_only(tv), eb.code, diag, o, b, x, z, g.d, (A)cc.c1[k], (A)cc.c2[k]);
@@ -734,9 +831,18 @@ static void update_first(Solver& S, const PcgUpdate& u, cudaStream_t s) {
   const GOp<A> o{(A)inv_h2, (A)S.shift, (A)(1.0 / (S.shift + 2.0 * G.dim * inv_h2))};
   VecSet<V>& g = LV::grid(H);
   V* bcopy = std::is_same<V, double>::value ? nullptr : g.b;
+  if constexpr (!std::is_same<V, double>::value) {
+    if (u.df) {
+      k_update_first_df<DIM, V><<<(unsigned)u.nblk, TILE_NODES, 0, s>>>(eb.pairs(), u, eb.code, diag_of<V>(eb), o,
+                                                                        bcopy, g.x, g.d, (float)(1.0 / cc.theta));
+      return;
+    }
+  }
   k_update_first<DIM, V><<<(unsigned)u.nblk, TILE_NODES, 0, s>>>(eb.pairs(), u, eb.code, diag_of<V>(eb), o, bcopy,
                                                                  g.x, g.d, (A)cc.theta);
 }
+
+int amg_levels(const Solver& S) { return S.H ? (int)S.H->L.size() : 0; }
 
 int amg_update_first(Solver& S, const PcgUpdate& u, cudaStream_t s) {
   if (!S.H || S.H->L.size() == 1) return 0;  // a single level has no smoothing step

@@ -13,6 +13,7 @@
 // p with beta) reduces them itself and CTA 0 records the scalars and, in the
 // device-side loop, runs the convergence test -- or by one CTA (k_finalize).
 // No scalar crosses to the host except at the end of the loop.
+#include "df.cuh"
 #include "eb_solver.cuh"
 #include "stencil.cuh"
 
@@ -242,6 +243,183 @@ __global__ void __launch_bounds__(TILE_NODES) k_xpby_apply(TileView tv, PairList
   if (threadIdx.x == 0) pq_part[blockIdx.x] = t;
 }
 
+// ------------------------------------------------- the DF outer iteration
+// The same iteration with x, r, p, q as double-float vectors (double-float
+// pairs in the buffers of doubles) and z in FP32 (the V-cycle's output, exact
+// in DF).  The reduction partials are DF too (one per CTA in the 8 bytes of a
+// slot), summed in DF by every CTA that needs them -- on the FP32 pipe, where
+// the FP64 path's redundant per-CTA sums cost FP64 issue slots -- and rounded
+// to FP64 once; alpha and beta are FP64 ratios, split into DF once per CTA.
+
+// The end of an iteration (k_xpby_apply in DF): p = z + beta p, q = B z + beta
+// q, the p.q partials.  B z is the unit stencil D_k z_k - sum of the
+// CP-neighbour values on the FP32 z: the neighbours by cascaded summation
+// (TwoSum errors collected), D_k z_k an exact product (interior points) or a
+// DF one (cut points), plus sigma h^2 z_k when SHIFT.  beta = 1 only (no
+// variable coefficient).
+template <int DIM, bool SHIFT, bool COND>
+__global__ void __launch_bounds__(TILE_NODES) k_xpby_apply_df(TileView tv, PairList pl, PcgScalars* sc,
+                                                              const uint8_t* code, const float2* diag_df, DF sig_h2,
+                                                              const float* z, double* p, double* q, int first,
+                                                              const double* rz_part, int nrz, const double* rzo_part,
+                                                              int nupd, double* pq_part, const double* rr_part,
+                                                              cudaGraphConditionalHandle h) {
+  __shared__ DF dsm[32];
+  __shared__ DF s_beta;
+  if (cta_done(sc)) {
+    if (COND && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+    return;
+  }
+  if (threadIdx.x == 0) s_beta = DF{0.0f, 0.0f};
+  if (!first) {
+    const double v = df_sum_parts(rz_part, nrz, dsm);
+    __syncthreads();
+    const double t = rzo_part ? df_sum_parts(rzo_part, nupd, dsm) : 0.0;
+    if (threadIdx.x == 0) {
+      const int k = sc->slot;
+      const bool ok = v > 0.0;
+      const double beta = ok ? (v - t) / sc->rz[k] : 0.0;
+      s_beta = df_from_double(beta);
+      if (blockIdx.x == 0) {
+        sc->beta = beta;
+        sc->rz[k ^ 1] = v;
+        if (!ok) {
+          sc->flags |= isfinite(v) ? PCG_FLAG_BREAKDOWN : PCG_FLAG_NONFINITE;
+          sc->done = 1;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const DF beta = s_beta;
+  if (COND && blockIdx.x == 0) {
+    const double v = df_sum_parts(rr_part, nupd, dsm);
+    if (threadIdx.x == 0) {
+      if (!sc->done) {
+        sc->rr = v;
+        sc->iters += 1;
+        if (!isfinite(v)) {
+          sc->flags |= PCG_FLAG_NONFINITE;
+          sc->done = 1;
+        } else if (v <= sc->tol2 * sc->bb) {
+          sc->done = 1;
+        }
+      }
+      cudaGraphSetConditional(h, (!sc->done && sc->iters < sc->maxit) ? 1u : 0u);
+    }
+  }
+  const int32_t nn = tv.nn, sy = tv.sy, sz = tv.sz;
+  DF s{0.0f, 0.0f};
+  EB_LIST_LOOP(pl, node) {
+    uint32_t c0, c1;
+    ld_codes(code, node, c0, c1);
+    const float2 zc = __ldg(reinterpret_cast<const float2*>(z + node));
+    const float left = node > 0 ? __ldg(z + node - 1) : 0.0f;
+    const float right = node + 2 < nn ? __ldg(z + node + 2) : 0.0f;
+    const float2 zero{0.0f, 0.0f};
+    const float2 dn = node >= sy ? __ldg(reinterpret_cast<const float2*>(z + node - sy)) : zero;
+    const float2 up = node + sy < nn ? __ldg(reinterpret_cast<const float2*>(z + node + sy)) : zero;
+    float2 bk = zero, fr = zero;
+    if (DIM == 3) {
+      bk = node >= sz ? __ldg(reinterpret_cast<const float2*>(z + node - sz)) : zero;
+      fr = node + sz < nn ? __ldg(reinterpret_cast<const float2*>(z + node + sz)) : zero;
+    }
+    // the neighbour sums by cascaded summation, then D_k z_k (an exact
+    // product: D_k = 2 dim at interior points, DF for cut ones) minus them
+    Sum2 s0 = sum2_start((c0 & 1) ? 0.0f : left), s1 = sum2_start((c1 & 1) ? 0.0f : zc.x);
+    sum2_add(s0, (c0 & 2) ? 0.0f : zc.y);
+    sum2_add(s1, (c1 & 2) ? 0.0f : right);
+    sum2_add(s0, (c0 & 4) ? 0.0f : dn.x);
+    sum2_add(s1, (c1 & 4) ? 0.0f : dn.y);
+    sum2_add(s0, (c0 & 8) ? 0.0f : up.x);
+    sum2_add(s1, (c1 & 8) ? 0.0f : up.y);
+    if (DIM == 3) {
+      sum2_add(s0, (c0 & 16) ? 0.0f : bk.x);
+      sum2_add(s1, (c1 & 16) ? 0.0f : bk.y);
+      sum2_add(s0, (c0 & 32) ? 0.0f : fr.x);
+      sum2_add(s1, (c1 & 32) ? 0.0f : fr.y);
+    }
+    float d0h = (float)(2 * DIM), d0l = 0.0f, d1h = d0h, d1l = 0.0f;
+    if (c0 & 0x7F) {
+      const float2 t = __ldg(diag_df + node);
+      d0h = t.x;
+      d0l = t.y;
+    }
+    if (c1 & 0x7F) {
+      const float2 t = __ldg(diag_df + node + 1);
+      d1h = t.x;
+      d1l = t.y;
+    }
+    float pr0, pe0, pr1, pe1;
+    two_prod(d0h, zc.x, pr0, pe0);
+    two_prod(d1h, zc.y, pr1, pe1);
+    pe0 = __fmaf_rn(d0l, zc.x, pe0);
+    pe1 = __fmaf_rn(d1l, zc.y, pe1);
+    DF a0 = df_prod_minus_sum2(pr0, pe0, s0), a1 = df_prod_minus_sum2(pr1, pe1, s1);
+    if (SHIFT) {
+      a0 = df_add(a0, df_mul_f(sig_h2, zc.x));
+      a1 = df_add(a1, df_mul_f(sig_h2, zc.y));
+    }
+    DF p0 = df_make(zc.x), p1 = df_make(zc.y), q0 = a0, q1 = a1;
+    if (!first) {
+      DF po0, po1, qo0, qo1;
+      df_ld2_rw(p, node, po0, po1);
+      df_ld2_rw(q, node, qo0, qo1);
+      p0 = df_add_f(df_mul(beta, po0), zc.x);
+      p1 = df_add_f(df_mul(beta, po1), zc.y);
+      q0 = df_add_fast(df_mul(beta, qo0), a0);
+      q1 = df_add_fast(df_mul(beta, qo1), a1);
+    }
+    if (!(c0 & CODE_CP)) q0 = DF{0.0f, 0.0f};
+    if (!(c1 & CODE_CP)) q1 = DF{0.0f, 0.0f};
+    df_st2(p, node, p0, p1);
+    df_st2(q, node, q0, q1);
+    df_acc_prod(s, p0, q0);
+    df_acc_prod(s, p1, q1);
+  }
+  const DF t = df_block_sum_df(s, dsm);
+  if (threadIdx.x == 0) df_part_store(pq_part, blockIdx.x, t);
+}
+
+// Into DF: xd = scale x and, in place, r = scale r (FP64 -> DF), over the CP
+// pairs; scale is a power of two (exact), chosen so that the scaled right-hand
+// side has a unit root mean square, well inside FP32's exponent range.
+__global__ void __launch_bounds__(TILE_NODES) k_df_in(PairList pl, const double* x, double* xd, double* r,
+                                                      double scale) {
+  EB_LIST_LOOP(pl, node) {
+    const Two<double> xv = ld2d(x + node), rv = ld2d(r + node);
+    df_st2(xd, node, df_from_double(xv.x * scale), df_from_double(xv.y * scale));
+    df_st2(r, node, df_from_double(rv.x * scale), df_from_double(rv.y * scale));
+  }
+}
+
+// Out of DF: x = xd / scale over the CP pairs
+__global__ void __launch_bounds__(TILE_NODES) k_df_out(PairList pl, const double* xd, double* x, double inv_scale) {
+  EB_LIST_LOOP(pl, node) {
+    DF a, b;
+    df_ld2_rw(xd, node, a, b);
+    st2(x + node, df_to_double(a) * inv_scale, df_to_double(b) * inv_scale);
+  }
+}
+
+// the DF copy of the cut CPs' diagonals D_k (the interior value 2 dim is
+// formed in the kernel)
+__global__ void __launch_bounds__(TILE_NODES) k_df_diag(PairList pl, const uint8_t* code, const double* diag,
+                                                        float2* out) {
+  EB_LIST_LOOP(pl, node) {
+    uint32_t c0, c1;
+    ld_codes(code, node, c0, c1);
+    if (c0 & 0x7F) {
+      const DF v = df_from_double(diag[node]);
+      out[node] = make_float2(v.hi, v.lo);
+    }
+    if (c1 & 0x7F) {
+      const DF v = df_from_double(diag[node + 1]);
+      out[node + 1] = make_float2(v.hi, v.lo);
+    }
+  }
+}
+
 // Right-hand side and guess of one implicit theta-scheme wave step (Sec. 3.5,
 // theta > 0): (sigma I + A) u^{n+1} = sigma (2 u^n - u^{n-1}) - c A u^n -
 // A u^{n-1}, sigma = 1 / (theta dt^2), c = (1 - 2 theta) / theta (the scheme
@@ -315,14 +493,22 @@ __global__ void __launch_bounds__(TILE_NODES) k_mask_copy(TileView tv, const uin
 }
 
 // Combine partials in a fixed order and advance the scalar recurrences.
-__global__ void k_finalize(const double* part, int nblk, int op, PcgScalars* sc) {
+// df: the partials are DF (the DF outer iteration; never FIN_INIT), each
+// thread's share summed in DF and rounded once
+__global__ void k_finalize(const double* part, int nblk, int op, PcgScalars* sc, int df) {
   __shared__ double sm[2][1024];
   double a = 0.0, b = 0.0;
   const bool pairs = op == FIN_INIT;
   const int stride = pairs ? 2 : 1;
-  for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
-    a += part[stride * i];
-    if (pairs) b += part[2 * i + 1];
+  if (df) {
+    DF t{0.0f, 0.0f};
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) t = df_add(t, df_part_load(part, i));
+    a = df_to_double(t);
+  } else {
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+      a += part[stride * i];
+      if (pairs) b += part[2 * i + 1];
+    }
   }
   sm[0][threadIdx.x] = a;
   sm[1][threadIdx.x] = b;
@@ -412,13 +598,14 @@ void Solver::free_work() {
   if (cap_stream) cudaStreamDestroy(cap_stream);
   cap_stream = nullptr;
   dfree(r, s); dfree(z, s); dfree(p, s); dfree(q, s); dfree(tmp, s); dfree(part, s); dfree(sc, s); dfree(wx, s);
+  dfree(diag_df, s);
   if (sc_host) cudaFreeHost(sc_host);
   sc_host = nullptr;
 }
 
 void Solver::finalize(int op, const double* src, cudaStream_t s, int count) {
   ++nlaunch;
-  k_finalize<<<1, 1024, 0, s>>>(src, count < 0 ? nblk : count, op, sc);
+  k_finalize<<<1, 1024, 0, s>>>(src, count < 0 ? nblk : count, op, sc, (df_on && op != FIN_INIT) ? 1 : 0);
 }
 
 void Solver::precondition(int kind, const double* rin, double* zout, cudaStream_t s, bool first_done) {
@@ -434,6 +621,7 @@ void Solver::precondition(int kind, const double* rin, double* zout, cudaStream_
     VcycleDot dot;
     dot.r = rin;
     dot.part = part_rz();
+    dot.df = df_on;
     const int fused = amg_vcycle_grid(*this, rin, zout, s, &dot, first_done);
     if (fused) {
       rz_n = fused;
@@ -464,6 +652,23 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
   EB_REQUIRE(b != x, EB_ERR_INVALID, "pcg: b and x must be different buffers");
   EB_REQUIRE(eb->pair_node != nullptr || eb->num_cp == 0, EB_ERR_INVALID, "pcg: the handle has no CP pair list");
   const int check = std::max(1, o.check_every);
+  EB_REQUIRE(o.outer_prec == EB_F64 || o.outer_prec == EB_DF64, EB_ERR_INVALID,
+             "pcg: outer_prec must be EB_F64 or EB_DF64");
+  df_on = o.outer_prec == EB_DF64;
+  if (df_on) {
+    EB_REQUIRE(kind == EB_PC_AMG && flexible() && amg_levels(*this) > 1, EB_ERR_NOT_IMPLEMENTED,
+               "pcg: the DF outer iteration needs the AMG preconditioner with an FP32 or BF16 V-cycle of at least "
+               "two levels");
+    EB_REQUIRE(!eb->has_beta(), EB_ERR_NOT_IMPLEMENTED,
+               "pcg: the DF outer iteration has no variable-coefficient stencil");
+    if (!diag_df) {
+      diag_df = dalloc<float2>(eb->g.num_nodes, s);
+      ++nlaunch;
+      k_df_diag<<<nblk, TILE_NODES, 0, s>>>(eb->pairs(), eb->code, eb->diag, diag_df);
+    }
+  }
+  // the vector the iteration updates: x itself, or its DF image in tmp
+  double* xi = df_on ? tmp : x;
   prof_begin(o.profile, s);
   nlaunch = 0;
   auto t0 = std::chrono::steady_clock::now();
@@ -499,6 +704,17 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
       break;
     }
     if (total_iters >= maxit) break;
+    double scale = 1.0;
+    if (df_on) {
+      // scale by a power of two so that the scaled b has a unit root mean square
+      const double ms = sc_host->bb / (double)std::max<int64_t>(eb->num_cp, 1);
+      scale = std::ldexp(1.0, -(int)std::lround(0.5 * std::log2(ms)));
+      ++nlaunch;
+      k_df_in<<<nblk, TILE_NODES, 0, s>>>(eb->pairs(), x, xi, r, scale);
+      sc_host->bb *= scale * scale;
+      sc_host->rr *= scale * scale;
+      EB_CUDA(cudaMemcpyAsync(sc, sc_host, sizeof(PcgScalars), cudaMemcpyHostToDevice, s));
+    }
     precondition(kind, r, z, s);
     const bool flex = flex_for(kind);
     finalize(FIN_RZ0, part_rz(), s, rz_n);
@@ -506,7 +722,7 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
     int it = 0;
     bool stop = false;
     if (o.use_graph == 1 && !prof_on) {  // the whole loop on the device
-      loop_prepare(kind, b, x, s);
+      loop_prepare(kind, b, xi, s);
       EB_CUDA(cudaGraphLaunch(lexec, s));
       EB_CUDA(cudaMemcpyAsync(sc_host, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
       EB_CUDA(cudaStreamSynchronize(s));
@@ -517,13 +733,13 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
       const int nb = std::min(check, maxit - (total_iters + it));
       bool graphed = false;
       if (o.use_graph && nb == check) {
-        graph_prepare(kind, b, x, check, prof_on ? prof_what : 0, s);
+        graph_prepare(kind, b, xi, check, prof_on ? prof_what : 0, s);
         EB_CUDA(cudaGraphLaunch(gexec, s));
         nlaunch += g_launches;
         graphed = true;
         it += nb;
       } else {
-        for (int j = 0; j < nb; ++j, ++it) iteration(kind, b, x, s);
+        for (int j = 0; j < nb; ++j, ++it) iteration(kind, b, xi, s);
       }
       EB_CUDA(cudaGetLastError());
       EB_CUDA(cudaMemcpyAsync(sc_host, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
@@ -537,8 +753,12 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
     }
     total_iters += sc_host->iters;
     flags |= sc_host->flags;
+    if (df_on) {
+      ++nlaunch;
+      k_df_out<<<nblk, TILE_NODES, 0, s>>>(eb->pairs(), xi, x, 1.0 / scale);
+    }
     if (flags & (PCG_FLAG_NONFINITE | PCG_FLAG_BREAKDOWN)) break;
-    // true residual at exit
+    // true residual at exit (FP64)
     EB_DIMV_LAUNCH(*eb, k_resid, nblk, tv, eb->code, eb->diag, op, b, x, r, part_pq());
     finalize(FIN_INIT, part_pq(), s);
     EB_CUDA(cudaMemcpyAsync(sc_host, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
@@ -646,15 +866,26 @@ void Solver::xpby_apply(const OpParams& op, bool flex, int first, cudaStream_t s
                         const cudaGraphConditionalHandle* cond) {
   const TileView tv = eb->tv();
   const PairList pl = eb->pairs();
-  const unsigned g = (unsigned)nblk;
+  const unsigned g = (unsigned)nblk_iter();
   const int dim = eb->g.dim;
   const double* rzo = flex ? part_rzo() : nullptr;
   const cudaGraphConditionalHandle h = cond ? *cond : cudaGraphConditionalHandle{};
   ++nlaunch;
   auto go = [&](auto shift, auto with_cond) {
-    launch_xpby_apply<decltype(shift)::value, decltype(with_cond)::value>(
-        *eb, g, s, tv, pl, sc, eb->code, eb->diag, op, z, p, q, first, part_rz(), rz_n, rzo, nblk, part_pq(),
-        part_rr(), h);
+    constexpr bool SH = decltype(shift)::value, CO = decltype(with_cond)::value;
+    if (df_on) {
+      const DF sig = df_from_double(op.sigma_h2);
+      const float* zf = reinterpret_cast<const float*>(z);
+      if (dim == 2)
+        k_xpby_apply_df<2, SH, CO><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, eb->code, diag_df, sig, zf, p, q, first,
+                                                            part_rz(), rz_n, rzo, (int)g, part_pq(), part_rr(), h);
+      else
+        k_xpby_apply_df<3, SH, CO><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, eb->code, diag_df, sig, zf, p, q, first,
+                                                            part_rz(), rz_n, rzo, (int)g, part_pq(), part_rr(), h);
+      return;
+    }
+    launch_xpby_apply<SH, CO>(*eb, g, s, tv, pl, sc, eb->code, eb->diag, op, z, p, q, first, part_rz(), rz_n, rzo,
+                              nblk, part_pq(), part_rr(), h);
   };
   using T = std::true_type;
   using F = std::false_type;
@@ -686,14 +917,16 @@ void Solver::iteration(int kind, const double* b, double* x, cudaStream_t s,
     u.p = p;
     u.q = q;
     u.pq_part = part_pq();
-    u.nblk = nblk;
+    u.nblk = nblk_iter();
     u.rr_part = part_rr();
     u.h2 = eb->g.h * eb->g.h;
     u.z = z;
     u.rzo_part = flex ? part_rzo() : nullptr;
+    u.df = df_on;
     fused = amg_update_first(*this, u, s) != 0;
     if (fused) ++nlaunch;
   }
+  EB_REQUIRE(fused || !df_on, EB_ERR_INVALID, "pcg: the DF outer iteration needs the fused x/r update");
   if (!fused)
     EB_DIM_LAUNCH(dim, k_update_xr, nblk, eb->pairs(), sc, x, r, p, q, part_pq(), nblk, part_rr(), eb->g.h * eb->g.h, z,
                   flex ? part_rzo() : nullptr);
@@ -704,7 +937,7 @@ void Solver::iteration(int kind, const double* b, double* x, cudaStream_t s,
   prof_mark(s, true, PROF_XPBY);
   xpby_apply(op, flex, 0, s, cond);
   prof_mark(s, false, PROF_XPBY);
-  if (!cond) finalize(FIN_RR, part_rr(), s);
+  if (!cond) finalize(FIN_RR, part_rr(), s, nblk_iter());
 }
 
 // Captures `iters` iterations into a CUDA graph (once per argument set).  The
@@ -712,7 +945,7 @@ void Solver::iteration(int kind, const double* b, double* x, cudaStream_t s,
 // default stream.
 void Solver::graph_prepare(int kind, const double* b, double* x, int iters, int profile, cudaStream_t s) {
   if (gexec && g_b == b && g_x == x && g_iters == iters && g_kind == kind && g_prof == profile && g_nn == nn &&
-      g_nn_mode == nn_mode && g_tile_gen == eb->tile_gen)
+      g_nn_mode == nn_mode && g_tile_gen == eb->tile_gen && g_df == (int)df_on)
     return;
   if (prof_on) {  // settle event pairs recorded so far before the capture reuses them
     EB_CUDA(cudaStreamSynchronize(s));
@@ -746,6 +979,7 @@ void Solver::graph_prepare(int kind, const double* b, double* x, int iters, int 
   g_nn = nn;
   g_nn_mode = nn_mode;
   g_tile_gen = eb->tile_gen;
+  g_df = (int)df_on;
 }
 
 void Solver::graph_release() {
@@ -794,7 +1028,7 @@ cudaGraphExec_t build_while_graph(cudaStream_t cap,
 // (once per argument set).
 void Solver::loop_prepare(int kind, const double* b, double* x, cudaStream_t s) {
   if (lexec && l_b == b && l_x == x && l_kind == kind && l_nn == nn && l_nn_mode == nn_mode &&
-      l_tile_gen == eb->tile_gen)
+      l_tile_gen == eb->tile_gen && l_df == (int)df_on)
     return;
   loop_release();
   (void)s;  // capturing runs nothing; the graph is launched on s
@@ -810,6 +1044,7 @@ void Solver::loop_prepare(int kind, const double* b, double* x, cudaStream_t s) 
   l_nn = nn;
   l_nn_mode = nn_mode;
   l_tile_gen = eb->tile_gen;
+  l_df = (int)df_on;
 }
 
 void Solver::loop_release() {

@@ -58,13 +58,16 @@ struct Solver {
   int nn_mode = 0;          // eb_nn_mode of that stage
   // reduction partials: [p'q | r'r] regions of 2 nblk each, then the r'z region
   // of 2 max(nblk, 8 SMs): r'z comes from the PCG's own dot kernel (nblk
-  // partials) or from the V-cycle's last smoothing launch (one per CTA of it)
+  // partials) or from the V-cycle's last smoothing launch (one per CTA of it),
+  // then the r'zold region of nblk
   double* part = nullptr;
   double* part_pq() const { return part; }
   double* part_rr() const { return part + 2 * (int64_t)nblk; }
   double* part_rz() const { return part + 4 * (int64_t)nblk; }
   // r'zold partials of the flexible beta (nblk, from the x/r update)
   double* part_rzo() const { return part + 4 * (int64_t)nblk + rz_cap; }
+  // CTAs (= partials) of the iteration's x/r update and p update + apply
+  int nblk_iter() const { return nblk; }
   int64_t rz_cap = 0;
   int nblk = 1;
   int rz_n = 1;  // r'z partials written by the last precondition()
@@ -96,6 +99,12 @@ struct Solver {
   int l_kind = -1, l_nn_mode = -1, l_tile_gen = -1;
   const nn_handle* l_nn = nullptr;
   int64_t l_launches = 0;  // kernel launches per loop iteration
+  // the DF outer iteration (pcg_opts.outer_prec = EB_DF64) for the current
+  // solve: x, r, p, q hold double-float pairs (x in tmp), z FP32; diag_df is
+  // the DF copy of the cut CPs' D_k (built on first use)
+  bool df_on = false;
+  float2* diag_df = nullptr;
+  int g_df = -1, l_df = -1;
 
   void alloc_work(cudaStream_t s);
   void free_work();
@@ -172,23 +181,27 @@ __device__ __forceinline__ double sum_parts(const double* part, int n, int strid
 // the CG step length over h^2), formed by every CTA in
 // the same order; CTA 0 records p'q, alpha and a breakdown (p'q <= 0 or not
 // finite).  All threads of the CTA call it; returns alpha to every thread.
+// thread 0's part of pcg_alpha, given the summed p'q: returns alpha (CTA 0
+// records p'q, alpha and a breakdown)
+__device__ __forceinline__ double pcg_alpha_from(PcgScalars* sc, double pq) {
+  const bool ok = pq > 0.0;  // false for NaN too
+  const double alpha = ok ? sc->rz[sc->iters & 1] / pq : 0.0;
+  if (blockIdx.x == 0) {
+    sc->pq = pq;
+    sc->alpha = alpha;
+    sc->slot = sc->iters & 1;
+    if (!ok) {
+      sc->flags |= isfinite(pq) ? PCG_FLAG_BREAKDOWN : PCG_FLAG_NONFINITE;
+      sc->done = 1;
+    }
+  }
+  return alpha;
+}
+
 __device__ __forceinline__ double pcg_alpha(PcgScalars* sc, const double* pq_part, int nblk, double* sm,
                                             double* s_alpha) {
   const double pq = sum_parts(pq_part, nblk, 1, sm);
-  if (threadIdx.x == 0) {
-    const bool ok = pq > 0.0;  // false for NaN too
-    const double alpha = ok ? sc->rz[sc->iters & 1] / pq : 0.0;
-    *s_alpha = alpha;
-    if (blockIdx.x == 0) {
-      sc->pq = pq;
-      sc->alpha = alpha;
-      sc->slot = sc->iters & 1;
-      if (!ok) {
-        sc->flags |= isfinite(pq) ? PCG_FLAG_BREAKDOWN : PCG_FLAG_NONFINITE;
-        sc->done = 1;
-      }
-    }
-  }
+  if (threadIdx.x == 0) *s_alpha = pcg_alpha_from(sc, pq);
   __syncthreads();
   return *s_alpha;
 }
@@ -207,6 +220,8 @@ struct PcgUpdate {
   // flexible CG: partials of (new r).z with the z still in z (r'zold)
   const double* z = nullptr;
   double* rzo_part = nullptr;
+  // the DF outer iteration: x, r, p, q hold double-float pairs, z FP32
+  bool df = false;
 };
 int amg_update_first(Solver& S, const PcgUpdate& u, cudaStream_t s);
 
@@ -217,11 +232,14 @@ int amg_update_first(Solver& S, const PcgUpdate& u, cudaStream_t s);
 struct VcycleDot {
   const double* r = nullptr;
   double* part = nullptr;
+  // the DF outer iteration: r holds double-float pairs, z is written in FP32
+  bool df = false;
 };
 // first_done: amg_update_first already did the first level-0 step for this r.
 int amg_vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, const VcycleDot* dot = nullptr,
                     bool first_done = false);
 void amg_fill_info(const Solver& S, amg_info_t* out);
+int amg_levels(const Solver& S);  // levels of the hierarchy (0 without one)
 void amg_copy_level(const Solver& S, int level, int which, int32_t* rowptr, int32_t* col, double* val, cudaStream_t s);
 
 // learned stage (cnn.cu): buffers for grids of eb's size (before any capture),
