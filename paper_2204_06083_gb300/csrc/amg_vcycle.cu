@@ -193,6 +193,29 @@ __global__ void __launch_bounds__(TILE_NODES) k_update_first(PairList pl, PcgUpd
 // V-cycle, the reduction partials DF.  x += (alpha h2) p, r -= alpha q in DF,
 // the r'r and r'zold partials summed in DF; the V-cycle's first step then
 // takes the FP32 high part of the new r (x = d = D^-1 b (1 / theta)).
+// one pair's inputs of k_update_first_df
+struct UfIn {
+  DF r0, r1, q0, q1, p0, p1, xa, xb;
+  float2 zv;
+  uint32_t c0, c1;
+};
+
+__device__ __forceinline__ void uf_load(UfIn& in, const PcgUpdate& u, const uint8_t* code, int32_t node) {
+  df_ld2_rw(u.r, node, in.r0, in.r1);
+  df_ld2(u.q, node, in.q0, in.q1);
+  df_ld2(u.p, node, in.p0, in.p1);
+  df_ld2_rw(u.x, node, in.xa, in.xb);
+  in.zv = u.rzo_part ? __ldg(reinterpret_cast<const float2*>(reinterpret_cast<const float*>(u.z) + node))
+                     : make_float2(0.0f, 0.0f);
+  ld_codes(code, node, in.c0, in.c1);
+}
+
+// k_update_first for the DF outer iteration: x, r, p, q are double-float
+// vectors (DF pairs in the buffers of doubles), z the FP32 output of the
+// V-cycle, the reduction partials DF.  x += (alpha h2) p, r -= alpha q in DF,
+// the r'r and r'zold partials summed in DF; the V-cycle's first step then
+// takes the FP32 high part of the new r (x = d = D^-1 b (1 / theta)).  A
+// thread's first pair is loaded before the partial sums that give alpha.
 template <int DIM, class V>
 __global__ void __launch_bounds__(TILE_NODES) k_update_first_df(PairList pl, PcgUpdate u, const uint8_t* __restrict__ code,
                                                                 const typename DiagOf<V>::type* __restrict__ diag,
@@ -208,6 +231,11 @@ __global__ void __launch_bounds__(TILE_NODES) k_update_first_df(PairList pl, Pcg
     }
     return;
   }
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  UfIn in;
+  int32_t node = li < pl.n ? __ldg(pl.node + li) : 0;
+  if (li < pl.n) uf_load(in, u, code, node);
   // alpha from the DF p'q partials (FP64 scalars), split into DF once per CTA
   const double pq = df_sum_parts(u.pq_part, u.nblk, dsm);
   if (threadIdx.x == 0) {
@@ -217,34 +245,30 @@ __global__ void __launch_bounds__(TILE_NODES) k_update_first_df(PairList pl, Pcg
   }
   __syncthreads();
   const DF a_df = s_a[0], ax_df = s_a[1];
-  const float* zf = reinterpret_cast<const float*>(u.z);
   DF srr{0.0f, 0.0f}, srzo{0.0f, 0.0f};
-  EB_LIST_LOOP(pl, node) {
-    DF r0, r1, q0, q1, p0, p1, xa, xb;
-    df_ld2_rw(u.r, node, r0, r1);
-    df_ld2(u.q, node, q0, q1);
-    df_ld2(u.p, node, p0, p1);
-    df_ld2_rw(u.x, node, xa, xb);
+  while (li < pl.n) {
+    const int64_t ln = li + step;
+    const int32_t nnode = ln < pl.n ? __ldg(pl.node + ln) : 0;
     // the residual update cancels by design: the accurate DF sum
-    r0 = df_sub(r0, df_mul(a_df, q0));
-    r1 = df_sub(r1, df_mul(a_df, q1));
-    df_st2(u.x, node, df_add_fast(xa, df_mul(ax_df, p0)), df_add_fast(xb, df_mul(ax_df, p1)));
+    const DF r0 = df_sub(in.r0, df_mul(a_df, in.q0)), r1 = df_sub(in.r1, df_mul(a_df, in.q1));
+    df_st2(u.x, node, df_add_fast(in.xa, df_mul(ax_df, in.p0)), df_add_fast(in.xb, df_mul(ax_df, in.p1)));
     df_st2(u.r, node, r0, r1);
     df_acc_prod(srr, r0, r0);
     df_acc_prod(srr, r1, r1);
     if (u.rzo_part) {
-      const float2 zv = __ldg(reinterpret_cast<const float2*>(zf + node));
-      df_acc_prod_f(srzo, r0, zv.x);
-      df_acc_prod_f(srzo, r1, zv.y);
+      df_acc_prod_f(srzo, r0, in.zv.x);
+      df_acc_prod_f(srzo, r1, in.zv.y);
     }
-    uint32_t c0, c1;
-    ld_codes(code, node, c0, c1);
+    const uint32_t c0 = in.c0, c1 = in.c1;
     const float b0 = (c0 & CODE_CP) ? r0.hi : 0.0f, b1 = (c1 & CODE_CP) ? r1.hi : 0.0f;
     if (b_out) st2o(b_out + node, b0, b1);
     const float v0 = (c0 & CODE_CP) ? inv_diag_t<float>(c0, diag, node, o) * b0 * inv_theta : 0.0f;
     const float v1 = (c1 & CODE_CP) ? inv_diag_t<float>(c1, diag, node + 1, o) * b1 * inv_theta : 0.0f;
     st2o(x0 + node, v0, v1);
     st2o(d + node, v0, v1);
+    if (ln < pl.n) uf_load(in, u, code, nnode);
+    li = ln;
+    node = nnode;
   }
   if (u.rzo_part) {
     const DF t = df_block_sum_df(srzo, dsm);

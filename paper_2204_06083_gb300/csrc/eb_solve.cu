@@ -257,6 +257,103 @@ __global__ void __launch_bounds__(TILE_NODES) k_xpby_apply(TileView tv, PairList
 // (TwoSum errors collected), D_k z_k an exact product (interior points) or a
 // DF one (cut points), plus sigma h^2 z_k when SHIFT.  beta = 1 only (no
 // variable coefficient).
+// one pair's inputs of k_xpby_apply_df
+struct XpIn {
+  uint32_t c0, c1;
+  float2 zc, dn, up, bk, fr;
+  float left, right;
+  DF po0, po1, qo0, qo1;
+};
+
+template <int DIM>
+__device__ __forceinline__ void xp_load(XpIn& in, const TileView& tv, const uint8_t* code, const float* z,
+                                        const double* p, const double* q, int first, int32_t node) {
+  const int32_t nn = tv.nn, sy = tv.sy, sz = tv.sz;
+  ld_codes(code, node, in.c0, in.c1);
+  const float2 zero{0.0f, 0.0f};
+  in.zc = __ldg(reinterpret_cast<const float2*>(z + node));
+  in.left = node > 0 ? __ldg(z + node - 1) : 0.0f;
+  in.right = node + 2 < nn ? __ldg(z + node + 2) : 0.0f;
+  in.dn = node >= sy ? __ldg(reinterpret_cast<const float2*>(z + node - sy)) : zero;
+  in.up = node + sy < nn ? __ldg(reinterpret_cast<const float2*>(z + node + sy)) : zero;
+  in.bk = zero;
+  in.fr = zero;
+  if (DIM == 3) {
+    in.bk = node >= sz ? __ldg(reinterpret_cast<const float2*>(z + node - sz)) : zero;
+    in.fr = node + sz < nn ? __ldg(reinterpret_cast<const float2*>(z + node + sz)) : zero;
+  }
+  if (!first) {
+    df_ld2_rw(p, node, in.po0, in.po1);
+    df_ld2_rw(q, node, in.qo0, in.qo1);
+  }
+}
+
+// p, q of one pair from its inputs; returns the pair's p.q terms added to s
+template <int DIM, bool SHIFT>
+__device__ __forceinline__ void xp_compute(const XpIn& in, const float2* diag_df, DF sig_h2, DF beta, int first,
+                                           double* p, double* q, int32_t node, DF& s) {
+  const uint32_t c0 = in.c0, c1 = in.c1;
+  const float2 zc = in.zc;
+  // the neighbour sums by cascaded summation, then D_k z_k (an exact product:
+  // D_k = 2 dim at interior points, DF for cut ones) minus them
+  Sum2 s0 = sum2_start((c0 & 1) ? 0.0f : in.left), s1 = sum2_start((c1 & 1) ? 0.0f : zc.x);
+  sum2_add(s0, (c0 & 2) ? 0.0f : zc.y);
+  sum2_add(s1, (c1 & 2) ? 0.0f : in.right);
+  sum2_add(s0, (c0 & 4) ? 0.0f : in.dn.x);
+  sum2_add(s1, (c1 & 4) ? 0.0f : in.dn.y);
+  sum2_add(s0, (c0 & 8) ? 0.0f : in.up.x);
+  sum2_add(s1, (c1 & 8) ? 0.0f : in.up.y);
+  if (DIM == 3) {
+    sum2_add(s0, (c0 & 16) ? 0.0f : in.bk.x);
+    sum2_add(s1, (c1 & 16) ? 0.0f : in.bk.y);
+    sum2_add(s0, (c0 & 32) ? 0.0f : in.fr.x);
+    sum2_add(s1, (c1 & 32) ? 0.0f : in.fr.y);
+  }
+  float d0h = (float)(2 * DIM), d0l = 0.0f, d1h = d0h, d1l = 0.0f;
+  if (c0 & 0x7F) {
+    const float2 t = __ldg(diag_df + node);
+    d0h = t.x;
+    d0l = t.y;
+  }
+  if (c1 & 0x7F) {
+    const float2 t = __ldg(diag_df + node + 1);
+    d1h = t.x;
+    d1l = t.y;
+  }
+  float pr0, pe0, pr1, pe1;
+  two_prod(d0h, zc.x, pr0, pe0);
+  two_prod(d1h, zc.y, pr1, pe1);
+  pe0 = __fmaf_rn(d0l, zc.x, pe0);
+  pe1 = __fmaf_rn(d1l, zc.y, pe1);
+  DF a0 = df_prod_minus_sum2(pr0, pe0, s0), a1 = df_prod_minus_sum2(pr1, pe1, s1);
+  if (SHIFT) {
+    a0 = df_add(a0, df_mul_f(sig_h2, zc.x));
+    a1 = df_add(a1, df_mul_f(sig_h2, zc.y));
+  }
+  DF p0 = df_make(zc.x), p1 = df_make(zc.y), q0 = a0, q1 = a1;
+  if (!first) {
+    p0 = df_add_f(df_mul(beta, in.po0), zc.x);
+    p1 = df_add_f(df_mul(beta, in.po1), zc.y);
+    q0 = df_add_fast(df_mul(beta, in.qo0), a0);
+    q1 = df_add_fast(df_mul(beta, in.qo1), a1);
+  }
+  if (!(c0 & CODE_CP)) q0 = DF{0.0f, 0.0f};
+  if (!(c1 & CODE_CP)) q1 = DF{0.0f, 0.0f};
+  df_st2(p, node, p0, p1);
+  df_st2(q, node, q0, q1);
+  df_acc_prod(s, p0, q0);
+  df_acc_prod(s, p1, q1);
+}
+
+// The end of an iteration (k_xpby_apply in DF): p = z + beta p, q = B z + beta
+// q, the p.q partials.  B z is the unit stencil D_k z_k - sum of the
+// CP-neighbour values on the FP32 z: the neighbours by cascaded summation
+// (TwoSum errors collected), D_k z_k an exact product (interior points) or a
+// DF one (cut points), plus sigma h^2 z_k when SHIFT.  beta = 1 only (no
+// variable coefficient).  The loads of a thread's first pair are issued before
+// the partial sums that give beta (the pass is bound by its load latency; a
+// double-buffered loop that also issued each pair's loads before the previous
+// pair's arithmetic was no faster).
 template <int DIM, bool SHIFT, bool COND>
 __global__ void __launch_bounds__(TILE_NODES) k_xpby_apply_df(TileView tv, PairList pl, PcgScalars* sc,
                                                               const uint8_t* code, const float2* diag_df, DF sig_h2,
@@ -270,6 +367,11 @@ __global__ void __launch_bounds__(TILE_NODES) k_xpby_apply_df(TileView tv, PairL
     if (COND && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
     return;
   }
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  XpIn cur;
+  int32_t node = li < pl.n ? __ldg(pl.node + li) : 0;
+  if (li < pl.n) xp_load<DIM>(cur, tv, code, z, p, q, first, node);
   if (threadIdx.x == 0) s_beta = DF{0.0f, 0.0f};
   if (!first) {
     const double v = df_sum_parts(rz_part, nrz, dsm);
@@ -308,74 +410,14 @@ __global__ void __launch_bounds__(TILE_NODES) k_xpby_apply_df(TileView tv, PairL
       cudaGraphSetConditional(h, (!sc->done && sc->iters < sc->maxit) ? 1u : 0u);
     }
   }
-  const int32_t nn = tv.nn, sy = tv.sy, sz = tv.sz;
   DF s{0.0f, 0.0f};
-  EB_LIST_LOOP(pl, node) {
-    uint32_t c0, c1;
-    ld_codes(code, node, c0, c1);
-    const float2 zc = __ldg(reinterpret_cast<const float2*>(z + node));
-    const float left = node > 0 ? __ldg(z + node - 1) : 0.0f;
-    const float right = node + 2 < nn ? __ldg(z + node + 2) : 0.0f;
-    const float2 zero{0.0f, 0.0f};
-    const float2 dn = node >= sy ? __ldg(reinterpret_cast<const float2*>(z + node - sy)) : zero;
-    const float2 up = node + sy < nn ? __ldg(reinterpret_cast<const float2*>(z + node + sy)) : zero;
-    float2 bk = zero, fr = zero;
-    if (DIM == 3) {
-      bk = node >= sz ? __ldg(reinterpret_cast<const float2*>(z + node - sz)) : zero;
-      fr = node + sz < nn ? __ldg(reinterpret_cast<const float2*>(z + node + sz)) : zero;
-    }
-    // the neighbour sums by cascaded summation, then D_k z_k (an exact
-    // product: D_k = 2 dim at interior points, DF for cut ones) minus them
-    Sum2 s0 = sum2_start((c0 & 1) ? 0.0f : left), s1 = sum2_start((c1 & 1) ? 0.0f : zc.x);
-    sum2_add(s0, (c0 & 2) ? 0.0f : zc.y);
-    sum2_add(s1, (c1 & 2) ? 0.0f : right);
-    sum2_add(s0, (c0 & 4) ? 0.0f : dn.x);
-    sum2_add(s1, (c1 & 4) ? 0.0f : dn.y);
-    sum2_add(s0, (c0 & 8) ? 0.0f : up.x);
-    sum2_add(s1, (c1 & 8) ? 0.0f : up.y);
-    if (DIM == 3) {
-      sum2_add(s0, (c0 & 16) ? 0.0f : bk.x);
-      sum2_add(s1, (c1 & 16) ? 0.0f : bk.y);
-      sum2_add(s0, (c0 & 32) ? 0.0f : fr.x);
-      sum2_add(s1, (c1 & 32) ? 0.0f : fr.y);
-    }
-    float d0h = (float)(2 * DIM), d0l = 0.0f, d1h = d0h, d1l = 0.0f;
-    if (c0 & 0x7F) {
-      const float2 t = __ldg(diag_df + node);
-      d0h = t.x;
-      d0l = t.y;
-    }
-    if (c1 & 0x7F) {
-      const float2 t = __ldg(diag_df + node + 1);
-      d1h = t.x;
-      d1l = t.y;
-    }
-    float pr0, pe0, pr1, pe1;
-    two_prod(d0h, zc.x, pr0, pe0);
-    two_prod(d1h, zc.y, pr1, pe1);
-    pe0 = __fmaf_rn(d0l, zc.x, pe0);
-    pe1 = __fmaf_rn(d1l, zc.y, pe1);
-    DF a0 = df_prod_minus_sum2(pr0, pe0, s0), a1 = df_prod_minus_sum2(pr1, pe1, s1);
-    if (SHIFT) {
-      a0 = df_add(a0, df_mul_f(sig_h2, zc.x));
-      a1 = df_add(a1, df_mul_f(sig_h2, zc.y));
-    }
-    DF p0 = df_make(zc.x), p1 = df_make(zc.y), q0 = a0, q1 = a1;
-    if (!first) {
-      DF po0, po1, qo0, qo1;
-      df_ld2_rw(p, node, po0, po1);
-      df_ld2_rw(q, node, qo0, qo1);
-      p0 = df_add_f(df_mul(beta, po0), zc.x);
-      p1 = df_add_f(df_mul(beta, po1), zc.y);
-      q0 = df_add_fast(df_mul(beta, qo0), a0);
-      q1 = df_add_fast(df_mul(beta, qo1), a1);
-    }
-    if (!(c0 & CODE_CP)) q0 = DF{0.0f, 0.0f};
-    if (!(c1 & CODE_CP)) q1 = DF{0.0f, 0.0f};
-    df_st2(p, node, p0, p1);
-    df_st2(q, node, q0, q1);
-    df_acc_prod(s, p0, q0);
-    df_acc_prod(s, p1, q1);
+  while (li < pl.n) {
+    const int64_t ln = li + step;
+    const int32_t nnode = ln < pl.n ? __ldg(pl.node + ln) : 0;
+    xp_compute<DIM, SHIFT>(cur, diag_df, sig_h2, beta, first, p, q, node, s);
+    if (ln < pl.n) xp_load<DIM>(cur, tv, code, z, p, q, first, nnode);
+    li = ln;
+    node = nnode;
   }
   const DF t = df_block_sum_df(s, dsm);
   if (threadIdx.x == 0) df_part_store(pq_part, blockIdx.x, t);
