@@ -909,8 +909,10 @@ def gpu_poisson(ctx, args, dim):
     if outer == eb.EB_DF64:
         pcg_apply = hbm_roof(f"k_xpby_apply_df<{dim}, false, true> (p update + next operator apply, double-float)",
                              37 * nc, xp_ms, xp_n)
+        pcg_apply["traffic"] = recorded_traffic("k_xpby_apply_df<3>")
         pcg_update = hbm_roof(f"k_update_first_df<{dim}, float> (x/r update in double-float + first level-0 "
                               "smoothing step)", 65 * nc, up_ms, up_n)
+        pcg_update["traffic"] = recorded_traffic("k_update_first_df<3, float>")
         extra["fp64_outer"]["p_update_apply_roofline"] = fp64_apply_roof(xp64_ms, xp64_n)
         extra["fp64_outer"]["xr_update_roofline"] = hbm_roof(
             f"k_update_first<{dim}, float> (x/r update + first level-0 smoothing step, FP64)", 69 * nc,
