@@ -17,8 +17,9 @@ wave       Leapfrog wave equation on the star r = 0.5 + 0.1 sin(5 phi), 4096^2
 batched    64 seeded stars on grids from 128^2 to 1024^2, backward-Euler heat
            with dt = h, 50 steps of all 64 geometries per bench step (one
            batch_heat_step per time step, forcing and boundary data frozen at
-           t = 0); the same time step solved geometry by geometry with the
-           plain FP64 AMG-PCG is timed beside it.
+           t = 0; the per-geometry PCG in double-float); the FP64 outer
+           iteration and the same time step solved geometry by geometry with
+           the plain FP64 AMG-PCG are timed beside it.
 conv       The learned stage's network alone: one forward pass (6 layers, the four
            32 -> 32 layers on tcgen05) over a 2048^2 image of seeded inputs.
 learned    The learned preconditioner stage: trained (outside the timed
@@ -185,7 +186,8 @@ def config_of(w, small=None):
                             "grids 128^2..1024^2, dt=h, 50 steps of all geometries per bench step, "
                             "forcing and boundary data of u=exp(-t) sin(2x) cos(3y) frozen at t=0",
                 "geometries": 64, "time_steps": 50, "rtol": RTOL,
-                "vcycle": "FP32 V-cycle on the block-diagonal hierarchy, per-geometry flexible FP64 PCG",
+                "vcycle": "FP32 V-cycle on the block-diagonal hierarchy, per-geometry flexible PCG with double-float "
+                          "vectors (batch_set_outer_prec EB_DF64), FP64 scalars and exit test",
                 "l2": "batch vectors exceed L2 (26M nodes x 8 B)"}
     if w == "conv":
         return {"workload": "learned-stage network forward, one 2048^2 image, He-initialised weights (seed 8), "
@@ -1121,6 +1123,8 @@ def gpu_batched(ctx, args):
     B.heat_setup(dts, 1.0, vcycle_prec=eb.EB_F32)
     torch.cuda.synchronize()
     setup_ms = 1000.0 * (time.perf_counter() - t0)
+    # the batched PCG in double-float (batch_set_outer_prec); FP64 beside it
+    B.set_outer(eb.EB_DF64)
     tile, tune = tune_tiles(lambda: autotune.tune_batch(B, reps=5))
     u0 = B.zeros()
     f = B.zeros()
@@ -1152,6 +1156,17 @@ def gpu_batched(ctx, args):
     prof_ms = sum(st[0].prof_kernel_ms for st in prof)
     prof_n = sum(st[0].prof_launches for st in prof)
     iters = [max(s.iterations for s in st) for st in res[-1]]
+    B.set_outer(eb.EB_F64)
+    o64 = []
+    for i in range(1 + args.steps):
+        ctx.flush()
+        t, st64 = timed(step)
+        if i >= 1:
+            o64.append(t)
+    B.set_outer(eb.EB_DF64)
+    fp64_outer = {"ms_per_time_step": statistics.mean(o64) / nsteps,
+                  "dof_steps_per_s": nc * nsteps / (statistics.mean(o64) / 1000.0),
+                  "max_iterations_per_time_step": [max(s.iterations for s in st) for st in st64]}
     # the plain FP64 AMG-PCG, geometry by geometry, on the first time step
     hs = [B.geometry(g) for g in range(B.count)]
     solvers = [eb.AMG(hs[g], 1.0 / dts[g]) for g in range(B.count)]
@@ -1188,10 +1203,11 @@ def gpu_batched(ctx, args):
     pk, kind = peaks()
     avg_s = (prof_ms / prof_n) / 1000.0 if prof_n else float("nan")
     achieved = CHEB_BYTES_PER_DOF["f32"] * nc / avg_s / 1e9 if prof_n else None
-    return {"value": value, "ms_per_step": ms_per_step, "dtype": "f64 outer, f32 V-cycle", "num_cp": nc,
-            "num_nodes": B.num_nodes, "setup_ms": setup_ms, "ms_per_time_step": ms_per_step / nsteps,
+    return {"value": value, "ms_per_step": ms_per_step,
+            "dtype": "df64 outer (double-float: FP32 pairs; exit test on the FP64 true residual), f32 V-cycle",
+            "num_cp": nc, "num_nodes": B.num_nodes, "setup_ms": setup_ms, "ms_per_time_step": ms_per_step / nsteps,
             "tile": tile, "autotune_us_per_vcycle": tune,
-            "max_iterations_per_time_step": iters,
+            "max_iterations_per_time_step": iters, "fp64_outer": fp64_outer,
             "sequential_fp64": {"ms_per_time_step": statistics.mean(seq),
                                 "dof_per_s": nc / (statistics.mean(seq) / 1000.0)},
             "roofline": {"bound": "hbm", "kernel": "k_g_cheb_step<2, float, float> (batch view)",

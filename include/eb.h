@@ -491,6 +491,15 @@ int batch_weighted_sum(const batch_handle* b, const double* w_all, const double*
  * duration and the launch count in prof_kernel_ms / prof_launches of every
  * geometry's stats (batch totals). */
 int batch_set_profile(batch_handle* b, int on);
+/* prec EB_DF64: later batch_heat_step calls run the outer PCG of every
+ * geometry in double-float (pcg_opts.outer_prec semantics: x, r, p, q as FP32
+ * pairs, the FP32 V-cycle output z, DF per-tile partials, FP64 scalars; each
+ * geometry's b and x cross into DF scaled by its own power of two; the exit
+ * test stays the FP64 true residual).  Needs a batch_heat_setup with an FP32
+ * or BF16 V-cycle of two or more levels (EB_ERR_NOT_IMPLEMENTED from the step
+ * otherwise).  EB_F64 (the default) restores the FP64 iteration.
+ * EB_ERR_INVALID for other values. */
+int batch_set_outer_prec(batch_handle* b, int prec);
 /* One theta-method step of every geometry (heat_step semantics, warm start
  * from u), u overwritten.  stats: host array of count entries (may be NULL).
  * Returns EB_ERR_NO_CONVERGENCE if any geometry missed rtol.  Synchronous. */

@@ -804,10 +804,13 @@ static int vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, co
     // part of the smoother-step timing
     const bool mark = !(k == cc.deg - 1 && dot);
     if (mark) S.prof_mark(s, true);
-    if (k == cc.deg - 1 && rdf)  // z in FP32 for the DF outer iteration
+    if (k == cc.deg - 1 && rdf && dot->part)  // z in FP32 for the DF outer iteration, with the r'z partials
       k_g_cheb_step<DIM, V, float, 2><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, x,
                                                                 reinterpret_cast<float*>(z), g.d, (A)cc.c1[k],
                                                                 (A)cc.c2[k], dot->r, dot->part);
+    else if (k == cc.deg - 1 && rdf)  // z in FP32 on every node of the active tiles, 0 off the CPs
+      k_g_cheb_step<(DIM & ~DIM_LIST), V, float><<<gb, TILE_NODES, 0, s>>>(
+          tiles_only(tv), eb.code, diag, o, b, x, reinterpret_cast<float*>(z), g.d, (A)cc.c1[k], (A)cc.c2[k]);
     else if (k == cc.deg - 1 && dot)
       k_g_cheb_step<DIM, V, double, 1><<<gb, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, x, z, g.d, (A)cc.c1[k],
                                                                  (A)cc.c2[k], dot->r, dot->part);
@@ -822,7 +825,7 @@ static int vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, co
   g.x = x;
   g.x2 = x2;
   EB_CUDA(cudaGetLastError());
-  return dot ? (int)gb : 0;
+  return (dot && dot->part) ? (int)gb : 0;
 }
 
 int amg_vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, const VcycleDot* dot, bool first_done) {

@@ -23,6 +23,7 @@
 // geometry's tiles are skipped by the update kernels.  The iteration is
 // captured in a CUDA graph.
 #include "amg_internal.cuh"
+#include "df.cuh"
 #include "stencil.cuh"
 
 #include <algorithm>
@@ -61,6 +62,15 @@ struct Batch {
   // event timing of the level-0 smoother launches inside the captured iteration
   bool profile = false;
   int g_prof = -1, g_pairs = 0;
+  // the DF outer iteration (batch_set_outer_prec): requested precision, whether
+  // the current solve runs it, per-geometry powers of two into DF, the DF copy
+  // of the cut CPs' diagonals; g_df / l_df key the captured graphs
+  int outer = EB_F64;
+  bool df = false;
+  double* gscale = nullptr;
+  double* xdf = nullptr;  // the DF image of x (the solver's tmp holds the right-hand side)
+  float2* diag_df = nullptr;
+  int g_df = -1, l_df = -1;
   // the whole loop on the device (conditional WHILE node) when not profiling
   cudaGraphExec_t lexec = nullptr;
   const double* l_b = nullptr;
@@ -252,7 +262,7 @@ static void destroy_batch(Batch& B) {
   dfree(V.code, s); dfree(V.diag, s); dfree(V.diag32, s); dfree(V.cp_of_node, s); dfree(V.cp_node, s);
   dfree(V.tile_base, s); dfree(V.tile_lim, s); dfree(V.tile_shift64, s); dfree(V.tile_shift32, s);
   dfree(B.tile_geo, s); dfree(B.geo_tile0, s); dfree(B.cut_off_cp, s); dfree(B.cut_c, s); dfree(B.gconst, s);
-  dfree(B.sc, s); dfree(B.part, s);
+  dfree(B.sc, s); dfree(B.part, s); dfree(B.gscale, s); dfree(B.diag_df, s); dfree(B.xdf, s);
   if (B.sc_host) cudaFreeHost(B.sc_host);
   B.sc_host = nullptr;
   for (eb_handle* e : B.geo) {
@@ -476,8 +486,209 @@ __global__ void __launch_bounds__(BT) k_b_heat_rhs(TileView tv, const int32_t* t
   }
 }
 
+// --------------------------------------------- the DF outer iteration (batch)
+// The batched iteration with x, r, p, q as double-float vectors (DF pairs in
+// the buffers of doubles), z the FP32 V-cycle output and DF per-tile partials
+// (in the slots of the doubles), as the single-grid DF iteration: every vector
+// operation on the FP32 pipe with error-free transformations.  A tile's
+// scalars (alpha or beta, the shift sigma') are split into DF once per tile.
+
+// x += alpha p, r -= alpha q in DF; per-tile DF partials r.r and, with z
+// (flexible CG), r.zold as pairs, else r.r alone (k_b_update_xr's layout)
+__global__ void __launch_bounds__(BT) k_b_update_xr_df(TileView tv, const int32_t* tile_geo, const PcgScalars* sc,
+                                                       double* x, double* r, const double* p, const double* q,
+                                                       const float* z, double* part) {
+  __shared__ DF dsm[BT / 32];
+  __shared__ DF s_a;
+  for (int64_t tt = blockIdx.x; tt < tv.ntiles; tt += gridDim.x) {
+    const PcgScalars& S = sc[tile_geo[tt]];
+    if (S.done) continue;
+    __syncthreads();  // s_a of the previous tile is read
+    if (threadIdx.x == 0) s_a = df_from_double(S.alpha);
+    __syncthreads();
+    const DF a = s_a;
+    int32_t node;
+    DF srr{0.0f, 0.0f}, srzo{0.0f, 0.0f};
+    if (tile_pair<2>(tv, tt, threadIdx.x, node)) {
+      DF r0, r1, q0, q1, p0, p1, xa, xb;
+      df_ld2_rw(r, node, r0, r1);
+      df_ld2(q, node, q0, q1);
+      df_ld2(p, node, p0, p1);
+      df_ld2_rw(x, node, xa, xb);
+      r0 = df_sub(r0, df_mul(a, q0));
+      r1 = df_sub(r1, df_mul(a, q1));
+      df_st2(x, node, df_add_fast(xa, df_mul(a, p0)), df_add_fast(xb, df_mul(a, p1)));
+      df_st2(r, node, r0, r1);
+      df_acc_prod(srr, r0, r0);
+      df_acc_prod(srr, r1, r1);
+      if (z) {
+        const float2 zv = __ldg(reinterpret_cast<const float2*>(z + node));
+        df_acc_prod_f(srzo, r0, zv.x);
+        df_acc_prod_f(srzo, r1, zv.y);
+      }
+    }
+    const DF t = df_block_sum_df(srr, dsm);
+    if (z) {
+      const DF u = df_block_sum_df(srzo, dsm);
+      if (threadIdx.x == 0) {
+        df_part_store(part, 2 * tt, t);
+        df_part_store(part, 2 * tt + 1, u);
+      }
+    } else if (threadIdx.x == 0) {
+      df_part_store(part, tt, t);
+    }
+  }
+}
+
+// per-tile DF partials r.z (pairs (r.z, 0)) for r in DF and the FP32 z
+__global__ void __launch_bounds__(BT) k_b_dot_df(TileView tv, const int32_t* tile_geo, const PcgScalars* sc,
+                                                 const double* r, const float* z, double* part) {
+  __shared__ DF dsm[BT / 32];
+  for (int64_t tt = blockIdx.x; tt < tv.ntiles; tt += gridDim.x) {
+    if (sc[tile_geo[tt]].done) continue;
+    int32_t node;
+    DF a{0.0f, 0.0f};
+    if (tile_pair<2>(tv, tt, threadIdx.x, node)) {
+      DF r0, r1;
+      df_ld2(r, node, r0, r1);
+      const float2 zv = __ldg(reinterpret_cast<const float2*>(z + node));
+      df_acc_prod_f(a, r0, zv.x);
+      df_acc_prod_f(a, r1, zv.y);
+    }
+    const DF u = df_block_sum_df(a, dsm);
+    if (threadIdx.x == 0) {
+      df_part_store(part, 2 * tt, u);
+      df_part_store(part, 2 * tt + 1, DF{0.0f, 0.0f});
+    }
+  }
+}
+
+// p = z + beta p, q = B z + beta q in DF with the per-tile DF partials p.q;
+// B z = (sigma' + D_k) z_k - sum of the CP-neighbour values on the FP32 z (the
+// neighbours by cascaded summation, D_k z_k exact or DF, sigma' z_k in DF)
+__global__ void __launch_bounds__(BT) k_b_xpby_apply_df(TileView tv, const int32_t* tile_geo, const PcgScalars* sc,
+                                                        const uint8_t* code, const float2* diag_df, const float* z,
+                                                        double* p, double* q, int first, double* part) {
+  __shared__ DF dsm[BT / 32];
+  __shared__ DF s_c[2];
+  for (int64_t tt = blockIdx.x; tt < tv.ntiles; tt += gridDim.x) {
+    const PcgScalars& S = sc[tile_geo[tt]];
+    if (S.done) continue;
+    __syncthreads();  // s_c of the previous tile is read
+    if (threadIdx.x == 0) {
+      s_c[0] = df_from_double(first ? 0.0 : S.beta);
+      s_c[1] = df_from_double(__ldg(tv.tshift64 + tt).x);
+    }
+    __syncthreads();
+    const DF beta = s_c[0], sig = s_c[1];
+    int32_t node;
+    DF s{0.0f, 0.0f};
+    if (tile_pair<2>(tv, tt, threadIdx.x, node)) {
+      uint32_t c0, c1;
+      ld_codes(code, node, c0, c1);
+      const int32_t nn = tv.nn, sy = tv.sy;
+      const float2 zero{0.0f, 0.0f};
+      const float2 zc = __ldg(reinterpret_cast<const float2*>(z + node));
+      const float left = node > 0 ? __ldg(z + node - 1) : 0.0f;
+      const float right = node + 2 < nn ? __ldg(z + node + 2) : 0.0f;
+      const float2 dn = node >= sy ? __ldg(reinterpret_cast<const float2*>(z + node - sy)) : zero;
+      const float2 up = node + sy < nn ? __ldg(reinterpret_cast<const float2*>(z + node + sy)) : zero;
+      Sum2 s0 = sum2_start((c0 & 1) ? 0.0f : left), s1 = sum2_start((c1 & 1) ? 0.0f : zc.x);
+      sum2_add(s0, (c0 & 2) ? 0.0f : zc.y);
+      sum2_add(s1, (c1 & 2) ? 0.0f : right);
+      sum2_add(s0, (c0 & 4) ? 0.0f : dn.x);
+      sum2_add(s1, (c1 & 4) ? 0.0f : dn.y);
+      sum2_add(s0, (c0 & 8) ? 0.0f : up.x);
+      sum2_add(s1, (c1 & 8) ? 0.0f : up.y);
+      float d0h = 4.0f, d0l = 0.0f, d1h = 4.0f, d1l = 0.0f;
+      if (c0 & 0x7F) {
+        const float2 t = __ldg(diag_df + node);
+        d0h = t.x;
+        d0l = t.y;
+      }
+      if (c1 & 0x7F) {
+        const float2 t = __ldg(diag_df + node + 1);
+        d1h = t.x;
+        d1l = t.y;
+      }
+      float pr0, pe0, pr1, pe1;
+      two_prod(d0h, zc.x, pr0, pe0);
+      two_prod(d1h, zc.y, pr1, pe1);
+      pe0 = __fmaf_rn(d0l, zc.x, pe0);
+      pe1 = __fmaf_rn(d1l, zc.y, pe1);
+      const DF a0 = df_add(df_prod_minus_sum2(pr0, pe0, s0), df_mul_f(sig, zc.x));
+      const DF a1 = df_add(df_prod_minus_sum2(pr1, pe1, s1), df_mul_f(sig, zc.y));
+      DF p0 = df_make(zc.x), p1 = df_make(zc.y), q0 = a0, q1 = a1;
+      if (!first) {
+        DF po0, po1, qo0, qo1;
+        df_ld2_rw(p, node, po0, po1);
+        df_ld2_rw(q, node, qo0, qo1);
+        p0 = df_add_f(df_mul(beta, po0), zc.x);
+        p1 = df_add_f(df_mul(beta, po1), zc.y);
+        q0 = df_add_fast(df_mul(beta, qo0), a0);
+        q1 = df_add_fast(df_mul(beta, qo1), a1);
+      }
+      if (!(c0 & CODE_CP)) q0 = DF{0.0f, 0.0f};
+      if (!(c1 & CODE_CP)) q1 = DF{0.0f, 0.0f};
+      df_st2(p, node, p0, p1);
+      df_st2(q, node, q0, q1);
+      df_acc_prod(s, p0, q0);
+      df_acc_prod(s, p1, q1);
+    }
+    const DF t = df_block_sum_df(s, dsm);
+    if (threadIdx.x == 0) df_part_store(part, tt, t);
+  }
+}
+
+// Into DF over the active tiles: xd = scale_g x and, in place, r = scale_g r,
+// scale_g the power of two of the tile's geometry; and back: x = xd / scale_g
+__global__ void __launch_bounds__(BT) k_b_df_in(TileView tv, const int32_t* tile_geo, const double* scale,
+                                                const double* x, double* xd, double* r) {
+  for (int64_t tt = blockIdx.x; tt < tv.ntiles; tt += gridDim.x) {
+    int32_t node;
+    if (!tile_pair<2>(tv, tt, threadIdx.x, node)) continue;
+    const double sc = scale[tile_geo[tt]];
+    const Two<double> xv = ld2d(x + node), rv = ld2d(r + node);
+    df_st2(xd, node, df_from_double(xv.x * sc), df_from_double(xv.y * sc));
+    df_st2(r, node, df_from_double(rv.x * sc), df_from_double(rv.y * sc));
+  }
+}
+
+__global__ void __launch_bounds__(BT) k_b_df_out(TileView tv, const int32_t* tile_geo, const double* scale,
+                                                 const double* xd, double* x) {
+  for (int64_t tt = blockIdx.x; tt < tv.ntiles; tt += gridDim.x) {
+    int32_t node;
+    if (!tile_pair<2>(tv, tt, threadIdx.x, node)) continue;
+    const double inv = 1.0 / scale[tile_geo[tt]];
+    DF a, b;
+    df_ld2_rw(xd, node, a, b);
+    st2(x + node, df_to_double(a) * inv, df_to_double(b) * inv);
+  }
+}
+
+// the DF copy of the cut CPs' diagonals of the batch view
+__global__ void __launch_bounds__(BT) k_b_df_diag(TileView tv, const uint8_t* code, const double* diag,
+                                                  float2* out) {
+  for (int64_t tt = blockIdx.x; tt < tv.ntiles; tt += gridDim.x) {
+    int32_t node;
+    if (!tile_pair<2>(tv, tt, threadIdx.x, node)) continue;
+    uint32_t c0, c1;
+    ld_codes(code, node, c0, c1);
+    if (c0 & 0x7F) {
+      const DF v = df_from_double(diag[node]);
+      out[node] = make_float2(v.hi, v.lo);
+    }
+    if (c1 & 0x7F) {
+      const DF v = df_from_double(diag[node + 1]);
+      out[node + 1] = make_float2(v.hi, v.lo);
+    }
+  }
+}
+
 // one CTA per geometry: combine the geometry's tile partials in a fixed order
-__global__ void k_b_finalize(const double* part, const int32_t* geo_tile0, int op, PcgScalars* sc) {
+// df: the partials are DF (the DF iteration; never FIN_INIT), each thread's
+// share summed in DF and rounded once.
+__global__ void k_b_finalize(const double* part, const int32_t* geo_tile0, int op, PcgScalars* sc, int df) {
   __shared__ double sm[2][256];
   const int g = blockIdx.x;
   const int t0 = geo_tile0[g], t1 = geo_tile0[g + 1];
@@ -485,11 +696,23 @@ __global__ void k_b_finalize(const double* part, const int32_t* geo_tile0, int o
   // partials, the others single ones
   const bool pairs = op != FIN_ALPHA && op != FIN_RR;
   PcgScalars& S = sc[g];
-  if (op != FIN_INIT && op != FIN_RZ0 && op != FIN_RZ0F && S.done) return;
+  // a geometry already done (converged at FIN_INIT, e.g. on a restart) has no
+  // fresh partials: the kernels skip its tiles
+  if (op != FIN_INIT && S.done) return;
   double a = 0.0, b = 0.0;
-  for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
-    a += pairs ? part[2 * t] : part[t];
-    if (pairs) b += part[2 * t + 1];
+  if (df) {
+    DF da{0.0f, 0.0f}, db{0.0f, 0.0f};
+    for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+      da = df_add(da, df_part_load(part, pairs ? 2 * (int64_t)t : t));
+      if (pairs) db = df_add(db, df_part_load(part, 2 * (int64_t)t + 1));
+    }
+    a = df_to_double(da);
+    b = df_to_double(db);
+  } else {
+    for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+      a += pairs ? part[2 * t] : part[t];
+      if (pairs) b += part[2 * t + 1];
+    }
   }
   sm[0][threadIdx.x] = a;
   sm[1][threadIdx.x] = b;
@@ -560,7 +783,7 @@ static unsigned bgrid(const Batch& B) {
 
 static void b_finalize(Batch& B, int op, cudaStream_t s) {
   ++B.nlaunch;
-  k_b_finalize<<<B.ngeo(), 256, 0, s>>>(B.part, B.geo_tile0, op, B.sc);
+  k_b_finalize<<<B.ngeo(), 256, 0, s>>>(B.part, B.geo_tile0, op, B.sc, (B.df && op != FIN_INIT) ? 1 : 0);
 }
 
 // z = M^-1 r for all geometries at once (block-diagonal V-cycle), then the
@@ -568,10 +791,31 @@ static void b_finalize(Batch& B, int op, cudaStream_t s) {
 static void b_precondition(Batch& B, const double* r, double* z, cudaStream_t s) {
   Solver& S = *B.S;
   const int64_t n0 = S.nlaunch;
-  amg_vcycle_grid(S, r, z, s);
+  if (B.df) {  // r in DF, z in FP32
+    VcycleDot in;
+    in.r = r;
+    in.df = true;
+    amg_vcycle_grid(S, r, z, s, &in);
+  } else {
+    amg_vcycle_grid(S, r, z, s);
+  }
   B.nlaunch += S.nlaunch - n0;
   ++B.nlaunch;
-  k_b_dot<<<bgrid(B), BT, 0, s>>>(B.view.tv(), B.tile_geo, B.sc, r, z, B.part);
+  if (B.df)
+    k_b_dot_df<<<bgrid(B), BT, 0, s>>>(B.view.tv(), B.tile_geo, B.sc, r, reinterpret_cast<const float*>(z), B.part);
+  else
+    k_b_dot<<<bgrid(B), BT, 0, s>>>(B.view.tv(), B.tile_geo, B.sc, r, z, B.part);
+}
+
+static void b_xpby_apply(Batch& B, int first, cudaStream_t s) {
+  Solver& S = *B.S;
+  ++B.nlaunch;
+  if (B.df)
+    k_b_xpby_apply_df<<<bgrid(B), BT, 0, s>>>(B.view.tv(), B.tile_geo, B.sc, B.view.code, B.diag_df,
+                                              reinterpret_cast<const float*>(S.z), S.p, S.q, first, B.part);
+  else
+    k_b_xpby_apply<<<bgrid(B), BT, 0, s>>>(B.view.tv(), B.tile_geo, B.sc, B.view.code, B.view.diag, S.z, S.p, S.q,
+                                           first, B.part);
 }
 
 // One batched iteration: alpha from the p.q partials of the previous
@@ -581,17 +825,21 @@ static void b_iteration(Batch& B, double* x, bool flex, cudaStream_t s) {
   Solver& S = *B.S;
   const TileView tv = B.view.tv();
   const unsigned gb = bgrid(B);
-  B.nlaunch += 2;
+  ++B.nlaunch;
   b_finalize(B, FIN_ALPHA, s);
-  k_b_update_xr<<<gb, BT, 0, s>>>(tv, B.tile_geo, B.sc, x, S.r, S.p, S.q, flex ? S.z : nullptr, B.part);
+  if (B.df)
+    k_b_update_xr_df<<<gb, BT, 0, s>>>(tv, B.tile_geo, B.sc, x, S.r, S.p, S.q,
+                                       flex ? reinterpret_cast<const float*>(S.z) : nullptr, B.part);
+  else
+    k_b_update_xr<<<gb, BT, 0, s>>>(tv, B.tile_geo, B.sc, x, S.r, S.p, S.q, flex ? S.z : nullptr, B.part);
   b_finalize(B, flex ? FIN_RRF : FIN_RR, s);
   b_precondition(B, S.r, S.z, s);
   b_finalize(B, flex ? FIN_BETAF : FIN_BETA, s);
-  k_b_xpby_apply<<<gb, BT, 0, s>>>(tv, B.tile_geo, B.sc, B.view.code, B.view.diag, S.z, S.p, S.q, 0, B.part);
+  b_xpby_apply(B, 0, s);
 }
 
 static void b_graph_prepare(Batch& B, const double* b, double* x, bool flex, cudaStream_t s) {
-  if (B.gexec && B.g_b == b && B.g_x == x && B.g_prof == (int)B.profile) return;
+  if (B.gexec && B.g_b == b && B.g_x == x && B.g_prof == (int)B.profile && B.g_df == (int)B.df) return;
   Solver& S = *B.S;
   if (B.gexec) cudaGraphExecDestroy(B.gexec);
   B.gexec = nullptr;
@@ -620,6 +868,7 @@ static void b_graph_prepare(Batch& B, const double* b, double* x, bool flex, cud
   B.nlaunch = n0;
   B.g_b = b;
   B.g_x = x;
+  B.g_df = (int)B.df;
 }
 
 // continue while some geometry is neither converged nor at its iteration limit
@@ -638,7 +887,7 @@ static void b_loop_release(Batch& B) {
 }
 
 static void b_loop_prepare(Batch& B, const double* b, double* x, bool flex) {
-  if (B.lexec && B.l_b == b && B.l_x == x) return;
+  if (B.lexec && B.l_b == b && B.l_x == x && B.l_df == (int)B.df) return;
   b_loop_release(B);
   if (!B.cap_stream) EB_CUDA(cudaStreamCreateWithFlags(&B.cap_stream, cudaStreamNonBlocking));
   const int64_t n0 = B.nlaunch;
@@ -651,6 +900,7 @@ static void b_loop_prepare(Batch& B, const double* b, double* x, bool flex) {
   B.nlaunch = n0;
   B.l_b = b;
   B.l_x = x;
+  B.l_df = (int)B.df;
 }
 
 static int batch_pcg(Batch& B, const double* b, double* x, double rtol, int maxit, pcg_stats* stats, cudaStream_t s) {
@@ -660,6 +910,22 @@ static int batch_pcg(Batch& B, const double* b, double* x, double rtol, int maxi
   const unsigned gb = bgrid(B);
   const bool flex = S.opts.vcycle_prec != EB_F64;
   EB_REQUIRE(rtol > 0.0 && maxit >= 0, EB_ERR_INVALID, "batch: rtol must be > 0 and maxit >= 0");
+  B.df = B.outer == EB_DF64;
+  if (B.df) {
+    EB_REQUIRE(flex && amg_levels(S) > 1, EB_ERR_NOT_IMPLEMENTED,
+               "batch: the DF outer iteration needs an FP32 or BF16 V-cycle of at least two levels");
+    if (!B.gscale) B.gscale = dalloc<double>(ng, s);
+    if (!B.xdf) B.xdf = dalloc<double>(B.view.g.num_nodes, s);
+    if (!B.diag_df) {
+      B.diag_df = dalloc<float2>(B.view.g.num_nodes, s);
+      ++B.nlaunch;
+      k_b_df_diag<<<gb, BT, 0, s>>>(tv, B.view.code, B.view.diag, B.diag_df);
+    }
+  }
+  // the vector the iteration updates: x itself, or its DF image
+  double* xi = B.df ? B.xdf : x;
+  EB_REQUIRE(xi != b, EB_ERR_INVALID, "batch: x and b share a buffer");
+  std::vector<double> gsc(ng, 1.0);
   auto t0 = std::chrono::steady_clock::now();
   std::vector<PcgScalars> init(ng);
   for (auto& p : init) {
@@ -682,14 +948,29 @@ static int batch_pcg(Batch& B, const double* b, double* x, double rtol, int maxi
     k_b_resid<<<gb, BT, 0, s>>>(tv, B.view.code, B.view.diag, b, x, S.r, B.part);
     b_finalize(B, FIN_INIT, s);
     int its = *std::max_element(iters.begin(), iters.end());
+    if (its < maxit && B.df) {
+      // per geometry a power of two that gives its b a unit root mean square
+      EB_CUDA(cudaMemcpyAsync(B.sc_host, B.sc, sizeof(PcgScalars) * ng, cudaMemcpyDeviceToHost, s));
+      EB_CUDA(cudaStreamSynchronize(s));
+      for (int g = 0; g < ng; ++g) {
+        const double ncp = (double)std::max<int64_t>(B.cp_off[g + 1] - B.cp_off[g], 1);
+        const double ms = B.sc_host[g].bb / ncp;
+        gsc[g] = (ms > 0.0 && std::isfinite(ms)) ? std::ldexp(1.0, -(int)std::lround(0.5 * std::log2(ms))) : 1.0;
+        B.sc_host[g].bb *= gsc[g] * gsc[g];
+        B.sc_host[g].rr *= gsc[g] * gsc[g];
+      }
+      EB_CUDA(cudaMemcpyAsync(B.sc, B.sc_host, sizeof(PcgScalars) * ng, cudaMemcpyHostToDevice, s));
+      EB_CUDA(cudaMemcpyAsync(B.gscale, gsc.data(), sizeof(double) * ng, cudaMemcpyHostToDevice, s));
+      ++B.nlaunch;
+      k_b_df_in<<<gb, BT, 0, s>>>(tv, B.tile_geo, B.gscale, x, xi, S.r);
+    }
     if (its < maxit) {
       b_precondition(B, S.r, S.z, s);
       b_finalize(B, FIN_RZ0, s);
-      ++B.nlaunch;
-      k_b_xpby_apply<<<gb, BT, 0, s>>>(tv, B.tile_geo, B.sc, B.view.code, B.view.diag, S.z, S.p, S.q, 1, B.part);
+      b_xpby_apply(B, 1, s);
       int it = 0;
       if (!B.profile) {  // the whole loop on the device
-        b_loop_prepare(B, b, x, flex);
+        b_loop_prepare(B, b, xi, flex);
         EB_CUDA(cudaGraphLaunch(B.lexec, s));
         EB_CUDA(cudaMemcpyAsync(B.sc_host, B.sc, sizeof(PcgScalars) * ng, cudaMemcpyDeviceToHost, s));
         EB_CUDA(cudaStreamSynchronize(s));
@@ -700,7 +981,7 @@ static int batch_pcg(Batch& B, const double* b, double* x, double rtol, int maxi
       }
       while (true) {
         if (its + it >= maxit) break;
-        b_graph_prepare(B, b, x, flex, s);
+        b_graph_prepare(B, b, xi, flex, s);
         EB_CUDA(cudaGraphLaunch(B.gexec, s));
         B.nlaunch += B.g_launches;
         ++it;
@@ -720,7 +1001,11 @@ static int batch_pcg(Batch& B, const double* b, double* x, double rtol, int maxi
       flags[g] |= B.sc_host[g].flags;
       hard = hard || (flags[g] & (PCG_FLAG_NONFINITE | PCG_FLAG_BREAKDOWN));
     }
-    // true residuals at exit
+    if (B.df && its < maxit) {
+      ++B.nlaunch;
+      k_b_df_out<<<gb, BT, 0, s>>>(tv, B.tile_geo, B.gscale, xi, x);
+    }
+    // true residuals at exit (FP64)
     B.nlaunch += 1;
     k_b_resid<<<gb, BT, 0, s>>>(tv, B.view.code, B.view.diag, b, x, S.r, B.part);
     b_finalize(B, FIN_INIT, s);
@@ -1002,6 +1287,15 @@ int batch_set_profile(batch_handle* b, int on) {
     return EB_ERR_INVALID;
   }
   b->b.profile = on != 0;
+  return EB_OK;
+}
+
+int batch_set_outer_prec(batch_handle* b, int prec) {
+  if (!b || (prec != EB_F64 && prec != EB_DF64)) {
+    set_error("batch_set_outer_prec: NULL handle or precision other than EB_F64 / EB_DF64");
+    return EB_ERR_INVALID;
+  }
+  b->b.outer = prec;
   return EB_OK;
 }
 

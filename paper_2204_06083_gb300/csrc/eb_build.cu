@@ -404,20 +404,34 @@ __device__ void rbf_curve(const LSDev& L, double t, Pt& g, Pt& g1, Pt& g2) {
 // samples, then Newton on (Gamma(t) - p) . Gamma'(t) = 0, steps limited to one
 // sample spacing
 constexpr int RBF_GUESS = 256;
-__device__ Pt rbf_closest(const LSDev& L, Pt p) {
+// The uniform samples are split over the 32 lanes of a warp (lane l takes
+// samples l, l + 32, ...); the nearest sample is the smallest distance with
+// the smallest index among equal ones -- the first minimum of the sequential
+// scan -- and every lane then runs the same Newton iteration from it.
+__device__ Pt rbf_closest(const LSDev& L, Pt p, int lane) {
   const double two_pi = 6.283185307179586;
   const double dmax = two_pi / RBF_GUESS;
-  double best = 1e300, t = 0.0;
+  double best = 1e300;
+  int kb = 0;
   Pt g, g1, g2;
-  for (int k = 0; k < RBF_GUESS; ++k) {
+  for (int k = lane; k < RBF_GUESS; k += 32) {
     const double tk = two_pi * k / RBF_GUESS;
     rbf_curve(L, tk, g, g1, g2);
     const double d = (g.x - p.x) * (g.x - p.x) + (g.y - p.y) * (g.y - p.y);
     if (d < best) {
       best = d;
-      t = tk;
+      kb = k;
     }
   }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int ok = __shfl_xor_sync(0xffffffffu, kb, o);
+    if (ob < best || (ob == best && ok < kb)) {
+      best = ob;
+      kb = ok;
+    }
+  }
+  double t = two_pi * kb / RBF_GUESS;
   for (int it = 0; it < 60; ++it) {
     rbf_curve(L, t, g, g1, g2);
     const double f = (g.x - p.x) * g1.x + (g.y - p.y) * g1.y;
@@ -521,7 +535,8 @@ __device__ bool rbf_weights(const Pt* q, double* w) {
   return isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]);
 }
 
-// One thread per RBF cut r (cut j = rbf_cut[r]): Algorithm 2 and the weights;
+// One warp per RBF cut r (cut j = rbf_cut[r]): Algorithm 2 and the weights
+// (the nearest-point searches split over the lanes, the rest on lane 0);
 // the cut's diagonal contribution becomes 1 - w_ij, its crossing G1 (distance
 // |x_BP - G1|), its first right-hand-side weight w_1; the second point G2 and
 // weight w_2 are stored per RBF cut.  bad = 1 if a system was singular or a
@@ -529,8 +544,9 @@ __device__ bool rbf_weights(const Pt* q, double* w) {
 __global__ void k_rbf(Geometry G, LSDev L, double eps, const int32_t* cp_node, const int32_t* rbf_cut, int64_t nrbf,
                       const int32_t* cut_cp, const int32_t* cut_dir, double* cut_c, double* cut_w1, double* cut_delta,
                       double* cut_xg, double* rbf_xg2, double* rbf_w, int32_t* rbf_rot, int* bad) {
-  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nrbf) return;
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= nrbf) return;  // whole warps: blockDim.x is a multiple of 32
   const int j = rbf_cut[r];
   const int64_t node = cp_node[cut_cp[j]];
   const int s = cut_dir[j];
@@ -540,8 +556,9 @@ __global__ void k_rbf(Geometry G, LSDev L, double eps, const int32_t* cp_node, c
   ij[axis] += sg;
   const Pt xbp{node_coord(G.lo[0], ij[0], G.h), node_coord(G.lo[1], ij[1], G.h)};
   const double h = G.h;
-  const Pt g1 = rbf_closest(L, xbp);
-  Pt g2 = rbf_closest(L, xij);
+  const Pt g1 = rbf_closest(L, xbp, lane);
+  Pt g2 = rbf_closest(L, xij, lane);
+  if (lane != 0) return;
   int rot = 0;
   if (!(hypot(g1.x - g2.x, g1.y - g2.y) > eps * h)) {
     const Pt v{g1.x - xbp.x, g1.y - xbp.y};
@@ -759,9 +776,9 @@ void build_handle(EBHandle& eb, const eb_grid& grid, const eb_levelset& ls, cuda
       k_rbf_list<<<blocks_for(nc, T), T, 0, s>>>(nc, flag, off, eb.rbf_cut, eb.cut_rbf);
       k_copy_f64<<<blocks_for(nc, T), T, 0, s>>>(nc, eb.cut_c, eb.cut_w1);  // w_1 = c_s on line-by-line cuts
       if (nr > 0)
-        k_rbf<<<blocks_for(nr, 64), 64, 0, s>>>(G, L, rbf_eps, eb.cp_node, eb.rbf_cut, nr, eb.cut_cp, eb.cut_dir,
-                                                eb.cut_c, eb.cut_w1, eb.cut_delta, eb.cut_xg, eb.rbf_xg2, eb.rbf_w,
-                                                eb.rbf_rot, bad);
+        k_rbf<<<blocks_for(32 * (int64_t)nr, 128), 128, 0, s>>>(G, L, rbf_eps, eb.cp_node, eb.rbf_cut, nr, eb.cut_cp,
+                                                                eb.cut_dir, eb.cut_c, eb.cut_w1, eb.cut_delta,
+                                                                eb.cut_xg, eb.rbf_xg2, eb.rbf_w, eb.rbf_rot, bad);
       const unsigned long long init = ~0ull;
       EB_CUDA(cudaMemcpyAsync(mkey, &init, sizeof(init), cudaMemcpyHostToDevice, s));
       k_diag_from_cuts<<<blocks_for(ncp, 128), 128, 0, s>>>(G, eb.cp_node, eb.code, eb.cut_off, eb.cut_c, ncp,

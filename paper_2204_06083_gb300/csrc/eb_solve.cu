@@ -640,7 +640,7 @@ void Solver::free_work() {
   if (cap_stream) cudaStreamDestroy(cap_stream);
   cap_stream = nullptr;
   dfree(r, s); dfree(z, s); dfree(p, s); dfree(q, s); dfree(tmp, s); dfree(part, s); dfree(sc, s); dfree(wx, s);
-  dfree(diag_df, s);
+  dfree(diag_df, s); dfree(xdf, s);
   if (sc_host) cudaFreeHost(sc_host);
   sc_host = nullptr;
 }
@@ -708,9 +708,10 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
       ++nlaunch;
       k_df_diag<<<nblk, TILE_NODES, 0, s>>>(eb->pairs(), eb->code, eb->diag, diag_df);
     }
+    if (!xdf) xdf = dalloc<double>(eb->g.num_nodes, s);
   }
-  // the vector the iteration updates: x itself, or its DF image in tmp
-  double* xi = df_on ? tmp : x;
+  // the vector the iteration updates: x itself, or its DF image
+  double* xi = df_on ? xdf : x;
   prof_begin(o.profile, s);
   nlaunch = 0;
   auto t0 = std::chrono::steady_clock::now();

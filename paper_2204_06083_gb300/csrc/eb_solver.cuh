@@ -100,10 +100,11 @@ struct Solver {
   const nn_handle* l_nn = nullptr;
   int64_t l_launches = 0;  // kernel launches per loop iteration
   // the DF outer iteration (pcg_opts.outer_prec = EB_DF64) for the current
-  // solve: x, r, p, q hold double-float pairs (x in tmp), z FP32; diag_df is
+  // solve: x, r, p, q hold double-float pairs (x in xdf), z FP32; diag_df is
   // the DF copy of the cut CPs' D_k (built on first use)
   bool df_on = false;
   float2* diag_df = nullptr;
+  double* xdf = nullptr;  // the DF image of x (tmp may hold the right-hand side)
   int g_df = -1, l_df = -1;
 
   void alloc_work(cudaStream_t s);
@@ -233,6 +234,7 @@ struct VcycleDot {
   const double* r = nullptr;
   double* part = nullptr;
   // the DF outer iteration: r holds double-float pairs, z is written in FP32
+  // (part null: no partials, z on every node of the active tiles)
   bool df = false;
 };
 // first_done: amg_update_first already did the first level-0 step for this r.
