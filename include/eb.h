@@ -500,6 +500,15 @@ int batch_set_profile(batch_handle* b, int on);
  * otherwise).  EB_F64 (the default) restores the FP64 iteration.
  * EB_ERR_INVALID for other values. */
 int batch_set_outer_prec(batch_handle* b, int prec);
+/* on != 0 (the default): the level-0 Chebyshev steps of the batched V-cycle
+ * (FP32 storage, tiles 16 to 128 nodes wide, batch row stride a multiple of 16
+ * nodes) stage each tile's x box with its halo, b, d and codes in shared
+ * memory through tensor copies (cp.async.bulk.tensor, a 4-stage ring) instead
+ * of loading them per thread; the results are the same bit for bit.  on = 0
+ * keeps the per-thread kernel (instrumentation: the paper has no
+ * counterpart).  A step whose bounded waits give up makes the next
+ * batch_heat_step return EB_ERR_TIMEOUT. */
+int batch_set_level0_tma(batch_handle* b, int on);
 /* One theta-method step of every geometry (heat_step semantics, warm start
  * from u), u overwritten.  stats: host array of count entries (may be NULL).
  * Returns EB_ERR_NO_CONVERGENCE if any geometry missed rtol.  Synchronous. */

@@ -157,6 +157,7 @@ _SIGS = {
     "batch_heat_step": (C.c_int, [_P, _P, _P, _P, C.c_double, C.c_int, _P, _P]),
     "batch_set_profile": (C.c_int, [_P, C.c_int]),
     "batch_set_outer_prec": (C.c_int, [_P, C.c_int]),
+    "batch_set_level0_tma": (C.c_int, [_P, C.c_int]),
     "nn_create": (C.c_int, [C.POINTER(_P), _P]),
     "nn_destroy": (None, [_P]),
     "nn_num_params": (C.c_int, []),
@@ -664,6 +665,10 @@ class Batch:
     def set_outer(self, prec):
         """batch_set_outer_prec: EB_DF64 runs the batched PCG in double-float, EB_F64 in FP64."""
         _check(load().batch_set_outer_prec(self._h, int(prec)))
+
+    def set_level0_tma(self, on: bool):
+        """batch_set_level0_tma: level-0 smoothing steps fed by tensor copies (default) or per-thread loads."""
+        _check(load().batch_set_level0_tma(self._h, int(bool(on))))
 
     def weighted_sum(self, w_all, u_all, stream=None):
         """Per-geometry sum of w u (batch_weighted_sum): a device tensor of count doubles."""

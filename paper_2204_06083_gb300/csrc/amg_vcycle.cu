@@ -16,6 +16,7 @@
 #include "amg_internal.cuh"
 #include "df.cuh"
 #include "stencil.cuh"
+#include "tma.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -333,6 +334,168 @@ __global__ void __launch_bounds__(TILE_NODES) k_g_cheb_step(TileView tv, const u
     const DF a = df_block_sum_df(srz_df, dsm);
     if (threadIdx.x == 0) df_part_store(part, blockIdx.x, a);
   }
+}
+
+// Level-0 Chebyshev step on a tile view without a pair list (batched grids,
+// 2D, FP32 storage), fed by tensor copies: per listed tile, one copy of the
+// x box with its halo (tx + 8 x ty + 2 nodes from (x0 - 4, y0 - 1): the
+// 16-byte aligned start left of the tile), and copies of the tile's b, d and
+// code boxes, into a ring of TS_STAGES shared-memory stages; one thread of
+// warp 4 issues them ahead while warps 0-3 (one node pair each) compute the
+// step from shared memory and store d and x' directly.  The arithmetic is
+// k_g_cheb_step's, operation for operation, so the results are the same bit
+// for bit; copies beyond the grid read zeros, where that kernel reads zeros
+// or values the node codes mask out.  Every wait is bounded: a wait that gives
+// up raises a shared abort flag, every role leaves its loop, *err is set, and
+// the copies in flight land (bounded wait) before the CTA ends.
+constexpr int TS_STAGES = 4;
+constexpr int TS_THREADS = 160;  // warps 0-3 compute, warp 4 copies
+constexpr uint32_t TS_SPIN = 1u << 22;
+
+struct TsMeta {
+  int32_t base, lim;
+  float sigma, dinv;
+};
+
+// shared-memory layout of one stage for tiles of tx x ty (x, b, d, code; 128-byte aligned)
+struct TsLayout {
+  int tx, ty, xw;  // xw = tx + 8: the x box width
+  uint32_t off_b, off_d, off_c, stage;
+  __host__ __device__ static uint32_t up128(uint32_t v) { return (v + 127u) & ~127u; }
+  __host__ __device__ TsLayout(int tx_, int ty_) : tx(tx_), ty(ty_), xw(tx_ + 8) {
+    off_b = up128((uint32_t)(xw * (ty + 2) * 4));
+    off_d = off_b + up128((uint32_t)(tx * ty * 4));
+    off_c = off_d + up128((uint32_t)(tx * ty * 4));
+    stage = off_c + up128((uint32_t)(tx * ty));
+  }
+};
+
+__device__ __forceinline__ bool ts_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+  for (uint32_t it = 0; it < TS_SPIN; ++it) {
+    uint32_t ok = 0;
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 63) == 63 && *abort) return false;
+  }
+  *abort = 1;
+  return false;
+}
+
+__device__ __forceinline__ void ts_copy2d(uint32_t dst, const CUtensorMap* map, int cx, int cy, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(cx), "r"(cy), "r"(bar)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(TS_THREADS) k_g_cheb_step_tma(
+    const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap bmap,
+    const __grid_constant__ CUtensorMap dmap, const __grid_constant__ CUtensorMap cmap, TileView tv, int tx, int ty,
+    const float* __restrict__ diag, GOp<float> o, float* __restrict__ xo, float* __restrict__ d, float c1, float c2,
+    int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char ts_smem[];
+  const TsLayout L(tx, ty);
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(ts_smem);
+  unsigned char* tail = ts_smem + TS_STAGES * L.stage;
+  TsMeta* meta = reinterpret_cast<TsMeta*>(tail);
+  const uint32_t bars = sbase + TS_STAGES * L.stage + TS_STAGES * (uint32_t)sizeof(TsMeta);  // 8-byte aligned
+  volatile int* abort = reinterpret_cast<volatile int*>(tail + TS_STAGES * sizeof(TsMeta) + 16 * TS_STAGES);
+  auto full = [&](int st) { return bars + 8 * st; };
+  auto empty = [&](int st) { return bars + 8 * (TS_STAGES + st); };
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool rd = c1 != 0.0f;
+  if (tid == 0) {
+    for (int st = 0; st < TS_STAGES; ++st) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full(st)));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(empty(st)));  // one arrive per compute warp
+    }
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncthreads();
+  const int64_t njob = tv.ntiles > (int64_t)blockIdx.x ? (tv.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int32_t S = tv.sy;
+  if (warp == 4) {
+    if (lane == 0) {
+      const uint32_t bytes = (uint32_t)(L.xw * (ty + 2) * 4 + tx * ty * 4 * (rd ? 2 : 1) + tx * ty);
+      int64_t k = 0;
+      for (; k < njob; ++k) {
+        const int st = (int)(k % TS_STAGES);
+        const uint32_t u = (uint32_t)(k / TS_STAGES);
+        if (u > 0 && !ts_wait(empty(st), (u - 1) & 1u, abort)) break;
+        const int64_t tt = blockIdx.x + k * gridDim.x;
+        const int32_t base = __ldg(tv.base + tt);
+        const float2 sh = tv.tshift32 ? __ldg(tv.tshift32 + tt) : make_float2(o.sigma, o.dinv_int);
+        meta[st] = TsMeta{base, __ldg(tv.lim + tt), sh.x, sh.y};
+        const int x0 = base % S, y0 = base / S;
+        const uint32_t sa = sbase + st * L.stage;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full(st)), "r"(bytes) : "memory");
+        ts_copy2d(sa, &xmap, x0 - 4, y0 - 1, full(st));
+        ts_copy2d(sa + L.off_b, &bmap, x0, y0, full(st));
+        if (rd) ts_copy2d(sa + L.off_d, &dmap, x0, y0, full(st));
+        ts_copy2d(sa + L.off_c, &cmap, x0, y0, full(st));
+      }
+      // copies still in flight (an aborted run) land before the CTA ends
+      for (int64_t q = k > TS_STAGES ? k - TS_STAGES : 0; q < k; ++q) {
+        volatile int never = 0;
+        ts_wait(full((int)(q % TS_STAGES)), (uint32_t)(q / TS_STAGES) & 1u, &never);
+      }
+    }
+  } else {
+    const int hp = tx >> 1;  // pairs per tile row
+    const int px = tid % hp, ly = tid / hp;
+    for (int64_t k = 0; k < njob; ++k) {
+      const int st = (int)(k % TS_STAGES);
+      const bool okw = ts_wait(full(st), (uint32_t)(k / TS_STAGES) & 1u, abort);
+      if (!__all_sync(0xffffffffu, okw)) {
+        *abort = 1;
+        break;
+      }
+      const TsMeta m = meta[st];
+      const unsigned char* sp = ts_smem + st * L.stage;
+      const float* sx = reinterpret_cast<const float*>(sp);
+      const float* sb = reinterpret_cast<const float*>(sp + L.off_b);
+      const float* sd = reinterpret_cast<const float*>(sp + L.off_d);
+      const uint8_t* sc = sp + L.off_c;
+      if (2 * px < (m.lim & 0xFF) && ly < ((m.lim >> 8) & 0xFF)) {
+        const int32_t node = m.base + 2 * px + ly * S;
+        GOp<float> ot = o;
+        ot.sigma = m.sigma;
+        ot.dinv_int = m.dinv;
+        const uint32_t k0 = sc[ly * tx + 2 * px], k1 = sc[ly * tx + 2 * px + 1];
+        const int row = (ly + 1) * L.xw + 4 + 2 * px;  // the pair's first node in the x box
+        const Two<float> xc{sx[row], sx[row + 1]};
+        const float left = sx[row - 1], right = sx[row + 2];
+        const Two<float> dn{sx[row - L.xw], sx[row - L.xw + 1]}, up{sx[row + L.xw], sx[row + L.xw + 1]};
+        // stencil_pair's sums, in its order
+        float s0 = ((k0 & 1) ? 0.0f : left) + ((k0 & 2) ? 0.0f : xc.y);
+        float s1 = ((k1 & 1) ? 0.0f : xc.x) + ((k1 & 2) ? 0.0f : right);
+        s0 += ((k0 & 4) ? 0.0f : dn.x) + ((k0 & 8) ? 0.0f : up.x);
+        s1 += ((k1 & 4) ? 0.0f : dn.y) + ((k1 & 8) ? 0.0f : up.y);
+        const float D0 = (k0 & 0x7F) ? __ldg(diag + node) : 4.0f;
+        const float D1 = (k1 & 0x7F) ? __ldg(diag + node + 1) : 4.0f;
+        const Two<float> core{D0 * xc.x - s0, D1 * xc.y - s1};
+        const int bi = ly * tx + 2 * px;
+        const Two<float> bv{sb[bi], sb[bi + 1]};
+        const Two<float> dv = rd ? Two<float>{sd[bi], sd[bi + 1]} : Two<float>{0.0f, 0.0f};
+        const float res0 = inv_diag_t<float>(k0, diag, node, ot) * (bv.x - (core.x * ot.inv_h2 + ot.sigma * xc.x));
+        const float res1 = inv_diag_t<float>(k1, diag, node + 1, ot) * (bv.y - (core.y * ot.inv_h2 + ot.sigma * xc.y));
+        const float d0 = (k0 & CODE_CP) ? c1 * dv.x + c2 * res0 : 0.0f;
+        const float d1 = (k1 & CODE_CP) ? c1 * dv.y + c2 * res1 : 0.0f;
+        st2(d + node, d0, d1);
+        st2(xo + node, (k0 & CODE_CP) ? xc.x + d0 : 0.0f, (k1 & CODE_CP) ? xc.y + d1 : 0.0f);
+      }
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(empty(st)) : "memory");
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && *abort) atomicExch(err, 1);
 }
 
 template <int DIM, class V>
@@ -732,6 +895,53 @@ static void vcycle_compact(Solver& S, size_t l, cudaStream_t s, bool warm = fals
   }
 }
 
+// tensor map of a 2D grid array (S columns x R rows, element size es) with boxes of bw x bh
+static CUtensorMap ts_map(const void* p, CUtensorMapDataType dt, int es, int64_t S, int64_t R, int bw, int bh) {
+  CUtensorMap m;
+  const cuuint64_t dims[2] = {(cuuint64_t)S, (cuuint64_t)R};
+  const cuuint64_t strides[1] = {(cuuint64_t)(S * es)};
+  const cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult rc = tensor_map_encoder()(&m, dt, 2, const_cast<void*>(p), dims, strides, box, estr,
+                                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  EB_REQUIRE(rc == CUDA_SUCCESS, EB_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)rc) + ")");
+  return m;
+}
+
+// whether the tensor-copy step applies to this view: 2D tiles without a pair
+// list, tiles 16 to 128 nodes wide (16-byte aligned code boxes, boxes of at
+// most 256), rows a multiple of 16 nodes (16-byte row pitch of the codes)
+static bool ts_eligible(const Solver& S, const EBHandle& eb) {
+  const TileView tv = eb.tv();
+  const int tx = 1 << tv.bx;
+  return S.l0_tma && eb.g.dim == 2 && !tv.pair_node && tv.ntiles > 0 && tx >= 16 && tx <= 128 && tv.sy % 16 == 0 &&
+         (int64_t)eb.g.num_nodes % tv.sy == 0;
+}
+
+// one level-0 Chebyshev step through k_g_cheb_step_tma (FP32 storage)
+static void ts_step(Solver& S, const EBHandle& eb, const GOp<float>& o, const float* b, const float* x, float* xo,
+                    float* d, float c1, float c2, cudaStream_t s) {
+  const TileView tv = eb.tv();
+  const int tx = 1 << tv.bx, ty = 1 << tv.by;
+  const int64_t Sx = tv.sy, R = (int64_t)eb.g.num_nodes / Sx;
+  const CUtensorMap xm = ts_map(x, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, Sx, R, tx + 8, ty + 2);
+  const CUtensorMap bm = ts_map(b, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, Sx, R, tx, ty);
+  const CUtensorMap dm = ts_map(d, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, Sx, R, tx, ty);
+  const CUtensorMap cm = ts_map(eb.code, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, Sx, R, tx, ty);
+  const TsLayout L(tx, ty);
+  const size_t smem = TS_STAGES * (size_t)L.stage + TS_STAGES * sizeof(TsMeta) + 16 * TS_STAGES + 16;
+  if (!S.dev_err) S.dev_err = dalloc<int>(1, s);
+  static size_t smem_set = 0;
+  if (smem > 48 * 1024 && smem > smem_set) {
+    EB_CUDA(cudaFuncSetAttribute(k_g_cheb_step_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    smem_set = smem;
+  }
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tv.ntiles, (int64_t)num_sms() * 8));
+  k_g_cheb_step_tma<<<grid, TS_THREADS, smem, s>>>(xm, bm, dm, cm, tv, tx, ty, diag_of<float>(eb), o, xo, d, c1, c2,
+                                                   S.dev_err);
+}
+
 template <class V, int DIM>
 static int vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, const VcycleDot* dot, bool first_done) {
   using LV = LevelView<V>;
@@ -775,9 +985,20 @@ static int vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, co
     k_g_cheb_first<DIM, V, true><<<gl, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, r, bcopy, x, g.d, (A)cc.theta);
   else
     k_g_cheb_first<DIM, V><<<gl, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, r, bcopy, x, g.d, (A)cc.theta);
+  // the tensor-copy step (batched 2D views, FP32 storage) or the sweep kernel
+  auto step = [&](const V* xin, V* xout, int k) {
+    if constexpr (std::is_same<V, float>::value && (DIM & (DIM_VB | DIM_LIST)) == 0 && dim_of(DIM) == 2) {
+      if (ts_eligible(S, eb)) {
+        ts_step(S, eb, o, b, xin, xout, g.d, (A)cc.c1[k], (A)cc.c2[k], s);
+        return;
+      }
+    }
+    k_g_cheb_step<DIM, V, V><<<gl, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, xin, xout, g.d, (A)cc.c1[k],
+                                                       (A)cc.c2[k]);
+  };
   for (int k = 1; k < cc.deg; ++k) {
     S.prof_mark(s, true);
-    k_g_cheb_step<DIM, V, V><<<gl, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, x, x2, g.d, (A)cc.c1[k], (A)cc.c2[k]);
+    step(x, x2, k);
     S.prof_mark(s, false);
     std::swap(x, x2);
   }
@@ -818,7 +1039,7 @@ static int vcycle_grid(Solver& S, const double* r, double* z, cudaStream_t s, co
       k_g_cheb_step<(DIM & ~DIM_LIST), V, double>
           <<<gb, TILE_NODES, 0, s>>>(tiles_only(tv), eb.code, diag, o, b, x, z, g.d, (A)cc.c1[k], (A)cc.c2[k]);
     else
-      k_g_cheb_step<DIM, V, V><<<gl, TILE_NODES, 0, s>>>(tv, eb.code, diag, o, b, x, x2, g.d, (A)cc.c1[k], (A)cc.c2[k]);
+      step(x, x2, k);
     if (mark) S.prof_mark(s, false);
     if (k != cc.deg - 1) std::swap(x, x2);
   }

@@ -66,6 +66,7 @@ struct Batch {
   // the current solve runs it, per-geometry powers of two into DF, the DF copy
   // of the cut CPs' diagonals; g_df / l_df key the captured graphs
   int outer = EB_F64;
+  bool l0_tma = true;  // batch_set_level0_tma, passed to the solver at setup
   bool df = false;
   double* gscale = nullptr;
   double* xdf = nullptr;  // the DF image of x (the solver's tmp holds the right-hand side)
@@ -1022,6 +1023,16 @@ static int batch_pcg(Batch& B, const double* b, double* x, double rtol, int maxi
   }
   const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   int worst = EB_OK;
+  if (S.dev_err) {  // a bounded wait of a tensor-copy smoothing step gave up
+    int e = 0;
+    EB_CUDA(cudaMemcpyAsync(&e, S.dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    EB_CUDA(cudaStreamSynchronize(s));
+    if (e) {
+      EB_CUDA(cudaMemsetAsync(S.dev_err, 0, sizeof(int), s));
+      set_error("batch_heat_step: a tensor-copy wait of the level-0 smoother gave up");
+      return EB_ERR_TIMEOUT;
+    }
+  }
   for (int g = 0; g < ng; ++g) {
     if (stats) {
       stats[g] = pcg_stats{};
@@ -1214,6 +1225,7 @@ int batch_heat_setup(batch_handle* b, const double* dt, double theta, const amg_
     B.S = new Solver();
     Solver& S = *B.S;
     S.eb = &B.view;
+    S.l0_tma = B.l0_tma;
     S.home = stream;
     S.shift = 0.0;  // per-tile shifts of the view take over
     S.opts = o;
@@ -1287,6 +1299,16 @@ int batch_set_profile(batch_handle* b, int on) {
     return EB_ERR_INVALID;
   }
   b->b.profile = on != 0;
+  return EB_OK;
+}
+
+int batch_set_level0_tma(batch_handle* b, int on) {
+  if (!b) {
+    set_error("batch_set_level0_tma: NULL handle");
+    return EB_ERR_INVALID;
+  }
+  b->b.l0_tma = on != 0;
+  if (b->b.S) b->b.S->l0_tma = b->b.l0_tma;
   return EB_OK;
 }
 

@@ -640,7 +640,7 @@ void Solver::free_work() {
   if (cap_stream) cudaStreamDestroy(cap_stream);
   cap_stream = nullptr;
   dfree(r, s); dfree(z, s); dfree(p, s); dfree(q, s); dfree(tmp, s); dfree(part, s); dfree(sc, s); dfree(wx, s);
-  dfree(diag_df, s); dfree(xdf, s);
+  dfree(diag_df, s); dfree(xdf, s); dfree(dev_err, s);
   if (sc_host) cudaFreeHost(sc_host);
   sc_host = nullptr;
 }

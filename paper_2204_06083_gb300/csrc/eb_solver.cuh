@@ -104,6 +104,10 @@ struct Solver {
   // the DF copy of the cut CPs' D_k (built on first use)
   bool df_on = false;
   float2* diag_df = nullptr;
+  // level-0 smoothing steps of batched 2D views through tensor copies (on by
+  // default; batch_set_level0_tma), and the device flag their bounded waits set
+  bool l0_tma = true;
+  int* dev_err = nullptr;
   double* xdf = nullptr;  // the DF image of x (tmp may hold the right-hand side)
   int g_df = -1, l_df = -1;
 

@@ -230,3 +230,45 @@ def test_full_size_batch_64_stars_matches_oracle():
             worst = max(worst, e)
             assert e <= tol, (outer, g, grids[g].n[0], e)
         print(f"64-star batch, 2 steps, outer {outer}: worst per-geometry rel-L2 {worst:.2e}")
+
+
+def test_batch_level0_tensor_copy_step_bit_identical():
+    """The level-0 Chebyshev steps fed by tensor copies (batch_set_level0_tma,
+    the default for FP32 batched V-cycles with tiles 16-128 nodes wide and a
+    row stride that is a multiple of 16 nodes) give the same heat step, bit
+    for bit, as the per-thread sweep kernel: the default 32 x 8 tiles, then
+    whatever shape the batch autotuner picks; also in double-float."""
+    import paper_2204_06083_gb300 as eb
+    grids, lss = _case((96, 128, 160, 112), (41, 42, 43, 44))
+    dts = [g.h for g in grids]
+    B = eb.Batch(grids, lss)
+    assert B.stride % 16 == 0
+    B.heat_setup(dts, theta=1.0, vcycle_prec=eb.EB_F32)
+    u0 = B.zeros()
+    mf = B.zeros()
+    ug = torch.zeros(max(B.num_cut, 1), dtype=torch.float64, device="cuda")
+    for g, gr in enumerate(grids):
+        X, Y = ei.grid_points(gr)
+        B.view(u0, g).copy_(torch.tensor(ei.u_heat(X, Y, 0.0)))
+        B.view(mf, g).copy_(torch.tensor(-ei.f_heat(X, Y, dts[g])))
+        xg = B.geometry(g).cuts()[3].cpu().numpy()
+        ug[B.cut_off[g]:B.cut_off[g + 1]] = torch.tensor(ei.u_heat(xg[:, 0], xg[:, 1], dts[g]))
+    b1 = B.rhs(mf, ug)
+
+    def run():
+        out = {}
+        for on in (True, False):
+            B.set_level0_tma(on)
+            u = u0.clone()
+            st = B.heat_step(u, b1, rtol=1e-10, maxit=300)
+            assert all(s.converged for s in st)
+            out[on] = (u, [s.iterations for s in st])
+        assert out[True][1] == out[False][1]
+        assert torch.equal(out[True][0], out[False][0])
+
+    run()
+    B.set_outer(eb.EB_DF64)
+    run()
+    B.set_outer(eb.EB_F64)
+    B.autotune(reps=3)
+    run()
