@@ -361,7 +361,8 @@ typedef struct {
                             FP64, and b and x cross to DF scaled by a power of two (the scaled b has a
                             unit root mean square).  The exit test is the FP64 true residual, as for
                             EB_F64.  EB_DF64 needs EB_PC_AMG with an FP32 or BF16 V-cycle of two or more
-                            levels and beta = 1 (EB_ERR_NOT_IMPLEMENTED otherwise) */
+                            levels (EB_ERR_NOT_IMPLEMENTED otherwise); a variable beta (eb_set_beta) enters
+                            through DF copies of beta at the half points and of D_k */
 } pcg_opts;
 
 typedef struct {
@@ -374,6 +375,14 @@ typedef struct {
   int prof_launches;         /* with opts.profile: their number */
   int64_t launches;          /* kernel launches this solve issued */
 } pcg_stats;
+
+/* The outer precision (pcg_opts.outer_prec) of the solves that take no
+ * options of their own: heat_step, wave_theta_step and pcg_solve with NULL
+ * opts.  EB_F64 (the default) or EB_DF64: double-float where that iteration
+ * applies (an FP32 or BF16 V-cycle of two or more levels), FP64 for the
+ * others (e.g. a hierarchy that a large shift leaves at one level).
+ * EB_ERR_INVALID for other values or a NULL handle. */
+int amg_set_outer_prec(amg_handle* amg, int prec);
 
 /* Solves (sigma I + A) x = b by PCG (Algorithm 1 step 4) with the
  * preconditioner of opts, stopping when ||r_k||_2 / ||b||_2 <= rtol; at exit

@@ -143,6 +143,7 @@ _SIGS = {
     "amg_info": (C.c_int, [_P, C.POINTER(amg_info_t)]),
     "amg_level_copy": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P, _P]),
     "amg_vcycle": (C.c_int, [_P, _P, _P, _P]),
+    "amg_set_outer_prec": (C.c_int, [_P, C.c_int]),
     "pcg_solve": (C.c_int, [_P, _P, _P, C.c_double, C.c_int, C.POINTER(pcg_opts), C.POINTER(pcg_stats), _P]),
     "heat_step": (C.c_int, [_P, C.c_double, C.c_double, _P, _P, _P, C.c_double, C.c_int, C.POINTER(pcg_stats), _P]),
     "wave_step": (C.c_int, [_P, C.c_int, C.c_double, _P, _P, C.c_int, _P]),
@@ -513,6 +514,10 @@ class AMG:
         _check(load().pcg_solve(self._h, _ptr(b), _ptr(x), float(rtol), int(maxit), C.byref(o), C.byref(st),
                                 _stream(stream)), allow=(EB_ERR_NO_CONVERGENCE,) if allow_noconv else ())
         return x, st
+
+    def set_outer(self, prec):
+        """amg_set_outer_prec: the outer precision of heat_step, wave_theta_step and option-less solves."""
+        _check(load().amg_set_outer_prec(self._h, int(prec)))
 
     def autotune(self, reps=20, stream=None) -> TuneResult:
         """Times V-cycles for every candidate tile shape of the grid and keeps the fastest."""

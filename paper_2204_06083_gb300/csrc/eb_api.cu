@@ -285,6 +285,15 @@ int amg_level_copy(const amg_handle* amg, int level, int which, int32_t* rowptr_
   return guarded([&] { amg_copy_level(amg->s, level, which, rowptr_dev, col_dev, val_dev, stream); });
 }
 
+int amg_set_outer_prec(amg_handle* amg, int prec) {
+  if (!amg || (prec != EB_F64 && prec != EB_DF64)) {
+    set_error("amg_set_outer_prec: NULL handle or precision other than EB_F64 / EB_DF64");
+    return EB_ERR_INVALID;
+  }
+  amg->s.outer_default = prec;
+  return EB_OK;
+}
+
 int amg_vcycle(const amg_handle* amg, const double* r_dev, double* z_dev, cudaStream_t stream) {
   if (!amg || !r_dev || !z_dev) {
     set_error("amg_vcycle: NULL argument");
@@ -302,7 +311,7 @@ int pcg_solve(const amg_handle* amg, const double* b_dev, double* x_dev, double 
     set_error("pcg_solve: NULL argument");
     return EB_ERR_INVALID;
   }
-  pcg_opts o{amg->s.H ? EB_PC_AMG : EB_PC_JACOBI, 1, 1, 0};
+  pcg_opts o{amg->s.H ? EB_PC_AMG : EB_PC_JACOBI, 1, 1, 0, amg->s.default_outer()};
   if (opts) o = *opts;
   int rc = EB_OK;
   int st = guarded([&] { rc = const_cast<Solver&>(amg->s).pcg(b_dev, x_dev, rtol, maxit, o, stats, stream); });

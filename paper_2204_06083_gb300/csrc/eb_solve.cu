@@ -251,12 +251,11 @@ __global__ void __launch_bounds__(TILE_NODES) k_xpby_apply(TileView tv, PairList
 // the FP64 path's redundant per-CTA sums cost FP64 issue slots -- and rounded
 // to FP64 once; alpha and beta are FP64 ratios, split into DF once per CTA.
 
-// The end of an iteration (k_xpby_apply in DF): p = z + beta p, q = B z + beta
-// q, the p.q partials.  B z is the unit stencil D_k z_k - sum of the
-// CP-neighbour values on the FP32 z: the neighbours by cascaded summation
-// (TwoSum errors collected), D_k z_k an exact product (interior points) or a
-// DF one (cut points), plus sigma h^2 z_k when SHIFT.  beta = 1 only (no
-// variable coefficient).
+// the DF copies of beta at the half points, per axis (variable coefficient)
+struct DfBeta {
+  const float2* b[3] = {nullptr, nullptr, nullptr};
+};
+
 // one pair's inputs of k_xpby_apply_df
 struct XpIn {
   uint32_t c0, c1;
@@ -278,7 +277,7 @@ __device__ __forceinline__ void xp_load(XpIn& in, const TileView& tv, const uint
   in.up = node + sy < nn ? __ldg(reinterpret_cast<const float2*>(z + node + sy)) : zero;
   in.bk = zero;
   in.fr = zero;
-  if (DIM == 3) {
+  if (dim_of(DIM) == 3) {
     in.bk = node >= sz ? __ldg(reinterpret_cast<const float2*>(z + node - sz)) : zero;
     in.fr = node + sz < nn ? __ldg(reinterpret_cast<const float2*>(z + node + sz)) : zero;
   }
@@ -288,14 +287,13 @@ __device__ __forceinline__ void xp_load(XpIn& in, const TileView& tv, const uint
   }
 }
 
-// p, q of one pair from its inputs; returns the pair's p.q terms added to s
-template <int DIM, bool SHIFT>
-__device__ __forceinline__ void xp_compute(const XpIn& in, const float2* diag_df, DF sig_h2, DF beta, int first,
-                                           double* p, double* q, int32_t node, DF& s) {
+// B z at the pair, beta = 1: the neighbour sums by cascaded summation, then
+// D_k z_k (an exact product: D_k = 2 dim at interior points, DF for cut ones)
+// minus them
+template <int D>
+__device__ __forceinline__ void xp_unit(const XpIn& in, const float2* diag_df, int32_t node, DF& a0, DF& a1) {
   const uint32_t c0 = in.c0, c1 = in.c1;
   const float2 zc = in.zc;
-  // the neighbour sums by cascaded summation, then D_k z_k (an exact product:
-  // D_k = 2 dim at interior points, DF for cut ones) minus them
   Sum2 s0 = sum2_start((c0 & 1) ? 0.0f : in.left), s1 = sum2_start((c1 & 1) ? 0.0f : zc.x);
   sum2_add(s0, (c0 & 2) ? 0.0f : zc.y);
   sum2_add(s1, (c1 & 2) ? 0.0f : in.right);
@@ -303,13 +301,13 @@ __device__ __forceinline__ void xp_compute(const XpIn& in, const float2* diag_df
   sum2_add(s1, (c1 & 4) ? 0.0f : in.dn.y);
   sum2_add(s0, (c0 & 8) ? 0.0f : in.up.x);
   sum2_add(s1, (c1 & 8) ? 0.0f : in.up.y);
-  if (DIM == 3) {
+  if (D == 3) {
     sum2_add(s0, (c0 & 16) ? 0.0f : in.bk.x);
     sum2_add(s1, (c1 & 16) ? 0.0f : in.bk.y);
     sum2_add(s0, (c0 & 32) ? 0.0f : in.fr.x);
     sum2_add(s1, (c1 & 32) ? 0.0f : in.fr.y);
   }
-  float d0h = (float)(2 * DIM), d0l = 0.0f, d1h = d0h, d1l = 0.0f;
+  float d0h = (float)(2 * D), d0l = 0.0f, d1h = d0h, d1l = 0.0f;
   if (c0 & 0x7F) {
     const float2 t = __ldg(diag_df + node);
     d0h = t.x;
@@ -325,7 +323,48 @@ __device__ __forceinline__ void xp_compute(const XpIn& in, const float2* diag_df
   two_prod(d1h, zc.y, pr1, pe1);
   pe0 = __fmaf_rn(d0l, zc.x, pe0);
   pe1 = __fmaf_rn(d1l, zc.y, pe1);
-  DF a0 = df_prod_minus_sum2(pr0, pe0, s0), a1 = df_prod_minus_sum2(pr1, pe1, s1);
+  a0 = df_prod_minus_sum2(pr0, pe0, s0);
+  a1 = df_prod_minus_sum2(pr1, pe1, s1);
+}
+
+// B z at the pair with a variable coefficient (eq. 3): D_k z_k minus the sum
+// over the CP neighbours of beta_j z_j, beta_j at the half point between the
+// node and the neighbour (beta_df: DF copies per axis), D_k read at every CP;
+// the products in DF, summed by the two-step DF sum
+template <int D>
+__device__ __forceinline__ void xp_varbeta(const XpIn& in, const float2* diag_df, const float2* const* beta_df,
+                                           int32_t node, int32_t sy, int32_t sz, DF& a0, DF& a1) {
+  const uint32_t c0 = in.c0, c1 = in.c1;
+  auto term = [&](uint32_t masked, int a, int32_t at, float v) {
+    if (masked) return DF{0.0f, 0.0f};
+    const float2 t = __ldg(beta_df[a] + at);
+    return df_mul_f(DF{t.x, t.y}, v);
+  };
+  DF s0 = df_add_fast(term(c0 & 1, 0, node - 1, in.left), term(c0 & 2, 0, node, in.zc.y));
+  DF s1 = df_add_fast(term(c1 & 1, 0, node, in.zc.x), term(c1 & 2, 0, node + 1, in.right));
+  s0 = df_add_fast(s0, df_add_fast(term(c0 & 4, 1, node - sy, in.dn.x), term(c0 & 8, 1, node, in.up.x)));
+  s1 = df_add_fast(s1, df_add_fast(term(c1 & 4, 1, node - sy + 1, in.dn.y), term(c1 & 8, 1, node + 1, in.up.y)));
+  if (D == 3) {
+    s0 = df_add_fast(s0, df_add_fast(term(c0 & 16, 2, node - sz, in.bk.x), term(c0 & 32, 2, node, in.fr.x)));
+    s1 = df_add_fast(s1, df_add_fast(term(c1 & 16, 2, node - sz + 1, in.bk.y), term(c1 & 32, 2, node + 1, in.fr.y)));
+  }
+  const float2 e0 = (c0 & CODE_CP) ? __ldg(diag_df + node) : make_float2(0.0f, 0.0f);
+  const float2 e1 = (c1 & CODE_CP) ? __ldg(diag_df + node + 1) : make_float2(0.0f, 0.0f);
+  a0 = df_sub(df_mul_f(DF{e0.x, e0.y}, in.zc.x), s0);
+  a1 = df_sub(df_mul_f(DF{e1.x, e1.y}, in.zc.y), s1);
+}
+
+// p, q of one pair from its inputs; the pair's p.q terms added to s.  DIM
+// carrying DIM_VB: the variable-coefficient stencil
+template <int DIM, bool SHIFT>
+__device__ __forceinline__ void xp_compute(const XpIn& in, const float2* diag_df, DF sig_h2, DF beta, int first,
+                                           double* p, double* q, int32_t node, DF& s, const float2* const* beta_df,
+                                           int32_t sy, int32_t sz) {
+  const uint32_t c0 = in.c0, c1 = in.c1;
+  const float2 zc = in.zc;
+  DF a0, a1;
+  if constexpr ((DIM & DIM_VB) != 0) xp_varbeta<dim_of(DIM)>(in, diag_df, beta_df, node, sy, sz, a0, a1);
+  else xp_unit<dim_of(DIM)>(in, diag_df, node, a0, a1);
   if (SHIFT) {
     a0 = df_add(a0, df_mul_f(sig_h2, zc.x));
     a1 = df_add(a1, df_mul_f(sig_h2, zc.y));
@@ -349,8 +388,9 @@ __device__ __forceinline__ void xp_compute(const XpIn& in, const float2* diag_df
 // q, the p.q partials.  B z is the unit stencil D_k z_k - sum of the
 // CP-neighbour values on the FP32 z: the neighbours by cascaded summation
 // (TwoSum errors collected), D_k z_k an exact product (interior points) or a
-// DF one (cut points), plus sigma h^2 z_k when SHIFT.  beta = 1 only (no
-// variable coefficient).  The loads of a thread's first pair are issued before
+// DF one (cut points), plus sigma h^2 z_k when SHIFT; with a variable
+// coefficient (DIM_VB) the beta-weighted form of xp_varbeta.  The loads of a
+// thread's first pair are issued before
 // the partial sums that give beta (the pass is bound by its load latency; a
 // double-buffered loop that also issued each pair's loads before the previous
 // pair's arithmetic was no faster).
@@ -360,7 +400,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_xpby_apply_df(TileView tv, PairL
                                                               const float* z, double* p, double* q, int first,
                                                               const double* rz_part, int nrz, const double* rzo_part,
                                                               int nupd, double* pq_part, const double* rr_part,
-                                                              cudaGraphConditionalHandle h) {
+                                                              cudaGraphConditionalHandle h, DfBeta bdf) {
   __shared__ DF dsm[32];
   __shared__ DF s_beta;
   if (cta_done(sc)) {
@@ -414,7 +454,7 @@ __global__ void __launch_bounds__(TILE_NODES) k_xpby_apply_df(TileView tv, PairL
   while (li < pl.n) {
     const int64_t ln = li + step;
     const int32_t nnode = ln < pl.n ? __ldg(pl.node + ln) : 0;
-    xp_compute<DIM, SHIFT>(cur, diag_df, sig_h2, beta, first, p, q, node, s);
+    xp_compute<DIM, SHIFT>(cur, diag_df, sig_h2, beta, first, p, q, node, s, bdf.b, tv.sy, tv.sz);
     if (ln < pl.n) xp_load<DIM>(cur, tv, code, z, p, q, first, nnode);
     li = ln;
     node = nnode;
@@ -444,8 +484,17 @@ __global__ void __launch_bounds__(TILE_NODES) k_df_out(PairList pl, const double
   }
 }
 
+// the DF copy of one axis of beta (every node: the stencil reads it at the
+// neighbours' half points)
+__global__ void k_df_full(int64_t n, const double* __restrict__ v, float2* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const DF d = df_from_double(v[i]);
+    out[i] = make_float2(d.hi, d.lo);
+  }
+}
+
 // the DF copy of the cut CPs' diagonals D_k (the interior value 2 dim is
-// formed in the kernel)
+// formed in the kernel; with a variable coefficient every CP's D_k)
 __global__ void __launch_bounds__(TILE_NODES) k_df_diag(PairList pl, const uint8_t* code, const double* diag,
                                                         float2* out) {
   EB_LIST_LOOP(pl, node) {
@@ -641,6 +690,7 @@ void Solver::free_work() {
   cap_stream = nullptr;
   dfree(r, s); dfree(z, s); dfree(p, s); dfree(q, s); dfree(tmp, s); dfree(part, s); dfree(sc, s); dfree(wx, s);
   dfree(diag_df, s); dfree(xdf, s); dfree(dev_err, s);
+  for (auto& bd : beta_df) dfree(bd, s);
   if (sc_host) cudaFreeHost(sc_host);
   sc_host = nullptr;
 }
@@ -678,6 +728,13 @@ void Solver::precondition(int kind, const double* rin, double* zout, cudaStream_
   }
 }
 
+// the outer precision of the option-less solves: outer_default where the DF
+// iteration applies (AMG with a reduced-precision V-cycle of two or more
+// levels), else FP64
+int Solver::default_outer() const {
+  return (outer_default == EB_DF64 && H && flexible() && amg_levels(*this) > 1) ? EB_DF64 : EB_F64;
+}
+
 int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_opts& o, pcg_stats* stats,
                 cudaStream_t s) {
   const int dim = eb->g.dim;
@@ -701,12 +758,22 @@ int Solver::pcg(const double* b, double* x, double rtol, int maxit, const pcg_op
     EB_REQUIRE(kind == EB_PC_AMG && flexible() && amg_levels(*this) > 1, EB_ERR_NOT_IMPLEMENTED,
                "pcg: the DF outer iteration needs the AMG preconditioner with an FP32 or BF16 V-cycle of at least "
                "two levels");
-    EB_REQUIRE(!eb->has_beta(), EB_ERR_NOT_IMPLEMENTED,
-               "pcg: the DF outer iteration has no variable-coefficient stencil");
-    if (!diag_df) {
-      diag_df = dalloc<float2>(eb->g.num_nodes, s);
+    // the DF copies of D_k and beta, rebuilt when the handle's geometry, tiles
+    // or beta changed (tile_gen)
+    if (!diag_df || df_gen != eb->tile_gen) {
+      if (!diag_df) diag_df = dalloc<float2>(eb->g.num_nodes, s);
       ++nlaunch;
       k_df_diag<<<nblk, TILE_NODES, 0, s>>>(eb->pairs(), eb->code, eb->diag, diag_df);
+      for (int a = 0; a < 3; ++a) {
+        if (eb->has_beta() && a < eb->g.dim) {
+          if (!beta_df[a]) beta_df[a] = dalloc<float2>(eb->g.num_nodes, s);
+          ++nlaunch;
+          k_df_full<<<(unsigned)(num_sms() * 8), 256, 0, s>>>(eb->g.num_nodes, eb->beta64[a], beta_df[a]);
+        } else {
+          dfree(beta_df[a], s);
+        }
+      }
+      df_gen = eb->tile_gen;
     }
     if (!xdf) xdf = dalloc<double>(eb->g.num_nodes, s);
   }
@@ -846,7 +913,9 @@ int Solver::heat(double dt, double theta, const double* b1, const double* b0, do
   EB_DIMV_LAUNCH(*eb, k_heat_rhs, nblk, eb->tv(), eb->code, eb->diag, 1.0 / (G.h * G.h), dt, theta, u, b1,
                 b0 ? b0 : b1, tmp);
   EB_CUDA(cudaGetLastError());
-  pcg_opts o{H ? EB_PC_AMG : EB_PC_JACOBI, 1, 1, 0};  // the loop on the device (tmp and u keep their addresses)
+  // the loop on the device (tmp and u keep their addresses); the solver's
+  // default outer precision (amg_set_outer_prec) where it applies
+  pcg_opts o{H ? EB_PC_AMG : EB_PC_JACOBI, 1, 1, 0, default_outer()};
   return pcg(tmp, u, rtol, maxit, o, stats, s);
 }
 
@@ -865,7 +934,7 @@ int Solver::wave_theta(double dt, double theta, double* ua, double* ub, int nste
   const double c = (1.0 - 2.0 * theta) / theta;
   const double inv_h2 = 1.0 / (G.h * G.h);
   const TileView tv = eb->tv();
-  pcg_opts o{H ? EB_PC_AMG : EB_PC_JACOBI, 1, 1, 0};
+  pcg_opts o{H ? EB_PC_AMG : EB_PC_JACOBI, 1, 1, 0, default_outer()};
   pcg_stats total{};
   total.converged = 1;
   int rc = EB_OK;
@@ -919,12 +988,13 @@ void Solver::xpby_apply(const OpParams& op, bool flex, int first, cudaStream_t s
     if (df_on) {
       const DF sig = df_from_double(op.sigma_h2);
       const float* zf = reinterpret_cast<const float*>(z);
-      if (dim == 2)
-        k_xpby_apply_df<2, SH, CO><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, eb->code, diag_df, sig, zf, p, q, first,
-                                                            part_rz(), rz_n, rzo, (int)g, part_pq(), part_rr(), h);
-      else
-        k_xpby_apply_df<3, SH, CO><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, eb->code, diag_df, sig, zf, p, q, first,
-                                                            part_rz(), rz_n, rzo, (int)g, part_pq(), part_rr(), h);
+      DfBeta bdf;
+      for (int a = 0; a < 3; ++a) bdf.b[a] = beta_df[a];
+      dim_dispatch(*eb, [&](auto D) {
+        k_xpby_apply_df<D.value, SH, CO><<<g, TILE_NODES, 0, s>>>(tv, pl, sc, eb->code, diag_df, sig, zf, p, q, first,
+                                                                  part_rz(), rz_n, rzo, (int)g, part_pq(), part_rr(),
+                                                                  h, bdf);
+      });
       return;
     }
     launch_xpby_apply<SH, CO>(*eb, g, s, tv, pl, sc, eb->code, eb->diag, op, z, p, q, first, part_rz(), rz_n, rzo,

@@ -104,6 +104,12 @@ struct Solver {
   // the DF copy of the cut CPs' D_k (built on first use)
   bool df_on = false;
   float2* diag_df = nullptr;
+  float2* beta_df[3] = {nullptr, nullptr, nullptr};  // DF copies of beta per axis (variable coefficient)
+  int df_gen = -1;  // the handle's tile_gen the DF copies were built for
+  // outer precision of the solves without their own options: heat_step,
+  // wave_theta_step, pcg_solve with NULL opts (amg_set_outer_prec)
+  int outer_default = EB_F64;
+  int default_outer() const;
   // level-0 smoothing steps of batched 2D views through tensor copies (on by
   // default; batch_set_level0_tma), and the device flag their bounded waits set
   bool l0_tma = true;

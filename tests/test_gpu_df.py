@@ -10,8 +10,12 @@ EB_DF64) against the oracle and against the FP64 outer iteration.
   order).
 * Exact power-of-two scaling: b 2^-100 and b 2^100 give x 2^-100 and x 2^100
   bit for bit (the DF image of b is rescaled to a unit root mean square).
-* A warm start, b = 0, and the cases DF does not cover (variable beta, Jacobi,
-  an FP64 V-cycle, a bad outer_prec).
+* A warm start, b = 0, and the cases DF does not cover (Jacobi, an FP64
+  V-cycle, a bad outer_prec).
+* A variable coefficient (eq. 3): DF solves against the exact oracle solve;
+  Crank-Nicolson heat steps and theta-scheme wave steps through the solver's
+  default outer precision (amg_set_outer_prec) against the FP64 outer
+  iteration.
 """
 import numpy as np
 import pytest
@@ -152,9 +156,102 @@ def test_df_rejects_what_it_does_not_cover():
     with pytest.raises(eb.EBError) as e:
         g32.solve(b, outer=7)
     assert e.value.code == eb.EB_ERR_INVALID
-    hb = eb.EB(grid, ls)
-    hb.set_beta(ei.beta_half_points(grid, ei.beta_bone))
-    gb = eb.AMG(hb, 0.0, vcycle_prec=eb.EB_F32)
     with pytest.raises(eb.EBError) as e:
-        gb.solve(b, outer=eb.EB_DF64)
-    assert e.value.code == eb.EB_ERR_NOT_IMPLEMENTED
+        g32.set_outer(5)
+    assert e.value.code == eb.EB_ERR_INVALID
+
+
+BETA_CASES = {
+    "circle130_bone": lambda: (*ei.circle_k1(130), ei.beta_bone),
+    "disk128_heat": lambda: (*ei.heat_disk(128), ei.beta_heat_disk),
+    "ellipsoid42_lin": lambda: (*ei.ellipsoid_k3(42, seed=0), lambda x, y, z: 1.5 + 0.4 * x - 0.3 * y + 0.2 * z),
+}
+
+
+@pytest.mark.parametrize("name", list(BETA_CASES))
+def test_df_pcg_variable_beta_matches_oracle(name):
+    """The DF outer iteration with a variable coefficient (eq. 3): beta at the
+    half points and D_k enter through DF copies; solutions to rtol 1e-12 match
+    the exact oracle solve within rel-L2 1e-8, and the iteration count to
+    1e-10 equals the FP64 outer iteration's within 1."""
+    import scipy.sparse.linalg as spla
+    eb = _eb()
+    grid, ls, bfun = BETA_CASES[name]()
+    betas = ei.beta_half_points(grid, bfun)
+    h = eb.EB(grid, ls)
+    h.set_beta(betas)
+    ref = oeb.build(grid, ls, beta=betas)
+    b_cp = np.random.default_rng(3).standard_normal(ref.num_cp)
+    b = torch.tensor(ref.to_grid(b_cp), device="cuda")
+    x_ref = spla.spsolve(ref.A.tocsc(), b_cp)
+    g = eb.AMG(h, 0.0, vcycle_prec=eb.EB_F32)
+    x, st = g.solve(b, rtol=1e-12, maxit=800, outer=eb.EB_DF64)
+    got = ref.from_grid(x.cpu().numpy())
+    err = np.linalg.norm(got - x_ref) / np.linalg.norm(x_ref)
+    print(f"{name}: DF its {st.iterations}, true rel res {st.true_rel_residual:.2e}, rel-L2 vs exact {err:.2e}")
+    assert st.converged and st.true_rel_residual <= 1e-12
+    assert err <= 1e-8
+    _, s64 = g.solve(b, rtol=1e-10, maxit=800)
+    _, sdf = g.solve(b, rtol=1e-10, maxit=800, outer=eb.EB_DF64)
+    assert abs(s64.iterations - sdf.iterations) <= 1
+
+
+def test_df_crank_nicolson_and_theta_wave_match_fp64():
+    """amg_set_outer_prec(EB_DF64): heat_step (Crank-Nicolson on the Sec. 3.4
+    disk with beta = 0.25 - r^2) and wave_theta_step run their solves in
+    double-float; after 5 steps the fields match those of the FP64 outer
+    iteration within rel-L2 1e-9 (both solve to 1e-11), with iteration totals
+    within 1 per step (heat); a single-level hierarchy runs FP64."""
+    eb = _eb()
+    grid, ls = ei.heat_disk(130)
+    betas = ei.beta_half_points(grid, ei.beta_heat_disk)
+    h = eb.EB(grid, ls)
+    h.set_beta(betas)
+    X, Y = ei.grid_points(grid)
+    dt, theta = grid.h, 0.5
+    zc = torch.zeros(max(h.info.num_cut, 1), dtype=torch.float64, device="cuda")
+    out = {}
+    for outer in (eb.EB_F64, eb.EB_DF64):
+        g = eb.AMG(h, 1.0 / (theta * dt), vcycle_prec=eb.EB_F32)
+        g.set_outer(outer)
+        u = torch.tensor(ei.u_heat_disk(X, Y, 0.0), device="cuda")
+        b0 = h.rhs(torch.tensor(-ei.f_heat_disk(X, Y, 0.0), device="cuda"), zc)
+        its = []
+        for k in range(5):
+            b1 = h.rhs(torch.tensor(-ei.f_heat_disk(X, Y, (k + 1) * dt), device="cuda"), zc)
+            st = g.heat_step(u, b1, dt, theta=theta, b0=b0, rtol=1e-11, maxit=300)
+            assert st.converged and st.true_rel_residual <= 1e-11
+            its.append(st.iterations)
+            b0 = b1
+        out[outer] = (u, its)
+    u64, udf = out[eb.EB_F64][0], out[eb.EB_DF64][0]
+    assert (torch.linalg.norm(udf - u64) / torch.linalg.norm(u64)).item() <= 1e-9
+    assert all(abs(a - b) <= 1 for a, b in zip(out[eb.EB_F64][1], out[eb.EB_DF64][1]))
+    # theta-scheme wave steps (theta = 1/4, dt = 2h: a shift that leaves the
+    # hierarchy two levels deep) on the same disk
+    dtw, th = 2.0 * grid.h, 0.25
+    wout = {}
+    for outer in (eb.EB_F64, eb.EB_DF64):
+        g = eb.AMG(h, 1.0 / (th * dtw * dtw), vcycle_prec=eb.EB_F32)
+        g.set_outer(outer)
+        ua = torch.tensor(np.exp(-40.0 * (X ** 2 + Y ** 2)), device="cuda")
+        ub = ua.clone()
+        st = g.wave_theta_step(ua, ub, dtw, th, 5, rtol=1e-11)
+        assert st.converged
+        wout[outer] = (ub.clone(), st.iterations)
+    w64, wdf = wout[eb.EB_F64][0], wout[eb.EB_DF64][0]
+    assert (torch.linalg.norm(wdf - w64) / torch.linalg.norm(w64)).item() <= 1e-9
+    assert abs(wout[eb.EB_F64][1] - wout[eb.EB_DF64][1]) <= 5
+    # theta = 1/12, dt = 0.85 h: the shift leaves one level, where the default
+    # outer precision falls back to FP64 -- the same result bit for bit
+    dtw, th = 0.85 * grid.h, 1.0 / 12.0
+    res = []
+    for outer in (eb.EB_F64, eb.EB_DF64):
+        g = eb.AMG(h, 1.0 / (th * dtw * dtw), vcycle_prec=eb.EB_F32)
+        assert g.num_levels == 1
+        g.set_outer(outer)
+        ua = torch.tensor(np.exp(-40.0 * (X ** 2 + Y ** 2)), device="cuda")
+        ub = ua.clone()
+        g.wave_theta_step(ua, ub, dtw, th, 3, rtol=1e-11)
+        res.append(ub)
+    assert torch.equal(res[0], res[1])
