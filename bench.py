@@ -960,8 +960,9 @@ def stencil_subrecords(ctx, args, h3):
     """The metric's stencil GB/s beside the solve: eb_apply on the solve's own
     256^3 grid (FP64 and FP32) and the leapfrog step of the 4096^2 star wave
     workload (FP32 and FP64, 320 steps = 10 graph chunks per timed call), each
-    against the measured HBM peak.  Algorithmic bytes per DOF: apply 16 (FP64)
-    / 8 (FP32): x read, y written; leapfrog 25 / 13: u^n, u^{n-1} read, u^{n+1}
+    against the measured HBM peak (the FP64 apply against the measured FP64
+    peak, which bounds it).  Algorithmic bytes per DOF: apply 16 (FP64) / 8
+    (FP32): x read, y written; leapfrog 25 / 13: u^n, u^{n-1} read, u^{n+1}
     written, the code byte."""
     from paper_2204_06083_gb300 import autotune
     import torch
@@ -971,29 +972,45 @@ def stencil_subrecords(ctx, args, h3):
     out = {}
     nc = h3.info.num_cp
     rng = torch.Generator(device=ctx.dev).manual_seed(5)
+    fp64_tflops = eb.fp64_peak_tflops(reps=20)
+    dim = len(h3.shape())
+    # FP64 instructions per CP of the apply: the 2 dim - 1 adds of the
+    # neighbour sum, D x - sum (one FMA), then core / h^2 + sigma x (a multiply
+    # and an FMA); the FP64 FMA peak (an FMA counted as 2 FLOP) issues half as
+    # many instructions
+    f64_instr = (2 * dim - 1 + 3) * nc
     for name, dtype, bpd in (("apply_256cubed_f64", torch.float64, 16), ("apply_256cubed_f32", torch.float32, 8)):
         xin = torch.randn(h3.shape(), generator=rng, device=ctx.dev, dtype=torch.float64).to(dtype)
         y = torch.zeros_like(xin)
         for _ in range(3):
             h3.apply(xin, out=y)
-        cold = []
-        for i in range(3 + args.steps):
-            ctx.flush()
-            torch.cuda.synchronize()
-            t, _ = timed(lambda: h3.apply(xin, out=y))
-            if i >= 3:
-                cold.append(t)
-        reps = 50
-        tw, _ = timed(lambda: [h3.apply(xin, out=y) for _ in range(reps)])
-        cold_s = statistics.mean(cold) / 1000.0
-        warm_s = tw / reps / 1000.0
-        out[name] = {"bound": "hbm", "kernel": "k_apply (eb_apply, matrix free, active tiles)",
-                     "achieved": bpd * nc / cold_s / 1e9, "peak": hbm, "unit": "GB/s",
-                     "frac": bpd * nc / cold_s / 1e9 / hbm, "algorithmic_bytes_per_launch": bpd * nc,
-                     "avg_launch_us": cold_s * 1e6,
-                     "timing": "one launch between CUDA events after a 512 MB L2 flush (DRAM-cold; the event "
-                               "pair's few microseconds included)",
-                     "warm_us": warm_s * 1e6, "warm_frac": bpd * nc / warm_s / 1e9 / hbm}
+        cold_us = h3.time_apply_us(xin, y, launches=20, clear_bytes=L2_CLEAR_BYTES)
+        warm_us = h3.time_apply_us(xin, y, launches=50)
+        copy_us = eb.time_copy_us(bpd * nc, launches=20, clear_bytes=L2_CLEAR_BYTES)
+        gbs = bpd * nc / (cold_us * 1e-6) / 1e9
+        rec = {"bound": "hbm", "kernel": f"k_apply<{'double' if dtype == torch.float64 else 'float'}, {dim}> "
+                                         "(eb_apply, matrix free, one CP pair per thread)",
+               "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+               "algorithmic_bytes_per_launch": bpd * nc, "avg_launch_us": cold_us,
+               "timing": "eb_time_apply: 20 back-to-back launches in one CUDA graph, CUDA events around the "
+                         "graph, each launch after a 512 MB read that leaves none of its data in L2 (the "
+                         "read's own time subtracted)",
+               "warm_us": warm_us, "warm_frac": bpd * nc / (warm_us * 1e-6) / 1e9 / hbm,
+               "size_matched_copy": {"copy_us": copy_us, "frac_of_copy": copy_us / cold_us}}
+        if dtype == torch.float64:
+            # the FP64 pipe, not HBM, bounds the FP64 apply on this part
+            instr_rate = fp64_tflops / 2.0 * 1e12
+            rec.update({"bound": "alu", "unit": "TFLOP/s", "peak": fp64_tflops,
+                        "achieved": 2.0 * f64_instr / (cold_us * 1e-6) / 1e12,
+                        "frac": f64_instr / (cold_us * 1e-6) / instr_rate,
+                        "peak_kind": "measured FP64 FMA throughput (eb_fp64_peak, this run)",
+                        "algorithmic_fp64_instructions_per_launch": f64_instr,
+                        "achieved_note": "FP64 instructions per second x 2 (the peak's FLOP per FMA)",
+                        "hbm_GBs": gbs, "hbm_frac": gbs / hbm,
+                        "alu_bound_us": f64_instr / instr_rate * 1e6,
+                        "warm_alu_frac": f64_instr / (warm_us * 1e-6) / instr_rate})
+            del rec["warm_frac"]
+        out[name] = rec
         del xin, y
     grid, ls = ei.star_wave(4096)
     hw = eb.EB(grid, ls)

@@ -208,7 +208,10 @@ int eb_rhs(const eb_handle* eb, const double* f_dev, const double* ugamma_dev, d
            cudaStream_t stream);
 
 /* y = A x, A = -L of eq. 3 with the line-by-line diagonal (Sec. 2.1), matrix
- * free.  x and y have the element type of prec (double, float, bf16). */
+ * free.  x and y have the element type of prec (double, float, bf16).  y is
+ * written at the CPs and, with 0, at the other node of every x-pair (2j,
+ * 2j + 1) that holds a CP; its other nodes keep their values (pass a zeroed y
+ * for a full-grid result).  x's entries off the CPs do not affect y. */
 int eb_apply(const eb_handle* eb, int prec, const void* x_dev, void* y_dev, cudaStream_t stream);
 
 /* --------------------------------------------------------------- tile shapes
@@ -331,6 +334,15 @@ enum { EB_TK_SMOOTH_STEP = 0 };
  * can be compared with the best a single launch of that size achieves.  The
  * buffers are allocated for the call.  Synchronous. */
 int eb_time_copy(int64_t bytes, int launches, int64_t clear_bytes, double* us_out, cudaStream_t stream);
+/* eb_apply timed like amg_time_kernel (instrumentation; the paper has no
+ * counterpart): `launches` (1..10000) back-to-back eb_apply launches of
+ * precision prec on x_dev -> y_dev, captured in one CUDA graph and timed by
+ * events around it; clear_bytes > 0 puts a read of a buffer of that many
+ * bytes before each launch (its own time subtracted), so that every launch
+ * finds its data in DRAM.  us_out: microseconds per launch.  y_dev is written
+ * as by eb_apply.  The clear buffer is allocated for the call.  Synchronous. */
+int eb_time_apply(const eb_handle* eb, int prec, const void* x_dev, void* y_dev, int launches, int64_t clear_bytes,
+                  double* us_out, cudaStream_t stream);
 int amg_time_kernel(const amg_handle* amg, int kernel, int level, int launches, int64_t clear_bytes, double* us_out,
                     cudaStream_t stream);
 

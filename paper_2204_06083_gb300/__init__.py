@@ -178,6 +178,7 @@ _SIGS = {
     "eb_fp64_peak": (C.c_int, [C.c_int, _P, _P]),
     "eb_set_beta": (C.c_int, [_P, _P, _P, _P, _P]),
     "eb_time_copy": (C.c_int, [C.c_int64, C.c_int, C.c_int64, _P, _P]),
+    "eb_time_apply": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, C.c_int64, _P, _P]),
     "batch_weighted_sum": (C.c_int, [_P, _P, _P, _P, _P]),
     "minres_solve": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.c_double, C.c_int, C.POINTER(pcg_stats), _P]),
     "wave_theta_step": (C.c_int, [_P, C.c_double, C.c_double, _P, _P, C.c_int, C.c_double, C.c_int,
@@ -399,6 +400,16 @@ class EB:
             out = torch.zeros_like(x)
         _check(load().eb_apply(self._h, prec, _ptr(x), _ptr(out), _stream(stream)))
         return out
+
+    def time_apply_us(self, x, out, launches: int = 20, clear_bytes: int = 0, stream=None) -> float:
+        """Microseconds per eb_apply launch on x -> out, launches captured in one
+        graph, each after a read of clear_bytes when > 0 (eb_time_apply)."""
+        import torch
+        prec = {torch.float64: EB_F64, torch.float32: EB_F32, torch.bfloat16: EB_BF16}[x.dtype]
+        us = C.c_double()
+        _check(load().eb_time_apply(self._h, prec, _ptr(x), _ptr(out), int(launches), int(clear_bytes),
+                                    C.byref(us), _stream(stream)))
+        return us.value
 
     def set_beta(self, betas, stream=None):
         """Variable coefficient of eq. 3: betas = one full-grid array per axis

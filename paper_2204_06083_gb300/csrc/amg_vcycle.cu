@@ -1324,6 +1324,36 @@ extern "C" int eb_time_copy(int64_t bytes, int launches, int64_t clear_bytes, do
   });
 }
 
+extern "C" int eb_time_apply(const eb_handle* eb, int prec, const void* x_dev, void* y_dev, int launches,
+                             int64_t clear_bytes, double* us_out, cudaStream_t stream) {
+  if (!eb || !x_dev || !y_dev || !us_out || launches < 1 || launches > 10000 || clear_bytes < 0 ||
+      (prec != EB_F64 && prec != EB_F32 && prec != EB_BF16)) {
+    set_error("eb_time_apply: invalid argument");
+    return EB_ERR_INVALID;
+  }
+  return guarded([&] {
+    const EBHandle& E = eb->h;
+    const int64_t nclear = clear_bytes / (int64_t)sizeof(uint4);
+    uint4* clear = nclear > 0 ? dalloc<uint4>(nclear, stream) : nullptr;
+    double us = 0.0;
+    try {
+      auto launch = [&](cudaStream_t s) {
+        if (prec == EB_F64) launch_apply<double>(E, (const double*)x_dev, (double*)y_dev, 0.0, s);
+        else if (prec == EB_F32) launch_apply<float>(E, (const float*)x_dev, (float*)y_dev, 0.0, s);
+        else launch_apply<__nv_bfloat16>(E, (const __nv_bfloat16*)x_dev, (__nv_bfloat16*)y_dev, 0.0, s);
+      };
+      EB_CUDA(cudaStreamSynchronize(stream));
+      us = time_alone(launch, launches, clear, nclear, stream);
+    } catch (...) {
+      dfree(clear, stream);
+      throw;
+    }
+    dfree(clear, stream);
+    EB_CUDA(cudaStreamSynchronize(stream));
+    *us_out = us;
+  });
+}
+
 extern "C" int amg_time_kernel(const amg_handle* amg, int kernel, int level, int launches, int64_t clear_bytes,
                                double* us_out, cudaStream_t stream) {
   if (!amg || !us_out || launches < 1 || launches > 10000 || clear_bytes < 0) {

@@ -55,33 +55,74 @@ struct Image {
 };
 
 // ------------------------------------------------------------ forward
-// layer 1 (2 -> 32) + ReLU; in: (s_hat, m) per pixel
-__global__ void k_l1_fwd(Image im, const float2* __restrict__ in, const float* __restrict__ P,
-                         bf16* __restrict__ y) {
-  __shared__ float w[W1_N + B1_N];
-  for (int i = threadIdx.x; i < W1_N + B1_N; i += blockDim.x) w[i] = P[OFF_W1 + i];
+// layer 1 (2 -> 32) + ReLU; in: (s_hat, m) per pixel.  A thread computes two
+// x-adjacent pixels: the 3 x 4 input window is loaded once and every weight
+// -- read from shared memory as float4s, two taps' two channels at a time --
+// is applied to both pixels, one FMA per multiply-add.
+__global__ void __launch_bounds__(128) k_l1_fwd(Image im, const float2* __restrict__ in, const float* __restrict__ P,
+                                                bf16* __restrict__ y) {
+  constexpr int WS = 20;  // a channel's 9 x 2 weights padded to five float4s
+  __shared__ __align__(16) float w[NC * WS + NC];
+  for (int i = threadIdx.x; i < NC * WS; i += blockDim.x) {
+    const int co = i / WS, j = i % WS;
+    w[i] = j < 18 ? P[OFF_W1 + co * 18 + j] : 0.0f;
+  }
+  for (int i = threadIdx.x; i < NC; i += blockDim.x) w[NC * WS + i] = P[OFF_W1 + W1_N + i];
   __syncthreads();
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= im.npx()) return;
-  const int x = (int)(p % im.W), r = (int)(p / im.W);
+  const int half = (im.W + 1) >> 1;
+  const int64_t pp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pp >= (int64_t)half * im.H) return;
+  const int r = (int)(pp / half), x = 2 * (int)(pp - (int64_t)r * half);
   const int lo = (r / im.R) * im.R, hi = lo + im.R;
-  float2 v[9];
+  float2 v[3][4];
 #pragma unroll
-  for (int d = 0; d < 9; ++d) {
-    const int xx = x + d % 3 - 1, rr = r + d / 3 - 1;
-    v[d] = (xx >= 0 && xx < im.W && rr >= lo && rr < hi) ? in[(int64_t)rr * im.W + xx] : make_float2(0.f, 0.f);
-  }
-  __align__(16) bf16 ov[NC];
-#pragma unroll 4
-  for (int co = 0; co < NC; ++co) {
-    float a = w[W1_N + co];
+  for (int dy = 0; dy < 3; ++dy) {
+    const int rr = r + dy - 1;
 #pragma unroll
-    for (int d = 0; d < 9; ++d) a += w[(co * 9 + d) * 2] * v[d].x + w[(co * 9 + d) * 2 + 1] * v[d].y;
-    ov[co] = __float2bfloat16_rn(fmaxf(a, 0.0f));
+    for (int dx = 0; dx < 4; ++dx) {
+      const int xx = x + dx - 1;
+      v[dy][dx] = (xx >= 0 && xx < im.W && rr >= lo && rr < hi) ? in[(int64_t)rr * im.W + xx] : make_float2(0.f, 0.f);
+    }
   }
+  uint32_t o0[NC / 2], o1[NC / 2];
+#pragma unroll
+  for (int co = 0; co < NC; co += 2) {
+    float a[2][2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const float* wc = w + (co + k) * WS;
+      float a0 = w[NC * WS + co + k], a1 = a0;
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        const float4 t = *reinterpret_cast<const float4*>(wc + 4 * q);
+        const int d0 = 2 * q, d1 = 2 * q + 1;
+        a0 = fmaf(t.x, v[d0 / 3][d0 % 3].x, a0);
+        a0 = fmaf(t.y, v[d0 / 3][d0 % 3].y, a0);
+        a1 = fmaf(t.x, v[d0 / 3][d0 % 3 + 1].x, a1);
+        a1 = fmaf(t.y, v[d0 / 3][d0 % 3 + 1].y, a1);
+        if (d1 < 9) {
+          a0 = fmaf(t.z, v[d1 / 3][d1 % 3].x, a0);
+          a0 = fmaf(t.w, v[d1 / 3][d1 % 3].y, a0);
+          a1 = fmaf(t.z, v[d1 / 3][d1 % 3 + 1].x, a1);
+          a1 = fmaf(t.w, v[d1 / 3][d1 % 3 + 1].y, a1);
+        }
+      }
+      a[k][0] = fmaxf(a0, 0.0f);
+      a[k][1] = fmaxf(a1, 0.0f);
+    }
+    const __nv_bfloat162 h0 = __floats2bfloat162_rn(a[0][0], a[1][0]);
+    const __nv_bfloat162 h1 = __floats2bfloat162_rn(a[0][1], a[1][1]);
+    o0[co / 2] = *reinterpret_cast<const uint32_t*>(&h0);
+    o1[co / 2] = *reinterpret_cast<const uint32_t*>(&h1);
+  }
+  const int64_t p = (int64_t)r * im.W + x;
   int4* dst = reinterpret_cast<int4*>(y + p * NC);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) dst[q] = reinterpret_cast<const int4*>(ov)[q];
+  for (int q = 0; q < 4; ++q) dst[q] = make_int4(o0[4 * q], o0[4 * q + 1], o0[4 * q + 2], o0[4 * q + 3]);
+  if (x + 1 < im.W) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dst[4 + q] = make_int4(o1[4 * q], o1[4 * q + 1], o1[4 * q + 2], o1[4 * q + 3]);
+  }
 }
 
 // Stages the rows r-1, r, r+1 (pixels x0-1 .. x0+TPX) of x into sIn [3][TPX+2][LDA],
@@ -999,7 +1040,8 @@ static void pack(NN& N, cudaStream_t s, int64_t& nl) {
 static void forward(NN& N, const Image& im, const float2* in, float* out, cudaStream_t s, int64_t& nl,
                     Solver* prof = nullptr) {
   const int64_t npx = npx_of(im);
-  k_l1_fwd<<<blocks_for(npx, 128), 128, 0, s>>>(im, in, N.P, N.act[1]);
+  const int64_t npairs = (int64_t)((im.W + 1) / 2) * im.H;  // layer 1: two pixels per thread
+  k_l1_fwd<<<blocks_for(npairs, 128), 128, 0, s>>>(im, in, N.P, N.act[1]);
   for (int l = 0; l < NMID; ++l) {
     const bool own = N.prof && !prof;  // events of the handle (not inside a solver's graph)
     if (own) {

@@ -220,7 +220,8 @@ void build_handle(EBHandle& eb, const eb_grid& grid, const eb_levelset& ls, cuda
                   const eb_build_opts* opts = nullptr);
 void destroy_handle(EBHandle& eb);
 
-// y = (sigma I + A) x over the active tiles (masked, non-CP outputs 0).
+// y = (sigma I + A) x at the CPs, 0 at the other node of a pair holding a CP
+// (the CP pair list), every other node untouched.
 template <class T>
 void launch_apply(const EBHandle& eb, const T* x, T* y, double sigma, cudaStream_t s);
 

@@ -108,14 +108,20 @@ void exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t
 }
 
 // ---------------------------------------------------------------- stencil
-// y = (sigma I + A) x on the active tiles, 0 at their non-CP nodes.
+// y = (sigma I + A) x at the CPs, 0 at the other node of a pair that holds a
+// CP.  With the view's CP pair list (every single grid that has a CP) one
+// thread takes one pair of the list, one pass over the grid of CTAs; without
+// it (no CP) the pairs of the active tiles, grid-stride.
+constexpr int APPLY_THREADS = 256;
+
 template <class T, int DIM>
-__global__ void __launch_bounds__(TILE_NODES) k_apply(TileView tv, const uint8_t* __restrict__ code,
-                                                      const typename DiagOf<T>::type* __restrict__ diag,
-                                                      const T* __restrict__ x, T* __restrict__ y,
-                                                      typename AccOf<T>::type sigma, typename AccOf<T>::type inv_h2) {
+__global__ void __launch_bounds__(APPLY_THREADS) k_apply(TileView tv, const uint8_t* __restrict__ code,
+                                                         const typename DiagOf<T>::type* __restrict__ diag,
+                                                         const T* __restrict__ x, T* __restrict__ y,
+                                                         typename AccOf<T>::type sigma,
+                                                         typename AccOf<T>::type inv_h2) {
   using A = typename AccOf<T>::type;
-  EB_PAIR_LOOP(DIM, tv, node) {
+  EB_SWEEP(DIM, tv, node) {
     uint32_t c0, c1;
     ld_codes(code, node, c0, c1);
     Two<A> xc, core;
@@ -130,8 +136,14 @@ template <class T>
 void launch_apply(const EBHandle& eb, const T* x, T* y, double sigma, cudaStream_t s) {
   using A = typename AccOf<T>::type;
   const A inv_h2 = (A)(1.0 / (eb.g.h * eb.g.h));
+  const TileView tv = eb.tv();
   dim_dispatch(eb, [&](auto D) {
-    k_apply<T, D.value><<<tile_grid(eb), TILE_NODES, 0, s>>>(eb.tv(), eb.code, diag_of<T>(eb), x, y, (A)sigma, inv_h2);
+    if (tv.pair_node)
+      k_apply<T, D.value | DIM_LIST><<<blocks_for(tv.npairs, APPLY_THREADS), APPLY_THREADS, 0, s>>>(
+          tv, eb.code, diag_of<T>(eb), x, y, (A)sigma, inv_h2);
+    else
+      k_apply<T, D.value><<<tile_grid(eb), APPLY_THREADS, 0, s>>>(tv, eb.code, diag_of<T>(eb), x, y, (A)sigma,
+                                                                  inv_h2);
   });
   EB_CUDA(cudaGetLastError());
 }

@@ -189,6 +189,35 @@ def test_apply_parity_all_precisions(name):
     assert e16 <= 1e-2, e16
 
 
+@pytest.mark.parametrize("name", ["circle130", "ellipsoid42"])
+def test_apply_write_set_and_timer(name):
+    """eb_apply writes A x at the CPs and 0 at the other node of every x-pair
+    (2j, 2j + 1) holding a CP, and nothing else; eb_time_apply leaves the same
+    y and reports a positive time."""
+    grid, ls = CASES[name]()
+    eb = _eb()
+    h = eb.EB(grid, ls)
+    ref = oeb.build(grid, ls)
+    rng = np.random.default_rng(3)
+    x = torch.tensor(rng.standard_normal(grid.shape()), device="cuda")
+    for dt in (torch.float64, torch.float32):
+        xd = x.to(dt)
+        fill = torch.full_like(xd, 7.0)
+        y = h.apply(xd, out=fill.clone()).reshape(-1).double().cpu().numpy()
+        cp = np.zeros(y.size, bool)
+        cp[ref.cp_nodes] = True
+        pair = cp.reshape(-1, 2).any(axis=1).repeat(2)
+        assert np.all(y[~pair] == 7.0)
+        assert np.all(y[pair & ~cp] == 0.0)
+        y_ref = ref.A @ ref.from_grid(x.cpu().numpy())
+        tol = 1e-14 if dt == torch.float64 else 1e-6
+        assert np.linalg.norm(y[ref.cp_nodes] - y_ref) / np.linalg.norm(y_ref) <= tol
+        y2 = fill.clone()
+        us = h.time_apply_us(xd, y2, launches=3, clear_bytes=1 << 20)
+        assert us > 0.0
+        assert np.array_equal(y2.reshape(-1).double().cpu().numpy(), y)
+
+
 def test_full_size_wave_geometry_star_4096():
     """The star of the wave workload at its full 4096^2 size: classes, cut list,
     diagonal; apply on sampled outputs."""
