@@ -65,6 +65,13 @@ LEAPFROG_BYTES_PER_DOF = {"f32": 13, "f64": 25}
 CONV_FLOP_PER_PX = 18432
 # and its bytes per pixel: 32 BF16 channels read and 32 written
 CONV_BYTES_PER_PX = 128
+# the whole network per pixel: 2 x 9 x (2 x 32 + 4 x 32 x 32 + 32 x 1) FLOP, of
+# which the four 32 -> 32 layers (on the tensor cores) are 4 x 18432
+NET_FLOP_PER_PX = 75456
+NET_TENSOR_FLOP_PER_PX = 4 * CONV_FLOP_PER_PX
+# and its bytes when all six layers run in one kernel: the two input channels
+# (float) read, the output (float) written
+NET_BYTES_PER_PX = 12
 ALONE_LAUNCHES = 20
 L2_CLEAR_BYTES = 512 << 20
 ALONE_NOTE = ("amg_time_kernel: back-to-back launches of the kernel on the solver's own level data in one CUDA "
@@ -1309,27 +1316,39 @@ def gpu_learned(ctx, args):
     pk, kind = peaks()
     px = int(grid.n[0]) * int(grid.n[1])
     avg_s = (prof_ms / prof_n) / 1000.0 if prof_n else float("nan")
-    achieved = CONV_FLOP_PER_PX * px / avg_s / 1e12 if prof_n else None
-    hbm_ach = CONV_BYTES_PER_PX * px / avg_s / 1e9 if prof_n else None
-    peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
     return {"value": value, "ms_per_step": ms_per_step, "dtype": "f64 outer, bf16 CNN (f32 accumulate)",
             "num_cp": nc, "iterations": sts[-1].iterations, "converged": bool(sts[-1].converged),
             "tile": tile, "autotune_us_per_vcycle": tune,
             "time_to_tol_ms": ms_per_step, "compare": compare,
             "training": {"pairs": npairs, "pair_generation_s": pairs_s, "train_s": train_s, "adam_steps": npairs // batch,
                          "batch": batch, "loss_log": log},
-            # the stage's 32 -> 32 convolutions: 144 FLOP per byte, below the ridge, so the HBM roof binds
-            "roofline": {"bound": "hbm", "kernel": "k_conv32_tma (32->32 implicit-GEMM conv: TMA-fed tcgen05 pipeline, TMEM)",
-                         "achieved": hbm_ach, "peak": pk["hbm_gbs"], "peak_kind": kind, "unit": "GB/s",
-                         "frac": (hbm_ach / pk["hbm_gbs"]) if hbm_ach else None, "traffic": recorded_traffic("k_conv32_tma"),
-                         "algorithmic_bytes_per_launch": CONV_BYTES_PER_PX * px, "avg_launch_us": avg_s * 1e6,
-                         "launches_timed": prof_n, "timing": PROF_NOTE,
-                         "tensor": {"achieved": achieved, "peak": peak, "peak_kind": kind + " bf16 sustained",
-                                    "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-                                    "algorithmic_flops_per_launch": CONV_FLOP_PER_PX * px}},
+            # the stage's network: one fused launch per application
+            "roofline": net_roofline(avg_s, px, prof_n, PROF_NOTE, sustained=True),
             "e2e": {"value": e2e_value, "unit": "DOF/s", "h2d_bytes_per_step": hb.numel() * 8,
                     "d2h_bytes_per_step": hx.numel() * 8},
             "gpu_launches": sts[-1].launches, "clocks": clocks}
+
+
+def net_roofline(avg_s, px, n, timing, sustained):
+    """Roofline of the one-launch forward k_net_fwd: far above the ridge (73728
+    tensor FLOP per 12 bytes of HBM traffic per pixel), so the tensor roof
+    binds; its HBM figure rides along."""
+    pk, kind = peaks()
+    peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops")) if sustained else pk.get("bf16_tflops")
+    ok = n and avg_s == avg_s
+    ach = NET_TENSOR_FLOP_PER_PX * px / avg_s / 1e12 if ok else None
+    gbs = NET_BYTES_PER_PX * px / avg_s / 1e9 if ok else None
+    return {"bound": "tensor", "kernel": "k_net_fwd (all six layers in one launch: layers 2-5 on tcgen05 with TMEM "
+                                        "accumulators, activations kept in shared memory)",
+            "achieved": ach, "peak": peak,
+            "peak_kind": kind + (" bf16 sustained" if sustained else " bf16 burst"), "unit": "TFLOP/s",
+            "frac": (ach / peak) if ach else None, "traffic": recorded_traffic("k_net_fwd"),
+            "algorithmic_flops_per_launch": NET_TENSOR_FLOP_PER_PX * px,
+            "all_layers_tflops": NET_FLOP_PER_PX * px / avg_s / 1e12 if ok else None,
+            "avg_launch_us": avg_s * 1e6, "launches_timed": n, "timing": timing,
+            "hbm": {"achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": (gbs / pk["hbm_gbs"]) if gbs else None,
+                    "algorithmic_bytes_per_launch": NET_BYTES_PER_PX * px}}
 
 
 def gpu_conv(ctx, args):
@@ -1354,12 +1373,27 @@ def gpu_conv(ctx, args):
     _, ms_per_step, clocks = loop(ctx, args, step, torch.cuda.current_device())
     px = n * n
     value = ctx.world * px / (ms_per_step / 1000.0)
-    net.set_profile(True)  # the convolution launches, in as many forwards right after the timed ones
+    net.set_profile(True)  # the fused launch, in as many forwards right after the timed ones
     for _ in range(args.steps):
         ctx.flush()
         net.forward(inp, out)
+    fz_ms, fz_n = net.profile()
+    net.status()
+    # the layer-by-layer launches on the same input, for comparison: the whole
+    # forward and its 32 -> 32 convolution launches
+    net.set_fused(False)
+    ref_out = out.clone()
+    net.forward(inp, out)
+    same = bool(torch.equal(out, ref_out))
+    net.profile()
+    lay = []
+    for _ in range(args.steps):
+        ctx.flush()
+        t, _ = timed(lambda: net.forward(inp, out))
+        lay.append(t)
     conv_ms, conv_n = net.profile()
     net.set_profile(False)
+    net.set_fused(True)
     net.status()
     hin = inp.cpu().pin_memory()
     hout = torch.empty_like(out, device="cpu").pin_memory()
@@ -1373,24 +1407,32 @@ def gpu_conv(ctx, args):
             e2e.append(t)
     e2e_value = ctx.world * px / (ctx.max_over_ranks(statistics.mean(e2e)) / 1000.0)
     pk, kind = peaks()
+    fz_s = (fz_ms / fz_n) / 1000.0 if fz_n else float("nan")
     avg_s = (conv_ms / conv_n) / 1000.0 if conv_n else float("nan")
     achieved = CONV_FLOP_PER_PX * px / avg_s / 1e12 if conv_n else None
     peak = pk.get("bf16_tflops", pk.get("bf16_tflops_sustained"))
     hbm_ach = CONV_BYTES_PER_PX * px / avg_s / 1e9 if conv_n else None
     return {"value": value, "ms_per_step": ms_per_step, "dtype": "bf16 (f32 accumulate)",
-            # 144 FLOP per byte moved, below the ridge (peak FLOP/s over peak B/s): HBM is the roof that binds
-            "roofline": {"bound": "hbm", "kernel": "k_conv32_tma (32->32 implicit-GEMM conv: TMA-fed tcgen05 pipeline, TMEM)",
-                         "achieved": hbm_ach, "peak": pk["hbm_gbs"], "peak_kind": kind, "unit": "GB/s",
-                         "frac": (hbm_ach / pk["hbm_gbs"]) if hbm_ach else None,
-                         "traffic": recorded_traffic("k_conv32_tma"),
-                         "algorithmic_bytes_per_launch": CONV_BYTES_PER_PX * px, "avg_launch_us": avg_s * 1e6,
-                         "launches_timed": conv_n,
-                         "tensor": {"achieved": achieved, "peak": peak, "peak_kind": kind + " bf16 burst",
-                                    "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-                                    "algorithmic_flops_per_launch": CONV_FLOP_PER_PX * px}},
+            "roofline": net_roofline(fz_s, px, fz_n, "CUDA events around the fused launch, one forward after each "
+                                     "512 MB L2 flush", sustained=False),
+            "layered": {
+                "ms_per_forward": statistics.mean(lay), "bitwise_equal_to_fused": same,
+                "launches_per_forward": 6,
+                # 144 FLOP per byte moved, below the ridge: HBM is the roof that binds a single convolution
+                "conv_roofline": {
+                    "bound": "hbm",
+                    "kernel": "k_conv32_tma (32->32 implicit-GEMM conv: TMA-fed tcgen05 pipeline, TMEM)",
+                    "achieved": hbm_ach, "peak": pk["hbm_gbs"], "peak_kind": kind, "unit": "GB/s",
+                    "frac": (hbm_ach / pk["hbm_gbs"]) if hbm_ach else None,
+                    "traffic": recorded_traffic("k_conv32_tma"),
+                    "algorithmic_bytes_per_launch": CONV_BYTES_PER_PX * px, "avg_launch_us": avg_s * 1e6,
+                    "launches_timed": conv_n,
+                    "tensor": {"achieved": achieved, "peak": peak, "peak_kind": kind + " bf16 burst",
+                               "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+                               "algorithmic_flops_per_launch": CONV_FLOP_PER_PX * px}}},
             "e2e": {"value": e2e_value, "unit": "pixels/s", "h2d_bytes_per_step": hin.numel() * 4,
                     "d2h_bytes_per_step": hout.numel() * 4},
-            "gpu_launches": 6, "clocks": clocks}
+            "gpu_launches": 1, "clocks": clocks}
 
 
 def _smoother_roofline(solver, nc, bytes_per_dof, note):

@@ -582,6 +582,15 @@ int nn_status(nn_handle* nn, cudaStream_t stream);
  * of timed launches since, and restarts the count. */
 int nn_set_profile(nn_handle* nn, int on);
 int nn_profile(nn_handle* nn, double* ms, int* launches, cudaStream_t stream);
+/* Forward path of nn_forward and of the learned stage in pcg_solve_nn /
+ * nn_precondition.  on != 0 (the default): one launch computes all six layers
+ * with the hidden activations kept in shared memory and tensor memory (strips
+ * of 116 columns walked down the rows); on = 0: one launch per layer through
+ * activation buffers in device memory, the path nn_backward and nn_train_step
+ * always take.  Both give bit-identical outputs.  With profiling on, the fused
+ * launch is the one timed launch of a forward.  Set it before a solve: a
+ * solver's captured iteration keeps the path it was captured with. */
+int nn_set_fused(nn_handle* nn, int on);
 /* Copies nn_num_params() floats from HOST memory into the network and resets
  * the Adam state (moments and step count).  Synchronous. */
 int nn_set_params(nn_handle* nn, const float* params_host, cudaStream_t stream);
@@ -590,8 +599,9 @@ int nn_set_params(nn_handle* nn, const float* params_host, cudaStream_t stream);
 int nn_get_params(const nn_handle* nn, float* params_host, float* grad_host, cudaStream_t stream);
 /* out = N(in): in is [images][height][width][2] floats (s_hat, m), out is
  * [images][height][width] floats, both device buffers (in 8-byte aligned).
- * width, height >= 1.  Activation memory is held by the handle and grows to
- * the largest images x height x width seen (64 bytes x 7 per pixel). */
+ * width, height >= 1.  Activation memory (layer-by-layer path only, see
+ * nn_set_fused) is held by the handle and grows to the largest images x
+ * height x width seen (64 bytes x 7 per pixel). */
 int nn_forward(nn_handle* nn, int width, int height, int images, const float* in_dev, float* out_dev,
                cudaStream_t stream);
 /* Gradient of sum(dout * N(in)) in the parameters (kept in the handle, read

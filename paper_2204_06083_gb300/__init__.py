@@ -164,6 +164,7 @@ _SIGS = {
     "nn_num_params": (C.c_int, []),
     "nn_status": (C.c_int, [_P, _P]),
     "nn_set_profile": (C.c_int, [_P, C.c_int]),
+    "nn_set_fused": (C.c_int, [_P, C.c_int]),
     "nn_profile": (C.c_int, [_P, _P, _P, _P]),
     "nn_set_params": (C.c_int, [_P, _P, _P]),
     "nn_get_params": (C.c_int, [_P, _P, _P, _P]),
@@ -760,8 +761,14 @@ class Net:
     def set_profile(self, on: bool):
         _check(load().nn_set_profile(self._h, int(bool(on))))
 
+    def set_fused(self, on: bool):
+        """nn_set_fused: the one-launch forward (default) or the layer-by-layer launches."""
+        _check(load().nn_set_fused(self._h, int(bool(on))))
+
     def profile(self, stream=None):
-        """(summed ms, launches) of the timed 32 -> 32 convolution launches since the last call."""
+        """(summed ms, launches) of the timed launches since the last call: the
+        32 -> 32 convolutions of a layer-by-layer forward, the one fused launch
+        of a fused forward."""
         ms = C.c_double()
         n = C.c_int()
         _check(load().nn_profile(self._h, C.byref(ms), C.byref(n), _stream(stream)))

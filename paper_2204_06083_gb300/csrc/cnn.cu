@@ -380,7 +380,10 @@ __global__ void __launch_bounds__(CP_THREADS, 3) k_conv32_tma(const __grid_const
   }
 }
 
-// layer 6 (32 -> 1); out = m * (conv + b6)
+// layer 6 (32 -> 1); out = m * (conv + b6).  Each tap's 32-channel sum is
+// formed on its own (one FMA chain from 0) and the nine are added to b6 in tap
+// order: the order of k_net_fwd, whose results this kernel reproduces bit for
+// bit.
 __global__ void k_l6_fwd(Image im, const bf16* __restrict__ y5, const float* __restrict__ P,
                          const float2* __restrict__ in, float* __restrict__ out) {
   __shared__ float w[W6_N + B6_N];
@@ -395,15 +398,356 @@ __global__ void k_l6_fwd(Image im, const bf16* __restrict__ y5, const float* __r
     const int xx = x + d % 3 - 1, rr = r + d / 3 - 1;
     if (xx < 0 || xx >= im.W || rr < lo || rr >= hi) continue;
     const int4* src = reinterpret_cast<const int4*>(y5 + ((int64_t)rr * im.W + xx) * NC);
+    float t = 0.0f;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int4 v = src[q];
       const bf16* e = reinterpret_cast<const bf16*>(&v);
 #pragma unroll
-      for (int c = 0; c < 8; ++c) a += w[d * NC + q * 8 + c] * __bfloat162float(e[c]);
+      for (int c = 0; c < 8; ++c) t = __fmaf_rn(w[d * NC + q * 8 + c], __bfloat162float(e[c]), t);
     }
+    a = __fadd_rn(a, t);
   }
   out[p] = in[p].y * a;
+}
+
+// --------------------------------------------- fused forward: all six layers
+// One launch computes N(in) with every hidden activation kept on chip.  A CTA
+// owns a strip of FZ_OUT = 116 output columns and a run of rows of one image
+// and walks down it one step at a time; step tau computes layer 1 at row tau,
+// layer l (2..5) at row tau - 2 (l - 1) and layer 6 at row tau - 10, so the
+// rows a step reads were all finished in earlier steps and the layers of one
+// step are independent.  Every layer computes 128 columns (the tensor cores'
+// M), the strip's 116 plus 6 on each side: layer l is exact on 128 - 2 (l - 1)
+// of them, which leaves layer 6 exact on the strip.
+//   * layer 1 (2 -> 32, CUDA cores, warps 4-7): one pixel per thread, the FMA
+//     order of k_l1_fwd; bf16 result into ring 0.
+//   * layers 2-5 (tcgen05, lane 0 of warp 8 + l - 2): 18 MMAs of 128 x 32 x 16
+//     per layer and step, A = three rows of ring l - 2 (64-byte swizzled
+//     K-major rows of 64 bytes, one per pixel, as k_conv32_tma's tensor copies
+//     lay them out), B = the layer's weights in shared memory, D = one of two
+//     TMEM accumulators per layer.
+//   * epilogues (warps 0-3, one TMEM lane = one pixel per thread): bias, ReLU,
+//     bf16, 0 outside the image (the next layer's zero padding); layers 2-4
+//     write ring l - 1 (the swizzle applied by hand), layer 5 forms the nine
+//     tap partials of layer 6 (a float per tap and pixel, ring T) from its
+//     bf16-rounded values, and layer 6 adds them up: out = m (b6 + sum).
+// Rings hold 4 rows (row rho in slot rho & 3): a step writes row rho + 2 of a
+// ring while the MMAs read rows rho - 1 .. rho + 1.  Every layer's arithmetic
+// is that of the layer-by-layer path (k_l1_fwd, k_conv32_tma, k_l6_fwd), so
+// the two give identical outputs.
+// Barriers (mbarriers, two of each kind per layer, by step parity): rdy[j][b]
+// (ring j rows of step k written: 4 warp arrivals -> MMA of layer j + 2 at
+// step k + 1), mdone[j][b] (commit of layer j + 2's MMAs at step k ->
+// epilogue; mdone[0] also frees ring 0's oldest row for layer 1), tempty[j][b]
+// (accumulator drained: 4 warp arrivals -> MMA at step k + 2).  With two
+// barriers per kind no waiter can fall two phases behind.  The epilogue of
+// layer l at step k overwrites the row of ring l - 1 that layer l + 1's MMAs
+// read at step k - 1: the epilogue warps waited for those (mdone of layer
+// l + 1, step k - 1) earlier in their own program order.  Every wait is
+// bounded; one that gives up raises a shared abort flag, after which every
+// role runs its remaining steps without waiting or computing (so the named
+// barriers of the epilogue warps still match), the CTA waits (bounded) for its
+// MMAs in flight, frees TMEM and sets *err.
+constexpr int FZ_OUT = TPX - 12;                       // 116
+constexpr int FZ_ROW = TC_PIX * NC * 2;                // 8320 bytes: one activation row, 130 pixel slots
+constexpr int FZ_RING = 4;                             // rows per ring
+constexpr int FZ_RINGB = FZ_RING * FZ_ROW;             // 33,280
+constexpr int FZ_W = 4 * FZ_RINGB;                     // weights of layers 2-5: 133,120
+constexpr int FZ_TROW = 9 * TC_PIX;                    // floats of a T row: 9 taps x 130 slots
+constexpr int FZ_T = FZ_W + NMID * TC_W;               // 206,848
+constexpr int FZ_W1 = FZ_T + FZ_RING * FZ_TROW * 4;    // 225,568: layer-1 weights, 20 per channel, + b1
+constexpr int FZ_W6 = FZ_W1 + (NC * 20 + NC) * 4;      // 228,256: W6, b6
+constexpr int FZ_BM = FZ_W6 + 1168;                    // 229,424: biases of layers 2-5
+constexpr int FZ_BAR = FZ_BM + NMID * NC * 4;          // 229,936
+constexpr int FZ_NBAR = 24;
+constexpr int FZ_SMEM = FZ_BAR + 8 * FZ_NBAR + 16;     // 230,144
+constexpr int FZ_THREADS = 384;                        // warps 0-3 epilogues, 4-7 layer 1, 8-11 MMAs
+static_assert(FZ_SMEM <= 232448, "fused forward: shared memory");
+static_assert(FZ_W % 1024 == 0 && FZ_T % 16 == 0 && FZ_BAR % 8 == 0, "fused forward: alignment");
+
+struct FzArgs {
+  Image im;
+  const float2* in;
+  float* out;
+  const float* P;
+  const bf16* wf;  // [4][9][32 n][32 k] bf16
+  int strips, segs, seg_rows;
+  int64_t units;
+  int* err;
+};
+
+// 64 bytes (32 bf16 = 16 words) into the pixel row at shared address row (a
+// multiple of 64) in the 64-byte swizzled layout: 16-byte chunk c of the row
+// lands at chunk c ^ (address bits 7-8)
+__device__ __forceinline__ void fz_st_row(uint32_t row, const uint32_t (&w)[NC / 2]) {
+  const uint32_t sw = (row >> 7) & 3u;
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(row + ((c ^ sw) << 4)), "r"(w[4 * c]),
+                 "r"(w[4 * c + 1]), "r"(w[4 * c + 2]), "r"(w[4 * c + 3])
+                 : "memory");
+}
+
+__device__ __forceinline__ void fz_unit(const FzArgs& a, int64_t u, int& img, int& r0, int& r1, int& x0) {
+  const int strip = (int)(u % a.strips);
+  const int64_t q = u / a.strips;
+  const int seg = (int)(q % a.segs);
+  img = (int)(q / a.segs);
+  x0 = strip * FZ_OUT;
+  r0 = seg * a.seg_rows;
+  r1 = min(r0 + a.seg_rows, a.im.R);
+}
+
+__global__ void __launch_bounds__(FZ_THREADS, 1) k_net_fwd(const __grid_constant__ FzArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const uint32_t base = smem_addr(smem_raw);
+  const uint32_t bars = base + FZ_BAR;
+  auto rdy = [&](int j, int b) { return bars + 8 * (2 * j + b); };
+  auto mdone = [&](int j, int b) { return bars + 8 * (8 + 2 * j + b); };
+  auto tempty = [&](int j, int b) { return bars + 8 * (16 + 2 * j + b); };
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem_raw + FZ_BAR + 8 * FZ_NBAR);
+  volatile int* abort = reinterpret_cast<volatile int*>(smem_raw + FZ_BAR + 8 * FZ_NBAR + 8);
+  float* sT = reinterpret_cast<float*>(smem_raw + FZ_T);
+  float* sW1 = reinterpret_cast<float*>(smem_raw + FZ_W1);
+  float* sW6 = reinterpret_cast<float*>(smem_raw + FZ_W6);
+  float* sBM = reinterpret_cast<float*>(smem_raw + FZ_BM);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const Image& im = a.im;
+
+  // rings and T start at 0 (slots 0 and 129 of every ring row stay 0)
+  for (int i = tid; i < FZ_W / 16; i += FZ_THREADS) reinterpret_cast<int4*>(smem_raw)[i] = make_int4(0, 0, 0, 0);
+  for (int i = tid; i < FZ_RING * FZ_TROW; i += FZ_THREADS) sT[i] = 0.0f;
+  for (int i = tid; i < NMID * 9 * NC * 4; i += FZ_THREADS) {  // B operands, as in k_conv32_tma
+    const int g = i & 3, n = (i >> 2) % NC, d = ((i >> 2) / NC) % 9, l = (i >> 2) / (NC * 9);
+    *reinterpret_cast<int4*>(smem_raw + FZ_W + l * TC_W + d * TC_WTAP + g * (NC * 16) + n * 16) =
+        *reinterpret_cast<const int4*>(a.wf + (int64_t)l * WM_N + (d * NC + n) * NC + g * 8);
+  }
+  for (int i = tid; i < NC * 20; i += FZ_THREADS) {
+    const int co = i / 20, j = i % 20;
+    sW1[i] = j < 18 ? a.P[OFF_W1 + co * 18 + j] : 0.0f;
+  }
+  for (int i = tid; i < NC; i += FZ_THREADS) sW1[NC * 20 + i] = a.P[OFF_W1 + W1_N + i];
+  for (int i = tid; i < W6_N + B6_N; i += FZ_THREADS) sW6[i] = a.P[OFF_W6 + i];
+  for (int i = tid; i < NMID * NC; i += FZ_THREADS) sBM[i] = a.P[off_wm(i / NC) + WM_N + i % NC];
+  if (tid == 0) {
+    for (int b = 0; b < FZ_NBAR; ++b) {
+      const uint32_t cnt = (b >= 8 && b < 16) ? 1u : 4u;  // mdone: one commit; rdy, tempty: four warps
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bars + 8 * b), "r"(cnt));
+    }
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 8) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_addr(tslot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;");  // zeroed rings and weights are read by the tensor cores
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tslot;
+
+  if (warp >= 8) {
+    // warp 8 + j issues the MMAs of layer j + 2 (ring j in): one issuing thread
+    // per layer, so that the four layers' MMAs of a step overlap on the tensor
+    // cores (an issuing thread waits out each MMA's operand fetch)
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc_idesc(128, NC);
+      const int j = warp - 8;
+      int64_t k = 0;
+      uint32_t last_bar = 0, last_par = 0;
+      bool ok = true;
+      for (int64_t u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
+        int img, r0, r1, x0;
+        fz_unit(a, u, img, r0, r1, x0);
+        const int nsteps = r1 - r0 + 15;
+        for (int st = 0; st < nsteps && ok; ++st, ++k) {
+          const int tau = r0 - 5 + st, b = (int)(k & 1);
+          {
+            if (k >= 1 && !cp_wait(rdy(j, (int)((k - 1) & 1)), (uint32_t)((k - 1) >> 1) & 1u, abort)) {
+              ok = false;
+              break;
+            }
+            if (k >= 2 && !cp_wait(tempty(j, b), (uint32_t)((k - 2) >> 1) & 1u, abort)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const int rho = tau - 2 * (j + 1);
+            const uint32_t ring = base + (uint32_t)(j * FZ_RINGB);
+#pragma unroll 1
+            for (int q = 0; q < 18; ++q) {
+              const int d = q >> 1, kh = q & 1, dy = d / 3, dx = d % 3;
+              const uint32_t row = ring + (uint32_t)(((rho - 1 + dy) & 3) * FZ_ROW);
+              const uint64_t da = tc_desc_sw64(row + dx * 64 + kh * 32);
+              const uint64_t db =
+                  tc_desc(base + FZ_W + j * TC_W + d * TC_WTAP + (2 * kh) * (NC * 16), NC * 16, 128);
+              asm volatile(
+                  "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(
+                      tmem + (uint32_t)((2 * j + b) * NC)),
+                  "l"(da), "l"(db), "r"(idesc), "r"((uint32_t)(q > 0)));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             mdone(j, b))
+                         : "memory");
+            last_bar = mdone(j, b);
+            last_par = (uint32_t)(k >> 1) & 1u;
+          }
+        }
+      }
+      if (last_bar) {  // the last commit covers every MMA this thread issued: they finish before TMEM is freed
+        volatile int never = 0;
+        cp_wait(last_bar, last_par, &never);
+      }
+    }
+  } else if (warp >= 4) {
+    // layer 1 (warps 4-7): thread t = pixel slot t + 1 of ring 0
+    const int t = tid - 128;
+    int64_t k = 0;
+    for (int64_t u = blockIdx.x; u < a.units; u += gridDim.x) {
+      int img, r0, r1, x0;
+      fz_unit(a, u, img, r0, r1, x0);
+      const int nsteps = r1 - r0 + 15;
+      const int x = x0 - 6 + t;
+      for (int st = 0; st < nsteps; ++st, ++k) {
+        const int tau = r0 - 5 + st;
+        bool ok = true;
+        if (k >= 1) ok = cp_wait(mdone(0, (int)((k - 1) & 1)), (uint32_t)((k - 1) >> 1) & 1u, abort);
+        uint32_t o[NC / 2];
+#pragma unroll
+        for (int c = 0; c < NC / 2; ++c) o[c] = 0u;
+        if (ok && !*abort && tau >= 0 && tau < im.R && x >= 0 && x < im.W) {
+          float2 v[9];
+#pragma unroll
+          for (int d = 0; d < 9; ++d) {
+            const int xx = x + d % 3 - 1, rr = tau + d / 3 - 1;
+            v[d] = (xx >= 0 && xx < im.W && rr >= 0 && rr < im.R)
+                       ? __ldg(a.in + ((int64_t)img * im.R + rr) * im.W + xx)
+                       : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int co = 0; co < NC; co += 2) {
+            float r2[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const float* wc = sW1 + (co + h) * 20;
+              float acc = sW1[NC * 20 + co + h];
+#pragma unroll
+              for (int q = 0; q < 5; ++q) {
+                const float4 w4 = *reinterpret_cast<const float4*>(wc + 4 * q);
+                acc = __fmaf_rn(w4.x, v[2 * q].x, acc);
+                acc = __fmaf_rn(w4.y, v[2 * q].y, acc);
+                if (2 * q + 1 < 9) {
+                  acc = __fmaf_rn(w4.z, v[2 * q + 1].x, acc);
+                  acc = __fmaf_rn(w4.w, v[2 * q + 1].y, acc);
+                }
+              }
+              r2[h] = fmaxf(acc, 0.0f);
+            }
+            const __nv_bfloat162 hv = __floats2bfloat162_rn(r2[0], r2[1]);
+            o[co / 2] = *reinterpret_cast<const uint32_t*>(&hv);
+          }
+        }
+        fz_st_row(base + (uint32_t)((tau & 3) * FZ_ROW + (t + 1) * 64), o);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(rdy(0, (int)(k & 1))) : "memory");
+      }
+    }
+  } else {
+    // epilogues of layers 2-5 and layer 6: thread i = TMEM lane i = pixel slot i + 1
+    const int i = tid;
+    int64_t k = 0;
+    for (int64_t u = blockIdx.x; u < a.units; u += gridDim.x) {
+      int img, r0, r1, x0;
+      fz_unit(a, u, img, r0, r1, x0);
+      const int nsteps = r1 - r0 + 15;
+      const int x = x0 - 6 + i;
+      for (int st = 0; st < nsteps; ++st, ++k) {
+        const int tau = r0 - 5 + st, b = (int)(k & 1);
+        for (int j = 0; j < NMID; ++j) {
+          const bool okl = cp_wait(mdone(j, b), (uint32_t)(k >> 1) & 1u, abort) && !*abort;
+          const bool okw = __all_sync(0xffffffffu, okl);  // tcgen05.ld is warp-collective
+          uint32_t v[NC];
+          if (okw) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+                "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((2 * j + b) * NC)));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          } else {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) v[c] = 0u;
+          }
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          __syncwarp();
+          if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tempty(j, b)) : "memory");
+          const int rho = tau - 2 * (j + 1);
+          const bool in_img = okw && rho >= 0 && rho < im.R && x >= 0 && x < im.W;
+          const float* bj = sBM + j * NC;
+          if (j < NMID - 1) {
+            uint32_t o[NC / 2];
+#pragma unroll
+            for (int c = 0; c < NC; c += 2) {
+              const float f0 = in_img ? fmaxf(__uint_as_float(v[c]) + bj[c], 0.0f) : 0.0f;
+              const float f1 = in_img ? fmaxf(__uint_as_float(v[c + 1]) + bj[c + 1], 0.0f) : 0.0f;
+              const __nv_bfloat162 hv = __floats2bfloat162_rn(f0, f1);
+              o[c / 2] = *reinterpret_cast<const uint32_t*>(&hv);
+            }
+            fz_st_row(base + (uint32_t)((j + 1) * FZ_RINGB + (rho & 3) * FZ_ROW + (i + 1) * 64), o);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0)
+              asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(rdy(j + 1, b)) : "memory");
+          } else {
+            // layer 6 at row tau - 10 from the tap partials of earlier steps
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            const int r6 = tau - 10;
+            if (!*abort && r6 >= r0 && r6 < r1 && i >= 6 && i < 6 + FZ_OUT && x < im.W) {
+              float acc = sW6[W6_N];
+#pragma unroll
+              for (int d = 0; d < 9; ++d) {
+                const int dy = d / 3, dx = d % 3;
+                acc = __fadd_rn(acc, sT[((r6 - 1 + dy) & 3) * FZ_TROW + d * TC_PIX + i + dx]);
+              }
+              const int64_t p = ((int64_t)img * im.R + r6) * im.W + x;
+              a.out[p] = __ldg(a.in + p).y * acc;
+            }
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            // tap partials of layer 5's row rho (bf16-rounded values, as layer 6 reads them)
+            float f[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+              f[c] = in_img ? __bfloat162float(__float2bfloat16_rn(fmaxf(__uint_as_float(v[c]) + bj[c], 0.0f)))
+                            : 0.0f;
+            float* tr = sT + (rho & 3) * FZ_TROW + i + 1;
+#pragma unroll
+            for (int d = 0; d < 9; ++d) {
+              float tsum = 0.0f;
+#pragma unroll
+              for (int c = 0; c < NC; ++c) tsum = __fmaf_rn(sW6[d * NC + c], f[c], tsum);
+              tr[d * TC_PIX] = tsum;
+            }
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (tid == 0 && *abort) atomicExch(a.err, 1);
+  if (warp == 8) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+  }
 }
 
 // ----------------------------------------------------------- backward
@@ -931,6 +1275,7 @@ struct NN {
   bf16* wb = nullptr;  // packed data-gradient weights
   int64_t steps = 0;
   cudaStream_t home = 0;
+  bool fused = true;  // nn_forward and the PCG stage: k_net_fwd (else the layer-by-layer launches)
   // activations (grown to the largest stack seen)
   int64_t cap_px = 0;
   bf16* act[6] = {};  // act[1..5]: outputs of layers 1..5
@@ -964,6 +1309,7 @@ static void set_attrs() {
   if (done) return;
   EB_CUDA(cudaFuncSetAttribute(k_conv32_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CP_SMEM));
   EB_CUDA(cudaFuncSetAttribute(k_conv32_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wgrad_smem()));
+  EB_CUDA(cudaFuncSetAttribute(k_net_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FZ_SMEM));
   done = true;
 }
 
@@ -1063,6 +1409,68 @@ static void forward(NN& N, const Image& im, const float2* in, float* out, cudaSt
   EB_CUDA(cudaGetLastError());
 }
 
+// The work units of k_net_fwd: strips of FZ_OUT columns x runs of rows of
+// one image.  A run of n rows takes n + 15 steps; the run length minimises
+// (waves of units over the SMs) x (steps per unit).
+static FzArgs fz_plan(const Image& im) {
+  FzArgs a{};
+  a.im = im;
+  a.strips = (im.W + FZ_OUT - 1) / FZ_OUT;
+  const int64_t nimg = im.H / im.R;
+  const int64_t nsm = num_sms();
+  int64_t best = -1;
+  for (int sg = 1; sg <= im.R; ++sg) {
+    const int rows = (im.R + sg - 1) / sg;
+    const int segs = (im.R + rows - 1) / rows;
+    const int64_t units = (int64_t)a.strips * nimg * segs;
+    const int64_t cost = ((units + nsm - 1) / nsm) * (rows + 15);
+    if (best < 0 || cost < best) {
+      best = cost;
+      a.segs = segs;
+      a.seg_rows = rows;
+      a.units = units;
+    }
+    if (units > 4 * nsm) break;
+  }
+  return a;
+}
+
+// out = N(in) in one launch of k_net_fwd
+static void forward_fused(NN& N, const Image& im, const float2* in, float* out, cudaStream_t s, int64_t& nl,
+                          Solver* prof = nullptr) {
+  EB_REQUIRE(im.R > 0 && im.H % im.R == 0, EB_ERR_INVALID, "forward: rows are not whole images");
+  FzArgs a = fz_plan(im);
+  a.in = in;
+  a.out = out;
+  a.P = N.P;
+  a.wf = N.wf;
+  a.err = N.err;
+  const bool own = N.prof && !prof;
+  if (own) {
+    if (N.prof_n >= (int)N.prof_ev.size()) {
+      cudaEvent_t e0, e1;
+      EB_CUDA(cudaEventCreate(&e0));
+      EB_CUDA(cudaEventCreate(&e1));
+      N.prof_ev.push_back({e0, e1});
+    }
+    EB_CUDA(cudaEventRecord(N.prof_ev[N.prof_n].first, s));
+  }
+  if (prof) prof->prof_mark(s, true, PROF_CONV);
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(a.units, num_sms()));
+  k_net_fwd<<<grid, FZ_THREADS, FZ_SMEM, s>>>(a);
+  if (prof) prof->prof_mark(s, false, PROF_CONV);
+  if (own) EB_CUDA(cudaEventRecord(N.prof_ev[N.prof_n++].second, s));
+  nl += 1;
+  EB_CUDA(cudaGetLastError());
+}
+
+// the inference forward: fused unless the handle asks for the layer-by-layer path
+static void forward_infer(NN& N, const Image& im, const float2* in, float* out, cudaStream_t s, int64_t& nl,
+                          Solver* prof = nullptr) {
+  if (N.fused) forward_fused(N, im, in, out, s, nl, prof);
+  else forward(N, im, in, out, s, nl, prof);
+}
+
 // gradient of sum(dout * out) into N.G (forward ran on the same input)
 static void backward(NN& N, const Image& im, const float2* in, const float* dout, cudaStream_t s, int64_t& nl) {
   const int64_t npx = npx_of(im);
@@ -1152,7 +1560,7 @@ void nn_stage_apply(nn_handle* h, const EBHandle& eb, double shift, int mode, co
   k_st_norm<<<1, 32, 0, s>>>(N.spart, (int)nb, (double)eb.num_cp, eb.g.h * eb.g.h, N.scal);
   k_st_input<<<nb, 256, 0, s>>>(nn, eb.code, N.s64, N.scal, N.in);
   const Image im{eb.g.n0, eb.g.n1, eb.g.n1};
-  forward(N, im, N.in, N.out, s, nl, prof);
+  forward_infer(N, im, N.in, N.out, s, nl, prof);
   if (mode == EB_NN_ENERGY) {
     k_st_energy<<<nb, 256, 0, s>>>(G, eb.g.h * eb.g.h, nn, eb.code, eb.diag, N.in, N.out, N.spart);
     k_st_omega<<<1, 32, 0, s>>>(N.spart, (int)nb, N.scal);
@@ -1234,6 +1642,15 @@ int nn_set_profile(nn_handle* h, int on) {
   }
   h->n.prof = on != 0;
   h->n.prof_n = 0;
+  return EB_OK;
+}
+
+int nn_set_fused(nn_handle* h, int on) {
+  if (!h) {
+    set_error("nn_set_fused: NULL handle");
+    return EB_ERR_INVALID;
+  }
+  h->n.fused = on != 0;
   return EB_OK;
 }
 
@@ -1322,9 +1739,9 @@ int nn_forward(nn_handle* h, int width, int height, int images, const float* in_
   return guarded([&] {
     NN& N = h->n;
     const Image im{width, height * images, height};
-    ensure_act(N, npx_of(im), stream);
+    if (!N.fused) ensure_act(N, npx_of(im), stream);
     int64_t nl = 0;
-    forward(N, im, reinterpret_cast<const float2*>(in_dev), out_dev, stream, nl);
+    forward_infer(N, im, reinterpret_cast<const float2*>(in_dev), out_dev, stream, nl);
   });
 }
 

@@ -86,7 +86,51 @@ def test_forward_parity(shape):
         assert _rel(out[k], refb) <= 4e-3, _rel(out[k], refb)
 
 
-def test_shift_network_exact():
+@pytest.mark.parametrize("shape", [(3, 37, 200), (1, 16, 64), (2, 9, 129), (1, 300, 470), (4, 1, 5),
+                                   (2, 2, 117), (1, 5, 1)])
+def test_fused_forward_matches_layered(shape):
+    """The one-launch forward (k_net_fwd) and the layer-by-layer launches give
+    bit-identical outputs: ragged strips (116 columns), several row runs per
+    image, stacked images, images smaller than a strip or a run's halo."""
+    eb = _pkg()
+    nimg, H, W = shape
+    s, m = _inputs(5, nimg, H, W)
+    inp = torch.from_numpy(np.stack([s, m], axis=-1).astype(np.float32)).cuda()
+    net = eb.Net(_params(4))
+    net.set_fused(True)
+    fused = net.forward(inp).clone()
+    net.status()
+    net.set_fused(False)
+    layered = net.forward(inp)
+    assert torch.equal(fused, layered), float((fused - layered).abs().max())
+
+
+def test_fused_forward_full_size_2048():
+    """The bench workload's image (2048^2, 8 row runs x 18 strips): fused and
+    layer-by-layer outputs bit-identical, and both agree with the oracle at
+    sampled pixels."""
+    eb = _pkg()
+    n = 2048
+    s, m = _inputs(6, 1, n, n)
+    inp = torch.from_numpy(np.stack([s, m], axis=-1).astype(np.float32)).cuda()
+    net = eb.Net(_params(7))
+    fused = net.forward(inp).clone()
+    net.set_fused(False)
+    layered = net.forward(inp)
+    assert torch.equal(fused, layered)
+    # oracle on a window around a strip corner (the network's receptive field is 6 pixels)
+    theta32 = _params(7).astype(np.float32).astype(np.float64)
+    r0, c0 = 250, 110  # a row-run boundary (256) and a strip boundary (116) inside the window
+    ws, wm = s[0, r0 - 6:r0 + 18, c0 - 6:c0 + 18], m[0, r0 - 6:r0 + 18, c0 - 6:c0 + 18]
+    ws = ws.astype(np.float32).astype(np.float64)
+    refb, _ = ocnn.forward(theta32, ws, wm, storage="bf16")
+    got = fused[0, r0:r0 + 12, c0:c0 + 12].double().cpu().numpy()
+    want = refb[6:18, 6:18]
+    assert _rel(got, want) <= 4e-3, _rel(got, want)
+
+
+@pytest.mark.parametrize("fused", [True, False])
+def test_shift_network_exact(fused):
     eb = _pkg()
     nimg, H, W = 2, 11, 150
     s, m = _inputs(3, nimg, H, W)
@@ -100,6 +144,7 @@ def test_shift_network_exact():
     layers[5] = (layers[5][0], np.array([0.25]))
     theta = ocnn.pack(layers)
     net = eb.Net(theta)
+    net.set_fused(fused)
     inp = torch.from_numpy(np.stack([s, m], axis=-1).astype(np.float32)).cuda()
     out = net.forward(inp).cpu().numpy().astype(np.float64)
     for k in range(nimg):
