@@ -420,49 +420,65 @@ __global__ void k_l6_fwd(Image im, const bf16* __restrict__ y5, const float* __r
 // step are independent.  Every layer computes 128 columns (the tensor cores'
 // M), the strip's 116 plus 6 on each side: layer l is exact on 128 - 2 (l - 1)
 // of them, which leaves layer 6 exact on the strip.
-//   * layer 1 (2 -> 32, CUDA cores, warps 4-7): one pixel per thread, the FMA
-//     order of k_l1_fwd; bf16 result into ring 0.
-//   * layers 2-5 (tcgen05, lane 0 of warp 8 + l - 2): 18 MMAs of 128 x 32 x 16
-//     per layer and step, A = three rows of ring l - 2 (64-byte swizzled
-//     K-major rows of 64 bytes, one per pixel, as k_conv32_tma's tensor copies
-//     lay them out), B = the layer's weights in shared memory, D = one of two
-//     TMEM accumulators per layer.
-//   * epilogues (warps 0-3, one TMEM lane = one pixel per thread): bias, ReLU,
-//     bf16, 0 outside the image (the next layer's zero padding); layers 2-4
-//     write ring l - 1 (the swizzle applied by hand), layer 5 forms the nine
-//     tap partials of layer 6 (a float per tap and pixel, ring T) from its
-//     bf16-rounded values, and layer 6 adds them up: out = m (b6 + sum).
-// Rings hold 4 rows (row rho in slot rho & 3): a step writes row rho + 2 of a
-// ring while the MMAs read rows rho - 1 .. rho + 1.  Every layer's arithmetic
-// is that of the layer-by-layer path (k_l1_fwd, k_conv32_tma, k_l6_fwd), so
-// the two give identical outputs.
+//   * layer 1 (2 -> 32, CUDA cores, warps 4-7): one pixel per thread, eight
+//     output channels' FMA chains side by side, each in k_l1_fwd's order;
+//     bf16 result into ring 0.  The input window is loaded a step ahead.
+//   * layers 2-5 (tcgen05, lane 0 of warp 8 + l - 2): the MMAs are input-row
+//     stationary.  At step tau layer l takes its newest input row, rho + 1
+//     (rho = the output row it finishes), from ring l - 2 (64-byte swizzled
+//     K-major rows of 64 bytes, one per pixel, as k_conv32_tma's tensor
+//     copies lay them out) and multiplies it, shifted by dx = 0, 1, 2 pixels
+//     and split in two channel halves, by the weights of the three tap rows
+//     at once: N = 96 = (dy, n), contributions to output rows rho + 2 - dy.
+//     Each output row accumulates in one of four 32-column TMEM slots per
+//     layer, placed so that rows rho + 2, rho + 1, rho lie at increasing
+//     columns; runs of adjacent slots take one MMA per (dx, kh), so a layer
+//     issues 6 MMAs per step (12 when the three slots wrap), a third of the
+//     18 of the output-stationary form.  The slot of row rho receives its taps
+//     in (dy, dx, kh) order, the order of k_conv32_tma's 18 MMAs, from zero.
+//   * epilogues of layers 2-4 (warps 0-3, one TMEM lane = one pixel per
+//     thread): read the finished slot of row rho and zero it for row rho + 4,
+//     bias, ReLU, bf16, 0 outside the image (the next layer's zero padding),
+//     into ring l - 1 (the swizzle applied by hand).
+//   * layers 5-6 (warps 12-15): layer 5's epilogue forms the nine tap
+//     partials of layer 6 (a float per tap and pixel, ring T) from its
+//     bf16-rounded values, nine FMA chains side by side; layer 6 adds them up:
+//     out = m (b6 + sum).
+// Activation rings hold 2 rows (row rho in slot rho & 1): a step reads row
+// rho + 1 of a ring and writes row rho + 2.  T holds 4.  Every layer's
+// arithmetic is that of the layer-by-layer path (k_l1_fwd, k_conv32_tma,
+// k_l6_fwd), so the two give identical outputs.
 // Barriers (mbarriers, two of each kind per layer, by step parity): rdy[j][b]
-// (ring j rows of step k written: 4 warp arrivals -> MMA of layer j + 2 at
+// (ring j row of step k written: 4 warp arrivals -> MMA of layer j + 2 at
 // step k + 1), mdone[j][b] (commit of layer j + 2's MMAs at step k ->
-// epilogue; mdone[0] also frees ring 0's oldest row for layer 1), tempty[j][b]
-// (accumulator drained: 4 warp arrivals -> MMA at step k + 2).  With two
-// barriers per kind no waiter can fall two phases behind.  The epilogue of
-// layer l at step k overwrites the row of ring l - 1 that layer l + 1's MMAs
-// read at step k - 1: the epilogue warps waited for those (mdone of layer
-// l + 1, step k - 1) earlier in their own program order.  Every wait is
+// epilogue; mdone[0] also frees ring 0's older row for layer 1), tempty[j][b]
+// (slot read and zeroed: 4 warp arrivals -> MMA at step k + 2, or k + 1 at a
+// unit's first step, after the last step of the unit before has cleared every
+// slot).  With two barriers per kind no waiter can fall two phases behind.
+// The epilogue of layer l at step k overwrites the row of ring l - 1 that
+// layer l + 1's MMAs read at step k - 1: for l = 2, 3 the epilogue warps
+// waited for those (mdone of layer l + 1, step k - 1) earlier in their own
+// program order, for l = 4 they wait for layer 5's explicitly.  Every wait is
 // bounded; one that gives up raises a shared abort flag, after which every
 // role runs its remaining steps without waiting or computing (so the named
-// barriers of the epilogue warps still match), the CTA waits (bounded) for its
-// MMAs in flight, frees TMEM and sets *err.
+// barriers still match), the CTA waits (bounded) for its MMAs in flight,
+// frees TMEM and sets *err.
 constexpr int FZ_OUT = TPX - 12;                       // 116
 constexpr int FZ_ROW = TC_PIX * NC * 2;                // 8320 bytes: one activation row, 130 pixel slots
-constexpr int FZ_RING = 4;                             // rows per ring
-constexpr int FZ_RINGB = FZ_RING * FZ_ROW;             // 33,280
-constexpr int FZ_W = 4 * FZ_RINGB;                     // weights of layers 2-5: 133,120
+constexpr int FZ_RING = 2;                             // rows per activation ring
+constexpr int FZ_RINGB = FZ_RING * FZ_ROW;             // 16,640
+constexpr int FZ_W = 4 * FZ_RINGB;                     // weights of layers 2-5: 66,560
+constexpr int FZ_WDX = 4 * 96 * 16;                    // B bytes of one horizontal tap: 6144
+constexpr int FZ_TRING = 4;                            // rows of the tap-partial ring
 constexpr int FZ_TROW = 9 * TC_PIX;                    // floats of a T row: 9 taps x 130 slots
-constexpr int FZ_T = FZ_W + NMID * TC_W;               // 206,848
-constexpr int FZ_W1 = FZ_T + FZ_RING * FZ_TROW * 4;    // 225,568: layer-1 weights, 20 per channel, + b1
-constexpr int FZ_W6 = FZ_W1 + (NC * 20 + NC) * 4;      // 228,256: W6, b6
-constexpr int FZ_BM = FZ_W6 + 1168;                    // 229,424: biases of layers 2-5
-constexpr int FZ_BAR = FZ_BM + NMID * NC * 4;          // 229,936
+constexpr int FZ_T = FZ_W + NMID * TC_W;               // 140,288
+constexpr int FZ_W1 = FZ_T + FZ_TRING * FZ_TROW * 4;   // 159,008: layer-1 weights [d][ci][co], then b1
+constexpr int FZ_W6 = FZ_W1 + (NC * 20 + NC) * 4;      // 161,696: W6 as [c][12 taps], then b6
+constexpr int FZ_BM = FZ_W6 + 1552;                    // 163,248: biases of layers 2-5
+constexpr int FZ_BAR = FZ_BM + NMID * NC * 4;          // 163,760
 constexpr int FZ_NBAR = 24;
-constexpr int FZ_SMEM = FZ_BAR + 8 * FZ_NBAR + 16;     // 230,144
-constexpr int FZ_THREADS = 384;                        // warps 0-3 epilogues, 4-7 layer 1, 8-11 MMAs
+constexpr int FZ_SMEM = FZ_BAR + 8 * FZ_NBAR + 16;     // 163,968
+constexpr int FZ_THREADS = 512;  // warps 0-3 epilogues 2-4, 4-7 layer 1, 8-11 MMAs, 12-15 layers 5-6
 static_assert(FZ_SMEM <= 232448, "fused forward: shared memory");
 static_assert(FZ_W % 1024 == 0 && FZ_T % 16 == 0 && FZ_BAR % 8 == 0, "fused forward: alignment");
 
@@ -487,6 +503,71 @@ __device__ __forceinline__ void fz_st_row(uint32_t row, const uint32_t (&w)[NC /
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(row + ((c ^ sw) << 4)), "r"(w[4 * c]),
                  "r"(w[4 * c + 1]), "r"(w[4 * c + 2]), "r"(w[4 * c + 3])
                  : "memory");
+}
+
+// tensor-memory column (within a layer's 128) of the accumulator of output row
+// r: four slots, r & 3 = 3, 2, 1, 0 at columns 0, 32, 64, 96, so that rows
+// r + 2, r + 1, r (which one input row feeds) lie at increasing columns
+__device__ __forceinline__ int fz_col(int r) { return 32 * (3 - (r & 3)); }
+
+// 32 zero columns of tensor memory at taddr for this warp's 32 lanes
+__device__ __forceinline__ void fz_tmem_zero32(uint32_t taddr) {
+  const uint32_t z = 0u;
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
+      "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
+      "r"(z)
+      : "memory");
+}
+
+// Reads the finished accumulator of output row rho of layer j + 2 (32 columns,
+// this warp's lanes; tlane = TMEM address of lane 32 (warp % 4), column 0)
+// into v, then starts zeroing its slot for row rho + 4 (all four slots of the
+// layer at a unit's last step, which leaves no partial sums to the next unit);
+// fz_release completes it.  okw (warp-uniform) false: nothing is read, v = 0.
+__device__ __forceinline__ void fz_take(uint32_t tlane, int j, int rho, bool okw, bool last, uint32_t (&v)[NC]) {
+  const uint32_t tacc = tlane + (uint32_t)(j * 128 + fz_col(rho));
+  if (okw) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+          "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(tacc));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (last) {
+      for (int c = 0; c < 128; c += 32) fz_tmem_zero32(tlane + (uint32_t)(j * 128 + c));
+    } else {
+      fz_tmem_zero32(tacc);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) v[c] = 0u;
+  }
+}
+
+// after fz_take: the zeroing stores are complete and the slot is released to
+// the MMAs (whose next write to it comes two steps on)
+__device__ __forceinline__ void fz_release(uint32_t tempty) {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tempty) : "memory");
+}
+
+// the 3 x 3 input window of pixel x in row tau of image img (0 outside the image)
+__device__ __forceinline__ void fz_window(const FzArgs& a, int img, int tau, int x, float2 (&v)[9]) {
+  const bool in = tau >= 0 && tau < a.im.R && x >= 0 && x < a.im.W;
+#pragma unroll
+  for (int d = 0; d < 9; ++d) {
+    const int xx = x + d % 3 - 1, rr = tau + d / 3 - 1;
+    v[d] = (in && xx >= 0 && xx < a.im.W && rr >= 0 && rr < a.im.R)
+               ? __ldg(a.in + ((int64_t)img * a.im.R + rr) * a.im.W + xx)
+               : make_float2(0.f, 0.f);
+  }
 }
 
 __device__ __forceinline__ void fz_unit(const FzArgs& a, int64_t u, int& img, int& r0, int& r1, int& x0) {
@@ -517,18 +598,27 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_net_fwd(const __grid_constant
 
   // rings and T start at 0 (slots 0 and 129 of every ring row stay 0)
   for (int i = tid; i < FZ_W / 16; i += FZ_THREADS) reinterpret_cast<int4*>(smem_raw)[i] = make_int4(0, 0, 0, 0);
-  for (int i = tid; i < FZ_RING * FZ_TROW; i += FZ_THREADS) sT[i] = 0.0f;
+  for (int i = tid; i < FZ_TRING * FZ_TROW; i += FZ_THREADS) sT[i] = 0.0f;
   for (int i = tid; i < NMID * 9 * NC * 4; i += FZ_THREADS) {  // B operands, as in k_conv32_tma
+    // [dx][channel group g][dy * 32 + n][8 k]: one horizontal tap's three tap rows side by side in N
     const int g = i & 3, n = (i >> 2) % NC, d = ((i >> 2) / NC) % 9, l = (i >> 2) / (NC * 9);
-    *reinterpret_cast<int4*>(smem_raw + FZ_W + l * TC_W + d * TC_WTAP + g * (NC * 16) + n * 16) =
+    const int dy = d / 3, dx = d % 3;
+    *reinterpret_cast<int4*>(smem_raw + FZ_W + l * TC_W + dx * FZ_WDX + g * (96 * 16) + (dy * NC + n) * 16) =
         *reinterpret_cast<const int4*>(a.wf + (int64_t)l * WM_N + (d * NC + n) * NC + g * 8);
   }
-  for (int i = tid; i < NC * 20; i += FZ_THREADS) {
-    const int co = i / 20, j = i % 20;
-    sW1[i] = j < 18 ? a.P[OFF_W1 + co * 18 + j] : 0.0f;
+  // layer 1: weight (tap d, input ci) of the 32 outputs contiguous, so that a
+  // thread feeds eight output channels' FMA chains from two float4 loads
+  for (int i = tid; i < 18 * NC; i += FZ_THREADS) {
+    const int co = i % NC, q = i / NC;
+    sW1[i] = a.P[OFF_W1 + co * 18 + q];
   }
-  for (int i = tid; i < NC; i += FZ_THREADS) sW1[NC * 20 + i] = a.P[OFF_W1 + W1_N + i];
-  for (int i = tid; i < W6_N + B6_N; i += FZ_THREADS) sW6[i] = a.P[OFF_W6 + i];
+  for (int i = tid; i < NC; i += FZ_THREADS) sW1[18 * NC + i] = a.P[OFF_W1 + W1_N + i];
+  // layer 6: the nine taps of input channel c contiguous (padded to 12)
+  for (int i = tid; i < NC * 12; i += FZ_THREADS) {
+    const int c = i / 12, d = i % 12;
+    sW6[i] = d < 9 ? a.P[OFF_W6 + d * NC + c] : 0.0f;
+  }
+  if (tid == 0) sW6[NC * 12] = a.P[OFF_W6 + W6_N];
   for (int i = tid; i < NMID * NC; i += FZ_THREADS) sBM[i] = a.P[off_wm(i / NC) + WM_N + i % NC];
   if (tid == 0) {
     for (int b = 0; b < FZ_NBAR; ++b) {
@@ -539,7 +629,7 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_net_fwd(const __grid_constant
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   if (warp == 8) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_addr(tslot)));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_addr(tslot)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("fence.proxy.async.shared::cta;");  // zeroed rings and weights are read by the tensor cores
@@ -547,13 +637,89 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_net_fwd(const __grid_constant
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tslot;
+  // every MMA accumulates: the output-row slots of tensor memory start at 0
+  if (warp < 4) {
+    for (int c = 0; c < 512; c += 32) fz_tmem_zero32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c);
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
 
-  if (warp >= 8) {
+  if (warp >= 12) {
+    // layer 5's epilogue, layer 6 and the tap partials (warps 12-15): thread t
+    // = TMEM lane t = pixel slot t + 1 (warp w reads lanes 32 (w - 12) ..)
+    const int t = tid - 384;
+    const uint32_t tlane = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    int64_t k = 0;
+    for (int64_t u = blockIdx.x; u < a.units; u += gridDim.x) {
+      int img, r0, r1, x0;
+      fz_unit(a, u, img, r0, r1, x0);
+      const int nsteps = r1 - r0 + 15;
+      const int x = x0 - 6 + t;
+      for (int st = 0; st < nsteps; ++st, ++k) {
+        const int tau = r0 - 5 + st;
+        // layer 6 writes row tau - 10 at the end of the step: its mask value now
+        const int r6 = tau - 10;
+        const bool out6 = r6 >= r0 && r6 < r1 && t >= 6 && t < 6 + FZ_OUT && x < im.W;
+        const int64_t p6 = ((int64_t)img * im.R + r6) * im.W + x;
+        const float m6 = out6 ? __ldg(a.in + p6).y : 0.0f;
+        // layer 5 (row tau - 8): its values, bf16-rounded as layer 6 reads them
+        const int j = NMID - 1, b = (int)(k & 1);
+        const bool okl = cp_wait(mdone(j, b), (uint32_t)(k >> 1) & 1u, abort) && !*abort;
+        const bool okw = __all_sync(0xffffffffu, okl);  // tcgen05.ld is warp-collective
+        const int rho = tau - 2 * (j + 1);
+        uint32_t v5[NC];
+        fz_take(tlane, j, rho, okw, st == nsteps - 1, v5);
+        const bool in_img = okw && rho >= 0 && rho < im.R && x >= 0 && x < im.W;
+        fz_release(tempty(j, b));
+        // layer 6 at row tau - 10 from the tap partials of earlier steps
+        asm volatile("bar.sync 2, 128;" ::: "memory");
+        if (!*abort && out6) {
+          float acc = sW6[NC * 12];
+#pragma unroll
+          for (int d = 0; d < 9; ++d) {
+            const int dy = d / 3, dx = d % 3;
+            acc = __fadd_rn(acc, sT[((r6 - 1 + dy) & 3) * FZ_TROW + d * TC_PIX + t + dx]);
+          }
+          a.out[p6] = m6 * acc;
+        }
+        asm volatile("bar.sync 2, 128;" ::: "memory");
+        // tap partials of layer 5's row rho
+        const float* bj = sBM + j * NC;
+        float f[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+          f[c] = in_img ? __bfloat162float(__float2bfloat16_rn(fmaxf(__uint_as_float(v5[c]) + bj[c], 0.0f))) : 0.0f;
+        // nine chains over c = 0 .. 31, side by side
+        float tsum[9];
+#pragma unroll
+        for (int d = 0; d < 9; ++d) tsum[d] = 0.0f;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const float4 wa = *reinterpret_cast<const float4*>(sW6 + c * 12);
+          const float4 wb = *reinterpret_cast<const float4*>(sW6 + c * 12 + 4);
+          const float wc = sW6[c * 12 + 8];
+          tsum[0] = __fmaf_rn(wa.x, f[c], tsum[0]);
+          tsum[1] = __fmaf_rn(wa.y, f[c], tsum[1]);
+          tsum[2] = __fmaf_rn(wa.z, f[c], tsum[2]);
+          tsum[3] = __fmaf_rn(wa.w, f[c], tsum[3]);
+          tsum[4] = __fmaf_rn(wb.x, f[c], tsum[4]);
+          tsum[5] = __fmaf_rn(wb.y, f[c], tsum[5]);
+          tsum[6] = __fmaf_rn(wb.z, f[c], tsum[6]);
+          tsum[7] = __fmaf_rn(wb.w, f[c], tsum[7]);
+          tsum[8] = __fmaf_rn(wc, f[c], tsum[8]);
+        }
+        float* tr = sT + (rho & 3) * FZ_TROW + t + 1;
+#pragma unroll
+        for (int d = 0; d < 9; ++d) tr[d * TC_PIX] = tsum[d];
+      }
+    }
+  } else if (warp >= 8) {
     // warp 8 + j issues the MMAs of layer j + 2 (ring j in): one issuing thread
     // per layer, so that the four layers' MMAs of a step overlap on the tensor
     // cores (an issuing thread waits out each MMA's operand fetch)
     if (lane == 0) {
-      constexpr uint32_t idesc = tc_idesc(128, NC);
       const int j = warp - 8;
       int64_t k = 0;
       uint32_t last_bar = 0, last_par = 0;
@@ -569,25 +735,43 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_net_fwd(const __grid_constant
               ok = false;
               break;
             }
-            if (k >= 2 && !cp_wait(tempty(j, b), (uint32_t)((k - 2) >> 1) & 1u, abort)) {
+            // slots are reused four rows later: the epilogue of step k - 2 has read and
+            // zeroed the slot written first here; the first step of a unit also waits
+            // for the step before, whose epilogue cleared the previous unit's slots
+            if (st == 0 && k >= 1) {
+              if (!cp_wait(tempty(j, (int)((k - 1) & 1)), (uint32_t)((k - 1) >> 1) & 1u, abort)) {
+                ok = false;
+                break;
+              }
+            } else if (k >= 2 && !cp_wait(tempty(j, b), (uint32_t)((k - 2) >> 1) & 1u, abort)) {
               ok = false;
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
+            // input row rho + 1 (the newest) enters output rows rho + 2, rho + 1 and
+            // rho (tap rows dy = 0, 1, 2): runs of those whose slots are adjacent
+            // in tensor memory take one MMA per (dx, kh), N = 32 x run length
             const int rho = tau - 2 * (j + 1);
-            const uint32_t ring = base + (uint32_t)(j * FZ_RINGB);
+            const uint32_t row = base + (uint32_t)(j * FZ_RINGB + ((rho + 1) & 1) * FZ_ROW);
+            const uint32_t wl = base + (uint32_t)(FZ_W + j * TC_W);
+            for (int dy = 0; dy < 3;) {
+              const int c0 = fz_col(rho + 2 - dy);
+              int n = 1;
+              while (dy + n < 3 && fz_col(rho + 2 - dy - n) == c0 + 32 * n) ++n;
+              const uint32_t idesc = tc_idesc(128, 32 * n);
 #pragma unroll 1
-            for (int q = 0; q < 18; ++q) {
-              const int d = q >> 1, kh = q & 1, dy = d / 3, dx = d % 3;
-              const uint32_t row = ring + (uint32_t)(((rho - 1 + dy) & 3) * FZ_ROW);
-              const uint64_t da = tc_desc_sw64(row + dx * 64 + kh * 32);
-              const uint64_t db =
-                  tc_desc(base + FZ_W + j * TC_W + d * TC_WTAP + (2 * kh) * (NC * 16), NC * 16, 128);
-              asm volatile(
-                  "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(
-                      tmem + (uint32_t)((2 * j + b) * NC)),
-                  "l"(da), "l"(db), "r"(idesc), "r"((uint32_t)(q > 0)));
+              for (int q = 0; q < 6; ++q) {
+                const int dx = q >> 1, kh = q & 1;
+                const uint64_t da = tc_desc_sw64(row + dx * 64 + kh * 32);
+                const uint64_t db =
+                    tc_desc(wl + (uint32_t)(dx * FZ_WDX + (2 * kh) * (96 * 16) + dy * NC * 16), 96 * 16, 128);
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(
+                        tmem + (uint32_t)(j * 128 + c0)),
+                    "l"(da), "l"(db), "r"(idesc), "r"(1u));
+              }
+              dy += n;
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              mdone(j, b))
@@ -611,54 +795,59 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_net_fwd(const __grid_constant
       fz_unit(a, u, img, r0, r1, x0);
       const int nsteps = r1 - r0 + 15;
       const int x = x0 - 6 + t;
+      float2 vn[9];
+      fz_window(a, img, r0 - 5, x, vn);
       for (int st = 0; st < nsteps; ++st, ++k) {
         const int tau = r0 - 5 + st;
+        // the input window of this step, loaded one step ahead; the next step's now
+        const bool l1_in = tau >= 0 && tau < im.R && x >= 0 && x < im.W;
+        float2 v[9];
+#pragma unroll
+        for (int d = 0; d < 9; ++d) v[d] = vn[d];
+        if (st + 1 < nsteps) fz_window(a, img, tau + 1, x, vn);
         bool ok = true;
         if (k >= 1) ok = cp_wait(mdone(0, (int)((k - 1) & 1)), (uint32_t)((k - 1) >> 1) & 1u, abort);
         uint32_t o[NC / 2];
 #pragma unroll
         for (int c = 0; c < NC / 2; ++c) o[c] = 0u;
-        if (ok && !*abort && tau >= 0 && tau < im.R && x >= 0 && x < im.W) {
-          float2 v[9];
+        if (ok && !*abort && l1_in) {
+          // eight output channels at a time, each one FMA chain in k_l1_fwd's order
 #pragma unroll
-          for (int d = 0; d < 9; ++d) {
-            const int xx = x + d % 3 - 1, rr = tau + d / 3 - 1;
-            v[d] = (xx >= 0 && xx < im.W && rr >= 0 && rr < im.R)
-                       ? __ldg(a.in + ((int64_t)img * im.R + rr) * im.W + xx)
-                       : make_float2(0.f, 0.f);
-          }
+          for (int cg = 0; cg < NC; cg += 8) {
+            float acc[8];
 #pragma unroll
-          for (int co = 0; co < NC; co += 2) {
-            float r2[2];
+            for (int q = 0; q < 8; ++q) acc[q] = sW1[18 * NC + cg + q];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const float* wc = sW1 + (co + h) * 20;
-              float acc = sW1[NC * 20 + co + h];
-#pragma unroll
-              for (int q = 0; q < 5; ++q) {
-                const float4 w4 = *reinterpret_cast<const float4*>(wc + 4 * q);
-                acc = __fmaf_rn(w4.x, v[2 * q].x, acc);
-                acc = __fmaf_rn(w4.y, v[2 * q].y, acc);
-                if (2 * q + 1 < 9) {
-                  acc = __fmaf_rn(w4.z, v[2 * q + 1].x, acc);
-                  acc = __fmaf_rn(w4.w, v[2 * q + 1].y, acc);
-                }
-              }
-              r2[h] = fmaxf(acc, 0.0f);
+            for (int e = 0; e < 18; ++e) {
+              const float4 wa = *reinterpret_cast<const float4*>(sW1 + e * NC + cg);
+              const float4 wb = *reinterpret_cast<const float4*>(sW1 + e * NC + cg + 4);
+              const float xv = (e & 1) ? v[e >> 1].y : v[e >> 1].x;
+              acc[0] = __fmaf_rn(wa.x, xv, acc[0]);
+              acc[1] = __fmaf_rn(wa.y, xv, acc[1]);
+              acc[2] = __fmaf_rn(wa.z, xv, acc[2]);
+              acc[3] = __fmaf_rn(wa.w, xv, acc[3]);
+              acc[4] = __fmaf_rn(wb.x, xv, acc[4]);
+              acc[5] = __fmaf_rn(wb.y, xv, acc[5]);
+              acc[6] = __fmaf_rn(wb.z, xv, acc[6]);
+              acc[7] = __fmaf_rn(wb.w, xv, acc[7]);
             }
-            const __nv_bfloat162 hv = __floats2bfloat162_rn(r2[0], r2[1]);
-            o[co / 2] = *reinterpret_cast<const uint32_t*>(&hv);
+#pragma unroll
+            for (int q = 0; q < 8; q += 2) {
+              const __nv_bfloat162 hv = __floats2bfloat162_rn(fmaxf(acc[q], 0.0f), fmaxf(acc[q + 1], 0.0f));
+              o[(cg + q) / 2] = *reinterpret_cast<const uint32_t*>(&hv);
+            }
           }
         }
-        fz_st_row(base + (uint32_t)((tau & 3) * FZ_ROW + (t + 1) * 64), o);
+        fz_st_row(base + (uint32_t)((tau & 1) * FZ_ROW + (t + 1) * 64), o);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(rdy(0, (int)(k & 1))) : "memory");
       }
     }
   } else {
-    // epilogues of layers 2-5 and layer 6: thread i = TMEM lane i = pixel slot i + 1
+    // epilogues of layers 2-4 (warps 0-3): thread i = TMEM lane i = pixel slot i + 1
     const int i = tid;
+    const uint32_t tlane = tmem + ((uint32_t)(warp * 32) << 16);
     int64_t k = 0;
     for (int64_t u = blockIdx.x; u < a.units; u += gridDim.x) {
       int img, r0, r1, x0;
@@ -667,76 +856,33 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_net_fwd(const __grid_constant
       const int x = x0 - 6 + i;
       for (int st = 0; st < nsteps; ++st, ++k) {
         const int tau = r0 - 5 + st, b = (int)(k & 1);
-        for (int j = 0; j < NMID; ++j) {
+#pragma unroll 1
+        for (int j = 0; j < NMID - 1; ++j) {
           const bool okl = cp_wait(mdone(j, b), (uint32_t)(k >> 1) & 1u, abort) && !*abort;
           const bool okw = __all_sync(0xffffffffu, okl);  // tcgen05.ld is warp-collective
-          uint32_t v[NC];
-          if (okw) {
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
-                "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((2 * j + b) * NC)));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          } else {
-#pragma unroll
-            for (int c = 0; c < NC; ++c) v[c] = 0u;
-          }
-          asm volatile("tcgen05.fence::before_thread_sync;");
-          __syncwarp();
-          if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tempty(j, b)) : "memory");
           const int rho = tau - 2 * (j + 1);
+          uint32_t v[NC];
+          fz_take(tlane, j, rho, okw, st == nsteps - 1, v);
+          fz_release(tempty(j, b));
           const bool in_img = okw && rho >= 0 && rho < im.R && x >= 0 && x < im.W;
           const float* bj = sBM + j * NC;
-          if (j < NMID - 1) {
-            uint32_t o[NC / 2];
+          uint32_t o[NC / 2];
 #pragma unroll
-            for (int c = 0; c < NC; c += 2) {
-              const float f0 = in_img ? fmaxf(__uint_as_float(v[c]) + bj[c], 0.0f) : 0.0f;
-              const float f1 = in_img ? fmaxf(__uint_as_float(v[c + 1]) + bj[c + 1], 0.0f) : 0.0f;
-              const __nv_bfloat162 hv = __floats2bfloat162_rn(f0, f1);
-              o[c / 2] = *reinterpret_cast<const uint32_t*>(&hv);
-            }
-            fz_st_row(base + (uint32_t)((j + 1) * FZ_RINGB + (rho & 3) * FZ_ROW + (i + 1) * 64), o);
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncwarp();
-            if (lane == 0)
-              asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(rdy(j + 1, b)) : "memory");
-          } else {
-            // layer 6 at row tau - 10 from the tap partials of earlier steps
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-            const int r6 = tau - 10;
-            if (!*abort && r6 >= r0 && r6 < r1 && i >= 6 && i < 6 + FZ_OUT && x < im.W) {
-              float acc = sW6[W6_N];
-#pragma unroll
-              for (int d = 0; d < 9; ++d) {
-                const int dy = d / 3, dx = d % 3;
-                acc = __fadd_rn(acc, sT[((r6 - 1 + dy) & 3) * FZ_TROW + d * TC_PIX + i + dx]);
-              }
-              const int64_t p = ((int64_t)img * im.R + r6) * im.W + x;
-              a.out[p] = __ldg(a.in + p).y * acc;
-            }
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-            // tap partials of layer 5's row rho (bf16-rounded values, as layer 6 reads them)
-            float f[NC];
-#pragma unroll
-            for (int c = 0; c < NC; ++c)
-              f[c] = in_img ? __bfloat162float(__float2bfloat16_rn(fmaxf(__uint_as_float(v[c]) + bj[c], 0.0f)))
-                            : 0.0f;
-            float* tr = sT + (rho & 3) * FZ_TROW + i + 1;
-#pragma unroll
-            for (int d = 0; d < 9; ++d) {
-              float tsum = 0.0f;
-#pragma unroll
-              for (int c = 0; c < NC; ++c) tsum = __fmaf_rn(sW6[d * NC + c], f[c], tsum);
-              tr[d * TC_PIX] = tsum;
-            }
+          for (int c = 0; c < NC; c += 2) {
+            const float f0 = in_img ? fmaxf(__uint_as_float(v[c]) + bj[c], 0.0f) : 0.0f;
+            const float f1 = in_img ? fmaxf(__uint_as_float(v[c + 1]) + bj[c + 1], 0.0f) : 0.0f;
+            const __nv_bfloat162 hv = __floats2bfloat162_rn(f0, f1);
+            o[c / 2] = *reinterpret_cast<const uint32_t*>(&hv);
           }
+          // the row overwritten here was read by layer j + 3's MMAs of the step
+          // before: layers 3 and 4 were waited for above at that step, layer 5's
+          // completion (waited by warps 4-7) is waited for here
+          if (j == NMID - 2 && k >= 1)
+            cp_wait(mdone(NMID - 1, (int)((k - 1) & 1)), (uint32_t)((k - 1) >> 1) & 1u, abort);
+          fz_st_row(base + (uint32_t)((j + 1) * FZ_RINGB + (rho & 1) * FZ_ROW + (i + 1) * 64), o);
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(rdy(j + 1, b)) : "memory");
         }
       }
     }
@@ -746,7 +892,7 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_net_fwd(const __grid_constant
   if (tid == 0 && *abort) atomicExch(a.err, 1);
   if (warp == 8) {
     asm volatile("tcgen05.fence::after_thread_sync;");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
   }
 }
 
