@@ -505,6 +505,38 @@ __device__ __forceinline__ void fz_st_row(uint32_t row, const uint32_t (&w)[NC /
                  : "memory");
 }
 
+// Bounded wait of the fused kernel: the waiting thread asks to be suspended
+// (up to 20 us per try) until the phase completes, so that spinning warps do
+// not take issue slots from the working ones on the same scheduler; gives up
+// after FZ_WAIT_NS of wall time (global timer) or when *abort is raised,
+// raising it itself on the time limit.
+constexpr uint64_t FZ_WAIT_NS = 200000000ull;  // 0.2 s
+__device__ __forceinline__ uint64_t fz_now() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool fz_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+  uint64_t t0 = 0;
+  for (uint32_t it = 0; it < (1u << 26); ++it) {  // the iteration bound backs up the time limit
+    uint32_t ok = 0;
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2, 20000;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (it == 0) t0 = fz_now();
+    if ((it & 15) == 15) {
+      if (*abort) return false;
+      if (fz_now() - t0 > FZ_WAIT_NS) break;
+    }
+  }
+  *abort = 1;
+  return false;
+}
+
 // tensor-memory column (within a layer's 128) of the accumulator of output row
 // r: four slots, r & 3 = 3, 2, 1, 0 at columns 0, 32, 64, 96, so that rows
 // r + 2, r + 1, r (which one input row feeds) lie at increasing columns
@@ -666,7 +698,7 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_net_fwd(const __grid_constant
         const float m6 = out6 ? __ldg(a.in + p6).y : 0.0f;
         // layer 5 (row tau - 8): its values, bf16-rounded as layer 6 reads them
         const int j = NMID - 1, b = (int)(k & 1);
-        const bool okl = cp_wait(mdone(j, b), (uint32_t)(k >> 1) & 1u, abort) && !*abort;
+        const bool okl = fz_wait(mdone(j, b), (uint32_t)(k >> 1) & 1u, abort) && !*abort;
         const bool okw = __all_sync(0xffffffffu, okl);  // tcgen05.ld is warp-collective
         const int rho = tau - 2 * (j + 1);
         uint32_t v5[NC];
@@ -731,7 +763,7 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_net_fwd(const __grid_constant
         for (int st = 0; st < nsteps && ok; ++st, ++k) {
           const int tau = r0 - 5 + st, b = (int)(k & 1);
           {
-            if (k >= 1 && !cp_wait(rdy(j, (int)((k - 1) & 1)), (uint32_t)((k - 1) >> 1) & 1u, abort)) {
+            if (k >= 1 && !fz_wait(rdy(j, (int)((k - 1) & 1)), (uint32_t)((k - 1) >> 1) & 1u, abort)) {
               ok = false;
               break;
             }
@@ -739,11 +771,11 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_net_fwd(const __grid_constant
             // zeroed the slot written first here; the first step of a unit also waits
             // for the step before, whose epilogue cleared the previous unit's slots
             if (st == 0 && k >= 1) {
-              if (!cp_wait(tempty(j, (int)((k - 1) & 1)), (uint32_t)((k - 1) >> 1) & 1u, abort)) {
+              if (!fz_wait(tempty(j, (int)((k - 1) & 1)), (uint32_t)((k - 1) >> 1) & 1u, abort)) {
                 ok = false;
                 break;
               }
-            } else if (k >= 2 && !cp_wait(tempty(j, b), (uint32_t)((k - 2) >> 1) & 1u, abort)) {
+            } else if (k >= 2 && !fz_wait(tempty(j, b), (uint32_t)((k - 2) >> 1) & 1u, abort)) {
               ok = false;
               break;
             }
@@ -783,7 +815,7 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_net_fwd(const __grid_constant
       }
       if (last_bar) {  // the last commit covers every MMA this thread issued: they finish before TMEM is freed
         volatile int never = 0;
-        cp_wait(last_bar, last_par, &never);
+        fz_wait(last_bar, last_par, &never);
       }
     }
   } else if (warp >= 4) {
@@ -806,7 +838,7 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_net_fwd(const __grid_constant
         for (int d = 0; d < 9; ++d) v[d] = vn[d];
         if (st + 1 < nsteps) fz_window(a, img, tau + 1, x, vn);
         bool ok = true;
-        if (k >= 1) ok = cp_wait(mdone(0, (int)((k - 1) & 1)), (uint32_t)((k - 1) >> 1) & 1u, abort);
+        if (k >= 1) ok = fz_wait(mdone(0, (int)((k - 1) & 1)), (uint32_t)((k - 1) >> 1) & 1u, abort);
         uint32_t o[NC / 2];
 #pragma unroll
         for (int c = 0; c < NC / 2; ++c) o[c] = 0u;
@@ -858,7 +890,7 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_net_fwd(const __grid_constant
         const int tau = r0 - 5 + st, b = (int)(k & 1);
 #pragma unroll 1
         for (int j = 0; j < NMID - 1; ++j) {
-          const bool okl = cp_wait(mdone(j, b), (uint32_t)(k >> 1) & 1u, abort) && !*abort;
+          const bool okl = fz_wait(mdone(j, b), (uint32_t)(k >> 1) & 1u, abort) && !*abort;
           const bool okw = __all_sync(0xffffffffu, okl);  // tcgen05.ld is warp-collective
           const int rho = tau - 2 * (j + 1);
           uint32_t v[NC];
@@ -878,7 +910,7 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_net_fwd(const __grid_constant
           // before: layers 3 and 4 were waited for above at that step, layer 5's
           // completion (waited by warps 4-7) is waited for here
           if (j == NMID - 2 && k >= 1)
-            cp_wait(mdone(NMID - 1, (int)((k - 1) & 1)), (uint32_t)((k - 1) >> 1) & 1u, abort);
+            fz_wait(mdone(NMID - 1, (int)((k - 1) & 1)), (uint32_t)((k - 1) >> 1) & 1u, abort);
           fz_st_row(base + (uint32_t)((j + 1) * FZ_RINGB + (rho & 1) * FZ_ROW + (i + 1) * 64), o);
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           __syncwarp();
