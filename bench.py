@@ -13,7 +13,8 @@ poisson2d  2D Poisson, plain FP64 AMG-PCG: circle R = 0.5 at (0.02, 0.01),
 wave       Leapfrog wave equation on the star r = 0.5 + 0.1 sin(5 phi), 4096^2
            nodes, dt = 0.9 of the periodic CFL limit, 10,000 steps from a
            seeded Gaussian pulse; one step = the whole 10,000-step run in FP32
-           (one persistent launch), FP64 timed beside it.
+           (one wave_step call: cached CUDA graphs of one launch per time
+           step), FP64 timed beside it.
 batched    64 seeded stars on grids from 128^2 to 1024^2, backward-Euler heat
            with dt = h, 50 steps of all 64 geometries per bench step (one
            batch_heat_step per time step, forcing and boundary data frozen at
