@@ -131,6 +131,7 @@ class ClockSampler:
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        self.q = q
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
@@ -148,6 +149,19 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
             self.f.close()
+            # a timed region shorter than nvidia-smi's start-up leaves no sample:
+            # take one right at its end (the clocks have not left the load state)
+            self.at_end = False
+            if not any(len(line.split(",")) >= 9 for line in open(self.path)):
+                try:
+                    out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.q}",
+                                          "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                         timeout=20).stdout
+                    with open(self.path, "a") as f:
+                        f.write(out)
+                    self.at_end = True
+                except (OSError, subprocess.TimeoutExpired):
+                    pass
 
     def summary(self):
         if self.proc is None or not os.path.exists(self.path):
@@ -166,8 +180,11 @@ class ClockSampler:
             for nm, v in zip(names, f[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+               "reasons": sorted(reasons), "samples": len(sm)}
+        if getattr(self, "at_end", False):
+            out["sampled"] = "once, right after the timed region (shorter than nvidia-smi's sampling start-up)"
+        return out
 
 
 # ---------------------------------------------------------------- workloads
