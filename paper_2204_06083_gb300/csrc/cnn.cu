@@ -15,7 +15,10 @@
 // the same kernel with flipped, transposed weights and the ReLU mask of the
 // layer input applied in its epilogue; weight gradients are GEMMs over pixels
 // (mma.sync fragments) with per-CTA partials summed in a fixed order.  The
-// 2 -> 32 and 32 -> 1 layers run on the CUDA cores.
+// 2 -> 32 and 32 -> 1 layers run on the CUDA cores.  Inference (nn_forward,
+// the stage in the PCG) runs all six layers in one launch instead
+// (k_net_fwd), with the hidden activations kept in shared memory and tensor
+// memory and results identical to the layer-by-layer launches.
 #include "eb_solver.cuh"
 #include "tma.cuh"
 
