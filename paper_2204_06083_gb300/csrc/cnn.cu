@@ -593,6 +593,27 @@ __device__ __forceinline__ void fz_release(uint32_t tempty) {
   if ((threadIdx.x & 31) == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tempty) : "memory");
 }
 
+// Packed FP32 pairs: fma.rn.f32x2 is two round-to-nearest FMAs in one
+// instruction, so each lane's result is the scalar __fmaf_rn's while the
+// fused kernel's CUDA-core layers issue half the FMA instructions.
+__device__ __forceinline__ uint64_t fz_pk(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void fz_upk(uint64_t v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ void fz_fma2(uint64_t& acc, uint64_t w, uint64_t x) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(w), "l"(x));
+}
+// (a0 + b0, a1 + b1), each rounded to nearest as a scalar addition
+__device__ __forceinline__ void fz_add2(float a0, float a1, float b0, float b1, float& r0, float& r1) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(fz_pk(a0, a1)), "l"(fz_pk(b0, b1)));
+  fz_upk(r, r0, r1);
+}
+
 // the 3 x 3 input window of pixel x in row tau of image img (0 outside the image)
 __device__ __forceinline__ void fz_window(const FzArgs& a, int img, int tau, int x, float2 (&v)[9]) {
   const bool in = tau >= 0 && tau < a.im.R && x >= 0 && x < a.im.W;
@@ -724,30 +745,38 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_net_fwd(const __grid_constant
         const float* bj = sBM + j * NC;
         float f[NC];
 #pragma unroll
-        for (int c = 0; c < NC; ++c)
-          f[c] = in_img ? __bfloat162float(__float2bfloat16_rn(fmaxf(__uint_as_float(v5[c]) + bj[c], 0.0f))) : 0.0f;
-        // nine chains over c = 0 .. 31, side by side
-        float tsum[9];
+        for (int c = 0; c < NC; c += 2) {
+          float s0, s1;
+          fz_add2(__uint_as_float(v5[c]), __uint_as_float(v5[c + 1]), bj[c], bj[c + 1], s0, s1);
+          f[c] = in_img ? __bfloat162float(__float2bfloat16_rn(fmaxf(s0, 0.0f))) : 0.0f;
+          f[c + 1] = in_img ? __bfloat162float(__float2bfloat16_rn(fmaxf(s1, 0.0f))) : 0.0f;
+        }
+        // nine chains over c = 0 .. 31, side by side (taps in pairs)
+        uint64_t tp[4];
 #pragma unroll
-        for (int d = 0; d < 9; ++d) tsum[d] = 0.0f;
+        for (int q = 0; q < 4; ++q) tp[q] = fz_pk(0.0f, 0.0f);
+        float t8 = 0.0f;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           const float4 wa = *reinterpret_cast<const float4*>(sW6 + c * 12);
           const float4 wb = *reinterpret_cast<const float4*>(sW6 + c * 12 + 4);
           const float wc = sW6[c * 12 + 8];
-          tsum[0] = __fmaf_rn(wa.x, f[c], tsum[0]);
-          tsum[1] = __fmaf_rn(wa.y, f[c], tsum[1]);
-          tsum[2] = __fmaf_rn(wa.z, f[c], tsum[2]);
-          tsum[3] = __fmaf_rn(wa.w, f[c], tsum[3]);
-          tsum[4] = __fmaf_rn(wb.x, f[c], tsum[4]);
-          tsum[5] = __fmaf_rn(wb.y, f[c], tsum[5]);
-          tsum[6] = __fmaf_rn(wb.z, f[c], tsum[6]);
-          tsum[7] = __fmaf_rn(wb.w, f[c], tsum[7]);
-          tsum[8] = __fmaf_rn(wc, f[c], tsum[8]);
+          const uint64_t f2 = fz_pk(f[c], f[c]);
+          fz_fma2(tp[0], fz_pk(wa.x, wa.y), f2);
+          fz_fma2(tp[1], fz_pk(wa.z, wa.w), f2);
+          fz_fma2(tp[2], fz_pk(wb.x, wb.y), f2);
+          fz_fma2(tp[3], fz_pk(wb.z, wb.w), f2);
+          t8 = __fmaf_rn(wc, f[c], t8);
         }
         float* tr = sT + (rho & 3) * FZ_TROW + t + 1;
 #pragma unroll
-        for (int d = 0; d < 9; ++d) tr[d * TC_PIX] = tsum[d];
+        for (int q = 0; q < 4; ++q) {
+          float ta, tb;
+          fz_upk(tp[q], ta, tb);
+          tr[(2 * q) * TC_PIX] = ta;
+          tr[(2 * q + 1) * TC_PIX] = tb;
+        }
+        tr[8 * TC_PIX] = t8;
       }
     }
   } else if (warp >= 8) {
@@ -849,27 +878,26 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_net_fwd(const __grid_constant
           // eight output channels at a time, each one FMA chain in k_l1_fwd's order
 #pragma unroll
           for (int cg = 0; cg < NC; cg += 8) {
-            float acc[8];
+            uint64_t acc[4];  // channel pairs (cg + 2q, cg + 2q + 1)
 #pragma unroll
-            for (int q = 0; q < 8; ++q) acc[q] = sW1[18 * NC + cg + q];
+            for (int q = 0; q < 4; ++q) acc[q] = fz_pk(sW1[18 * NC + cg + 2 * q], sW1[18 * NC + cg + 2 * q + 1]);
 #pragma unroll
             for (int e = 0; e < 18; ++e) {
               const float4 wa = *reinterpret_cast<const float4*>(sW1 + e * NC + cg);
               const float4 wb = *reinterpret_cast<const float4*>(sW1 + e * NC + cg + 4);
               const float xv = (e & 1) ? v[e >> 1].y : v[e >> 1].x;
-              acc[0] = __fmaf_rn(wa.x, xv, acc[0]);
-              acc[1] = __fmaf_rn(wa.y, xv, acc[1]);
-              acc[2] = __fmaf_rn(wa.z, xv, acc[2]);
-              acc[3] = __fmaf_rn(wa.w, xv, acc[3]);
-              acc[4] = __fmaf_rn(wb.x, xv, acc[4]);
-              acc[5] = __fmaf_rn(wb.y, xv, acc[5]);
-              acc[6] = __fmaf_rn(wb.z, xv, acc[6]);
-              acc[7] = __fmaf_rn(wb.w, xv, acc[7]);
+              const uint64_t x2 = fz_pk(xv, xv);
+              fz_fma2(acc[0], fz_pk(wa.x, wa.y), x2);
+              fz_fma2(acc[1], fz_pk(wa.z, wa.w), x2);
+              fz_fma2(acc[2], fz_pk(wb.x, wb.y), x2);
+              fz_fma2(acc[3], fz_pk(wb.z, wb.w), x2);
             }
 #pragma unroll
-            for (int q = 0; q < 8; q += 2) {
-              const __nv_bfloat162 hv = __floats2bfloat162_rn(fmaxf(acc[q], 0.0f), fmaxf(acc[q + 1], 0.0f));
-              o[(cg + q) / 2] = *reinterpret_cast<const uint32_t*>(&hv);
+            for (int q = 0; q < 4; ++q) {
+              float a0, a1;
+              fz_upk(acc[q], a0, a1);
+              const __nv_bfloat162 hv = __floats2bfloat162_rn(fmaxf(a0, 0.0f), fmaxf(a1, 0.0f));
+              o[cg / 2 + q] = *reinterpret_cast<const uint32_t*>(&hv);
             }
           }
         }
@@ -904,8 +932,10 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_net_fwd(const __grid_constant
           uint32_t o[NC / 2];
 #pragma unroll
           for (int c = 0; c < NC; c += 2) {
-            const float f0 = in_img ? fmaxf(__uint_as_float(v[c]) + bj[c], 0.0f) : 0.0f;
-            const float f1 = in_img ? fmaxf(__uint_as_float(v[c + 1]) + bj[c + 1], 0.0f) : 0.0f;
+            float s0, s1;
+            fz_add2(__uint_as_float(v[c]), __uint_as_float(v[c + 1]), bj[c], bj[c + 1], s0, s1);
+            const float f0 = in_img ? fmaxf(s0, 0.0f) : 0.0f;
+            const float f1 = in_img ? fmaxf(s1, 0.0f) : 0.0f;
             const __nv_bfloat162 hv = __floats2bfloat162_rn(f0, f1);
             o[c / 2] = *reinterpret_cast<const uint32_t*>(&hv);
           }
